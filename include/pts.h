@@ -1,0 +1,236 @@
+/*
+ * pts.h -- C ABI of the GB300 (sm_103a) library for perspective texture
+ * synthesis by energy optimisation (Bashir & Ghouri, arXiv:2006.11851).
+ *
+ * The library implements the hot path of the method's optimisation stage:
+ *   - the search phase (E-step, section 2.1 and Eq. 4): every output
+ *     neighbourhood on the 2x2-patch grid (section 2.2) is matched to its
+ *     nearest exemplar neighbourhood, searched after PCA reduction
+ *     (section 2.2);
+ *   - the optimization phase (M-step, Eq. 8 minimised over x): output pixels
+ *     become the weighted mean of the matched windows that cover them, with
+ *     IRLS weights W_p = ||x_p - z_p||^(r-2) (Eqs. 5-7);
+ *   - the coarse-to-fine driver (section 2.1).
+ *
+ * Conventions used by every entry point:
+ *   images     float32, H x W x 3, row-major, channel fastest (HWC), DEVICE
+ *              memory owned by the caller;
+ *   window     the w x w block whose top-left pixel is (y0, x0); vector
+ *              element (dy, dx, c) is number (dy*w + dx)*3 + c; D = 3 w^2;
+ *   exemplar   windows at every stride-1 origin inside the exemplar:
+ *              N = (He-w+1)(We-w+1), index n = y*(We-w+1) + x;
+ *   queries    output windows whose origins lie on the stride grid
+ *              y0 in {0, s, ..., Ho-w}: Q = ((Ho-w)/s+1)((Wo-w)/s+1),
+ *              index q = (y0/s)*((Wo-w)/s+1) + x0/s.  (Ho-w) and (Wo-w) must
+ *              be multiples of s, and w a multiple of s, so that every pixel
+ *              is covered and all pixels of an s x s patch share one covering
+ *              set;
+ *   streams    every call is asynchronous on `stream` (a cudaStream_t, NULL =
+ *              legacy default stream) unless its comment says it synchronises;
+ *   errors     a call returns PTS_OK or a negative pts_status.  Argument
+ *              errors are detected on the host before anything is launched.
+ *              Device-side checks (index bounds, bounded waits) set a status
+ *              word in the index; synchronising calls return it as
+ *              PTS_ERR_DEVICE / PTS_ERR_TIMEOUT, and pts_index_device_status
+ *              reads it.  pts_last_error() gives a thread-local message.
+ *   threading  an index must not be used by two host threads at once.
+ */
+#ifndef PTS_H
+#define PTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PTS_OK = 0,
+    PTS_ERR_INVALID_ARG = -1, /* bad size, pointer, mode or grid */
+    PTS_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    PTS_ERR_OOM = -3,         /* device allocation failed */
+    PTS_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    PTS_ERR_UNSUPPORTED = -6, /* valid request this build does not support */
+    PTS_ERR_DEVICE = -7       /* a device-side check failed (see message) */
+} pts_status;
+
+/* Search modes of the E-step.
+ *   PTS_EXACT_F32     the full-dimension nearest neighbour of Eq. 4.  PCA
+ *                     coordinates plus the residual norm give a lower bound
+ *                     on every full-dimension distance; the 32 best bounds
+ *                     are re-ranked in full dimension and certified, and
+ *                     uncertified queries get a second, bound-pruned exact
+ *                     pass.  FP32 SIMT, no tensor cores.
+ *   PTS_BF16_RERANK   PCA-space distances as a BF16 tensor-core GEMM (FP32
+ *                     accumulate), top-32, exact FP32 full-dimension re-rank.
+ *   PTS_FP8_RERANK    as BF16 with FP8-E4M3 operands and per-dimension scales.
+ *   PTS_PROPOSAL_BF16 learned cluster proposal + BF16 probe + re-rank, with
+ *                     the exact search as fallback. */
+typedef enum {
+    PTS_EXACT_F32 = 0,
+    PTS_BF16_RERANK = 1,
+    PTS_FP8_RERANK = 2,
+    PTS_PROPOSAL_BF16 = 3
+} pts_mode;
+
+typedef struct pts_index_s *pts_index; /* opaque, owned by the library */
+
+typedef struct {
+    int d;           /* PCA dimensions, 1..64; <= 0: smallest d whose retained
+                        variance reaches var_frac (section 2.2 keeps 95%),
+                        capped at 64 */
+    double var_frac; /* used when d <= 0 */
+    int max_iters;   /* eigen-solver iteration cap (0 = 200) */
+} pts_index_params;
+
+typedef struct {
+    int He, We, w, D, N, d;
+    int da;                  /* search vector length: d coordinates + residual, padded to 4 */
+    double var_retained;     /* sum of the d eigenvalues / trace of the covariance */
+    double eig_top;          /* largest eigenvalue */
+    int eig_iters;           /* subspace iterations used */
+    float unorm2_max;        /* max_n ||v_n - mu||^2 over exemplar windows */
+} pts_index_info;
+
+typedef struct {
+    long long queries;        /* queries of the last nn_search */
+    long long certified;      /* exact mode: certified from the 32 best bounds */
+    long long range_queries;  /* exact mode: queries sent to the pruned pass */
+    long long range_pairs;    /* exact mode: full-dimension pairs evaluated there */
+    long long brute_queries;  /* exact mode: queries that needed a full scan */
+} pts_search_stats;
+
+/* Message describing the last error on this host thread ("" if none). */
+const char *pts_last_error(void);
+
+/* Library version string. */
+const char *pts_version(void);
+
+/*
+ * pca_fit -- PCA of the exemplar's neighbourhood vectors (section 2.2: the
+ * search runs on PCA-reduced vectors; the paper keeps 95% of the variance).
+ *   mu    = (1/N) sum_n v_n,  Sigma = (1/N) sum_n (v_n - mu)(v_n - mu)^T,
+ * both accumulated in FP64 on the GPU; the top-d eigenpairs of Sigma come
+ * from FP64 subspace iteration with Rayleigh-Ritz steps solved by Jacobi.
+ * exemplar    device, He x We x 3 float32.
+ * d           1..64, or <= 0 to choose the smallest d reaching var_frac.
+ * mean_out    device, D float32 (may be NULL).
+ * basis_out   device, d x D float32, row j = unit eigenvector j (eigenvalues
+ *             descending); must hold 64 x D floats when d <= 0.
+ * eigvals_out device, d float64 (may be NULL).
+ * d_out       host int receiving the d used (may be NULL).
+ * Synchronises `stream`.  Errors: INVALID_ARG if w > He or We, d > min(D, N-1).
+ */
+pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double var_frac,
+                   float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream);
+
+/*
+ * build_exemplar_index -- everything the search needs about one exemplar and
+ * window width: a device copy of the exemplar, the PCA (as pca_fit), and the
+ * projected exemplar windows y_n = B^T(v_n - mu) with their residual norms
+ * ||(I - B B^T)(v_n - mu)|| and squared norms ||v_n - mu||^2 (section 2.2).
+ * exemplar is a device pointer; the index keeps its own copy, so the caller
+ * may free it afterwards.  Synchronises `stream`.  *out receives a new index
+ * (release it with pts_index_destroy).
+ */
+pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
+                                const pts_index_params *params, void *stream, pts_index *out);
+
+/* Frees an index and all its device memory (NULL is ignored).  Synchronises
+ * the device. */
+void pts_index_destroy(pts_index index);
+
+/* Fills *info (host) with the index's sizes and PCA summary. */
+pts_status pts_index_get_info(pts_index index, pts_index_info *info);
+
+/* Reads and clears the index's device status word (synchronises `stream`).
+ * Returns PTS_OK, PTS_ERR_DEVICE or PTS_ERR_TIMEOUT. */
+pts_status pts_index_device_status(pts_index index, void *stream);
+
+/*
+ * nn_search -- the search phase (E-step, Eq. 4): for every query window of
+ * `output` (device, Ho x Wo x 3 float32) on the stride grid, the index n of
+ * its nearest exemplar window and the squared full-dimension distance
+ * ||x_p - z_n||^2 computed in FP32 from the pixels.
+ * nn_out     device, Q int32.   dist2_out  device, Q float32.
+ * Ties within FP32 rounding may resolve to either window; exact ties go to
+ * the smallest n.  Asynchronous; uses workspace owned by the index.
+ */
+pts_status nn_search(pts_index index, const float *output, int Ho, int Wo, int stride, int mode,
+                     int32_t *nn_out, float *dist2_out, void *stream);
+
+/* Statistics of the last nn_search on this index (synchronises `stream`). */
+pts_status pts_index_search_stats(pts_index index, pts_search_stats *stats, void *stream);
+
+/*
+ * irls_weights -- IRLS weights and energy (Eqs. 5-8): with d_p = sqrt(dist2_p),
+ *   W_p = max(d_p, delta)^(r-2)      (Eq. 7; delta > 0 keeps W finite at d_p = 0)
+ *   energy = sum_p d_p^r             (Eq. 5; Eq. 4 when r = 2)
+ * dist2 device Q float32; weights_out device Q float32 (may be NULL);
+ * energy_out device, one float64 (may be NULL).  The sum is deterministic
+ * (fixed grid, fixed reduction order).  Asynchronous.
+ */
+pts_status irls_weights(const float *dist2, int Q, float r, float delta, float *weights_out,
+                        double *energy_out, void *stream);
+
+/*
+ * m_step -- the optimization phase (Eq. 8 minimised over x): every pixel of
+ * `output` becomes
+ *   x_i = sum_{p covers i} W_p z_{nn(p)}[i - p] / sum_{p covers i} W_p,
+ * computed once per s x s patch (section 2.2) by gathering from the index's
+ * exemplar copy, in increasing query order, without atomics.
+ * nn device Q int32 (values in [0, N)); weights device Q float32 or NULL
+ * (all 1); output device Ho x Wo x 3 float32, overwritten (not read).
+ * Out-of-range nn values are clamped and flagged in the device status word.
+ */
+pts_status m_step(pts_index index, const int32_t *nn, const float *weights, int Ho, int Wo,
+                  int stride, float *output, void *stream);
+
+/*
+ * synthesize_level -- `iters` EM iterations of the energy optimisation
+ * (section 2.1) on one level: search phase (nn_search in `mode`), IRLS
+ * weights (r, delta), optimization phase (m_step), repeated; then one last
+ * search phase so that energy_out[iters] is the energy of the result.
+ * output      device Ho x Wo x 3: in = initial image, out = result.
+ * energy_out  HOST, iters + 1 float64: energy_out[t] is the energy of the
+ *             iterate entering iteration t (Eq. 4 / Eq. 5).
+ * Synchronises `stream` once at the end and returns the device status.
+ */
+pts_status synthesize_level(pts_index index, float *output, int Ho, int Wo, int stride, int iters,
+                            float r, float delta, int mode, double *energy_out, void *stream);
+
+/*
+ * Pyramid filters for coarse-to-fine synthesis (section 2.1: a coarse result
+ * is up-sampled by interpolation to initialise the next level).  The paper
+ * names no filter; the library uses
+ *   pts_downsample2: separable binomial [1 4 6 4 1]/16, mirrored border
+ *                    (index -1 -> 1, H -> H-2), even samples kept:
+ *                    out is ((H+1)/2) x ((W+1)/2) x 3;
+ *   pts_upsample2:   bilinear x2, half-pixel centres, clamped: out is 2H x 2W x 3.
+ * Device pointers; asynchronous.
+ */
+pts_status pts_downsample2(const float *in, int H, int W, float *out, void *stream);
+pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream);
+
+/*
+ * Measurement support (no counterpart in the paper).  The library counts
+ * every kernel it launches, and while profiling is on it brackets each launch
+ * of the named kernel classes with CUDA events recorded on the launch stream.
+ *   pts_launch_count     kernels launched by this process so far.
+ *   pts_profile_enable   on != 0 starts recording (and clears old records).
+ *   pts_profile_read     total device milliseconds and launch count of one
+ *                        kernel class ("search_topk", "search_range",
+ *                        "rerank", "project", "m_step"); synchronises on the
+ *                        recorded events.  Returns INVALID_ARG for an unknown
+ *                        name.
+ */
+long long pts_launch_count(void);
+void pts_profile_enable(int on);
+pts_status pts_profile_read(const char *kernel, double *total_ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTS_H */

@@ -1,0 +1,24 @@
+"""GB300 (sm_103a) library for perspective texture synthesis by energy optimisation.
+
+Bashir & Ghouri, "Perspective Texture Synthesis Based on Improved Energy
+Optimization" (arXiv:2006.11851).  The compute path is the C-ABI CUDA library
+``libpts`` (include/pts.h); this package is a thin ctypes binding with the same
+entry-point names that takes torch CUDA tensors and passes their pointers,
+sizes and the current stream.  There is no CPU fallback: every call raises if
+the CUDA library is not built or no GPU is present.
+"""
+from ._binding import (  # noqa: F401
+    MODES,
+    ExemplarIndex,
+    PtsError,
+    build_exemplar_index,
+    downsample2,
+    irls_weights,
+    lib,
+    m_step,
+    nn_search,
+    pca_fit,
+    synthesize_level,
+    upsample2,
+)
+from .pyramid import synthesize_pyramid  # noqa: F401

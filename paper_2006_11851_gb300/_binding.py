@@ -1,0 +1,254 @@
+"""ctypes binding of libpts (include/pts.h): argument marshalling only.
+
+Tensors must be contiguous CUDA tensors on the current device; every call
+runs on torch's current CUDA stream.  Errors from the library raise PtsError
+with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MODES = {"exact": 0, "bf16": 1, "fp8": 2, "proposal": 3}
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class PtsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pts status {status}: {msg}")
+        self.status = status
+
+
+class _IndexParams(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("var_frac", ctypes.c_double), ("max_iters", ctypes.c_int)]
+
+
+class _IndexInfo(ctypes.Structure):
+    _fields_ = [("He", ctypes.c_int), ("We", ctypes.c_int), ("w", ctypes.c_int), ("D", ctypes.c_int),
+                ("N", ctypes.c_int), ("d", ctypes.c_int), ("da", ctypes.c_int),
+                ("var_retained", ctypes.c_double), ("eig_top", ctypes.c_double),
+                ("eig_iters", ctypes.c_int), ("unorm2_max", ctypes.c_float)]
+
+
+class _SearchStats(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_longlong), ("certified", ctypes.c_longlong),
+                ("range_queries", ctypes.c_longlong), ("range_pairs", ctypes.c_longlong),
+                ("brute_queries", ctypes.c_longlong)]
+
+
+_vp = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_Dd = ctypes.c_double
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libpts (building it with nvcc if needed)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.lib_path()
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libpts is not built ({path}); run python -m paper_2006_11851_gb300.build")
+        L = ctypes.CDLL(path)
+        L.pts_last_error.restype = ctypes.c_char_p
+        L.pts_version.restype = ctypes.c_char_p
+        L.pca_fit.argtypes = [_vp, _I, _I, _I, _I, _Dd, _vp, _vp, _vp, ctypes.POINTER(_I), _vp]
+        L.build_exemplar_index.argtypes = [_vp, _I, _I, _I, ctypes.POINTER(_IndexParams), _vp,
+                                           ctypes.POINTER(_vp)]
+        L.pts_index_destroy.argtypes = [_vp]
+        L.pts_index_destroy.restype = None
+        L.pts_index_get_info.argtypes = [_vp, ctypes.POINTER(_IndexInfo)]
+        L.pts_index_device_status.argtypes = [_vp, _vp]
+        L.nn_search.argtypes = [_vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
+        L.pts_index_search_stats.argtypes = [_vp, ctypes.POINTER(_SearchStats), _vp]
+        L.irls_weights.argtypes = [_vp, _I, _F, _F, _vp, _vp, _vp]
+        L.m_step.argtypes = [_vp, _vp, _vp, _I, _I, _I, _vp, _vp]
+        L.synthesize_level.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _vp, _vp]
+        L.pts_downsample2.argtypes = [_vp, _I, _I, _vp, _vp]
+        L.pts_upsample2.argtypes = [_vp, _I, _I, _vp, _vp]
+        _declare_optional(L)
+        _LIB = L
+        return L
+
+
+def _declare_optional(L: ctypes.CDLL) -> None:
+    """Entry points of later layers (declared when the library exports them)."""
+    return None
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise PtsError(status, lib().pts_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype: torch.dtype, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, str):
+        return MODES[mode]
+    return int(mode)
+
+
+def pca_fit(exemplar: torch.Tensor, w: int, d: int, var_frac: float = 0.95):
+    """(mean[D] f32, basis[d, D] f32, eigenvalues[d] f64, d_used) on the GPU."""
+    _need(exemplar, torch.float32, "exemplar")
+    He, We, _ = exemplar.shape
+    D = 3 * w * w
+    cap = d if d > 0 else 64
+    mean = torch.empty(D, device=exemplar.device, dtype=torch.float32)
+    basis = torch.empty(cap, D, device=exemplar.device, dtype=torch.float32)
+    eig = torch.empty(cap, device=exemplar.device, dtype=torch.float64)
+    dout = ctypes.c_int(0)
+    _check(lib().pca_fit(_ptr(exemplar), He, We, w, d, var_frac, _ptr(mean), _ptr(basis), _ptr(eig),
+                         ctypes.byref(dout), _stream()))
+    k = dout.value
+    return mean, basis[:k].contiguous(), eig[:k].contiguous(), k
+
+
+class ExemplarIndex:
+    """Owns a pts_index (build_exemplar_index); freed by close() or on GC."""
+
+    def __init__(self, exemplar: torch.Tensor, w: int, d: int = 0, var_frac: float = 0.95,
+                 max_iters: int = 0):
+        L = lib()
+        _need(exemplar, torch.float32, "exemplar")
+        He, We, C = exemplar.shape
+        if C != 3:
+            raise ValueError("exemplar must be H x W x 3")
+        self._h = ctypes.c_void_p()
+        p = _IndexParams(int(d), float(var_frac), int(max_iters))
+        _check(L.build_exemplar_index(_ptr(exemplar), He, We, w, ctypes.byref(p), _stream(),
+                                      ctypes.byref(self._h)))
+        self.device = exemplar.device
+        info = _IndexInfo()
+        _check(L.pts_index_get_info(self._h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _IndexInfo._fields_}
+        self.w, self.N, self.d, self.D = info.w, info.N, info.d, info.D
+        self.He, self.We = He, We
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("index is closed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().pts_index_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_queries(self, Ho: int, Wo: int, stride: int = 2) -> int:
+        return ((Ho - self.w) // stride + 1) * ((Wo - self.w) // stride + 1)
+
+    def search_stats(self) -> dict:
+        s = _SearchStats()
+        _check(lib().pts_index_search_stats(self.handle, ctypes.byref(s), _stream()))
+        return {f: getattr(s, f) for f, _ in _SearchStats._fields_}
+
+    def device_status(self) -> None:
+        _check(lib().pts_index_device_status(self.handle, _stream()))
+
+
+def build_exemplar_index(exemplar: torch.Tensor, w: int, d: int = 0, var_frac: float = 0.95,
+                         max_iters: int = 0) -> ExemplarIndex:
+    return ExemplarIndex(exemplar, w, d, var_frac, max_iters)
+
+
+def nn_search(index: ExemplarIndex, output: torch.Tensor, stride: int = 2, mode="exact",
+              nn_out: torch.Tensor | None = None, d2_out: torch.Tensor | None = None):
+    """(nn int32[Q], dist2 float32[Q]) of every query window of `output`."""
+    _need(output, torch.float32, "output")
+    Ho, Wo, _ = output.shape
+    Q = index.num_queries(Ho, Wo, stride) if (Ho - index.w) % stride == 0 and (Wo - index.w) % stride == 0 else 0
+    if nn_out is None:
+        nn_out = torch.empty(max(Q, 1), device=output.device, dtype=torch.int32)
+    if d2_out is None:
+        d2_out = torch.empty(max(Q, 1), device=output.device, dtype=torch.float32)
+    _check(lib().nn_search(index.handle, _ptr(output), Ho, Wo, stride, _mode(mode), _ptr(nn_out),
+                           _ptr(d2_out), _stream()))
+    return nn_out[:Q], d2_out[:Q]
+
+
+def irls_weights(dist2: torch.Tensor, r: float = 2.0, delta: float = 1e-3):
+    """(weights float32[Q], energy float64 scalar tensor)."""
+    _need(dist2, torch.float32, "dist2")
+    W = torch.empty_like(dist2)
+    E = torch.empty(1, device=dist2.device, dtype=torch.float64)
+    _check(lib().irls_weights(_ptr(dist2), dist2.numel(), r, delta, _ptr(W), _ptr(E), _stream()))
+    return W, E[0]
+
+
+def m_step(index: ExemplarIndex, nn: torch.Tensor, weights: torch.Tensor | None, Ho: int, Wo: int,
+           stride: int = 2, out: torch.Tensor | None = None) -> torch.Tensor:
+    _need(nn, torch.int32, "nn")
+    if weights is not None:
+        _need(weights, torch.float32, "weights")
+    if out is None:
+        out = torch.empty(Ho, Wo, 3, device=nn.device, dtype=torch.float32)
+    _need(out, torch.float32, "out", (Ho, Wo, 3))
+    Q = index.num_queries(Ho, Wo, stride)
+    if nn.numel() != Q or (weights is not None and weights.numel() != Q):
+        raise ValueError("nn/weights must have one entry per query")
+    _check(lib().m_step(index.handle, _ptr(nn), _ptr(weights), Ho, Wo, stride, _ptr(out), _stream()))
+    return out
+
+
+def synthesize_level(index: ExemplarIndex, output: torch.Tensor, iters: int, r: float = 2.0,
+                     delta: float = 1e-3, mode="exact", stride: int = 2) -> np.ndarray:
+    """Runs EM in place on `output`; returns the iters + 1 energies (host)."""
+    _need(output, torch.float32, "output")
+    Ho, Wo, _ = output.shape
+    E = np.zeros(iters + 1, dtype=np.float64)
+    _check(lib().synthesize_level(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta,
+                                  _mode(mode), E.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return E
+
+
+def downsample2(img: torch.Tensor) -> torch.Tensor:
+    _need(img, torch.float32, "img")
+    H, W, _ = img.shape
+    out = torch.empty((H + 1) // 2, (W + 1) // 2, 3, device=img.device, dtype=torch.float32)
+    _check(lib().pts_downsample2(_ptr(img), H, W, _ptr(out), _stream()))
+    return out
+
+
+def upsample2(img: torch.Tensor) -> torch.Tensor:
+    _need(img, torch.float32, "img")
+    H, W, _ = img.shape
+    out = torch.empty(2 * H, 2 * W, 3, device=img.device, dtype=torch.float32)
+    _check(lib().pts_upsample2(_ptr(img), H, W, _ptr(out), _stream()))
+    return out

@@ -1,0 +1,379 @@
+// capi.cu -- the C ABI (include/pts.h): argument checks, the index object,
+// workspace management and the E-step / EM drivers that sequence the kernels.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "pts_internal.cuh"
+
+namespace pts {
+
+namespace {
+thread_local std::string g_last_error;
+
+// Rounding slack of the PCA lower bound: tau_q = c sqrt(D) 2^-24 (||u_q||^2 +
+// max_n ||u_n||^2).  FP32 dot products of length D carry errors that grow like
+// sqrt(D) units in the last place in practice (Higham, "Accuracy and
+// Stability of Numerical Algorithms", section 3.1), relative to the operand
+// norms; c = 8 leaves a wide margin.
+constexpr float kTauC = 8.0f;
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+pts_status check_grid(int H, int W, int w, int stride, const char *what) {
+    if (stride != 1 && stride != 2 && stride != 4)
+        return set_error(PTS_ERR_INVALID_ARG, std::string(what) + ": stride must be 1, 2 or 4");
+    if (w < 1 || w > H || w > W)
+        return set_error(PTS_ERR_INVALID_ARG, std::string(what) + ": window larger than the image");
+    if ((H - w) % stride || (W - w) % stride || w % stride)
+        return set_error(PTS_ERR_INVALID_ARG,
+                         std::string(what) + ": (H-w), (W-w) and w must be multiples of the stride");
+    return PTS_OK;
+}
+
+pts_status ensure_workspace(pts_index idx, int Q) {
+    Workspace &ws = idx->ws;
+    if (Q <= ws.q_cap && ws.counters.ptr) return PTS_OK;
+    const int cap = std::max(Q, 1024);
+    const size_t qpad = (size_t)ceil_div(cap, kBQ) * kBQ;
+    PTS_TRY(ws.qcoord.ensure(qpad * idx->da, "query vectors"));
+    PTS_TRY(ws.qnorm.ensure(qpad, "query norms"));
+    PTS_TRY(ws.tau.ensure(qpad, "query slack"));
+    PTS_TRY(ws.cand_idx.ensure((size_t)cap * kTopK, "candidate indices"));
+    PTS_TRY(ws.cand_lb.ensure((size_t)cap * kTopK, "candidate bounds"));
+    PTS_TRY(ws.fail_list.ensure(cap, "fail list"));
+    PTS_TRY(ws.best64.ensure(cap, "packed minima"));
+    ws.pair_cap = std::max<size_t>((size_t)cap * 256, (size_t)1 << 20);
+    PTS_TRY(ws.pairs.ensure(ws.pair_cap, "pair list"));
+    PTS_TRY(ws.counters.ensure(4, "counters"));
+    PTS_TRY(ws.nn.ensure(cap, "nn"));
+    PTS_TRY(ws.d2.ensure(cap, "d2"));
+    PTS_TRY(ws.wts.ensure(cap, "weights"));
+    PTS_TRY(ws.partial.ensure(kIrlsGrid, "reduction partials"));
+    if (!ws.ticket.ptr) {
+        PTS_TRY(ws.ticket.ensure(1, "reduction ticket"));
+        PTS_CUDA_TRY(cudaMemset(ws.ticket.ptr, 0, sizeof(unsigned int)));
+    }
+    ws.q_cap = cap;
+    return PTS_OK;
+}
+
+pts_status read_status(pts_index idx, cudaStream_t st) {
+    int h = 0;
+    PTS_CUDA_TRY(cudaMemcpyAsync(&h, idx->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h & (kDevErrBounds | kDevErrTimeout | kDevErrNumeric)) {
+        PTS_CUDA_TRY(cudaMemsetAsync(idx->status.ptr, 0, sizeof(int), st));
+        PTS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h & kDevErrTimeout) return set_error(PTS_ERR_TIMEOUT, "a bounded device wait gave up");
+        if (h & kDevErrBounds) return set_error(PTS_ERR_DEVICE, "an index input was out of range");
+        return set_error(PTS_ERR_DEVICE, "a factorisation met a non-positive pivot");
+    }
+    return PTS_OK;
+}
+
+// the E-step in exact mode (see include/pts.h)
+pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q,
+                        int32_t *nn_out, float *d2_out, cudaStream_t st) {
+    Workspace &ws = idx->ws;
+    const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
+    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0,
+                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
+    PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
+    launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
+                       idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
+    RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
+                  idx->nx, idx->N, Q};
+    unsigned int *fail_count = ws.counters.ptr + 0;
+    unsigned int *pair_count = ws.counters.ptr + 1;
+    unsigned int *brute_count = ws.counters.ptr + 2;
+    launch_rerank(ra, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out,
+                  ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
+    launch_search_range(ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, Q, idx->da, ws.fail_list.ptr,
+                        fail_count, ws.best64.ptr, idx->et.ptr, idx->enorm.ptr, idx->ntiles, idx->N,
+                        pair_count, ws.pairs.ptr, (unsigned int)ws.pair_cap, idx->status.ptr, st);
+    launch_pair_eval(ra, ws.pairs.ptr, pair_count, (unsigned int)ws.pair_cap, ws.best64.ptr, st);
+    launch_brute_fallback(ra, ws.fail_list.ptr, fail_count, pair_count, (unsigned int)ws.pair_cap,
+                          brute_count, ws.best64.ptr, idx->status.ptr, st);
+    launch_resolve(ws.fail_list.ptr, fail_count, ws.best64.ptr, Q, nn_out, d2_out, st);
+    return PTS_OK;
+}
+
+pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int stride, int mode,
+                          int32_t *nn_out, float *d2_out, cudaStream_t st) {
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "nn_search"));
+    if (!X || !nn_out || !d2_out) return set_error(PTS_ERR_INVALID_ARG, "nn_search: null pointer");
+    const long Ql = (long)((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
+    if (Ql > (1L << 30)) return set_error(PTS_ERR_INVALID_ARG, "nn_search: too many queries");
+    const int Q = (int)Ql;
+    PTS_TRY(ensure_workspace(idx, Q));
+    idx->last_mode = mode;
+    idx->last.queries = Q;
+    switch (mode) {
+        case PTS_EXACT_F32:
+            PTS_TRY(search_exact(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
+            break;
+        case PTS_BF16_RERANK:
+        case PTS_FP8_RERANK:
+        case PTS_PROPOSAL_BF16:
+            return set_error(PTS_ERR_UNSUPPORTED, "nn_search: mode not available in this build");
+        default:
+            return set_error(PTS_ERR_INVALID_ARG, "nn_search: unknown mode");
+    }
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
+}  // namespace
+
+pts_status set_error(pts_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+pts_status cuda_error(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return PTS_ERR_CUDA;
+}
+
+}  // namespace pts
+
+using namespace pts;
+
+extern "C" {
+
+const char *pts_last_error(void) { return g_last_error.c_str(); }
+
+const char *pts_version(void) { return "pts-gb300 0.1 (sm_103a)"; }
+
+pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double var_frac,
+                   float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream) {
+    if (!exemplar || !basis_out) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: null pointer");
+    if (w < 1 || w > He || w > We) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: bad window");
+    if (d > kMaxD) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: d > 64");
+    if (d <= 0 && !(var_frac > 0.0 && var_frac <= 1.0))
+        return set_error(PTS_ERR_INVALID_ARG, "pca_fit: var_frac must be in (0, 1]");
+    cudaStream_t st = as_stream(stream);
+    DevBuf<int> status;
+    PTS_TRY(status.ensure(1, "status"));
+    PTS_CUDA_TRY(cudaMemsetAsync(status.ptr, 0, sizeof(int), st));
+    int dd = 0;
+    pts_status s = pca_fit_device(exemplar, He, We, w, d, var_frac, 0, mean_out, basis_out,
+                                  eigvals_out, &dd, nullptr, nullptr, nullptr, status.ptr, st);
+    if (s == PTS_OK) {
+        int h = 0;
+        cudaMemcpy(&h, status.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (h) s = set_error(PTS_ERR_DEVICE, "pca_fit: eigen-solver did not converge cleanly");
+    }
+    status.release();
+    if (d_out) *d_out = dd;
+    return s;
+}
+
+pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
+                                const pts_index_params *params, void *stream, pts_index *out) {
+    if (!out || !exemplar || !params)
+        return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: null pointer");
+    *out = nullptr;
+    if (w < 1 || w > He || w > We)
+        return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad window");
+    if (params->d > kMaxD) return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: d > 64");
+    const long N = (long)(He - w + 1) * (We - w + 1);
+    if (N < 2 || N > (1L << 30))
+        return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad exemplar size");
+    cudaStream_t st = as_stream(stream);
+    pts_index idx = new pts_index_s();
+    auto fail = [&](pts_status s) {
+        pts_index_destroy(idx);
+        return s;
+    };
+    cudaGetDevice(&idx->device);
+    idx->He = He;
+    idx->We = We;
+    idx->w = w;
+    idx->D = 3 * w * w;
+    idx->ny = He - w + 1;
+    idx->nx = We - w + 1;
+    idx->N = (int)N;
+    pts_status s;
+    if ((s = idx->exemplar.ensure((size_t)He * We * 3, "exemplar")) != PTS_OK) return fail(s);
+    if ((s = idx->status.ensure(1, "status")) != PTS_OK) return fail(s);
+    if ((s = idx->mu.ensure(idx->D, "mean")) != PTS_OK) return fail(s);
+    if ((s = idx->basis.ensure((size_t)kMaxD * idx->D, "basis")) != PTS_OK) return fail(s);
+    if ((s = idx->eig.ensure(kMaxD, "eigenvalues")) != PTS_OK) return fail(s);
+    if ((s = idx->umax.ensure(1, "norm max")) != PTS_OK) return fail(s);
+    cudaError_t e = cudaMemcpyAsync(idx->exemplar.ptr, exemplar, sizeof(float) * He * We * 3,
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(cuda_error(e, "copy exemplar"));
+    cudaMemsetAsync(idx->status.ptr, 0, sizeof(int), st);
+    int dd = 0;
+    s = pca_fit_device(idx->exemplar.ptr, He, We, w, params->d, params->var_frac, params->max_iters,
+                       idx->mu.ptr, idx->basis.ptr, idx->eig.ptr, &dd, &idx->var_retained,
+                       &idx->eig_top, &idx->eig_iters, idx->status.ptr, st);
+    if (s != PTS_OK) return fail(s);
+    idx->d = dd;
+    idx->da = (dd + 1 + 3) & ~3;
+    idx->ntiles = ceil_div(N, kBN);
+    if ((s = idx->et.ensure((size_t)idx->ntiles * idx->da * kBN, "exemplar vectors")) != PTS_OK)
+        return fail(s);
+    if ((s = idx->enorm.ensure((size_t)idx->ntiles * kBN, "exemplar norms")) != PTS_OK) return fail(s);
+    launch_exemplar_pad(idx->et.ptr, idx->enorm.ptr, idx->N, idx->ntiles, idx->da, st);
+    launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basis.ptr, dd, idx->da, 1,
+                   idx->et.ptr, idx->enorm.ptr, nullptr, 0.0f, nullptr, st);
+    launch_norm_max(idx->enorm.ptr, idx->N, idx->umax.ptr, st);
+    e = cudaMemcpyAsync(&idx->unorm2_max, idx->umax.ptr, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(cuda_error(e, "read norm max"));
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_error(e, "build_exemplar_index"));
+    if ((s = read_status(idx, st)) != PTS_OK) return fail(s);
+    *out = idx;
+    return PTS_OK;
+}
+
+void pts_index_destroy(pts_index idx) {
+    if (!idx) return;
+    cudaDeviceSynchronize();
+    Workspace &ws = idx->ws;
+    ws.qcoord.release();
+    ws.qnorm.release();
+    ws.tau.release();
+    ws.cand_idx.release();
+    ws.cand_lb.release();
+    ws.fail_list.release();
+    ws.best64.release();
+    ws.pairs.release();
+    ws.counters.release();
+    ws.nn.release();
+    ws.d2.release();
+    ws.wts.release();
+    ws.energy.release();
+    ws.partial.release();
+    ws.ticket.release();
+    idx->exemplar.release();
+    idx->mu.release();
+    idx->basis.release();
+    idx->eig.release();
+    idx->et.release();
+    idx->enorm.release();
+    idx->umax.release();
+    idx->status.release();
+    delete idx;
+}
+
+pts_status pts_index_get_info(pts_index idx, pts_index_info *info) {
+    if (!idx || !info) return set_error(PTS_ERR_INVALID_ARG, "pts_index_get_info: null pointer");
+    info->He = idx->He;
+    info->We = idx->We;
+    info->w = idx->w;
+    info->D = idx->D;
+    info->N = idx->N;
+    info->d = idx->d;
+    info->da = idx->da;
+    info->var_retained = idx->var_retained;
+    info->eig_top = idx->eig_top;
+    info->eig_iters = idx->eig_iters;
+    info->unorm2_max = idx->unorm2_max;
+    return PTS_OK;
+}
+
+pts_status pts_index_device_status(pts_index idx, void *stream) {
+    if (!idx) return set_error(PTS_ERR_INVALID_ARG, "pts_index_device_status: null index");
+    return read_status(idx, as_stream(stream));
+}
+
+pts_status nn_search(pts_index idx, const float *output, int Ho, int Wo, int stride, int mode,
+                     int32_t *nn_out, float *dist2_out, void *stream) {
+    if (!idx) return set_error(PTS_ERR_INVALID_ARG, "nn_search: null index");
+    return nn_search_impl(idx, output, Ho, Wo, stride, mode, nn_out, dist2_out, as_stream(stream));
+}
+
+pts_status pts_index_search_stats(pts_index idx, pts_search_stats *stats, void *stream) {
+    if (!idx || !stats) return set_error(PTS_ERR_INVALID_ARG, "pts_index_search_stats: null pointer");
+    cudaStream_t st = as_stream(stream);
+    *stats = idx->last;
+    if (idx->ws.counters.ptr && idx->last_mode == PTS_EXACT_F32) {
+        unsigned int c[4] = {0, 0, 0, 0};
+        PTS_CUDA_TRY(cudaMemcpyAsync(c, idx->ws.counters.ptr, sizeof(c), cudaMemcpyDeviceToHost, st));
+        PTS_CUDA_TRY(cudaStreamSynchronize(st));
+        stats->range_queries = c[0];
+        stats->certified = stats->queries - c[0];
+        stats->range_pairs = c[1];
+        stats->brute_queries = c[2];
+    }
+    return PTS_OK;
+}
+
+pts_status irls_weights(const float *dist2, int Q, float r, float delta, float *weights_out,
+                        double *energy_out, void *stream) {
+    if (!dist2 || Q < 0) return set_error(PTS_ERR_INVALID_ARG, "irls_weights: bad input");
+    if (!(r > 0.0f && r <= 2.0f) || !(delta > 0.0f))
+        return set_error(PTS_ERR_INVALID_ARG, "irls_weights: need 0 < r <= 2 and delta > 0");
+    cudaStream_t st = as_stream(stream);
+    DevBuf<double> partial;
+    DevBuf<unsigned int> ticket;
+    PTS_TRY(partial.ensure(kIrlsGrid, "partials"));
+    PTS_TRY(ticket.ensure(1, "ticket"));
+    PTS_CUDA_TRY(cudaMemsetAsync(ticket.ptr, 0, sizeof(unsigned int), st));
+    launch_irls(dist2, Q, r, delta, weights_out, energy_out, partial.ptr, ticket.ptr, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    partial.release();
+    ticket.release();
+    if (e != cudaSuccess) return cuda_error(e, "irls_weights");
+    return PTS_OK;
+}
+
+pts_status m_step(pts_index idx, const int32_t *nn, const float *weights, int Ho, int Wo,
+                  int stride, float *output, void *stream) {
+    if (!idx || !nn || !output) return set_error(PTS_ERR_INVALID_ARG, "m_step: null pointer");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "m_step"));
+    launch_m_step(nn, weights, idx->exemplar.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride,
+                  output, idx->status.ptr, as_stream(stream));
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
+pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int stride, int iters,
+                            float r, float delta, int mode, double *energy_out, void *stream) {
+    if (!idx || !output || !energy_out)
+        return set_error(PTS_ERR_INVALID_ARG, "synthesize_level: null pointer");
+    if (iters < 0) return set_error(PTS_ERR_INVALID_ARG, "synthesize_level: iters < 0");
+    if (!(r > 0.0f && r <= 2.0f) || !(delta > 0.0f))
+        return set_error(PTS_ERR_INVALID_ARG, "synthesize_level: need 0 < r <= 2 and delta > 0");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "synthesize_level"));
+    cudaStream_t st = as_stream(stream);
+    const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
+    PTS_TRY(ensure_workspace(idx, Q));
+    Workspace &ws = idx->ws;
+    PTS_TRY(ws.energy.ensure(iters + 1, "energies"));
+    for (int t = 0; t <= iters; ++t) {
+        PTS_TRY(nn_search_impl(idx, output, Ho, Wo, stride, mode, ws.nn.ptr, ws.d2.ptr, st));
+        launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, ws.energy.ptr + t, ws.partial.ptr,
+                    ws.ticket.ptr, st);
+        if (t == iters) break;
+        launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar.ptr, idx->We, idx->nx, idx->N, idx->w, Ho,
+                      Wo, stride, output, idx->status.ptr, st);
+    }
+    PTS_CUDA_TRY(cudaGetLastError());
+    PTS_CUDA_TRY(cudaMemcpyAsync(energy_out, ws.energy.ptr, sizeof(double) * (iters + 1),
+                                 cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    return read_status(idx, st);
+}
+
+pts_status pts_downsample2(const float *in, int H, int W, float *out, void *stream) {
+    if (!in || !out || H < 1 || W < 1) return set_error(PTS_ERR_INVALID_ARG, "pts_downsample2");
+    launch_downsample2(in, H, W, out, as_stream(stream));
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
+pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream) {
+    if (!in || !out || H < 1 || W < 1) return set_error(PTS_ERR_INVALID_ARG, "pts_upsample2");
+    launch_upsample2(in, H, W, out, as_stream(stream));
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// mstep.cu -- optimization phase (M-step), IRLS weights/energy and the
+// pyramid filters.
+//
+// M-step (Eq. 8 minimised over x): pixel i becomes
+//   x_i = sum_{p covers i} W_p z_{nn(p)}[i - p] / sum_{p covers i} W_p.
+// With the patch stride s dividing w, the s x s pixels of a patch share one
+// covering set of query windows (section 2.2, 2x2 patch processing), so one
+// thread owns one patch: it walks the covering windows in increasing query
+// order (the order of the sum above), gathers the co-located s x s block of
+// each matched exemplar window and writes its s*s*3 outputs once.  No
+// atomics, deterministic.  The exemplar (<= a few MB) stays in L2.
+#include "pts_internal.cuh"
+
+namespace pts {
+namespace {
+
+template <int S>
+__global__ void __launch_bounds__(128)
+    k_m_step(const int *__restrict__ nn, const float *__restrict__ wts, const float *__restrict__ Z,
+             int We, int ex, int N, int w, int Ho, int Wo, int qy_n, int qx_n,
+             float *__restrict__ out, int *__restrict__ status) {
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    const int py = blockIdx.y;
+    if (px >= Wo / S || py >= Ho / S) return;
+    const int ws = w / S;
+    const int qy_lo = max(0, py - ws + 1), qy_hi = min(py, qy_n - 1);
+    const int qx_lo = max(0, px - ws + 1), qx_hi = min(px, qx_n - 1);
+    float num[S][S][3];
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) num[t][u][c] = 0.0f;
+    float den = 0.0f;
+    bool bad = false;
+    for (int qy = qy_lo; qy <= qy_hi; ++qy) {
+        const int oy = (py - qy) * S;
+        for (int qx = qx_lo; qx <= qx_hi; ++qx) {
+            const int p = qy * qx_n + qx;
+            int n = __ldg(nn + p);
+            if (n < 0 || n >= N) {
+                bad = true;
+                n = n < 0 ? 0 : N - 1;
+            }
+            const float wt = wts ? __ldg(wts + p) : 1.0f;
+            const int ey = n / ex, exx = n - ey * ex;
+            const int ox = (px - qx) * S;
+            const float *zb = Z + ((size_t)(ey + oy) * We + (exx + ox)) * 3;
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+#pragma unroll
+                for (int u = 0; u < S; ++u)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        num[t][u][c] = fmaf(wt, __ldg(zb + ((size_t)t * We + u) * 3 + c), num[t][u][c]);
+            den += wt;
+        }
+    }
+    if (bad) atomicOr(status, kDevErrBounds);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        float *o = out + ((size_t)(py * S + t) * Wo + px * S) * 3;
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[u * 3 + c] = num[t][u][c] / den;
+    }
+}
+
+// IRLS weights and energy (Eqs. 5-8).  Fixed grid; each block sums its
+// grid-stride slice in FP64, tree-reduces, and the last block to finish adds
+// the block partials in block order, so the energy is bitwise reproducible.
+__global__ void __launch_bounds__(256)
+    k_irls(const float *__restrict__ d2, int Q, float r, float delta, float *__restrict__ wts,
+           double *__restrict__ energy_out, double *__restrict__ partial,
+           unsigned int *__restrict__ ticket) {
+    __shared__ double red[256];
+    __shared__ bool last;
+    double acc = 0.0;
+    const bool quad = (r == 2.0f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x) {
+        const float t = fmaxf(d2[i], 0.0f);
+        if (quad) {
+            if (wts) wts[i] = 1.0f;
+            acc += (double)t;
+        } else {
+            const float dp = sqrtf(t);
+            if (wts) wts[i] = powf(fmaxf(dp, delta), r - 2.0f);
+            acc += (double)powf(dp, r);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = red[0];
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double *)partial)[b];
+        if (energy_out) *energy_out = s;
+        *ticket = 0u;
+    }
+}
+
+__device__ __forceinline__ int mirror_idx(int i, int n) {
+    if (n == 1) return 0;
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * (n - 1) - i;
+    }
+    return i;
+}
+
+// binomial [1 4 6 4 1]/16 separable down-sampling by 2, mirrored border
+__global__ void k_downsample2(const float *__restrict__ in, int H, int W, float *__restrict__ out) {
+    const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= Wo || y >= Ho) return;
+    const float k[5] = {1.0f / 16, 4.0f / 16, 6.0f / 16, 4.0f / 16, 1.0f / 16};
+    float s[3] = {0.0f, 0.0f, 0.0f};
+    for (int a = 0; a < 5; ++a) {
+        const int yy = mirror_idx(2 * y + a - 2, H);
+        for (int b = 0; b < 5; ++b) {
+            const int xx = mirror_idx(2 * x + b - 2, W);
+            const float kk = k[a] * k[b];
+            for (int c = 0; c < 3; ++c) s[c] = fmaf(kk, in[((size_t)yy * W + xx) * 3 + c], s[c]);
+        }
+    }
+    for (int c = 0; c < 3; ++c) out[((size_t)y * Wo + x) * 3 + c] = s[c];
+}
+
+// bilinear up-sampling by 2 with half-pixel centres, clamped
+__global__ void k_upsample2(const float *__restrict__ in, int H, int W, float *__restrict__ out) {
+    const int Ho = 2 * H, Wo = 2 * W;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+    if (X >= Wo || Y >= Ho) return;
+    float sy = (Y + 0.5f) * 0.5f - 0.5f, sx = (X + 0.5f) * 0.5f - 0.5f;
+    sy = fminf(fmaxf(sy, 0.0f), (float)(H - 1));
+    sx = fminf(fmaxf(sx, 0.0f), (float)(W - 1));
+    const int y0 = (int)floorf(sy), x0 = (int)floorf(sx);
+    const int y1 = min(y0 + 1, H - 1), x1 = min(x0 + 1, W - 1);
+    const float fy = sy - y0, fx = sx - x0;
+    for (int c = 0; c < 3; ++c) {
+        const float v00 = in[((size_t)y0 * W + x0) * 3 + c], v01 = in[((size_t)y0 * W + x1) * 3 + c];
+        const float v10 = in[((size_t)y1 * W + x0) * 3 + c], v11 = in[((size_t)y1 * W + x1) * 3 + c];
+        out[((size_t)Y * Wo + X) * 3 + c] =
+            (1.0f - fy) * ((1.0f - fx) * v00 + fx * v01) + fy * ((1.0f - fx) * v10 + fx * v11);
+    }
+}
+
+}  // namespace
+
+void launch_m_step(const int *nn, const float *wts, const float *Z, int We, int ex, int N, int w,
+                   int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st) {
+    const int qy_n = (Ho - w) / stride + 1, qx_n = (Wo - w) / stride + 1;
+    const int PX = Wo / stride, PY = Ho / stride;
+    dim3 block(128), grid(ceil_div(PX, 128), PY);
+    ProfScope ps(kProfMStep, st, 1);
+    switch (stride) {
+        case 1:
+            k_m_step<1><<<grid, block, 0, st>>>(nn, wts, Z, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            break;
+        case 2:
+            k_m_step<2><<<grid, block, 0, st>>>(nn, wts, Z, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            break;
+        case 4:
+            k_m_step<4><<<grid, block, 0, st>>>(nn, wts, Z, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            break;
+        default:
+            break;  // rejected by the caller
+    }
+}
+
+void launch_irls(const float *d2, int Q, float r, float delta, float *wts, double *energy_out,
+                 double *partial, unsigned int *ticket, cudaStream_t st) {
+    count_launches(1);
+    k_irls<<<kIrlsGrid, 256, 0, st>>>(d2, Q, r, delta, wts, energy_out, partial, ticket);
+}
+
+void launch_downsample2(const float *in, int H, int W, float *out, cudaStream_t st) {
+    const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+    count_launches(1);
+    k_downsample2<<<dim3(ceil_div(Wo, 128), Ho), 128, 0, st>>>(in, H, W, out);
+}
+
+void launch_upsample2(const float *in, int H, int W, float *out, cudaStream_t st) {
+    count_launches(1);
+    k_upsample2<<<dim3(ceil_div(2 * W, 128), 2 * H), 128, 0, st>>>(in, H, W, out);
+}
+
+}  // namespace pts

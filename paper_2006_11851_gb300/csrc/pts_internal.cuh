@@ -1,0 +1,268 @@
+// pts_internal.cuh -- shared declarations of the CUDA library (not part of the
+// public ABI, which is include/pts.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pts.h"
+
+namespace pts {
+
+// ---------------------------------------------------------------------------
+// tile shapes of the FP32 SIMT search (see search_f32.cu)
+// ---------------------------------------------------------------------------
+constexpr int kBN = 128;   // exemplar windows per tile (32 lanes x 4)
+constexpr int kBQ = 64;    // queries per CTA (8 warps x 8 rows)
+constexpr int kTopK = 32;  // candidates kept per query (one per lane)
+constexpr int kMaxDA = 68; // d <= 64 coordinates + residual, padded to 4
+constexpr int kMaxD = 64;
+
+// device status word bits (OR-ed by kernels, read at synchronising calls)
+constexpr int kDevErrBounds = 1;   // an index read from an input was out of range
+constexpr int kDevErrTimeout = 2;  // a bounded wait gave up
+constexpr int kDevErrNumeric = 4;  // a factorisation met a non-positive pivot
+constexpr int kDevErrCapacity = 8; // a list overflowed (handled, informational)
+
+// ---------------------------------------------------------------------------
+// host-side error reporting
+// ---------------------------------------------------------------------------
+pts_status set_error(pts_status s, const std::string &msg);
+pts_status cuda_error(cudaError_t e, const char *where);
+
+#define PTS_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return ::pts::cuda_error(_e, #expr); \
+    } while (0)
+
+#define PTS_TRY(expr)                          \
+    do {                                       \
+        pts_status _s = (expr);                \
+        if (_s != PTS_OK) return _s;           \
+    } while (0)
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// device memory owned by the library
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t count = 0;
+    pts_status ensure(size_t n, const char *what) {
+        if (n <= count && ptr) return PTS_OK;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        count = 0;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            cudaGetLastError();
+            return set_error(PTS_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+        }
+        count = n;
+        return PTS_OK;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        count = 0;
+    }
+};
+
+struct Workspace {
+    int q_cap = 0;
+    DevBuf<float> qcoord;      // [Qpad][da] query search vectors (y, r, 0...)
+    DevBuf<float> qnorm;       // [Qpad] ||u_q||^2
+    DevBuf<float> tau;         // [Qpad] rounding slack of the bound
+    DevBuf<int> cand_idx;      // [Q][32]
+    DevBuf<float> cand_lb;     // [Q][32]
+    DevBuf<int> fail_list;     // [Q]
+    DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
+    DevBuf<uint2> pairs;       // [pair_cap] (q, n)
+    size_t pair_cap = 0;
+    DevBuf<unsigned int> counters;  // [4]: fail, pairs, brute, spare
+    DevBuf<int> nn;            // [Q] (synthesize_level)
+    DevBuf<float> d2;          // [Q]
+    DevBuf<float> wts;         // [Q]
+    DevBuf<double> energy;     // [iters+1]
+    DevBuf<double> partial;    // reduction partials
+    DevBuf<unsigned int> ticket;
+};
+
+}  // namespace pts
+
+struct pts_index_s {
+    int device = 0;
+    int He = 0, We = 0, w = 0, D = 0, N = 0, d = 0, da = 0;
+    int ny = 0, nx = 0;  // exemplar window grid
+    int ntiles = 0;      // ceil(N / kBN)
+    double var_retained = 0.0, eig_top = 0.0;
+    int eig_iters = 0;
+    float unorm2_max = 0.0f;
+    pts::DevBuf<float> exemplar;  // He*We*3
+    pts::DevBuf<float> mu;        // D
+    pts::DevBuf<float> basis;     // d*D
+    pts::DevBuf<double> eig;      // d
+    pts::DevBuf<float> et;        // [ntiles][da][kBN] = -2 * (y_n, r_n, 0...)
+    pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
+    pts::DevBuf<float> umax;      // [1]
+    pts::DevBuf<int> status;      // [1] device status word
+    pts::Workspace ws;
+    pts_search_stats last{};
+    int last_mode = 0;
+};
+
+namespace pts {
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the .cu files
+// ---------------------------------------------------------------------------
+// pca.cu
+pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, double var_frac,
+                          int max_iters, float *mean_out, float *basis_out, double *eig_out,
+                          int *d_used, double *var_retained, double *eig_top, int *iters_used,
+                          int *status, cudaStream_t st);
+// project.cu
+void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
+                    const float *basis, int d, int da, int layout, float *out_coord,
+                    float *out_norm, float *out_tau, float tau_scale, const float *umax,
+                    cudaStream_t st);
+void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st);
+void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
+// search_f32.cu
+void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
+                        const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
+                        cudaStream_t st);
+void launch_search_range(const float *qcoord, const float *qnorm, const float *tau, int Q, int da,
+                         const int *fail_list, const unsigned int *fail_count,
+                         const unsigned long long *best64, const float *et, const float *enorm,
+                         int ntiles, int N, unsigned int *pair_count, uint2 *pairs,
+                         unsigned int pair_cap, int *status, cudaStream_t st);
+// rerank.cu
+struct RerankArgs {
+    const float *X;
+    int Ho, Wo, stride, qx;
+    const float *Z;
+    int We, w, ex, N;
+    int Q;
+};
+void launch_rerank(const RerankArgs &a, const int *cand_idx, const float *cand_lb,
+                   const float *tau, int certify, int *nn_out, float *d2_out, int *fail_list,
+                   unsigned int *fail_count, unsigned long long *best64, int *status,
+                   cudaStream_t st);
+void launch_pair_eval(const RerankArgs &a, const uint2 *pairs, const unsigned int *pair_count,
+                      unsigned int pair_cap, unsigned long long *best64, cudaStream_t st);
+void launch_brute_fallback(const RerankArgs &a, const int *fail_list,
+                           const unsigned int *fail_count, const unsigned int *pair_count,
+                           unsigned int pair_cap, unsigned int *brute_count,
+                           unsigned long long *best64, int *status, cudaStream_t st);
+void launch_resolve(const int *fail_list, const unsigned int *fail_count,
+                    const unsigned long long *best64, int Q, int *nn_out, float *d2_out,
+                    cudaStream_t st);
+// profile.cu: launch counting and event timing of kernel classes
+enum ProfClass { kProfSearchTopk = 0, kProfSearchRange, kProfRerank, kProfProject, kProfMStep,
+                 kProfSearchTc, kProfMlp, kProfProbe, kProfClasses };
+void count_launches(int n);
+void prof_begin(int cls, cudaStream_t st, void **token);
+void prof_end(int cls, cudaStream_t st, void *token);
+struct ProfScope {
+    int cls;
+    cudaStream_t st;
+    void *tok;
+    ProfScope(int c, cudaStream_t s, int nlaunch) : cls(c), st(s), tok(nullptr) {
+        count_launches(nlaunch);
+        prof_begin(c, s, &tok);
+    }
+    ~ProfScope() { prof_end(cls, st, tok); }
+};
+// mstep.cu
+void launch_m_step(const int *nn, const float *wts, const float *Z, int We, int ex, int N, int w,
+                   int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st);
+void launch_irls(const float *d2, int Q, float r, float delta, float *wts, double *energy_out,
+                 double *partial, unsigned int *ticket, cudaStream_t st);
+void launch_downsample2(const float *in, int H, int W, float *out, cudaStream_t st);
+void launch_upsample2(const float *in, int H, int W, float *out, cudaStream_t st);
+constexpr int kIrlsGrid = 152;
+
+}  // namespace pts
+
+// ---------------------------------------------------------------------------
+// device helpers: mbarrier + bulk copies with bounded waits
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace pts {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity to complete.  Gives up after
+// ~1 s of wall time (or 2^26 polls), sets kDevErrTimeout and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && global_timer_ns() - t0 > 1000000000ull) break;
+    }
+    atomicOr(status, kDevErrTimeout);
+    return false;
+}
+
+// 1-D bulk copy global -> shared completing on an mbarrier (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long pack_dist_idx(float d2, int n) {
+    return (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) |
+           static_cast<unsigned int>(n);
+}
+
+}  // namespace pts
+#endif

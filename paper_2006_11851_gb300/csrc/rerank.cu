@@ -1,0 +1,216 @@
+// rerank.cu -- exact full-dimension distances of Eq. 4 for candidate lists.
+//
+// k_rerank       one warp per query: evaluates the query's candidates in
+//                increasing order of their lower bound, skipping those whose
+//                bound (minus the rounding slack tau) already exceeds the best
+//                distance found, and keeps the lexicographically smallest
+//                (d2, n).  With certify != 0 (exact mode) the result is final
+//                when d2_best <= LB_32 - tau_q: every window outside the list
+//                has LB >= LB_32, hence a distance >= d2_best.  Otherwise the
+//                query joins the fail list with U_q = d2_best as a bound.
+// k_pair_eval    one warp per (q, n) pair of the bound-pruned pass; keeps the
+//                minimum packed (d2 bits, n) per query with a 64-bit atomicMin,
+//                which also breaks exact ties toward the smallest n.
+// k_brute        only when the pair list overflowed: full scan of every exemplar
+//                window for each failing query (one CTA per query).
+// k_resolve      writes nn/d2 of the failing queries from the packed minima.
+//
+// Distances are sums of squared FP32 differences read straight from the two
+// images (a window row is 3w contiguous floats in HWC layout), reduced across
+// the warp by a fixed butterfly, so the result is deterministic.
+#include "pts_internal.cuh"
+
+namespace pts {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Full-dimension squared distance between the query window at (y0, x0) of X
+// and exemplar window n, one warp, lanes striding over each window row.
+__device__ __forceinline__ float window_dist2(const RerankArgs &a, int y0, int x0, int n, int lane) {
+    const int ey = n / a.ex, ex0 = n - ey * a.ex;
+    const int row = 3 * a.w;
+    const float *xq = a.X + ((size_t)y0 * a.Wo + x0) * 3;
+    const float *zn = a.Z + ((size_t)ey * a.We + ex0) * 3;
+    float s = 0.0f;
+    for (int dy = 0; dy < a.w; ++dy) {
+        const float *xr = xq + (size_t)dy * a.Wo * 3;
+        const float *zr = zn + (size_t)dy * a.We * 3;
+        for (int e = lane; e < row; e += 32) {
+            const float t = __ldg(xr + e) - __ldg(zr + e);
+            s = fmaf(t, t, s);
+        }
+    }
+    return warp_sum(s);
+}
+
+__global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restrict__ cand_idx,
+                                                const float *__restrict__ cand_lb,
+                                                const float *__restrict__ tau, int certify,
+                                                int *__restrict__ nn_out, float *__restrict__ d2_out,
+                                                int *__restrict__ fail_list,
+                                                unsigned int *__restrict__ fail_count,
+                                                unsigned long long *__restrict__ best64,
+                                                int *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= a.Q) return;
+    const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
+    const int my_idx = cand_idx[(size_t)q * kTopK + lane];
+    const float my_lb = cand_lb[(size_t)q * kTopK + lane];
+    const float tq = certify ? tau[q] : 0.0f;
+    float best = INFINITY;
+    int best_n = -1;
+    for (int i = 0; i < kTopK; ++i) {
+        const int n = __shfl_sync(kFull, my_idx, i);
+        const float lb = __shfl_sync(kFull, my_lb, i);
+        if (n < 0) break;  // fewer than 32 windows exist
+        if (n >= a.N) {
+            if (lane == 0) atomicOr(status, kDevErrBounds);
+            continue;
+        }
+        if (certify && lb - tq > best) break;  // bounds are ascending
+        const float d = window_dist2(a, y0, x0, n, lane);
+        if (d < best || (d == best && n < best_n)) {
+            best = d;
+            best_n = n;
+        }
+    }
+    const int last_idx = __shfl_sync(kFull, my_idx, kTopK - 1);
+    const float last_lb = __shfl_sync(kFull, my_lb, kTopK - 1);
+    const bool done = !certify || last_idx < 0 || best <= last_lb - tq;
+    if (lane == 0) {
+        if (done) {
+            nn_out[q] = best_n;
+            d2_out[q] = best;
+        } else {
+            const unsigned int slot = atomicAdd(fail_count, 1u);
+            fail_list[slot] = q;
+            best64[q] = pack_dist_idx(best, best_n);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pair_eval(RerankArgs a, const uint2 *__restrict__ pairs,
+                                                   const unsigned int *__restrict__ pair_count,
+                                                   unsigned int pair_cap,
+                                                   unsigned long long *__restrict__ best64) {
+    const unsigned int total = min(*pair_count, pair_cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
+        const uint2 pr = pairs[i];
+        const int q = static_cast<int>(pr.x), n = static_cast<int>(pr.y);
+        if (q >= a.Q || n >= a.N) continue;
+        const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
+        const float d = window_dist2(a, y0, x0, n, lane);
+        if (lane == 0) atomicMin(&best64[q], pack_dist_idx(d, n));
+    }
+}
+
+// One CTA per failing query; each thread scores whole windows (used only when
+// the pruned pass overflowed its pair list).
+__global__ void __launch_bounds__(256) k_brute(RerankArgs a, const int *__restrict__ fail_list,
+                                               const unsigned int *__restrict__ fail_count,
+                                               const unsigned int *__restrict__ pair_count,
+                                               unsigned int pair_cap,
+                                               unsigned int *__restrict__ brute_count,
+                                               unsigned long long *__restrict__ best64,
+                                               int *__restrict__ status) {
+    if (*pair_count <= pair_cap) return;
+    const unsigned int nf = *fail_count;
+    __shared__ unsigned long long red[256];
+    for (unsigned int f = blockIdx.x; f < nf; f += gridDim.x) {
+        const int q = fail_list[f];
+        if (q < 0 || q >= a.Q) {
+            if (threadIdx.x == 0) atomicOr(status, kDevErrBounds);
+            continue;
+        }
+        if (threadIdx.x == 0) atomicAdd(brute_count, 1u);
+        const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
+        unsigned long long mine = ~0ull;
+        for (int n = threadIdx.x; n < a.N; n += blockDim.x) {
+            const int ey = n / a.ex, ex0 = n - ey * a.ex;
+            float s = 0.0f;
+            for (int dy = 0; dy < a.w; ++dy) {
+                const float *xr = a.X + ((size_t)(y0 + dy) * a.Wo + x0) * 3;
+                const float *zr = a.Z + ((size_t)(ey + dy) * a.We + ex0) * 3;
+                for (int e = 0; e < 3 * a.w; ++e) {
+                    const float t = __ldg(xr + e) - __ldg(zr + e);
+                    s = fmaf(t, t, s);
+                }
+            }
+            const unsigned long long pk = pack_dist_idx(s, n);
+            mine = pk < mine ? pk : mine;
+        }
+        red[threadIdx.x] = mine;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                const unsigned long long other = red[threadIdx.x + o];
+                if (other < red[threadIdx.x]) red[threadIdx.x] = other;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) best64[q] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_resolve(const int *__restrict__ fail_list,
+                          const unsigned int *__restrict__ fail_count,
+                          const unsigned long long *__restrict__ best64, int Q,
+                          int *__restrict__ nn_out, float *__restrict__ d2_out) {
+    const unsigned int nf = *fail_count;
+    for (unsigned int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf;
+         f += gridDim.x * blockDim.x) {
+        const int q = fail_list[f];
+        if (q < 0 || q >= Q) continue;
+        const unsigned long long pk = best64[q];
+        nn_out[q] = static_cast<int>(pk & 0xffffffffu);
+        d2_out[q] = __uint_as_float(static_cast<unsigned int>(pk >> 32));
+    }
+}
+
+}  // namespace
+
+void launch_rerank(const RerankArgs &a, const int *cand_idx, const float *cand_lb,
+                   const float *tau, int certify, int *nn_out, float *d2_out, int *fail_list,
+                   unsigned int *fail_count, unsigned long long *best64, int *status,
+                   cudaStream_t st) {
+    if (a.Q == 0) return;
+    const int grid = ceil_div((long)a.Q * 32, 256);
+    ProfScope ps(kProfRerank, st, 1);
+    k_rerank<<<grid, 256, 0, st>>>(a, cand_idx, cand_lb, tau, certify, nn_out, d2_out, fail_list,
+                                   fail_count, best64, status);
+}
+
+void launch_pair_eval(const RerankArgs &a, const uint2 *pairs, const unsigned int *pair_count,
+                      unsigned int pair_cap, unsigned long long *best64, cudaStream_t st) {
+    count_launches(1);
+    k_pair_eval<<<152 * 8, 256, 0, st>>>(a, pairs, pair_count, pair_cap, best64);
+}
+
+void launch_brute_fallback(const RerankArgs &a, const int *fail_list,
+                           const unsigned int *fail_count, const unsigned int *pair_count,
+                           unsigned int pair_cap, unsigned int *brute_count,
+                           unsigned long long *best64, int *status, cudaStream_t st) {
+    count_launches(1);
+    k_brute<<<152 * 2, 256, 0, st>>>(a, fail_list, fail_count, pair_count, pair_cap, brute_count,
+                                     best64, status);
+}
+
+void launch_resolve(const int *fail_list, const unsigned int *fail_count,
+                    const unsigned long long *best64, int Q, int *nn_out, float *d2_out,
+                    cudaStream_t st) {
+    count_launches(1);
+    k_resolve<<<152, 256, 0, st>>>(fail_list, fail_count, best64, Q, nn_out, d2_out);
+}
+
+}  // namespace pts

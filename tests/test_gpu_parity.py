@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are the seeded synthetic exemplars and initialisations of pts_inputs.
+Tolerances: NN indices per the tie rule in tests/_util.py; pixels 1e-4
+absolute (FP32 path); energies 1e-5 relative per E-step, final energy of an
+EM run within 1.001x; eigenvalues 1e-9 relative; PCA projector 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pts_inputs as P
+from _util import check_nn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2006_11851_gb300 as pts  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """64x64 exemplar (shrink 3), w = 8, d = 24: the tiny plain-method workload."""
+    Z = P.synthetic_exemplar(0, 64, 3.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=24)
+    yield Z, idx
+    idx.close()
+
+
+# --------------------------------------------------------------------------
+# pyramid filters
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W", [(64, 64), (37, 22), (1, 5)])
+def test_downsample_upsample(H, W):
+    img = P.SplitMix64(3).uniform(H * W * 3).reshape(H, W, 3).astype(np.float32)
+    g = pts.downsample2(_t(img)).cpu().numpy()
+    np.testing.assert_allclose(g, oracle.downsample2(img), atol=2e-7)
+    g = pts.upsample2(_t(img)).cpu().numpy()
+    np.testing.assert_allclose(g, oracle.upsample2(img), atol=2e-7)
+
+
+# --------------------------------------------------------------------------
+# PCA (section 2.2)
+# --------------------------------------------------------------------------
+def _projector_dist(B1, B2):
+    B1 = np.asarray(B1, np.float64)
+    B2 = np.asarray(B2, np.float64)
+    return np.linalg.norm(B1.T @ B1 - B2.T @ B2)
+
+
+@pytest.mark.parametrize("size,w,d", [(64, 8, 24), (48, 16, 64), (40, 4, 12), (12, 8, 8)])
+def test_pca_fit(size, w, d):
+    Z = P.synthetic_exemplar(1, size, 3.0)
+    mu_o, B_o, ev_o, _ = oracle.pca_fit(Z, w, d)
+    mean, basis, eig, k = pts.pca_fit(_t(Z), w, d)
+    assert k == d
+    eig = eig.cpu().numpy()
+    np.testing.assert_allclose(eig, ev_o[:d], rtol=1e-9, atol=1e-12 * ev_o[0])
+    np.testing.assert_allclose(mean.cpu().numpy(), mu_o, atol=1e-6)
+    gap = ev_o[d - 1] - ev_o[d] if len(ev_o) > d else ev_o[d - 1]
+    if gap > 1e-6 * ev_o[0]:
+        # FP32 export of the basis limits the projector to ~1e-6
+        assert _projector_dist(basis.cpu().numpy(), B_o) < 1e-5
+    Bg = basis.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(Bg @ Bg.T, np.eye(d), atol=1e-5)
+
+
+def test_pca_large_window_gram_branch():
+    """w = 32 (D = 3072) on a 64x64 exemplar: N = 1089 < D."""
+    Z = oracle.exemplar_pyramid(P.synthetic_exemplar(0, 256, 4.0), 3)[0].astype(np.float32)
+    mu_o, B_o, ev_o, _ = oracle.pca_fit(Z, 32, 64)
+    mean, basis, eig, k = pts.pca_fit(_t(Z), 32, 64)
+    np.testing.assert_allclose(eig.cpu().numpy(), ev_o[:64], rtol=1e-9)
+    assert _projector_dist(basis.cpu().numpy(), B_o) < 1e-5
+
+
+def test_pca_variance_fraction():
+    Z = P.synthetic_exemplar(2, 48, 3.0)
+    _, _, ev_o, _ = oracle.pca_fit(Z, 8, 64)
+    # the oracle's full spectrum is min(N, D) values; its sum is the trace
+    frac = np.cumsum(ev_o) / ev_o.sum()
+    want = int(np.searchsorted(frac, 0.95) + 1)
+    _, _, _, k = pts.pca_fit(_t(Z), 8, 0, var_frac=0.95)
+    assert k == min(want, 64)
+
+
+# --------------------------------------------------------------------------
+# E-step (Eq. 4), exact mode
+# --------------------------------------------------------------------------
+def test_nn_search_random_init(c1):
+    Z, idx = c1
+    X = P.random_patch_init(Z, 128, 128, 8, 0)
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "exact")
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, 8, 2)
+    check_nn(X, Z, 8, 2, nn.cpu().numpy(), d2.cpu().numpy(), nn_o, d2_o, max_mismatch_frac=0.01)
+    st = idx.search_stats()
+    assert st["queries"] == 3721
+
+
+def test_nn_search_along_oracle_trajectory(c1):
+    Z, idx = c1
+    X0 = P.random_patch_init(Z, 128, 128, 8, 1)
+    ref = oracle.synthesize_level(Z, X0, 8, 3, keep_trajectory=True)
+    for Xt, nn_o, d2_o, _ in ref["trajectory"]:
+        nn, d2 = pts.nn_search(idx, _t(Xt), 2, "exact")
+        check_nn(Xt, Z, 8, 2, nn.cpu().numpy(), d2.cpu().numpy(), nn_o, d2_o, max_mismatch_frac=0.01)
+
+
+@pytest.mark.parametrize("He,Ho,w,d,stride", [
+    (10, 20, 8, 8, 2),     # N = 9 < 32 candidates
+    (40, 46, 8, 64, 2),    # max d, ragged query count
+    (33, 36, 16, 40, 2),   # D = 768
+    (24, 29, 5, 10, 1),    # stride 1, odd w
+    (30, 40, 8, 20, 4),    # stride 4
+])
+def test_nn_search_edge_cases(He, Ho, w, d, stride):
+    Z = P.synthetic_exemplar(4, He, 3.0)
+    X = P.random_patch_init(Z, Ho, Ho, w, 2)
+    idx = pts.ExemplarIndex(_t(Z), w, d=d)
+    nn, d2 = pts.nn_search(idx, _t(X), stride, "exact")
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, w, stride)
+    check_nn(X, Z, w, stride, nn.cpu().numpy(), d2.cpu().numpy(), nn_o, d2_o)
+    idx.close()
+
+
+def test_nn_search_duplicate_windows_tie_smallest_index():
+    half = P.synthetic_exemplar(5, 20, 3.0)[:, :14]
+    Z = np.ascontiguousarray(np.concatenate([half, half], axis=1))
+    X = np.ascontiguousarray(Z[2:14, 4:16])
+    idx = pts.ExemplarIndex(_t(Z), 4, d=8)
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "exact")
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, 4, 2)
+    np.testing.assert_array_equal(nn.cpu().numpy(), nn_o)
+    assert np.all(d2.cpu().numpy() == 0.0)
+    idx.close()
+
+
+# --------------------------------------------------------------------------
+# IRLS weights / energy (Eqs. 5-8) and M-step (Eq. 8)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("r", [2.0, 0.8])
+def test_irls(r):
+    d2 = (P.SplitMix64(6).uniform(5000) * 3.0).astype(np.float32)
+    d2[:7] = 0.0
+    W_o, E_o, _ = oracle.irls(d2, r, 1e-3)
+    W, E = pts.irls_weights(_t(d2), r, 1e-3)
+    np.testing.assert_allclose(W.cpu().numpy(), W_o, rtol=2e-6)
+    assert abs(E.item() / E_o - 1) < 1e-6
+    W2, E2 = pts.irls_weights(_t(d2), r, 1e-3)
+    assert E2.item() == E.item()  # deterministic reduction
+
+
+@pytest.mark.parametrize("He,Ho,w,stride,weighted", [
+    (64, 128, 8, 2, True), (64, 128, 8, 2, False), (48, 64, 16, 2, True),
+    (40, 37, 5, 1, True), (40, 48, 8, 4, True), (70, 96, 32, 2, True)])
+def test_m_step(He, Ho, w, stride, weighted):
+    Z = P.synthetic_exemplar(7, He, 3.0)
+    idx = pts.ExemplarIndex(_t(Z), w, d=4)
+    Q = oracle.num_queries(Ho, Ho, w, stride)
+    N = oracle.num_exemplar_windows(He, He, w)
+    nn = P.random_nn(8, Q, N)
+    Wt = P.random_weights(9, Q) if weighted else None
+    out = pts.m_step(idx, torch.from_numpy(nn).to(DEV), None if Wt is None else _t(Wt), Ho, Ho, stride)
+    ref = oracle.m_step(nn, None if Wt is None else Wt.astype(np.float64), Z, w, Ho, Ho, stride)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=1e-4)
+    assert np.abs(out.cpu().numpy() - ref).max() < 2e-6
+    idx.close()
+
+
+# --------------------------------------------------------------------------
+# EM (section 2.1): step-wise and end to end
+# --------------------------------------------------------------------------
+def test_em_stepwise_against_oracle(c1):
+    """Each GPU half-step applied to the oracle's own iterate."""
+    Z, idx = c1
+    X0 = P.random_patch_init(Z, 128, 128, 8, 3)
+    ref = oracle.synthesize_level(Z, X0, 8, 4, r=0.8, keep_trajectory=True)
+    traj = ref["trajectory"]
+    for t in range(len(traj) - 1):
+        Xt, nn_o, d2_o, W_o = traj[t]
+        _, d2_g = pts.nn_search(idx, _t(Xt), 2, "exact")
+        W_g, E_g = pts.irls_weights(d2_g, 0.8, 1e-3)
+        assert abs(E_g.item() / ref["E"][t] - 1) < 1e-5
+        out = pts.m_step(idx, torch.from_numpy(nn_o).to(DEV), _t(W_o), 128, 128, 2)
+        np.testing.assert_allclose(out.cpu().numpy(), traj[t + 1][0], atol=1e-4)
+
+
+@pytest.mark.parametrize("r", [2.0, 0.8])
+def test_synthesize_level_end_to_end(c1, r):
+    Z, idx = c1
+    X0 = P.random_patch_init(Z, 128, 128, 8, 4)
+    xt = _t(X0)
+    E = pts.synthesize_level(idx, xt, 5, r=r, mode="exact")
+    ref = oracle.synthesize_level(Z, X0, 8, 5, r=r)
+    np.testing.assert_allclose(E, ref["E"], rtol=1e-3)
+    assert abs(E[-1] / ref["E"][-1] - 1) < 1e-3
+    diff = np.abs(xt.cpu().numpy() - ref["X"])
+    # pixels agree to FP32 rounding unless a near-tie flipped a match somewhere
+    assert np.mean(diff < 1e-4) > 0.99
+    if r == 2.0:
+        assert np.all(np.diff(E) <= 1e-6 * E[0])
+
+
+def test_exact_reproduction_gpu(c1):
+    Z, idx = c1
+    xt = _t(Z)
+    E = pts.synthesize_level(idx, xt, 2, r=2.0, mode="exact")
+    assert np.all(E == 0.0)
+    np.testing.assert_allclose(xt.cpu().numpy(), Z, atol=1e-6)
+
+
+def test_pyramid_three_levels_small():
+    """Coarse-to-fine on a small exemplar: per-level energies against the oracle."""
+    from paper_2006_11851_gb300.pyramid import PyramidIndex, synthesize_pyramid
+    Z = P.synthetic_exemplar(0, 96, 4.0)
+    windows = [8, 8, 8]
+    pidx = PyramidIndex(_t(Z), windows, d=16)
+    pyr_o = oracle.exemplar_pyramid(Z, 3)
+    for zg, zo in zip(pidx.exemplars, pyr_o):
+        np.testing.assert_allclose(zg.cpu().numpy(), zo, atol=1e-6)
+    X0 = P.random_patch_init(pyr_o[0].astype(np.float32), 48, 48, 8, 0)
+    X, E, _ = synthesize_pyramid(pidx, _t(X0), iters=3)
+    Xo = X0
+    for lev in range(3):
+        ref = oracle.synthesize_level(pyr_o[lev].astype(np.float32), Xo, 8, 3)
+        assert abs(E[lev][-1] / ref["E"][-1] - 1) < 1e-3
+        Xo = oracle.upsample2(ref["X"]) if lev < 2 else ref["X"]
+    pidx.close()
+
+
+# --------------------------------------------------------------------------
+# full-size workload, sampled queries
+# --------------------------------------------------------------------------
+def test_full_size_fine_level_sampled():
+    """256x256 exemplar, w = 8, d = 64, 512x512 output: 64,009 queries against
+    62,001 windows, in the launch configuration the benchmark times; the
+    oracle checks a seeded sample of queries."""
+    Z = P.synthetic_exemplar(0, 256, 4.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=64)
+    X = P.random_patch_init(Z, 512, 512, 8, 0)
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "exact")
+    Q = oracle.num_queries(512, 512, 8)
+    sub = P.sample_indices(11, Q, 192)
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, 8, 2, qlist=sub)
+    check_nn(X, Z, 8, 2, nn.cpu().numpy()[sub], d2.cpu().numpy()[sub], nn_o, d2_o, qlist=sub)
+    st = idx.search_stats()
+    assert st["queries"] == Q and st["certified"] + st["range_queries"] == Q
+    idx.close()
+
+
+# --------------------------------------------------------------------------
+# argument errors surface as PtsError, nothing launched
+# --------------------------------------------------------------------------
+def test_invalid_arguments(c1):
+    Z, idx = c1
+    with pytest.raises(pts.PtsError):
+        pts.nn_search(idx, torch.zeros(127, 128, 3, device=DEV), 2, "exact")  # (Ho - w) odd
+    with pytest.raises(pts.PtsError):
+        pts.nn_search(idx, torch.zeros(128, 128, 3, device=DEV), 3, "exact")
+    with pytest.raises(pts.PtsError):
+        pts.ExemplarIndex(_t(Z[:6, :6]), 8)
+    with pytest.raises(pts.PtsError):
+        pts.pca_fit(_t(Z), 8, 65)
