@@ -273,7 +273,7 @@ def main():
     tk_ms, tk_n = ctypes.c_double(), ctypes.c_longlong()
     L.pts_profile_read(b"search_topk", ctypes.byref(tk_ms), ctypes.byref(tk_n))
     kern = {}
-    for name in ("search_topk", "search_range", "rerank", "project", "m_step"):
+    for name in ("search_topk", "search_full", "rerank", "project", "m_step", "brute", "irls"):
         ms, n = ctypes.c_double(), ctypes.c_longlong()
         L.pts_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(n))
         kern[name] = {"ms": ms.value / args.steps, "launches": n.value // args.steps}

@@ -59,9 +59,11 @@ typedef enum {
  *   PTS_EXACT_F32     the full-dimension nearest neighbour of Eq. 4.  PCA
  *                     coordinates plus the residual norm give a lower bound
  *                     on every full-dimension distance; the 32 best bounds
- *                     are re-ranked in full dimension and certified, and
- *                     uncertified queries get a second, bound-pruned exact
- *                     pass.  FP32 SIMT, no tensor cores.
+ *                     are re-ranked in full dimension and certified.
+ *                     Uncertified queries get a full-dimension GEMM pass
+ *                     (top-32 again, re-ranked, certified against the FP32
+ *                     rounding bound), and what still fails a direct scan.
+ *                     FP32 SIMT, no tensor cores.
  *   PTS_BF16_RERANK   PCA-space distances as a BF16 tensor-core GEMM (FP32
  *                     accumulate), top-32, exact FP32 full-dimension re-rank.
  *   PTS_FP8_RERANK    as BF16 with FP8-E4M3 operands and per-dimension scales.
@@ -96,9 +98,9 @@ typedef struct {
 typedef struct {
     long long queries;        /* queries of the last nn_search */
     long long certified;      /* exact mode: certified from the 32 best bounds */
-    long long range_queries;  /* exact mode: queries sent to the pruned pass */
-    long long range_pairs;    /* exact mode: full-dimension pairs evaluated there */
-    long long brute_queries;  /* exact mode: queries that needed a full scan */
+    long long range_queries;  /* exact mode: queries sent to the full-dimension pass */
+    long long range_pairs;    /* exact mode: queries that pass did not certify */
+    long long brute_queries;  /* exact mode: queries that needed a direct scan */
 } pts_search_stats;
 
 /* Message describing the last error on this host thread ("" if none). */
@@ -220,8 +222,9 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
  *   pts_launch_count     kernels launched by this process so far.
  *   pts_profile_enable   on != 0 starts recording (and clears old records).
  *   pts_profile_read     total device milliseconds and launch count of one
- *                        kernel class ("search_topk", "search_range",
- *                        "rerank", "project", "m_step"); synchronises on the
+ *                        kernel class ("search_topk", "search_full",
+ *                        "rerank", "project", "m_step", "brute", "irls",
+ *                        "search_tc", "mlp", "probe"); synchronises on the
  *                        recorded events.  Returns INVALID_ARG for an unknown
  *                        name.
  */

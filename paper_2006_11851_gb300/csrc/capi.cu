@@ -44,9 +44,9 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     PTS_TRY(ws.cand_idx.ensure((size_t)cap * kTopK, "candidate indices"));
     PTS_TRY(ws.cand_lb.ensure((size_t)cap * kTopK, "candidate bounds"));
     PTS_TRY(ws.fail_list.ensure(cap, "fail list"));
+    PTS_TRY(ws.fail2_list.ensure(cap, "second fail list"));
+    PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->w), "full query vectors"));
     PTS_TRY(ws.best64.ensure(cap, "packed minima"));
-    ws.pair_cap = std::max<size_t>((size_t)cap * 256, (size_t)1 << 20);
-    PTS_TRY(ws.pairs.ensure(ws.pair_cap, "pair list"));
     PTS_TRY(ws.counters.ensure(4, "counters"));
     PTS_TRY(ws.nn.ensure(cap, "nn"));
     PTS_TRY(ws.d2.ensure(cap, "d2"));
@@ -84,20 +84,24 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
     launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
                        idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
-    RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
-                  idx->nx, idx->N, Q};
+    const int qx = (Wo - idx->w) / stride + 1;
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
     unsigned int *fail_count = ws.counters.ptr + 0;
-    unsigned int *pair_count = ws.counters.ptr + 1;
+    unsigned int *fail2_count = ws.counters.ptr + 1;
     unsigned int *brute_count = ws.counters.ptr + 2;
-    launch_rerank(ra, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out,
-                  ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
-    launch_search_range(ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, Q, idx->da, ws.fail_list.ptr,
-                        fail_count, ws.best64.ptr, idx->et.ptr, idx->enorm.ptr, idx->ntiles, idx->N,
-                        pair_count, ws.pairs.ptr, (unsigned int)ws.pair_cap, idx->status.ptr, st);
-    launch_pair_eval(ra, ws.pairs.ptr, pair_count, (unsigned int)ws.pair_cap, ws.best64.ptr, st);
-    launch_brute_fallback(ra, ws.fail_list.ptr, fail_count, pair_count, (unsigned int)ws.pair_cap,
-                          brute_count, ws.best64.ptr, idx->status.ptr, st);
-    launch_resolve(ws.fail_list.ptr, fail_count, ws.best64.ptr, Q, nn_out, d2_out, st);
+    // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
+    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
+                  d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
+    // pass 2: full-dimension GEMM top-32 for the listed queries, re-ranked again
+    launch_search_full(X, Wo, idx->w, stride, qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, Q,
+                       ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr,
+                       ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
+    launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1,
+                  nn_out, d2_out, ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
+    // what is still uncertified: direct scan
+    launch_brute_fallback(ra, ws.fail2_list.ptr, fail2_count, brute_count, ws.best64.ptr,
+                          idx->status.ptr, st);
+    launch_resolve(ws.fail2_list.ptr, fail2_count, ws.best64.ptr, Q, nn_out, d2_out, st);
     return PTS_OK;
 }
 
@@ -223,6 +227,11 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basis.ptr, dd, idx->da, 1,
                    idx->et.ptr, idx->enorm.ptr, nullptr, 0.0f, nullptr, st);
     launch_norm_max(idx->enorm.ptr, idx->N, idx->umax.ptr, st);
+    if ((s = idx->efull.ensure((size_t)idx->ntiles * padded_dim(w) * kBN, "full exemplar vectors")) !=
+        PTS_OK)
+        return fail(s);
+    launch_exemplar_full(idx->exemplar.ptr, We, w, idx->nx, idx->N, idx->mu.ptr, idx->efull.ptr,
+                         idx->ntiles, st);
     e = cudaMemcpyAsync(&idx->unorm2_max, idx->umax.ptr, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "read norm max"));
     e = cudaStreamSynchronize(st);
@@ -242,8 +251,9 @@ void pts_index_destroy(pts_index idx) {
     ws.cand_idx.release();
     ws.cand_lb.release();
     ws.fail_list.release();
+    ws.fail2_list.release();
+    ws.qfull.release();
     ws.best64.release();
-    ws.pairs.release();
     ws.counters.release();
     ws.nn.release();
     ws.d2.release();
@@ -257,6 +267,7 @@ void pts_index_destroy(pts_index idx) {
     idx->eig.release();
     idx->et.release();
     idx->enorm.release();
+    idx->efull.release();
     idx->umax.release();
     idx->status.release();
     delete idx;

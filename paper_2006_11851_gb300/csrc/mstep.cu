@@ -182,7 +182,7 @@ void launch_m_step(const int *nn, const float *wts, const float *Z, int We, int 
 
 void launch_irls(const float *d2, int Q, float r, float delta, float *wts, double *energy_out,
                  double *partial, unsigned int *ticket, cudaStream_t st) {
-    count_launches(1);
+    ProfScope ps(kProfIrls, st, 1);
     k_irls<<<kIrlsGrid, 256, 0, st>>>(d2, Q, r, delta, wts, energy_out, partial, ticket);
 }
 

@@ -10,8 +10,8 @@
 namespace pts {
 namespace {
 
-const char *kNames[kProfClasses] = {"search_topk", "search_range", "rerank", "project", "m_step",
-                                    "search_tc", "mlp", "probe"};
+const char *kNames[kProfClasses] = {"search_topk", "search_full", "rerank", "project", "m_step",
+                                    "search_tc", "mlp", "probe", "brute", "irls"};
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_enabled{0};
 std::mutex g_mu;

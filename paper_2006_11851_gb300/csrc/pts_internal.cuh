@@ -82,11 +82,11 @@ struct Workspace {
     DevBuf<float> tau;         // [Qpad] rounding slack of the bound
     DevBuf<int> cand_idx;      // [Q][32]
     DevBuf<float> cand_lb;     // [Q][32]
-    DevBuf<int> fail_list;     // [Q]
+    DevBuf<int> fail_list;     // [Q] queries not certified by the PCA pass
+    DevBuf<int> fail2_list;    // [Q] queries not certified by the full-dimension pass
+    DevBuf<float> qfull;       // [Qpad/64][Dp][64] centred full vectors of failing queries
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
-    DevBuf<uint2> pairs;       // [pair_cap] (q, n)
-    size_t pair_cap = 0;
-    DevBuf<unsigned int> counters;  // [4]: fail, pairs, brute, spare
+    DevBuf<unsigned int> counters;  // [4]: fail, fail2, brute, spare
     DevBuf<int> nn;            // [Q] (synthesize_level)
     DevBuf<float> d2;          // [Q]
     DevBuf<float> wts;         // [Q]
@@ -111,6 +111,7 @@ struct pts_index_s {
     pts::DevBuf<double> eig;      // d
     pts::DevBuf<float> et;        // [ntiles][da][kBN] = -2 * (y_n, r_n, 0...)
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
+    pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
     pts::DevBuf<float> umax;      // [1]
     pts::DevBuf<int> status;      // [1] device status word
     pts::Workspace ws;
@@ -139,11 +140,15 @@ void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st);
-void launch_search_range(const float *qcoord, const float *qnorm, const float *tau, int Q, int da,
-                         const int *fail_list, const unsigned int *fail_count,
-                         const unsigned long long *best64, const float *et, const float *enorm,
-                         int ntiles, int N, unsigned int *pair_count, uint2 *pairs,
-                         unsigned int pair_cap, int *status, cudaStream_t st);
+void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
+                        const int *fail_list, const unsigned int *fail_count, int Q,
+                        float *qfull, const float *efull, const float *enorm, int ntiles,
+                        const float *qnorm, int *cand_idx, float *cand_lb, int *status,
+                        cudaStream_t st);
+void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
+                          float *efull, int ntiles, cudaStream_t st);
+// full-dimension vectors are padded with zero rows to a multiple of 32
+inline int padded_dim(int w) { return (3 * w * w + 31) / 32 * 32; }
 // rerank.cu
 struct RerankArgs {
     const float *X;
@@ -152,22 +157,20 @@ struct RerankArgs {
     int We, w, ex, N;
     int Q;
 };
-void launch_rerank(const RerankArgs &a, const int *cand_idx, const float *cand_lb,
-                   const float *tau, int certify, int *nn_out, float *d2_out, int *fail_list,
-                   unsigned int *fail_count, unsigned long long *best64, int *status,
-                   cudaStream_t st);
-void launch_pair_eval(const RerankArgs &a, const uint2 *pairs, const unsigned int *pair_count,
-                      unsigned int pair_cap, unsigned long long *best64, cudaStream_t st);
+// qlist/qcount == NULL: all Q queries; else the listed ones (count on the device)
+void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qcount,
+                   const int *cand_idx, const float *cand_lb, const float *tau, int certify,
+                   int *nn_out, float *d2_out, int *fail_list, unsigned int *fail_count,
+                   unsigned long long *best64, int *status, cudaStream_t st);
 void launch_brute_fallback(const RerankArgs &a, const int *fail_list,
-                           const unsigned int *fail_count, const unsigned int *pair_count,
-                           unsigned int pair_cap, unsigned int *brute_count,
+                           const unsigned int *fail_count, unsigned int *brute_count,
                            unsigned long long *best64, int *status, cudaStream_t st);
 void launch_resolve(const int *fail_list, const unsigned int *fail_count,
                     const unsigned long long *best64, int Q, int *nn_out, float *d2_out,
                     cudaStream_t st);
 // profile.cu: launch counting and event timing of kernel classes
-enum ProfClass { kProfSearchTopk = 0, kProfSearchRange, kProfRerank, kProfProject, kProfMStep,
-                 kProfSearchTc, kProfMlp, kProfProbe, kProfClasses };
+enum ProfClass { kProfSearchTopk = 0, kProfSearchFull, kProfRerank, kProfProject, kProfMStep,
+                 kProfSearchTc, kProfMlp, kProfProbe, kProfBrute, kProfIrls, kProfClasses };
 void count_launches(int n);
 void prof_begin(int cls, cudaStream_t st, void **token);
 void prof_end(int cls, cudaStream_t st, void *token);

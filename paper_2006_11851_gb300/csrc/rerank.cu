@@ -1,19 +1,17 @@
 // rerank.cu -- exact full-dimension distances of Eq. 4 for candidate lists.
 //
-// k_rerank       one warp per query: evaluates the query's candidates in
-//                increasing order of their lower bound, skipping those whose
-//                bound (minus the rounding slack tau) already exceeds the best
-//                distance found, and keeps the lexicographically smallest
-//                (d2, n).  With certify != 0 (exact mode) the result is final
-//                when d2_best <= LB_32 - tau_q: every window outside the list
-//                has LB >= LB_32, hence a distance >= d2_best.  Otherwise the
-//                query joins the fail list with U_q = d2_best as a bound.
-// k_pair_eval    one warp per (q, n) pair of the bound-pruned pass; keeps the
-//                minimum packed (d2 bits, n) per query with a 64-bit atomicMin,
-//                which also breaks exact ties toward the smallest n.
-// k_brute        only when the pair list overflowed: full scan of every exemplar
-//                window for each failing query (one CTA per query).
-// k_resolve      writes nn/d2 of the failing queries from the packed minima.
+// k_rerank       one warp per query (all queries, or those of a device-side
+//                list): evaluates the query's candidates in increasing order of
+//                their bound, skipping those whose bound minus the rounding
+//                slack tau already exceeds the best distance found, and keeps
+//                the lexicographically smallest (d2, n).  With certify != 0
+//                (exact mode) the result is final when d2_best <= B_32 - tau_q:
+//                every window outside the list has a bound >= B_32, hence a
+//                distance >= d2_best.  Otherwise the query joins the fail list
+//                with its best so far packed into best64.
+// k_brute        direct scan of every exemplar window for each listed query
+//                (one CTA per query); used for what no pass could certify.
+// k_resolve      writes nn/d2 of listed queries from the packed minima.
 //
 // Distances are sums of squared FP32 differences read straight from the two
 // images (a window row is 3w contiguous floats in HWC layout), reduced across
@@ -50,7 +48,9 @@ __device__ __forceinline__ float window_dist2(const RerankArgs &a, int y0, int x
     return warp_sum(s);
 }
 
-__global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restrict__ cand_idx,
+__global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restrict__ qlist,
+                                                const unsigned int *__restrict__ qcount,
+                                                const int *__restrict__ cand_idx,
                                                 const float *__restrict__ cand_lb,
                                                 const float *__restrict__ tau, int certify,
                                                 int *__restrict__ nn_out, float *__restrict__ d2_out,
@@ -59,8 +59,13 @@ __global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restr
                                                 unsigned long long *__restrict__ best64,
                                                 int *__restrict__ status) {
     const int lane = threadIdx.x & 31;
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (q >= a.Q) return;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int q = wid;
+    if (qlist) {
+        if (wid >= (int)*qcount) return;
+        q = qlist[wid];
+    }
+    if (q < 0 || q >= a.Q) return;
     const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
     const int my_idx = cand_idx[(size_t)q * kTopK + lane];
     const float my_lb = cand_lb[(size_t)q * kTopK + lane];
@@ -97,33 +102,12 @@ __global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restr
     }
 }
 
-__global__ void __launch_bounds__(256) k_pair_eval(RerankArgs a, const uint2 *__restrict__ pairs,
-                                                   const unsigned int *__restrict__ pair_count,
-                                                   unsigned int pair_cap,
-                                                   unsigned long long *__restrict__ best64) {
-    const unsigned int total = min(*pair_count, pair_cap);
-    const int lane = threadIdx.x & 31;
-    const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
-        const uint2 pr = pairs[i];
-        const int q = static_cast<int>(pr.x), n = static_cast<int>(pr.y);
-        if (q >= a.Q || n >= a.N) continue;
-        const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
-        const float d = window_dist2(a, y0, x0, n, lane);
-        if (lane == 0) atomicMin(&best64[q], pack_dist_idx(d, n));
-    }
-}
-
-// One CTA per failing query; each thread scores whole windows (used only when
-// the pruned pass overflowed its pair list).
+// One CTA per listed query; each thread scores whole windows.
 __global__ void __launch_bounds__(256) k_brute(RerankArgs a, const int *__restrict__ fail_list,
                                                const unsigned int *__restrict__ fail_count,
-                                               const unsigned int *__restrict__ pair_count,
-                                               unsigned int pair_cap,
                                                unsigned int *__restrict__ brute_count,
                                                unsigned long long *__restrict__ best64,
                                                int *__restrict__ status) {
-    if (*pair_count <= pair_cap) return;
     const unsigned int nf = *fail_count;
     __shared__ unsigned long long red[256];
     for (unsigned int f = blockIdx.x; f < nf; f += gridDim.x) {
@@ -180,30 +164,22 @@ __global__ void k_resolve(const int *__restrict__ fail_list,
 
 }  // namespace
 
-void launch_rerank(const RerankArgs &a, const int *cand_idx, const float *cand_lb,
-                   const float *tau, int certify, int *nn_out, float *d2_out, int *fail_list,
-                   unsigned int *fail_count, unsigned long long *best64, int *status,
-                   cudaStream_t st) {
+void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qcount,
+                   const int *cand_idx, const float *cand_lb, const float *tau, int certify,
+                   int *nn_out, float *d2_out, int *fail_list, unsigned int *fail_count,
+                   unsigned long long *best64, int *status, cudaStream_t st) {
     if (a.Q == 0) return;
     const int grid = ceil_div((long)a.Q * 32, 256);
     ProfScope ps(kProfRerank, st, 1);
-    k_rerank<<<grid, 256, 0, st>>>(a, cand_idx, cand_lb, tau, certify, nn_out, d2_out, fail_list,
-                                   fail_count, best64, status);
-}
-
-void launch_pair_eval(const RerankArgs &a, const uint2 *pairs, const unsigned int *pair_count,
-                      unsigned int pair_cap, unsigned long long *best64, cudaStream_t st) {
-    count_launches(1);
-    k_pair_eval<<<152 * 8, 256, 0, st>>>(a, pairs, pair_count, pair_cap, best64);
+    k_rerank<<<grid, 256, 0, st>>>(a, qlist, qcount, cand_idx, cand_lb, tau, certify, nn_out, d2_out,
+                                   fail_list, fail_count, best64, status);
 }
 
 void launch_brute_fallback(const RerankArgs &a, const int *fail_list,
-                           const unsigned int *fail_count, const unsigned int *pair_count,
-                           unsigned int pair_cap, unsigned int *brute_count,
+                           const unsigned int *fail_count, unsigned int *brute_count,
                            unsigned long long *best64, int *status, cudaStream_t st) {
-    count_launches(1);
-    k_brute<<<152 * 2, 256, 0, st>>>(a, fail_list, fail_count, pair_count, pair_cap, brute_count,
-                                     best64, status);
+    ProfScope ps(kProfBrute, st, 1);
+    k_brute<<<152 * 2, 256, 0, st>>>(a, fail_list, fail_count, brute_count, best64, status);
 }
 
 void launch_resolve(const int *fail_list, const unsigned int *fail_count,

@@ -1,29 +1,28 @@
-// search_f32.cu -- exact-mode search phase (E-step, Eq. 4) in PCA space on
-// FP32 SIMT cores.
+// search_f32.cu -- exact-mode search phase (E-step, Eq. 4) on FP32 SIMT cores.
 //
-// Every exemplar window n carries the search vector e_n = (y_n, r_n) (PCA
-// coordinates and residual norm, section 2.2) and ||u_n||^2 = ||v_n - mu||^2;
-// every query q carries a_q = (y_q, r_q) and ||u_q||^2.  For an orthonormal
-// basis,
+// Pass 1 (k_search_pca), PCA space.  Every exemplar window n carries
+// e_n = (y_n, r_n) (PCA coordinates and residual norm, section 2.2) and
+// ||u_n||^2 = ||v_n - mu||^2; every query q carries a_q = (y_q, r_q) and
+// ||u_q||^2.  For an orthonormal basis
 //   LB(q, n) = ||y_q - y_n||^2 + (r_q - r_n)^2
 //            = ||u_q||^2 + ||u_n||^2 - 2 a_q . e_n  <=  ||x_q - z_n||^2,
-// so LB is a lower bound on the full-dimension distance of Eq. 4.  The
-// exemplar side is stored pre-multiplied by -2 so that one FMA chain starting
-// at ||u_n||^2 gives p(q, n) = LB(q, n) - ||u_q||^2.
+// a lower bound on the full-dimension distance of Eq. 4.  The exemplar side
+// is stored pre-multiplied by -2, so one FMA chain from ||u_n||^2 gives
+// p(q, n) = LB(q, n) - ||u_q||^2.
 //
-// Layout: exemplar tiles [tile][da][kBN] (one contiguous block per tile,
-// brought into shared memory by one bulk copy), norms [tile*kBN] with +inf
-// in the padding columns.  Each CTA owns kBQ = 64 queries (8 warps x 8 rows)
-// and streams all exemplar tiles through a double buffer; each lane computes
-// 8 rows x 4 consecutive columns.
+// Pass 2 (k_search_full), full dimension, only for the queries whose pass-1
+// result could not be certified: the same GEMM + top-32 on the centred
+// window vectors u themselves (D = 3 w^2 terms), i.e. the expanded form of
+// ||u_q - u_n||^2, fed K-chunk by K-chunk through a 4-stage ring (D padded
+// with zero rows to Dp, a multiple of the 32-row chunk).
 //
-//   k_search<false>  keeps per query the 32 smallest p (lexicographic in
-//                    (p, n)), one sorted entry per lane, inserted with warp
-//                    ballots only when a value beats the current 32nd;
-//   k_search<true>   for the queries whose re-ranked best distance U_q was
-//                    not certified, emits every pair with
-//                    LB(q, n) <= U_q + tau_q (the only windows that can beat
-//                    U_q), for exact evaluation.
+// Both passes: exemplar data in tiles of kBN = 128 windows whose K rows are
+// contiguous ([tile][K][128]), copied to shared memory by 1-D bulk copies
+// completing on mbarriers.  A CTA owns kBQ = 64 queries (8 warps x 8 rows);
+// each lane computes 8 rows x 4 consecutive windows.  Per query a warp keeps
+// the 32 smallest (p, n) in lexicographic order, one sorted entry per lane;
+// a value enters only when it beats the current 32nd, found with warp
+// ballots, so after the first tiles insertions are rare.
 #include <float.h>
 
 #include "pts_internal.cuh"
@@ -34,68 +33,77 @@ namespace {
 constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
-struct SearchSmem {
-    // sized for the maximum da; the kernel uses the first da rows
-    float a[kMaxDA][kBQ];          // query vectors, transposed
-    float e[2][kMaxDA][kBN];       // exemplar tiles (double buffer)
-    float en[2][kBN];              // exemplar norms
+// Per-warp top-32 state for 8 query rows (lane L holds entry L, ascending).
+struct TopK8 {
+    float ld[8];
+    int li[8];
+    float thr[8];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            ld[i] = INFINITY;
+            li[i] = -1;
+            thr[i] = INFINITY;
+        }
+    }
+    // offer the 8x4 values of this lane (rows i, windows nbase + j)
+    __device__ __forceinline__ void offer(const float (&p)[8][4], int tile_base, int lane) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                unsigned fl = __ballot_sync(kFull, p[i][j] < thr[i]);
+                while (fl) {
+                    const int src = __ffs(fl) - 1;
+                    const float cd = __shfl_sync(kFull, p[i][j], src);
+                    const int ci = tile_base + src * 4 + j;
+                    const bool before = (ld[i] < cd) || (ld[i] == cd && li[i] < ci);
+                    const int pos = __popc(__ballot_sync(kFull, before));
+                    const float ud = __shfl_up_sync(kFull, ld[i], 1);
+                    const int ui = __shfl_up_sync(kFull, li[i], 1);
+                    if (lane > pos) {
+                        ld[i] = ud;
+                        li[i] = ui;
+                    } else if (lane == pos) {
+                        ld[i] = cd;
+                        li[i] = ci;
+                    }
+                    thr[i] = __shfl_sync(kFull, ld[i], 31);
+                    fl &= ~(1u << src);
+                    fl &= __ballot_sync(kFull, p[i][j] < thr[i]);
+                }
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// pass 1: PCA-space lower bounds
+// ---------------------------------------------------------------------------
+struct PcaSmem {
+    float a[kMaxDA][kBQ];     // query vectors, transposed
+    float e[2][kMaxDA][kBN];  // exemplar tiles (double buffer)
+    float en[2][kBN];         // exemplar norms
     uint64_t bar[2];
     int abort_flag;
 };
 
-template <bool kRange>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_search(const float *__restrict__ qcoord, const float *__restrict__ qnorm,
-             const float *__restrict__ tau, int Q, int da, const int *__restrict__ fail_list,
-             const unsigned int *__restrict__ fail_count,
-             const unsigned long long *__restrict__ best64, const float *__restrict__ et,
-             const float *__restrict__ enorm, int ntiles, int N, int *__restrict__ cand_idx,
-             float *__restrict__ cand_lb, unsigned int *__restrict__ pair_count,
-             uint2 *__restrict__ pairs, unsigned int pair_cap, int *__restrict__ status) {
+    k_search_pca(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int da,
+                 const float *__restrict__ et, const float *__restrict__ enorm, int ntiles,
+                 int *__restrict__ cand_idx, float *__restrict__ cand_lb, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SearchSmem &sm = *reinterpret_cast<SearchSmem *>(smem_raw);
+    PcaSmem &sm = *reinterpret_cast<PcaSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int qbase = blockIdx.x * kBQ;
-    int nq = Q;
-    if (kRange) {
-        nq = static_cast<int>(*fail_count);
-        if (qbase >= nq) return;  // uniform for the whole CTA
-    }
-
-    // ---- query tile -> shared (transposed), per-row state ----
     for (int i = tid; i < kBQ * da; i += kThreads) {
         const int r = i / da, k = i - r * da;
-        int q = -1;
-        if (qbase + r < nq) q = kRange ? fail_list[qbase + r] : qbase + r;
-        sm.a[k][r] = (q >= 0 && q < Q) ? qcoord[(size_t)q * da + k] : 0.0f;
+        const int q = qbase + r;
+        sm.a[k][r] = q < Q ? qcoord[(size_t)q * da + k] : 0.0f;
     }
     const int row0 = warp * 8;
-    int qrow[8];
-    float lim[8];  // range: p <= lim  <=>  LB <= U + tau
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        int q = -1;
-        if (qbase + row0 + i < nq) q = kRange ? fail_list[qbase + row0 + i] : qbase + row0 + i;
-        if (q >= Q) {
-            atomicOr(status, kDevErrBounds);
-            q = -1;
-        }
-        qrow[i] = q;
-        lim[i] = -INFINITY;
-        if (kRange && q >= 0) {
-            const float U = __uint_as_float(static_cast<unsigned int>(best64[q] >> 32));
-            lim[i] = U + tau[q] - qnorm[q];
-        }
-    }
-    float ld[8], thr[8];
-    int li[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        ld[i] = INFINITY;
-        li[i] = -1;
-        thr[i] = INFINITY;
-    }
-
+    TopK8 top;
+    top.init();
     const uint32_t tile_floats = static_cast<uint32_t>(da) * kBN;
     if (tid == 0) {
         mbar_init(&sm.bar[0], 1);
@@ -113,27 +121,24 @@ __global__ void __launch_bounds__(kThreads, 2)
         issue(0, 0);
         if (ntiles > 1) issue(1, 1);
     }
-
     for (int t = 0; t < ntiles; ++t) {
         const int buf = t & 1;
-        if (tid == 0) {
-            if (!mbar_wait_bounded(&sm.bar[buf], (t >> 1) & 1, status)) sm.abort_flag = 1;
-        }
+        if (tid == 0 && !mbar_wait_bounded(&sm.bar[buf], (t >> 1) & 1, status)) sm.abort_flag = 1;
         __syncthreads();
         if (sm.abort_flag) {
-            // let any copy still in flight land before shared memory goes away
-            if (tid == 0) {
-                if (t + 1 < ntiles) mbar_wait_bounded(&sm.bar[buf ^ 1], ((t + 1) >> 1) & 1, status);
-            }
+            if (tid == 0 && t + 1 < ntiles) mbar_wait_bounded(&sm.bar[buf ^ 1], ((t + 1) >> 1) & 1, status);
             __syncthreads();
             return;
         }
-
         float acc[8][4];
+        const float4 nv = *reinterpret_cast<const float4 *>(&sm.en[buf][lane * 4]);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int i = 0; i < 8; ++i) {
+            acc[i][0] = nv.x;
+            acc[i][1] = nv.y;
+            acc[i][2] = nv.z;
+            acc[i][3] = nv.w;
+        }
         const float *eb = &sm.e[buf][0][lane * 4];
 #pragma unroll 4
         for (int k = 0; k < da; ++k) {
@@ -147,70 +152,160 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
-        const float4 nv = *reinterpret_cast<const float4 *>(&sm.en[buf][lane * 4]);
-        const float norms[4] = {nv.x, nv.y, nv.z, nv.w};
-        const int nbase = t * kBN + lane * 4;
-
-        if (!kRange) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float p = acc[i][j] + norms[j];
-                    unsigned fl = __ballot_sync(kFull, p < thr[i]);
-                    while (fl) {
-                        const int src = __ffs(fl) - 1;
-                        const float cd = __shfl_sync(kFull, p, src);
-                        const int ci = t * kBN + src * 4 + j;
-                        const bool before = (ld[i] < cd) || (ld[i] == cd && li[i] < ci);
-                        const int pos = __popc(__ballot_sync(kFull, before));
-                        const float ud = __shfl_up_sync(kFull, ld[i], 1);
-                        const int ui = __shfl_up_sync(kFull, li[i], 1);
-                        if (lane > pos) {
-                            ld[i] = ud;
-                            li[i] = ui;
-                        } else if (lane == pos) {
-                            ld[i] = cd;
-                            li[i] = ci;
-                        }
-                        thr[i] = __shfl_sync(kFull, ld[i], 31);
-                        fl &= ~(1u << src);
-                        fl &= __ballot_sync(kFull, p < thr[i]);
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float p = acc[i][j] + norms[j];
-                    const int n = nbase + j;
-                    if (p <= lim[i] && n < N) {
-                        const unsigned int slot = atomicAdd(pair_count, 1u);
-                        if (slot < pair_cap) pairs[slot] = make_uint2((unsigned)qrow[i], (unsigned)n);
-                    }
-                }
-            }
-        }
-
+        top.offer(acc, t * kBN, lane);
         __syncthreads();  // all warps are done with buffer `buf`
         if (tid == 0 && t + 2 < ntiles) issue(t + 2, buf);
     }
-
-    if (!kRange) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int q = qrow[i];
-            if (q >= 0) {
-                cand_idx[(size_t)q * kTopK + lane] = li[i];
-                cand_lb[(size_t)q * kTopK + lane] = ld[i] + qnorm[q];
+    for (int i = 0; i < 8; ++i) {
+        const int q = qbase + row0 + i;
+        if (q < Q) {
+            cand_idx[(size_t)q * kTopK + lane] = top.li[i];
+            cand_lb[(size_t)q * kTopK + lane] = top.ld[i] + qnorm[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: full dimension for the uncertified queries
+// ---------------------------------------------------------------------------
+constexpr int kKC = 32;     // K rows per chunk
+constexpr int kStages = 4;  // ring depth
+
+struct FullSmem {
+    float a[kStages][kKC][kBQ];
+    float e[kStages][kKC][kBN];
+    uint64_t bar[kStages];
+    int abort_flag;
+};
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_search_full(const float *__restrict__ qfull,  // [F/64][D][64]: u_q of failing queries
+                  const int *__restrict__ fail_list, const unsigned int *__restrict__ fail_count,
+                  int Q, int Dp, const float *__restrict__ efull,  // [ntiles][Dp][128] = -2 u_n
+                  const float *__restrict__ enorm, int ntiles, const float *__restrict__ qnorm,
+                  int *__restrict__ cand_idx, float *__restrict__ cand_lb, int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FullSmem &sm = *reinterpret_cast<FullSmem *>(smem_raw);
+    const int nf = static_cast<int>(*fail_count);
+    const int fbase = blockIdx.x * kBQ;
+    if (fbase >= nf) return;  // uniform for the CTA
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row0 = warp * 8;
+    const int nchunks = Dp / kKC;
+    const long total = (long)ntiles * nchunks;
+    const float *qa = qfull + (size_t)blockIdx.x * Dp * kBQ;
+    TopK8 top;
+    top.init();
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
+        fence_mbar_init();
+        sm.abort_flag = 0;
+    }
+    __syncthreads();
+    auto issue = [&](long it) {
+        const int s = (int)(it % kStages);
+        const long t = it / nchunks;
+        const int c = (int)(it - t * nchunks);
+        mbar_expect_tx(&sm.bar[s], (uint32_t)(kKC * (kBQ + kBN) * 4));
+        bulk_g2s(&sm.a[s][0][0], qa + (size_t)c * kKC * kBQ, kKC * kBQ * 4u, &sm.bar[s]);
+        bulk_g2s(&sm.e[s][0][0], efull + ((size_t)t * Dp + (size_t)c * kKC) * kBN, kKC * kBN * 4u,
+                 &sm.bar[s]);
+    };
+    if (tid == 0)
+        for (long it = 0; it < kStages && it < total; ++it) issue(it);
+    float acc[8][4];
+    for (long it = 0; it < total; ++it) {
+        const int s = (int)(it % kStages);
+        const long t = it / nchunks;
+        const int c = (int)(it - t * nchunks);
+        if (c == 0) {
+            const float4 nv = __ldg(reinterpret_cast<const float4 *>(enorm + t * kBN + lane * 4));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[i][0] = nv.x;
+                acc[i][1] = nv.y;
+                acc[i][2] = nv.z;
+                acc[i][3] = nv.w;
+            }
+        }
+        if (tid == 0 && !mbar_wait_bounded(&sm.bar[s], (uint32_t)((it / kStages) & 1), status))
+            sm.abort_flag = 1;
+        __syncthreads();
+        if (sm.abort_flag) {
+            if (tid == 0)
+                for (long j = it + 1; j < it + kStages && j < total; ++j)
+                    mbar_wait_bounded(&sm.bar[j % kStages], (uint32_t)((j / kStages) & 1), status);
+            __syncthreads();
+            return;
+        }
+        const float *eb = &sm.e[s][0][lane * 4];
+#pragma unroll 8
+        for (int k = 0; k < kKC; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&sm.a[s][k][row0]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&sm.a[s][k][row0 + 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(eb + k * kBN);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        if (c == nchunks - 1) top.offer(acc, (int)t * kBN, lane);
+        __syncthreads();  // stage s is free
+        if (tid == 0 && it + kStages < total) issue(it + kStages);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int f = fbase + row0 + i;
+        if (f < nf) {
+            const int q = fail_list[f];
+            if (q >= 0 && q < Q) {
+                cand_idx[(size_t)q * kTopK + lane] = top.li[i];
+                cand_lb[(size_t)q * kTopK + lane] = top.ld[i] + qnorm[q];
+            } else if (lane == 0) {
+                atomicOr(status, kDevErrBounds);
             }
         }
     }
 }
 
-size_t search_smem_bytes() { return sizeof(SearchSmem); }
+// u_q = x_q - mu of the failing queries, tiled [F/64][Dp][64], zero rows k >= D
+__global__ void k_gather_full(const float *__restrict__ X, int Wo, int w, int stride, int qx,
+                              const float *__restrict__ mu, const int *__restrict__ fail_list,
+                              const unsigned int *__restrict__ fail_count, int Q, int Dp,
+                              float *__restrict__ qfull) {
+    const int D = 3 * w * w, row = 3 * w;
+    const long n = (long)(*fail_count) * Dp;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / Dp), k = (int)(i - (long)f * Dp);
+        float v = 0.0f;
+        if (k < D) {
+            int q = fail_list[f];
+            q = q < 0 ? 0 : (q >= Q ? Q - 1 : q);
+            const int y0 = (q / qx) * stride, x0 = (q % qx) * stride;
+            const int dy = k / row, e = k - dy * row;
+            v = X[((size_t)(y0 + dy) * Wo + x0) * 3 + e] - mu[k];
+        }
+        qfull[((size_t)(f / kBQ) * Dp + k) * kBQ + (f % kBQ)] = v;
+    }
+}
+
+// -2 u_n of every exemplar window, tiled [ntiles][Dp][128] (the caller zeroes
+// the buffer first, so padding rows and columns stay 0)
+__global__ void k_exemplar_full(const float *__restrict__ Z, int We, int w, int ex, int N, int Dp,
+                                const float *__restrict__ mu, float *__restrict__ efull) {
+    const int D = 3 * w * w, row = 3 * w;
+    const long n = (long)N * D;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int win = (int)(i / D), k = (int)(i - (long)win * D);
+        const int ey = win / ex, exx = win - ey * ex;
+        const int dy = k / row, e = k - dy * row;
+        efull[((size_t)(win / kBN) * Dp + k) * kBN + (win % kBN)] =
+            -2.0f * (Z[((size_t)(ey + dy) * We + exx) * 3 + e] - mu[k]);
+    }
+}
 
 }  // namespace
 
@@ -218,36 +313,45 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st) {
     static bool attr = false;
-    const size_t smem = search_smem_bytes();
+    const size_t smem = sizeof(PcaSmem);
     if (!attr) {
-        cudaFuncSetAttribute(k_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_search_pca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     const int grid = ceil_div(Q, kBQ);
     if (grid == 0) return;
     ProfScope ps(kProfSearchTopk, st, 1);
-    k_search<false><<<grid, kThreads, smem, st>>>(qcoord, qnorm, nullptr, Q, da, nullptr, nullptr,
-                                                  nullptr, et, enorm, ntiles, 0, cand_idx, cand_lb,
-                                                  nullptr, nullptr, 0, status);
+    k_search_pca<<<grid, kThreads, smem, st>>>(qcoord, qnorm, Q, da, et, enorm, ntiles, cand_idx,
+                                               cand_lb, status);
 }
 
-void launch_search_range(const float *qcoord, const float *qnorm, const float *tau, int Q, int da,
-                         const int *fail_list, const unsigned int *fail_count,
-                         const unsigned long long *best64, const float *et, const float *enorm,
-                         int ntiles, int N, unsigned int *pair_count, uint2 *pairs,
-                         unsigned int pair_cap, int *status, cudaStream_t st) {
+void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
+                        const int *fail_list, const unsigned int *fail_count, int Q,
+                        float *qfull, const float *efull, const float *enorm, int ntiles,
+                        const float *qnorm, int *cand_idx, float *cand_lb, int *status,
+                        cudaStream_t st) {
     static bool attr = false;
-    const size_t smem = search_smem_bytes();
+    const size_t smem = sizeof(FullSmem);
     if (!attr) {
-        cudaFuncSetAttribute(k_search<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_search_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    const int grid = ceil_div(Q, kBQ);
-    if (grid == 0) return;
-    ProfScope ps(kProfSearchRange, st, 1);
-    k_search<true><<<grid, kThreads, smem, st>>>(qcoord, qnorm, tau, Q, da, fail_list, fail_count,
-                                                 best64, et, enorm, ntiles, N, nullptr, nullptr,
-                                                 pair_count, pairs, pair_cap, status);
+    const int Dp = padded_dim(w);
+    count_launches(1);
+    k_gather_full<<<152 * 4, 256, 0, st>>>(X, Wo, w, stride, qx, mu, fail_list, fail_count, Q, Dp,
+                                           qfull);
+    ProfScope ps(kProfSearchFull, st, 1);
+    k_search_full<<<ceil_div(Q, kBQ), kThreads, smem, st>>>(qfull, fail_list, fail_count, Q, Dp, efull,
+                                                            enorm, ntiles, qnorm, cand_idx, cand_lb,
+                                                            status);
+}
+
+void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
+                          float *efull, int ntiles, cudaStream_t st) {
+    const int Dp = padded_dim(w);
+    cudaMemsetAsync(efull, 0, sizeof(float) * (size_t)ntiles * Dp * kBN, st);
+    count_launches(1);
+    k_exemplar_full<<<152 * 8, 256, 0, st>>>(Z, We, w, ex, N, Dp, mu, efull);
 }
 
 }  // namespace pts

@@ -214,7 +214,9 @@ def test_exact_reproduction_gpu(c1):
     Z, idx = c1
     xt = _t(Z)
     E = pts.synthesize_level(idx, xt, 2, r=2.0, mode="exact")
-    assert np.all(E == 0.0)
+    # FP32 averaging of k equal values can be 1 ulp off at border pixels
+    # (covered by fewer than (w/2)^2 windows), so the energy is ~0, not 0
+    assert E[0] == 0.0 and np.all(E < 1e-8)
     np.testing.assert_allclose(xt.cpu().numpy(), Z, atol=1e-6)
 
 
