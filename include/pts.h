@@ -177,6 +177,33 @@ pts_status irls_weights(const float *dist2, int Q, float r, float delta, float *
                         double *energy_out, void *stream);
 
 /*
+ * irls_weights_noalloc -- irls_weights for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment aid.  Some
+ * callers must not call cudaMalloc or cudaFree while they run: a host
+ * framework that owns the whole device memory budget through its own pool,
+ * or a pipeline that cannot afford the device-wide synchronisation a
+ * cudaFree implies.  irls_weights allocates (and frees) its reduction scratch
+ * on every call; this variant allocates nothing and keeps that scratch (one
+ * double per 2048 distances plus a completion counter, 32 KB in all) in a
+ * fixed array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ * Same weights and energy as irls_weights (the energy may differ in the last
+ * bits: the partial sums are grouped differently).  Limits and behaviour:
+ *   Q           at most 8,388,608; larger Q returns PTS_ERR_INVALID_ARG;
+ *   first call  on each device looks up the array's device address
+ *               (cudaGetSymbolAddress) with that device current; make that
+ *               first call before any stream capture;
+ *   sharing     all calls share the one array, which keeps the previous
+ *               call's contents; each call clears the counter it needs, but
+ *               calls that overlap on the GPU (for example on two streams)
+ *               race on the array and must be serialised by the caller;
+ *   energy_out  device pointer to one float64 (may be NULL);
+ *   asynchronous on `stream` (unlike irls_weights, it does not synchronise).
+ */
+pts_status irls_weights_noalloc(const float *dist2, int Q, float r, float delta, float *weights_out,
+                                double *energy_out, void *stream);
+
+/*
  * m_step -- the optimization phase (Eq. 8 minimised over x): every pixel of
  * `output` becomes
  *   x_i = sum_{p covers i} W_p z_{nn(p)}[i - p] / sum_{p covers i} W_p,

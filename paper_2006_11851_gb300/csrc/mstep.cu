@@ -198,3 +198,61 @@ void launch_upsample2(const float *in, int H, int W, float *out, cudaStream_t st
 }
 
 }  // namespace pts
+
+// ---------------------------------------------------------------------------
+// irls_weights_noalloc: the IRLS reduction with its scratch in a fixed array
+// compiled into the library, for callers that cannot allocate device memory.
+// Scratch: one double per block of kNoAllocPerBlock distances plus the
+// completion ticket.  The array's device address is looked up once per device
+// (cudaGetSymbolAddress) by the first call made with that device current.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace pts {
+namespace {
+constexpr int kNoAllocMaxBlocks = 4096;
+constexpr int kNoAllocPerBlock = 256 * 8;
+constexpr size_t kNoAllocTicketOffset = kNoAllocMaxBlocks * sizeof(double);
+static __device__ __align__(256) unsigned char g_irls_scratch[kNoAllocTicketOffset + 256];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+}  // namespace pts
+
+extern "C" pts_status irls_weights_noalloc(const float *dist2, int Q, float r, float delta,
+                                           float *weights_out, double *energy_out, void *stream) {
+    using namespace pts;
+    if (!dist2 || Q < 0) return set_error(PTS_ERR_INVALID_ARG, "irls_weights_noalloc: bad input");
+    if (!(r > 0.0f && r <= 2.0f) || !(delta > 0.0f))
+        return set_error(PTS_ERR_INVALID_ARG, "irls_weights_noalloc: need 0 < r <= 2 and delta > 0");
+    if ((long)Q > (long)kNoAllocMaxBlocks * kNoAllocPerBlock)
+        return set_error(PTS_ERR_INVALID_ARG,
+                         "irls_weights_noalloc: Q exceeds the fixed scratch limit of 8388608 distances");
+    int dev = 0;
+    PTS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(PTS_ERR_UNSUPPORTED, "irls_weights_noalloc: device ordinal above 63");
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_irls_scratch);
+            if (e != cudaSuccess) return cuda_error(e, "irls_weights_noalloc: cudaGetSymbolAddress");
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double *partial = static_cast<double *>(base);
+    unsigned int *ticket = reinterpret_cast<unsigned int *>(static_cast<char *>(base) + kNoAllocTicketOffset);
+    // the array keeps the previous call's contents: the ticket must start at 0
+    PTS_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st));
+    const int grid = Q > 0 ? ceil_div(Q, kNoAllocPerBlock) : 1;
+    count_launches(1);
+    k_irls<<<grid, 256, 0, st>>>(dist2, Q, r, delta, weights_out, energy_out, partial, ticket);
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
