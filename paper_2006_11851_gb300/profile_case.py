@@ -1,0 +1,52 @@
+"""Runs E-steps of one level of the benchmark workload, for profiling a kernel in isolation.
+
+    python -m paper_2006_11851_gb300.profile_case --level 2 --mode exact --steps 2
+
+Levels follow the 3-level workload (256x256 exemplar, shrink 4; windows 32/16/8; outputs
+128/256/512, d = 64).  The output image is a seeded random-patch initialisation.  Prints the
+per-E-step device time of each step.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import paper_2006_11851_gb300 as pts  # noqa: E402
+import pts_inputs as P  # noqa: E402
+
+LEVELS = [(64, 32, 128), (128, 16, 256), (256, 8, 512)]  # (exemplar, window, output)
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--level", type=int, default=2)
+    ap.add_argument("--mode", default="exact")
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--d", type=int, default=64)
+    args = ap.parse_args()
+    He, w, Ho = LEVELS[args.level]
+    dev = torch.device("cuda:0")
+    Z = P.synthetic_exemplar(0, 256, 4.0)
+    z = torch.from_numpy(Z).to(dev)
+    for _ in range(2 - args.level):
+        z = pts.downsample2(z)
+    idx = pts.ExemplarIndex(z.contiguous(), w, d=args.d)
+    X = torch.from_numpy(P.random_patch_init(z.cpu().numpy(), Ho, Ho, w, 0)).to(dev)
+    for s in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pts.nn_search(idx, X, 2, args.mode)
+        e1.record()
+        e1.synchronize()
+        print(f"step {s}: {e0.elapsed_time(e1):.3f} ms  {idx.search_stats()}")
+    idx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
