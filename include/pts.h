@@ -256,6 +256,14 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
  *                        name.
  */
 long long pts_launch_count(void);
+
+/* Self-test of the tensor-core operand layout (no counterpart in the paper):
+ * one 128 x N x K BF16 tcgen05 MMA through the same shared-memory and
+ * instruction descriptors the search uses, on seeded data generated here,
+ * compared with an FP64 host product.  N, K multiples of 16 (N <= 256,
+ * K <= 128).  Writes the largest absolute error and the largest |reference|.
+ * Synchronises the device. */
+pts_status pts_tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref);
 void pts_profile_enable(int on);
 pts_status pts_profile_read(const char *kernel, double *total_ms, long long *launches);
 

@@ -20,6 +20,13 @@ thread_local std::string g_last_error;
 // norms; c = 8 leaves a wide margin.
 constexpr float kTauC = 8.0f;
 
+// Margin added to a warm-start bound for the BF16 search.  The bound is
+// computed from the very BF16 operands the tensor cores multiply, so it only
+// differs from the search's values by FP32 summation order over K <= 80
+// terms of size <= ||u_q|| ||u_n||: 2^-16 (||u_q||^2 + max_n ||u_n||^2)
+// covers that with a wide margin.
+constexpr float kWarmEps = 1.0f / 65536.0f;
+
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 pts_status check_grid(int H, int W, int w, int stride, const char *what) {
@@ -47,6 +54,7 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     PTS_TRY(ws.fail2_list.ensure(cap, "second fail list"));
     PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->w), "full query vectors"));
     PTS_TRY(ws.best64.ensure(cap, "packed minima"));
+    PTS_TRY(ws.thr0.ensure(cap, "warm-start bounds"));
     PTS_TRY(ws.counters.ensure(4, "counters"));
     PTS_TRY(ws.nn.ensure(cap, "nn"));
     PTS_TRY(ws.d2.ensure(cap, "d2"));
@@ -119,7 +127,24 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
         case PTS_EXACT_F32:
             PTS_TRY(search_exact(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
             break;
-        case PTS_BF16_RERANK:
+        case PTS_BF16_RERANK: {
+            Workspace &ws = idx->ws;
+            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0,
+                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
+            // the candidate lists of the previous search on this grid seed the bound
+            const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
+            if (warm)
+                launch_warm_threshold(ws.cand_idx.ptr, ws.qcoord.ptr, ws.qnorm.ptr, idx->etc.ptr, idx->umax.ptr, Q,
+                                      idx->d, idx->da, idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
+            launch_search_tc(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->d, idx->da, idx->ktc, idx->etc.ptr,
+                             idx->ntiles, warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr,
+                             idx->status.ptr, st);
+            RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
+                          idx->nx, idx->N, Q};
+            launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
+                          ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
+            break;
+        }
         case PTS_FP8_RERANK:
         case PTS_PROPOSAL_BF16:
             return set_error(PTS_ERR_UNSUPPORTED, "nn_search: mode not available in this build");
@@ -127,6 +152,10 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             return set_error(PTS_ERR_INVALID_ARG, "nn_search: unknown mode");
     }
     PTS_CUDA_TRY(cudaGetLastError());
+    idx->ws.warm_q = Q;
+    idx->ws.warm_ho = Ho;
+    idx->ws.warm_wo = Wo;
+    idx->ws.warm_stride = stride;
     return PTS_OK;
 }
 
@@ -232,6 +261,11 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return fail(s);
     launch_exemplar_full(idx->exemplar.ptr, We, w, idx->nx, idx->N, idx->mu.ptr, idx->efull.ptr,
                          idx->ntiles, st);
+    idx->ktc = tc_padded_k(dd);
+    if ((s = idx->etc.ensure((size_t)idx->ntiles * kBN * idx->ktc, "bf16 exemplar tiles")) != PTS_OK)
+        return fail(s);
+    launch_pack_exemplar_bf16(idx->et.ptr, idx->enorm.ptr, idx->ntiles, dd, idx->da, idx->ktc, idx->etc.ptr,
+                              st);
     e = cudaMemcpyAsync(&idx->unorm2_max, idx->umax.ptr, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "read norm max"));
     e = cudaStreamSynchronize(st);
@@ -268,6 +302,7 @@ void pts_index_destroy(pts_index idx) {
     idx->et.release();
     idx->enorm.release();
     idx->efull.release();
+    idx->etc.release();
     idx->umax.release();
     idx->status.release();
     delete idx;
@@ -371,6 +406,11 @@ pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int st
                                  cudaMemcpyDeviceToHost, st));
     PTS_CUDA_TRY(cudaStreamSynchronize(st));
     return read_status(idx, st);
+}
+
+pts_status pts_tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref) {
+    if (!max_abs_err || !max_abs_ref) return set_error(PTS_ERR_INVALID_ARG, "pts_tc_selftest: null pointer");
+    return tc_selftest(N, K, max_abs_err, max_abs_ref);
 }
 
 pts_status pts_downsample2(const float *in, int H, int W, float *out, void *stream) {

@@ -2,6 +2,7 @@
 // public ABI, which is include/pts.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -86,6 +87,8 @@ struct Workspace {
     DevBuf<int> fail2_list;    // [Q] queries not certified by the full-dimension pass
     DevBuf<float> qfull;       // [Qpad/64][Dp][64] centred full vectors of failing queries
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
+    DevBuf<float> thr0;        // [Q] warm-start bounds
+    int warm_q = -1, warm_ho = -1, warm_wo = -1, warm_stride = -1;  // geometry of cand_idx
     DevBuf<unsigned int> counters;  // [4]: fail, fail2, brute, spare
     DevBuf<int> nn;            // [Q] (synthesize_level)
     DevBuf<float> d2;          // [Q]
@@ -112,6 +115,8 @@ struct pts_index_s {
     pts::DevBuf<float> et;        // [ntiles][da][kBN] = -2 * (y_n, r_n, 0...)
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
     pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
+    pts::DevBuf<__nv_bfloat16> etc;  // [ntiles][128 x Ktc] BF16 MMA operand tiles
+    int ktc = 0;                  // K of the tensor-core search
     pts::DevBuf<float> umax;      // [1]
     pts::DevBuf<int> status;      // [1] device status word
     pts::Workspace ws;
@@ -147,6 +152,17 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
                         cudaStream_t st);
 void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st);
+// search_tc.cu
+int tc_padded_k(int d);
+void launch_pack_exemplar_bf16(const float *et, const float *enorm, int ntiles, int d, int da, int K,
+                               __nv_bfloat16 *out, cudaStream_t st);
+void launch_search_tc(const float *qcoord, const float *qnorm, int Q, int d, int da, int K,
+                      const __nv_bfloat16 *etile, int ntiles, const float *thr0, int *cand_idx, float *cand_lb,
+                      int *status, cudaStream_t st);
+void launch_warm_threshold(const int *prev_idx, const float *qcoord, const float *qnorm,
+                           const __nv_bfloat16 *etile, const float *umax, int Q, int d, int da, int K, int N,
+                           float eps_scale, float *thr0, cudaStream_t st);
+pts_status tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref);
 // full-dimension vectors are padded with zero rows to a multiple of 32
 inline int padded_dim(int w) { return (3 * w * w + 31) / 32 * 32; }
 // rerank.cu

@@ -1,0 +1,107 @@
+"""Precision modes of the search phase (tensor cores) against the FP64 oracle.
+
+BF16 mode: PCA-space distances from a tcgen05 BF16 GEMM (FP32 accumulation),
+top-32, exact FP32 full-dimension re-rank.  It is not certified, so parity is
+stated as errors against the oracle's exact search: the returned window can
+never beat the exact minimum, its reported distance is the exact FP32
+full-dimension distance of that window, the index mismatch rate is bounded,
+and the end-to-end energy stays within 1.01x of exact mode.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import pts_inputs as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2006_11851_gb300 as pts  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+@pytest.mark.parametrize("N,K", [(64, 80), (64, 32), (128, 64), (16, 16)])
+def test_tensor_core_operand_layout(N, K):
+    L = pts.lib()
+    L.pts_tc_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    err, ref = ctypes.c_double(), ctypes.c_double()
+    assert L.pts_tc_selftest(N, K, ctypes.byref(err), ctypes.byref(ref)) == 0
+    assert ref.value > 1.0
+    assert err.value <= 1e-5 * ref.value * K
+
+
+def _check_not_better_than_exact(X, Z, w, nn_g, d2_g, nn_o, d2_o):
+    pd = oracle.pair_dist2(X, Z, w, 2, np.arange(len(nn_g)), nn_g)
+    np.testing.assert_allclose(d2_g, pd, rtol=1e-5, atol=1e-6)  # exact distance of the chosen window
+    assert np.all(pd >= d2_o * (1 - 1e-12) - 1e-12)               # never below the true minimum
+    return float(np.mean(nn_g != nn_o)), float(np.max(pd / np.maximum(d2_o, 1e-12)))
+
+
+def _ideal_pca_top32_mismatch(X, Z, w, d, nn_o):
+    """Mismatch rate of the same method in exact arithmetic: the oracle's FP64
+    PCA bound, its 32 best windows re-ranked in full dimension."""
+    mu, B, _, _ = oracle.pca_fit(Z, w, d)
+    ye, _, re = oracle.project(Z, w, 1, mu, B)
+    yq, _, rq = oracle.project(X, w, 2, mu, B)
+    lb = ((yq[:, None, :] - ye[None, :, :]) ** 2).sum(-1) + (rq[:, None] - re[None, :]) ** 2
+    top = np.argsort(lb, axis=1, kind="stable")[:, :32]
+    q = np.repeat(np.arange(len(yq)), top.shape[1])
+    dd = oracle.pair_dist2(X, Z, w, 2, q, top.reshape(-1)).reshape(top.shape)
+    best = top[np.arange(len(top)), np.argmin(dd, axis=1)]
+    return float(np.mean(best != nn_o))
+
+
+@pytest.mark.parametrize("He,Ho,w,d", [(64, 128, 8, 24), (48, 64, 16, 64), (40, 60, 8, 64)])
+def test_bf16_search_against_oracle(He, Ho, w, d):
+    Z = P.synthetic_exemplar(0, He, 3.0)
+    idx = pts.ExemplarIndex(_t(Z), w, d=d)
+    X = P.random_patch_init(Z, Ho, Ho, w, 5)
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "bf16")
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, w, 2)
+    mism, worst = _check_not_better_than_exact(X, Z, w, nn.cpu().numpy(), d2.cpu().numpy().astype(np.float64),
+                                               nn_o, d2_o)
+    ideal = _ideal_pca_top32_mismatch(X, Z, w, d, nn_o)
+    # BF16 rounding may cost a little on top of what the PCA top-32 itself misses
+    assert mism <= ideal + 0.02, (mism, ideal)
+    idx.close()
+
+
+def test_bf16_energy_within_1_01_of_exact():
+    Z = P.synthetic_exemplar(0, 64, 3.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=24)
+    X0 = P.random_patch_init(Z, 128, 128, 8, 6)
+    xe, xb = _t(X0), _t(X0)
+    Ee = pts.synthesize_level(idx, xe, 5, mode="exact")
+    Eb = pts.synthesize_level(idx, xb, 5, mode="bf16")
+    # the final energy of both outputs, measured by the exact search
+    nn, d2 = pts.nn_search(idx, xb, 2, "exact")
+    Eb_exact = float(d2.double().sum())
+    assert Eb_exact <= 1.01 * Ee[-1], (Eb_exact, Ee[-1], Eb[-1])
+    idx.close()
+
+
+def test_bf16_full_size_fine_level_sampled():
+    Z = P.synthetic_exemplar(0, 256, 4.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=64)
+    X = P.random_patch_init(Z, 512, 512, 8, 0)
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "bf16")
+    Q = oracle.num_queries(512, 512, 8)
+    sub = P.sample_indices(12, Q, 128)
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, 8, 2, qlist=sub)
+    nn_g, d2_g = nn.cpu().numpy()[sub], d2.cpu().numpy()[sub].astype(np.float64)
+    pd = oracle.pair_dist2(X, Z, 8, 2, sub, nn_g)
+    np.testing.assert_allclose(d2_g, pd, rtol=1e-5, atol=1e-6)
+    assert np.all(pd >= d2_o * (1 - 1e-12))
+    assert np.mean(nn_g != nn_o) < 0.05
+    idx.close()
