@@ -82,13 +82,13 @@ def _declare(L: ctypes.CDLL) -> None:
 
 
 def _declare_learn(L: ctypes.CDLL) -> None:
+    L.or_kmeans_pp.argtypes = [_d, _I, _I, _I, _d, _d, _i32]
     L.or_kmeans_assign.argtypes = [_d, _I, _I, _d, _I, _i32, _d]
-    L.or_kmeans_update.argtypes = [_d, _I, _I, _i32, _I, _d, _i32]
-    L.or_mlp_forward.argtypes = [_d, _I, _I, _I, _I, _I, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d]
-    L.or_mlp_backward.argtypes = [_d, _I, _I, _I, _I, _I, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
-                                  _i32, _d, _d, _d, _d, _d, _d, _d]
+    L.or_kmeans_update.argtypes = [_d, _I, _I, _i32, _I, _d, _i32, _d]
+    L.or_mlp_forward.argtypes = [_d, _I, _I, _I, _I, _I] + [_d] * 11
     L.or_ce_loss.argtypes = [_d, _I, _I, _i32, _d]
     L.or_ce_loss.restype = _D
+    L.or_mlp_backward.argtypes = [_d, _I, _I, _I, _I, _I] + [_d] * 11 + [_i32] + [_d] * 6
 
 
 def _p(a: np.ndarray, ctype=ctypes.c_double):
@@ -321,3 +321,92 @@ def synthesize_level(Z, X0, w: int, iters: int, r: float = 2.0, delta: float = 1
     if keep_trajectory:
         out["trajectory"] = traj
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned cluster proposal (replaces the k-means tree of section 2.2)
+# ---------------------------------------------------------------------------
+def kmeans_pp(Y, k: int, u):
+    """k-means++ seeding with the given uniforms u[k] in [0, 1)."""
+    Y, u = _f64(Y), _f64(u)
+    n, d = Y.shape
+    C = np.empty((k, d))
+    idx = np.empty(k, np.int32)
+    lib().or_kmeans_pp(_p(Y), n, d, k, _p(u), _p(C), _p(idx, ctypes.c_int32))
+    return C, idx
+
+
+def kmeans_assign(Y, C):
+    Y, C = _f64(Y), _f64(C)
+    n, d = Y.shape
+    a = np.empty(n, np.int32)
+    cost = np.empty(n)
+    lib().or_kmeans_assign(_p(Y), n, d, _p(C), C.shape[0], _p(a, ctypes.c_int32), _p(cost))
+    return a, cost
+
+
+def kmeans_update(Y, assign, k: int, cost=None):
+    Y = _f64(Y)
+    assign = _i32a(assign)
+    n, d = Y.shape
+    C = np.zeros((k, d))
+    cnt = np.empty(k, np.int32)
+    cst = None if cost is None else _f64(cost)
+    lib().or_kmeans_update(_p(Y), n, d, _p(assign, ctypes.c_int32), k, _p(C), _p(cnt, ctypes.c_int32),
+                           None if cst is None else _p(cst))
+    return C, cnt
+
+
+def kmeans(Y, k: int, u, iters: int = 25):
+    """(centroids, assignment, inertia per iteration): k-means++ then Lloyd,
+    stopping early when the assignment no longer changes."""
+    C, _ = kmeans_pp(Y, k, u)
+    a_prev, hist = None, []
+    for _ in range(iters):
+        a, cost = kmeans_assign(Y, C)
+        hist.append(float(cost.sum()))
+        if a_prev is not None and np.array_equal(a, a_prev):
+            break
+        C, _ = kmeans_update(Y, a, k, cost)
+        a_prev = a
+    a, cost = kmeans_assign(Y, C)
+    return C, a, hist
+
+
+MLP_SHAPES = (64, 256, 256, 1024)
+
+
+def mlp_forward(X, params):
+    """params: dict W1 b1 W2 b2 W3 b3 (rows = outputs).  Returns the cache."""
+    X = _f64(X)
+    B, din = X.shape
+    W1, b1, W2, b2, W3, b3 = (_f64(params[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    h1, h2, out = W1.shape[0], W2.shape[0], W3.shape[0]
+    c = {"A1": np.empty((B, h1)), "H1": np.empty((B, h1)), "A2": np.empty((B, h2)),
+         "H2": np.empty((B, h2)), "Z": np.empty((B, out))}
+    lib().or_mlp_forward(_p(X), B, din, h1, h2, out, _p(W1), _p(b1), _p(W2), _p(b2), _p(W3), _p(b3),
+                         _p(c["A1"]), _p(c["H1"]), _p(c["A2"]), _p(c["H2"]), _p(c["Z"]))
+    return c
+
+
+def ce_loss(Z, labels):
+    Z = _f64(Z)
+    labels = _i32a(labels)
+    P = np.empty_like(Z)
+    loss = lib().or_ce_loss(_p(Z), Z.shape[0], Z.shape[1], _p(labels, ctypes.c_int32), _p(P))
+    return loss, P
+
+
+def mlp_backward(X, params, cache, P, labels):
+    X = _f64(X)
+    labels = _i32a(labels)
+    B, din = X.shape
+    W1, b1, W2, b2, W3, b3 = (_f64(params[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    h1, h2, out = W1.shape[0], W2.shape[0], W3.shape[0]
+    g = {"W1": np.empty_like(W1), "b1": np.empty_like(b1), "W2": np.empty_like(W2), "b2": np.empty_like(b2),
+         "W3": np.empty_like(W3), "b3": np.empty_like(b3)}
+    lib().or_mlp_backward(_p(X), B, din, h1, h2, out, _p(W1), _p(b1), _p(W2), _p(b2), _p(W3), _p(b3),
+                          _p(_f64(cache["A1"])), _p(_f64(cache["H1"])), _p(_f64(cache["A2"])),
+                          _p(_f64(cache["H2"])), _p(_f64(P)), _p(labels, ctypes.c_int32),
+                          _p(g["W1"]), _p(g["b1"]), _p(g["W2"]), _p(g["b2"]), _p(g["W3"]), _p(g["b3"]))
+    return g
