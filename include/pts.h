@@ -101,7 +101,21 @@ typedef struct {
     long long range_queries;  /* exact mode: queries sent to the full-dimension pass */
     long long range_pairs;    /* exact mode: queries that pass did not certify */
     long long brute_queries;  /* exact mode: queries that needed a direct scan */
+    long long fallback_queries; /* proposal mode: queries sent to the exact search */
 } pts_search_stats;
+
+/* Parameters of the learned cluster proposal (pts_train_proposal). */
+typedef struct {
+    int n_clusters;        /* k-means clusters over the exemplar's PCA vectors, 4..1024 */
+    int kmeans_iters;      /* Lloyd iteration cap (0 = 25) */
+    int epochs;            /* training epochs (0 = 8) */
+    int batch;             /* minibatch size, a multiple of 8 (0 = 4096) */
+    float lr;              /* peak AdamW learning rate, cosine decay to 0 (0 = 1e-3) */
+    float weight_decay;    /* AdamW decoupled weight decay (0 = 1e-4) */
+    float fallback_factor; /* exact fallback when the re-ranked distance exceeds this many
+                              times the median distance of the window's cluster (0 = 1.2) */
+    unsigned long long seed; /* k-means++ uniforms, weight initialisation and batch order */
+} pts_proposal_params;
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *pts_last_error(void);
@@ -161,6 +175,50 @@ pts_status pts_index_device_status(pts_index index, void *stream);
  */
 pts_status nn_search(pts_index index, const float *output, int Ho, int Wo, int stride, int mode,
                      int32_t *nn_out, float *dist2_out, void *stream);
+
+/*
+ * pts_project_queries -- PCA coordinates y_q = B^T (x_q - mu) (section 2.2) of every query
+ * window of `output` (device Ho x Wo x 3), written to y_out (device Q x d float32, row-major).
+ * Used to collect training pairs for the proposal.  Asynchronous.
+ */
+pts_status pts_project_queries(pts_index index, const float *output, int Ho, int Wo, int stride, float *y_out,
+                               void *stream);
+
+/*
+ * pts_train_proposal -- builds the learned cluster proposal of PTS_PROPOSAL_BF16, which takes
+ * the place of the paper's k-means search tree (section 2.2):
+ *   1. k-means (k-means++ seeding, Lloyd) over the exemplar windows' PCA coordinates;
+ *   2. labels: the cluster of each training pair's exact nearest window; per-cluster median
+ *      of the pairs' nearest-neighbour distances (global median for clusters with < 5 pairs);
+ *   3. trains the network 64 -> 256 -> 256 -> n_clusters (GELU) with softmax cross-entropy and
+ *      AdamW on BF16 tensor-core GEMMs with FP32 master weights.
+ * y       device n x d float32: query PCA coordinates (pts_project_queries);
+ * nn, d2  device n int32 / float32: their exact nearest windows and squared distances
+ *         (nn_search in PTS_EXACT_F32).
+ * loss_out host array of `epochs` doubles (mean loss of each epoch's last batch), may be NULL.
+ * Synchronises `stream`.
+ */
+pts_status pts_train_proposal(pts_index index, const float *y, const int32_t *nn, const float *d2, int n,
+                              const pts_proposal_params *params, double *loss_out, void *stream);
+
+/* Standalone k-means (test support, no counterpart in the paper): points device n x d float32,
+ * u host k doubles in [0, 1) (k-means++ uniforms), centroids_out device k x d float32,
+ * assign_out device n int32.  Returns the Lloyd iterations run in *iters_out (host, may be
+ * NULL).  Synchronises the stream. */
+pts_status pts_kmeans(const float *points, int n, int d, int k, const double *u, int iters,
+                      float *centroids_out, int32_t *assign_out, int *iters_out, void *stream);
+
+/* One forward/backward pass of the proposal network (test support): params device float32
+ * packed [W1 256x64, b1 256, W2 256x256, b2 256, W3 Cx256, b3 C] (row-major [out][in]), X device
+ * B x 64 float32 (rounded to BF16 here, as in training), labels device B int32; writes the
+ * gradients of the mean cross-entropy (same packing) to grads_out and the loss to *loss_out
+ * (host).  Synchronises the stream. */
+pts_status pts_mlp_grad(int C, const float *params, const float *X, const int32_t *labels, int B,
+                        float *grads_out, double *loss_out, void *stream);
+
+/* Self-test of the BF16 tensor-core GEMM (test support): C = A B^T + bias, GELU, on seeded
+ * data against an FP64 host product; writes the largest relative error.  Synchronises. */
+pts_status pts_gemm_selftest(int M, int N, int K, double *max_rel_err);
 
 /* Statistics of the last nn_search on this index (synchronises `stream`). */
 pts_status pts_index_search_stats(pts_index index, pts_search_stats *stats, void *stream);

@@ -13,12 +13,17 @@ from ._binding import (  # noqa: F401
     PtsError,
     build_exemplar_index,
     downsample2,
+    gemm_selftest,
     irls_weights,
+    kmeans,
     lib,
     m_step,
+    mlp_grad,
     nn_search,
     pca_fit,
+    project_queries,
     synthesize_level,
+    train_proposal,
     upsample2,
 )
 from .pyramid import synthesize_pyramid  # noqa: F401

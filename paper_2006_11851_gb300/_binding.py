@@ -41,7 +41,13 @@ class _IndexInfo(ctypes.Structure):
 class _SearchStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_longlong), ("certified", ctypes.c_longlong),
                 ("range_queries", ctypes.c_longlong), ("range_pairs", ctypes.c_longlong),
-                ("brute_queries", ctypes.c_longlong)]
+                ("brute_queries", ctypes.c_longlong), ("fallback_queries", ctypes.c_longlong)]
+
+
+class _ProposalParams(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_int), ("kmeans_iters", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("lr", ctypes.c_float), ("weight_decay", ctypes.c_float),
+                ("fallback_factor", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
 
 
 _vp = ctypes.c_void_p
@@ -84,8 +90,16 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 
 
 def _declare_optional(L: ctypes.CDLL) -> None:
-    """Entry points of later layers (declared when the library exports them)."""
-    return None
+    """Entry points of the learned proposal and the test-support self-tests."""
+    L.pts_project_queries.argtypes = [_vp, _vp, _I, _I, _I, _vp, _vp]
+    L.pts_train_proposal.argtypes = [_vp, _vp, _vp, _vp, _I, ctypes.POINTER(_ProposalParams), _vp, _vp]
+    L.pts_kmeans.argtypes = [_vp, _I, _I, _I, _vp, _I, _vp, _vp, ctypes.POINTER(_I), _vp]
+    L.pts_mlp_grad.argtypes = [_I, _vp, _vp, _vp, _I, _vp, ctypes.POINTER(_Dd), _vp]
+    L.pts_gemm_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd)]
+    L.pts_tc_selftest.argtypes = [_I, _I, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
+    L.pts_launch_count.restype = ctypes.c_longlong
+    L.pts_profile_enable.argtypes = [_I]
+    L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
 
 
 def _check(status: int) -> None:
@@ -252,3 +266,63 @@ def upsample2(img: torch.Tensor) -> torch.Tensor:
     out = torch.empty(2 * H, 2 * W, 3, device=img.device, dtype=torch.float32)
     _check(lib().pts_upsample2(_ptr(img), H, W, _ptr(out), _stream()))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned cluster proposal
+# ---------------------------------------------------------------------------
+def project_queries(index: ExemplarIndex, output: torch.Tensor, stride: int = 2) -> torch.Tensor:
+    """PCA coordinates [Q, d] of every query window of `output`."""
+    _need(output, torch.float32, "output")
+    Ho, Wo, _ = output.shape
+    y = torch.empty(index.num_queries(Ho, Wo, stride), index.d, device=output.device, dtype=torch.float32)
+    _check(lib().pts_project_queries(index.handle, _ptr(output), Ho, Wo, stride, _ptr(y), _stream()))
+    return y
+
+
+def train_proposal(index: ExemplarIndex, y: torch.Tensor, nn: torch.Tensor, d2: torch.Tensor, n_clusters: int = 1024,
+                   kmeans_iters: int = 25, epochs: int = 8, batch: int = 4096, lr: float = 1e-3,
+                   weight_decay: float = 1e-4, fallback_factor: float = 1.2, seed: int = 0) -> np.ndarray:
+    """Builds the proposal of mode "proposal" on `index`; returns the per-epoch loss."""
+    _need(y, torch.float32, "y")
+    _need(nn, torch.int32, "nn")
+    _need(d2, torch.float32, "d2")
+    n = y.shape[0]
+    if y.shape[1] != index.d or nn.numel() != n or d2.numel() != n:
+        raise ValueError("y must be [n, d] with one nn and d2 per row")
+    p = _ProposalParams(n_clusters, kmeans_iters, epochs, batch, lr, weight_decay, fallback_factor, seed)
+    loss = np.zeros(max(epochs, 1))
+    _check(lib().pts_train_proposal(index.handle, _ptr(y), _ptr(nn), _ptr(d2), n, ctypes.byref(p),
+                                    loss.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return loss
+
+
+def kmeans(points: torch.Tensor, k: int, u: np.ndarray, iters: int = 25):
+    """(centroids [k, d], assignment [n], Lloyd iterations) on the GPU."""
+    _need(points, torch.float32, "points")
+    n, d = points.shape
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    C = torch.empty(k, d, device=points.device, dtype=torch.float32)
+    a = torch.empty(n, device=points.device, dtype=torch.int32)
+    it = ctypes.c_int(0)
+    _check(lib().pts_kmeans(_ptr(points), n, d, k, u.ctypes.data_as(ctypes.c_void_p), iters, _ptr(C), _ptr(a),
+                            ctypes.byref(it), _stream()))
+    return C, a, it.value
+
+
+def mlp_grad(C: int, params: torch.Tensor, X: torch.Tensor, labels: torch.Tensor):
+    """(gradients, loss) of one forward/backward pass of the proposal network."""
+    _need(params, torch.float32, "params")
+    _need(X, torch.float32, "X")
+    _need(labels, torch.int32, "labels")
+    g = torch.empty_like(params)
+    loss = ctypes.c_double(0.0)
+    _check(lib().pts_mlp_grad(C, _ptr(params), _ptr(X), _ptr(labels), X.shape[0], _ptr(g), ctypes.byref(loss),
+                              _stream()))
+    return g, loss.value
+
+
+def gemm_selftest(M: int, N: int, K: int) -> float:
+    e = ctypes.c_double(0.0)
+    _check(lib().pts_gemm_selftest(M, N, K, ctypes.byref(e)))
+    return e.value

@@ -4,7 +4,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
+#include <vector>
 
 #include "pts_internal.cuh"
 
@@ -82,6 +84,50 @@ pts_status read_status(pts_index idx, cudaStream_t st) {
     return PTS_OK;
 }
 
+// Exact search for the queries listed in ws.fail_list (count on the device): full-dimension
+// GEMM top-32, certified re-rank, direct scan for what is still uncertified.
+void exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail_count, unsigned int *fail2_count,
+                   unsigned int *brute_count, int32_t *nn_out, float *d2_out, cudaStream_t st) {
+    Workspace &ws = idx->ws;
+    launch_search_full(ra.X, ra.Wo, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
+                       ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr,
+                       ws.cand_lb.ptr, idx->status.ptr, st);
+    launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out,
+                  ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
+    launch_brute_fallback(ra, ws.fail2_list.ptr, fail2_count, brute_count, ws.best64.ptr, idx->status.ptr, st);
+    launch_resolve(ws.fail2_list.ptr, fail2_count, ws.best64.ptr, ra.Q, nn_out, d2_out, st);
+}
+
+// the learned proposal: network -> 4 clusters -> probe -> re-rank -> exact fallback
+pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q, int32_t *nn_out,
+                           float *d2_out, cudaStream_t st) {
+    Workspace &ws = idx->ws;
+    ProposalState &pr = idx->prop;
+    if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no proposal trained on this index");
+    const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
+    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
+                   ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
+    PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
+    PTS_TRY(pr.mlp.ensure(pr.C, std::min(Q, kMlpChunk), st));
+    for (int q0 = 0; q0 < Q; q0 += kMlpChunk) {
+        const int B = std::min(kMlpChunk, Q - q0);
+        mlp_gather(pr.mlp, ws.qcoord.ptr + (size_t)q0 * idx->da, idx->d, idx->da, nullptr, 0, B, nullptr, st);
+        mlp_forward(pr.mlp, B, 0, idx->status.ptr, st);
+        launch_top4(pr.mlp.z.ptr, B, pr.C, pr.top.ptr + (size_t)q0 * 4, st);
+    }
+    launch_probe(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, pr.top.ptr, pr.off.ptr, pr.members.ptr, pr.mrow.ptr,
+                 pr.mnorm.ptr, ws.cand_idx.ptr, ws.cand_lb.ptr, st);
+    const int qx = (Wo - idx->w) / stride + 1;
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
+    PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
+    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
+                  ws.fail_list.ptr, ws.counters.ptr + 3, ws.best64.ptr, idx->status.ptr, st);
+    launch_fallback(nn_out, d2_out, Q, pr.assign.ptr, pr.median.ptr, pr.factor, idx->N, ws.fail_list.ptr,
+                    ws.counters.ptr + 0, st);
+    exact_on_list(idx, ra, ws.counters.ptr + 0, ws.counters.ptr + 1, ws.counters.ptr + 2, nn_out, d2_out, st);
+    return PTS_OK;
+}
+
 // the E-step in exact mode (see include/pts.h)
 pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q,
                         int32_t *nn_out, float *d2_out, cudaStream_t st) {
@@ -100,16 +146,7 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
                   d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
-    // pass 2: full-dimension GEMM top-32 for the listed queries, re-ranked again
-    launch_search_full(X, Wo, idx->w, stride, qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, Q,
-                       ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr,
-                       ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
-    launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1,
-                  nn_out, d2_out, ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
-    // what is still uncertified: direct scan
-    launch_brute_fallback(ra, ws.fail2_list.ptr, fail2_count, brute_count, ws.best64.ptr,
-                          idx->status.ptr, st);
-    launch_resolve(ws.fail2_list.ptr, fail2_count, ws.best64.ptr, Q, nn_out, d2_out, st);
+    exact_on_list(idx, ra, fail_count, fail2_count, brute_count, nn_out, d2_out, st);
     return PTS_OK;
 }
 
@@ -145,8 +182,10 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
             break;
         }
-        case PTS_FP8_RERANK:
         case PTS_PROPOSAL_BF16:
+            PTS_TRY(search_proposal(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
+            break;
+        case PTS_FP8_RERANK:
             return set_error(PTS_ERR_UNSUPPORTED, "nn_search: mode not available in this build");
         default:
             return set_error(PTS_ERR_INVALID_ARG, "nn_search: unknown mode");
@@ -303,6 +342,23 @@ void pts_index_destroy(pts_index idx) {
     idx->enorm.release();
     idx->efull.release();
     idx->etc.release();
+    {
+        ProposalState &pr = idx->prop;
+        pr.centroids.release();
+        pr.assign.release();
+        pr.counts.release();
+        pr.off.release();
+        pr.members.release();
+        pr.mrow.release();
+        pr.mnorm.release();
+        pr.median.release();
+        pr.top.release();
+        MlpState &m = pr.mlp;
+        for (auto *b : {&m.params, &m.grads, &m.adam_m, &m.adam_v, &m.a1, &m.a2, &m.z, &m.dh, &m.loss}) b->release();
+        for (auto *b : {&m.wb, &m.wt, &m.xb, &m.xt, &m.h1b, &m.h1t, &m.h2b, &m.h2t, &m.dzb, &m.dzt, &m.dab, &m.dat})
+            b->release();
+        m.labels.release();
+    }
     idx->umax.release();
     idx->status.release();
     delete idx;
@@ -339,12 +395,19 @@ pts_status pts_index_search_stats(pts_index idx, pts_search_stats *stats, void *
     if (!idx || !stats) return set_error(PTS_ERR_INVALID_ARG, "pts_index_search_stats: null pointer");
     cudaStream_t st = as_stream(stream);
     *stats = idx->last;
-    if (idx->ws.counters.ptr && idx->last_mode == PTS_EXACT_F32) {
+    stats->fallback_queries = 0;
+    if (idx->ws.counters.ptr && (idx->last_mode == PTS_EXACT_F32 || idx->last_mode == PTS_PROPOSAL_BF16)) {
         unsigned int c[4] = {0, 0, 0, 0};
         PTS_CUDA_TRY(cudaMemcpyAsync(c, idx->ws.counters.ptr, sizeof(c), cudaMemcpyDeviceToHost, st));
         PTS_CUDA_TRY(cudaStreamSynchronize(st));
-        stats->range_queries = c[0];
-        stats->certified = stats->queries - c[0];
+        if (idx->last_mode == PTS_EXACT_F32) {
+            stats->range_queries = c[0];
+            stats->certified = stats->queries - c[0];
+        } else {
+            stats->fallback_queries = c[0];
+            stats->range_queries = 0;
+            stats->certified = 0;
+        }
         stats->range_pairs = c[1];
         stats->brute_queries = c[2];
     }
@@ -406,6 +469,172 @@ pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int st
                                  cudaMemcpyDeviceToHost, st));
     PTS_CUDA_TRY(cudaStreamSynchronize(st));
     return read_status(idx, st);
+}
+
+pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int Wo, int stride, float *y_out,
+                               void *stream) {
+    if (!idx || !output || !y_out) return set_error(PTS_ERR_INVALID_ARG, "pts_project_queries: null pointer");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "pts_project_queries"));
+    const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
+    PTS_TRY(ensure_workspace(idx, Q));
+    cudaStream_t st = as_stream(stream);
+    Workspace &ws = idx->ws;
+    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
+                   ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
+    PTS_CUDA_TRY(cudaMemcpy2DAsync(y_out, sizeof(float) * idx->d, ws.qcoord.ptr, sizeof(float) * idx->da,
+                                   sizeof(float) * idx->d, Q, cudaMemcpyDeviceToDevice, st));
+    return PTS_OK;
+}
+
+pts_status pts_train_proposal(pts_index idx, const float *y, const int32_t *nn, const float *d2, int n,
+                              const pts_proposal_params *prm, double *loss_out, void *stream) {
+    if (!idx || !y || !nn || !d2 || !prm) return set_error(PTS_ERR_INVALID_ARG, "pts_train_proposal: null pointer");
+    const int C = prm->n_clusters;
+    if (C < 4 || C > 1024 || C > idx->N) return set_error(PTS_ERR_INVALID_ARG, "pts_train_proposal: bad n_clusters");
+    const int iters = prm->kmeans_iters > 0 ? prm->kmeans_iters : 25;
+    const int epochs = prm->epochs > 0 ? prm->epochs : 8;
+    const int batch = prm->batch > 0 ? prm->batch : 4096;
+    if (batch % 8) return set_error(PTS_ERR_INVALID_ARG, "pts_train_proposal: batch must be a multiple of 8");
+    if (n < batch) return set_error(PTS_ERR_INVALID_ARG, "pts_train_proposal: fewer pairs than one batch");
+    const float lr = prm->lr > 0 ? prm->lr : 1e-3f;
+    const float wd = prm->weight_decay > 0 ? prm->weight_decay : 1e-4f;
+    cudaStream_t st = as_stream(stream);
+    ProposalState &pr = idx->prop;
+    pr.ready = 0;
+    pr.C = C;
+    pr.factor = prm->fallback_factor > 0 ? prm->fallback_factor : 1.2f;
+    const int N = idx->N, d = idx->d, da = idx->da;
+    // SplitMix64 stream of the method's random draws (k-means++ uniforms, init, batch order)
+    uint64_t state = prm->seed;
+    auto next_u64 = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto uniform = [&]() { return (double)(next_u64() >> 11) * (1.0 / 9007199254740992.0); };
+    DevBuf<float> Y, cost;
+    PTS_TRY(Y.ensure((size_t)N * d, "proposal points"));
+    PTS_TRY(cost.ensure(N, "kmeans cost"));
+    PTS_TRY(pr.centroids.ensure((size_t)C * d, "centroids"));
+    PTS_TRY(pr.assign.ensure(N, "cluster of each window"));
+    PTS_TRY(pr.counts.ensure(C, "cluster sizes"));
+    PTS_TRY(pr.off.ensure(C + 1, "cluster offsets"));
+    PTS_TRY(pr.members.ensure(N, "cluster members"));
+    PTS_TRY(pr.mrow.ensure((size_t)N * da, "member vectors"));
+    PTS_TRY(pr.mnorm.ensure(N, "member norms"));
+    PTS_TRY(pr.median.ensure(C, "cluster medians"));
+    launch_extract_y(idx->et.ptr, N, da, d, Y.ptr, st);
+    std::vector<double> u(C);
+    for (int i = 0; i < C; ++i) u[i] = uniform();
+    PTS_TRY(kmeans_device(Y.ptr, N, d, C, u.data(), iters, pr.centroids.ptr, pr.assign.ptr, cost.ptr, pr.counts.ptr,
+                          pr.off.ptr, pr.members.ptr, nullptr, st));
+    launch_member_rows(idx->et.ptr, idx->enorm.ptr, N, da, pr.members.ptr, pr.mrow.ptr, pr.mnorm.ptr, st);
+    DevBuf<int> lab;
+    DevBuf<float> dist;
+    PTS_TRY(lab.ensure(n, "pair labels"));
+    PTS_TRY(dist.ensure(n, "pair distances"));
+    PTS_TRY(cluster_medians(nn, d2, n, pr.assign.ptr, N, C, lab.ptr, dist.ptr, pr.median.ptr, st));
+    // network: Kaiming-normal weights (Box-Muller on the same stream), zero biases
+    MlpState &m = pr.mlp;
+    PTS_TRY(m.ensure(C, std::max(batch, kMlpChunk), st));
+    const long np = mlp_param_count(C);
+    std::vector<float> hp(np, 0.0f);
+    auto normal = [&]() {
+        const double u1 = uniform(), u2 = uniform();
+        return std::sqrt(-2.0 * std::log1p(-u1)) * std::cos(6.283185307179586 * u2);
+    };
+    long o = 0;
+    const int fan_in[3] = {64, kMlpH, kMlpH}, fan_out[3] = {kMlpH, kMlpH, C};
+    for (int l = 0; l < 3; ++l) {
+        const double sdev = std::sqrt(2.0 / fan_in[l]);
+        for (long i = 0; i < (long)fan_out[l] * fan_in[l]; ++i) hp[o + i] = (float)(sdev * normal());
+        o += (long)fan_out[l] * fan_in[l] + fan_out[l];
+    }
+    PTS_CUDA_TRY(cudaMemcpyAsync(m.params.ptr, hp.data(), sizeof(float) * np, cudaMemcpyHostToDevice, st));
+    PTS_CUDA_TRY(cudaMemsetAsync(m.adam_m.ptr, 0, sizeof(float) * np, st));
+    PTS_CUDA_TRY(cudaMemsetAsync(m.adam_v.ptr, 0, sizeof(float) * np, st));
+    mlp_refresh_bf16(m, st);
+    DevBuf<int> perm;
+    PTS_TRY(perm.ensure(n, "batch order"));
+    std::vector<int> hperm(n);
+    std::vector<float> hloss(batch);
+    const int steps_per_epoch = n / batch;
+    const long total_steps = (long)steps_per_epoch * epochs;
+    long step = 0;
+    for (int e = 0; e < epochs; ++e) {
+        for (int i = 0; i < n; ++i) hperm[i] = i;
+        for (int i = n - 1; i > 0; --i) std::swap(hperm[i], hperm[(int)(uniform() * (i + 1))]);
+        PTS_CUDA_TRY(cudaMemcpyAsync(perm.ptr, hperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        double esum = 0.0;
+        for (int b = 0; b < steps_per_epoch; ++b) {
+            ++step;
+            const float lr_t = lr * 0.5f * (1.0f + cosf(3.14159265f * (float)(step - 1) / (float)total_steps));
+            mlp_gather(m, y, d, d, perm.ptr, b * batch, batch, lab.ptr, st);
+            mlp_forward(m, batch, 1, idx->status.ptr, st);
+            mlp_backward(m, batch, m.labels.ptr, idx->status.ptr, st);
+            mlp_adamw(m, lr_t, wd, (int)step, st);
+            mlp_refresh_bf16(m, st);
+            if (b == steps_per_epoch - 1) {
+                PTS_CUDA_TRY(cudaMemcpyAsync(hloss.data(), m.loss.ptr, sizeof(float) * batch, cudaMemcpyDeviceToHost, st));
+                PTS_CUDA_TRY(cudaStreamSynchronize(st));
+                for (int i = 0; i < batch; ++i) esum += hloss[i];
+            }
+        }
+        if (loss_out) loss_out[e] = esum / batch;  // loss of the epoch's last batch
+    }
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    PTS_TRY(read_status(idx, st));
+    pr.ready = 1;
+    return PTS_OK;
+}
+
+pts_status pts_kmeans(const float *points, int n, int d, int k, const double *u, int iters, float *centroids_out,
+                      int32_t *assign_out, int *iters_out, void *stream) {
+    if (!points || !u || !centroids_out || !assign_out) return set_error(PTS_ERR_INVALID_ARG, "pts_kmeans: null pointer");
+    cudaStream_t st = as_stream(stream);
+    DevBuf<float> cost;
+    DevBuf<int> counts, off, members;
+    PTS_TRY(cost.ensure(n, "kmeans cost"));
+    PTS_TRY(counts.ensure(k, "kmeans counts"));
+    PTS_TRY(off.ensure(k + 1, "kmeans offsets"));
+    PTS_TRY(members.ensure(n, "kmeans members"));
+    return kmeans_device(points, n, d, k, u, iters > 0 ? iters : 25, centroids_out, assign_out, cost.ptr, counts.ptr,
+                         off.ptr, members.ptr, iters_out, st);
+}
+
+pts_status pts_mlp_grad(int C, const float *params, const float *X, const int32_t *labels, int B, float *grads_out,
+                        double *loss_out, void *stream) {
+    if (!params || !X || !labels || !grads_out || !loss_out) return set_error(PTS_ERR_INVALID_ARG, "pts_mlp_grad: null pointer");
+    if (C < 1 || C > 1024 || B < 8 || B % 8) return set_error(PTS_ERR_INVALID_ARG, "pts_mlp_grad: bad sizes");
+    cudaStream_t st = as_stream(stream);
+    MlpState m;
+    PTS_TRY(m.ensure(C, B, st));
+    DevBuf<int> status;
+    PTS_TRY(status.ensure(1, "status"));
+    PTS_CUDA_TRY(cudaMemsetAsync(status.ptr, 0, sizeof(int), st));
+    const long np = mlp_param_count(C);
+    PTS_CUDA_TRY(cudaMemcpyAsync(m.params.ptr, params, sizeof(float) * np, cudaMemcpyDeviceToDevice, st));
+    mlp_refresh_bf16(m, st);
+    mlp_gather(m, X, 64, 64, nullptr, 0, B, labels, st);
+    mlp_forward(m, B, 1, status.ptr, st);
+    mlp_backward(m, B, m.labels.ptr, status.ptr, st);
+    PTS_CUDA_TRY(cudaMemcpyAsync(grads_out, m.grads.ptr, sizeof(float) * np, cudaMemcpyDeviceToDevice, st));
+    std::vector<float> hl(B);
+    PTS_CUDA_TRY(cudaMemcpyAsync(hl.data(), m.loss.ptr, sizeof(float) * B, cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int i = 0; i < B; ++i) s += hl[i];
+    *loss_out = s / B;
+    int h = 0;
+    PTS_CUDA_TRY(cudaMemcpy(&h, status.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return set_error(PTS_ERR_TIMEOUT, "pts_mlp_grad: a completion wait gave up");
+    return PTS_OK;
+}
+
+pts_status pts_gemm_selftest(int M, int N, int K, double *max_rel_err) {
+    if (!max_rel_err) return set_error(PTS_ERR_INVALID_ARG, "pts_gemm_selftest: null pointer");
+    return gemm_selftest(M, N, K, max_rel_err);
 }
 
 pts_status pts_tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref) {

@@ -98,6 +98,37 @@ struct Workspace {
     DevBuf<unsigned int> ticket;
 };
 
+// ---------------------------------------------------------------------------
+// learned proposal state (kmeans.cu, mlp.cu, probe.cu)
+// ---------------------------------------------------------------------------
+constexpr int kMlpH = 256;       // hidden width of the proposal network
+constexpr int kMlpChunk = 65536; // queries per inference chunk
+
+struct MlpState {
+    int C = 0, bmax = 0;
+    DevBuf<float> params, grads, adam_m, adam_v;  // FP32 master weights, packed
+    DevBuf<__nv_bfloat16> wb, wt;                 // BF16 weights and their transposes
+    DevBuf<__nv_bfloat16> xb, xt, h1b, h1t, h2b, h2t, dzb, dzt, dab, dat;
+    DevBuf<float> a1, a2, z, dh, loss;
+    DevBuf<int> labels;
+    pts_status ensure(int C_, int Bmax, cudaStream_t st);
+};
+
+struct ProposalState {
+    int ready = 0, C = 0;
+    float factor = 1.2f;
+    DevBuf<float> centroids;  // [C][d]
+    DevBuf<int> assign;       // [N] cluster of each exemplar window
+    DevBuf<int> counts;       // [C]
+    DevBuf<int> off;          // [C+1] CSR offsets
+    DevBuf<int> members;      // [N] windows in cluster order
+    DevBuf<float> mrow;       // [N][da] search vectors in cluster order
+    DevBuf<float> mnorm;      // [N]
+    DevBuf<float> median;     // [C] median nearest-neighbour distance of the cluster's pairs
+    DevBuf<int> top;          // [Q][4] probed clusters
+    MlpState mlp;
+};
+
 }  // namespace pts
 
 struct pts_index_s {
@@ -122,6 +153,7 @@ struct pts_index_s {
     pts::Workspace ws;
     pts_search_stats last{};
     int last_mode = 0;
+    pts::ProposalState prop;
 };
 
 namespace pts {
@@ -163,6 +195,30 @@ void launch_warm_threshold(const int *prev_idx, const float *qcoord, const float
                            const __nv_bfloat16 *etile, const float *umax, int Q, int d, int da, int K, int N,
                            float eps_scale, float *thr0, cudaStream_t st);
 pts_status tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref);
+// kmeans.cu
+pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, int iters, float *C, int *assign,
+                         float *cost, int *counts, int *off, int *members, int *iters_used, cudaStream_t st);
+void launch_extract_y(const float *et, int N, int da, int d, float *Y, cudaStream_t st);
+void launch_member_rows(const float *et, const float *enorm, int N, int da, const int *members, float *mrow,
+                        float *mnorm, cudaStream_t st);
+pts_status cluster_medians(const int *nn, const float *d2, int n, const int *assign, int N, int C, int *lab,
+                           float *dist, float *median, cudaStream_t st);
+// probe.cu
+void launch_top4(const float *logits, int Q, int C, int *top, cudaStream_t st);
+void launch_probe(const float *qcoord, const float *qnorm, int Q, int da, const int *top, const int *off,
+                  const int *members, const float *mrow, const float *mnorm, int *cand_idx, float *cand_lb,
+                  cudaStream_t st);
+void launch_fallback(const int *nn, const float *d2, int Q, const int *assign, const float *median, float factor,
+                     int N, int *list, unsigned int *count, cudaStream_t st);
+// mlp.cu / gemm_tc.cu
+long mlp_param_count(int C);
+void mlp_refresh_bf16(MlpState &s, cudaStream_t st);
+void mlp_forward(MlpState &s, int B, int train, int *status, cudaStream_t st);
+void mlp_backward(MlpState &s, int B, const int *labels, int *status, cudaStream_t st);
+void mlp_adamw(MlpState &s, float lr, float wd, int step, cudaStream_t st);
+void mlp_gather(MlpState &s, const float *Y, int d, int ldy, const int *perm, int off, int B, const int *lab_all,
+                cudaStream_t st);
+pts_status gemm_selftest(int M, int N, int K, double *max_rel_err);
 // full-dimension vectors are padded with zero rows to a multiple of 32
 inline int padded_dim(int w) { return (3 * w * w + 31) / 32 * 32; }
 // rerank.cu

@@ -52,22 +52,6 @@ struct TcSmem {
     int abort_flag;
 };
 
-__device__ __forceinline__ void list_insert(float &ld, int &li, float &thr, float cap, float cd, int ci,
-                                            int lane) {
-    const bool before = (ld < cd) || (ld == cd && li < ci);
-    const int pos = __popc(__ballot_sync(kFull, before));
-    const float ud = __shfl_up_sync(kFull, ld, 1);
-    const int ui = __shfl_up_sync(kFull, li, 1);
-    if (lane > pos) {
-        ld = ud;
-        li = ui;
-    } else if (lane == pos) {
-        ld = cd;
-        li = ci;
-    }
-    thr = fminf(cap, __shfl_sync(kFull, ld, 31));
-}
-
 // (a, ia) < (b, ib) lexicographically
 __device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
     return (a < b) || (a == b && ia < ib);

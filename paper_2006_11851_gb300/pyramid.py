@@ -38,14 +38,16 @@ def synthesize_pyramid(pidx: PyramidIndex, init_coarse: torch.Tensor, iters: int
                        keep_levels: bool = False):
     """Runs every level in place, coarse to fine.
 
+    mode is one search mode for every level or a list with one per level.
     Returns (final image, energies [levels, iters + 1], per-level images if
     keep_levels).  init_coarse is the initial image of level 0.
     """
     X = init_coarse.contiguous()
     energies = np.zeros((pidx.levels, iters + 1))
     imgs = []
+    modes = list(mode) if isinstance(mode, (list, tuple)) else [mode] * pidx.levels
     for lev, ix in enumerate(pidx.indices):
-        energies[lev] = synthesize_level(ix, X, iters, r=r, delta=delta, mode=mode, stride=stride)
+        energies[lev] = synthesize_level(ix, X, iters, r=r, delta=delta, mode=modes[lev], stride=stride)
         if keep_levels:
             imgs.append(X.clone())
         if lev + 1 < pidx.levels:
