@@ -186,13 +186,38 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+LEVEL_MODES = {
+    "exact": ["exact", "exact", "exact"],
+    "f16": ["f16", "f16", "f16"],
+    # the coarsest level (1,089 windows of 3,072 dimensions) searched exactly
+    "f16c": ["exact", "f16", "f16"],
+    # the learned proposal on the finest level (the proposal trained there); the coarse levels,
+    # whose exemplars hold 1-13k windows, use the FP16 tensor-core brute force
+    "proposal": ["f16", "f16", "proposal"],
+}
+PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return m.get("bf16_tflops"), m.get("bf16_tflops_sustained"), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="exact", choices=["exact", "bf16", "fp8", "proposal"])
+    ap.add_argument("--mode", default="proposal", choices=list(LEVEL_MODES))
+    ap.add_argument("--train-seeds", type=int, default=16)
+    ap.add_argument("--train-pairs", type=int, default=2_000_000)
+    ap.add_argument("--clusters", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries per level for the CPU baseline")
     args = ap.parse_args()
@@ -206,6 +231,7 @@ def main():
     import torch
 
     import paper_2006_11851_gb300 as pts
+    from paper_2006_11851_gb300.proposal import train_level_proposal
     from paper_2006_11851_gb300.pyramid import PyramidIndex, synthesize_pyramid
     import pts_inputs as P
 
@@ -219,74 +245,98 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     L = pts.lib()
-    L.pts_launch_count.restype = ctypes.c_longlong
-    L.pts_profile_enable.argtypes = [ctypes.c_int]
-    L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
-                                   ctypes.POINTER(ctypes.c_longlong)]
 
     cfg = WORKLOAD
     sizes = level_sizes(cfg)
+    modes = LEVEL_MODES[args.mode]
     Z = P.synthetic_exemplar(0, cfg["exemplar"], cfg["shrink"])
-    t_build0 = time.perf_counter()
+    t0 = time.perf_counter()
     pidx = PyramidIndex(torch.from_numpy(Z).to(dev), cfg["windows"], d=cfg["d"])
     torch.cuda.synchronize()
-    index_build_s = time.perf_counter() - t_build0
+    index_build_s = time.perf_counter() - t0
     z0 = pidx.exemplars[0].cpu().numpy()
+    Hc, wc = sizes[0]["Ho"], sizes[0]["w"]
+
+    def init_dev(seed):
+        return torch.from_numpy(P.random_patch_init(z0, Hc, Hc, wc, seed)).to(dev)
+
+    train_s, n_pairs, train_loss = 0.0, 0, []
+    if "proposal" in modes:
+        # training seeds 1000.. are disjoint from the timed seeds 0..(warmup + steps)
+        t0 = time.perf_counter()
+        loss, n_pairs = train_level_proposal(pidx, modes.index("proposal"),
+                                             [1000 + s for s in range(args.train_seeds)], iters=cfg["iters"],
+                                             n_pairs=args.train_pairs, init_fn=init_dev, n_clusters=args.clusters,
+                                             epochs=args.epochs, seed=7)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        train_loss = [float(x) for x in loss]
+
     n_total = args.warmup + args.steps
-    inits = [P.random_patch_init(z0, sizes[0]["Ho"], sizes[0]["Ho"], sizes[0]["w"], s) for s in range(n_total)]
-    init_dev = [torch.from_numpy(x).to(dev) for x in inits]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(x0):
-        X, E, _ = synthesize_pyramid(pidx, x0, iters=cfg["iters"], r=cfg["r"], mode=args.mode)
+    def step(x0, mode_list):
+        X, E, _ = synthesize_pyramid(pidx, x0, iters=cfg["iters"], r=cfg["r"], mode=mode_list)
         return X, E
 
-    # exact-mode reference energy for the energy-ratio check (seed 0)
-    X_ex, E_ex = step(init_dev[0].clone())
-    for i in range(args.warmup):
-        step(init_dev[i].clone())
-    torch.cuda.synchronize()
+    def exact_energy(X):
+        _, d2 = pts.nn_search(pidx.indices[-1], X, cfg["stride"], "exact")
+        return float(d2.double().sum())
 
-    # ---- device-timed region ----
-    work = [init_dev[args.warmup + i].clone() for i in range(args.steps)]
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches0 = L.pts_launch_count()
-    L.pts_profile_enable(1)
-    times = []
-    energies = []
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            _, E = step(work[i])
-            ev1.record(stream)
-            ev1.synchronize()
-            times.append(ev0.elapsed_time(ev1))
-            energies.append(E)
-    torch.cuda.synchronize()
-    launches = L.pts_launch_count() - launches0
-    tk_ms, tk_n = ctypes.c_double(), ctypes.c_longlong()
-    L.pts_profile_read(b"search_topk", ctypes.byref(tk_ms), ctypes.byref(tk_n))
-    kern = {}
-    for name in ("search_topk", "search_full", "rerank", "project", "m_step", "brute", "irls"):
-        ms, n = ctypes.c_double(), ctypes.c_longlong()
-        L.pts_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(n))
-        kern[name] = {"ms": ms.value / args.steps, "launches": n.value // args.steps}
-    L.pts_profile_enable(0)
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    def timed_run(mode_list, profile):
+        for i in range(args.warmup):
+            step(init_dev(i), mode_list)
+        work = [init_dev(args.warmup + i) for i in range(args.steps)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        launches0 = L.pts_launch_count()
+        if profile:
+            L.pts_profile_enable(1)
+        times, finals = [], []
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                X, _ = step(work[i], mode_list)
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+                finals.append(X)
+        torch.cuda.synchronize()
+        launches = L.pts_launch_count() - launches0
+        kern = {}
+        if profile:
+            for name in ("search_topk", "search_full", "search_tc", "rerank", "project", "m_step", "brute", "irls",
+                         "mlp", "probe"):
+                ms, n = ctypes.c_double(), ctypes.c_longlong()
+                L.pts_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(n))
+                if n.value:
+                    kern[name] = {"ms_per_step": ms.value / args.steps, "launches_per_step": n.value / args.steps}
+            L.pts_profile_enable(0)
+        total_ms = sum(times)
+        if dist:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = t.item()
+        energies = [exact_energy(X) for X in finals]
+        return total_ms, launches, kern, energies, clk.summary()
+
+    total_ms, launches, kern, energies, clocks = timed_run(modes, True)
     qps = queries_per_step(cfg) * args.steps * world / (total_ms / 1000.0)
+    if args.mode == "exact":
+        ex_ms, ex_energies = total_ms, energies
+    else:
+        ex_ms, _, _, ex_energies, _ = timed_run(LEVEL_MODES["exact"], False)
+    exact_qps = queries_per_step(cfg) * args.steps * world / (ex_ms / 1000.0)
+    ratios = [e / x for e, x in zip(energies, ex_energies)]
 
     # ---- end to end through the public API with host buffers ----
-    pinned = [torch.from_numpy(inits[args.warmup + i]).pin_memory() for i in range(args.steps)]
+    inits = [P.random_patch_init(z0, Hc, Hc, wc, args.warmup + i) for i in range(args.steps)]
+    pinned = [torch.from_numpy(x).pin_memory() for x in inits]
     out_host = torch.empty(sizes[-1]["Ho"], sizes[-1]["Ho"], 3, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     if dist:
@@ -298,7 +348,7 @@ def main():
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         x0 = pinned[i].to(dev, non_blocking=True)
-        X, _ = step(x0)
+        X, _ = step(x0, modes)
         out_host.copy_(X, non_blocking=True)
         ev1.record(stream)
         ev1.synchronize()
@@ -309,37 +359,50 @@ def main():
         e2e_ms = t.item()
     e2e_qps = queries_per_step(cfg) * args.steps * world / (e2e_ms / 1000.0)
 
-    # ---- roofline of the dominant kernel (FP32 SIMT bound search) ----
-    flops_per_step = sum(2.0 * (min(cfg["d"], 3 * l["w"] ** 2) + 1) * l["N"] * l["Q"] * (cfg["iters"] + 1)
-                         for l in sizes)
-    achieved_tflops = flops_per_step * args.steps / (tk_ms.value / 1000.0) / 1e12 if tk_ms.value > 0 else None
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    roof = {"kernel": "k_search (PCA-space lower-bound GEMM + top-32, FP32 SIMT)", "bound": "alu",
-            "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved_tflops / peak_tflops if achieved_tflops else None, "traffic": None,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived)",
-            "kernel_ms_per_step": tk_ms.value / args.steps, "launches_per_step": tk_n.value // args.steps}
+    # ---- roofline of the dominant kernel of this mode ----
+    bf16_burst, bf16_sust, peak_src = _peaks()
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"]) if kern else None
+    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
+    it = cfg["iters"] + 1
+    if dom == "search_tc":
+        dfs = [ix.info["d_fast"] for ix in pidx.indices]
+        fl = sum(2.0 * (df + 1) * l["N"] * l["Q"] * it for l, m, df in zip(sizes, modes, dfs) if m == "f16")
+        ach = fl / (kern[dom]["ms_per_step"] / 1000.0) / 1e12
+        roof.update(bound="tensor", achieved=ach, peak=bf16_sust, unit="TFLOP/s", frac=ach / bf16_sust,
+                    kernel="k_search_tc (FP16 tcgen05 PCA-space GEMM + top-32)",
+                    note=f"algorithmic 2(d_fast+1) flops per (query, window) pair, d_fast={dfs}; peak = BF16 "
+                         f"sustained (dense FP16 has the BF16 rate), {peak_src}")
+    elif dom == "search_topk":
+        fl = sum(2.0 * (cfg["d"] + 1) * l["N"] * l["Q"] * it for l, m in zip(sizes, modes) if m == "exact")
+        ach = fl / (kern[dom]["ms_per_step"] / 1000.0) / 1e12
+        roof.update(bound="alu", achieved=ach, peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=ach / PEAK_FP32_TFLOPS,
+                    kernel="k_search_pca (FP32 SIMT PCA-bound GEMM + top-32)", traffic=35.3e6,
+                    note="algorithmic 2(d+1) flops per pair; peak = 152 SMs x 128 lanes x 2 x 2070 MHz (derived); "
+                         "traffic = ncu dram read+write of one finest-level launch")
+    elif dom is not None:
+        roof.update(note="dominant kernel without a roofline model in this script")
 
-    energy_ratio = float(np.mean([e[-1][-1] for e in energies]) / 1.0)
     line = {
         "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(cfg, mode=args.mode, l2="flushed between steps (256 MB write)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32" if args.mode != "exact" else "f32",
+        "data": "synthetic",
+        "config": dict(cfg, mode=args.mode, level_modes=modes, l2="flushed between steps (256 MB write)",
                        queries_per_step=queries_per_step(cfg), index_build_s=index_build_s,
-                       parallelism=f"replicas x{world}"),
+                       proposal_train_s=train_s, proposal_pairs=n_pairs, proposal_clusters=args.clusters,
+                       proposal_train_loss=train_loss, parallelism=f"replicas x{world}"),
+        "exact_fp32": {"value": exact_qps, "ms_per_step": ex_ms / args.steps},
+        "speedup_vs_exact": qps / exact_qps,
+        "final_energy_ratio_vs_exact": {"max": max(ratios), "mean": float(np.mean(ratios)),
+                                        "within_1.01": bool(max(ratios) <= 1.01)},
         "roofline": roof,
-        "e2e": {"value": e2e_qps, "unit": "queries/s",
-                "h2d_bytes_per_step": int(inits[0].nbytes),
+        "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(inits[0].nbytes),
                 "d2h_bytes_per_step": int(out_host.numel() * 4 + 8 * (cfg["iters"] + 1) * cfg["levels"])},
         "gpu_launches": int(launches),
         "kernels_per_step": kern,
-        "final_energy": float(energies[0][-1][-1]),
-        "final_energy_exact_seed0": float(E_ex[-1][-1]),
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
         n = args.cpu_sample or 0
         per = [n] * 3 if n else [512, 1024, 3072]
         rate, threads, timed, secs = oracle_sample_rate(per)
@@ -347,7 +410,6 @@ def main():
                                 "sample": f"{per} queries per level (coarse to fine) of one E-step each, "
                                           f"FP64 full-dimension brute force, {secs:.1f} s, rate weighted by the "
                                           "workload's query mix"}
-    del energy_ratio
     if rank == 0:
         print(json.dumps(line), flush=True)
     pidx.close()

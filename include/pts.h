@@ -64,16 +64,19 @@ typedef enum {
  *                     (top-32 again, re-ranked, certified against the FP32
  *                     rounding bound), and what still fails a direct scan.
  *                     FP32 SIMT, no tensor cores.
- *   PTS_BF16_RERANK   PCA-space distances as a BF16 tensor-core GEMM (FP32
- *                     accumulate), top-32, exact FP32 full-dimension re-rank.
- *   PTS_FP8_RERANK    as BF16 with FP8-E4M3 operands and per-dimension scales.
- *   PTS_PROPOSAL_BF16 learned cluster proposal + BF16 probe + re-rank, with
+ *   PTS_F16_RERANK    PCA-space bounds (d_fast coordinates + residual) as an
+ *                     FP16 tensor-core GEMM (FP32 accumulate), top-32 by
+ *                     bound, exact FP32 full-dimension re-rank.  Not
+ *                     certified: a window whose FP16-rounded bound misses the
+ *                     32 best is lost.
+ *   PTS_FP8_RERANK    as F16 with FP8-E4M3 operands (not available).
+ *   PTS_PROPOSAL      learned cluster proposal + FP32 probe + re-rank, with
  *                     the exact search as fallback. */
 typedef enum {
     PTS_EXACT_F32 = 0,
-    PTS_BF16_RERANK = 1,
+    PTS_F16_RERANK = 1,
     PTS_FP8_RERANK = 2,
-    PTS_PROPOSAL_BF16 = 3
+    PTS_PROPOSAL = 3
 } pts_mode;
 
 typedef struct pts_index_s *pts_index; /* opaque, owned by the library */
@@ -84,11 +87,14 @@ typedef struct {
                         capped at 64 */
     double var_frac; /* used when d <= 0 */
     int max_iters;   /* eigen-solver iteration cap (0 = 200) */
+    int d_fast;      /* PCA dimensions of the tensor-core and proposal searches, 1..92
+                        (0 = 92, capped by the covariance rank) */
 } pts_index_params;
 
 typedef struct {
     int He, We, w, D, N, d;
     int da;                  /* search vector length: d coordinates + residual, padded to 4 */
+    int d_fast;              /* PCA dimensions of the tensor-core and proposal searches */
     double var_retained;     /* sum of the d eigenvalues / trace of the covariance */
     double eig_top;          /* largest eigenvalue */
     int eig_iters;           /* subspace iterations used */
@@ -126,11 +132,12 @@ const char *pts_version(void);
 /*
  * pca_fit -- PCA of the exemplar's neighbourhood vectors (section 2.2: the
  * search runs on PCA-reduced vectors; the paper keeps 95% of the variance).
+ * d may be up to 128 here; an index keeps up to max(d, d_fast) components.
  *   mu    = (1/N) sum_n v_n,  Sigma = (1/N) sum_n (v_n - mu)(v_n - mu)^T,
  * both accumulated in FP64 on the GPU; the top-d eigenpairs of Sigma come
  * from FP64 subspace iteration with Rayleigh-Ritz steps solved by Jacobi.
  * exemplar    device, He x We x 3 float32.
- * d           1..64, or <= 0 to choose the smallest d reaching var_frac.
+ * d           1..128, or <= 0 to choose the smallest d <= 64 reaching var_frac.
  * mean_out    device, D float32 (may be NULL).
  * basis_out   device, d x D float32, row j = unit eigenvector j (eigenvalues
  *             descending); must hold 64 x D floats when d <= 0.
@@ -185,7 +192,7 @@ pts_status pts_project_queries(pts_index index, const float *output, int Ho, int
                                void *stream);
 
 /*
- * pts_train_proposal -- builds the learned cluster proposal of PTS_PROPOSAL_BF16, which takes
+ * pts_train_proposal -- builds the learned cluster proposal of PTS_PROPOSAL, which takes
  * the place of the paper's k-means search tree (section 2.2):
  *   1. k-means (k-means++ seeding, Lloyd) over the exemplar windows' PCA coordinates;
  *   2. labels: the cluster of each training pair's exact nearest window; per-cluster median
@@ -316,12 +323,13 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
 long long pts_launch_count(void);
 
 /* Self-test of the tensor-core operand layout (no counterpart in the paper):
- * one 128 x N x K BF16 tcgen05 MMA through the same shared-memory and
- * instruction descriptors the search uses, on seeded data generated here,
+ * one 128 x N x K tcgen05 MMA (f16 != 0: FP16 operands as in the search;
+ * f16 == 0: BF16 as in the proposal network) through the same shared-memory
+ * and instruction descriptors the kernels use, on seeded data generated here,
  * compared with an FP64 host product.  N, K multiples of 16 (N <= 256,
  * K <= 128).  Writes the largest absolute error and the largest |reference|.
  * Synchronises the device. */
-pts_status pts_tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref);
+pts_status pts_tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref);
 void pts_profile_enable(int on);
 pts_status pts_profile_read(const char *kernel, double *total_ms, long long *launches);
 

@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-MODES = {"exact": 0, "bf16": 1, "fp8": 2, "proposal": 3}
+MODES = {"exact": 0, "f16": 1, "fp8": 2, "proposal": 3}
 
 _LOCK = threading.Lock()
 _LIB = None
@@ -28,12 +28,13 @@ class PtsError(RuntimeError):
 
 
 class _IndexParams(ctypes.Structure):
-    _fields_ = [("d", ctypes.c_int), ("var_frac", ctypes.c_double), ("max_iters", ctypes.c_int)]
+    _fields_ = [("d", ctypes.c_int), ("var_frac", ctypes.c_double), ("max_iters", ctypes.c_int),
+                ("d_fast", ctypes.c_int)]
 
 
 class _IndexInfo(ctypes.Structure):
     _fields_ = [("He", ctypes.c_int), ("We", ctypes.c_int), ("w", ctypes.c_int), ("D", ctypes.c_int),
-                ("N", ctypes.c_int), ("d", ctypes.c_int), ("da", ctypes.c_int),
+                ("N", ctypes.c_int), ("d", ctypes.c_int), ("da", ctypes.c_int), ("d_fast", ctypes.c_int),
                 ("var_retained", ctypes.c_double), ("eig_top", ctypes.c_double),
                 ("eig_iters", ctypes.c_int), ("unorm2_max", ctypes.c_float)]
 
@@ -96,7 +97,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     L.pts_kmeans.argtypes = [_vp, _I, _I, _I, _vp, _I, _vp, _vp, ctypes.POINTER(_I), _vp]
     L.pts_mlp_grad.argtypes = [_I, _vp, _vp, _vp, _I, _vp, ctypes.POINTER(_Dd), _vp]
     L.pts_gemm_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd)]
-    L.pts_tc_selftest.argtypes = [_I, _I, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
+    L.pts_tc_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
     L.pts_launch_count.restype = ctypes.c_longlong
     L.pts_profile_enable.argtypes = [_I]
     L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
@@ -151,14 +152,14 @@ class ExemplarIndex:
     """Owns a pts_index (build_exemplar_index); freed by close() or on GC."""
 
     def __init__(self, exemplar: torch.Tensor, w: int, d: int = 0, var_frac: float = 0.95,
-                 max_iters: int = 0):
+                 max_iters: int = 0, d_fast: int = 0):
         L = lib()
         _need(exemplar, torch.float32, "exemplar")
         He, We, C = exemplar.shape
         if C != 3:
             raise ValueError("exemplar must be H x W x 3")
         self._h = ctypes.c_void_p()
-        p = _IndexParams(int(d), float(var_frac), int(max_iters))
+        p = _IndexParams(int(d), float(var_frac), int(max_iters), int(d_fast))
         _check(L.build_exemplar_index(_ptr(exemplar), He, We, w, ctypes.byref(p), _stream(),
                                       ctypes.byref(self._h)))
         self.device = exemplar.device

@@ -22,12 +22,12 @@ thread_local std::string g_last_error;
 // norms; c = 8 leaves a wide margin.
 constexpr float kTauC = 8.0f;
 
-// Margin added to a warm-start bound for the BF16 search.  The bound is
-// computed from the very BF16 operands the tensor cores multiply, so it only
-// differs from the search's values by FP32 summation order over K <= 80
-// terms of size <= ||u_q|| ||u_n||: 2^-16 (||u_q||^2 + max_n ||u_n||^2)
-// covers that with a wide margin.
-constexpr float kWarmEps = 1.0f / 65536.0f;
+// Margin added to a warm-start bound for the FP16 tensor-core search.  The
+// bound is computed from the very FP16 operands the tensor cores multiply
+// (their products are exact in FP32), so it only differs from the search's
+// values by the FP32 summation order: at most 2 K 2^-24 sum|terms| with
+// K <= 128 and sum|terms| <= ||u_q||^2 + 2 max_n ||u_n||^2.  2^-13 doubles that.
+constexpr float kWarmEps = 1.0f / 8192.0f;
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -47,7 +47,7 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     if (Q <= ws.q_cap && ws.counters.ptr) return PTS_OK;
     const int cap = std::max(Q, 1024);
     const size_t qpad = (size_t)ceil_div(cap, kBQ) * kBQ;
-    PTS_TRY(ws.qcoord.ensure(qpad * idx->da, "query vectors"));
+    PTS_TRY(ws.qcoord.ensure(qpad * std::max(idx->da, idx->da_fast), "query vectors"));
     PTS_TRY(ws.qnorm.ensure(qpad, "query norms"));
     PTS_TRY(ws.tau.ensure(qpad, "query slack"));
     PTS_TRY(ws.cand_idx.ensure((size_t)cap * kTopK, "candidate indices"));
@@ -105,17 +105,18 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     ProposalState &pr = idx->prop;
     if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no proposal trained on this index");
     const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
-    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
-                   ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
+    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
     PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
     PTS_TRY(pr.mlp.ensure(pr.C, std::min(Q, kMlpChunk), st));
     for (int q0 = 0; q0 < Q; q0 += kMlpChunk) {
         const int B = std::min(kMlpChunk, Q - q0);
-        mlp_gather(pr.mlp, ws.qcoord.ptr + (size_t)q0 * idx->da, idx->d, idx->da, nullptr, 0, B, nullptr, st);
+        mlp_gather(pr.mlp, ws.qcoord.ptr + (size_t)q0 * idx->da_fast, std::min(idx->d, 64), idx->da_fast, nullptr, 0,
+                   B, nullptr, st);
         mlp_forward(pr.mlp, B, 0, idx->status.ptr, st);
         launch_top4(pr.mlp.z.ptr, B, pr.C, pr.top.ptr + (size_t)q0 * 4, st);
     }
-    launch_probe(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, pr.top.ptr, pr.off.ptr, pr.members.ptr, pr.mrow.ptr,
+    launch_probe(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da_fast, pr.top.ptr, pr.off.ptr, pr.members.ptr, pr.mrow.ptr,
                  pr.mnorm.ptr, ws.cand_idx.ptr, ws.cand_lb.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
     RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
@@ -164,25 +165,32 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
         case PTS_EXACT_F32:
             PTS_TRY(search_exact(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
             break;
-        case PTS_BF16_RERANK: {
+        case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
-            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0,
+            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
+            const int nparts = tc_parts(Q, idx->ntiles);
+            PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
+            if (nparts > 1) {
+                PTS_TRY(ws.part_v.ensure((size_t)Q * nparts * kTopK, "part lists"));
+                PTS_TRY(ws.part_i.ensure((size_t)Q * nparts * kTopK, "part lists"));
+            }
+            launch_pack_queries(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->ktc, ws.qtile.ptr, st);
             // the candidate lists of the previous search on this grid seed the bound
             const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
             if (warm)
-                launch_warm_threshold(ws.cand_idx.ptr, ws.qcoord.ptr, ws.qnorm.ptr, idx->etc.ptr, idx->umax.ptr, Q,
-                                      idx->d, idx->da, idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
-            launch_search_tc(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->d, idx->da, idx->ktc, idx->etc.ptr,
-                             idx->ntiles, warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr,
-                             idx->status.ptr, st);
+                launch_warm_threshold(ws.cand_idx.ptr, ws.qtile.ptr, ws.qnorm.ptr, idx->etc.ptr, idx->umax.ptr, Q,
+                                      idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
+            launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, idx->ntiles, nparts,
+                             warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr,
+                             ws.part_i.ptr, idx->status.ptr, st);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
                           idx->nx, idx->N, Q};
             launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
             break;
         }
-        case PTS_PROPOSAL_BF16:
+        case PTS_PROPOSAL:
             PTS_TRY(search_proposal(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
             break;
         case PTS_FP8_RERANK:
@@ -224,7 +232,7 @@ pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double v
                    float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream) {
     if (!exemplar || !basis_out) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: null pointer");
     if (w < 1 || w > He || w > We) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: bad window");
-    if (d > kMaxD) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: d > 64");
+    if (d > kMaxDPca) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: d > 128");
     if (d <= 0 && !(var_frac > 0.0 && var_frac <= 1.0))
         return set_error(PTS_ERR_INVALID_ARG, "pca_fit: var_frac must be in (0, 1]");
     cudaStream_t st = as_stream(stream);
@@ -233,7 +241,7 @@ pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double v
     PTS_CUDA_TRY(cudaMemsetAsync(status.ptr, 0, sizeof(int), st));
     int dd = 0;
     pts_status s = pca_fit_device(exemplar, He, We, w, d, var_frac, 0, mean_out, basis_out,
-                                  eigvals_out, &dd, nullptr, nullptr, nullptr, status.ptr, st);
+                                  eigvals_out, &dd, nullptr, nullptr, nullptr, nullptr, status.ptr, st);
     if (s == PTS_OK) {
         int h = 0;
         cudaMemcpy(&h, status.ptr, sizeof(int), cudaMemcpyDeviceToHost);
@@ -252,6 +260,8 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     if (w < 1 || w > He || w > We)
         return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad window");
     if (params->d > kMaxD) return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: d > 64");
+    if (params->d_fast > kMaxDFast)
+        return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: d_fast > 92");
     const long N = (long)(He - w + 1) * (We - w + 1);
     if (N < 2 || N > (1L << 30))
         return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad exemplar size");
@@ -273,19 +283,52 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     if ((s = idx->exemplar.ensure((size_t)He * We * 3, "exemplar")) != PTS_OK) return fail(s);
     if ((s = idx->status.ensure(1, "status")) != PTS_OK) return fail(s);
     if ((s = idx->mu.ensure(idx->D, "mean")) != PTS_OK) return fail(s);
-    if ((s = idx->basis.ensure((size_t)kMaxD * idx->D, "basis")) != PTS_OK) return fail(s);
-    if ((s = idx->eig.ensure(kMaxD, "eigenvalues")) != PTS_OK) return fail(s);
+    if ((s = idx->basis.ensure((size_t)kMaxDPca * idx->D, "basis")) != PTS_OK) return fail(s);
+    if ((s = idx->eig.ensure(kMaxDPca, "eigenvalues")) != PTS_OK) return fail(s);
     if ((s = idx->umax.ensure(1, "norm max")) != PTS_OK) return fail(s);
     cudaError_t e = cudaMemcpyAsync(idx->exemplar.ptr, exemplar, sizeof(float) * He * We * 3,
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "copy exemplar"));
     cudaMemsetAsync(idx->status.ptr, 0, sizeof(int), st);
+    // one PCA serves both searches: the exact search uses its first d components, the
+    // tensor-core and proposal searches the first d_fast (components are ordered by variance)
+    const long rank_cap = std::min<long>(idx->D, N - 1);
+    int d_fast = params->d_fast > 0 ? params->d_fast : kMaxDFast;
+    d_fast = (int)std::min<long>(d_fast, rank_cap);
+    const int d_req = params->d > 0 ? params->d : kMaxD;
+    const int d_pca = (int)std::min<long>(std::max(d_req, d_fast), rank_cap);
     int dd = 0;
-    s = pca_fit_device(idx->exemplar.ptr, He, We, w, params->d, params->var_frac, params->max_iters,
+    double trace = 0.0;
+    s = pca_fit_device(idx->exemplar.ptr, He, We, w, d_pca, params->var_frac, params->max_iters,
                        idx->mu.ptr, idx->basis.ptr, idx->eig.ptr, &dd, &idx->var_retained,
-                       &idx->eig_top, &idx->eig_iters, idx->status.ptr, st);
+                       &idx->eig_top, &idx->eig_iters, &trace, idx->status.ptr, st);
     if (s != PTS_OK) return fail(s);
+    if (params->d > 0) {
+        dd = std::min(params->d, dd);
+    } else {  // smallest d (<= 64) whose eigenvalues reach var_frac of the trace
+        std::vector<double> ev(dd);
+        cudaMemcpy(ev.data(), idx->eig.ptr, sizeof(double) * dd, cudaMemcpyDeviceToHost);
+        double acc = 0.0;
+        int pick = std::min(dd, kMaxD);
+        for (int j = 0; j < std::min(dd, kMaxD); ++j) {
+            acc += ev[j];
+            if (acc >= params->var_frac * trace) {
+                pick = j + 1;
+                break;
+            }
+        }
+        dd = pick;
+    }
+    {
+        std::vector<double> ev(dd);
+        cudaMemcpy(ev.data(), idx->eig.ptr, sizeof(double) * dd, cudaMemcpyDeviceToHost);
+        double kept = 0.0;
+        for (double v : ev) kept += v;
+        idx->var_retained = trace > 0 ? kept / trace : 0.0;
+    }
     idx->d = dd;
+    idx->d_fast = std::max(1, d_fast);
+    idx->da_fast = (idx->d_fast + 1 + 3) & ~3;
     idx->da = (dd + 1 + 3) & ~3;
     idx->ntiles = ceil_div(N, kBN);
     if ((s = idx->et.ensure((size_t)idx->ntiles * idx->da * kBN, "exemplar vectors")) != PTS_OK)
@@ -300,11 +343,23 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return fail(s);
     launch_exemplar_full(idx->exemplar.ptr, We, w, idx->nx, idx->N, idx->mu.ptr, idx->efull.ptr,
                          idx->ntiles, st);
-    idx->ktc = tc_padded_k(dd);
-    if ((s = idx->etc.ensure((size_t)idx->ntiles * kBN * idx->ktc, "bf16 exemplar tiles")) != PTS_OK)
+    // fast-mode search vectors: d_fast coordinates + the residual beyond them
+    if ((s = idx->et_fast.ensure((size_t)idx->ntiles * idx->da_fast * kBN, "fast exemplar vectors")) != PTS_OK)
         return fail(s);
-    launch_pack_exemplar_bf16(idx->et.ptr, idx->enorm.ptr, idx->ntiles, dd, idx->da, idx->ktc, idx->etc.ptr,
-                              st);
+    {
+        DevBuf<float> norm_tmp;
+        if ((s = norm_tmp.ensure((size_t)idx->ntiles * kBN, "norm scratch")) != PTS_OK) return fail(s);
+        launch_exemplar_pad(idx->et_fast.ptr, norm_tmp.ptr, idx->N, idx->ntiles, idx->da_fast, st);
+        launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 1,
+                       idx->et_fast.ptr, norm_tmp.ptr, nullptr, 0.0f, nullptr, st);
+        cudaStreamSynchronize(st);
+        norm_tmp.release();
+    }
+    idx->ktc = tc_padded_k(idx->d_fast);
+    if ((s = idx->etc.ensure((size_t)idx->ntiles * kBN * idx->ktc, "fp16 exemplar tiles")) != PTS_OK)
+        return fail(s);
+    launch_pack_exemplar(idx->et_fast.ptr, idx->enorm.ptr, idx->ntiles, idx->d_fast, idx->da_fast, idx->ktc,
+                         idx->etc.ptr, st);
     e = cudaMemcpyAsync(&idx->unorm2_max, idx->umax.ptr, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "read norm max"));
     e = cudaStreamSynchronize(st);
@@ -342,6 +397,7 @@ void pts_index_destroy(pts_index idx) {
     idx->enorm.release();
     idx->efull.release();
     idx->etc.release();
+    idx->et_fast.release();
     {
         ProposalState &pr = idx->prop;
         pr.centroids.release();
@@ -373,6 +429,7 @@ pts_status pts_index_get_info(pts_index idx, pts_index_info *info) {
     info->N = idx->N;
     info->d = idx->d;
     info->da = idx->da;
+    info->d_fast = idx->d_fast;
     info->var_retained = idx->var_retained;
     info->eig_top = idx->eig_top;
     info->eig_iters = idx->eig_iters;
@@ -396,7 +453,7 @@ pts_status pts_index_search_stats(pts_index idx, pts_search_stats *stats, void *
     cudaStream_t st = as_stream(stream);
     *stats = idx->last;
     stats->fallback_queries = 0;
-    if (idx->ws.counters.ptr && (idx->last_mode == PTS_EXACT_F32 || idx->last_mode == PTS_PROPOSAL_BF16)) {
+    if (idx->ws.counters.ptr && (idx->last_mode == PTS_EXACT_F32 || idx->last_mode == PTS_PROPOSAL)) {
         unsigned int c[4] = {0, 0, 0, 0};
         PTS_CUDA_TRY(cudaMemcpyAsync(c, idx->ws.counters.ptr, sizeof(c), cudaMemcpyDeviceToHost, st));
         PTS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -521,7 +578,7 @@ pts_status pts_train_proposal(pts_index idx, const float *y, const int32_t *nn, 
     PTS_TRY(pr.counts.ensure(C, "cluster sizes"));
     PTS_TRY(pr.off.ensure(C + 1, "cluster offsets"));
     PTS_TRY(pr.members.ensure(N, "cluster members"));
-    PTS_TRY(pr.mrow.ensure((size_t)N * da, "member vectors"));
+    PTS_TRY(pr.mrow.ensure((size_t)N * idx->da_fast, "member vectors"));
     PTS_TRY(pr.mnorm.ensure(N, "member norms"));
     PTS_TRY(pr.median.ensure(C, "cluster medians"));
     launch_extract_y(idx->et.ptr, N, da, d, Y.ptr, st);
@@ -529,7 +586,8 @@ pts_status pts_train_proposal(pts_index idx, const float *y, const int32_t *nn, 
     for (int i = 0; i < C; ++i) u[i] = uniform();
     PTS_TRY(kmeans_device(Y.ptr, N, d, C, u.data(), iters, pr.centroids.ptr, pr.assign.ptr, cost.ptr, pr.counts.ptr,
                           pr.off.ptr, pr.members.ptr, nullptr, st));
-    launch_member_rows(idx->et.ptr, idx->enorm.ptr, N, da, pr.members.ptr, pr.mrow.ptr, pr.mnorm.ptr, st);
+    launch_member_rows(idx->et_fast.ptr, idx->enorm.ptr, N, idx->da_fast, pr.members.ptr, pr.mrow.ptr, pr.mnorm.ptr,
+                       st);
     DevBuf<int> lab;
     DevBuf<float> dist;
     PTS_TRY(lab.ensure(n, "pair labels"));
@@ -637,9 +695,9 @@ pts_status pts_gemm_selftest(int M, int N, int K, double *max_rel_err) {
     return gemm_selftest(M, N, K, max_rel_err);
 }
 
-pts_status pts_tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref) {
+pts_status pts_tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref) {
     if (!max_abs_err || !max_abs_ref) return set_error(PTS_ERR_INVALID_ARG, "pts_tc_selftest: null pointer");
-    return tc_selftest(N, K, max_abs_err, max_abs_ref);
+    return tc_selftest(N, K, f16, max_abs_err, max_abs_ref);
 }
 
 pts_status pts_downsample2(const float *in, int H, int W, float *out, void *stream) {

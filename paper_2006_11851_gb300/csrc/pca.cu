@@ -23,7 +23,8 @@
 namespace pts {
 namespace {
 
-constexpr int kMaxM = 112;  // subspace width bound (2 m^2 doubles fit in shared memory)
+constexpr int kMaxM = 112;     // subspace widths up to this keep the m x m work in shared memory
+constexpr int kMaxMBig = 256;  // beyond it (up to this) the m x m matrices live in global memory
 
 __global__ void __launch_bounds__(256)
     k_win_mean(const float *__restrict__ Z, int We, int w, int ex, long N, double *__restrict__ mu) {
@@ -180,10 +181,13 @@ __global__ void __launch_bounds__(256)
 }
 
 // Cholesky G = L L^T of an m x m SPD matrix, one CTA, in place (lower part).
-__global__ void __launch_bounds__(512) k_chol(double *__restrict__ G, int m, int *__restrict__ status) {
-    extern __shared__ double sG[];
+__global__ void __launch_bounds__(512) k_chol(double *__restrict__ G, int m, int in_global,
+                                              int *__restrict__ status) {
+    extern __shared__ double sG_dyn[];
+    double *sG = in_global ? G : sG_dyn;
     const int tid = threadIdx.x;
-    for (int i = tid; i < m * m; i += blockDim.x) sG[i] = G[i];
+    if (!in_global)
+        for (int i = tid; i < m * m; i += blockDim.x) sG[i] = G[i];
     __syncthreads();
     for (int k = 0; k < m; ++k) {
         if (tid == 0) {
@@ -228,12 +232,13 @@ __global__ void k_trsm_rows(double *__restrict__ V, int rows, int m, const doubl
 // eigenvector j.
 __global__ void __launch_bounds__(512)
     k_jacobi_small(const double *__restrict__ Hin, int m, double *__restrict__ evals,
-                   double *__restrict__ Vout, int *__restrict__ status) {
+                   double *__restrict__ Vout, double *__restrict__ work, int *__restrict__ status) {
     extern __shared__ double sm_j[];
-    double *sH = sm_j;
+    // work != NULL: H and V live in that global scratch (2 m^2 doubles) instead
+    double *sH = work ? work : sm_j;
     double *sV = sH + m * m;
-    __shared__ int pp[kMaxM / 2 + 1], qq[kMaxM / 2 + 1], act[kMaxM / 2 + 1];
-    __shared__ double cc[kMaxM / 2 + 1], ss[kMaxM / 2 + 1];
+    __shared__ int pp[kMaxMBig / 2 + 1], qq[kMaxMBig / 2 + 1], act[kMaxMBig / 2 + 1];
+    __shared__ double cc[kMaxMBig / 2 + 1], ss[kMaxMBig / 2 + 1];
     __shared__ int nrot, np_sh;
     __shared__ double fro_sh;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(512)
     }
     if (!converged && tid == 0) atomicOr(status, kDevErrNumeric);
     // order by decreasing eigenvalue (thread 0 computes the permutation)
-    __shared__ int ord[kMaxM];
+    __shared__ int ord[kMaxMBig];
     if (tid == 0) {
         for (int i = 0; i < m; ++i) ord[i] = i;
         for (int i = 0; i < m; ++i) {
@@ -419,7 +424,7 @@ struct Scratch {
 pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, double var_frac,
                           int max_iters, float *mean_out, float *basis_out, double *eig_out,
                           int *d_used, double *var_retained, double *eig_top, int *iters_used,
-                          int *status, cudaStream_t st) {
+                          double *trace_out, int *status, cudaStream_t st) {
     const int D = 3 * w * w;
     const int ex = We - w + 1;
     const long N = (long)(He - w + 1) * ex;
@@ -428,7 +433,7 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
     if (dd < 1) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: too few exemplar windows");
     if (d > 0 && d > dd) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: d exceeds min(D, N-1)");
     int m = std::min<long>(std::min<long>(D, N - 1), dd + std::max(16, dd / 2));
-    m = std::min(m, kMaxM);
+    m = std::min(m, kMaxMBig);
     if (max_iters <= 0) max_iters = 200;
 
     Scratch sc;
@@ -450,9 +455,12 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
     PTS_TRY(sc.get(&th, m, "pca theta"));
     PTS_TRY(sc.get(&res, m, "pca residual"));
     PTS_TRY(sc.get(&diag, D, "pca diag"));
+    const bool big = m > kMaxM;
+    double *jwork = nullptr;
+    if (big) PTS_TRY(sc.get(&jwork, (size_t)2 * m * m, "pca jacobi scratch"));
 
-    const size_t jac_smem = sizeof(double) * 2 * m * m;
-    const size_t chol_smem = sizeof(double) * m * m;
+    const size_t jac_smem = big ? 0 : sizeof(double) * 2 * m * m;
+    const size_t chol_smem = big ? 0 : sizeof(double) * m * m;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -477,7 +485,7 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
         for (int rep = 0; rep < 2; ++rep) {
             dgemm<true, false>(m, m, D, Vm, m, Vm, m, G, m, st);
             count_launches(1);
-            k_chol<<<1, 512, chol_smem, st>>>(G, m, status);
+            k_chol<<<1, 512, chol_smem, st>>>(G, m, big ? 1 : 0, status);
             count_launches(1);
             k_trsm_rows<<<ceil_div(D, 128), 128, 0, st>>>(Vm, D, m, G);
         }
@@ -492,7 +500,7 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
         dgemm<false, false>(D, m, D, C, D, V, m, Y, m, st);  // Y = Sigma V
         dgemm<true, false>(m, m, D, V, m, Y, m, G, m, st);   // H = V^T Y
         count_launches(1);
-        k_jacobi_small<<<1, 512, jac_smem, st>>>(G, m, th, S, status);
+        k_jacobi_small<<<1, 512, jac_smem, st>>>(G, m, th, S, jwork, status);
         dgemm<false, false>(D, m, m, V, m, S, m, Vr, m, st);  // Ritz vectors
         dgemm<false, false>(D, m, m, Y, m, S, m, Yr, m, st);  // Sigma * Ritz vectors
         count_launches(1);
@@ -530,6 +538,7 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
     PTS_CUDA_TRY(cudaStreamSynchronize(st));
     PTS_CUDA_TRY(cudaGetLastError());
     if (d_used) *d_used = dfin;
+    if (trace_out) *trace_out = trace;
     if (var_retained) *var_retained = trace > 0 ? kept / trace : 0.0;
     if (eig_top) *eig_top = hth[0];
     if (iters_used) *iters_used = std::min(it, max_iters);

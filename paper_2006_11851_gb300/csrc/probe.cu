@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_probe(const float *__restrict__ qcoord,
                                                const int *__restrict__ off, const int *__restrict__ members,
                                                const float *__restrict__ mrow, const float *__restrict__ mnorm,
                                                int *__restrict__ cand_idx, float *__restrict__ cand_lb) {
-    __shared__ float qa[8][kMaxDA];
+    __shared__ float qa[8][kMaxDAFast];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= Q) return;

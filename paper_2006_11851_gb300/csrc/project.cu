@@ -8,7 +8,7 @@
 // owns 32 consecutive windows of one window row; for each window row dy it
 // stages the shared pixel strip, the matching D/w slice of the basis and of mu
 // in shared memory, and 8 thread groups each accumulate d/8 coordinates of
-// all 32 windows.
+// all 32 windows (d <= 128).
 //
 // layout 0 (queries):  coord[win][da]              = (y, r, 0, ...)
 //                      tau[win] = tau_scale * (||u||^2 + max_n ||u_n||^2)
@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(256)
     const int qy = blockIdx.y, qx0 = blockIdx.x * kPW;
     const int tid = threadIdx.x, m = tid & 31, g = tid >> 5;
     const int y0 = qy * stride, x0 = qx0 * stride;
-    float acc[8];
+    float acc[kMaxDPca / 8];
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) acc[jj] = 0.0f;
+    for (int jj = 0; jj < kMaxDPca / 8; ++jj) acc[jj] = 0.0f;
     float un = 0.0f;
     const size_t img_row = (size_t)W * 3;
     for (int dy = 0; dy < w; ++dy) {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256)
             const float a = xs[e] - s_mu[e];
             un = fmaf(a, a, un);
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
+            for (int jj = 0; jj < kMaxDPca / 8; ++jj) {
                 const int j = g + 8 * jj;
                 if (j < d) acc[jj] = fmaf(s_basis[j * row + e], a, acc[jj]);
             }
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
     }
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
+    for (int jj = 0; jj < kMaxDPca / 8; ++jj) {
         const int j = g + 8 * jj;
         if (j < d) s_y[m * d + j] = acc[jj];
     }

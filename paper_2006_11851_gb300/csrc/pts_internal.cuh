@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,8 +19,11 @@ namespace pts {
 constexpr int kBN = 128;   // exemplar windows per tile (32 lanes x 4)
 constexpr int kBQ = 64;    // queries per CTA (8 warps x 8 rows)
 constexpr int kTopK = 32;  // candidates kept per query (one per lane)
-constexpr int kMaxDA = 68; // d <= 64 coordinates + residual, padded to 4
-constexpr int kMaxD = 64;
+constexpr int kMaxDA = 68;     // exact search: d <= 64 coordinates + residual, padded to 4
+constexpr int kMaxD = 64;      // PCA dimensions of the exact search
+constexpr int kMaxDPca = 128;  // PCA dimensions an index may keep (fast modes use up to kMaxDFast)
+constexpr int kMaxDFast = 124;  // tensor-core / proposal search: d + residual + 3 norm slots <= 128
+constexpr int kMaxDAFast = 128;
 
 // device status word bits (OR-ed by kernels, read at synchronising calls)
 constexpr int kDevErrBounds = 1;   // an index read from an input was out of range
@@ -88,6 +92,9 @@ struct Workspace {
     DevBuf<float> qfull;       // [Qpad/64][Dp][64] centred full vectors of failing queries
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
     DevBuf<float> thr0;        // [Q] warm-start bounds
+    DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
+    DevBuf<float> part_v;      // [Q][parts][32] per-part candidate lists of the tensor-core search
+    DevBuf<int> part_i;
     int warm_q = -1, warm_ho = -1, warm_wo = -1, warm_stride = -1;  // geometry of cand_idx
     DevBuf<unsigned int> counters;  // [4]: fail, fail2, brute, spare
     DevBuf<int> nn;            // [Q] (synthesize_level)
@@ -134,6 +141,7 @@ struct ProposalState {
 struct pts_index_s {
     int device = 0;
     int He = 0, We = 0, w = 0, D = 0, N = 0, d = 0, da = 0;
+    int d_fast = 0, da_fast = 0;  // PCA dimensions / vector length of the fast modes
     int ny = 0, nx = 0;  // exemplar window grid
     int ntiles = 0;      // ceil(N / kBN)
     double var_retained = 0.0, eig_top = 0.0;
@@ -146,7 +154,8 @@ struct pts_index_s {
     pts::DevBuf<float> et;        // [ntiles][da][kBN] = -2 * (y_n, r_n, 0...)
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
     pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
-    pts::DevBuf<__nv_bfloat16> etc;  // [ntiles][128 x Ktc] BF16 MMA operand tiles
+    pts::DevBuf<float> et_fast;   // [ntiles][da_fast][kBN] = -2 (y_n, r_n, 0...) with d_fast coordinates
+    pts::DevBuf<__half> etc;      // [ntiles][128 x Ktc] FP16 MMA operand tiles
     int ktc = 0;                  // K of the tensor-core search
     pts::DevBuf<float> umax;      // [1]
     pts::DevBuf<int> status;      // [1] device status word
@@ -165,7 +174,7 @@ namespace pts {
 pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, double var_frac,
                           int max_iters, float *mean_out, float *basis_out, double *eig_out,
                           int *d_used, double *var_retained, double *eig_top, int *iters_used,
-                          int *status, cudaStream_t st);
+                          double *trace_out, int *status, cudaStream_t st);
 // project.cu
 void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
                     const float *basis, int d, int da, int layout, float *out_coord,
@@ -186,15 +195,17 @@ void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const fl
                           float *efull, int ntiles, cudaStream_t st);
 // search_tc.cu
 int tc_padded_k(int d);
-void launch_pack_exemplar_bf16(const float *et, const float *enorm, int ntiles, int d, int da, int K,
-                               __nv_bfloat16 *out, cudaStream_t st);
-void launch_search_tc(const float *qcoord, const float *qnorm, int Q, int d, int da, int K,
-                      const __nv_bfloat16 *etile, int ntiles, const float *thr0, int *cand_idx, float *cand_lb,
+int tc_query_blocks(int Q);
+int tc_parts(int Q, int ntiles);
+void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st);
+void launch_pack_exemplar(const float *et, const float *enorm, int ntiles, int d, int da, int K, __half *out,
+                          cudaStream_t st);
+void launch_warm_threshold(const int *prev_idx, const __half *qtile, const float *qnorm, const __half *etile,
+                           const float *umax, int Q, int K, int N, float eps_scale, float *thr0, cudaStream_t st);
+void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
+                      int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st);
-void launch_warm_threshold(const int *prev_idx, const float *qcoord, const float *qnorm,
-                           const __nv_bfloat16 *etile, const float *umax, int Q, int d, int da, int K, int N,
-                           float eps_scale, float *thr0, cudaStream_t st);
-pts_status tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref);
+pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref);
 // kmeans.cu
 pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, int iters, float *C, int *assign,
                          float *cost, int *counts, int *off, int *members, int *iters_used, cudaStream_t st);

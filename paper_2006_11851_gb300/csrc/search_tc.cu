@@ -1,23 +1,34 @@
-// search_tc.cu -- PCA-space search phase (E-step) on the tcgen05 tensor cores, BF16 operands,
-// FP32 accumulation in tensor memory.
+// search_tc.cu -- PCA-space search phase (E-step) on the tcgen05 tensor cores: FP16 operands,
+// FP32 accumulation in tensor memory, a per-query top-32 in the epilogue.
 //
-// The GEMM is laid out transposed: M = 128 exemplar windows per tile (TMEM lanes), N = 64
-// queries per CTA (TMEM columns), K = the search vector (d PCA coordinates, the residual norm,
-// and three slots that carry ||u_n||^2 as a BF16 hi/mid/lo split against query-side ones, so
-// the accumulator already holds p(q, n) = ||u_n||^2 - 2 a_q . e_n with no epilogue add).
-// An epilogue warp reads a 32-lane quarter of TMEM (32 exemplar windows) x 16 columns (16
-// queries): its lanes span windows and its registers span queries, so the per-query top-32
-// lists stay warp-resident (one sorted entry per lane) and insertions never diverge.
+// Score of query q against exemplar window n (section 2.2: PCA coordinates plus the residual
+// norm bound the full-dimension distance from below):
+//   p(q, n) = ||u_n||^2 - 2 (y_q . y_n + r_q r_n),   LB(q, n) = p(q, n) + ||u_q||^2.
+// K carries d coordinates, the residual and three slots holding ||u_n||^2 split FP16
+// hi/mid/lo against query-side ones, so the accumulator is p with no epilogue add.
 //
-// Warp roles (18 warps): 0-15 epilogue (TMEM lane quarter = warp % 4, query chunk = warp / 4),
-// 16 producer (1-D bulk copies of pre-laid-out exemplar tiles into an 8-stage ring), 17 MMA
-// issuer and TMEM owner.  One accumulator stage holds 4 exemplar tiles (4 x 64 columns) so the
-// MMA -> epilogue -> release handoff is paid once per 512 windows; two stages fill all 512 TMEM
-// columns.  Every wait is bounded; on a timeout the kernel flags the status word, drains what
-// it issued and frees TMEM.  Each quarter keeps its own partial lists; they are merged in shared
-// memory at the end.  An optional per-query bound thr0 (warm start) caps the lists' threshold.
+// GEMM layout: M = 128 queries per CTA (TMEM lane = query), N = 128 windows per exemplar tile
+// (TMEM columns), both operands K-major in the no-swizzle core-matrix layout, staged by 1-D bulk
+// copies of pre-packed tiles.  Four accumulator stages of 128 columns fill TMEM's 512.
+//
+// Warps (6): 0-3 epilogue (TMEM lane quarter = warp), 4 producer, 5 MMA issuer and TMEM owner.
+// An epilogue thread owns one query.  Per tile it loads its 128 accumulators (two 64-column
+// tcgen05.ld), takes their minimum and, only when that beats the query's threshold, appends the
+// windows below it to a per-thread queue in shared memory: a store, no dependent loads.  When a
+// queue fills, the warp merges it into the query's sorted 32-entry list cooperatively (bitonic
+// sort of the queue, bitonic merge with the list, one entry per lane), and the list's last entry
+// becomes the new threshold.  Lists and queues use odd row strides, so neither a warp's appends
+// (one slot, 32 threads) nor its merges (32 slots, one query) collide on banks.
+//
+// The exemplar tiles of a query block may be split across blockIdx.y; each part writes its
+// sorted 32 and k_merge_parts merges them.  An optional per-query bound thr0 (warm start) seeds
+// the lists with sentinels (thr0, INT_MAX): only windows strictly below it are kept, and at least
+// 32 windows are (the previous search's 32, re-scored, lie below thr0).  All waits are bounded;
+// on a timeout the kernel flags the status word, drains its copies and frees TMEM.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "tc_common.cuh"
@@ -25,32 +36,32 @@
 namespace pts {
 namespace {
 
-constexpr int kTcM = 128;
-constexpr int kTcN = 64;
-constexpr int kTcSub = 4;      // exemplar tiles per accumulator stage
-constexpr int kTcStages = 5;   // exemplar tiles in flight
-constexpr int kTcQueue = 16;   // pending candidates per query before a merge
-constexpr int kTcEpiWarps = 16;
-constexpr int kTcThreads = (kTcEpiWarps + 2) * 32;
-constexpr int kTcMaxK = 80;
-constexpr int kTcStageCols = kTcSub * kTcN;  // 256 TMEM columns per accumulator stage
-constexpr int kTcCols = 2 * kTcStageCols;    // 512: all of TMEM (one CTA per SM)
+constexpr int kQM = 128;            // queries per CTA (MMA M)
+constexpr int kTN = 128;            // exemplar windows per tile (MMA N)
+constexpr int kAcc = 4;             // accumulator stages of kTN columns
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
+constexpr int kMaxKt = 128;         // K of the search vectors
+constexpr int kRing = 96 * 1024;    // bytes of exemplar-tile ring
+constexpr int kMaxStages = 8;
+constexpr int kQueue = 32;          // queued candidates per query before a merge
+constexpr int kListStride = kTopK + 1;
+constexpr int kQueueStride = kQM + 1;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNoWindow = INT_MAX;
 
 struct TcSmem {
-    alignas(128) __nv_bfloat16 q[kTcN * kTcMaxK];
-    alignas(128) __nv_bfloat16 e[kTcStages][kTcM * kTcMaxK];
-    // per epilogue warp, per query of its chunk: the partial top-32 list (entry = lane)
-    float lst_d[kTcEpiWarps][16][kTopK];
-    int lst_i[kTcEpiWarps][16][kTopK];
-    // per epilogue warp, per query: candidates that passed the filter, not merged yet
-    float que_d[kTcEpiWarps][16][kTcQueue];
-    int que_i[kTcEpiWarps][16][kTcQueue];
-    float cap[kTcN];
-    uint64_t full[kTcStages], empty[kTcStages], acc_full[2], acc_empty[2], done;
+    alignas(1024) unsigned char q[kQM * kMaxKt * 2];
+    alignas(1024) unsigned char e[kRing];
+    float lv[kQM * kListStride];    // per query: sorted (value, window) list
+    int li[kQM * kListStride];
+    float qv[kQueue * kQueueStride];  // per query: pending candidates, slot-major
+    int qi[kQueue * kQueueStride];
+    uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAcc], acc_empty[kAcc], q_full, done;
     uint32_t tmem_base;
     int abort_flag;
 };
+static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "tensor-core search tile set exceeds shared memory");
 
 // (a, ia) < (b, ib) lexicographically
 __device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
@@ -75,114 +86,122 @@ __device__ __forceinline__ void warp_sort32(float &v, int &i, int lane) {
     }
 }
 
-// Merge a sorted batch (v, i) into the sorted list (ld, li), keeping the 32
-// smallest: min of the list and the reversed batch is bitonic; 5 merge stages
-// sort it.
-__device__ __forceinline__ void warp_merge32(float &ld, int &li, float &thr, float cap, float v, int i,
-                                             int lane) {
-    const float rv = __shfl_sync(kFull, v, 31 - lane);
-    const int ri = __shfl_sync(kFull, i, 31 - lane);
-    if (lex_less(rv, ri, ld, li)) {
-        ld = rv;
-        li = ri;
+// (v, i) := the 32 smallest of two ascending lists (v, i) and (w, j), ascending: the
+// elementwise min of one list and the other reversed is bitonic; five stages sort it.
+__device__ __forceinline__ void warp_merge32(float &v, int &i, float w, int j, int lane) {
+    const float rw = __shfl_sync(kFull, w, 31 - lane);
+    const int rj = __shfl_sync(kFull, j, 31 - lane);
+    if (lex_less(rw, rj, v, i)) {
+        v = rw;
+        i = rj;
     }
 #pragma unroll
-    for (int j = 16; j > 0; j >>= 1) {
-        const float ov = __shfl_xor_sync(kFull, ld, j);
-        const int oi = __shfl_xor_sync(kFull, li, j);
-        const bool take = ((lane & j) == 0) ? lex_less(ov, oi, ld, li) : lex_less(ld, li, ov, oi);
+    for (int s = 16; s > 0; s >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, v, s);
+        const int oi = __shfl_xor_sync(kFull, i, s);
+        const bool take = ((lane & s) == 0) ? lex_less(ov, oi, v, i) : lex_less(v, i, ov, oi);
         if (take) {
-            ld = ov;
-            li = oi;
+            v = ov;
+            i = oi;
         }
     }
-    thr = fminf(cap, __shfl_sync(kFull, ld, 31));
 }
 
-// Merges a query's pending queue (count entries) into its list, both in
-// shared memory (list entry / queue entry = lane), and returns the new
-// threshold.  Out of line, so the unrolled per-query loop stays small.
-__device__ __noinline__ float flush_queue(float *lst_d, int *lst_i, const float *que_d, const int *que_i,
-                                          int count, float cap, float thr, int lane) {
-    float ld = lst_d[lane];
-    int li = lst_i[lane];
-    float v = lane < count ? que_d[lane] : INFINITY;
-    int i = lane < count ? que_i[lane] : 0x7fffffff;
-    warp_sort32(v, i, lane);
-    warp_merge32(ld, li, thr, cap, v, i, lane);
-    lst_d[lane] = ld;
-    lst_i[lane] = li;
+// Merges the queues of this warp's queries that hold at least min_cnt entries into their lists,
+// one query at a time with the whole warp (entry = lane).  Returns the calling lane's threshold
+// (its list's last value if its queue was merged, else thr); the caller clears those counts.
+__device__ __noinline__ float flush_queues(float *lv, int *li, const float *qv, const int *qi, int cnt, float thr,
+                                           int min_cnt, int row0, int lane) {
+    __syncwarp();  // the queues' appends are visible to the whole warp
+    unsigned todo = __ballot_sync(kFull, cnt >= min_cnt && cnt > 0);
+    while (todo) {
+        const int r = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int c = __shfl_sync(kFull, cnt, r);
+        const int row = row0 + r;
+        float v = lane < c ? qv[lane * kQueueStride + row] : INFINITY;
+        int i = lane < c ? qi[lane * kQueueStride + row] : kNoWindow;
+        warp_sort32(v, i, lane);
+        float l = lv[row * kListStride + lane];
+        int j = li[row * kListStride + lane];
+        warp_merge32(l, j, v, i, lane);
+        lv[row * kListStride + lane] = l;
+        li[row * kListStride + lane] = j;
+        const float t = __shfl_sync(kFull, l, 31);
+        if (lane == r) thr = t;
+    }
     __syncwarp();
     return thr;
 }
 
-// Merges one candidate per lane (the lanes set in fl) straight into a list.
-__device__ __noinline__ float merge_lanes(float *lst_d, int *lst_i, float cap, float thr, float cv, int ci,
-                                          unsigned fl, int lane) {
-    float ld = lst_d[lane];
-    int li = lst_i[lane];
-    float v = ((fl >> lane) & 1u) ? cv : INFINITY;
-    int i = ((fl >> lane) & 1u) ? ci : 0x7fffffff;
-    warp_sort32(v, i, lane);
-    warp_merge32(ld, li, thr, cap, v, i, lane);
-    lst_d[lane] = ld;
-    lst_i[lane] = li;
-    __syncwarp();
-    return thr;
+// One half (64 columns, from OFF) of a tile for the calling thread's query: queue the windows
+// below the threshold, merging the warp's queues whenever one fills.
+template <int OFF>
+__device__ __forceinline__ void scan64(const float (&v)[128], int nb, float &thr, int &cnt, TcSmem &sm, int row0,
+                                       int lane) {
+    float m[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        m[j] = fminf(fminf(fminf(v[OFF + 8 * j], v[OFF + 8 * j + 1]), fminf(v[OFF + 8 * j + 2], v[OFF + 8 * j + 3])),
+                     fminf(fminf(v[OFF + 8 * j + 4], v[OFF + 8 * j + 5]),
+                           fminf(v[OFF + 8 * j + 6], v[OFF + 8 * j + 7])));
+    const float mm =
+        fminf(fminf(fminf(m[0], m[1]), fminf(m[2], m[3])), fminf(fminf(m[4], m[5]), fminf(m[6], m[7])));
+    if (!__any_sync(kFull, mm < thr)) return;
+    const int row = row0 + lane;
+    // windows arrive in increasing index order, so a strict value test keeps the
+    // lexicographically smallest (value, index) pairs; groups of 8 whose minimum no lane
+    // beats are skipped whole
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        if (!__any_sync(kFull, m[g] < thr)) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float x = v[OFF + 8 * g + e];
+            if (x < thr) {
+                sm.qv[cnt * kQueueStride + row] = x;
+                sm.qi[cnt * kQueueStride + row] = nb + 8 * g + e;
+                ++cnt;
+            }
+        }
+        // room for the next group's 8
+        if (__any_sync(kFull, cnt > kQueue - 8)) {
+            const bool f = cnt >= kQueue / 2;
+            thr = flush_queues(sm.lv, sm.li, sm.qv, sm.qi, cnt, thr, kQueue / 2, row0, lane);
+            if (f) cnt = 0;
+        }
+    }
 }
 
-// Merges a sorted list held by another warp into this list (both in shared memory).
-__device__ __noinline__ float merge_smem(float *lst_d, int *lst_i, float cap, float thr, const float *od,
-                                         const int *oi, int lane) {
-    float ld = lst_d[lane];
-    int li = lst_i[lane];
-    const float cv = od[lane];
-    const int ci = oi[lane];
-    if (__any_sync(kFull, cv < thr)) warp_merge32(ld, li, thr, cap, cv, ci, lane);
-    lst_d[lane] = ld;
-    lst_i[lane] = li;
-    __syncwarp();
-    return thr;
-}
-
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_search_tc(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int d, int da,
-                int K, const __nv_bfloat16 *__restrict__ etile, int ntiles, const float *__restrict__ thr0,
-                int *__restrict__ cand_idx, float *__restrict__ cand_lb, int *__restrict__ status) {
+__global__ void __launch_bounds__(kThreads, 1)
+    k_search_tc(const __half *__restrict__ qtile, const float *__restrict__ qnorm, int Q, int K,
+                const __half *__restrict__ etile, int ntiles, int tiles_per_part, int nstages,
+                const float *__restrict__ thr0, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
+                float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
+    TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     volatile int *abort_flag = &sm.abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int qbase = blockIdx.x * kTcN;
+    const int nparts = gridDim.y, part = blockIdx.y;
+    const int t_begin = part * tiles_per_part;
+    const int nt = max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
+    const uint32_t stage_bytes = (uint32_t)(kTN * K * 2);
+    const uint32_t q_bytes = (uint32_t)(kQM * K * 2);
 
-    // query tile -> shared memory, core-matrix layout
-    for (int i = tid; i < kTcN * K; i += kTcThreads) {
-        const int r = i / K, k = i - r * K;
-        const int q = qbase + r;
-        float v = 0.0f;
-        if (q < Q) {
-            if (k <= d)
-                v = qcoord[(size_t)q * da + k];
-            else if (k <= d + 3)
-                v = 1.0f;
-        }
-        *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(sm.q) + core_offset(r, k, kTcN)) =
-            __float2bfloat16_rn(v);
-    }
-    fence_proxy_async_smem();
-    if (warp == kTcEpiWarps + 1) {
-        tmem_alloc(&sm.tmem_base, kTcCols);
+    if (warp == kEpiWarps + 1) {
+        tmem_alloc(&sm.tmem_base, kAcc * kTN);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < nstages; ++s) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sm.acc_full[b], 1);
-            mbar_init(&sm.acc_empty[b], kTcEpiWarps);
+        for (int a = 0; a < kAcc; ++a) {
+            mbar_init(&sm.acc_full[a], 1);
+            mbar_init(&sm.acc_empty[a], kEpiWarps);
         }
+        mbar_init(&sm.q_full, 1);
         mbar_init(&sm.done, 1);
         fence_mbar_init();
         sm.abort_flag = 0;
@@ -191,59 +210,51 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
-    const uint32_t tile_bytes = (uint32_t)(kTcM * K * 2);
 
-    if (warp == kTcEpiWarps) {
+    if (warp == kEpiWarps) {
         // ---------------- producer ----------------
         if (lane == 0) {
+            mbar_expect_tx(&sm.q_full, q_bytes);
+            bulk_g2s(sm.q, qtile + (size_t)blockIdx.x * kQM * K, q_bytes, &sm.q_full);
             int issued = 0;
-            for (int t = 0; t < ntiles; ++t) {
-                const int s = t % kTcStages;
-                if (t >= kTcStages &&
-                    !mbar_wait_or_abort(&sm.empty[s], (uint32_t)(((t / kTcStages) - 1) & 1), status, abort_flag))
+            for (int i = 0; i < nt; ++i) {
+                const int s = i % nstages;
+                if (i >= nstages &&
+                    !mbar_wait_or_abort(&sm.empty[s], (uint32_t)(((i / nstages) - 1) & 1), status, abort_flag))
                     break;
-                mbar_expect_tx(&sm.full[s], tile_bytes);
-                bulk_g2s(&sm.e[s][0], etile + (size_t)t * kTcM * K, tile_bytes, &sm.full[s]);
-                issued = t + 1;
+                mbar_expect_tx(&sm.full[s], stage_bytes);
+                bulk_g2s(sm.e + (size_t)s * stage_bytes, etile + (size_t)(t_begin + i) * kTN * K, stage_bytes,
+                         &sm.full[s]);
+                issued = i + 1;
             }
-            if (*abort_flag) {  // let the copies this thread issued land
-                for (int t = issued - kTcStages; t < issued; ++t)
-                    if (t >= 0) mbar_wait_bounded(&sm.full[t % kTcStages], (uint32_t)((t / kTcStages) & 1), status);
-            }
+            // every copy this thread issued has landed before the CTA may exit
+            mbar_wait_bounded(&sm.q_full, 0, status);
+            for (int i = max(0, issued - nstages); i < issued; ++i)
+                mbar_wait_bounded(&sm.full[i % nstages], (uint32_t)((i / nstages) & 1), status);
         }
-    } else if (warp == kTcEpiWarps + 1) {
+    } else if (warp == kEpiWarps + 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(kTcM, kTcN);
-            const uint32_t lbo_e = (uint32_t)(kTcM / 8) * 128u, lbo_q = (uint32_t)(kTcN / 8) * 128u;
+            const uint32_t idesc = idesc_f16(kQM, kTN);
+            const uint32_t lbo_q = (uint32_t)(kQM / 8) * 128u, lbo_e = (uint32_t)(kTN / 8) * 128u;
             const uint32_t qaddr = smem_u32(sm.q);
-            const int nsuper = (ntiles + kTcSub - 1) / kTcSub;
-            bool ok = true;
-            for (int u = 0; u < nsuper && ok; ++u) {
-                const int b = u & 1;
-                if (u >= 2 && !mbar_wait_or_abort(&sm.acc_empty[b], (uint32_t)(((u >> 1) - 1) & 1), status,
-                                                  abort_flag))
+            bool ok = mbar_wait_or_abort(&sm.q_full, 0, status, abort_flag);
+            for (int i = 0; i < nt && ok; ++i) {
+                const int s = i % nstages, a = i % kAcc;
+                if (i >= kAcc &&
+                    !mbar_wait_or_abort(&sm.acc_empty[a], (uint32_t)(((i / kAcc) - 1) & 1), status, abort_flag))
                     break;
+                if (!mbar_wait_or_abort(&sm.full[s], (uint32_t)((i / nstages) & 1), status, abort_flag)) break;
                 tc_fence_after();
-                for (int sub = 0; sub < kTcSub; ++sub) {
-                    const int t = u * kTcSub + sub;
-                    if (t >= ntiles) break;
-                    const int s = t % kTcStages;
-                    if (!mbar_wait_or_abort(&sm.full[s], (uint32_t)((t / kTcStages) & 1), status, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t eaddr = smem_u32(&sm.e[s][0]);
-                    const uint32_t dcol = tmem + (uint32_t)(b * kTcStageCols + sub * kTcN);
-                    for (int ks = 0; ks < K / 16; ++ks) {
-                        const uint64_t adesc = smem_desc(eaddr + ks * 2u * lbo_e, lbo_e, 128u);
-                        const uint64_t bdesc = smem_desc(qaddr + ks * 2u * lbo_q, lbo_q, 128u);
-                        mma_bf16(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
-                    }
-                    mma_commit(&sm.empty[s]);
+                const uint32_t eaddr = smem_u32(sm.e + (size_t)s * stage_bytes);
+                const uint32_t dcol = tmem + (uint32_t)(a * kTN);
+                for (int ks = 0; ks < K / 16; ++ks) {
+                    const uint64_t adesc = smem_desc(qaddr + ks * 2u * lbo_q, lbo_q, 128u);
+                    const uint64_t bdesc = smem_desc(eaddr + ks * 2u * lbo_e, lbo_e, 128u);
+                    mma_bf16(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
                 }
-                if (ok) mma_commit(&sm.acc_full[b]);
+                mma_commit(&sm.empty[s]);
+                mma_commit(&sm.acc_full[a]);
             }
             // all MMAs issued by this thread have completed once `done` fires
             mma_commit(&sm.done);
@@ -251,183 +262,173 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // ---------------- epilogue ----------------
-        const int quarter = warp & 3, chunk = warp >> 2;
-        // thr[j] starts at the warm-start bound (an upper bound on the query's
-        // 32nd best value) and never rises above it while the list fills
-        float thr[16];
-        int qc[16];  // pending queue lengths (warp-uniform)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int q = qbase + chunk * 16 + j;
-            thr[j] = (thr0 && q < Q) ? thr0[q] : INFINITY;
-            qc[j] = 0;
-            sm.lst_d[warp][j][lane] = INFINITY;
-            sm.lst_i[warp][j][lane] = -1;
-            if (quarter == 0 && lane == 0) sm.cap[chunk * 16 + j] = thr[j];
+        const int row0 = warp * 32, row = row0 + lane;
+        const int q = blockIdx.x * kQM + row;
+        float thr = q < Q ? (thr0 ? thr0[q] : INFINITY) : -INFINITY;
+        for (int k = 0; k < kTopK; ++k) {
+            sm.lv[row * kListStride + k] = thr;
+            sm.li[row * kListStride + k] = kNoWindow;
         }
         __syncwarp();
-        const unsigned lt_mask = (1u << lane) - 1u;
-        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        const int nsuper = (ntiles + kTcSub - 1) / kTcSub;
-        for (int u = 0; u < nsuper; ++u) {
-            const int b = u & 1;
-            const bool ok = mbar_wait_or_abort(&sm.acc_full[b], (uint32_t)((u >> 1) & 1), status, abort_flag);
+        int cnt = 0;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int i = 0; i < nt; ++i) {
+            const int a = i % kAcc;
+            const bool ok = mbar_wait_or_abort(&sm.acc_full[a], (uint32_t)((i / kAcc) & 1), status, abort_flag);
             if (!__all_sync(kFull, ok)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            for (int sub = 0; sub < kTcSub; ++sub) {
-                const int t = u * kTcSub + sub;
-                if (t >= ntiles) break;
-                float v[16];
-                tmem_ld16(tmem + lane_addr + (uint32_t)(b * kTcStageCols + sub * kTcN + chunk * 16), v);
-                bool any = false;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) any |= v[j] < thr[j];
-                if (__any_sync(kFull, any)) {
-                    const int nb = t * kTcM + quarter * 32;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        unsigned fl = __ballot_sync(kFull, v[j] < thr[j]);
-                        if (fl) {
-                            int c = __popc(fl);
-                            if (qc[j] + c > kTcQueue) {  // make room: merge the queue first
-                                thr[j] = flush_queue(&sm.lst_d[warp][j][0], &sm.lst_i[warp][j][0], &sm.que_d[warp][j][0],
-                                                     &sm.que_i[warp][j][0], qc[j], sm.cap[chunk * 16 + j], thr[j],
-                                                     lane);
-                                qc[j] = 0;
-                                fl = __ballot_sync(kFull, v[j] < thr[j]);
-                                c = __popc(fl);
-                            }
-                            if (c > kTcQueue) {
-                                thr[j] = merge_lanes(&sm.lst_d[warp][j][0], &sm.lst_i[warp][j][0],
-                                                     sm.cap[chunk * 16 + j], thr[j], v[j], nb + lane, fl, lane);
-                            } else if (c) {
-                                if ((fl >> lane) & 1u) {
-                                    const int pos = qc[j] + __popc(fl & lt_mask);
-                                    sm.que_d[warp][j][pos] = v[j];
-                                    sm.que_i[warp][j][pos] = nb + lane;
-                                }
-                                qc[j] += c;
-                            }
-                        }
-                    }
-                }
-            }
+            const int nb = (t_begin + i) * kTN;
+            float v[128];
+            tmem_ld128(lane_addr + (uint32_t)(a * kTN), v);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
+            if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
+            scan64<0>(v, nb, thr, cnt, sm, row0, lane);
+            scan64<64>(v, nb + 64, thr, cnt, sm, row0, lane);
         }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (qc[j])
-                thr[j] = flush_queue(&sm.lst_d[warp][j][0], &sm.lst_i[warp][j][0], &sm.que_d[warp][j][0],
-                                     &sm.que_i[warp][j][0], qc[j], sm.cap[chunk * 16 + j], thr[j], lane);
-        // merge the four quarters' partial lists (all in shared memory)
-        __syncthreads();  // (1) every quarter's lists are final
-        if (quarter == 0 && !*abort_flag) {
-            for (int j = 0; j < 16; ++j) {
-                const int qq = chunk * 16 + j;
-                float t = fminf(sm.cap[qq], sm.lst_d[warp][j][31]);
-                for (int o = 1; o < 4; ++o)
-                    t = merge_smem(&sm.lst_d[warp][j][0], &sm.lst_i[warp][j][0], sm.cap[qq], t,
-                                   &sm.lst_d[warp + o][j][0], &sm.lst_i[warp + o][j][0], lane);
-                const int q = qbase + qq;
-                if (q < Q) {
-                    cand_idx[(size_t)q * kTopK + lane] = sm.lst_i[warp][j][lane];
-                    cand_lb[(size_t)q * kTopK + lane] = sm.lst_d[warp][j][lane] + qnorm[q];
+        thr = flush_queues(sm.lv, sm.li, sm.qv, sm.qi, cnt, thr, 1, row0, lane);
+        if (!*abort_flag) {
+            for (int r = 0; r < 32; ++r) {
+                const int rr = row0 + r;
+                const int qq = blockIdx.x * kQM + rr;
+                if (qq >= Q) break;
+                const float v0 = sm.lv[rr * kListStride + lane];
+                const int i0 = sm.li[rr * kListStride + lane];
+                if (nparts == 1) {
+                    const bool real = i0 != kNoWindow;
+                    cand_idx[(size_t)qq * kTopK + lane] = real ? i0 : -1;
+                    cand_lb[(size_t)qq * kTopK + lane] = real ? v0 + qnorm[qq] : INFINITY;
+                } else {
+                    const size_t o = ((size_t)qq * nparts + part) * kTopK + lane;
+                    part_v[o] = v0;
+                    part_i[o] = i0;
                 }
             }
         }
-        __syncthreads();  // (2)
-    }
-    if (warp >= kTcEpiWarps) {
-        __syncthreads();  // (1)
-        __syncthreads();  // (2)
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kTcEpiWarps + 1) {
+    if (warp == kEpiWarps + 1) {
         __syncwarp();
-        tmem_dealloc(tmem, kTcCols);
+        tmem_dealloc(tmem, kAcc * kTN);
     }
 }
 
-// Warm start: the previous search's 32 windows of each query, scored in FP32
-// for the new query vector.  Their largest p (plus a rounding margin of the
-// BF16 search) is an upper bound on the query's 32nd best p, so the search
-// only has to insert windows below it.  One warp per query.
-__global__ void k_warm_threshold(const int *__restrict__ prev_idx, const float *__restrict__ qcoord,
-                                 const float *__restrict__ qnorm, const __nv_bfloat16 *__restrict__ etile,
-                                 const float *__restrict__ umax, int Q, int d, int da, int K, int N,
-                                 float eps_scale, float *__restrict__ thr0) {
+// One warp per query: merges the sorted part lists into the final candidate list.
+__global__ void k_merge_parts(const float *__restrict__ part_v, const int *__restrict__ part_i, int Q, int nparts,
+                              const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                              float *__restrict__ cand_lb) {
+    const int lane = threadIdx.x & 31;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    const size_t base = (size_t)q * nparts * kTopK;
+    float v = part_v[base + lane];
+    int i = part_i[base + lane];
+    for (int p = 1; p < nparts; ++p) {
+        const float w = part_v[base + (size_t)p * kTopK + lane];
+        const int j = part_i[base + (size_t)p * kTopK + lane];
+        if (__any_sync(kFull, lex_less(w, j, __shfl_sync(kFull, v, 31), __shfl_sync(kFull, i, 31))))
+            warp_merge32(v, i, w, j, lane);
+    }
+    const bool real = i != kNoWindow;
+    cand_idx[(size_t)q * kTopK + lane] = real ? i : -1;
+    cand_lb[(size_t)q * kTopK + lane] = real ? v + qnorm[q] : INFINITY;
+}
+
+// Query vectors as FP16 MMA operand tiles: rows = queries, K = (y, r, 1, 1, 1, 0...); rows past Q
+// are zero.  One tile of 128 queries is contiguous.
+__global__ void k_pack_queries(const float *__restrict__ qcoord, int Q, int d, int da, int K, int nblocks,
+                               __half *__restrict__ out) {
+    const long total = (long)nblocks * kQM * K;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / (kQM * K));
+        const int rem = (int)(i - (long)b * kQM * K);
+        const int r = rem / K, k = rem - r * K;
+        const int q = b * kQM + r;
+        float v = 0.0f;
+        if (q < Q) {
+            if (k <= d)
+                v = qcoord[(size_t)q * da + k];
+            else if (k <= d + 3)
+                v = 1.0f;
+        }
+        *reinterpret_cast<__half *>(reinterpret_cast<unsigned char *>(out + (size_t)b * kQM * K) +
+                                    core_offset(r, k, kQM)) = __float2half_rn(v);
+    }
+}
+
+// Exemplar vectors as FP16 MMA operand tiles: rows = windows, K = (-2 y, -2 r, norm hi/mid/lo,
+// 0...).  Padding windows carry +inf in the hi slot, so their score is +inf.
+__global__ void k_pack_exemplar(const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int d,
+                                int da, int K, __half *__restrict__ out) {
+    const long total = (long)ntiles * kTN * K;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(i / (kTN * K));
+        const int rem = (int)(i - (long)t * kTN * K);
+        const int m = rem / K, k = rem - m * K;
+        const float nrm = enorm[(size_t)t * kTN + m];
+        float v = 0.0f;
+        if (k <= d) {
+            v = isinf(nrm) ? 0.0f : et[((size_t)t * da + k) * kTN + m];
+        } else if (k <= d + 3) {
+            if (isinf(nrm)) {
+                v = (k == d + 1) ? nrm : 0.0f;
+            } else {
+                const float hi = __half2float(__float2half_rn(nrm));
+                const float r1 = nrm - hi;
+                const float mid = __half2float(__float2half_rn(r1));
+                v = (k == d + 1) ? hi : (k == d + 2) ? mid : (r1 - mid);
+            }
+        }
+        *reinterpret_cast<__half *>(reinterpret_cast<unsigned char *>(out + (size_t)t * kTN * K) +
+                                    core_offset(m, k, kTN)) = __float2half_rn(v);
+    }
+}
+
+// Warm start: the previous search's 32 windows of each query, scored in FP32 from the same FP16
+// operands the tensor cores multiply.  Their largest score plus a margin for a different
+// summation order is an upper bound on the query's 32nd best score.  One warp per query.
+__global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half *__restrict__ qtile,
+                                 const float *__restrict__ qnorm, const __half *__restrict__ etile,
+                                 const float *__restrict__ umax, int Q, int K, int N, float eps_scale,
+                                 float *__restrict__ thr0) {
     const int lane = threadIdx.x & 31;
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= Q) return;
     const int n = prev_idx[(size_t)q * kTopK + lane];
     float p = INFINITY;
     if (n >= 0 && n < N) {
-        // the same BF16 operands the tensor-core search multiplies
-        const unsigned char *e = reinterpret_cast<const unsigned char *>(etile + (size_t)(n / kTcM) * kTcM * K);
-        const int m = n % kTcM;
+        const unsigned char *e = reinterpret_cast<const unsigned char *>(etile + (size_t)(n / kTN) * kTN * K);
+        const unsigned char *a = reinterpret_cast<const unsigned char *>(qtile + (size_t)(q / kQM) * kQM * K);
+        const int m = n % kTN, r = q % kQM;
         p = 0.0f;
-        for (int k = 0; k <= d + 3; ++k) {
-            const float a = k <= d ? __bfloat162float(__float2bfloat16_rn(qcoord[(size_t)q * da + k])) : 1.0f;
-            p = fmaf(a, __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(e + core_offset(m, k, kTcM))), p);
-        }
+        for (int k = 0; k < K; ++k)
+            p = fmaf(__half2float(*reinterpret_cast<const __half *>(a + core_offset(r, k, kQM))),
+                     __half2float(*reinterpret_cast<const __half *>(e + core_offset(m, k, kTN))), p);
     }
-    float m = p;
+    float mx = p;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-    if (lane == 0) thr0[q] = m + eps_scale * (qnorm[q] + *umax);
-}
-
-// BF16 exemplar tiles in the MMA operand layout: rows = windows, K = (-2 y, -2 r, norm hi/mid/lo, 0...)
-__global__ void k_pack_exemplar_bf16(const float *__restrict__ et, const float *__restrict__ enorm, int ntiles,
-                                     int d, int da, int K, __nv_bfloat16 *__restrict__ out) {
-    const long total = (long)ntiles * kTcM * K;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const int t = (int)(i / (kTcM * K));
-        const int rem = (int)(i - (long)t * kTcM * K);
-        const int m = rem / K, k = rem - m * K;
-        const float nrm = enorm[(size_t)t * kTcM + m];
-        float v = 0.0f;
-        if (k <= d) {
-            v = et[((size_t)t * da + k) * kTcM + m];
-        } else if (k <= d + 3) {
-            const float hi = __bfloat162float(__float2bfloat16_rn(nrm));
-            if (k == d + 1) {
-                v = nrm;  // rounds to hi below
-            } else if (isinf(nrm)) {
-                v = 0.0f;
-            } else {
-                const float r1 = nrm - hi;
-                const float mid = __bfloat162float(__float2bfloat16_rn(r1));
-                v = (k == d + 2) ? r1 : (r1 - mid);
-            }
-        }
-        *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(out + (size_t)t * kTcM * K) +
-                                           core_offset(m, k, kTcM)) = __float2bfloat16_rn(v);
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    // |error| of an FP32 sum of K exact products <= K 2^-24 sum|terms|, sum|terms| <= qnorm + 2 umax
+    if (lane == 0) thr0[q] = mx + eps_scale * (qnorm[q] + 2.0f * *umax);
 }
 
 // --- self-test: one 128 x N x K tile through the same descriptors, written back row-major ---
-__global__ void __launch_bounds__(128) k_tc_selftest(const __nv_bfloat16 *__restrict__ A,
-                                                     const __nv_bfloat16 *__restrict__ B, int N, int K,
-                                                     float *__restrict__ D, int *__restrict__ status) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, const T *__restrict__ B, int N, int K,
+                                                     uint32_t idesc, float *__restrict__ D, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     unsigned char *sa = sm_raw;
-    unsigned char *sb = sm_raw + kTcM * K * 2;
+    unsigned char *sb = sm_raw + kQM * K * 2;
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5;
-    for (int i = tid; i < kTcM * K; i += 128)
-        *reinterpret_cast<__nv_bfloat16 *>(sa + core_offset(i / K, i % K, kTcM)) = A[i];
-    for (int i = tid; i < N * K; i += 128)
-        *reinterpret_cast<__nv_bfloat16 *>(sb + core_offset(i / K, i % K, N)) = B[i];
+    for (int i = tid; i < kQM * K; i += 128) *reinterpret_cast<T *>(sa + core_offset(i / K, i % K, kQM)) = A[i];
+    for (int i = tid; i < N * K; i += 128) *reinterpret_cast<T *>(sb + core_offset(i / K, i % K, N)) = B[i];
     fence_proxy_async_smem();
     if (warp == 0) {
         tmem_alloc(&tbase, 256);
@@ -442,10 +443,10 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const __nv_bfloat16 *__rest
     tc_fence_after();
     const uint32_t tmem = tbase;
     if (tid == 0) {
-        const uint32_t lbo_a = (uint32_t)(kTcM / 8) * 128u, lbo_b = (uint32_t)(N / 8) * 128u;
+        const uint32_t lbo_a = (uint32_t)(kQM / 8) * 128u, lbo_b = (uint32_t)(N / 8) * 128u;
         for (int ks = 0; ks < K / 16; ++ks)
             mma_bf16(tmem, smem_desc(smem_u32(sa) + ks * 2u * lbo_a, lbo_a, 128u),
-                     smem_desc(smem_u32(sb) + ks * 2u * lbo_b, lbo_b, 128u), idesc_bf16(kTcM, N), ks > 0 ? 1u : 0u);
+                     smem_desc(smem_u32(sb) + ks * 2u * lbo_b, lbo_b, 128u), idesc, ks > 0 ? 1u : 0u);
         mma_commit(&bar);
     }
     __syncwarp();
@@ -464,26 +465,109 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const __nv_bfloat16 *__rest
     if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
+template <typename T>
+pts_status run_selftest(int N, int K, uint32_t idesc, double *max_abs_err, double *max_abs_ref) {
+    std::vector<T> hA((size_t)kQM * K), hB((size_t)N * K);
+    std::vector<float> fA(hA.size()), fB(hB.size());
+    uint64_t z = 0x1234567ull;
+    auto nextf = [&]() {
+        z = z * 6364136223846793005ull + 1442695040888963407ull;
+        return (float)((z >> 40) & 0xFFFF) / 32768.0f - 1.0f;
+    };
+    auto cvt = [](float x) -> T {
+        if constexpr (std::is_same<T, __half>::value)
+            return __float2half_rn(x);
+        else
+            return __float2bfloat16_rn(x);
+    };
+    auto back = [](T x) -> float {
+        if constexpr (std::is_same<T, __half>::value)
+            return __half2float(x);
+        else
+            return __bfloat162float(x);
+    };
+    for (size_t i = 0; i < hA.size(); ++i) {
+        hA[i] = cvt(nextf());
+        fA[i] = back(hA[i]);
+    }
+    for (size_t i = 0; i < hB.size(); ++i) {
+        hB[i] = cvt(nextf());
+        fB[i] = back(hB[i]);
+    }
+    DevBuf<T> dA, dB;
+    DevBuf<float> dD;
+    DevBuf<int> dst;
+    PTS_TRY(dA.ensure(hA.size(), "selftest A"));
+    PTS_TRY(dB.ensure(hB.size(), "selftest B"));
+    PTS_TRY(dD.ensure((size_t)kQM * N, "selftest D"));
+    PTS_TRY(dst.ensure(1, "selftest status"));
+    PTS_CUDA_TRY(cudaMemcpy(dA.ptr, hA.data(), hA.size() * 2, cudaMemcpyHostToDevice));
+    PTS_CUDA_TRY(cudaMemcpy(dB.ptr, hB.data(), hB.size() * 2, cudaMemcpyHostToDevice));
+    PTS_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
+    const size_t smem = (size_t)(kQM + N) * K * 2;
+    cudaFuncSetAttribute(k_tc_selftest<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launches(1);
+    k_tc_selftest<T><<<1, 128, smem>>>(dA.ptr, dB.ptr, N, K, idesc, dD.ptr, dst.ptr);
+    PTS_CUDA_TRY(cudaGetLastError());
+    PTS_CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<float> hD((size_t)kQM * N);
+    int hst = 0;
+    PTS_CUDA_TRY(cudaMemcpy(hD.data(), dD.ptr, hD.size() * 4, cudaMemcpyDeviceToHost));
+    PTS_CUDA_TRY(cudaMemcpy(&hst, dst.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    double err = 0.0, ref_max = 0.0;
+    for (int i = 0; i < kQM; ++i)
+        for (int j = 0; j < N; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += (double)fA[(size_t)i * K + k] * fB[(size_t)j * K + k];
+            err = std::max(err, std::fabs(s - hD[(size_t)i * N + j]));
+            ref_max = std::max(ref_max, std::fabs(s));
+        }
+    *max_abs_err = err;
+    *max_abs_ref = ref_max;
+    if (hst) return set_error(PTS_ERR_TIMEOUT, "pts_tc_selftest: MMA completion wait gave up");
+    return PTS_OK;
+}
+
 }  // namespace
 
 int tc_padded_k(int d) { return ((d + 4) + 15) / 16 * 16; }
 
-void launch_warm_threshold(const int *prev_idx, const float *qcoord, const float *qnorm,
-                           const __nv_bfloat16 *etile, const float *umax, int Q, int d, int da, int K, int N,
-                           float eps_scale, float *thr0, cudaStream_t st) {
-    count_launches(1);
-    k_warm_threshold<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qcoord, qnorm, etile, umax, Q, d, da,
-                                                                   K, N, eps_scale, thr0);
+int tc_query_blocks(int Q) { return (Q + kQM - 1) / kQM; }
+
+// Parts per query block.  Each part keeps its own 32 best per query, and a running top-32 over
+// n windows inserts about 32 (1 + ln(n / 32)) of them, so splitting the exemplar multiplies the
+// insertion work; it only pays when the query blocks alone leave most SMs idle.
+int tc_parts(int Q, int ntiles) {
+    const int nqb = tc_query_blocks(Q);
+    int p = 1;
+    while (nqb * (p + 1) <= 152 && ntiles / (p + 1) >= 32) ++p;
+    return p;
 }
 
-void launch_pack_exemplar_bf16(const float *et, const float *enorm, int ntiles, int d, int da, int K,
-                               __nv_bfloat16 *out, cudaStream_t st) {
+void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st) {
+    const int nb = tc_query_blocks(Q);
+    if (nb == 0) return;
     count_launches(1);
-    k_pack_exemplar_bf16<<<152 * 4, 256, 0, st>>>(et, enorm, ntiles, d, da, K, out);
+    k_pack_queries<<<std::min<long>(ceil_div((long)nb * kQM * K, 256), 152 * 8), 256, 0, st>>>(qcoord, Q, d, da, K,
+                                                                                               nb, qtile);
 }
 
-void launch_search_tc(const float *qcoord, const float *qnorm, int Q, int d, int da, int K,
-                      const __nv_bfloat16 *etile, int ntiles, const float *thr0, int *cand_idx, float *cand_lb,
+void launch_pack_exemplar(const float *et, const float *enorm, int ntiles, int d, int da, int K, __half *out,
+                          cudaStream_t st) {
+    count_launches(1);
+    k_pack_exemplar<<<152 * 4, 256, 0, st>>>(et, enorm, ntiles, d, da, K, out);
+}
+
+void launch_warm_threshold(const int *prev_idx, const __half *qtile, const float *qnorm, const __half *etile,
+                           const float *umax, int Q, int K, int N, float eps_scale, float *thr0, cudaStream_t st) {
+    if (Q == 0) return;
+    count_launches(1);
+    k_warm_threshold<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qtile, qnorm, etile, umax, Q, K, N,
+                                                                   eps_scale, thr0);
+}
+
+void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
+                      int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st) {
     static bool attr = false;
     const size_t smem = sizeof(TcSmem) + 1024;
@@ -491,67 +575,23 @@ void launch_search_tc(const float *qcoord, const float *qnorm, int Q, int d, int
         cudaFuncSetAttribute(k_search_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    const int grid = ceil_div(Q, kTcN);
-    if (grid == 0) return;
-    ProfScope ps(kProfSearchTc, st, 1);
-    k_search_tc<<<grid, kTcThreads, smem, st>>>(qcoord, qnorm, Q, d, da, K, etile, ntiles, thr0, cand_idx,
-                                                cand_lb, status);
+    const int nqb = tc_query_blocks(Q);
+    if (nqb == 0) return;
+    const int tpp = (ntiles + nparts - 1) / nparts;
+    const int nstages = std::min(kMaxStages, kRing / (kTN * K * 2));
+    ProfScope ps(kProfSearchTc, st, nparts > 1 ? 2 : 1);
+    k_search_tc<<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages, thr0,
+                                                           cand_idx, cand_lb, part_v, part_i, status);
+    if (nparts > 1)
+        k_merge_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, Q, nparts, qnorm, cand_idx,
+                                                                   cand_lb);
 }
 
-pts_status tc_selftest(int N, int K, double *max_abs_err, double *max_abs_ref) {
+pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref) {
     if (N < 16 || N > 256 || N % 16 || K < 16 || K > 128 || K % 16)
         return set_error(PTS_ERR_INVALID_ARG, "pts_tc_selftest: N in 16..256 and K in 16..128, multiples of 16");
-    std::vector<__nv_bfloat16> hA((size_t)kTcM * K), hB((size_t)N * K);
-    std::vector<float> fA(hA.size()), fB(hB.size());
-    uint64_t z = 0x1234567ull;
-    auto nextf = [&]() {
-        z = z * 6364136223846793005ull + 1442695040888963407ull;
-        return (float)((z >> 40) & 0xFFFF) / 32768.0f - 1.0f;
-    };
-    for (size_t i = 0; i < hA.size(); ++i) {
-        hA[i] = __float2bfloat16_rn(nextf());
-        fA[i] = __bfloat162float(hA[i]);
-    }
-    for (size_t i = 0; i < hB.size(); ++i) {
-        hB[i] = __float2bfloat16_rn(nextf());
-        fB[i] = __bfloat162float(hB[i]);
-    }
-    DevBuf<__nv_bfloat16> dA, dB;
-    DevBuf<float> dD;
-    DevBuf<int> dst;
-    PTS_TRY(dA.ensure(hA.size(), "selftest A"));
-    PTS_TRY(dB.ensure(hB.size(), "selftest B"));
-    PTS_TRY(dD.ensure((size_t)kTcM * N, "selftest D"));
-    PTS_TRY(dst.ensure(1, "selftest status"));
-    PTS_CUDA_TRY(cudaMemcpy(dA.ptr, hA.data(), hA.size() * 2, cudaMemcpyHostToDevice));
-    PTS_CUDA_TRY(cudaMemcpy(dB.ptr, hB.data(), hB.size() * 2, cudaMemcpyHostToDevice));
-    PTS_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
-    const size_t smem = (size_t)(kTcM + N) * K * 2;
-    cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    count_launches(1);
-    k_tc_selftest<<<1, 128, smem>>>(dA.ptr, dB.ptr, N, K, dD.ptr, dst.ptr);
-    PTS_CUDA_TRY(cudaGetLastError());
-    PTS_CUDA_TRY(cudaDeviceSynchronize());
-    std::vector<float> hD((size_t)kTcM * N);
-    int hst = 0;
-    PTS_CUDA_TRY(cudaMemcpy(hD.data(), dD.ptr, hD.size() * 4, cudaMemcpyDeviceToHost));
-    PTS_CUDA_TRY(cudaMemcpy(&hst, dst.ptr, sizeof(int), cudaMemcpyDeviceToHost));
-    double err = 0.0, ref_max = 0.0;
-    for (int i = 0; i < kTcM; ++i)
-        for (int j = 0; j < N; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < K; ++k) s += (double)fA[(size_t)i * K + k] * fB[(size_t)j * K + k];
-            err = std::max(err, std::fabs(s - hD[(size_t)i * N + j]));
-            ref_max = std::max(ref_max, std::fabs(s));
-        }
-    dA.release();
-    dB.release();
-    dD.release();
-    dst.release();
-    *max_abs_err = err;
-    *max_abs_ref = ref_max;
-    if (hst) return set_error(PTS_ERR_TIMEOUT, "pts_tc_selftest: MMA completion wait gave up");
-    return PTS_OK;
+    if (f16) return run_selftest<__half>(N, K, idesc_f16(kQM, N), max_abs_err, max_abs_ref);
+    return run_selftest<__nv_bfloat16>(N, K, idesc_bf16(kQM, N), max_abs_err, max_abs_ref);
 }
 
 }  // namespace pts

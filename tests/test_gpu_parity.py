@@ -57,7 +57,9 @@ def _projector_dist(B1, B2):
     return np.linalg.norm(B1.T @ B1 - B2.T @ B2)
 
 
-@pytest.mark.parametrize("size,w,d", [(64, 8, 24), (48, 16, 64), (40, 4, 12), (12, 8, 8)])
+# d = 92 and 128: the component counts of the tensor-core search (Rayleigh-Ritz beyond 112)
+@pytest.mark.parametrize("size,w,d", [(64, 8, 24), (48, 16, 64), (40, 4, 12), (12, 8, 8), (64, 8, 92),
+                                      (48, 16, 128)])
 def test_pca_fit(size, w, d):
     Z = P.synthetic_exemplar(1, size, 3.0)
     mu_o, B_o, ev_o, _ = oracle.pca_fit(Z, w, d)
@@ -74,12 +76,13 @@ def test_pca_fit(size, w, d):
     np.testing.assert_allclose(Bg @ Bg.T, np.eye(d), atol=1e-5)
 
 
-def test_pca_large_window_gram_branch():
+@pytest.mark.parametrize("d", [64, 92])
+def test_pca_large_window_gram_branch(d):
     """w = 32 (D = 3072) on a 64x64 exemplar: N = 1089 < D."""
     Z = oracle.exemplar_pyramid(P.synthetic_exemplar(0, 256, 4.0), 3)[0].astype(np.float32)
-    mu_o, B_o, ev_o, _ = oracle.pca_fit(Z, 32, 64)
-    mean, basis, eig, k = pts.pca_fit(_t(Z), 32, 64)
-    np.testing.assert_allclose(eig.cpu().numpy(), ev_o[:64], rtol=1e-9)
+    mu_o, B_o, ev_o, _ = oracle.pca_fit(Z, 32, d)
+    mean, basis, eig, k = pts.pca_fit(_t(Z), 32, d)
+    np.testing.assert_allclose(eig.cpu().numpy(), ev_o[:d], rtol=1e-9)
     assert _projector_dist(basis.cpu().numpy(), B_o) < 1e-5
 
 
@@ -271,4 +274,4 @@ def test_invalid_arguments(c1):
     with pytest.raises(pts.PtsError):
         pts.ExemplarIndex(_t(Z[:6, :6]), 8)
     with pytest.raises(pts.PtsError):
-        pts.pca_fit(_t(Z), 8, 65)
+        pts.pca_fit(_t(Z), 8, 129)

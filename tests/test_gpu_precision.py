@@ -1,10 +1,11 @@
 """Precision modes of the search phase (tensor cores) against the FP64 oracle.
 
-BF16 mode: PCA-space distances from a tcgen05 BF16 GEMM (FP32 accumulation),
+F16 mode: PCA-space lower bounds from a tcgen05 FP16 GEMM (FP32 accumulation),
 top-32, exact FP32 full-dimension re-rank.  It is not certified, so parity is
 stated as errors against the oracle's exact search: the returned window can
 never beat the exact minimum, its reported distance is the exact FP32
-full-dimension distance of that window, the index mismatch rate is bounded,
+full-dimension distance of that window, the index mismatch rate is bounded by
+what the same method misses in exact arithmetic plus a small FP16 allowance,
 and the end-to-end energy stays within 1.01x of exact mode.
 """
 import ctypes
@@ -30,13 +31,12 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
 
 
-@pytest.mark.parametrize("N,K", [(64, 80), (64, 32), (128, 64), (16, 16)])
-def test_tensor_core_operand_layout(N, K):
+@pytest.mark.parametrize("f16", [1, 0])
+@pytest.mark.parametrize("N,K", [(64, 80), (64, 32), (128, 64), (16, 16), (128, 128), (128, 96)])
+def test_tensor_core_operand_layout(N, K, f16):
     L = pts.lib()
-    L.pts_tc_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                  ctypes.POINTER(ctypes.c_double)]
     err, ref = ctypes.c_double(), ctypes.c_double()
-    assert L.pts_tc_selftest(N, K, ctypes.byref(err), ctypes.byref(ref)) == 0
+    assert L.pts_tc_selftest(N, K, f16, ctypes.byref(err), ctypes.byref(ref)) == 0
     assert ref.value > 1.0
     assert err.value <= 1e-5 * ref.value * K
 
@@ -62,28 +62,43 @@ def _ideal_pca_top32_mismatch(X, Z, w, d, nn_o):
     return float(np.mean(best != nn_o))
 
 
-@pytest.mark.parametrize("He,Ho,w,d", [(64, 128, 8, 24), (48, 64, 16, 64), (40, 60, 8, 64)])
-def test_bf16_search_against_oracle(He, Ho, w, d):
+@pytest.mark.parametrize("He,Ho,w,d,d_fast", [(64, 128, 8, 24, 0), (48, 64, 16, 64, 0), (40, 60, 8, 64, 0),
+                                              (64, 128, 8, 24, 60), (48, 64, 4, 16, 0)])
+def test_f16_search_against_oracle(He, Ho, w, d, d_fast):
     Z = P.synthetic_exemplar(0, He, 3.0)
-    idx = pts.ExemplarIndex(_t(Z), w, d=d)
+    idx = pts.ExemplarIndex(_t(Z), w, d=d, d_fast=d_fast)
     X = P.random_patch_init(Z, Ho, Ho, w, 5)
-    nn, d2 = pts.nn_search(idx, _t(X), 2, "bf16")
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "f16")
     nn_o, d2_o = oracle.nn_bruteforce(X, Z, w, 2)
     mism, worst = _check_not_better_than_exact(X, Z, w, nn.cpu().numpy(), d2.cpu().numpy().astype(np.float64),
                                                nn_o, d2_o)
-    ideal = _ideal_pca_top32_mismatch(X, Z, w, d, nn_o)
-    # BF16 rounding may cost a little on top of what the PCA top-32 itself misses
-    assert mism <= ideal + 0.02, (mism, ideal)
+    # the tensor-core search ranks by the index's d_fast leading components
+    ideal = _ideal_pca_top32_mismatch(X, Z, w, idx.info["d_fast"], nn_o)
+    # FP16 rounding may cost a little on top of what the PCA top-32 itself misses
+    assert mism <= ideal + 0.01, (mism, ideal)
     idx.close()
 
 
-def test_bf16_energy_within_1_01_of_exact():
+def test_f16_warm_start_and_parts_change_nothing():
+    """A second search of the same image starts from the first one's lists (warm bound);
+    the 512x512 fine level splits the exemplar tiles over several CTAs per query block.
+    Neither may change the 32 candidates, hence the result."""
+    Z = P.synthetic_exemplar(0, 256, 4.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=64)
+    X = _t(P.random_patch_init(Z, 512, 512, 8, 3))
+    nn1, d21 = pts.nn_search(idx, X, 2, "f16")
+    nn2, d22 = pts.nn_search(idx, X, 2, "f16")
+    assert torch.equal(nn1, nn2) and torch.equal(d21, d22)
+    idx.close()
+
+
+def test_f16_energy_within_1_01_of_exact():
     Z = P.synthetic_exemplar(0, 64, 3.0)
     idx = pts.ExemplarIndex(_t(Z), 8, d=24)
     X0 = P.random_patch_init(Z, 128, 128, 8, 6)
     xe, xb = _t(X0), _t(X0)
     Ee = pts.synthesize_level(idx, xe, 5, mode="exact")
-    Eb = pts.synthesize_level(idx, xb, 5, mode="bf16")
+    Eb = pts.synthesize_level(idx, xb, 5, mode="f16")
     # the final energy of both outputs, measured by the exact search
     nn, d2 = pts.nn_search(idx, xb, 2, "exact")
     Eb_exact = float(d2.double().sum())
@@ -91,11 +106,11 @@ def test_bf16_energy_within_1_01_of_exact():
     idx.close()
 
 
-def test_bf16_full_size_fine_level_sampled():
+def test_f16_full_size_fine_level_sampled():
     Z = P.synthetic_exemplar(0, 256, 4.0)
     idx = pts.ExemplarIndex(_t(Z), 8, d=64)
     X = P.random_patch_init(Z, 512, 512, 8, 0)
-    nn, d2 = pts.nn_search(idx, _t(X), 2, "bf16")
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "f16")
     Q = oracle.num_queries(512, 512, 8)
     sub = P.sample_indices(12, Q, 128)
     nn_o, d2_o = oracle.nn_bruteforce(X, Z, 8, 2, qlist=sub)
@@ -103,5 +118,5 @@ def test_bf16_full_size_fine_level_sampled():
     pd = oracle.pair_dist2(X, Z, 8, 2, sub, nn_g)
     np.testing.assert_allclose(d2_g, pd, rtol=1e-5, atol=1e-6)
     assert np.all(pd >= d2_o * (1 - 1e-12))
-    assert np.mean(nn_g != nn_o) < 0.05
+    assert np.mean(nn_g != nn_o) < 0.02
     idx.close()
