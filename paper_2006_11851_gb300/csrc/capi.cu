@@ -86,16 +86,22 @@ pts_status read_status(pts_index idx, cudaStream_t st) {
 
 // Exact search for the queries listed in ws.fail_list (count on the device): full-dimension
 // GEMM top-32, certified re-rank, direct scan for what is still uncertified.
-void exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail_count, unsigned int *fail2_count,
-                   unsigned int *brute_count, int32_t *nn_out, float *d2_out, cudaStream_t st) {
+pts_status exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail_count, unsigned int *fail2_count,
+                         unsigned int *brute_count, int32_t *nn_out, float *d2_out, cudaStream_t st) {
     Workspace &ws = idx->ws;
+    const int np = full_parts(ra.Q, idx->ntiles);
+    if (np > 1) {
+        PTS_TRY(ws.part_v.ensure((size_t)ra.Q * np * kTopK, "part lists"));
+        PTS_TRY(ws.part_i.ensure((size_t)ra.Q * np * kTopK, "part lists"));
+    }
     launch_search_full(ra.X, ra.Wo, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
                        ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr,
-                       ws.cand_lb.ptr, idx->status.ptr, st);
+                       ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, np, idx->status.ptr, st);
     launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out,
                   ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
     launch_brute_fallback(ra, ws.fail2_list.ptr, fail2_count, brute_count, ws.best64.ptr, idx->status.ptr, st);
     launch_resolve(ws.fail2_list.ptr, fail2_count, ws.best64.ptr, ra.Q, nn_out, d2_out, st);
+    return PTS_OK;
 }
 
 // the learned proposal: network -> 4 clusters -> probe -> re-rank -> exact fallback
@@ -125,7 +131,8 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
                   ws.fail_list.ptr, ws.counters.ptr + 3, ws.best64.ptr, idx->status.ptr, st);
     launch_fallback(nn_out, d2_out, Q, pr.assign.ptr, pr.median.ptr, pr.factor, idx->N, ws.fail_list.ptr,
                     ws.counters.ptr + 0, st);
-    exact_on_list(idx, ra, ws.counters.ptr + 0, ws.counters.ptr + 1, ws.counters.ptr + 2, nn_out, d2_out, st);
+    PTS_TRY(exact_on_list(idx, ra, ws.counters.ptr + 0, ws.counters.ptr + 1, ws.counters.ptr + 2, nn_out, d2_out,
+                          st));
     return PTS_OK;
 }
 
@@ -147,7 +154,7 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
                   d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
-    exact_on_list(idx, ra, fail_count, fail2_count, brute_count, nn_out, d2_out, st);
+    PTS_TRY(exact_on_list(idx, ra, fail_count, fail2_count, brute_count, nn_out, d2_out, st));
     return PTS_OK;
 }
 

@@ -4,11 +4,11 @@
 //   y = B^T (v - mu)         (d coordinates)
 //   ||u||^2 = ||v - mu||^2
 //   r = sqrt(max(0, ||u||^2 - ||y||^2))  (norm of the discarded part)
-// Windows are read straight from the HWC image, never materialised: a block
-// owns 32 consecutive windows of one window row; for each window row dy it
-// stages the shared pixel strip, the matching D/w slice of the basis and of mu
-// in shared memory, and 8 thread groups each accumulate d/8 coordinates of
-// all 32 windows (d <= 128).
+// A tiled SIMT GEMM (windows x D) (D x d): a block owns 64 windows and all d <= 128 outputs.
+// Windows are read straight from the HWC image, never materialised: per 32-element slice of
+// the window vector the block stages the 64 centred slices and the basis slice in shared memory
+// (per-window base offsets and per-element offsets are precomputed, so a staged element is one
+// gather), and each thread accumulates a 4-window x 8-coordinate register tile.
 //
 // layout 0 (queries):  coord[win][da]              = (y, r, 0, ...)
 //                      tau[win] = tau_scale * (||u||^2 + max_n ||u_n||^2)
@@ -21,75 +21,125 @@
 namespace pts {
 namespace {
 
-constexpr int kPW = 32;
+constexpr int kPWin = 64;           // windows per block
+constexpr int kPK = 32;             // window-vector elements per slice
+constexpr int kPD = kMaxDPca;       // coordinates per block (d <= 128)
+constexpr int kXs = kPWin + 1;      // row stride of the staged window slices
+constexpr int kBs = kPD + 4;        // row stride of the staged basis slice (16-byte rows)
+
+struct ProjSmem {
+    union {
+        struct {
+            float xs[kPK * kXs];              // [k][window], centred
+            alignas(16) float bs[kPK * kBs];  // [k][coordinate]
+        } st;
+        float ys[kPWin * (kPD + 1)];          // the finished tile, [window][coordinate]
+    } u;
+    long base[kPWin];               // image offset of each window's first element
+    int koff[kPK];                  // image offset of each element of the slice
+    float un[kPWin];
+};
 
 __global__ void __launch_bounds__(256)
-    k_project(const float *__restrict__ img, int W, int w, int stride, int qx_n,
+    k_project(const float *__restrict__ img, int W, int w, int stride, int qx_n, int Qn,
               const float *__restrict__ mu, const float *__restrict__ basis, int d, int da,
               int layout, float *__restrict__ out_coord, float *__restrict__ out_norm,
               float *__restrict__ out_tau, float tau_scale, const float *__restrict__ umax) {
-    extern __shared__ __align__(16) float smp[];
+    __shared__ ProjSmem sm;
+    float *const xs = sm.u.st.xs;
+    float *const bs = sm.u.st.bs;
+    float *const ys = sm.u.ys;
     const int row = 3 * w, D = row * w;
-    const int strip = ((kPW - 1) * stride + w) * 3;
-    float *s_strip = smp;
-    float *s_basis = s_strip + ((strip + 3) & ~3);
-    float *s_mu = s_basis + d * row;
-    float *s_y = s_mu + ((row + 3) & ~3);  // [kPW][d]
-
-    const int qy = blockIdx.y, qx0 = blockIdx.x * kPW;
-    const int tid = threadIdx.x, m = tid & 31, g = tid >> 5;
-    const int y0 = qy * stride, x0 = qx0 * stride;
-    float acc[kMaxDPca / 8];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long win0 = (long)blockIdx.x * kPWin;
+    if (tid < kPWin) {
+        const long win = win0 + tid;
+        const long wq = win < Qn ? win : 0;
+        const long qy = wq / qx_n, qx = wq - qy * qx_n;
+        sm.base[tid] = (qy * stride * (long)W + qx * stride) * 3;
+        sm.un[tid] = 0.0f;
+    }
+    float acc[4][8];
 #pragma unroll
-    for (int jj = 0; jj < kMaxDPca / 8; ++jj) acc[jj] = 0.0f;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
     float un = 0.0f;
-    const size_t img_row = (size_t)W * 3;
-    for (int dy = 0; dy < w; ++dy) {
-        const float *src = img + (size_t)(y0 + dy) * img_row + (size_t)x0 * 3;
-        const int avail = (W - x0) * 3;
-        for (int i = tid; i < strip; i += 256) s_strip[i] = (i < avail) ? __ldg(src + i) : 0.0f;
-        for (int i = tid; i < d * row; i += 256) {
-            const int j = i / row, e = i - j * row;
-            s_basis[i] = __ldg(basis + (size_t)j * D + dy * row + e);
+    for (int k0 = 0; k0 < D; k0 += kPK) {
+        if (tid < kPK) {
+            const int k = min(k0 + tid, D - 1);
+            const int dy = k / row, e = k - dy * row;
+            sm.koff[tid] = dy * W * 3 + e;
         }
-        for (int i = tid; i < row; i += 256) s_mu[i] = __ldg(mu + dy * row + i);
         __syncthreads();
-        const float *xs = s_strip + m * stride * 3;
-        for (int e = 0; e < row; ++e) {
-            const float a = xs[e] - s_mu[e];
-            un = fmaf(a, a, un);
+        // window slices: consecutive threads take consecutive elements of one window
 #pragma unroll
-            for (int jj = 0; jj < kMaxDPca / 8; ++jj) {
-                const int j = g + 8 * jj;
-                if (j < d) acc[jj] = fmaf(s_basis[j * row + e], a, acc[jj]);
+        for (int it = 0; it < kPWin * kPK / 256; ++it) {
+            const int idx = tid + 256 * it;
+            const int wl = idx / kPK, kk = idx - wl * kPK;
+            const int k = k0 + kk;
+            float v = 0.0f;
+            if (k < D && win0 + wl < Qn) v = __ldg(img + sm.base[wl] + sm.koff[kk]) - __ldg(mu + k);
+            xs[kk * kXs + wl] = v;
+        }
+        // basis slice: row j of the basis is contiguous in k
+        for (int idx = tid; idx < kPD * kPK; idx += 256) {
+            const int j = idx / kPK, kk = idx - j * kPK;
+            const int k = k0 + kk;
+            bs[kk * kBs + j] = (j < d && k < D) ? __ldg(basis + (size_t)j * D + k) : 0.0f;
+        }
+        __syncthreads();
+        if (tid < kPWin) {
+#pragma unroll 8
+            for (int kk = 0; kk < kPK; ++kk) {
+                const float a = xs[kk * kXs + tid];
+                un = fmaf(a, a, un);
             }
         }
+#pragma unroll 4
+        for (int kk = 0; kk < kPK; ++kk) {
+            float a[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = xs[kk * kXs + ty * 4 + i];
+            const float4 b0 = *reinterpret_cast<const float4 *>(&bs[kk * kBs + tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&bs[kk * kBs + tx * 8 + 4]);
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
         __syncthreads();
     }
+    // (the loop ends with a barrier, so the staging buffers may be overwritten)
 #pragma unroll
-    for (int jj = 0; jj < kMaxDPca / 8; ++jj) {
-        const int j = g + 8 * jj;
-        if (j < d) s_y[m * d + j] = acc[jj];
-    }
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ys[(ty * 4 + i) * (kPD + 1) + tx * 8 + j] = acc[i][j];
+    if (tid < kPWin) sm.un[tid] = un;
     __syncthreads();
-    if (g != 0 || qx0 + m >= qx_n) return;
-    const long win = (long)qy * qx_n + qx0 + m;
-    float yn = 0.0f;
-    for (int j = 0; j < d; ++j) yn = fmaf(s_y[m * d + j], s_y[m * d + j], yn);
-    const float r = sqrtf(fmaxf(un - yn, 0.0f));
-    out_norm[win] = un;
-    if (layout == 0) {
-        float *o = out_coord + win * da;
-        for (int j = 0; j < d; ++j) o[j] = s_y[m * d + j];
-        o[d] = r;
-        for (int j = d + 1; j < da; ++j) o[j] = 0.0f;
-        out_tau[win] = tau_scale * (un + *umax);
-    } else {
-        const long tile = win / kBN, col = win - tile * kBN;
-        float *o = out_coord + tile * (long)da * kBN + col;
-        for (int j = 0; j < d; ++j) o[(long)j * kBN] = -2.0f * s_y[m * d + j];
-        o[(long)d * kBN] = -2.0f * r;
-        for (int j = d + 1; j < da; ++j) o[(long)j * kBN] = 0.0f;
+    // one warp per window row of the tile: ||y||^2, r, and the coalesced writes
+    const int lane = tid & 31, wp = tid >> 5;
+    for (int wl = wp; wl < kPWin; wl += 8) {
+        const long win = win0 + wl;
+        if (win >= Qn) break;
+        const float *yr = &ys[wl * (kPD + 1)];
+        float yn = 0.0f;
+        for (int j = lane; j < d; j += 32) yn = fmaf(yr[j], yr[j], yn);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) yn += __shfl_xor_sync(0xffffffffu, yn, o);
+        const float u2 = sm.un[wl];
+        const float r = sqrtf(fmaxf(u2 - yn, 0.0f));
+        if (layout == 0) {
+            float *o = out_coord + win * da;
+            for (int j = lane; j < da; j += 32) o[j] = j < d ? yr[j] : (j == d ? r : 0.0f);
+            if (lane == 0) out_tau[win] = tau_scale * (u2 + *umax);
+        } else {
+            const long tile = win / kBN, col = win - tile * kBN;
+            float *o = out_coord + tile * (long)da * kBN + col;
+            for (int j = lane; j < da; j += 32) o[(long)j * kBN] = j < d ? -2.0f * yr[j] : (j == d ? -2.0f * r : 0.0f);
+        }
+        if (lane == 0) out_norm[win] = u2;
     }
 }
 
@@ -119,18 +169,11 @@ void launch_project(const float *img, int H, int W, int w, int stride, const flo
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
                     cudaStream_t st) {
     const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
-    const int row = 3 * w;
-    const int strip = ((kPW - 1) * stride + w) * 3;
-    const size_t smem = sizeof(float) * (((strip + 3) & ~3) + d * row + ((row + 3) & ~3) + kPW * d);
-    static size_t attr_set = 0;
-    if (smem > 48 * 1024 && smem > attr_set) {
-        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = smem;
-    }
-    dim3 grid(ceil_div(qx_n, kPW), qy_n);
+    const long Qn = (long)qy_n * qx_n;
+    if (Qn <= 0) return;
     ProfScope ps(kProfProject, st, 1);
-    k_project<<<grid, 256, smem, st>>>(img, W, w, stride, qx_n, mu, basis, d, da, layout, out_coord,
-                                       out_norm, out_tau, tau_scale, umax);
+    k_project<<<(unsigned)ceil_div(Qn, kPWin), 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basis, d, da,
+                                                            layout, out_coord, out_norm, out_tau, tau_scale, umax);
 }
 
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st) {

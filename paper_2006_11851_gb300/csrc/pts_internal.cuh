@@ -189,8 +189,9 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
 void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
-                        const float *qnorm, int *cand_idx, float *cand_lb, int *status,
-                        cudaStream_t st);
+                        const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
+                        int nparts, int *status, cudaStream_t st);
+int full_parts(int Q, int ntiles);
 void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st);
 // search_tc.cu

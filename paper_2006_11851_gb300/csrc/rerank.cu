@@ -102,6 +102,105 @@ __global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restr
     }
 }
 
+// k_rerank for a window width known at compile time: the query window is loaded into registers
+// once, and each candidate's rows are fully unrolled, two candidates at a time, so their loads are
+// in flight together.  Per lane the terms are summed in the order of window_dist2 (row by row,
+// element lane + 32p within a row) and reduced by the same butterfly: the distances are bitwise
+// those of k_rerank.  Evaluating the second candidate of a pair that k_rerank would have skipped
+// cannot change the minimum (its distance exceeds the best so far).
+template <int W>
+__global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__restrict__ qlist,
+                                                  const unsigned int *__restrict__ qcount,
+                                                  const int *__restrict__ cand_idx,
+                                                  const float *__restrict__ cand_lb,
+                                                  const float *__restrict__ tau, int certify,
+                                                  int *__restrict__ nn_out, float *__restrict__ d2_out,
+                                                  int *__restrict__ fail_list,
+                                                  unsigned int *__restrict__ fail_count,
+                                                  unsigned long long *__restrict__ best64,
+                                                  int *__restrict__ status) {
+    constexpr int R = 3 * W, PER = (R + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int q = wid;
+    if (qlist) {
+        if (wid >= (int)*qcount) return;
+        q = qlist[wid];
+    }
+    if (q < 0 || q >= a.Q) return;
+    const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
+    const float *xq = a.X + ((size_t)y0 * a.Wo + x0) * 3;
+    float xv[W][PER];
+#pragma unroll
+    for (int dy = 0; dy < W; ++dy)
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int e = lane + 32 * p;
+            xv[dy][p] = e < R ? __ldg(xq + (size_t)dy * a.Wo * 3 + e) : 0.0f;
+        }
+    const int my_idx = cand_idx[(size_t)q * kTopK + lane];
+    const float my_lb = cand_lb[(size_t)q * kTopK + lane];
+    const float tq = certify ? tau[q] : 0.0f;
+    float best = INFINITY;
+    int best_n = -1;
+    const size_t zrow = (size_t)a.We * 3;
+    for (int i = 0; i < kTopK; i += 2) {
+        int n0 = __shfl_sync(kFull, my_idx, i);
+        int n1 = __shfl_sync(kFull, my_idx, i + 1);
+        const float lb0 = __shfl_sync(kFull, my_lb, i);
+        if (n0 < 0) break;  // fewer than 32 windows exist
+        if (certify && lb0 - tq > best) break;  // bounds are ascending
+        if (n0 >= a.N) {
+            if (lane == 0) atomicOr(status, kDevErrBounds);
+            n0 = -1;
+        }
+        if (n1 >= a.N) {
+            if (lane == 0) atomicOr(status, kDevErrBounds);
+            n1 = -1;
+        }
+        const int m0 = n0 < 0 ? 0 : n0, m1 = n1 < 0 ? 0 : n1;
+        const int ey0 = m0 / a.ex, ey1 = m1 / a.ex;
+        const float *z0 = a.Z + ((size_t)ey0 * a.We + (m0 - ey0 * a.ex)) * 3;
+        const float *z1 = a.Z + ((size_t)ey1 * a.We + (m1 - ey1 * a.ex)) * 3;
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int dy = 0; dy < W; ++dy)
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int e = lane + 32 * p;
+                if (e < R) {
+                    const float t0 = xv[dy][p] - __ldg(z0 + dy * zrow + e);
+                    const float t1 = xv[dy][p] - __ldg(z1 + dy * zrow + e);
+                    s0 = fmaf(t0, t0, s0);
+                    s1 = fmaf(t1, t1, s1);
+                }
+            }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (n0 >= 0 && (s0 < best || (s0 == best && n0 < best_n))) {
+            best = s0;
+            best_n = n0;
+        }
+        if (n1 >= 0 && (s1 < best || (s1 == best && n1 < best_n))) {
+            best = s1;
+            best_n = n1;
+        }
+    }
+    const int last_idx = __shfl_sync(kFull, my_idx, kTopK - 1);
+    const float last_lb = __shfl_sync(kFull, my_lb, kTopK - 1);
+    const bool done = !certify || last_idx < 0 || best <= last_lb - tq;
+    if (lane == 0) {
+        if (done) {
+            nn_out[q] = best_n;
+            d2_out[q] = best;
+        } else {
+            const unsigned int slot = atomicAdd(fail_count, 1u);
+            fail_list[slot] = q;
+            best64[q] = pack_dist_idx(best, best_n);
+        }
+    }
+}
+
 // One CTA per listed query; each thread scores whole windows.
 __global__ void __launch_bounds__(256) k_brute(RerankArgs a, const int *__restrict__ fail_list,
                                                const unsigned int *__restrict__ fail_count,
@@ -171,8 +270,16 @@ void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qc
     if (a.Q == 0) return;
     const int grid = ceil_div((long)a.Q * 32, 256);
     ProfScope ps(kProfRerank, st, 1);
-    k_rerank<<<grid, 256, 0, st>>>(a, qlist, qcount, cand_idx, cand_lb, tau, certify, nn_out, d2_out,
-                                   fail_list, fail_count, best64, status);
+#define PTS_RERANK_ARGS a, qlist, qcount, cand_idx, cand_lb, tau, certify, nn_out, d2_out, fail_list, fail_count, \
+                        best64, status
+    switch (a.w) {
+        case 4: k_rerank_w<4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 8: k_rerank_w<8><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 16: k_rerank_w<16><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 32: k_rerank_w<32><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        default: k_rerank<<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+    }
+#undef PTS_RERANK_ARGS
 }
 
 void launch_brute_fallback(const RerankArgs &a, const int *fail_list,

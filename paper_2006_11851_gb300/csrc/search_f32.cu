@@ -25,6 +25,8 @@
 // ballots, so after the first tiles insertions are rare.
 #include <float.h>
 
+#include <algorithm>
+
 #include "pts_internal.cuh"
 
 namespace pts {
@@ -183,8 +185,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_search_full(const float *__restrict__ qfull,  // [F/64][D][64]: u_q of failing queries
                   const int *__restrict__ fail_list, const unsigned int *__restrict__ fail_count,
                   int Q, int Dp, const float *__restrict__ efull,  // [ntiles][Dp][128] = -2 u_n
-                  const float *__restrict__ enorm, int ntiles, const float *__restrict__ qnorm,
-                  int *__restrict__ cand_idx, float *__restrict__ cand_lb, int *__restrict__ status) {
+                  const float *__restrict__ enorm, int ntiles, int tiles_per_part,
+                  const float *__restrict__ qnorm, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
+                  float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FullSmem &sm = *reinterpret_cast<FullSmem *>(smem_raw);
     const int nf = static_cast<int>(*fail_count);
@@ -193,7 +196,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = warp * 8;
     const int nchunks = Dp / kKC;
-    const long total = (long)ntiles * nchunks;
+    // this CTA's exemplar tiles (blockIdx.y splits them; parts are merged afterwards)
+    const int t_begin = blockIdx.y * tiles_per_part;
+    const int nt = max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
+    const long total = (long)nt * nchunks;
     const float *qa = qfull + (size_t)blockIdx.x * Dp * kBQ;
     TopK8 top;
     top.init();
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int c = (int)(it - t * nchunks);
         mbar_expect_tx(&sm.bar[s], (uint32_t)(kKC * (kBQ + kBN) * 4));
         bulk_g2s(&sm.a[s][0][0], qa + (size_t)c * kKC * kBQ, kKC * kBQ * 4u, &sm.bar[s]);
-        bulk_g2s(&sm.e[s][0][0], efull + ((size_t)t * Dp + (size_t)c * kKC) * kBN, kKC * kBN * 4u,
+        bulk_g2s(&sm.e[s][0][0], efull + ((size_t)(t_begin + t) * Dp + (size_t)c * kKC) * kBN, kKC * kBN * 4u,
                  &sm.bar[s]);
     };
     if (tid == 0)
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const long t = it / nchunks;
         const int c = (int)(it - t * nchunks);
         if (c == 0) {
-            const float4 nv = __ldg(reinterpret_cast<const float4 *>(enorm + t * kBN + lane * 4));
+            const float4 nv = __ldg(reinterpret_cast<const float4 *>(enorm + (t_begin + t) * kBN + lane * 4));
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 acc[i][0] = nv.x;
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
-        if (c == nchunks - 1) top.offer(acc, (int)t * kBN, lane);
+        if (c == nchunks - 1) top.offer(acc, (int)(t_begin + t) * kBN, lane);
         __syncthreads();  // stage s is free
         if (tid == 0 && it + kStages < total) issue(it + kStages);
     }
@@ -260,6 +266,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int i = 0; i < 8; ++i) {
         const int f = fbase + row0 + i;
         if (f < nf) {
+            if (gridDim.y > 1) {
+                const size_t o = ((size_t)f * gridDim.y + blockIdx.y) * kTopK + lane;
+                part_v[o] = top.ld[i];
+                part_i[o] = top.li[i];
+                continue;
+            }
             const int q = fail_list[f];
             if (q >= 0 && q < Q) {
                 cand_idx[(size_t)q * kTopK + lane] = top.li[i];
@@ -268,6 +280,50 @@ __global__ void __launch_bounds__(kThreads, 2)
                 atomicOr(status, kDevErrBounds);
             }
         }
+    }
+}
+
+// (a, ia) < (b, ib) lexicographically; window -1 (no window) only ever pairs with +inf
+__device__ __forceinline__ bool lex_less_f(float a, int ia, float b, int ib) {
+    return (a < b) || (a == b && ia < ib);
+}
+
+// One warp per listed query: the 32 smallest (p, n) over the parts' sorted lists (the elementwise
+// minimum of a list and another reversed is bitonic; five stages sort it).
+__global__ void k_merge_fail_parts(const float *__restrict__ part_v, const int *__restrict__ part_i, int nparts,
+                                   const int *__restrict__ fail_list, const unsigned int *__restrict__ fail_count,
+                                   int Q, const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                   float *__restrict__ cand_lb, int *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= (int)*fail_count) return;
+    const size_t base = (size_t)f * nparts * kTopK;
+    float v = part_v[base + lane];
+    int i = part_i[base + lane];
+    for (int p = 1; p < nparts; ++p) {
+        const float w = __shfl_sync(kFull, part_v[base + (size_t)p * kTopK + lane], 31 - lane);
+        const int j = __shfl_sync(kFull, part_i[base + (size_t)p * kTopK + lane], 31 - lane);
+        if (lex_less_f(w, j, v, i)) {
+            v = w;
+            i = j;
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const float ov = __shfl_xor_sync(kFull, v, s);
+            const int oi = __shfl_xor_sync(kFull, i, s);
+            const bool take = ((lane & s) == 0) ? lex_less_f(ov, oi, v, i) : lex_less_f(v, i, ov, oi);
+            if (take) {
+                v = ov;
+                i = oi;
+            }
+        }
+    }
+    const int q = fail_list[f];
+    if (q >= 0 && q < Q) {
+        cand_idx[(size_t)q * kTopK + lane] = i;
+        cand_lb[(size_t)q * kTopK + lane] = v + qnorm[q];
+    } else if (lane == 0) {
+        atomicOr(status, kDevErrBounds);
     }
 }
 
@@ -328,8 +384,8 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
 void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
-                        const float *qnorm, int *cand_idx, float *cand_lb, int *status,
-                        cudaStream_t st) {
+                        const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
+                        int nparts, int *status, cudaStream_t st) {
     static bool attr = false;
     const size_t smem = sizeof(FullSmem);
     if (!attr) {
@@ -340,10 +396,22 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
     count_launches(1);
     k_gather_full<<<152 * 4, 256, 0, st>>>(X, Wo, w, stride, qx, mu, fail_list, fail_count, Q, Dp,
                                            qfull);
-    ProfScope ps(kProfSearchFull, st, 1);
-    k_search_full<<<ceil_div(Q, kBQ), kThreads, smem, st>>>(qfull, fail_list, fail_count, Q, Dp, efull,
-                                                            enorm, ntiles, qnorm, cand_idx, cand_lb,
-                                                            status);
+    const int tpp = ceil_div(ntiles, nparts);
+    const int np = ceil_div(ntiles, tpp);
+    ProfScope ps(kProfSearchFull, st, np > 1 ? 2 : 1);
+    k_search_full<<<dim3(ceil_div(Q, kBQ), np), kThreads, smem, st>>>(qfull, fail_list, fail_count, Q, Dp,
+                                                                      efull, enorm, ntiles, tpp, qnorm, cand_idx,
+                                                                      cand_lb, part_v, part_i, status);
+    if (np > 1)
+        k_merge_fail_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, fail_list, fail_count,
+                                                                        Q, qnorm, cand_idx, cand_lb, status);
+}
+
+// Exemplar parts of the full-dimension pass: enough CTAs for two per SM when the query blocks
+// alone leave SMs idle.
+int full_parts(int Q, int ntiles) {
+    const int nqb = ceil_div(Q, kBQ);
+    return std::max(1, std::min(ntiles, (2 * 152) / std::max(nqb, 1)));
 }
 
 void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,

@@ -12,19 +12,25 @@
 // copies of pre-packed tiles.  Four accumulator stages of 128 columns fill TMEM's 512.
 //
 // Warps (6): 0-3 epilogue (TMEM lane quarter = warp), 4 producer, 5 MMA issuer and TMEM owner.
-// An epilogue thread owns one query.  Per tile it loads its 128 accumulators (two 64-column
-// tcgen05.ld), takes their minimum and, only when that beats the query's threshold, appends the
-// windows below it to a per-thread queue in shared memory: a store, no dependent loads.  When a
-// queue fills, the warp merges it into the query's sorted 32-entry list cooperatively (bitonic
-// sort of the queue, bitonic merge with the list, one entry per lane), and the list's last entry
-// becomes the new threshold.  Lists and queues use odd row strides, so neither a warp's appends
-// (one slot, 32 threads) nor its merges (32 slots, one query) collide on banks.
+// Selection works on groups of 8 consecutive windows.  An epilogue thread owns one query and
+// keeps, in registers, the 16 groups with the smallest minimum score seen so far, sorted by
+// (minimum, group); the 8 scores of each kept group sit in a shared-memory slot that moves with
+// the group.  Per tile the thread loads its query's 128 accumulators (two 64-column tcgen05.ld),
+// reduces each group of 8 to its minimum and, only for a group whose minimum beats the 16th
+// kept one, shifts it into the register list and stores its 8 scores into the slot of the
+// evicted group.  Every window among the query's 16 best lies in one of its 16 best groups, and
+// the list is the exact 16 best groups whatever the scan order (ties go to the smaller group,
+// which comes first).  At the end each warp takes its queries one at a time, loads the 128 kept
+// scores (4 per lane) and keeps the 32 smallest (score, window) pairs by bitonic sort and merge.
+// Padding windows score NaN: a group minimum ignores them and they are dropped at the end.
 //
 // The exemplar tiles of a query block may be split across blockIdx.y; each part writes its
-// sorted 32 and k_merge_parts merges them.  An optional per-query bound thr0 (warm start) seeds
-// the lists with sentinels (thr0, INT_MAX): only windows strictly below it are kept, and at least
-// 32 windows are (the previous search's 32, re-scored, lie below thr0).  All waits are bounded;
-// on a timeout the kernel flags the status word, drains its copies and frees TMEM.
+// sorted 32 and k_merge_parts merges them.  An optional per-query bound thr0 (warm start, an
+// upper bound on the query's 16th best group minimum) seeds the group list with sentinels
+// (thr0, none): only groups whose minimum is below it are kept, and since at least 16 are, the
+// kept groups are the same 16 as without the bound.
+// All waits are bounded; on a timeout the kernel flags the status word, drains its copies and
+// frees TMEM.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -44,19 +50,18 @@ constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kMaxKt = 128;         // K of the search vectors
 constexpr int kRing = 96 * 1024;    // bytes of exemplar-tile ring
 constexpr int kMaxStages = 8;
-constexpr int kQueue = 32;          // queued candidates per query before a merge
-constexpr int kListStride = kTopK + 1;
-constexpr int kQueueStride = kQM + 1;
+constexpr int kG = 8;               // windows per group
+constexpr int kKeep = 16;           // groups kept per query
+constexpr int kPayStride = kKeep * kG + 4;  // floats per query row of kept scores (odd 16-byte units)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNoWindow = INT_MAX;
+constexpr int kNoGroup = 0x7FFFFFF;  // group field of a sentinel (27 bits)
 
 struct TcSmem {
     alignas(1024) unsigned char q[kQM * kMaxKt * 2];
     alignas(1024) unsigned char e[kRing];
-    float lv[kQM * kListStride];    // per query: sorted (value, window) list
-    int li[kQM * kListStride];
-    float qv[kQueue * kQueueStride];  // per query: pending candidates, slot-major
-    int qi[kQueue * kQueueStride];
+    alignas(16) float pay[kQM * kPayStride];  // per query, per slot: the 8 scores of a kept group
+    int gmap[kQM * (kKeep + 1)];               // per query, per slot: the group held (at the end)
     uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAcc], acc_empty[kAcc], q_full, done;
     uint32_t tmem_base;
     int abort_flag;
@@ -107,68 +112,50 @@ __device__ __forceinline__ void warp_merge32(float &v, int &i, float w, int j, i
     }
 }
 
-// Merges the queues of this warp's queries that hold at least min_cnt entries into their lists,
-// one query at a time with the whole warp (entry = lane).  Returns the calling lane's threshold
-// (its list's last value if its queue was merged, else thr); the caller clears those counts.
-__device__ __noinline__ float flush_queues(float *lv, int *li, const float *qv, const int *qi, int cnt, float thr,
-                                           int min_cnt, int row0, int lane) {
-    __syncwarp();  // the queues' appends are visible to the whole warp
-    unsigned todo = __ballot_sync(kFull, cnt >= min_cnt && cnt > 0);
-    while (todo) {
-        const int r = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int c = __shfl_sync(kFull, cnt, r);
-        const int row = row0 + r;
-        float v = lane < c ? qv[lane * kQueueStride + row] : INFINITY;
-        int i = lane < c ? qi[lane * kQueueStride + row] : kNoWindow;
-        warp_sort32(v, i, lane);
-        float l = lv[row * kListStride + lane];
-        int j = li[row * kListStride + lane];
-        warp_merge32(l, j, v, i, lane);
-        lv[row * kListStride + lane] = l;
-        li[row * kListStride + lane] = j;
-        const float t = __shfl_sync(kFull, l, 31);
-        if (lane == r) thr = t;
+// Sorted register list of the kept groups: value gv[k] (group minimum) and gs[k] = group << 4 |
+// slot, ascending in (value, group).
+struct GroupList {
+    float gv[kKeep];
+    int gs[kKeep];
+};
+
+// Shifts (x, group) into the list (the caller checked x < gv[kKeep - 1]), reusing the evicted
+// entry's slot, and returns that slot.  Groups arrive in increasing order, so a strict value test
+// places ties after the groups already kept.
+__device__ __forceinline__ int group_insert(GroupList &L, float x, int group) {
+    const int slot = L.gs[kKeep - 1] & 15;
+    const int packed = (group << 4) | slot;
+#pragma unroll
+    for (int k = kKeep - 1; k > 0; --k) {
+        const bool before_prev = x < L.gv[k - 1];
+        const bool here = x < L.gv[k];
+        L.gv[k] = before_prev ? L.gv[k - 1] : (here ? x : L.gv[k]);
+        L.gs[k] = before_prev ? L.gs[k - 1] : (here ? packed : L.gs[k]);
     }
-    __syncwarp();
-    return thr;
+    if (x < L.gv[0]) {
+        L.gv[0] = x;
+        L.gs[0] = packed;
+    }
+    return slot;
 }
 
-// One half (64 columns, from OFF) of a tile for the calling thread's query: queue the windows
-// below the threshold, merging the warp's queues whenever one fills.
-template <int OFF>
-__device__ __forceinline__ void scan64(const float (&v)[128], int nb, float &thr, int &cnt, TcSmem &sm, int row0,
-                                       int lane) {
+// One half (64 columns) of a tile for the calling thread's query.
+__device__ __forceinline__ void scan_half(const float (&v)[64], int group0, GroupList &L, float *pay_row) {
     float m[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-        m[j] = fminf(fminf(fminf(v[OFF + 8 * j], v[OFF + 8 * j + 1]), fminf(v[OFF + 8 * j + 2], v[OFF + 8 * j + 3])),
-                     fminf(fminf(v[OFF + 8 * j + 4], v[OFF + 8 * j + 5]),
-                           fminf(v[OFF + 8 * j + 6], v[OFF + 8 * j + 7])));
+    for (int g = 0; g < 8; ++g)
+        m[g] = fminf(fminf(fminf(v[8 * g], v[8 * g + 1]), fminf(v[8 * g + 2], v[8 * g + 3])),
+                     fminf(fminf(v[8 * g + 4], v[8 * g + 5]), fminf(v[8 * g + 6], v[8 * g + 7])));
     const float mm =
         fminf(fminf(fminf(m[0], m[1]), fminf(m[2], m[3])), fminf(fminf(m[4], m[5]), fminf(m[6], m[7])));
-    if (!__any_sync(kFull, mm < thr)) return;
-    const int row = row0 + lane;
-    // windows arrive in increasing index order, so a strict value test keeps the
-    // lexicographically smallest (value, index) pairs; groups of 8 whose minimum no lane
-    // beats are skipped whole
+    if (!__any_sync(kFull, mm < L.gv[kKeep - 1])) return;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
-        if (!__any_sync(kFull, m[g] < thr)) continue;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float x = v[OFF + 8 * g + e];
-            if (x < thr) {
-                sm.qv[cnt * kQueueStride + row] = x;
-                sm.qi[cnt * kQueueStride + row] = nb + 8 * g + e;
-                ++cnt;
-            }
-        }
-        // room for the next group's 8
-        if (__any_sync(kFull, cnt > kQueue - 8)) {
-            const bool f = cnt >= kQueue / 2;
-            thr = flush_queues(sm.lv, sm.li, sm.qv, sm.qi, cnt, thr, kQueue / 2, row0, lane);
-            if (f) cnt = 0;
+        if (m[g] < L.gv[kKeep - 1]) {
+            const int slot = group_insert(L, m[g], group0 + g);
+            float4 *dst = reinterpret_cast<float4 *>(pay_row + slot * kG);
+            dst[0] = make_float4(v[8 * g], v[8 * g + 1], v[8 * g + 2], v[8 * g + 3]);
+            dst[1] = make_float4(v[8 * g + 4], v[8 * g + 5], v[8 * g + 6], v[8 * g + 7]);
         }
     }
 }
@@ -262,15 +249,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------- epilogue ----------------
-        const int row0 = warp * 32, row = row0 + lane;
+        const int row = warp * 32 + lane;
         const int q = blockIdx.x * kQM + row;
-        float thr = q < Q ? (thr0 ? thr0[q] : INFINITY) : -INFINITY;
-        for (int k = 0; k < kTopK; ++k) {
-            sm.lv[row * kListStride + k] = thr;
-            sm.li[row * kListStride + k] = kNoWindow;
+        GroupList L;
+        {
+            const float t = q < Q ? (thr0 ? thr0[q] : INFINITY) : -INFINITY;
+#pragma unroll
+            for (int k = 0; k < kKeep; ++k) {
+                L.gv[k] = t;
+                L.gs[k] = (kNoGroup << 4) | k;
+            }
         }
-        __syncwarp();
-        int cnt = 0;
+        float *pay_row = &sm.pay[row * kPayStride];
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         for (int i = 0; i < nt; ++i) {
             const int a = i % kAcc;
@@ -280,31 +270,49 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int nb = (t_begin + i) * kTN;
-            float v[128];
-            tmem_ld128(lane_addr + (uint32_t)(a * kTN), v);
+            const int group0 = (t_begin + i) * (kTN / kG);
+            float v[64];
+            tmem_ld64(lane_addr + (uint32_t)(a * kTN), v);
+            scan_half(v, group0, L, pay_row);
+            tmem_ld64(lane_addr + (uint32_t)(a * kTN + 64), v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
-            scan64<0>(v, nb, thr, cnt, sm, row0, lane);
-            scan64<64>(v, nb + 64, thr, cnt, sm, row0, lane);
+            scan_half(v, group0 + 8, L, pay_row);
         }
-        thr = flush_queues(sm.lv, sm.li, sm.qv, sm.qi, cnt, thr, 1, row0, lane);
+        // publish which group each slot holds, then select each query's 32 best windows
+#pragma unroll
+        for (int k = 0; k < kKeep; ++k) sm.gmap[row * (kKeep + 1) + (L.gs[k] & 15)] = L.gs[k] >> 4;
+        __syncwarp();
         if (!*abort_flag) {
             for (int r = 0; r < 32; ++r) {
-                const int rr = row0 + r;
+                const int rr = warp * 32 + r;
                 const int qq = blockIdx.x * kQM + rr;
                 if (qq >= Q) break;
-                const float v0 = sm.lv[rr * kListStride + lane];
-                const int i0 = sm.li[rr * kListStride + lane];
+                float sv[4];
+                int si[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int k = lane + 32 * c;  // slot k / 8, element k % 8
+                    const int grp = sm.gmap[rr * (kKeep + 1) + k / kG];
+                    const float x = sm.pay[rr * kPayStride + k];
+                    const bool real = grp != kNoGroup && !isnan(x);
+                    sv[c] = real ? x : INFINITY;
+                    si[c] = real ? grp * kG + (k % kG) : kNoWindow;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) warp_sort32(sv[c], si[c], lane);
+                warp_merge32(sv[0], si[0], sv[1], si[1], lane);
+                warp_merge32(sv[2], si[2], sv[3], si[3], lane);
+                warp_merge32(sv[0], si[0], sv[2], si[2], lane);
                 if (nparts == 1) {
-                    const bool real = i0 != kNoWindow;
-                    cand_idx[(size_t)qq * kTopK + lane] = real ? i0 : -1;
-                    cand_lb[(size_t)qq * kTopK + lane] = real ? v0 + qnorm[qq] : INFINITY;
+                    const bool real = si[0] != kNoWindow;
+                    cand_idx[(size_t)qq * kTopK + lane] = real ? si[0] : -1;
+                    cand_lb[(size_t)qq * kTopK + lane] = real ? sv[0] + qnorm[qq] : INFINITY;
                 } else {
                     const size_t o = ((size_t)qq * nparts + part) * kTopK + lane;
-                    part_v[o] = v0;
-                    part_i[o] = i0;
+                    part_v[o] = sv[0];
+                    part_i[o] = si[0];
                 }
             }
         }
@@ -362,7 +370,8 @@ __global__ void k_pack_queries(const float *__restrict__ qcoord, int Q, int d, i
 }
 
 // Exemplar vectors as FP16 MMA operand tiles: rows = windows, K = (-2 y, -2 r, norm hi/mid/lo,
-// 0...).  Padding windows carry +inf in the hi slot, so their score is +inf.
+// 0...).  Padding windows carry +inf and -inf in the hi and mid slots, so their score is NaN and
+// fails every comparison.
 __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int d,
                                 int da, int K, __half *__restrict__ out) {
     const long total = (long)ntiles * kTN * K;
@@ -376,7 +385,7 @@ __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__res
             v = isinf(nrm) ? 0.0f : et[((size_t)t * da + k) * kTN + m];
         } else if (k <= d + 3) {
             if (isinf(nrm)) {
-                v = (k == d + 1) ? nrm : 0.0f;
+                v = (k == d + 1) ? INFINITY : (k == d + 2) ? -INFINITY : 0.0f;
             } else {
                 const float hi = __half2float(__float2half_rn(nrm));
                 const float r1 = nrm - hi;
@@ -390,8 +399,10 @@ __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__res
 }
 
 // Warm start: the previous search's 32 windows of each query, scored in FP32 from the same FP16
-// operands the tensor cores multiply.  Their largest score plus a margin for a different
-// summation order is an upper bound on the query's 32nd best score.  One warp per query.
+// operands the tensor cores multiply.  A window's score bounds its group's minimum from above, so
+// with g_1 <= g_2 <= ... the smallest score of each distinct group among them, the query's 16th
+// best group minimum is at most g_16; plus a margin for a different summation order, that is the
+// bound.  With fewer than 16 distinct groups the bound is +inf (a cold search).  One warp per query.
 __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half *__restrict__ qtile,
                                  const float *__restrict__ qnorm, const __half *__restrict__ etile,
                                  const float *__restrict__ umax, int Q, int K, int N, float eps_scale,
@@ -400,8 +411,9 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= Q) return;
     const int n = prev_idx[(size_t)q * kTopK + lane];
+    const bool valid = n >= 0 && n < N;
     float p = INFINITY;
-    if (n >= 0 && n < N) {
+    if (valid) {
         const unsigned char *e = reinterpret_cast<const unsigned char *>(etile + (size_t)(n / kTN) * kTN * K);
         const unsigned char *a = reinterpret_cast<const unsigned char *>(qtile + (size_t)(q / kQM) * kQM * K);
         const int m = n % kTN, r = q % kQM;
@@ -410,11 +422,20 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
             p = fmaf(__half2float(*reinterpret_cast<const __half *>(a + core_offset(r, k, kQM))),
                      __half2float(*reinterpret_cast<const __half *>(e + core_offset(m, k, kTN))), p);
     }
-    float mx = p;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    // keep each group's smallest score once (ties: lowest lane)
+    const int grp = valid ? n / kG : -1 - lane;
+    bool first = valid;
+    for (int j = 0; j < 32; ++j) {
+        const int gj = __shfl_sync(kFull, grp, j);
+        const float pj = __shfl_sync(kFull, p, j);
+        if (j != lane && gj == grp && (pj < p || (pj == p && j < lane))) first = false;
+    }
+    float key = first ? p : INFINITY;
+    int idx = lane;
+    warp_sort32(key, idx, lane);
+    const float g16 = __shfl_sync(kFull, key, kKeep - 1);
     // |error| of an FP32 sum of K exact products <= K 2^-24 sum|terms|, sum|terms| <= qnorm + 2 umax
-    if (lane == 0) thr0[q] = mx + eps_scale * (qnorm[q] + 2.0f * *umax);
+    if (lane == 0) thr0[q] = isinf(g16) ? INFINITY : g16 + eps_scale * (qnorm[q] + 2.0f * *umax);
 }
 
 // --- self-test: one 128 x N x K tile through the same descriptors, written back row-major ---
