@@ -56,7 +56,7 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     PTS_TRY(ws.fail2_list.ensure(cap, "second fail list"));
     PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->w), "full query vectors"));
     PTS_TRY(ws.best64.ensure(cap, "packed minima"));
-    PTS_TRY(ws.thr0.ensure(cap, "warm-start bounds"));
+    PTS_TRY(ws.thr0.ensure(2 * (size_t)cap, "warm-start bounds"));
     PTS_TRY(ws.counters.ensure(4, "counters"));
     PTS_TRY(ws.nn.ensure(cap, "nn"));
     PTS_TRY(ws.d2.ensure(cap, "d2"));

@@ -91,7 +91,7 @@ struct Workspace {
     DevBuf<int> fail2_list;    // [Q] queries not certified by the full-dimension pass
     DevBuf<float> qfull;       // [Qpad/64][Dp][64] centred full vectors of failing queries
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
-    DevBuf<float> thr0;        // [Q] warm-start bounds
+    DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
     DevBuf<float> part_v;      // [Q][parts][32] per-part candidate lists of the tensor-core search
     DevBuf<int> part_i;

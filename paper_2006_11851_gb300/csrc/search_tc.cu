@@ -11,24 +11,25 @@
 // (TMEM columns), both operands K-major in the no-swizzle core-matrix layout, staged by 1-D bulk
 // copies of pre-packed tiles.  Four accumulator stages of 128 columns fill TMEM's 512.
 //
-// Warps (6): 0-3 epilogue (TMEM lane quarter = warp), 4 producer, 5 MMA issuer and TMEM owner.
-// Selection works on groups of 8 consecutive windows.  An epilogue thread owns one query and
-// keeps, in registers, the 16 groups with the smallest minimum score seen so far, sorted by
-// (minimum, group); the 8 scores of each kept group sit in a shared-memory slot that moves with
-// the group.  Per tile the thread loads its query's 128 accumulators (two 64-column tcgen05.ld),
-// reduces each group of 8 to its minimum and, only for a group whose minimum beats the 16th
-// kept one, shifts it into the register list and stores its 8 scores into the slot of the
-// evicted group.  Every window among the query's 16 best lies in one of its 16 best groups, and
-// the list is the exact 16 best groups whatever the scan order (ties go to the smaller group,
-// which comes first).  At the end each warp takes its queries one at a time, loads the 128 kept
-// scores (4 per lane) and keeps the 32 smallest (score, window) pairs by bitonic sort and merge.
-// Padding windows score NaN: a group minimum ignores them and they are dropped at the end.
+// Warps (10): 0-7 epilogue (TMEM lane quarter = warp % 4, column half = warp / 4), 8 producer,
+// 9 MMA issuer and TMEM owner.  Selection works on groups of 8 consecutive windows; a tile's
+// 16 groups are split 8/8 between its column halves.  An epilogue thread owns one (query, half)
+// and keeps, in registers, the 8 groups of its half with the smallest minimum score seen so
+// far, sorted by (minimum, group); the 8 scores of each kept group sit in a shared-memory slot
+// that moves with the group.  Per tile the thread loads its 64 accumulators (one tcgen05.ld),
+// reduces each group of 8 to its minimum and, only for a group whose minimum beats the 8th kept
+// one, shifts it into the register list and stores its 8 scores into the slot of the evicted
+// group.  Every window among the query's 8 best of a half lies in one of that half's 8 best
+// groups, and each list is exactly those 8 groups whatever the scan order (ties go to the
+// smaller group, which comes first).  At the end each warp takes queries one at a time, loads
+// the 2 x 64 kept scores (4 per lane) and keeps the 32 smallest (score, window) pairs by bitonic
+// sort and merge.  Padding windows score NaN: a group minimum ignores them and they are dropped.
 //
 // The exemplar tiles of a query block may be split across blockIdx.y; each part writes its
-// sorted 32 and k_merge_parts merges them.  An optional per-query bound thr0 (warm start, an
-// upper bound on the query's 16th best group minimum) seeds the group list with sentinels
-// (thr0, none): only groups whose minimum is below it are kept, and since at least 16 are, the
-// kept groups are the same 16 as without the bound.
+// sorted 32 and k_merge_parts merges them.  Optional per-query, per-half bounds thr0 (warm
+// start, an upper bound on the 8th best group minimum of each half) seed the group lists with
+// sentinels (thr0, none): only groups whose minimum is below the bound are kept, and since at
+// least 8 are, the kept groups are the same as without the bound.
 // All waits are bounded; on a timeout the kernel flags the status word, drains its copies and
 // frees TMEM.
 #include <algorithm>
@@ -45,14 +46,15 @@ namespace {
 constexpr int kQM = 128;            // queries per CTA (MMA M)
 constexpr int kTN = 128;            // exemplar windows per tile (MMA N)
 constexpr int kAcc = 4;             // accumulator stages of kTN columns
-constexpr int kEpiWarps = 4;
-constexpr int kThreads = (kEpiWarps + 2) * 32;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = kEpiThreads + 64;
 constexpr int kMaxKt = 128;         // K of the search vectors
 constexpr int kRing = 96 * 1024;    // bytes of exemplar-tile ring
 constexpr int kMaxStages = 8;
 constexpr int kG = 8;               // windows per group
-constexpr int kKeep = 16;           // groups kept per query
-constexpr int kPayStride = kKeep * kG + 4;  // floats per query row of kept scores (odd 16-byte units)
+constexpr int kKeep = 8;            // groups kept per (query, column half)
+constexpr int kPayStride = kKeep * kG + 4;  // floats per thread of kept scores (odd 16-byte units)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNoWindow = INT_MAX;
 constexpr int kNoGroup = 0x7FFFFFF;  // group field of a sentinel (27 bits)
@@ -60,8 +62,8 @@ constexpr int kNoGroup = 0x7FFFFFF;  // group field of a sentinel (27 bits)
 struct TcSmem {
     alignas(1024) unsigned char q[kQM * kMaxKt * 2];
     alignas(1024) unsigned char e[kRing];
-    alignas(16) float pay[kQM * kPayStride];  // per query, per slot: the 8 scores of a kept group
-    int gmap[kQM * (kKeep + 1)];               // per query, per slot: the group held (at the end)
+    alignas(16) float pay[kEpiThreads * kPayStride];  // per thread, per slot: a kept group's 8 scores
+    int gmap[kEpiThreads * (kKeep + 1)];               // per thread, per slot: its group (at the end)
     uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAcc], acc_empty[kAcc], q_full, done;
     uint32_t tmem_base;
     int abort_flag;
@@ -123,7 +125,7 @@ struct GroupList {
 // entry's slot, and returns that slot.  Groups arrive in increasing order, so a strict value test
 // places ties after the groups already kept.
 __device__ __forceinline__ int group_insert(GroupList &L, float x, int group) {
-    const int slot = L.gs[kKeep - 1] & 15;
+    const int slot = L.gs[kKeep - 1] & 15;  // kKeep <= 16
     const int packed = (group << 4) | slot;
 #pragma unroll
     for (int k = kKeep - 1; k > 0; --k) {
@@ -249,19 +251,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------- epilogue ----------------
-        const int row = warp * 32 + lane;
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
         const int q = blockIdx.x * kQM + row;
         GroupList L;
         {
-            const float t = q < Q ? (thr0 ? thr0[q] : INFINITY) : -INFINITY;
+            const float t = q < Q ? (thr0 ? thr0[2 * (size_t)q + half] : INFINITY) : -INFINITY;
 #pragma unroll
             for (int k = 0; k < kKeep; ++k) {
                 L.gv[k] = t;
                 L.gs[k] = (kNoGroup << 4) | k;
             }
         }
-        float *pay_row = &sm.pay[row * kPayStride];
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        float *pay_row = &sm.pay[tid * kPayStride];
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
         for (int i = 0; i < nt; ++i) {
             const int a = i % kAcc;
             const bool ok = mbar_wait_or_abort(&sm.acc_full[a], (uint32_t)((i / kAcc) & 1), status, abort_flag);
@@ -270,32 +273,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const int group0 = (t_begin + i) * (kTN / kG);
             float v[64];
             tmem_ld64(lane_addr + (uint32_t)(a * kTN), v);
-            scan_half(v, group0, L, pay_row);
-            tmem_ld64(lane_addr + (uint32_t)(a * kTN + 64), v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
-            scan_half(v, group0 + 8, L, pay_row);
+            scan_half(v, (t_begin + i) * (kTN / kG) + half * 8, L, pay_row);
         }
         // publish which group each slot holds, then select each query's 32 best windows
 #pragma unroll
-        for (int k = 0; k < kKeep; ++k) sm.gmap[row * (kKeep + 1) + (L.gs[k] & 15)] = L.gs[k] >> 4;
-        __syncwarp();
+        for (int k = 0; k < kKeep; ++k) sm.gmap[tid * (kKeep + 1) + (L.gs[k] & 15)] = L.gs[k] >> 4;
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
         if (!*abort_flag) {
-            for (int r = 0; r < 32; ++r) {
-                const int rr = warp * 32 + r;
+            for (int r = 0; r < kQM / kEpiWarps; ++r) {
+                const int rr = warp * (kQM / kEpiWarps) + r;
                 const int qq = blockIdx.x * kQM + rr;
                 if (qq >= Q) break;
                 float sv[4];
                 int si[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int k = lane + 32 * c;  // slot k / 8, element k % 8
-                    const int grp = sm.gmap[rr * (kKeep + 1) + k / kG];
-                    const float x = sm.pay[rr * kPayStride + k];
+                    // entries 0..63: the half-0 thread of row rr (index rr), 64..127: half 1 (rr + 128)
+                    const int owner = rr + (c >> 1) * kQM;
+                    const int k = lane + 32 * (c & 1);  // slot k / 8, element k % 8
+                    const int grp = sm.gmap[owner * (kKeep + 1) + k / kG];
+                    const float x = sm.pay[owner * kPayStride + k];
                     const bool real = grp != kNoGroup && !isnan(x);
                     sv[c] = real ? x : INFINITY;
                     si[c] = real ? grp * kG + (k % kG) : kNoWindow;
@@ -399,10 +401,12 @@ __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__res
 }
 
 // Warm start: the previous search's 32 windows of each query, scored in FP32 from the same FP16
-// operands the tensor cores multiply.  A window's score bounds its group's minimum from above, so
-// with g_1 <= g_2 <= ... the smallest score of each distinct group among them, the query's 16th
-// best group minimum is at most g_16; plus a margin for a different summation order, that is the
-// bound.  With fewer than 16 distinct groups the bound is +inf (a cold search).  One warp per query.
+// operands the tensor cores multiply (16-byte rows of the operand layout, 8 values per load).  A
+// window's score bounds its group's minimum from above, so with g_1 <= g_2 <= ... the smallest
+// score of each distinct group of one column half among them, that half's 8th best group
+// minimum is at most g_8; plus a margin for a different summation order, that is the half's
+// bound (thr0[2 q + half]).  With fewer than 8 distinct groups in a half its bound is +inf.
+// One warp per query.
 __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half *__restrict__ qtile,
                                  const float *__restrict__ qnorm, const __half *__restrict__ etile,
                                  const float *__restrict__ umax, int Q, int K, int N, float eps_scale,
@@ -418,24 +422,37 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
         const unsigned char *a = reinterpret_cast<const unsigned char *>(qtile + (size_t)(q / kQM) * kQM * K);
         const int m = n % kTN, r = q % kQM;
         p = 0.0f;
-        for (int k = 0; k < K; ++k)
-            p = fmaf(__half2float(*reinterpret_cast<const __half *>(a + core_offset(r, k, kQM))),
-                     __half2float(*reinterpret_cast<const __half *>(e + core_offset(m, k, kTN))), p);
+        for (int k8 = 0; k8 < K; k8 += 8) {
+            const uint4 av = *reinterpret_cast<const uint4 *>(a + core_offset(r, k8, kQM));
+            const uint4 ev = __ldg(reinterpret_cast<const uint4 *>(e + core_offset(m, k8, kTN)));
+            const __half2 *ah = reinterpret_cast<const __half2 *>(&av);
+            const __half2 *eh = reinterpret_cast<const __half2 *>(&ev);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float2 af = __half22float2(ah[h]), ef = __half22float2(eh[h]);
+                p = fmaf(af.x, ef.x, p);
+                p = fmaf(af.y, ef.y, p);
+            }
+        }
     }
-    // keep each group's smallest score once (ties: lowest lane)
+    // each group's smallest score once (ties: lowest lane), per column half
     const int grp = valid ? n / kG : -1 - lane;
+    const int half = valid ? (grp % (kTN / kG)) / kKeep : -1;
     bool first = valid;
     for (int j = 0; j < 32; ++j) {
         const int gj = __shfl_sync(kFull, grp, j);
         const float pj = __shfl_sync(kFull, p, j);
         if (j != lane && gj == grp && (pj < p || (pj == p && j < lane))) first = false;
     }
-    float key = first ? p : INFINITY;
-    int idx = lane;
-    warp_sort32(key, idx, lane);
-    const float g16 = __shfl_sync(kFull, key, kKeep - 1);
-    // |error| of an FP32 sum of K exact products <= K 2^-24 sum|terms|, sum|terms| <= qnorm + 2 umax
-    if (lane == 0) thr0[q] = isinf(g16) ? INFINITY : g16 + eps_scale * (qnorm[q] + 2.0f * *umax);
+    const float eps = eps_scale * (qnorm[q] + 2.0f * *umax);
+    for (int h = 0; h < 2; ++h) {
+        float key = first && half == h ? p : INFINITY;
+        int idx = lane;
+        warp_sort32(key, idx, lane);
+        const float g8 = __shfl_sync(kFull, key, kKeep - 1);
+        // |error| of an FP32 sum of K exact products <= K 2^-24 sum|terms|, sum|terms| <= qnorm + 2 umax
+        if (lane == 0) thr0[2 * (size_t)q + h] = isinf(g8) ? INFINITY : g8 + eps;
+    }
 }
 
 // --- self-test: one 128 x N x K tile through the same descriptors, written back row-major ---
