@@ -29,6 +29,11 @@ constexpr float kTauC = 8.0f;
 // K <= 128 and sum|terms| <= ||u_q||^2 + 2 max_n ||u_n||^2.  2^-13 doubles that.
 constexpr float kWarmEps = 1.0f / 8192.0f;
 
+// The exact search runs its PCA-space pass only when the d components keep at least this
+// fraction of the exemplar's variance; below it most queries fail the certificate and the pass
+// is wasted, so every query goes straight to the full-dimension pass.
+constexpr double kPcaPassMinVar = 0.85;
+
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 pts_status check_grid(int H, int W, int w, int stride, const char *what) {
@@ -112,7 +117,7 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no proposal trained on this index");
     const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
     launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
-                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
+                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st, &ws.proj_part);
     PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
     PTS_TRY(pr.mlp.ensure(pr.C, std::min(Q, kMlpChunk), st));
     for (int q0 = 0; q0 < Q; q0 += kMlpChunk) {
@@ -141,19 +146,27 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
                         int32_t *nn_out, float *d2_out, cudaStream_t st) {
     Workspace &ws = idx->ws;
     const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
-    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0,
-                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
-    PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
-    launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
-                       idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
     RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
     unsigned int *fail_count = ws.counters.ptr + 0;
     unsigned int *fail2_count = ws.counters.ptr + 1;
     unsigned int *brute_count = ws.counters.ptr + 2;
-    // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
-    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
-                  d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
+    PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
+    if (idx->var_retained < kPcaPassMinVar) {
+        // the d-dimensional bound would certify few queries: every query goes to the
+        // full-dimension pass (its bound needs only ||u_q||^2 and the slack)
+        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, 0, idx->da, 0, nullptr,
+                       ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
+        launch_list_all(ws.fail_list.ptr, fail_count, Q, st);
+    } else {
+        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0,
+                       ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st, &ws.proj_part);
+        launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
+                           idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
+        // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
+        launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
+                      d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
+    }
     PTS_TRY(exact_on_list(idx, ra, fail_count, fail2_count, brute_count, nn_out, d2_out, st));
     return PTS_OK;
 }
@@ -174,8 +187,12 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             break;
         case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
+            // slack of an FP16 bound: operand rounding (1 + 2^-11)^2 - 1 < 2^-10 per product of
+            // sum |products| <= ||u_q||^2 + max ||u_n||^2, the FP32 sum of K <= 128 terms, and the
+            // FP32 slack of the full-dimension distance; 2^-9 covers the first two
+            const float tau_f16 = 1.0f / 512.0f + kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
             launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
-                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
+                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_f16, idx->umax.ptr, st, &ws.proj_part);
             const int nparts = tc_parts(Q, idx->ntiles);
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
             if (nparts > 1) {
@@ -193,7 +210,8 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
                              ws.part_i.ptr, idx->status.ptr, st);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
                           idx->nx, idx->N, Q};
-            launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
+            // candidates in ascending bound order; stop where bound - slack exceeds the best
+            launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out, d2_out,
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
             break;
         }

@@ -16,6 +16,8 @@
 //                      (the tiled, pre-scaled form the search streams)
 #include <math.h>
 
+#include <algorithm>
+
 #include "pts_internal.cuh"
 
 namespace pts {
@@ -23,35 +25,68 @@ namespace {
 
 constexpr int kPWin = 64;           // windows per block
 constexpr int kPK = 32;             // window-vector elements per slice
-constexpr int kPD = kMaxDPca;       // coordinates per block (d <= 128)
 constexpr int kXs = kPWin + 1;      // row stride of the staged window slices
-constexpr int kBs = kPD + 4;        // row stride of the staged basis slice (16-byte rows)
 
+template <int PD>
 struct ProjSmem {
+    static constexpr int kBs = PD + 4;  // row stride of the staged basis slice (16-byte rows)
     union {
         struct {
             float xs[kPK * kXs];              // [k][window], centred
             alignas(16) float bs[kPK * kBs];  // [k][coordinate]
         } st;
-        float ys[kPWin * (kPD + 1)];          // the finished tile, [window][coordinate]
+        float ys[kPWin * (PD + 1)];           // the finished tile, [window][coordinate]
     } u;
     long base[kPWin];               // image offset of each window's first element
     int koff[kPK];                  // image offset of each element of the slice
     float un[kPWin];
 };
 
+struct ProjOut {
+    int d, da, layout;
+    float *coord, *norm, *tau;
+    float tau_scale;
+    const float *umax;
+};
+
+// ||y||^2, r and the output rows of one window, written by one warp (y in shared or global
+// memory, row of PD + 1 floats: coordinates then ||u||^2)
+__device__ __forceinline__ void write_window(const ProjOut &o, long win, const float *yr, float u2, int lane) {
+    float yn = 0.0f;
+    for (int j = lane; j < o.d; j += 32) yn = fmaf(yr[j], yr[j], yn);
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) yn += __shfl_xor_sync(0xffffffffu, yn, s);
+    const float r = sqrtf(fmaxf(u2 - yn, 0.0f));
+    if (o.layout == 0) {
+        float *c = o.coord + win * o.da;
+        for (int j = lane; j < o.da; j += 32) c[j] = j < o.d ? yr[j] : (j == o.d ? r : 0.0f);
+        if (lane == 0) o.tau[win] = o.tau_scale * (u2 + *o.umax);
+    } else {
+        const long tile = win / kBN, col = win - tile * kBN;
+        float *c = o.coord + tile * (long)o.da * kBN + col;
+        for (int j = lane; j < o.da; j += 32) c[(long)j * kBN] = j < o.d ? -2.0f * yr[j] : (j == o.d ? -2.0f * r : 0.0f);
+    }
+    if (lane == 0) o.norm[win] = u2;
+}
+
+// PD = 64 or 128 output columns (d <= PD); thread tile 4 windows x PD/16 coordinates.  With
+// gridDim.y > 1 the block covers one slice range of the window vector and writes its partial
+// sums to part[blockIdx.y][win][PD + 1] (coordinates, then ||u||^2), reduced by k_project_finish.
+template <int PD>
 __global__ void __launch_bounds__(256)
     k_project(const float *__restrict__ img, int W, int w, int stride, int qx_n, int Qn,
-              const float *__restrict__ mu, const float *__restrict__ basis, int d, int da,
-              int layout, float *__restrict__ out_coord, float *__restrict__ out_norm,
-              float *__restrict__ out_tau, float tau_scale, const float *__restrict__ umax) {
-    __shared__ ProjSmem sm;
+              const float *__restrict__ mu, const float *__restrict__ basis, int kper, ProjOut o,
+              float *__restrict__ part) {
+    constexpr int JD = PD / 16;
+    constexpr int kBs = ProjSmem<PD>::kBs;
+    __shared__ ProjSmem<PD> sm;
     float *const xs = sm.u.st.xs;
     float *const bs = sm.u.st.bs;
     float *const ys = sm.u.ys;
-    const int row = 3 * w, D = row * w;
+    const int row = 3 * w, D = row * w, d = o.d;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long win0 = (long)blockIdx.x * kPWin;
+    const int kbeg = blockIdx.y * kper, kend = min(D, kbeg + kper);
     if (tid < kPWin) {
         const long win = win0 + tid;
         const long wq = win < Qn ? win : 0;
@@ -59,13 +94,13 @@ __global__ void __launch_bounds__(256)
         sm.base[tid] = (qy * stride * (long)W + qx * stride) * 3;
         sm.un[tid] = 0.0f;
     }
-    float acc[4][8];
+    float acc[4][JD];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < JD; ++j) acc[i][j] = 0.0f;
     float un = 0.0f;
-    for (int k0 = 0; k0 < D; k0 += kPK) {
+    for (int k0 = kbeg; k0 < kend; k0 += kPK) {
         if (tid < kPK) {
             const int k = min(k0 + tid, D - 1);
             const int dy = k / row, e = k - dy * row;
@@ -79,14 +114,14 @@ __global__ void __launch_bounds__(256)
             const int wl = idx / kPK, kk = idx - wl * kPK;
             const int k = k0 + kk;
             float v = 0.0f;
-            if (k < D && win0 + wl < Qn) v = __ldg(img + sm.base[wl] + sm.koff[kk]) - __ldg(mu + k);
+            if (k < kend && win0 + wl < Qn) v = __ldg(img + sm.base[wl] + sm.koff[kk]) - __ldg(mu + k);
             xs[kk * kXs + wl] = v;
         }
         // basis slice: row j of the basis is contiguous in k
-        for (int idx = tid; idx < kPD * kPK; idx += 256) {
+        for (int idx = tid; idx < PD * kPK; idx += 256) {
             const int j = idx / kPK, kk = idx - j * kPK;
             const int k = k0 + kk;
-            bs[kk * kBs + j] = (j < d && k < D) ? __ldg(basis + (size_t)j * D + k) : 0.0f;
+            bs[kk * kBs + j] = (j < d && k < kend) ? __ldg(basis + (size_t)j * D + k) : 0.0f;
         }
         __syncthreads();
         if (tid < kPWin) {
@@ -101,45 +136,91 @@ __global__ void __launch_bounds__(256)
             float a[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = xs[kk * kXs + ty * 4 + i];
-            const float4 b0 = *reinterpret_cast<const float4 *>(&bs[kk * kBs + tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&bs[kk * kBs + tx * 8 + 4]);
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            float b[JD];
+#pragma unroll
+            for (int j4 = 0; j4 < JD / 4; ++j4) {
+                const float4 bv = *reinterpret_cast<const float4 *>(&bs[kk * kBs + tx * JD + 4 * j4]);
+                b[4 * j4] = bv.x;
+                b[4 * j4 + 1] = bv.y;
+                b[4 * j4 + 2] = bv.z;
+                b[4 * j4 + 3] = bv.w;
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < JD; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
+    }
+    if (gridDim.y > 1) {
+        float *pb = part + (size_t)blockIdx.y * Qn * (PD + 1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long win = win0 + ty * 4 + i;
+            if (win < Qn)
+#pragma unroll
+                for (int j = 0; j < JD; ++j) pb[win * (PD + 1) + tx * JD + j] = acc[i][j];
+        }
+        if (tid < kPWin && win0 + tid < Qn) pb[(win0 + tid) * (PD + 1) + PD] = un;
+        return;
     }
     // (the loop ends with a barrier, so the staging buffers may be overwritten)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) ys[(ty * 4 + i) * (kPD + 1) + tx * 8 + j] = acc[i][j];
+        for (int j = 0; j < JD; ++j) ys[(ty * 4 + i) * (PD + 1) + tx * JD + j] = acc[i][j];
     if (tid < kPWin) sm.un[tid] = un;
     __syncthreads();
-    // one warp per window row of the tile: ||y||^2, r, and the coalesced writes
     const int lane = tid & 31, wp = tid >> 5;
     for (int wl = wp; wl < kPWin; wl += 8) {
         const long win = win0 + wl;
         if (win >= Qn) break;
-        const float *yr = &ys[wl * (kPD + 1)];
-        float yn = 0.0f;
-        for (int j = lane; j < d; j += 32) yn = fmaf(yr[j], yr[j], yn);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) yn += __shfl_xor_sync(0xffffffffu, yn, o);
-        const float u2 = sm.un[wl];
-        const float r = sqrtf(fmaxf(u2 - yn, 0.0f));
-        if (layout == 0) {
-            float *o = out_coord + win * da;
-            for (int j = lane; j < da; j += 32) o[j] = j < d ? yr[j] : (j == d ? r : 0.0f);
-            if (lane == 0) out_tau[win] = tau_scale * (u2 + *umax);
-        } else {
-            const long tile = win / kBN, col = win - tile * kBN;
-            float *o = out_coord + tile * (long)da * kBN + col;
-            for (int j = lane; j < da; j += 32) o[(long)j * kBN] = j < d ? -2.0f * yr[j] : (j == d ? -2.0f * r : 0.0f);
+        write_window(o, win, &ys[wl * (PD + 1)], sm.un[wl], lane);
+    }
+}
+
+// Sums the slice partials of each window in slice order (deterministic) and writes its outputs.
+template <int PD>
+__global__ void __launch_bounds__(256) k_project_finish(const float *__restrict__ part, int nsplit, int Qn, ProjOut o) {
+    __shared__ float ys[8][PD + 1];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const long win = (long)blockIdx.x * 8 + wp;
+    if (win >= Qn) return;
+    for (int j = lane; j <= PD; j += 32) {
+        float sacc = 0.0f;
+        for (int p = 0; p < nsplit; ++p) sacc += part[((size_t)p * Qn + win) * (PD + 1) + j];
+        ys[wp][j] = sacc;
+    }
+    __syncwarp();
+    write_window(o, win, ys[wp], ys[wp][PD], lane);
+}
+
+// ||v - mu||^2 (and tau) of each window only, one warp per window (the search needs no
+// coordinates when it runs in full dimension).
+__global__ void __launch_bounds__(256) k_window_norms(const float *__restrict__ img, int W, int w, int stride, int qx_n,
+                                                      int Qn, const float *__restrict__ mu, ProjOut o) {
+    const int lane = threadIdx.x & 31;
+    const long win = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (win >= Qn) return;
+    const int row = 3 * w;
+    const long qy = win / qx_n, qx = win - qy * qx_n;
+    const float *src = img + (qy * stride * (long)W + qx * stride) * 3;
+    float un = 0.0f;
+    for (int dy = 0; dy < w; ++dy)
+        for (int e = lane; e < row; e += 32) {
+            const float a = __ldg(src + (size_t)dy * W * 3 + e) - __ldg(mu + dy * row + e);
+            un = fmaf(a, a, un);
         }
-        if (lane == 0) out_norm[win] = u2;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) un += __shfl_xor_sync(0xffffffffu, un, s);
+    if (lane == 0) {
+        o.norm[win] = un;
+        if (o.tau) o.tau[win] = o.tau_scale * (un + *o.umax);
+        if (o.coord) {
+            float *c = o.coord + win * o.da;
+            c[0] = sqrtf(un);
+            for (int j = 1; j < o.da; ++j) c[j] = 0.0f;
+        }
     }
 }
 
@@ -167,13 +248,40 @@ __global__ void k_norm_max(const float *__restrict__ v, int n, float *__restrict
 void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
                     const float *basis, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
-                    cudaStream_t st) {
+                    cudaStream_t st, DevBuf<float> *scratch) {
     const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
     const long Qn = (long)qy_n * qx_n;
     if (Qn <= 0) return;
+    const ProjOut o{d, da, layout, out_coord, out_norm, out_tau, tau_scale, umax};
     ProfScope ps(kProfProject, st, 1);
-    k_project<<<(unsigned)ceil_div(Qn, kPWin), 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basis, d, da,
-                                                            layout, out_coord, out_norm, out_tau, tau_scale, umax);
+    if (d <= 0) {
+        k_window_norms<<<(unsigned)ceil_div(Qn * 32, 256), 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, o);
+        return;
+    }
+    const int D = 3 * w * w;
+    const long nblk = ceil_div(Qn, kPWin);
+    // slices of the window vector per block: enough blocks for two per SM when the windows alone
+    // leave SMs idle, each slice range at least 256 long
+    int nsplit = 1;
+    if (scratch && nblk < 2 * 152) nsplit = (int)std::max(1L, std::min<long>(2 * 152 / nblk, D / 256));
+    const int PDc = d <= 64 ? 64 : 128;
+    if (nsplit > 1 && scratch->ensure((size_t)nsplit * Qn * (PDc + 1), "projection partials") != PTS_OK)
+        nsplit = 1;
+    const int kper = ceil_div(ceil_div(D, nsplit), kPK) * kPK;
+    nsplit = ceil_div(D, kper);
+    const dim3 grid((unsigned)nblk, nsplit);
+    float *part = nsplit > 1 ? scratch->ptr : nullptr;
+    if (PDc == 64)
+        k_project<64><<<grid, 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basis, kper, o, part);
+    else
+        k_project<128><<<grid, 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basis, kper, o, part);
+    if (nsplit > 1) {
+        count_launches(1);
+        if (PDc == 64)
+            k_project_finish<64><<<(unsigned)ceil_div(Qn, 8), 256, 0, st>>>(part, nsplit, (int)Qn, o);
+        else
+            k_project_finish<128><<<(unsigned)ceil_div(Qn, 8), 256, 0, st>>>(part, nsplit, (int)Qn, o);
+    }
 }
 
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st) {

@@ -93,6 +93,7 @@ struct Workspace {
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
     DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
+    DevBuf<float> proj_part;   // per-slice partial sums of a split projection
     DevBuf<float> part_v;      // [Q][parts][32] per-part candidate lists of the tensor-core search
     DevBuf<int> part_i;
     int warm_q = -1, warm_ho = -1, warm_wo = -1, warm_stride = -1;  // geometry of cand_idx
@@ -179,7 +180,7 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
 void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
                     const float *basis, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
-                    cudaStream_t st);
+                    cudaStream_t st, DevBuf<float> *scratch = nullptr);
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st);
 void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
 // search_f32.cu
@@ -242,6 +243,7 @@ struct RerankArgs {
     int Q;
 };
 // qlist/qcount == NULL: all Q queries; else the listed ones (count on the device)
+void launch_list_all(int *list, unsigned int *count, int Q, cudaStream_t st);
 void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qcount,
                    const int *cand_idx, const float *cand_lb, const float *tau, int certify,
                    int *nn_out, float *d2_out, int *fail_list, unsigned int *fail_count,

@@ -2,9 +2,10 @@
 //
 // k_rerank       one warp per query (all queries, or those of a device-side
 //                list): evaluates the query's candidates in increasing order of
-//                their bound, skipping those whose bound minus the rounding
-//                slack tau already exceeds the best distance found, and keeps
-//                the lexicographically smallest (d2, n).  With certify != 0
+//                their bound and keeps the lexicographically smallest (d2, n).
+//                With certify != 0 it stops at the first candidate whose bound
+//                minus the slack tau_q exceeds the best distance found (no later
+//                candidate can win).  With certify == 1
 //                (exact mode) the result is final when d2_best <= B_32 - tau_q:
 //                every window outside the list has a bound >= B_32, hence a
 //                distance >= d2_best.  Otherwise the query joins the fail list
@@ -16,6 +17,8 @@
 // Distances are sums of squared FP32 differences read straight from the two
 // images (a window row is 3w contiguous floats in HWC layout), reduced across
 // the warp by a fixed butterfly, so the result is deterministic.
+#include <algorithm>
+
 #include "pts_internal.cuh"
 
 namespace pts {
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restr
     }
     const int last_idx = __shfl_sync(kFull, my_idx, kTopK - 1);
     const float last_lb = __shfl_sync(kFull, my_lb, kTopK - 1);
-    const bool done = !certify || last_idx < 0 || best <= last_lb - tq;
+    const bool done = certify != 1 || last_idx < 0 || best <= last_lb - tq;
     if (lane == 0) {
         if (done) {
             nn_out[q] = best_n;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__res
     }
     const int last_idx = __shfl_sync(kFull, my_idx, kTopK - 1);
     const float last_lb = __shfl_sync(kFull, my_lb, kTopK - 1);
-    const bool done = !certify || last_idx < 0 || best <= last_lb - tq;
+    const bool done = certify != 1 || last_idx < 0 || best <= last_lb - tq;
     if (lane == 0) {
         if (done) {
             nn_out[q] = best_n;
@@ -261,7 +264,17 @@ __global__ void k_resolve(const int *__restrict__ fail_list,
     }
 }
 
+__global__ void k_list_all(int *__restrict__ list, unsigned int *__restrict__ count, int Q) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) list[q] = q;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = (unsigned int)Q;
+}
+
 }  // namespace
+
+void launch_list_all(int *list, unsigned int *count, int Q, cudaStream_t st) {
+    count_launches(1);
+    k_list_all<<<std::max(1, std::min(152 * 4, ceil_div(Q, 256))), 256, 0, st>>>(list, count, Q);
+}
 
 void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qcount,
                    const int *cand_idx, const float *cand_lb, const float *tau, int certify,
