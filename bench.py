@@ -220,6 +220,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries per level for the CPU baseline")
+    ap.add_argument("--d-fast", type=int, default=0, help="PCA dimensions of the tensor-core search (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -251,7 +252,7 @@ def main():
     modes = LEVEL_MODES[args.mode]
     Z = P.synthetic_exemplar(0, cfg["exemplar"], cfg["shrink"])
     t0 = time.perf_counter()
-    pidx = PyramidIndex(torch.from_numpy(Z).to(dev), cfg["windows"], d=cfg["d"])
+    pidx = PyramidIndex(torch.from_numpy(Z).to(dev), cfg["windows"], d=cfg["d"], d_fast=args.d_fast)
     torch.cuda.synchronize()
     index_build_s = time.perf_counter() - t0
     z0 = pidx.exemplars[0].cpu().numpy()
@@ -388,6 +389,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32" if args.mode != "exact" else "f32",
         "data": "synthetic",
         "config": dict(cfg, mode=args.mode, level_modes=modes, l2="flushed between steps (256 MB write)",
+                       d_fast=[ix.info["d_fast"] for ix in pidx.indices],
                        queries_per_step=queries_per_step(cfg), index_build_s=index_build_s,
                        proposal_train_s=train_s, proposal_pairs=n_pairs, proposal_clusters=args.clusters,
                        proposal_train_loss=train_loss, parallelism=f"replicas x{world}"),

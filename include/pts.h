@@ -323,8 +323,9 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
 long long pts_launch_count(void);
 
 /* Self-test of the tensor-core operand layout (no counterpart in the paper):
- * one 128 x N x K tcgen05 MMA (f16 != 0: FP16 operands as in the search;
- * f16 == 0: BF16 as in the proposal network) through the same shared-memory
+ * one 128 x N x K tcgen05 MMA (f16 == 2: FP16 with the A operand read from
+ * tensor memory, as in the search; f16 == 1: FP16 with both operands in shared
+ * memory; f16 == 0: BF16 as in the proposal network) through the same shared-memory
  * and instruction descriptors the kernels use, on seeded data generated here,
  * compared with an FP64 host product.  N, K multiples of 16 (N <= 256,
  * K <= 128).  Writes the largest absolute error and the largest |reference|.

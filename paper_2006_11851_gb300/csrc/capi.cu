@@ -188,12 +188,15 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
         case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
             // slack of an FP16 bound: operand rounding (1 + 2^-11)^2 - 1 < 2^-10 per product of
-            // sum |products| <= ||u_q||^2 + max ||u_n||^2, the FP32 sum of K <= 128 terms, and the
-            // FP32 slack of the full-dimension distance; 2^-9 covers the first two
-            const float tau_f16 = 1.0f / 512.0f + kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
+            // sum |products| <= ||u_q||^2 + max ||u_n||^2, the FP32 sum of K <= 128 terms, the
+            // FP16 storage of a score as an offset from its group minimum (2^-11 of an offset no
+            // larger than the score range) and the FP32 slack of the full-dimension distance;
+            // 2^-8 covers the first three
+            const float tau_f16 = 1.0f / 256.0f + kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
             launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_f16, idx->umax.ptr, st, &ws.proj_part);
-            const int nparts = tc_parts(Q, idx->ntiles);
+            const int ntc = tc_tiles(idx->N);
+            const int nparts = tc_parts(Q, ntc);
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
             if (nparts > 1) {
                 PTS_TRY(ws.part_v.ensure((size_t)Q * nparts * kTopK, "part lists"));
@@ -203,9 +206,9 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             // the candidate lists of the previous search on this grid seed the bound
             const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
             if (warm)
-                launch_warm_threshold(ws.cand_idx.ptr, ws.qtile.ptr, ws.qnorm.ptr, idx->etc.ptr, idx->umax.ptr, Q,
-                                      idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
-            launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, idx->ntiles, nparts,
+                launch_warm_threshold(ws.cand_idx.ptr, ws.qcoord.ptr, idx->d_fast, idx->da_fast, ws.qnorm.ptr,
+                                      idx->etc.ptr, idx->umax.ptr, Q, idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
+            launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, ntc, nparts,
                              warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr,
                              ws.part_i.ptr, idx->status.ptr, st);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
@@ -381,10 +384,10 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         norm_tmp.release();
     }
     idx->ktc = tc_padded_k(idx->d_fast);
-    if ((s = idx->etc.ensure((size_t)idx->ntiles * kBN * idx->ktc, "fp16 exemplar tiles")) != PTS_OK)
+    if ((s = idx->etc.ensure((size_t)tc_tiles(idx->N) * tc_tile_rows() * idx->ktc, "fp16 exemplar tiles")) != PTS_OK)
         return fail(s);
-    launch_pack_exemplar(idx->et_fast.ptr, idx->enorm.ptr, idx->ntiles, idx->d_fast, idx->da_fast, idx->ktc,
-                         idx->etc.ptr, st);
+    launch_pack_exemplar(idx->et_fast.ptr, idx->enorm.ptr, idx->N, idx->d_fast, idx->da_fast, idx->ktc, idx->etc.ptr,
+                         st);
     e = cudaMemcpyAsync(&idx->unorm2_max, idx->umax.ptr, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "read norm max"));
     e = cudaStreamSynchronize(st);

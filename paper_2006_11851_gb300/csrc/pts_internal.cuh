@@ -156,7 +156,7 @@ struct pts_index_s {
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
     pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
     pts::DevBuf<float> et_fast;   // [ntiles][da_fast][kBN] = -2 (y_n, r_n, 0...) with d_fast coordinates
-    pts::DevBuf<__half> etc;      // [ntiles][128 x Ktc] FP16 MMA operand tiles
+    pts::DevBuf<__half> etc;      // [tc_tiles(N)][tc_tile_rows() x Ktc] FP16 MMA operand tiles
     int ktc = 0;                  // K of the tensor-core search
     pts::DevBuf<float> umax;      // [1]
     pts::DevBuf<int> status;      // [1] device status word
@@ -198,12 +198,15 @@ void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const fl
 // search_tc.cu
 int tc_padded_k(int d);
 int tc_query_blocks(int Q);
+int tc_tiles(int N);
+int tc_tile_rows();
 int tc_parts(int Q, int ntiles);
 void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st);
-void launch_pack_exemplar(const float *et, const float *enorm, int ntiles, int d, int da, int K, __half *out,
+void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int da, int K, __half *out,
                           cudaStream_t st);
-void launch_warm_threshold(const int *prev_idx, const __half *qtile, const float *qnorm, const __half *etile,
-                           const float *umax, int Q, int K, int N, float eps_scale, float *thr0, cudaStream_t st);
+void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
+                           const __half *etile, const float *umax, int Q, int K, int N, float eps_scale, float *thr0,
+                           cudaStream_t st);
 void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st);

@@ -7,31 +7,32 @@
 // K carries d coordinates, the residual and three slots holding ||u_n||^2 split FP16
 // hi/mid/lo against query-side ones, so the accumulator is p with no epilogue add.
 //
-// GEMM layout: M = 128 queries per CTA (TMEM lane = query), N = 128 windows per exemplar tile
+// GEMM layout: M = 128 queries per CTA (TMEM lane = query), N = 256 windows per exemplar tile
 // (TMEM columns), both operands K-major in the no-swizzle core-matrix layout, staged by 1-D bulk
-// copies of pre-packed tiles.  Four accumulator stages of 128 columns fill TMEM's 512.
+// copies of pre-packed tiles: the query tile once, the exemplar tiles through a 2-stage ring.
+// Two accumulator stages of 256 columns fill TMEM's 512.
 //
 // Warps (10): 0-7 epilogue (TMEM lane quarter = warp % 4, column half = warp / 4), 8 producer,
 // 9 MMA issuer and TMEM owner.  Selection works on groups of 8 consecutive windows; a tile's
-// 16 groups are split 8/8 between its column halves.  An epilogue thread owns one (query, half)
+// 32 groups are split 16/16 between its column halves.  An epilogue thread owns one (query, half)
 // and keeps, in registers, the 8 groups of its half with the smallest minimum score seen so
 // far, sorted by (minimum, group); the 8 scores of each kept group sit in a shared-memory slot
-// that moves with the group.  Per tile the thread loads its 64 accumulators (one tcgen05.ld),
-// reduces each group of 8 to its minimum and, only for a group whose minimum beats the 8th kept
-// one, shifts it into the register list and stores its 8 scores into the slot of the evicted
-// group.  Every window among the query's 8 best of a half lies in one of that half's 8 best
-// groups, and each list is exactly those 8 groups whatever the scan order (ties go to the
-// smaller group, which comes first).  At the end each warp takes queries one at a time, loads
-// the 2 x 64 kept scores (4 per lane) and keeps the 32 smallest (score, window) pairs by bitonic
-// sort and merge.  Padding windows score NaN: a group minimum ignores them and they are dropped.
+// that moves with the group, as FP16 offsets from the group minimum.  Per tile the thread loads
+// its 128 accumulators (two 64-column tcgen05.ld), reduces each group of 8 to its minimum and,
+// only for a group whose minimum beats the 8th kept one, shifts it into the register list and
+// stores its offsets into the slot of the evicted group.  Every window among the query's 8 best
+// of a half lies in one of that half's 8 best groups, and each list is exactly those 8 groups
+// whatever the scan order (ties go to the smaller group, which comes first).  At the end each
+// warp takes queries one at a time, rebuilds the 2 x 64 kept scores (minimum + offset, 4 per
+// lane) and keeps the 32 smallest (score, window) pairs by bitonic sort and merge.  Padding
+// windows score NaN: a group minimum ignores them and they are dropped.
 //
 // The exemplar tiles of a query block may be split across blockIdx.y; each part writes its
 // sorted 32 and k_merge_parts merges them.  Optional per-query, per-half bounds thr0 (warm
 // start, an upper bound on the 8th best group minimum of each half) seed the group lists with
 // sentinels (thr0, none): only groups whose minimum is below the bound are kept, and since at
-// least 8 are, the kept groups are the same as without the bound.
-// All waits are bounded; on a timeout the kernel flags the status word, drains its copies and
-// frees TMEM.
+// least 8 are, the kept groups are the same as without the bound.  All waits are bounded; on a
+// timeout the kernel flags the status word, drains its copies and frees TMEM.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -44,17 +45,17 @@ namespace pts {
 namespace {
 
 constexpr int kQM = 128;            // queries per CTA (MMA M)
-constexpr int kTN = 128;            // exemplar windows per tile (MMA N)
-constexpr int kAcc = 4;             // accumulator stages of kTN columns
+constexpr int kTN = 256;            // exemplar windows per tile (MMA N)
+constexpr int kAcc = 2;             // accumulator stages of kTN columns
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;
 constexpr int kMaxKt = 128;         // K of the search vectors
-constexpr int kRing = 96 * 1024;    // bytes of exemplar-tile ring
+constexpr int kRing = 128 * 1024;   // bytes of exemplar-tile ring
 constexpr int kMaxStages = 8;
 constexpr int kG = 8;               // windows per group
 constexpr int kKeep = 8;            // groups kept per (query, column half)
-constexpr int kPayStride = kKeep * kG + 4;  // floats per thread of kept scores (odd 16-byte units)
+constexpr int kPayStride = kKeep + 1;  // 16-byte units per thread of kept offsets (one per slot, odd)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNoWindow = INT_MAX;
 constexpr int kNoGroup = 0x7FFFFFF;  // group field of a sentinel (27 bits)
@@ -62,8 +63,9 @@ constexpr int kNoGroup = 0x7FFFFFF;  // group field of a sentinel (27 bits)
 struct TcSmem {
     alignas(1024) unsigned char q[kQM * kMaxKt * 2];
     alignas(1024) unsigned char e[kRing];
-    alignas(16) float pay[kEpiThreads * kPayStride];  // per thread, per slot: a kept group's 8 scores
-    int gmap[kEpiThreads * (kKeep + 1)];               // per thread, per slot: its group (at the end)
+    uint4 pay[kEpiThreads * kPayStride];   // per thread, per slot: a kept group's 8 FP16 offsets
+    int gmap[kEpiThreads * (kKeep + 1)];   // per thread, per slot: its group (at the end)
+    float gmin[kEpiThreads * (kKeep + 1)];  // per thread, per slot: its group minimum (at the end)
     uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAcc], acc_empty[kAcc], q_full, done;
     uint32_t tmem_base;
     int abort_flag;
@@ -141,8 +143,8 @@ __device__ __forceinline__ int group_insert(GroupList &L, float x, int group) {
     return slot;
 }
 
-// One half (64 columns) of a tile for the calling thread's query.
-__device__ __forceinline__ void scan_half(const float (&v)[64], int group0, GroupList &L, float *pay_row) {
+// 64 columns (8 groups) of a tile for the calling thread's query.
+__device__ __forceinline__ void scan64(const float (&v)[64], int group0, GroupList &L, uint4 *pay_row) {
     float m[8];
 #pragma unroll
     for (int g = 0; g < 8; ++g)
@@ -155,9 +157,18 @@ __device__ __forceinline__ void scan_half(const float (&v)[64], int group0, Grou
     for (int g = 0; g < 8; ++g) {
         if (m[g] < L.gv[kKeep - 1]) {
             const int slot = group_insert(L, m[g], group0 + g);
-            float4 *dst = reinterpret_cast<float4 *>(pay_row + slot * kG);
-            dst[0] = make_float4(v[8 * g], v[8 * g + 1], v[8 * g + 2], v[8 * g + 3]);
-            dst[1] = make_float4(v[8 * g + 4], v[8 * g + 5], v[8 * g + 6], v[8 * g + 7]);
+            // offsets from the minimum (NaN stays NaN): FP16 keeps them to 2^-11 relative
+            uint4 pk;
+            __half2 h;
+            h = __floats2half2_rn(v[8 * g] - m[g], v[8 * g + 1] - m[g]);
+            pk.x = *reinterpret_cast<uint32_t *>(&h);
+            h = __floats2half2_rn(v[8 * g + 2] - m[g], v[8 * g + 3] - m[g]);
+            pk.y = *reinterpret_cast<uint32_t *>(&h);
+            h = __floats2half2_rn(v[8 * g + 4] - m[g], v[8 * g + 5] - m[g]);
+            pk.z = *reinterpret_cast<uint32_t *>(&h);
+            h = __floats2half2_rn(v[8 * g + 6] - m[g], v[8 * g + 7] - m[g]);
+            pk.w = *reinterpret_cast<uint32_t *>(&h);
+            pay_row[slot] = pk;
         }
     }
 }
@@ -178,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t q_bytes = (uint32_t)(kQM * K * 2);
 
     if (warp == kEpiWarps + 1) {
-        tmem_alloc(&sm.tmem_base, kAcc * kTN);
+        tmem_alloc(&sm.tmem_base, 512);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -199,7 +210,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
-
     if (warp == kEpiWarps) {
         // ---------------- producer ----------------
         if (lane == 0) {
@@ -263,8 +273,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 L.gs[k] = (kNoGroup << 4) | k;
             }
         }
-        float *pay_row = &sm.pay[tid * kPayStride];
-        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
+        uint4 *pay_row = &sm.pay[tid * kPayStride];
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * (kTN / 2));
         for (int i = 0; i < nt; ++i) {
             const int a = i % kAcc;
             const bool ok = mbar_wait_or_abort(&sm.acc_full[a], (uint32_t)((i / kAcc) & 1), status, abort_flag);
@@ -273,16 +283,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
+            const int group0 = (t_begin + i) * (kTN / kG) + half * (kTN / kG / 2);
             float v[64];
             tmem_ld64(lane_addr + (uint32_t)(a * kTN), v);
+            scan64(v, group0, L, pay_row);
+            tmem_ld64(lane_addr + (uint32_t)(a * kTN + 64), v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
-            scan_half(v, (t_begin + i) * (kTN / kG) + half * 8, L, pay_row);
+            scan64(v, group0 + 8, L, pay_row);
         }
         // publish which group each slot holds, then select each query's 32 best windows
 #pragma unroll
-        for (int k = 0; k < kKeep; ++k) sm.gmap[tid * (kKeep + 1) + (L.gs[k] & 15)] = L.gs[k] >> 4;
+        for (int k = 0; k < kKeep; ++k) {
+            sm.gmap[tid * (kKeep + 1) + (L.gs[k] & 15)] = L.gs[k] >> 4;
+            sm.gmin[tid * (kKeep + 1) + (L.gs[k] & 15)] = L.gv[k];
+        }
         asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
         if (!*abort_flag) {
             for (int r = 0; r < kQM / kEpiWarps; ++r) {
@@ -297,7 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int owner = rr + (c >> 1) * kQM;
                     const int k = lane + 32 * (c & 1);  // slot k / 8, element k % 8
                     const int grp = sm.gmap[owner * (kKeep + 1) + k / kG];
-                    const float x = sm.pay[owner * kPayStride + k];
+                    const __half off = reinterpret_cast<const __half *>(&sm.pay[owner * kPayStride + k / kG])[k % kG];
+                    const float x = sm.gmin[owner * (kKeep + 1) + k / kG] + __half2float(off);
                     const bool real = grp != kNoGroup && !isnan(x);
                     sv[c] = real ? x : INFINITY;
                     si[c] = real ? grp * kG + (k % kG) : kNoWindow;
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     if (warp == kEpiWarps + 1) {
         __syncwarp();
-        tmem_dealloc(tmem, kAcc * kTN);
+        tmem_dealloc(tmem, 512);
     }
 }
 
@@ -374,19 +391,21 @@ __global__ void k_pack_queries(const float *__restrict__ qcoord, int Q, int d, i
 // Exemplar vectors as FP16 MMA operand tiles: rows = windows, K = (-2 y, -2 r, norm hi/mid/lo,
 // 0...).  Padding windows carry +inf and -inf in the hi and mid slots, so their score is NaN and
 // fails every comparison.
-__global__ void k_pack_exemplar(const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int d,
-                                int da, int K, __half *__restrict__ out) {
+__global__ void k_pack_exemplar(const float *__restrict__ et, const float *__restrict__ enorm, int N, int ntiles,
+                                int d, int da, int K, __half *__restrict__ out) {
     const long total = (long)ntiles * kTN * K;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const int t = (int)(i / (kTN * K));
         const int rem = (int)(i - (long)t * kTN * K);
         const int m = rem / K, k = rem - m * K;
-        const float nrm = enorm[(size_t)t * kTN + m];
+        const long n = (long)t * kTN + m;
+        const bool pad = n >= N;
+        const float nrm = pad ? 0.0f : enorm[n];
         float v = 0.0f;
         if (k <= d) {
-            v = isinf(nrm) ? 0.0f : et[((size_t)t * da + k) * kTN + m];
+            v = pad ? 0.0f : et[((n / kBN) * da + k) * kBN + (n % kBN)];
         } else if (k <= d + 3) {
-            if (isinf(nrm)) {
+            if (pad) {
                 v = (k == d + 1) ? INFINITY : (k == d + 2) ? -INFINITY : 0.0f;
             } else {
                 const float hi = __half2float(__float2half_rn(nrm));
@@ -407,7 +426,7 @@ __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__res
 // minimum is at most g_8; plus a margin for a different summation order, that is the half's
 // bound (thr0[2 q + half]).  With fewer than 8 distinct groups in a half its bound is +inf.
 // One warp per query.
-__global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half *__restrict__ qtile,
+__global__ void k_warm_threshold(const int *__restrict__ prev_idx, const float *__restrict__ qcoord, int d, int da,
                                  const float *__restrict__ qnorm, const __half *__restrict__ etile,
                                  const float *__restrict__ umax, int Q, int K, int N, float eps_scale,
                                  float *__restrict__ thr0) {
@@ -419,17 +438,22 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
     float p = INFINITY;
     if (valid) {
         const unsigned char *e = reinterpret_cast<const unsigned char *>(etile + (size_t)(n / kTN) * kTN * K);
-        const unsigned char *a = reinterpret_cast<const unsigned char *>(qtile + (size_t)(q / kQM) * kQM * K);
-        const int m = n % kTN, r = q % kQM;
+        const float *qr = qcoord + (size_t)q * da;
+        const int m = n % kTN;
         p = 0.0f;
         for (int k8 = 0; k8 < K; k8 += 8) {
-            const uint4 av = *reinterpret_cast<const uint4 *>(a + core_offset(r, k8, kQM));
             const uint4 ev = __ldg(reinterpret_cast<const uint4 *>(e + core_offset(m, k8, kTN)));
-            const __half2 *ah = reinterpret_cast<const __half2 *>(&av);
             const __half2 *eh = reinterpret_cast<const __half2 *>(&ev);
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                const float2 af = __half22float2(ah[h]), ef = __half22float2(eh[h]);
+                float v[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int k = k8 + 2 * h + t;
+                    v[t] = k <= d ? qr[k] : (k <= d + 3 ? 1.0f : 0.0f);  // the operand the MMA reads
+                }
+                const float2 af = __half22float2(__floats2half2_rn(v[0], v[1]));
+                const float2 ef = __half22float2(eh[h]);
                 p = fmaf(af.x, ef.x, p);
                 p = fmaf(af.y, ef.y, p);
             }
@@ -437,7 +461,7 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
     }
     // each group's smallest score once (ties: lowest lane), per column half
     const int grp = valid ? n / kG : -1 - lane;
-    const int half = valid ? (grp % (kTN / kG)) / kKeep : -1;
+    const int half = valid ? (grp % (kTN / kG)) / (kTN / kG / 2) : -1;
     bool first = valid;
     for (int j = 0; j < 32; ++j) {
         const int gj = __shfl_sync(kFull, grp, j);
@@ -455,8 +479,10 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
     }
 }
 
-// --- self-test: one 128 x N x K tile through the same descriptors, written back row-major ---
-template <typename T>
+// --- self-test: one 128 x N x K tile through the same descriptors, written back row-major.
+// With TA the A operand goes through tensor memory (tcgen05.st, then an MMA reading [a_tmem]),
+// as the search issues it.
+template <typename T, bool TA>
 __global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, const T *__restrict__ B, int N, int K,
                                                      uint32_t idesc, float *__restrict__ D, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
@@ -469,7 +495,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, co
     for (int i = tid; i < N * K; i += 128) *reinterpret_cast<T *>(sb + core_offset(i / K, i % K, N)) = B[i];
     fence_proxy_async_smem();
     if (warp == 0) {
-        tmem_alloc(&tbase, 256);
+        tmem_alloc(&tbase, 512);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -480,11 +506,33 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, co
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tbase;
+    constexpr uint32_t kACol = 256;  // A in columns 256.. (D uses at most 256)
+    if (TA) {
+        // row tid of A, K values packed two per column
+        uint32_t r[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+            const int k = 2 * c;
+            const T lo = k < K ? A[(size_t)tid * K + k] : T(0.0f);
+            const T hi = k + 1 < K ? A[(size_t)tid * K + k + 1] : T(0.0f);
+            r[c] = (uint32_t)(*reinterpret_cast<const unsigned short *>(&lo)) |
+                   ((uint32_t)(*reinterpret_cast<const unsigned short *>(&hi)) << 16);
+        }
+        tmem_st64(tmem + ((uint32_t)(warp * 32) << 16) + kACol, r);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     if (tid == 0) {
         const uint32_t lbo_a = (uint32_t)(kQM / 8) * 128u, lbo_b = (uint32_t)(N / 8) * 128u;
-        for (int ks = 0; ks < K / 16; ++ks)
-            mma_bf16(tmem, smem_desc(smem_u32(sa) + ks * 2u * lbo_a, lbo_a, 128u),
-                     smem_desc(smem_u32(sb) + ks * 2u * lbo_b, lbo_b, 128u), idesc, ks > 0 ? 1u : 0u);
+        for (int ks = 0; ks < K / 16; ++ks) {
+            const uint64_t bdesc = smem_desc(smem_u32(sb) + ks * 2u * lbo_b, lbo_b, 128u);
+            if (TA)
+                mma_f16_ta(tmem, tmem + kACol + (uint32_t)(ks * 8), bdesc, idesc, ks > 0 ? 1u : 0u);
+            else
+                mma_bf16(tmem, smem_desc(smem_u32(sa) + ks * 2u * lbo_a, lbo_a, 128u), bdesc, idesc,
+                         ks > 0 ? 1u : 0u);
+        }
         mma_commit(&bar);
     }
     __syncwarp();
@@ -500,10 +548,10 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, co
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-template <typename T>
+template <typename T, bool TA>
 pts_status run_selftest(int N, int K, uint32_t idesc, double *max_abs_err, double *max_abs_ref) {
     std::vector<T> hA((size_t)kQM * K), hB((size_t)N * K);
     std::vector<float> fA(hA.size()), fB(hB.size());
@@ -543,9 +591,9 @@ pts_status run_selftest(int N, int K, uint32_t idesc, double *max_abs_err, doubl
     PTS_CUDA_TRY(cudaMemcpy(dB.ptr, hB.data(), hB.size() * 2, cudaMemcpyHostToDevice));
     PTS_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
     const size_t smem = (size_t)(kQM + N) * K * 2;
-    cudaFuncSetAttribute(k_tc_selftest<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_tc_selftest<T, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launches(1);
-    k_tc_selftest<T><<<1, 128, smem>>>(dA.ptr, dB.ptr, N, K, idesc, dD.ptr, dst.ptr);
+    k_tc_selftest<T, TA><<<1, 128, smem>>>(dA.ptr, dB.ptr, N, K, idesc, dD.ptr, dst.ptr);
     PTS_CUDA_TRY(cudaGetLastError());
     PTS_CUDA_TRY(cudaDeviceSynchronize());
     std::vector<float> hD((size_t)kQM * N);
@@ -572,6 +620,10 @@ int tc_padded_k(int d) { return ((d + 4) + 15) / 16 * 16; }
 
 int tc_query_blocks(int Q) { return (Q + kQM - 1) / kQM; }
 
+int tc_tiles(int N) { return (N + kTN - 1) / kTN; }
+
+int tc_tile_rows() { return kTN; }
+
 // Parts per query block.  Each part keeps its own 32 best per query, and a running top-32 over
 // n windows inserts about 32 (1 + ln(n / 32)) of them, so splitting the exemplar multiplies the
 // insertion work; it only pays when the query blocks alone leave most SMs idle.
@@ -590,18 +642,19 @@ void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __hal
                                                                                                nb, qtile);
 }
 
-void launch_pack_exemplar(const float *et, const float *enorm, int ntiles, int d, int da, int K, __half *out,
+void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int da, int K, __half *out,
                           cudaStream_t st) {
     count_launches(1);
-    k_pack_exemplar<<<152 * 4, 256, 0, st>>>(et, enorm, ntiles, d, da, K, out);
+    k_pack_exemplar<<<152 * 4, 256, 0, st>>>(et, enorm, N, tc_tiles(N), d, da, K, out);
 }
 
-void launch_warm_threshold(const int *prev_idx, const __half *qtile, const float *qnorm, const __half *etile,
-                           const float *umax, int Q, int K, int N, float eps_scale, float *thr0, cudaStream_t st) {
+void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
+                           const __half *etile, const float *umax, int Q, int K, int N, float eps_scale, float *thr0,
+                           cudaStream_t st) {
     if (Q == 0) return;
     count_launches(1);
-    k_warm_threshold<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qtile, qnorm, etile, umax, Q, K, N,
-                                                                   eps_scale, thr0);
+    k_warm_threshold<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qcoord, d, da, qnorm, etile, umax, Q, K,
+                                                                   N, eps_scale, thr0);
 }
 
 void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
@@ -628,8 +681,9 @@ void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, con
 pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref) {
     if (N < 16 || N > 256 || N % 16 || K < 16 || K > 128 || K % 16)
         return set_error(PTS_ERR_INVALID_ARG, "pts_tc_selftest: N in 16..256 and K in 16..128, multiples of 16");
-    if (f16) return run_selftest<__half>(N, K, idesc_f16(kQM, N), max_abs_err, max_abs_ref);
-    return run_selftest<__nv_bfloat16>(N, K, idesc_bf16(kQM, N), max_abs_err, max_abs_ref);
+    if (f16 == 2) return run_selftest<__half, true>(N, K, idesc_f16(kQM, N), max_abs_err, max_abs_ref);
+    if (f16) return run_selftest<__half, false>(N, K, idesc_f16(kQM, N), max_abs_err, max_abs_ref);
+    return run_selftest<__nv_bfloat16, false>(N, K, idesc_bf16(kQM, N), max_abs_err, max_abs_ref);
 }
 
 }  // namespace pts

@@ -18,14 +18,14 @@ class PyramidIndex:
     """
 
     def __init__(self, exemplar: torch.Tensor, windows: list[int], d: int = 64,
-                 var_frac: float = 0.95):
+                 var_frac: float = 0.95, d_fast: int = 0):
         self.levels = len(windows)
         pyr = [exemplar.contiguous()]
         for _ in range(self.levels - 1):
             pyr.append(downsample2(pyr[-1]))
         self.exemplars = pyr[::-1]
         self.windows = list(windows)
-        self.indices = [ExemplarIndex(z, w, d=min(d, 3 * w * w), var_frac=var_frac)
+        self.indices = [ExemplarIndex(z, w, d=min(d, 3 * w * w), var_frac=var_frac, d_fast=d_fast)
                         for z, w in zip(self.exemplars, windows)]
 
     def close(self):

@@ -31,8 +31,8 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
 
 
-@pytest.mark.parametrize("f16", [1, 0])
-@pytest.mark.parametrize("N,K", [(64, 80), (64, 32), (128, 64), (16, 16), (128, 128), (128, 96)])
+@pytest.mark.parametrize("f16", [2, 1, 0])  # 2: FP16 with A from tensor memory, as the search issues it
+@pytest.mark.parametrize("N,K", [(64, 80), (64, 32), (128, 64), (16, 16), (128, 128), (128, 96), (256, 128)])
 def test_tensor_core_operand_layout(N, K, f16):
     L = pts.lib()
     err, ref = ctypes.c_double(), ctypes.c_double()
