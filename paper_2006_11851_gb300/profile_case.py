@@ -1,6 +1,8 @@
-"""Runs E-steps of one level of the benchmark workload, for profiling a kernel in isolation.
+"""Runs E-steps of one level of the benchmark workload, for profiling a kernel in isolation,
+or (--pyramid) whole coarse-to-fine syntheses with a search mode per level.
 
     python -m paper_2006_11851_gb300.profile_case --level 2 --mode exact --steps 2
+    python -m paper_2006_11851_gb300.profile_case --pyramid --modes exact,f16,f16 --steps 2
 
 Levels follow the 3-level workload (256x256 exemplar, shrink 4; windows 32/16/8; outputs
 128/256/512, d = 64).  The output image is a seeded random-patch initialisation.  Prints the
@@ -28,7 +30,11 @@ def main() -> int:
     ap.add_argument("--mode", default="exact")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--d", type=int, default=64)
+    ap.add_argument("--pyramid", action="store_true")
+    ap.add_argument("--modes", default="exact,f16,f16")
     args = ap.parse_args()
+    if args.pyramid:
+        return run_pyramid(args)
     He, w, Ho = LEVELS[args.level]
     dev = torch.device("cuda:0")
     Z = P.synthetic_exemplar(0, 256, 4.0)
@@ -45,6 +51,25 @@ def main() -> int:
         e1.synchronize()
         print(f"step {s}: {e0.elapsed_time(e1):.3f} ms  {idx.search_stats()}")
     idx.close()
+    return 0
+
+
+def run_pyramid(args) -> int:
+    from paper_2006_11851_gb300.pyramid import PyramidIndex, synthesize_pyramid
+    dev = torch.device("cuda:0")
+    Z = P.synthetic_exemplar(0, 256, 4.0)
+    pidx = PyramidIndex(torch.from_numpy(Z).to(dev), [w for _, w, _ in LEVELS], d=args.d)
+    z0 = pidx.exemplars[0].cpu().numpy()
+    modes = args.modes.split(",")
+    for s in range(args.steps):
+        x0 = torch.from_numpy(P.random_patch_init(z0, LEVELS[0][2], LEVELS[0][2], LEVELS[0][1], s)).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, E, _ = synthesize_pyramid(pidx, x0, iters=5, mode=modes)
+        e1.record()
+        e1.synchronize()
+        print(f"synthesis {s}: {e0.elapsed_time(e1):.3f} ms  final energies {E[:, -1]}")
+    pidx.close()
     return 0
 
 
