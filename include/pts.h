@@ -208,6 +208,11 @@ pts_status pts_project_queries(pts_index index, const float *output, int Ho, int
 pts_status pts_train_proposal(pts_index index, const float *y, const int32_t *nn, const float *d2, int n,
                               const pts_proposal_params *params, double *loss_out, void *stream);
 
+/* Inspection of a trained proposal (test support, no counterpart in the paper): the number of
+ * clusters, and optionally their sizes (host, n_clusters ints) and the cluster of every exemplar
+ * window (host, N ints).  Synchronises the device.  INVALID_ARG when no proposal is trained. */
+pts_status pts_proposal_info(pts_index index, int *n_clusters, int *sizes_out, int *assign_out);
+
 /* Standalone k-means (test support, no counterpart in the paper): points device n x d float32,
  * u host k doubles in [0, 1) (k-means++ uniforms), centroids_out device k x d float32,
  * assign_out device n int32.  Returns the Lloyd iterations run in *iters_out (host, may be

@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     nn_search,
     pca_fit,
     project_queries,
+    proposal_info,
     synthesize_level,
     train_proposal,
     upsample2,

@@ -98,6 +98,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     L.pts_mlp_grad.argtypes = [_I, _vp, _vp, _vp, _I, _vp, ctypes.POINTER(_Dd), _vp]
     L.pts_gemm_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd)]
     L.pts_tc_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
+    L.pts_proposal_info.argtypes = [_vp, ctypes.POINTER(_I), _vp, _vp]
     L.pts_launch_count.restype = ctypes.c_longlong
     L.pts_profile_enable.argtypes = [_I]
     L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
@@ -296,6 +297,18 @@ def train_proposal(index: ExemplarIndex, y: torch.Tensor, nn: torch.Tensor, d2: 
     _check(lib().pts_train_proposal(index.handle, _ptr(y), _ptr(nn), _ptr(d2), n, ctypes.byref(p),
                                     loss.ctypes.data_as(ctypes.c_void_p), _stream()))
     return loss
+
+
+def proposal_info(index: ExemplarIndex):
+    """(cluster sizes [C], cluster of each exemplar window [N]) of the index's trained proposal."""
+    L = lib()
+    C = ctypes.c_int(0)
+    _check(L.pts_proposal_info(index.handle, ctypes.byref(C), None, None))
+    sizes = np.zeros(C.value, dtype=np.int32)
+    assign = np.zeros(index.N, dtype=np.int32)
+    _check(L.pts_proposal_info(index.handle, ctypes.byref(C), sizes.ctypes.data_as(ctypes.c_void_p),
+                               assign.ctypes.data_as(ctypes.c_void_p)))
+    return sizes, assign
 
 
 def kmeans(points: torch.Tensor, k: int, u: np.ndarray, iters: int = 25):

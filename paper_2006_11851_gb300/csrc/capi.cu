@@ -36,6 +36,13 @@ constexpr double kPcaPassMinVar = 0.85;
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// tau_q / (||u_q||^2 + max_n ||u_n||^2) for a bound from the FP16 tensor-core search: operand
+// rounding (1 + 2^-11)^2 - 1 < 2^-10 per product of sum |products| <= ||u_q||^2 + max ||u_n||^2,
+// the FP32 sum of K <= 128 terms, the FP16 storage of a kept score as an offset from its group
+// minimum (2^-11 of an offset no larger than the score range), and the FP32 slack of the
+// full-dimension distance; 2^-8 covers the first three.
+float f16_slack(pts_index idx) { return 1.0f / 256.0f + kTauC * sqrtf((float)idx->D) * 5.9604645e-8f; }
+
 pts_status check_grid(int H, int W, int w, int stride, const char *what) {
     if (stride != 1 && stride != 2 && stride != 4)
         return set_error(PTS_ERR_INVALID_ARG, std::string(what) + ": stride must be 1, 2 or 4");
@@ -115,9 +122,8 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     Workspace &ws = idx->ws;
     ProposalState &pr = idx->prop;
     if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no proposal trained on this index");
-    const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
     launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
-                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st, &ws.proj_part);
+                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
     PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
     PTS_TRY(pr.mlp.ensure(pr.C, std::min(Q, kMlpChunk), st));
     for (int q0 = 0; q0 < Q; q0 += kMlpChunk) {
@@ -136,8 +142,15 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
                   ws.fail_list.ptr, ws.counters.ptr + 3, ws.best64.ptr, idx->status.ptr, st);
     launch_fallback(nn_out, d2_out, Q, pr.assign.ptr, pr.median.ptr, pr.factor, idx->N, ws.fail_list.ptr,
                     ws.counters.ptr + 0, st);
-    PTS_TRY(exact_on_list(idx, ra, ws.counters.ptr + 0, ws.counters.ptr + 1, ws.counters.ptr + 2, nn_out, d2_out,
-                          st));
+    // the fallback: the FP16 tensor-core search over every window for the listed queries
+    PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
+    launch_pack_queries(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->ktc, ws.qtile.ptr, st, ws.fail_list.ptr,
+                        ws.counters.ptr + 0);
+    launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, tc_tiles(idx->N), 1, nullptr,
+                     ws.cand_idx.ptr, ws.cand_lb.ptr, nullptr, nullptr, idx->status.ptr, st, ws.fail_list.ptr,
+                     ws.counters.ptr + 0);
+    launch_rerank(ra, ws.fail_list.ptr, ws.counters.ptr + 0, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out,
+                  d2_out, ws.fail2_list.ptr, ws.counters.ptr + 1, ws.best64.ptr, idx->status.ptr, st);
     return PTS_OK;
 }
 
@@ -187,14 +200,8 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             break;
         case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
-            // slack of an FP16 bound: operand rounding (1 + 2^-11)^2 - 1 < 2^-10 per product of
-            // sum |products| <= ||u_q||^2 + max ||u_n||^2, the FP32 sum of K <= 128 terms, the
-            // FP16 storage of a score as an offset from its group minimum (2^-11 of an offset no
-            // larger than the score range) and the FP32 slack of the full-dimension distance;
-            // 2^-8 covers the first three
-            const float tau_f16 = 1.0f / 256.0f + kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
             launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
-                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_f16, idx->umax.ptr, st, &ws.proj_part);
+                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
             const int nparts = tc_parts(Q, ntc);
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
@@ -568,6 +575,18 @@ pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int W
                    ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
     PTS_CUDA_TRY(cudaMemcpy2DAsync(y_out, sizeof(float) * idx->d, ws.qcoord.ptr, sizeof(float) * idx->da,
                                    sizeof(float) * idx->d, Q, cudaMemcpyDeviceToDevice, st));
+    return PTS_OK;
+}
+
+pts_status pts_proposal_info(pts_index idx, int *n_clusters, int *sizes_out, int *assign_out) {
+    if (!idx || !n_clusters) return set_error(PTS_ERR_INVALID_ARG, "pts_proposal_info: null pointer");
+    ProposalState &pr = idx->prop;
+    if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "pts_proposal_info: no proposal trained on this index");
+    PTS_CUDA_TRY(cudaSetDevice(idx->device));
+    *n_clusters = pr.C;
+    PTS_CUDA_TRY(cudaDeviceSynchronize());
+    if (sizes_out) PTS_CUDA_TRY(cudaMemcpy(sizes_out, pr.counts.ptr, sizeof(int) * pr.C, cudaMemcpyDeviceToHost));
+    if (assign_out) PTS_CUDA_TRY(cudaMemcpy(assign_out, pr.assign.ptr, sizeof(int) * idx->N, cudaMemcpyDeviceToHost));
     return PTS_OK;
 }
 

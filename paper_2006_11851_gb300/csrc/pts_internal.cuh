@@ -201,7 +201,8 @@ int tc_query_blocks(int Q);
 int tc_tiles(int N);
 int tc_tile_rows();
 int tc_parts(int Q, int ntiles);
-void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st);
+void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st,
+                         const int *qlist = nullptr, const unsigned int *qcount = nullptr);
 void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int da, int K, __half *out,
                           cudaStream_t st);
 void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
@@ -209,7 +210,7 @@ void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int 
                            cudaStream_t st);
 void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                      int *status, cudaStream_t st);
+                      int *status, cudaStream_t st, const int *qlist = nullptr, const unsigned int *qcount = nullptr);
 pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref);
 // kmeans.cu
 pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, int iters, float *C, int *assign,

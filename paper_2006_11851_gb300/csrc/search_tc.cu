@@ -176,8 +176,12 @@ __device__ __forceinline__ void scan64(const float (&v)[64], int group0, GroupLi
 __global__ void __launch_bounds__(kThreads, 1)
     k_search_tc(const __half *__restrict__ qtile, const float *__restrict__ qnorm, int Q, int K,
                 const __half *__restrict__ etile, int ntiles, int tiles_per_part, int nstages,
-                const float *__restrict__ thr0, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
+                const float *__restrict__ thr0, const int *__restrict__ qlist,
+                const unsigned int *__restrict__ qcount, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
                 float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status) {
+    // with a query list, tile row f holds query qlist[f] (f < *qcount); blocks past the list exit
+    const int nrows = qlist ? (int)min((unsigned int)Q, *qcount) : Q;
+    if ((int)blockIdx.x * kQM >= nrows) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     volatile int *abort_flag = &sm.abort_flag;
@@ -263,10 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue ----------------
         const int quarter = warp & 3, half = warp >> 2;
         const int row = quarter * 32 + lane;
-        const int q = blockIdx.x * kQM + row;
+        const int f = blockIdx.x * kQM + row;
+        const int q = f < nrows ? (qlist ? qlist[f] : f) : -1;
         GroupList L;
         {
-            const float t = q < Q ? (thr0 ? thr0[2 * (size_t)q + half] : INFINITY) : -INFINITY;
+            const float t = q >= 0 ? (thr0 ? thr0[2 * (size_t)q + half] : INFINITY) : -INFINITY;
 #pragma unroll
             for (int k = 0; k < kKeep; ++k) {
                 L.gv[k] = t;
@@ -303,8 +308,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!*abort_flag) {
             for (int r = 0; r < kQM / kEpiWarps; ++r) {
                 const int rr = warp * (kQM / kEpiWarps) + r;
-                const int qq = blockIdx.x * kQM + rr;
-                if (qq >= Q) break;
+                const int fr = blockIdx.x * kQM + rr;
+                if (fr >= nrows) break;
+                const int qq = qlist ? qlist[fr] : fr;
+                if (qq < 0 || qq >= Q) {
+                    if (lane == 0) atomicOr(status, kDevErrBounds);
+                    continue;
+                }
                 float sv[4];
                 int si[4];
 #pragma unroll
@@ -369,15 +379,18 @@ __global__ void k_merge_parts(const float *__restrict__ part_v, const int *__res
 // Query vectors as FP16 MMA operand tiles: rows = queries, K = (y, r, 1, 1, 1, 0...); rows past Q
 // are zero.  One tile of 128 queries is contiguous.
 __global__ void k_pack_queries(const float *__restrict__ qcoord, int Q, int d, int da, int K, int nblocks,
+                               const int *__restrict__ qlist, const unsigned int *__restrict__ qcount,
                                __half *__restrict__ out) {
-    const long total = (long)nblocks * kQM * K;
+    const int nrows = qlist ? (int)min((unsigned int)Q, *qcount) : Q;
+    const long total = (long)min(nblocks, (nrows + kQM - 1) / kQM) * kQM * K;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const int b = (int)(i / (kQM * K));
         const int rem = (int)(i - (long)b * kQM * K);
         const int r = rem / K, k = rem - r * K;
-        const int q = b * kQM + r;
+        const int f = b * kQM + r;
+        const int q = f < nrows ? (qlist ? qlist[f] : f) : -1;
         float v = 0.0f;
-        if (q < Q) {
+        if (q >= 0 && q < Q) {
             if (k <= d)
                 v = qcoord[(size_t)q * da + k];
             else if (k <= d + 3)
@@ -634,12 +647,13 @@ int tc_parts(int Q, int ntiles) {
     return p;
 }
 
-void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st) {
+void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st,
+                         const int *qlist, const unsigned int *qcount) {
     const int nb = tc_query_blocks(Q);
     if (nb == 0) return;
     count_launches(1);
-    k_pack_queries<<<std::min<long>(ceil_div((long)nb * kQM * K, 256), 152 * 8), 256, 0, st>>>(qcoord, Q, d, da, K,
-                                                                                               nb, qtile);
+    k_pack_queries<<<std::min<long>(ceil_div((long)nb * kQM * K, 256), 152 * 8), 256, 0, st>>>(
+        qcoord, Q, d, da, K, nb, qlist, qcount, qtile);
 }
 
 void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int da, int K, __half *out,
@@ -659,7 +673,8 @@ void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int 
 
 void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                      int *status, cudaStream_t st) {
+                      int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount) {
+    if (qlist) nparts = 1;  // a listed search writes its candidates directly
     static bool attr = false;
     const size_t smem = sizeof(TcSmem) + 1024;
     if (!attr) {
@@ -672,7 +687,7 @@ void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, con
     const int nstages = std::min(kMaxStages, kRing / (kTN * K * 2));
     ProfScope ps(kProfSearchTc, st, nparts > 1 ? 2 : 1);
     k_search_tc<<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages, thr0,
-                                                           cand_idx, cand_lb, part_v, part_i, status);
+                                                           qlist, qcount, cand_idx, cand_lb, part_v, part_i, status);
     if (nparts > 1)
         k_merge_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, Q, nparts, qnorm, cand_idx,
                                                                    cand_lb);
