@@ -69,7 +69,11 @@ typedef enum {
  *                     bound, exact FP32 full-dimension re-rank.  Not
  *                     certified: a window whose FP16-rounded bound misses the
  *                     32 best is lost.
- *   PTS_FP8_RERANK    as F16 with FP8-E4M3 operands (not available).
+ *   PTS_FP8_RERANK    as F16 with FP8-E4M3 operands (kind::f8f6f4): the exemplar
+ *                     side holds -2 y / s_j with per-dimension scales s_j =
+ *                     max_n |2 y_nj| / 448, the query y s_j / t_q with a per-row
+ *                     scale t_q; the epilogue forms ||u_n||^2 + t_q acc in FP32.
+ *                     Not certified; every candidate is re-ranked in FP32.
  *   PTS_PROPOSAL      learned cluster proposal + FP32 probe + re-rank, with
  *                     the exact search as fallback. */
 typedef enum {
@@ -328,9 +332,10 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
 long long pts_launch_count(void);
 
 /* Self-test of the tensor-core operand layout (no counterpart in the paper):
- * one 128 x N x K tcgen05 MMA (f16 == 2: FP16 with the A operand read from
- * tensor memory, as in the search; f16 == 1: FP16 with both operands in shared
- * memory; f16 == 0: BF16 as in the proposal network) through the same shared-memory
+ * one 128 x N x K tcgen05 MMA (f16 == 3: FP8 E4M3, kind::f8f6f4, K a multiple of 32;
+ * f16 == 2: FP16 with the A operand read from tensor memory; f16 == 1: FP16 with both
+ * operands in shared memory, as in the search; f16 == 0: BF16 as in the proposal
+ * network) through the same shared-memory
  * and instruction descriptors the kernels use, on seeded data generated here,
  * compared with an FP64 host product.  N, K multiples of 16 (N <= 256,
  * K <= 128).  Writes the largest absolute error and the largest |reference|.

@@ -228,8 +228,32 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
         case PTS_PROPOSAL:
             PTS_TRY(search_proposal(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
             break;
-        case PTS_FP8_RERANK:
-            return set_error(PTS_ERR_UNSUPPORTED, "nn_search: mode not available in this build");
+        case PTS_FP8_RERANK: {
+            // FP8 E4M3 operands with per-dimension scales (the epilogue adds the FP32 norms); the
+            // bound's rounding error is too large for a useful early exit, so every candidate is
+            // re-ranked
+            Workspace &ws = idx->ws;
+            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
+            const int ntc = tc_tiles(idx->N);
+            const int nparts = tc_parts(Q, ntc);
+            PTS_TRY(ws.qtile8.ensure((size_t)tc_query_blocks(Q) * 128 * idx->kf8, "fp8 query tiles"));
+            PTS_TRY(ws.qscale.ensure((size_t)std::max(Q, 1), "fp8 query scales"));
+            if (nparts > 1) {
+                PTS_TRY(ws.part_v.ensure((size_t)Q * nparts * kTopK, "part lists"));
+                PTS_TRY(ws.part_i.ensure((size_t)Q * nparts * kTopK, "part lists"));
+            }
+            launch_pack_queries_f8(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->kf8, idx->f8scale.ptr,
+                                   ws.qtile8.ptr, ws.qscale.ptr, st);
+            launch_search_tc(ws.qtile8.ptr, ws.qnorm.ptr, Q, idx->kf8, idx->etc8.ptr, ntc, nparts, nullptr,
+                             ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st,
+                             nullptr, nullptr, 1, ws.qscale.ptr, idx->enorm.ptr, idx->N);
+            RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
+                          idx->nx, idx->N, Q};
+            launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
+                          ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
+            break;
+        }
         default:
             return set_error(PTS_ERR_INVALID_ARG, "nn_search: unknown mode");
     }
@@ -395,6 +419,12 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return fail(s);
     launch_pack_exemplar(idx->et_fast.ptr, idx->enorm.ptr, idx->N, idx->d_fast, idx->da_fast, idx->ktc, idx->etc.ptr,
                          st);
+    idx->kf8 = tc_padded_k8(idx->d_fast);
+    if ((s = idx->etc8.ensure((size_t)tc_tiles(idx->N) * tc_tile_rows() * idx->kf8, "fp8 exemplar tiles")) != PTS_OK)
+        return fail(s);
+    if ((s = idx->f8scale.ensure((size_t)idx->d_fast + 1, "fp8 scales")) != PTS_OK) return fail(s);
+    launch_fp8_tables(idx->et_fast.ptr, idx->N, idx->d_fast, idx->da_fast, idx->kf8, idx->f8scale.ptr, idx->etc8.ptr,
+                      st);
     e = cudaMemcpyAsync(&idx->unorm2_max, idx->umax.ptr, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "read norm max"));
     e = cudaStreamSynchronize(st);

@@ -93,6 +93,8 @@ struct Workspace {
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
     DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
+    DevBuf<uint8_t> qtile8;    // [ceil(Q/128)][128 x Kf8] FP8 query operand tiles
+    DevBuf<float> qscale;      // [Q] FP8 query row scales
     DevBuf<float> proj_part;   // per-slice partial sums of a split projection
     DevBuf<float> part_v;      // [Q][parts][32] per-part candidate lists of the tensor-core search
     DevBuf<int> part_i;
@@ -157,6 +159,9 @@ struct pts_index_s {
     pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
     pts::DevBuf<float> et_fast;   // [ntiles][da_fast][kBN] = -2 (y_n, r_n, 0...) with d_fast coordinates
     pts::DevBuf<__half> etc;      // [tc_tiles(N)][tc_tile_rows() x Ktc] FP16 MMA operand tiles
+    pts::DevBuf<uint8_t> etc8;    // [tc_tiles(N)][tc_tile_rows() x Kf8] FP8 E4M3 operand tiles
+    pts::DevBuf<float> f8scale;   // [d_fast + 1] per-dimension scales of the FP8 tiles
+    int kf8 = 0;                  // K of the FP8 search
     int ktc = 0;                  // K of the tensor-core search
     pts::DevBuf<float> umax;      // [1]
     pts::DevBuf<int> status;      // [1] device status word
@@ -208,9 +213,15 @@ void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int
 void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
                            const __half *etile, const float *umax, int Q, int K, int N, float eps_scale, float *thr0,
                            cudaStream_t st);
-void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
+void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const void *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                      int *status, cudaStream_t st, const int *qlist = nullptr, const unsigned int *qcount = nullptr);
+                      int *status, cudaStream_t st, const int *qlist = nullptr, const unsigned int *qcount = nullptr,
+                      int fp8 = 0, const float *qscale = nullptr, const float *enorm = nullptr, int N = 0);
+int tc_padded_k8(int d);
+void launch_fp8_tables(const float *et, int N, int d, int da, int K, float *scale, uint8_t *out, cudaStream_t st);
+void launch_pack_queries_f8(const float *qcoord, int Q, int d, int da, int K, const float *scale, uint8_t *qtile,
+                            float *qscale, cudaStream_t st, const int *qlist = nullptr,
+                            const unsigned int *qcount = nullptr);
 pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref);
 // kmeans.cu
 pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, int iters, float *C, int *assign,

@@ -173,9 +173,36 @@ __device__ __forceinline__ void scan64(const float (&v)[64], int group0, GroupLi
     }
 }
 
+// FP8 scores: p = ||u_n||^2 + t_q acc for 64 consecutive windows from col0 (NaN past N).  The
+// norms are the same for every lane of a warp (one broadcast load each).
+__device__ __forceinline__ void fp8_finish(float (&v)[64], float tq, const float *__restrict__ enorm, int col0,
+                                           int N) {
+#pragma unroll
+    for (int j4 = 0; j4 < 16; ++j4) {
+        const int c = col0 + 4 * j4;
+        float4 e;
+        if (c + 3 < N) {
+            e = __ldg(reinterpret_cast<const float4 *>(enorm + c));
+        } else {
+            e.x = c < N ? __ldg(enorm + c) : NAN;
+            e.y = c + 1 < N ? __ldg(enorm + c + 1) : NAN;
+            e.z = c + 2 < N ? __ldg(enorm + c + 2) : NAN;
+            e.w = c + 3 < N ? __ldg(enorm + c + 3) : NAN;
+        }
+        v[4 * j4] = fmaf(tq, v[4 * j4], e.x);
+        v[4 * j4 + 1] = fmaf(tq, v[4 * j4 + 1], e.y);
+        v[4 * j4 + 2] = fmaf(tq, v[4 * j4 + 2], e.z);
+        v[4 * j4 + 3] = fmaf(tq, v[4 * j4 + 3], e.w);
+    }
+}
+
+// EB = operand bytes: 2 for FP16 (kind::f16, the norms ride in K), 1 for FP8 E4M3
+// (kind::f8f6f4, per-dimension scales; the epilogue forms p = ||u_n||^2 + t_q acc).
+template <int EB>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_search_tc(const __half *__restrict__ qtile, const float *__restrict__ qnorm, int Q, int K,
-                const __half *__restrict__ etile, int ntiles, int tiles_per_part, int nstages,
+    k_search_tc(const void *__restrict__ qtile, const float *__restrict__ qnorm, int Q, int K,
+                const void *__restrict__ etile, int ntiles, int tiles_per_part, int nstages,
+                const float *__restrict__ qscale, const float *__restrict__ enorm, int N,
                 const float *__restrict__ thr0, const int *__restrict__ qlist,
                 const unsigned int *__restrict__ qcount, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
                 float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status) {
@@ -189,8 +216,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nparts = gridDim.y, part = blockIdx.y;
     const int t_begin = part * tiles_per_part;
     const int nt = max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
-    const uint32_t stage_bytes = (uint32_t)(kTN * K * 2);
-    const uint32_t q_bytes = (uint32_t)(kQM * K * 2);
+    const uint32_t stage_bytes = (uint32_t)(kTN * K * EB);
+    const uint32_t q_bytes = (uint32_t)(kQM * K * EB);
+    const unsigned char *qtile_b = static_cast<const unsigned char *>(qtile);
+    const unsigned char *etile_b = static_cast<const unsigned char *>(etile);
 
     if (warp == kEpiWarps + 1) {
         tmem_alloc(&sm.tmem_base, 512);
@@ -218,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- producer ----------------
         if (lane == 0) {
             mbar_expect_tx(&sm.q_full, q_bytes);
-            bulk_g2s(sm.q, qtile + (size_t)blockIdx.x * kQM * K, q_bytes, &sm.q_full);
+            bulk_g2s(sm.q, qtile_b + (size_t)blockIdx.x * q_bytes, q_bytes, &sm.q_full);
             int issued = 0;
             for (int i = 0; i < nt; ++i) {
                 const int s = i % nstages;
@@ -226,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     !mbar_wait_or_abort(&sm.empty[s], (uint32_t)(((i / nstages) - 1) & 1), status, abort_flag))
                     break;
                 mbar_expect_tx(&sm.full[s], stage_bytes);
-                bulk_g2s(sm.e + (size_t)s * stage_bytes, etile + (size_t)(t_begin + i) * kTN * K, stage_bytes,
+                bulk_g2s(sm.e + (size_t)s * stage_bytes, etile_b + (size_t)(t_begin + i) * stage_bytes, stage_bytes,
                          &sm.full[s]);
                 issued = i + 1;
             }
@@ -238,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kEpiWarps + 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16(kQM, kTN);
+            const uint32_t idesc = EB == 2 ? idesc_f16(kQM, kTN) : idesc_e4m3(kQM, kTN);
             const uint32_t lbo_q = (uint32_t)(kQM / 8) * 128u, lbo_e = (uint32_t)(kTN / 8) * 128u;
             const uint32_t qaddr = smem_u32(sm.q);
             bool ok = mbar_wait_or_abort(&sm.q_full, 0, status, abort_flag);
@@ -251,10 +280,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t eaddr = smem_u32(sm.e + (size_t)s * stage_bytes);
                 const uint32_t dcol = tmem + (uint32_t)(a * kTN);
-                for (int ks = 0; ks < K / 16; ++ks) {
+                // one instruction per 32 bytes of K (16 FP16 or 32 FP8 values): two core-matrix columns
+                for (int ks = 0; ks < K * EB / 32; ++ks) {
                     const uint64_t adesc = smem_desc(qaddr + ks * 2u * lbo_q, lbo_q, 128u);
                     const uint64_t bdesc = smem_desc(eaddr + ks * 2u * lbo_e, lbo_e, 128u);
-                    mma_bf16(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
+                    if constexpr (EB == 2)
+                        mma_bf16(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
+                    else
+                        mma_f8(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
                 }
                 mma_commit(&sm.empty[s]);
                 mma_commit(&sm.acc_full[a]);
@@ -279,6 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         uint4 *pay_row = &sm.pay[tid * kPayStride];
+        const float tq = (EB == 1 && q >= 0) ? qscale[q] : 0.0f;
         const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * (kTN / 2));
         for (int i = 0; i < nt; ++i) {
             const int a = i % kAcc;
@@ -289,13 +323,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const int group0 = (t_begin + i) * (kTN / kG) + half * (kTN / kG / 2);
+            const int col0 = group0 * kG;
             float v[64];
             tmem_ld64(lane_addr + (uint32_t)(a * kTN), v);
+            if constexpr (EB == 1) fp8_finish(v, tq, enorm, col0, N);
             scan64(v, group0, L, pay_row);
             tmem_ld64(lane_addr + (uint32_t)(a * kTN + 64), v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
+            if constexpr (EB == 1) fp8_finish(v, tq, enorm, col0 + 64, N);
             scan64(v, group0 + 8, L, pay_row);
         }
         // publish which group each slot holds, then select each query's 32 best windows
@@ -432,6 +469,64 @@ __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__res
     }
 }
 
+// FP8 operands (E4M3, saturating).  Per search dimension j (coordinates and the residual) the
+// exemplar side stores -2 y_nj / s_j with s_j = max_n |2 y_nj| / 448; the query absorbs s_j and a
+// per-row scale t_q = max_j |y_qj s_j| / 448, so acc = sum_j q_j e_j = -2 (y_q . y_n + r_q r_n) / t_q.
+__global__ void k_fp8_dim_scale(const float *__restrict__ et, int N, int d, int da, float *__restrict__ scale) {
+    const int j = blockIdx.x;  // 0..d (coordinates, then the residual)
+    float m = 0.0f;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) m = fmaxf(m, fabsf(et[((size_t)(n / kBN) * da + j) * kBN + (n % kBN)]));
+    __shared__ float red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scale[j] = red[0] > 0.0f ? red[0] / 448.0f : 1.0f;
+}
+
+__global__ void k_pack_exemplar_f8(const float *__restrict__ et, int N, int ntiles, int d, int da, int K,
+                                   const float *__restrict__ scale, uint8_t *__restrict__ out) {
+    const long total = (long)ntiles * kTN * K;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(i / (kTN * K));
+        const int rem = (int)(i - (long)t * kTN * K);
+        const int m = rem / K, k = rem - m * K;
+        const long n = (long)t * kTN + m;
+        float v = 0.0f;
+        if (n < N && k <= d) v = et[((n / kBN) * da + k) * kBN + (n % kBN)] / scale[k];
+        const __nv_fp8_e4m3 h(v);
+        out[(size_t)t * kTN * K + core_offset8(m, k, kTN)] = *reinterpret_cast<const uint8_t *>(&h);
+    }
+}
+
+// one warp per query row of the FP8 query tiles (rows past the list or Q are zero)
+__global__ void k_pack_queries_f8(const float *__restrict__ qcoord, int Q, int d, int da, int K, int nblocks,
+                                  const float *__restrict__ scale, const int *__restrict__ qlist,
+                                  const unsigned int *__restrict__ qcount, uint8_t *__restrict__ out,
+                                  float *__restrict__ qscale) {
+    const int nrows = qlist ? (int)min((unsigned int)Q, *qcount) : Q;
+    const int lane = threadIdx.x & 31;
+    const long f = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= (long)nblocks * kQM) return;
+    const int q = f < nrows ? (qlist ? qlist[f] : (int)f) : -1;
+    const bool ok = q >= 0 && q < Q;
+    float m = 0.0f;
+    for (int k = lane; k <= d; k += 32) m = ok ? fmaxf(m, fabsf(qcoord[(size_t)q * da + k] * scale[k])) : m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    const float tq = m > 0.0f ? m / 448.0f : 1.0f;
+    const int b = (int)(f / kQM), r = (int)(f % kQM);
+    for (int k = lane; k < K; k += 32) {
+        float v = 0.0f;
+        if (ok && k <= d) v = qcoord[(size_t)q * da + k] * scale[k] / tq;
+        const __nv_fp8_e4m3 h(v);
+        out[(size_t)b * kQM * K + core_offset8(r, k, kQM)] = *reinterpret_cast<const uint8_t *>(&h);
+    }
+    if (ok && lane == 0) qscale[q] = tq;
+}
+
 // Warm start: the previous search's 32 windows of each query, scored in FP32 from the same FP16
 // operands the tensor cores multiply (16-byte rows of the operand layout, 8 values per load).  A
 // window's score bounds its group's minimum from above, so with g_1 <= g_2 <= ... the smallest
@@ -564,6 +659,105 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, co
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// FP8 (E4M3) variant of the self-test: bytes in the 8-bit core-matrix layout, K = 32 per MMA.
+__global__ void __launch_bounds__(128) k_tc_selftest_f8(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B,
+                                                        int N, int K, float *__restrict__ D, int *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char *sa = sm_raw;
+    unsigned char *sb = sm_raw + kQM * K;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kQM * K; i += 128) sa[core_offset8(i / K, i % K, kQM)] = A[i];
+    for (int i = tid; i < N * K; i += 128) sb[core_offset8(i / K, i % K, N)] = B[i];
+    fence_proxy_async_smem();
+    if (warp == 0) {
+        tmem_alloc(&tbase, 512);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tbase;
+    if (tid == 0) {
+        const uint32_t lbo_a = (uint32_t)(kQM / 8) * 128u, lbo_b = (uint32_t)(N / 8) * 128u;
+        for (int ks = 0; ks < K / 32; ++ks)
+            mma_f8(tmem, smem_desc(smem_u32(sa) + ks * 2u * lbo_a, lbo_a, 128u),
+                   smem_desc(smem_u32(sb) + ks * 2u * lbo_b, lbo_b, 128u), idesc_e4m3(kQM, N), ks > 0 ? 1u : 0u);
+        mma_commit(&bar);
+    }
+    __syncwarp();
+    mbar_wait_bounded(&bar, 0, status);
+    tc_fence_after();
+    for (int c = 0; c < N; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        const int row = warp * 32 + (tid & 31);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) D[(size_t)row * N + c + j] = v[j];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+pts_status run_selftest_f8(int N, int K, double *max_abs_err, double *max_abs_ref) {
+    std::vector<uint8_t> hA((size_t)kQM * K), hB((size_t)N * K);
+    std::vector<float> fA(hA.size()), fB(hB.size());
+    uint64_t z = 0x1234567ull;
+    auto nextf = [&]() {
+        z = z * 6364136223846793005ull + 1442695040888963407ull;
+        return (float)((z >> 40) & 0xFFFF) / 8192.0f - 4.0f;
+    };
+    for (size_t i = 0; i < hA.size(); ++i) {
+        const __nv_fp8_e4m3 v(nextf());
+        hA[i] = *reinterpret_cast<const uint8_t *>(&v);
+        fA[i] = (float)v;
+    }
+    for (size_t i = 0; i < hB.size(); ++i) {
+        const __nv_fp8_e4m3 v(nextf());
+        hB[i] = *reinterpret_cast<const uint8_t *>(&v);
+        fB[i] = (float)v;
+    }
+    DevBuf<uint8_t> dA, dB;
+    DevBuf<float> dD;
+    DevBuf<int> dst;
+    PTS_TRY(dA.ensure(hA.size(), "selftest A"));
+    PTS_TRY(dB.ensure(hB.size(), "selftest B"));
+    PTS_TRY(dD.ensure((size_t)kQM * N, "selftest D"));
+    PTS_TRY(dst.ensure(1, "selftest status"));
+    PTS_CUDA_TRY(cudaMemcpy(dA.ptr, hA.data(), hA.size(), cudaMemcpyHostToDevice));
+    PTS_CUDA_TRY(cudaMemcpy(dB.ptr, hB.data(), hB.size(), cudaMemcpyHostToDevice));
+    PTS_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
+    const size_t smem = (size_t)(kQM + N) * K;
+    cudaFuncSetAttribute(k_tc_selftest_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launches(1);
+    k_tc_selftest_f8<<<1, 128, smem>>>(dA.ptr, dB.ptr, N, K, dD.ptr, dst.ptr);
+    PTS_CUDA_TRY(cudaGetLastError());
+    PTS_CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<float> hD((size_t)kQM * N);
+    int hst = 0;
+    PTS_CUDA_TRY(cudaMemcpy(hD.data(), dD.ptr, hD.size() * 4, cudaMemcpyDeviceToHost));
+    PTS_CUDA_TRY(cudaMemcpy(&hst, dst.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    double err = 0.0, ref_max = 0.0;
+    for (int i = 0; i < kQM; ++i)
+        for (int j = 0; j < N; ++j) {
+            double sacc = 0.0;
+            for (int k = 0; k < K; ++k) sacc += (double)fA[(size_t)i * K + k] * fB[(size_t)j * K + k];
+            err = std::max(err, std::fabs(sacc - hD[(size_t)i * N + j]));
+            ref_max = std::max(ref_max, std::fabs(sacc));
+        }
+    *max_abs_err = err;
+    *max_abs_ref = ref_max;
+    if (hst) return set_error(PTS_ERR_TIMEOUT, "pts_tc_selftest: MMA completion wait gave up");
+    return PTS_OK;
+}
+
 template <typename T, bool TA>
 pts_status run_selftest(int N, int K, uint32_t idesc, double *max_abs_err, double *max_abs_ref) {
     std::vector<T> hA((size_t)kQM * K), hB((size_t)N * K);
@@ -671,31 +865,63 @@ void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int 
                                                                    N, eps_scale, thr0);
 }
 
-void launch_search_tc(const __half *qtile, const float *qnorm, int Q, int K, const __half *etile, int ntiles,
+void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const void *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                      int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount) {
+                      int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount, int fp8,
+                      const float *qscale, const float *enorm, int N) {
     if (qlist) nparts = 1;  // a listed search writes its candidates directly
-    static bool attr = false;
+    static bool attr[2] = {false, false};
     const size_t smem = sizeof(TcSmem) + 1024;
-    if (!attr) {
-        cudaFuncSetAttribute(k_search_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+    if (!attr[fp8 ? 1 : 0]) {
+        if (fp8)
+            cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else
+            cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr[fp8 ? 1 : 0] = true;
     }
     const int nqb = tc_query_blocks(Q);
     if (nqb == 0) return;
     const int tpp = (ntiles + nparts - 1) / nparts;
-    const int nstages = std::min(kMaxStages, kRing / (kTN * K * 2));
+    const int eb = fp8 ? 1 : 2;
+    const int nstages = std::min(kMaxStages, kRing / (kTN * K * eb));
     ProfScope ps(kProfSearchTc, st, nparts > 1 ? 2 : 1);
-    k_search_tc<<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages, thr0,
-                                                           qlist, qcount, cand_idx, cand_lb, part_v, part_i, status);
+    if (fp8)
+        k_search_tc<1><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
+                                                                  qscale, enorm, N, thr0, qlist, qcount, cand_idx,
+                                                                  cand_lb, part_v, part_i, status);
+    else
+        k_search_tc<2><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
+                                                                  qscale, enorm, N, thr0, qlist, qcount, cand_idx,
+                                                                  cand_lb, part_v, part_i, status);
     if (nparts > 1)
         k_merge_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, Q, nparts, qnorm, cand_idx,
                                                                    cand_lb);
 }
 
+int tc_padded_k8(int d) { return ((d + 1) + 31) / 32 * 32; }
+
+void launch_fp8_tables(const float *et, int N, int d, int da, int K, float *scale, uint8_t *out, cudaStream_t st) {
+    count_launches(2);
+    k_fp8_dim_scale<<<d + 1, 256, 0, st>>>(et, N, d, da, scale);
+    k_pack_exemplar_f8<<<152 * 4, 256, 0, st>>>(et, N, tc_tiles(N), d, da, K, scale, out);
+}
+
+void launch_pack_queries_f8(const float *qcoord, int Q, int d, int da, int K, const float *scale, uint8_t *qtile,
+                            float *qscale, cudaStream_t st, const int *qlist, const unsigned int *qcount) {
+    const int nb = tc_query_blocks(Q);
+    if (nb == 0) return;
+    count_launches(1);
+    k_pack_queries_f8<<<(unsigned)ceil_div((long)nb * kQM * 32, 256), 256, 0, st>>>(qcoord, Q, d, da, K, nb, scale,
+                                                                                     qlist, qcount, qtile, qscale);
+}
+
 pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref) {
     if (N < 16 || N > 256 || N % 16 || K < 16 || K > 128 || K % 16)
         return set_error(PTS_ERR_INVALID_ARG, "pts_tc_selftest: N in 16..256 and K in 16..128, multiples of 16");
+    if (f16 == 3) {
+        if (K % 32) return set_error(PTS_ERR_INVALID_ARG, "pts_tc_selftest: FP8 needs K a multiple of 32");
+        return run_selftest_f8(N, K, max_abs_err, max_abs_ref);
+    }
     if (f16 == 2) return run_selftest<__half, true>(N, K, idesc_f16(kQM, N), max_abs_err, max_abs_ref);
     if (f16) return run_selftest<__half, false>(N, K, idesc_f16(kQM, N), max_abs_err, max_abs_ref);
     return run_selftest<__nv_bfloat16, false>(N, K, idesc_bf16(kQM, N), max_abs_err, max_abs_ref);

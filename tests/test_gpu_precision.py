@@ -31,9 +31,12 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
 
 
-@pytest.mark.parametrize("f16", [2, 1, 0])  # 2: FP16 with A from tensor memory, as the search issues it
+# 3: FP8 E4M3 (kind::f8f6f4), 2: FP16 with A from tensor memory, 1: FP16 as the search issues it, 0: BF16
+@pytest.mark.parametrize("f16", [3, 2, 1, 0])
 @pytest.mark.parametrize("N,K", [(64, 80), (64, 32), (128, 64), (16, 16), (128, 128), (128, 96), (256, 128)])
 def test_tensor_core_operand_layout(N, K, f16):
+    if f16 == 3 and K % 32:
+        pytest.skip("FP8 MMAs step K by 32")
     L = pts.lib()
     err, ref = ctypes.c_double(), ctypes.c_double()
     assert L.pts_tc_selftest(N, K, f16, ctypes.byref(err), ctypes.byref(ref)) == 0
@@ -121,4 +124,39 @@ def test_f16_full_size_fine_level_sampled():
     # a random-patch initialisation is the hardest case for the PCA-space ranking (most windows
     # straddle patch seams); on converging images the rate is several times lower
     assert np.mean(nn_g != nn_o) < 0.035
+    idx.close()
+
+
+@pytest.mark.parametrize("He,Ho,w,d", [(64, 128, 8, 24), (48, 64, 16, 64)])
+def test_fp8_search_errors_against_oracle(He, Ho, w, d):
+    """FP8 E4M3 mode: the chosen window's reported distance is its exact FP32 distance and never
+    beats the exact minimum; the index mismatch rate and the distance excess are the stated
+    errors of the mode (E4M3 keeps 3 mantissa bits, so the ranking is coarse)."""
+    Z = P.synthetic_exemplar(0, He, 3.0)
+    idx = pts.ExemplarIndex(_t(Z), w, d=d)
+    X = P.random_patch_init(Z, Ho, Ho, w, 5)
+    nn, d2 = pts.nn_search(idx, _t(X), 2, "fp8")
+    nn_o, d2_o = oracle.nn_bruteforce(X, Z, w, 2)
+    nn_g = nn.cpu().numpy()
+    mism, worst = _check_not_better_than_exact(X, Z, w, nn_g, d2.cpu().numpy().astype(np.float64), nn_o, d2_o)
+    pd = oracle.pair_dist2(X, Z, w, 2, np.arange(len(nn_g)), nn_g)
+    excess = float((pd.sum() - d2_o.sum()) / max(d2_o.sum(), 1e-30))  # energy the mode gives away
+    print(f"fp8 {He}->{Ho} w={w}: index mismatch {mism:.4f}, mean d2 excess {excess:.5f}, worst ratio {worst:.4f}")
+    assert mism < 0.35 and excess < 0.05
+    idx.close()
+
+
+def test_fp8_energy_reported():
+    """The FP8 mode's final energy against exact mode on the tiny configuration (stated, and
+    within 10%)."""
+    Z = P.synthetic_exemplar(0, 64, 3.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=24)
+    X0 = P.random_patch_init(Z, 128, 128, 8, 6)
+    xe, x8 = _t(X0), _t(X0)
+    Ee = pts.synthesize_level(idx, xe, 5, mode="exact")
+    pts.synthesize_level(idx, x8, 5, mode="fp8")
+    _, d2 = pts.nn_search(idx, x8, 2, "exact")
+    ratio = float(d2.double().sum()) / Ee[-1]
+    print(f"fp8 final energy ratio vs exact: {ratio:.5f}")
+    assert ratio < 1.10
     idx.close()
