@@ -331,6 +331,35 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
  */
 long long pts_launch_count(void);
 
+/*
+ * Batched synthesis (no counterpart in the paper; the batched form of the EM loop of section 2.1
+ * for many independent jobs of uneven sizes).  A job is one level: `iters` EM iterations on its
+ * own index and output, then the final search phase.
+ */
+typedef struct {
+    pts_index index;  /* the job's exemplar index; no two jobs of a batch may share one */
+    float *output;    /* device Ho x Wo x 3 float32; in: initial image, out: result */
+    int Ho, Wo, stride;
+    int mode;         /* PTS_EXACT_F32, PTS_F16_RERANK or PTS_FP8_RERANK */
+    double *energy;   /* device, iters + 1 doubles: energy entering each iteration, then the final */
+} pts_job;
+
+typedef struct pts_batch_s *pts_batch; /* opaque, owned by the library */
+
+/* Builds a batch: runs one search per job (sizing every workspace), with tune != 0 picks the
+ * tensor-core search's exemplar split per job shape by timing the candidates (cached per
+ * process), then captures all jobs' iterations into one CUDA graph, jobs spread round-robin
+ * over n_streams (1..64) forked streams.  The job structs are copied; outputs and energy arrays
+ * stay the caller's.  Synchronises `stream`.  Jobs' outputs are searched (not modified) here. */
+pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r, float delta, int n_streams,
+                            int tune, void *stream, pts_batch *out);
+/* Replays the batch's graph on `stream` (asynchronous): every job runs from its current output. */
+pts_status pts_batch_run(pts_batch batch, void *stream);
+/* Kernel launches one run issues, and (parts_out, n_jobs ints, may be NULL) each job's exemplar
+ * split chosen by the autotuner (0 for exact jobs). */
+pts_status pts_batch_info(pts_batch batch, long long *launches_per_run, int *parts_out);
+void pts_batch_destroy(pts_batch batch);
+
 /* Self-test of the tensor-core operand layout (no counterpart in the paper):
  * one 128 x N x K tcgen05 MMA (f16 == 3: FP8 E4M3, kind::f8f6f4, K a multiple of 32;
  * f16 == 2: FP16 with the A operand read from tensor memory; f16 == 1: FP16 with both

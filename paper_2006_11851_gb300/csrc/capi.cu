@@ -54,6 +54,12 @@ pts_status check_grid(int H, int W, int w, int stride, const char *what) {
     return PTS_OK;
 }
 
+}  // namespace
+
+pts_status check_grid_public(int H, int W, int w, int stride, const char *what) {
+    return check_grid(H, W, w, stride, what);
+}
+
 pts_status ensure_workspace(pts_index idx, int Q) {
     Workspace &ws = idx->ws;
     if (Q <= ws.q_cap && ws.counters.ptr) return PTS_OK;
@@ -203,7 +209,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
-            const int nparts = tc_parts(Q, ntc);
+            const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
             if (nparts > 1) {
                 PTS_TRY(ws.part_v.ensure((size_t)Q * nparts * kTopK, "part lists"));
@@ -236,7 +242,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
-            const int nparts = tc_parts(Q, ntc);
+            const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
             PTS_TRY(ws.qtile8.ensure((size_t)tc_query_blocks(Q) * 128 * idx->kf8, "fp8 query tiles"));
             PTS_TRY(ws.qscale.ensure((size_t)std::max(Q, 1), "fp8 query scales"));
             if (nparts > 1) {
@@ -265,7 +271,6 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
     return PTS_OK;
 }
 
-}  // namespace
 
 pts_status set_error(pts_status s, const std::string &msg) {
     g_last_error = msg;

@@ -46,6 +46,17 @@ void clear_records() {
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Event timing is switched off while a CUDA graph is being captured (an event recorded into a
+// capture would become a graph node, not a timing point); on = true restores the previous state.
+void prof_suspend(bool on) {
+    static int saved = 0;
+    if (!on) {
+        saved = g_enabled.exchange(0);
+    } else {
+        g_enabled.store(saved);
+    }
+}
+
 void prof_begin(int cls, cudaStream_t st, void **token) {
     *token = nullptr;
     if (!g_enabled.load(std::memory_order_relaxed)) return;

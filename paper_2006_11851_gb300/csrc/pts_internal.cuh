@@ -168,6 +168,7 @@ struct pts_index_s {
     pts::Workspace ws;
     pts_search_stats last{};
     int last_mode = 0;
+    int tc_parts_override = 0;  // exemplar split of the tensor-core search chosen by the autotuner
     pts::ProposalState prop;
 };
 
@@ -177,6 +178,11 @@ namespace pts {
 // launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
 // pca.cu
+pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int stride, int mode, int32_t *nn_out,
+                          float *d2_out, cudaStream_t st);
+pts_status ensure_workspace(pts_index idx, int Q);
+pts_status check_grid_public(int H, int W, int w, int stride, const char *what);
+void prof_suspend(bool on);
 pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, double var_frac,
                           int max_iters, float *mean_out, float *basis_out, double *eig_out,
                           int *d_used, double *var_retained, double *eig_top, int *iters_used,
