@@ -139,12 +139,29 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
         mlp_forward(pr.mlp, B, 0, idx->status.ptr, st);
         launch_top4(pr.mlp.z.ptr, B, pr.C, pr.top.ptr + (size_t)q0 * 4, st);
     }
-    launch_probe(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da_fast, pr.top.ptr, pr.off.ptr, pr.members.ptr, pr.mrow.ptr,
-                 pr.mnorm.ptr, ws.cand_idx.ptr, ws.cand_lb.ptr, st);
+    // probe: the tensor-core search restricted, per (query, cluster) pair, to the cluster's tiles
+    const int maxb = ivf_max_blocks(Q, pr.C);
+    PTS_TRY(pr.ivf_cnt.ensure(pr.C, "probe counts"));
+    PTS_TRY(pr.ivf_poff.ensure(pr.C, "probe offsets"));
+    PTS_TRY(pr.ivf_cursor.ensure(pr.C, "probe cursors"));
+    PTS_TRY(pr.ivf_nblk.ensure(1, "probe blocks"));
+    PTS_TRY(pr.pair_q.ensure((size_t)4 * std::max(Q, 1), "probe pairs"));
+    PTS_TRY(pr.pair_r.ensure((size_t)4 * std::max(Q, 1), "probe pairs"));
+    PTS_TRY(pr.ivf_blk.ensure((size_t)maxb, "probe block table"));
+    PTS_TRY(pr.ivf_qtile.ensure((size_t)maxb * 128 * idx->ktc, "probe query tiles"));
+    PTS_TRY(pr.ivf_part_v.ensure((size_t)std::max(Q, 1) * 4 * kTopK, "probe lists"));
+    PTS_TRY(pr.ivf_part_i.ensure((size_t)std::max(Q, 1) * 4 * kTopK, "probe lists"));
+    PTS_TRY(pr.ivf_kept.ensure(tc_kept_bytes(Q, 4), "probe kept groups"));
+    IvfBuffers ib{pr.ivf_cnt.ptr, pr.ivf_poff.ptr, pr.ivf_cursor.ptr, pr.ivf_nblk.ptr, pr.pair_q.ptr,
+                  pr.pair_r.ptr, pr.ivf_blk.ptr, pr.ivf_qtile.ptr, pr.ivf_part_v.ptr, pr.ivf_part_i.ptr,
+                  pr.ivf_kept.ptr};
+    launch_ivf_probe(pr.top.ptr, Q, pr.C, pr.off.ptr, ws.qcoord.ptr, ws.qnorm.ptr, idx->d_fast, idx->da_fast, idx->ktc,
+                     pr.etc_ivf.ptr, tc_tiles(idx->N), idx->N, pr.members.ptr, ib, ws.cand_idx.ptr, ws.cand_lb.ptr,
+                     idx->status.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
     RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
-    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
+    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out, d2_out,
                   ws.fail_list.ptr, ws.counters.ptr + 3, ws.best64.ptr, idx->status.ptr, st);
     launch_fallback(nn_out, d2_out, Q, pr.assign.ptr, pr.median.ptr, pr.factor, idx->N, ws.fail_list.ptr,
                     ws.counters.ptr + 0, st);
@@ -152,9 +169,10 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
     launch_pack_queries(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->ktc, ws.qtile.ptr, st, ws.fail_list.ptr,
                         ws.counters.ptr + 0);
+    PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, 1), "kept groups"));
     launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, tc_tiles(idx->N), 1, nullptr,
                      ws.cand_idx.ptr, ws.cand_lb.ptr, nullptr, nullptr, idx->status.ptr, st, ws.fail_list.ptr,
-                     ws.counters.ptr + 0);
+                     ws.counters.ptr + 0, 0, nullptr, nullptr, idx->N, ws.kept.ptr);
     launch_rerank(ra, ws.fail_list.ptr, ws.counters.ptr + 0, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out,
                   d2_out, ws.fail2_list.ptr, ws.counters.ptr + 1, ws.best64.ptr, idx->status.ptr, st);
     return PTS_OK;
@@ -221,9 +239,11 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             if (warm)
                 launch_warm_threshold(ws.cand_idx.ptr, ws.qcoord.ptr, idx->d_fast, idx->da_fast, ws.qnorm.ptr,
                                       idx->etc.ptr, idx->umax.ptr, Q, idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
+            PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, nparts), "kept groups"));
             launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, ntc, nparts,
                              warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr,
-                             ws.part_i.ptr, idx->status.ptr, st);
+                             ws.part_i.ptr, idx->status.ptr, st, nullptr, nullptr, 0, nullptr, nullptr, idx->N,
+                             ws.kept.ptr);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
                           idx->nx, idx->N, Q};
             // candidates in ascending bound order; stop where bound - slack exceeds the best
@@ -251,9 +271,10 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             }
             launch_pack_queries_f8(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->kf8, idx->f8scale.ptr,
                                    ws.qtile8.ptr, ws.qscale.ptr, st);
+            PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, nparts), "kept groups"));
             launch_search_tc(ws.qtile8.ptr, ws.qnorm.ptr, Q, idx->kf8, idx->etc8.ptr, ntc, nparts, nullptr,
                              ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st,
-                             nullptr, nullptr, 1, ws.qscale.ptr, idx->enorm.ptr, idx->N);
+                             nullptr, nullptr, 1, ws.qscale.ptr, idx->enorm.ptr, idx->N, ws.kept.ptr);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
                           idx->nx, idx->N, Q};
             launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
@@ -475,8 +496,6 @@ void pts_index_destroy(pts_index idx) {
         pr.counts.release();
         pr.off.release();
         pr.members.release();
-        pr.mrow.release();
-        pr.mnorm.release();
         pr.median.release();
         pr.top.release();
         MlpState &m = pr.mlp;
@@ -660,16 +679,16 @@ pts_status pts_train_proposal(pts_index idx, const float *y, const int32_t *nn, 
     PTS_TRY(pr.counts.ensure(C, "cluster sizes"));
     PTS_TRY(pr.off.ensure(C + 1, "cluster offsets"));
     PTS_TRY(pr.members.ensure(N, "cluster members"));
-    PTS_TRY(pr.mrow.ensure((size_t)N * idx->da_fast, "member vectors"));
-    PTS_TRY(pr.mnorm.ensure(N, "member norms"));
     PTS_TRY(pr.median.ensure(C, "cluster medians"));
     launch_extract_y(idx->et.ptr, N, da, d, Y.ptr, st);
     std::vector<double> u(C);
     for (int i = 0; i < C; ++i) u[i] = uniform();
     PTS_TRY(kmeans_device(Y.ptr, N, d, C, u.data(), iters, pr.centroids.ptr, pr.assign.ptr, cost.ptr, pr.counts.ptr,
                           pr.off.ptr, pr.members.ptr, nullptr, st));
-    launch_member_rows(idx->et_fast.ptr, idx->enorm.ptr, N, idx->da_fast, pr.members.ptr, pr.mrow.ptr, pr.mnorm.ptr,
-                       st);
+    // the exemplar's FP16 search tiles with the windows in cluster order, for the probe
+    PTS_TRY(pr.etc_ivf.ensure((size_t)tc_tiles(N) * tc_tile_rows() * idx->ktc, "cluster-ordered tiles"));
+    launch_pack_exemplar(idx->et_fast.ptr, idx->enorm.ptr, N, idx->d_fast, idx->da_fast, idx->ktc, pr.etc_ivf.ptr, st,
+                         pr.members.ptr);
     DevBuf<int> lab;
     DevBuf<float> dist;
     PTS_TRY(lab.ensure(n, "pair labels"));

@@ -204,17 +204,6 @@ __global__ void k_extract_y(const float *__restrict__ et, int N, int da, int d, 
 }
 
 // member search vectors in cluster order, row-major [N][da], and their norms
-__global__ void k_member_rows(const float *__restrict__ et, const float *__restrict__ enorm, int N, int da,
-                              const int *__restrict__ members, float *__restrict__ mrow, float *__restrict__ mnorm) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)N * da; i += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(i / da), k = (int)(i % da);
-        const int n = members[j];
-        mrow[i] = et[((size_t)(n / kBN) * da + k) * kBN + (n % kBN)];
-        if (k == 0) mnorm[j] = enorm[n];
-    }
-}
-
-// labels of training pairs = cluster of their nearest exemplar window; distances sqrt(d2)
 __global__ void k_pair_labels(const int *__restrict__ nn, const float *__restrict__ d2, int n,
                               const int *__restrict__ assign, int N, int *__restrict__ lab, float *__restrict__ dist) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -326,12 +315,6 @@ pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, i
 void launch_extract_y(const float *et, int N, int da, int d, float *Y, cudaStream_t st) {
     count_launches(1);
     k_extract_y<<<152 * 4, 256, 0, st>>>(et, N, da, d, Y);
-}
-
-void launch_member_rows(const float *et, const float *enorm, int N, int da, const int *members, float *mrow,
-                        float *mnorm, cudaStream_t st) {
-    count_launches(1);
-    k_member_rows<<<152 * 4, 256, 0, st>>>(et, enorm, N, da, members, mrow, mnorm);
 }
 
 pts_status cluster_medians(const int *nn, const float *d2, int n, const int *assign, int N, int C, int *lab,

@@ -1,14 +1,13 @@
 // probe.cu -- the learned-proposal search phase (E-step).  The network ranks the k-means
 // clusters for each query; the query is compared with the members of its 4 best-ranked
-// clusters only, and the 32 smallest PCA-space bounds are re-ranked in full dimension.  A query
-// whose re-ranked distance exceeds 1.2 x the median nearest-neighbour distance of its chosen
-// window's cluster goes to the exact search instead (the fallback).
+// clusters only (the FP16 tensor-core search restricted to the tiles of each cluster, with the
+// exemplar windows stored in cluster order: launch_ivf_probe in search_tc.cu), and the 32
+// smallest PCA-space bounds are re-ranked in full dimension.  A query whose re-ranked distance
+// exceeds 1.2 x the median nearest-neighbour distance of its chosen window's cluster goes to
+// the FP16 search over every window instead (the fallback).
 //
 //   k_top4     one warp per query: each lane keeps the 4 largest logits of its stripe, then
 //              4 rounds of warp arg-max (largest logit, smallest cluster id on ties).
-//   k_probe    one warp per query: lanes stride over the members of the 4 clusters (their
-//              search vectors are stored contiguously in cluster order), compute
-//              p = ||u_n||^2 - 2 a_q . e_n in FP32 and keep a warp-resident top-32.
 //   k_fallback lists the queries whose result fails the median test.
 #include "pts_internal.cuh"
 
@@ -68,63 +67,6 @@ __global__ void __launch_bounds__(256) k_top4(const float *__restrict__ logits, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_probe(const float *__restrict__ qcoord, const float *__restrict__ qnorm,
-                                               int Q, int da, const int *__restrict__ top,
-                                               const int *__restrict__ off, const int *__restrict__ members,
-                                               const float *__restrict__ mrow, const float *__restrict__ mnorm,
-                                               int *__restrict__ cand_idx, float *__restrict__ cand_lb) {
-    __shared__ float qa[8][kMaxDAFast];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (q >= Q) return;
-    for (int k = lane; k < da; k += 32) qa[w][k] = qcoord[(size_t)q * da + k];
-    __syncwarp();
-    float ld = INFINITY, thr = INFINITY;
-    int li = -1;
-    for (int r = 0; r < 4; ++r) {
-        const int c = top[(size_t)q * 4 + r];
-        const int a = off[c], b = off[c + 1];
-        for (int j0 = a; j0 < b; j0 += 32) {
-            const int j = j0 + lane;
-            float p = INFINITY;
-            if (j < b) {
-                const float4 *e = reinterpret_cast<const float4 *>(mrow + (size_t)j * da);
-                p = mnorm[j];
-                for (int k4 = 0; k4 < da / 4; ++k4) {
-                    const float4 x = e[k4];
-                    p = fmaf(qa[w][4 * k4 + 0], x.x, p);
-                    p = fmaf(qa[w][4 * k4 + 1], x.y, p);
-                    p = fmaf(qa[w][4 * k4 + 2], x.z, p);
-                    p = fmaf(qa[w][4 * k4 + 3], x.w, p);
-                }
-            }
-            const int n = j < b ? members[j] : -1;
-            unsigned fl = __ballot_sync(kFull, p < thr);
-            while (fl) {
-                const int src = __ffs(fl) - 1;
-                const float cd = __shfl_sync(kFull, p, src);
-                const int ci = __shfl_sync(kFull, n, src);
-                const bool before = (ld < cd) || (ld == cd && li < ci);
-                const int pos = __popc(__ballot_sync(kFull, before));
-                const float ud = __shfl_up_sync(kFull, ld, 1);
-                const int ui = __shfl_up_sync(kFull, li, 1);
-                if (lane > pos) {
-                    ld = ud;
-                    li = ui;
-                } else if (lane == pos) {
-                    ld = cd;
-                    li = ci;
-                }
-                thr = __shfl_sync(kFull, ld, 31);
-                fl &= ~(1u << src);
-                fl &= __ballot_sync(kFull, p < thr);
-            }
-        }
-    }
-    cand_idx[(size_t)q * kTopK + lane] = li;
-    cand_lb[(size_t)q * kTopK + lane] = ld + qnorm[q];
-}
-
 __global__ void k_fallback(const int *__restrict__ nn, const float *__restrict__ d2, int Q,
                            const int *__restrict__ assign, const float *__restrict__ median, float factor, int N,
                            int *__restrict__ list, unsigned int *__restrict__ count) {
@@ -140,14 +82,6 @@ __global__ void k_fallback(const int *__restrict__ nn, const float *__restrict__
 void launch_top4(const float *logits, int Q, int C, int *top, cudaStream_t st) {
     count_launches(1);
     k_top4<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(logits, Q, C, top);
-}
-
-void launch_probe(const float *qcoord, const float *qnorm, int Q, int da, const int *top, const int *off,
-                  const int *members, const float *mrow, const float *mnorm, int *cand_idx, float *cand_lb,
-                  cudaStream_t st) {
-    ProfScope ps(kProfProbe, st, 1);
-    k_probe<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(qcoord, qnorm, Q, da, top, off, members, mrow, mnorm, cand_idx,
-                                                         cand_lb);
 }
 
 void launch_fallback(const int *nn, const float *d2, int Q, const int *assign, const float *median, float factor,

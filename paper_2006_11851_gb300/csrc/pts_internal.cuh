@@ -96,6 +96,7 @@ struct Workspace {
     DevBuf<uint8_t> qtile8;    // [ceil(Q/128)][128 x Kf8] FP8 query operand tiles
     DevBuf<float> qscale;      // [Q] FP8 query row scales
     DevBuf<float> proj_part;   // per-slice partial sums of a split projection
+    DevBuf<unsigned char> kept;  // kept groups of the tensor-core search, one record per (row, half)
     DevBuf<float> part_v;      // [Q][parts][32] per-part candidate lists of the tensor-core search
     DevBuf<int> part_i;
     int warm_q = -1, warm_ho = -1, warm_wo = -1, warm_stride = -1;  // geometry of cand_idx
@@ -132,10 +133,15 @@ struct ProposalState {
     DevBuf<int> counts;       // [C]
     DevBuf<int> off;          // [C+1] CSR offsets
     DevBuf<int> members;      // [N] windows in cluster order
-    DevBuf<float> mrow;       // [N][da] search vectors in cluster order
-    DevBuf<float> mnorm;      // [N]
     DevBuf<float> median;     // [C] median nearest-neighbour distance of the cluster's pairs
     DevBuf<int> top;          // [Q][4] probed clusters
+    DevBuf<__half> etc_ivf;   // FP16 exemplar tiles with the windows in cluster order (members)
+    DevBuf<int> ivf_cnt, ivf_poff, ivf_cursor, ivf_nblk, pair_q, pair_r;
+    DevBuf<int4> ivf_blk;
+    DevBuf<__half> ivf_qtile;
+    DevBuf<float> ivf_part_v;
+    DevBuf<int> ivf_part_i;
+    DevBuf<unsigned char> ivf_kept;
     MlpState mlp;
 };
 
@@ -215,14 +221,28 @@ int tc_parts(int Q, int ntiles);
 void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __half *qtile, cudaStream_t st,
                          const int *qlist = nullptr, const unsigned int *qcount = nullptr);
 void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int da, int K, __half *out,
-                          cudaStream_t st);
+                          cudaStream_t st, const int *perm = nullptr);
+// learned proposal probe on the tensor cores (cluster-ordered exemplar tiles)
+struct IvfBuffers {
+    int *cnt, *poff, *cursor, *nblk, *pair_q, *pair_r;
+    int4 *blk;
+    __half *qtile;
+    float *part_v;
+    int *part_i;
+    void *kept;
+};
+int ivf_max_blocks(int Q, int C);
+size_t tc_kept_bytes(int Q, int nparts);
+void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float *qcoord, const float *qnorm, int d,
+                      int da, int K, const __half *etile_ivf, int ntiles, int N, const int *members, IvfBuffers &b,
+                      int *cand_idx, float *cand_lb, int *status, cudaStream_t st);
 void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
                            const __half *etile, const float *umax, int Q, int K, int N, float eps_scale, float *thr0,
                            cudaStream_t st);
 void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const void *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                      int *status, cudaStream_t st, const int *qlist = nullptr, const unsigned int *qcount = nullptr,
-                      int fp8 = 0, const float *qscale = nullptr, const float *enorm = nullptr, int N = 0);
+                      int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount, int fp8,
+                      const float *qscale, const float *enorm, int N, void *kept_buf);
 int tc_padded_k8(int d);
 void launch_fp8_tables(const float *et, int N, int d, int da, int K, float *scale, uint8_t *out, cudaStream_t st);
 void launch_pack_queries_f8(const float *qcoord, int Q, int d, int da, int K, const float *scale, uint8_t *qtile,
@@ -233,15 +253,10 @@ pts_status tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_a
 pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, int iters, float *C, int *assign,
                          float *cost, int *counts, int *off, int *members, int *iters_used, cudaStream_t st);
 void launch_extract_y(const float *et, int N, int da, int d, float *Y, cudaStream_t st);
-void launch_member_rows(const float *et, const float *enorm, int N, int da, const int *members, float *mrow,
-                        float *mnorm, cudaStream_t st);
 pts_status cluster_medians(const int *nn, const float *d2, int n, const int *assign, int N, int C, int *lab,
                            float *dist, float *median, cudaStream_t st);
 // probe.cu
 void launch_top4(const float *logits, int Q, int C, int *top, cudaStream_t st);
-void launch_probe(const float *qcoord, const float *qnorm, int Q, int da, const int *top, const int *off,
-                  const int *members, const float *mrow, const float *mnorm, int *cand_idx, float *cand_lb,
-                  cudaStream_t st);
 void launch_fallback(const int *nn, const float *d2, int Q, const int *assign, const float *median, float factor,
                      int N, int *list, unsigned int *count, cudaStream_t st);
 // mlp.cu / gemm_tc.cu

@@ -64,8 +64,6 @@ struct TcSmem {
     alignas(1024) unsigned char q[kQM * kMaxKt * 2];
     alignas(1024) unsigned char e[kRing];
     uint4 pay[kEpiThreads * kPayStride];   // per thread, per slot: a kept group's 8 FP16 offsets
-    int gmap[kEpiThreads * (kKeep + 1)];   // per thread, per slot: its group (at the end)
-    float gmin[kEpiThreads * (kKeep + 1)];  // per thread, per slot: its group minimum (at the end)
     uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAcc], acc_empty[kAcc], q_full, done;
     uint32_t tmem_base;
     int abort_flag;
@@ -196,6 +194,23 @@ __device__ __forceinline__ void fp8_finish(float (&v)[64], float tq, const float
     }
 }
 
+// Cluster-restricted blocks (the learned proposal's probe): block b covers rows f0 .. f0+nrows-1
+// of the (query, probed cluster) pair list and the exemplar tiles t_begin .. t_begin+nt-1 of its
+// cluster (exemplar tiles in cluster order); a row's 32 best go to part slot pair_r of pair_q.
+// What an epilogue thread keeps for its (output row, column half): the 8 groups' minima and
+// indices, and each group's 8 scores as FP16 offsets from its minimum (slot order).
+struct KeptGroups {
+    float gmin[kKeep];
+    int gmap[kKeep];
+    uint4 pay[kKeep];
+};
+
+struct IvfArgs {
+    const int4 *blk;         // [nblk] (f0, nrows, t_begin, nt)
+    const int *nblk;         // device count of blocks
+    const int *pair_q, *pair_r;
+};
+
 // EB = operand bytes: 2 for FP16 (kind::f16, the norms ride in K), 1 for FP8 E4M3
 // (kind::f8f6f4, per-dimension scales; the epilogue forms p = ||u_n||^2 + t_q acc).
 template <int EB>
@@ -204,18 +219,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const void *__restrict__ etile, int ntiles, int tiles_per_part, int nstages,
                 const float *__restrict__ qscale, const float *__restrict__ enorm, int N,
                 const float *__restrict__ thr0, const int *__restrict__ qlist,
-                const unsigned int *__restrict__ qcount, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
-                float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status) {
+                const unsigned int *__restrict__ qcount, IvfArgs ivf, KeptGroups *__restrict__ kept,
+                int *__restrict__ status) {
     // with a query list, tile row f holds query qlist[f] (f < *qcount); blocks past the list exit
     const int nrows = qlist ? (int)min((unsigned int)Q, *qcount) : Q;
-    if ((int)blockIdx.x * kQM >= nrows) return;
+    int4 blk = make_int4(0, 0, 0, 0);
+    if (ivf.blk) {
+        if ((int)blockIdx.x >= *ivf.nblk) return;
+        blk = ivf.blk[blockIdx.x];
+    } else if ((int)blockIdx.x * kQM >= nrows) {
+        return;
+    }
+    // tile row r -> query (and, for cluster-restricted blocks, its part slot); -1 when empty
+    auto row_query = [&](int r, int *slot) -> int {
+        if (ivf.blk) {
+            if (r >= blk.y) return -1;
+            *slot = ivf.pair_r[blk.x + r];
+            return ivf.pair_q[blk.x + r];
+        }
+        const int f = blockIdx.x * kQM + r;
+        *slot = blockIdx.y;
+        return f < nrows ? (qlist ? qlist[f] : f) : -1;
+    };
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     volatile int *abort_flag = &sm.abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nparts = gridDim.y, part = blockIdx.y;
-    const int t_begin = part * tiles_per_part;
-    const int nt = max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
+    const int nparts = ivf.blk ? 4 : gridDim.y;
+    const int t_begin = ivf.blk ? blk.z : blockIdx.y * tiles_per_part;
+    const int nt = ivf.blk ? blk.w : max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
     const uint32_t stage_bytes = (uint32_t)(kTN * K * EB);
     const uint32_t q_bytes = (uint32_t)(kQM * K * EB);
     const unsigned char *qtile_b = static_cast<const unsigned char *>(qtile);
@@ -300,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue ----------------
         const int quarter = warp & 3, half = warp >> 2;
         const int row = quarter * 32 + lane;
-        const int f = blockIdx.x * kQM + row;
-        const int q = f < nrows ? (qlist ? qlist[f] : f) : -1;
+        int slot_unused = 0;
+        const int q = row_query(row, &slot_unused);
         GroupList L;
         {
             const float t = q >= 0 ? (thr0 ? thr0[2 * (size_t)q + half] : INFINITY) : -INFINITY;
@@ -335,51 +367,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             if constexpr (EB == 1) fp8_finish(v, tq, enorm, col0 + 64, N);
             scan64(v, group0 + 8, L, pay_row);
         }
-        // publish which group each slot holds, then select each query's 32 best windows
+        // hand the kept groups to k_select (one record per output row and column half)
+        if (!*abort_flag && q >= 0) {
+            int slot = 0;
+            row_query(row, &slot);
+            KeptGroups *rec = kept + (((size_t)q * nparts + slot) * 2 + half);
 #pragma unroll
-        for (int k = 0; k < kKeep; ++k) {
-            sm.gmap[tid * (kKeep + 1) + (L.gs[k] & 15)] = L.gs[k] >> 4;
-            sm.gmin[tid * (kKeep + 1) + (L.gs[k] & 15)] = L.gv[k];
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
-        if (!*abort_flag) {
-            for (int r = 0; r < kQM / kEpiWarps; ++r) {
-                const int rr = warp * (kQM / kEpiWarps) + r;
-                const int fr = blockIdx.x * kQM + rr;
-                if (fr >= nrows) break;
-                const int qq = qlist ? qlist[fr] : fr;
-                if (qq < 0 || qq >= Q) {
-                    if (lane == 0) atomicOr(status, kDevErrBounds);
-                    continue;
-                }
-                float sv[4];
-                int si[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    // entries 0..63: the half-0 thread of row rr (index rr), 64..127: half 1 (rr + 128)
-                    const int owner = rr + (c >> 1) * kQM;
-                    const int k = lane + 32 * (c & 1);  // slot k / 8, element k % 8
-                    const int grp = sm.gmap[owner * (kKeep + 1) + k / kG];
-                    const __half off = reinterpret_cast<const __half *>(&sm.pay[owner * kPayStride + k / kG])[k % kG];
-                    const float x = sm.gmin[owner * (kKeep + 1) + k / kG] + __half2float(off);
-                    const bool real = grp != kNoGroup && !isnan(x);
-                    sv[c] = real ? x : INFINITY;
-                    si[c] = real ? grp * kG + (k % kG) : kNoWindow;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) warp_sort32(sv[c], si[c], lane);
-                warp_merge32(sv[0], si[0], sv[1], si[1], lane);
-                warp_merge32(sv[2], si[2], sv[3], si[3], lane);
-                warp_merge32(sv[0], si[0], sv[2], si[2], lane);
-                if (nparts == 1) {
-                    const bool real = si[0] != kNoWindow;
-                    cand_idx[(size_t)qq * kTopK + lane] = real ? si[0] : -1;
-                    cand_lb[(size_t)qq * kTopK + lane] = real ? sv[0] + qnorm[qq] : INFINITY;
-                } else {
-                    const size_t o = ((size_t)qq * nparts + part) * kTopK + lane;
-                    part_v[o] = sv[0];
-                    part_i[o] = si[0];
-                }
+            for (int k = 0; k < kKeep; ++k) {
+                const int sl = L.gs[k] & 15;
+                rec->gmin[sl] = L.gv[k];
+                rec->gmap[sl] = L.gs[k] >> 4;
+                rec->pay[sl] = pay_row[sl];
             }
         }
     }
@@ -392,10 +390,88 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// One warp per output row (query x part): the 32 smallest (score, window) pairs among the 2 x 8
+// kept groups of its two column halves, sorted; to the candidate lists (+ ||u_q||^2) when the
+// row is the query's only part, else to the part lists.  Windows are indexed through perm when
+// the tiles hold them in another order.
+__global__ void __launch_bounds__(256) k_select(const KeptGroups *__restrict__ kept, int Q, int nparts,
+                                                const float *__restrict__ qnorm, const int *__restrict__ perm, int N,
+                                                int *__restrict__ cand_idx, float *__restrict__ cand_lb,
+                                                float *__restrict__ part_v, int *__restrict__ part_i) {
+    const int lane = threadIdx.x & 31;
+    const long o = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (o >= (long)Q * nparts) return;
+    float sv[4];
+    int si[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const KeptGroups &rec = kept[o * 2 + (c >> 1)];
+        const int k = lane + 32 * (c & 1);  // slot k / 8, element k % 8
+        const int grp = rec.gmap[k / kG];
+        const __half off = reinterpret_cast<const __half *>(&rec.pay[k / kG])[k % kG];
+        const float x = rec.gmin[k / kG] + __half2float(off);
+        const bool real = grp != kNoGroup && !isnan(x);
+        sv[c] = real ? x : INFINITY;
+        si[c] = real ? grp * kG + (k % kG) : kNoWindow;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) warp_sort32(sv[c], si[c], lane);
+    warp_merge32(sv[0], si[0], sv[1], si[1], lane);
+    warp_merge32(sv[2], si[2], sv[3], si[3], lane);
+    warp_merge32(sv[0], si[0], sv[2], si[2], lane);
+    if (nparts == 1) {
+        bool real = si[0] != kNoWindow;
+        int n = si[0];
+        if (real && perm) {
+            real = n >= 0 && n < N;
+            n = real ? perm[n] : -1;
+        }
+        cand_idx[o * kTopK + lane] = real ? n : -1;
+        cand_lb[o * kTopK + lane] = real ? sv[0] + qnorm[o] : INFINITY;
+    } else {
+        part_v[o * kTopK + lane] = sv[0];
+        part_i[o * kTopK + lane] = si[0];
+    }
+}
+
+// k_select for a device-side query list (one part per query)
+__global__ void __launch_bounds__(256) k_select_list(const KeptGroups *__restrict__ kept, const int *__restrict__ qlist,
+                                                     const unsigned int *__restrict__ qcount, int Q,
+                                                     const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                     float *__restrict__ cand_lb) {
+    const long f = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= (long)min((unsigned int)Q, *qcount)) return;
+    const int q = qlist[f];
+    if (q < 0 || q >= Q) return;
+    // same as k_select for row q with one part
+    const int lane = threadIdx.x & 31;
+    float sv[4];
+    int si[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const KeptGroups &rec = kept[(long)q * 2 + (c >> 1)];
+        const int k = lane + 32 * (c & 1);
+        const int grp = rec.gmap[k / kG];
+        const __half off = reinterpret_cast<const __half *>(&rec.pay[k / kG])[k % kG];
+        const float x = rec.gmin[k / kG] + __half2float(off);
+        const bool real = grp != kNoGroup && !isnan(x);
+        sv[c] = real ? x : INFINITY;
+        si[c] = real ? grp * kG + (k % kG) : kNoWindow;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) warp_sort32(sv[c], si[c], lane);
+    warp_merge32(sv[0], si[0], sv[1], si[1], lane);
+    warp_merge32(sv[2], si[2], sv[3], si[3], lane);
+    warp_merge32(sv[0], si[0], sv[2], si[2], lane);
+    const bool real = si[0] != kNoWindow;
+    cand_idx[(size_t)q * kTopK + lane] = real ? si[0] : -1;
+    cand_lb[(size_t)q * kTopK + lane] = real ? sv[0] + qnorm[q] : INFINITY;
+}
+
 // One warp per query: merges the sorted part lists into the final candidate list.
 __global__ void k_merge_parts(const float *__restrict__ part_v, const int *__restrict__ part_i, int Q, int nparts,
                               const float *__restrict__ qnorm, int *__restrict__ cand_idx,
-                              float *__restrict__ cand_lb) {
+                              float *__restrict__ cand_lb, const int *__restrict__ perm, int nperm) {
     const int lane = threadIdx.x & 31;
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= Q) return;
@@ -408,7 +484,11 @@ __global__ void k_merge_parts(const float *__restrict__ part_v, const int *__res
         if (__any_sync(kFull, lex_less(w, j, __shfl_sync(kFull, v, 31), __shfl_sync(kFull, i, 31))))
             warp_merge32(v, i, w, j, lane);
     }
-    const bool real = i != kNoWindow;
+    bool real = i != kNoWindow;
+    if (real && perm) {  // cluster-ordered positions -> window indices
+        real = i >= 0 && i < nperm;
+        i = real ? perm[i] : kNoWindow;
+    }
     cand_idx[(size_t)q * kTopK + lane] = real ? i : -1;
     cand_lb[(size_t)q * kTopK + lane] = real ? v + qnorm[q] : INFINITY;
 }
@@ -442,14 +522,15 @@ __global__ void k_pack_queries(const float *__restrict__ qcoord, int Q, int d, i
 // 0...).  Padding windows carry +inf and -inf in the hi and mid slots, so their score is NaN and
 // fails every comparison.
 __global__ void k_pack_exemplar(const float *__restrict__ et, const float *__restrict__ enorm, int N, int ntiles,
-                                int d, int da, int K, __half *__restrict__ out) {
+                                int d, int da, int K, const int *__restrict__ perm, __half *__restrict__ out) {
     const long total = (long)ntiles * kTN * K;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
         const int t = (int)(i / (kTN * K));
         const int rem = (int)(i - (long)t * kTN * K);
         const int m = rem / K, k = rem - m * K;
-        const long n = (long)t * kTN + m;
-        const bool pad = n >= N;
+        const long p = (long)t * kTN + m;
+        const bool pad = p >= N;
+        const long n = pad ? 0 : (perm ? perm[p] : p);  // row p holds window perm[p]
         const float nrm = pad ? 0.0f : enorm[n];
         float v = 0.0f;
         if (k <= d) {
@@ -525,6 +606,79 @@ __global__ void k_pack_queries_f8(const float *__restrict__ qcoord, int Q, int d
         out[(size_t)b * kQM * K + core_offset8(r, k, kQM)] = *reinterpret_cast<const uint8_t *>(&h);
     }
     if (ok && lane == 0) qscale[q] = tq;
+}
+
+// --- cluster-restricted probe planning (learned proposal) ---
+// Pairs (query q, probe rank r, cluster top[4q + r]) grouped by cluster; each cluster's pairs are
+// cut into blocks of <= 128 rows that scan the tiles holding the cluster's members.
+__global__ void k_ivf_count(const int *__restrict__ top, int Q, int C, int *__restrict__ cnt) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 4L * Q; i += (long)gridDim.x * blockDim.x) {
+        const int c = top[i];
+        if (c >= 0 && c < C) atomicAdd(&cnt[c], 1);
+    }
+}
+
+// one block: pair offsets, per-cluster fill cursors, and the block table (C <= 1024)
+__global__ void __launch_bounds__(1024) k_ivf_plan(const int *__restrict__ cnt, const int *__restrict__ moff, int C,
+                                                   int max_blocks, int *__restrict__ poff, int *__restrict__ cursor,
+                                                   int4 *__restrict__ blk, int *__restrict__ nblk) {
+    __shared__ int sp[1024], sb[1024];
+    const int c = threadIdx.x;
+    const int n = c < C ? cnt[c] : 0;
+    const int nb = (n + kQM - 1) / kQM;
+    sp[c] = n;
+    sb[c] = nb;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scans
+        const int a = c >= o ? sp[c - o] : 0, b = c >= o ? sb[c - o] : 0;
+        __syncthreads();
+        sp[c] += a;
+        sb[c] += b;
+        __syncthreads();
+    }
+    const int p0 = sp[c] - n, b0 = sb[c] - nb;
+    if (c < C) {
+        poff[c] = p0;
+        cursor[c] = p0;
+        const int lo = moff[c], hi = moff[c + 1];
+        const int t0 = lo / kTN, t1 = hi > lo ? (hi - 1) / kTN : t0 - 1;
+        for (int j = 0; j < nb && b0 + j < max_blocks; ++j)
+            blk[b0 + j] = make_int4(p0 + j * kQM, min(kQM, n - j * kQM), t0, t1 - t0 + 1);
+    }
+    if (c == 1023) *nblk = min(sb[1023], max_blocks);
+}
+
+__global__ void k_ivf_scatter(const int *__restrict__ top, int Q, int C, int *__restrict__ cursor,
+                              int *__restrict__ pair_q, int *__restrict__ pair_r) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 4L * Q; i += (long)gridDim.x * blockDim.x) {
+        const int c = top[i];
+        if (c < 0 || c >= C) continue;
+        const int slot = atomicAdd(&cursor[c], 1);
+        pair_q[slot] = (int)(i >> 2);
+        pair_r[slot] = (int)(i & 3);
+    }
+}
+
+// FP16 query tiles of the cluster-restricted blocks: block b, row r = pair f0 + r
+__global__ void k_pack_queries_ivf(const float *__restrict__ qcoord, int d, int da, int K, const int4 *__restrict__ blk,
+                                   const int *__restrict__ nblk, const int *__restrict__ pair_q,
+                                   __half *__restrict__ out) {
+    const int b = blockIdx.x;
+    if (b >= *nblk) return;
+    const int4 e = blk[b];
+    for (int i = threadIdx.x; i < kQM * K; i += blockDim.x) {
+        const int r = i / K, k = i - r * K;
+        float v = 0.0f;
+        if (r < e.y) {
+            const int q = pair_q[e.x + r];
+            if (k <= d)
+                v = qcoord[(size_t)q * da + k];
+            else if (k <= d + 3)
+                v = 1.0f;
+        }
+        *reinterpret_cast<__half *>(reinterpret_cast<unsigned char *>(out + (size_t)b * kQM * K) +
+                                    core_offset(r, k, kQM)) = __float2half_rn(v);
+    }
 }
 
 // Warm start: the previous search's 32 windows of each query, scored in FP32 from the same FP16
@@ -851,9 +1005,45 @@ void launch_pack_queries(const float *qcoord, int Q, int d, int da, int K, __hal
 }
 
 void launch_pack_exemplar(const float *et, const float *enorm, int N, int d, int da, int K, __half *out,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int *perm) {
     count_launches(1);
-    k_pack_exemplar<<<152 * 4, 256, 0, st>>>(et, enorm, N, tc_tiles(N), d, da, K, out);
+    k_pack_exemplar<<<152 * 4, 256, 0, st>>>(et, enorm, N, tc_tiles(N), d, da, K, perm, out);
+}
+
+int ivf_max_blocks(int Q, int C) { return (4 * Q + kQM - 1) / kQM + C; }
+
+void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float *qcoord, const float *qnorm, int d,
+                      int da, int K, const __half *etile_ivf, int ntiles, int N, const int *members, IvfBuffers &b,
+                      int *cand_idx, float *cand_lb, int *status, cudaStream_t st) {
+    if (Q == 0) return;
+    const int maxb = ivf_max_blocks(Q, C);
+    cudaMemsetAsync(b.cnt, 0, sizeof(int) * C, st);
+    count_launches(5);
+    k_ivf_count<<<152 * 4, 256, 0, st>>>(top, Q, C, b.cnt);
+    k_ivf_plan<<<1, 1024, 0, st>>>(b.cnt, moff, C, maxb, b.poff, b.cursor, b.blk, b.nblk);
+    k_ivf_scatter<<<152 * 4, 256, 0, st>>>(top, Q, C, b.cursor, b.pair_q, b.pair_r);
+    k_pack_queries_ivf<<<maxb, 256, 0, st>>>(qcoord, d, da, K, b.blk, b.nblk, b.pair_q, b.qtile);
+    // a record no block writes (none should) reads as empty: NaN minima are dropped by k_select
+    cudaMemsetAsync(b.kept, 0xFF, tc_kept_bytes(Q, 4), st);
+    static bool attr = false;
+    const size_t smem = sizeof(TcSmem) + 1024;
+    if (!attr) {
+        cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const int nstages = std::min(kMaxStages, kRing / (kTN * K * 2));
+    {
+        ProfScope ps(kProfProbe, st, 1);
+        const IvfArgs ivf{b.blk, b.nblk, b.pair_q, b.pair_r};
+        k_search_tc<2><<<maxb, kThreads, smem, st>>>(b.qtile, qnorm, Q, K, etile_ivf, ntiles, ntiles, nstages, nullptr,
+                                                    nullptr, N, nullptr, nullptr, nullptr, ivf,
+                                                    reinterpret_cast<KeptGroups *>(b.kept), status);
+    }
+    count_launches(2);
+    k_select<<<ceil_div((long)Q * 4 * 32, 256), 256, 0, st>>>(reinterpret_cast<const KeptGroups *>(b.kept), Q, 4, qnorm,
+                                                              nullptr, N, cand_idx, cand_lb, b.part_v, b.part_i);
+    k_merge_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(b.part_v, b.part_i, Q, 4, qnorm, cand_idx, cand_lb,
+                                                               members, N);
 }
 
 void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
@@ -868,7 +1058,7 @@ void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int 
 void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const void *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount, int fp8,
-                      const float *qscale, const float *enorm, int N) {
+                      const float *qscale, const float *enorm, int N, void *kept_buf) {
     if (qlist) nparts = 1;  // a listed search writes its candidates directly
     static bool attr[2] = {false, false};
     const size_t smem = sizeof(TcSmem) + 1024;
@@ -884,19 +1074,29 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
     const int tpp = (ntiles + nparts - 1) / nparts;
     const int eb = fp8 ? 1 : 2;
     const int nstages = std::min(kMaxStages, kRing / (kTN * K * eb));
-    ProfScope ps(kProfSearchTc, st, nparts > 1 ? 2 : 1);
+    KeptGroups *kept = reinterpret_cast<KeptGroups *>(kept_buf);
+    ProfScope ps(kProfSearchTc, st, nparts > 1 ? 3 : 2);
     if (fp8)
         k_search_tc<1><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
-                                                                  qscale, enorm, N, thr0, qlist, qcount, cand_idx,
-                                                                  cand_lb, part_v, part_i, status);
+                                                                  qscale, enorm, N, thr0, qlist, qcount, IvfArgs{},
+                                                                  kept, status);
     else
         k_search_tc<2><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
-                                                                  qscale, enorm, N, thr0, qlist, qcount, cand_idx,
-                                                                  cand_lb, part_v, part_i, status);
+                                                                  qscale, enorm, N, thr0, qlist, qcount, IvfArgs{},
+                                                                  kept, status);
+    if (qlist) {
+        // listed queries only: select for every row of the list
+        k_select_list<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(kept, qlist, qcount, Q, qnorm, cand_idx, cand_lb);
+        return;
+    }
+    k_select<<<ceil_div((long)Q * nparts * 32, 256), 256, 0, st>>>(kept, Q, nparts, qnorm, nullptr, N, cand_idx,
+                                                                    cand_lb, part_v, part_i);
     if (nparts > 1)
         k_merge_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, Q, nparts, qnorm, cand_idx,
-                                                                   cand_lb);
+                                                                   cand_lb, nullptr, 0);
 }
+
+size_t tc_kept_bytes(int Q, int nparts) { return sizeof(KeptGroups) * 2 * (size_t)std::max(Q, 1) * nparts; }
 
 int tc_padded_k8(int d) { return ((d + 1) + 31) / 32 * 32; }
 
