@@ -199,9 +199,9 @@ LEVEL_MODES = {
     # 76% of the variance) searched exactly, the two finer levels on the FP16 tensor cores
     "f16c": ["exact", "f16", "f16"],
     "fp8c": ["exact", "fp8", "fp8"],
-    # the learned proposal on the finest level (the proposal trained there); the coarse levels,
-    # whose exemplars hold 1-13k windows, use the FP16 tensor-core brute force
-    "proposal": ["f16", "f16", "proposal"],
+    # the learned proposal on the finest level (the proposal trained there), the middle level on
+    # the FP16 tensor-core brute force, the coarsest exact (as f16c)
+    "proposal": ["exact", "f16", "proposal"],
 }
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
 

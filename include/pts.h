@@ -212,6 +212,13 @@ pts_status pts_project_queries(pts_index index, const float *output, int Ho, int
 pts_status pts_train_proposal(pts_index index, const float *y, const int32_t *nn, const float *d2, int n,
                               const pts_proposal_params *params, double *loss_out, void *stream);
 
+/* The 4 clusters the trained network ranks first for each query of `output` (test support,
+ * no counterpart in the paper): fused != 0 runs the fused inference kernel the search uses,
+ * fused == 0 the training-side GEMM path plus a separate top-4 (the two must agree).
+ * top_out device, Q x 4 int32.  Asynchronous. */
+pts_status pts_proposal_top4(pts_index index, const float *output, int Ho, int Wo, int stride, int fused,
+                             int32_t *top_out, void *stream);
+
 /* Inspection of a trained proposal (test support, no counterpart in the paper): the number of
  * clusters, and optionally their sizes (host, n_clusters ints) and the cluster of every exemplar
  * window (host, N ints).  Synchronises the device.  INVALID_ARG when no proposal is trained. */

@@ -23,6 +23,7 @@ from ._binding import (  # noqa: F401
     pca_fit,
     project_queries,
     proposal_info,
+    proposal_top4,
     synthesize_level,
     train_proposal,
     upsample2,

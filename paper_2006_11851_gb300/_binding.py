@@ -99,6 +99,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     L.pts_gemm_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd)]
     L.pts_tc_selftest.argtypes = [_I, _I, _I, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
     L.pts_proposal_info.argtypes = [_vp, ctypes.POINTER(_I), _vp, _vp]
+    L.pts_proposal_top4.argtypes = [_vp, _vp, _I, _I, _I, _I, _vp, _vp]
     L.pts_launch_count.restype = ctypes.c_longlong
     L.pts_profile_enable.argtypes = [_I]
     L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
@@ -297,6 +298,15 @@ def train_proposal(index: ExemplarIndex, y: torch.Tensor, nn: torch.Tensor, d2: 
     _check(lib().pts_train_proposal(index.handle, _ptr(y), _ptr(nn), _ptr(d2), n, ctypes.byref(p),
                                     loss.ctypes.data_as(ctypes.c_void_p), _stream()))
     return loss
+
+
+def proposal_top4(index: ExemplarIndex, output: torch.Tensor, stride: int = 2, fused: bool = True) -> torch.Tensor:
+    """[Q, 4] int32: the network's 4 best-ranked clusters per query (fused kernel or GEMM path)."""
+    _need(output, torch.float32, "output")
+    Ho, Wo, _ = output.shape
+    top = torch.empty(index.num_queries(Ho, Wo, stride), 4, dtype=torch.int32, device=output.device)
+    _check(lib().pts_proposal_top4(index.handle, _ptr(output), Ho, Wo, stride, 1 if fused else 0, _ptr(top), _stream()))
+    return top
 
 
 def proposal_info(index: ExemplarIndex):

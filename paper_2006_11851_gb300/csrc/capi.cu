@@ -131,14 +131,7 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
                    ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
     PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
-    PTS_TRY(pr.mlp.ensure(pr.C, std::min(Q, kMlpChunk), st));
-    for (int q0 = 0; q0 < Q; q0 += kMlpChunk) {
-        const int B = std::min(kMlpChunk, Q - q0);
-        mlp_gather(pr.mlp, ws.qcoord.ptr + (size_t)q0 * idx->da_fast, std::min(idx->d, 64), idx->da_fast, nullptr, 0,
-                   B, nullptr, st);
-        mlp_forward(pr.mlp, B, 0, idx->status.ptr, st);
-        launch_top4(pr.mlp.z.ptr, B, pr.C, pr.top.ptr + (size_t)q0 * 4, st);
-    }
+    launch_mlp_top4(pr.infer, ws.qcoord.ptr, Q, std::min(idx->d, 64), idx->da_fast, pr.top.ptr, idx->status.ptr, st);
     // probe: the tensor-core search restricted, per (query, cluster) pair, to the cluster's tiles
     const int maxb = ivf_max_blocks(Q, pr.C);
     PTS_TRY(pr.ivf_cnt.ensure(pr.C, "probe counts"));
@@ -632,6 +625,34 @@ pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int W
     return PTS_OK;
 }
 
+pts_status pts_proposal_top4(pts_index idx, const float *output, int Ho, int Wo, int stride, int fused,
+                             int32_t *top_out, void *stream) {
+    if (!idx || !output || !top_out) return set_error(PTS_ERR_INVALID_ARG, "pts_proposal_top4: null pointer");
+    ProposalState &pr = idx->prop;
+    if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "pts_proposal_top4: no proposal trained on this index");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "pts_proposal_top4"));
+    cudaStream_t st = as_stream(stream);
+    const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
+    PTS_TRY(ensure_workspace(idx, Q));
+    Workspace &ws = idx->ws;
+    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+                   ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
+    if (fused) {
+        launch_mlp_top4(pr.infer, ws.qcoord.ptr, Q, std::min(idx->d, 64), idx->da_fast, top_out, idx->status.ptr, st);
+    } else {
+        PTS_TRY(pr.mlp.ensure(pr.C, std::min(Q, kMlpChunk), st));
+        for (int q0 = 0; q0 < Q; q0 += kMlpChunk) {
+            const int B = std::min(kMlpChunk, Q - q0);
+            mlp_gather(pr.mlp, ws.qcoord.ptr + (size_t)q0 * idx->da_fast, std::min(idx->d, 64), idx->da_fast, nullptr,
+                       0, B, nullptr, st);
+            mlp_forward(pr.mlp, B, 0, idx->status.ptr, st);
+            launch_top4(pr.mlp.z.ptr, B, pr.C, top_out + (size_t)q0 * 4, st);
+        }
+    }
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
 pts_status pts_proposal_info(pts_index idx, int *n_clusters, int *sizes_out, int *assign_out) {
     if (!idx || !n_clusters) return set_error(PTS_ERR_INVALID_ARG, "pts_proposal_info: null pointer");
     ProposalState &pr = idx->prop;
@@ -744,6 +765,7 @@ pts_status pts_train_proposal(pts_index idx, const float *y, const int32_t *nn, 
     }
     PTS_CUDA_TRY(cudaStreamSynchronize(st));
     PTS_TRY(read_status(idx, st));
+    PTS_TRY(mlp_pack_infer(pr.mlp, pr.infer, st));
     pr.ready = 1;
     return PTS_OK;
 }

@@ -125,6 +125,13 @@ struct MlpState {
     pts_status ensure(int C_, int Bmax, cudaStream_t st);
 };
 
+struct MlpInfer {  // packed weights of the fused inference kernel (mlp_infer.cu)
+    int ready = 0, nchunk = 0;
+    DevBuf<__nv_bfloat16> wp1, wp2, wp3;
+    DevBuf<float> b3p;
+    const float *b1 = nullptr, *b2 = nullptr;
+};
+
 struct ProposalState {
     int ready = 0, C = 0;
     float factor = 1.2f;
@@ -143,6 +150,7 @@ struct ProposalState {
     DevBuf<int> ivf_part_i;
     DevBuf<unsigned char> ivf_kept;
     MlpState mlp;
+    MlpInfer infer;
 };
 
 }  // namespace pts
@@ -255,6 +263,10 @@ pts_status kmeans_device(const float *Y, int n, int d, int k, const double *u, i
 void launch_extract_y(const float *et, int N, int da, int d, float *Y, cudaStream_t st);
 pts_status cluster_medians(const int *nn, const float *d2, int n, const int *assign, int N, int C, int *lab,
                            float *dist, float *median, cudaStream_t st);
+// mlp_infer.cu
+pts_status mlp_pack_infer(MlpState &s, MlpInfer &f, cudaStream_t st);
+void launch_mlp_top4(const MlpInfer &f, const float *qcoord, int Q, int d, int ldq, int *top, int *status,
+                     cudaStream_t st);
 // probe.cu
 void launch_top4(const float *logits, int Q, int C, int *top, cudaStream_t st);
 void launch_fallback(const int *nn, const float *d2, int Q, const int *assign, const float *median, float factor,

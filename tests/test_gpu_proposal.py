@@ -105,6 +105,18 @@ def test_training_reduces_loss(trained):
     assert loss[-1] < np.log(256.0)
 
 
+def test_fused_inference_matches_gemm_path(trained):
+    """The fused inference kernel ranks the same 4 clusters as the training-side GEMMs + top-4."""
+    pidx, init, _ = trained
+    ix = pidx.indices[1]
+    X = init(22)
+    pts.synthesize_level(pidx.indices[0], X, 3, mode="exact")
+    X = pts.upsample2(X)
+    a = pts.proposal_top4(ix, X, 2, fused=True)
+    b = pts.proposal_top4(ix, X, 2, fused=False)
+    assert torch.equal(a, b)
+
+
 def test_proposal_search_against_exact(trained):
     pidx, init, _ = trained
     ix = pidx.indices[1]
