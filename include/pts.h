@@ -171,6 +171,16 @@ void pts_index_destroy(pts_index index);
 /* Fills *info (host) with the index's sizes and PCA summary. */
 pts_status pts_index_get_info(pts_index index, pts_index_info *info);
 
+/* Sets how many CTAs split the exemplar tiles of one 128-query block in the
+ * tensor-core searches (PTS_F16_RERANK, PTS_FP8_RERANK); 0 restores the
+ * automatic choice, which fills the 152 SMs when the query blocks alone do not.
+ * The candidates, hence the results, are the same for every split: each part
+ * keeps its own best groups and the merge takes the best of their union.
+ * A tuning knob only (pts_batch_create sets it from timings).  PTS_ERR_INVALID_ARG
+ * for a NULL index or parts < 0; parts larger than the tile count act as the
+ * tile count. */
+pts_status pts_index_set_tc_parts(pts_index index, int parts);
+
 /* Reads and clears the index's device status word (synchronises `stream`).
  * Returns PTS_OK, PTS_ERR_DEVICE or PTS_ERR_TIMEOUT. */
 pts_status pts_index_device_status(pts_index index, void *stream);

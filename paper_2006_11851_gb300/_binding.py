@@ -78,6 +78,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.pts_index_destroy.restype = None
         L.pts_index_get_info.argtypes = [_vp, ctypes.POINTER(_IndexInfo)]
         L.pts_index_device_status.argtypes = [_vp, _vp]
+        L.pts_index_set_tc_parts.argtypes = [_vp, _I]
         L.nn_search.argtypes = [_vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
         L.pts_index_search_stats.argtypes = [_vp, ctypes.POINTER(_SearchStats), _vp]
         L.irls_weights.argtypes = [_vp, _I, _F, _F, _vp, _vp, _vp]
@@ -198,6 +199,10 @@ class ExemplarIndex:
 
     def device_status(self) -> None:
         _check(lib().pts_index_device_status(self.handle, _stream()))
+
+    def set_tc_parts(self, parts: int) -> None:
+        """Exemplar split of the tensor-core searches (0 = automatic); results do not depend on it."""
+        _check(lib().pts_index_set_tc_parts(self.handle, int(parts)))
 
 
 def build_exemplar_index(exemplar: torch.Tensor, w: int, d: int = 0, var_frac: float = 0.95,

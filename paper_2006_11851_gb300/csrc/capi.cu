@@ -222,10 +222,6 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             const int ntc = tc_tiles(idx->N);
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
-            if (nparts > 1) {
-                PTS_TRY(ws.part_v.ensure((size_t)Q * nparts * kTopK, "part lists"));
-                PTS_TRY(ws.part_i.ensure((size_t)Q * nparts * kTopK, "part lists"));
-            }
             launch_pack_queries(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->ktc, ws.qtile.ptr, st);
             // the candidate lists of the previous search on this grid seed the bound
             const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
@@ -258,10 +254,6 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
             PTS_TRY(ws.qtile8.ensure((size_t)tc_query_blocks(Q) * 128 * idx->kf8, "fp8 query tiles"));
             PTS_TRY(ws.qscale.ensure((size_t)std::max(Q, 1), "fp8 query scales"));
-            if (nparts > 1) {
-                PTS_TRY(ws.part_v.ensure((size_t)Q * nparts * kTopK, "part lists"));
-                PTS_TRY(ws.part_i.ensure((size_t)Q * nparts * kTopK, "part lists"));
-            }
             launch_pack_queries_f8(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->kf8, idx->f8scale.ptr,
                                    ws.qtile8.ptr, ws.qscale.ptr, st);
             PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, nparts), "kept groups"));
@@ -516,6 +508,12 @@ pts_status pts_index_get_info(pts_index idx, pts_index_info *info) {
     info->eig_top = idx->eig_top;
     info->eig_iters = idx->eig_iters;
     info->unorm2_max = idx->unorm2_max;
+    return PTS_OK;
+}
+
+pts_status pts_index_set_tc_parts(pts_index idx, int parts) {
+    if (!idx || parts < 0) return set_error(PTS_ERR_INVALID_ARG, "pts_index_set_tc_parts: null index or parts < 0");
+    idx->tc_parts_override = parts;
     return PTS_OK;
 }
 

@@ -27,8 +27,9 @@
 // lane) and keeps the 32 smallest (score, window) pairs by bitonic sort and merge.  Padding
 // windows score NaN: a group minimum ignores them and they are dropped.
 //
-// The exemplar tiles of a query block may be split across blockIdx.y; each part writes its
-// sorted 32 and k_merge_parts merges them.  Optional per-query, per-half bounds thr0 (warm
+// The exemplar tiles of a query block may be split across blockIdx.y; each part keeps the 8 best
+// groups of its own tiles and k_select_parts takes the 8 best of their union per half, so the
+// result does not depend on the split.  Optional per-query, per-half bounds thr0 (warm
 // start, an upper bound on the 8th best group minimum of each half) seed the group lists with
 // sentinels (thr0, none): only groups whose minimum is below the bound are kept, and since at
 // least 8 are, the kept groups are the same as without the bound.  All waits are bounded; on a
@@ -111,6 +112,44 @@ __device__ __forceinline__ void warp_merge32(float &v, int &i, float w, int j, i
             v = ov;
             i = oi;
         }
+    }
+}
+
+// (value, index) pairs as one 64-bit key ordered like the pair: the float's bits mapped to an
+// unsigned order (negative values flipped) in the high word, the index in the low word.
+__device__ __forceinline__ unsigned long long pack_key(float v, int i) {
+    unsigned int u = __float_as_uint(v);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (unsigned int)i;
+}
+__device__ __forceinline__ float key_value(unsigned long long k) {
+    unsigned int u = (unsigned int)(k >> 32);
+    u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    return __uint_as_float(u);
+}
+__device__ __forceinline__ int key_index(unsigned long long k) { return (int)(unsigned int)(k & 0xffffffffu); }
+
+// Ascending bitonic sort of one key per lane, branch-free compare-exchange.
+__device__ __forceinline__ void warp_sort_keys(unsigned long long &k, int lane) {
+#pragma unroll
+    for (int s = 2; s <= 32; s <<= 1) {
+#pragma unroll
+        for (int j = s >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, k, j);
+            const bool keep_min = ((lane & s) == 0) == ((lane & j) == 0);
+            k = (keep_min == (o < k)) ? o : k;
+        }
+    }
+}
+
+// k := the 32 smallest of two ascending key lists k and w, ascending.
+__device__ __forceinline__ void warp_merge_keys(unsigned long long &k, unsigned long long w, int lane) {
+    const unsigned long long rw = __shfl_sync(kFull, w, 31 - lane);
+    k = rw < k ? rw : k;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, k, s);
+        k = (((lane & s) == 0) == (o < k)) ? o : k;
     }
 }
 
@@ -401,8 +440,8 @@ __global__ void __launch_bounds__(256) k_select(const KeptGroups *__restrict__ k
     const int lane = threadIdx.x & 31;
     const long o = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (o >= (long)Q * nparts) return;
-    float sv[4];
-    int si[4];
+    const unsigned long long kNone = pack_key(INFINITY, kNoWindow);
+    unsigned long long key[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const KeptGroups &rec = kept[o * 2 + (c >> 1)];
@@ -410,28 +449,90 @@ __global__ void __launch_bounds__(256) k_select(const KeptGroups *__restrict__ k
         const int grp = rec.gmap[k / kG];
         const __half off = reinterpret_cast<const __half *>(&rec.pay[k / kG])[k % kG];
         const float x = rec.gmin[k / kG] + __half2float(off);
-        const bool real = grp != kNoGroup && !isnan(x);
-        sv[c] = real ? x : INFINITY;
-        si[c] = real ? grp * kG + (k % kG) : kNoWindow;
+        key[c] = (grp != kNoGroup && !isnan(x)) ? pack_key(x, grp * kG + (k % kG)) : kNone;
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) warp_sort32(sv[c], si[c], lane);
-    warp_merge32(sv[0], si[0], sv[1], si[1], lane);
-    warp_merge32(sv[2], si[2], sv[3], si[3], lane);
-    warp_merge32(sv[0], si[0], sv[2], si[2], lane);
+    for (int c = 0; c < 4; ++c) warp_sort_keys(key[c], lane);
+    warp_merge_keys(key[0], key[1], lane);
+    warp_merge_keys(key[2], key[3], lane);
+    warp_merge_keys(key[0], key[2], lane);
+    const float v = key_value(key[0]);
+    const int i = key_index(key[0]);
     if (nparts == 1) {
-        bool real = si[0] != kNoWindow;
-        int n = si[0];
+        bool real = i != kNoWindow;
+        int n = i;
         if (real && perm) {
             real = n >= 0 && n < N;
             n = real ? perm[n] : -1;
         }
         cand_idx[o * kTopK + lane] = real ? n : -1;
-        cand_lb[o * kTopK + lane] = real ? sv[0] + qnorm[o] : INFINITY;
+        cand_lb[o * kTopK + lane] = real ? v + qnorm[o] : INFINITY;
     } else {
-        part_v[o * kTopK + lane] = sv[0];
-        part_i[o * kTopK + lane] = si[0];
+        part_v[o * kTopK + lane] = v;
+        part_i[o * kTopK + lane] = i;
     }
+}
+
+// One warp per query of a search whose tiles were split into nparts parts of tpp tiles.  Each
+// part kept the 8 best groups of its own tiles per column half, so their union holds the 8 best
+// of the whole half: first those, by (minimum, group), then the 32 smallest (score, window) pairs
+// of the 2 x 8 groups.  The result is the single-part one, whatever the split or a warm bound.
+__global__ void __launch_bounds__(256) k_select_parts(const KeptGroups *__restrict__ kept, int Q, int nparts, int tpp,
+                                                      const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                      float *__restrict__ cand_lb) {
+    const int lane = threadIdx.x & 31;
+    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    const unsigned long long kNone = pack_key(INFINITY, kNoWindow);
+    unsigned long long best[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        best[h] = kNone;
+        for (int p0 = 0; p0 < nparts; p0 += 32 / kKeep) {
+            const int p = p0 + lane / kKeep, s = lane % kKeep;
+            unsigned long long g = kNone;
+            if (p < nparts) {
+                const KeptGroups &rec = kept[(q * nparts + p) * 2 + h];
+                const int grp = rec.gmap[s];
+                const float m = rec.gmin[s];
+                if (grp != kNoGroup && !isnan(m)) g = pack_key(m, grp);
+            }
+            warp_sort_keys(g, lane);
+            if (p0 == 0)
+                best[h] = g;
+            else
+                warp_merge_keys(best[h], g, lane);
+        }
+    }
+    // lanes 0..7 of best[h]: the 8 best groups of half h, ascending
+    unsigned long long key[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int h = c >> 1;
+        const int k = lane + 32 * (c & 1);  // rank k / 8 in half h, element k % 8
+        const unsigned long long g = __shfl_sync(kFull, best[h], k / kG);
+        key[c] = kNone;
+        if (g != kNone) {
+            const int grp = key_index(g);
+            const int p = grp / (kTN / kG) / tpp;
+            const KeptGroups &rec = kept[(q * nparts + p) * 2 + h];
+            int j = 0;
+#pragma unroll
+            for (int s = 1; s < kKeep; ++s) j = rec.gmap[s] == grp ? s : j;
+            const __half off = reinterpret_cast<const __half *>(&rec.pay[j])[k % kG];
+            const float x = rec.gmin[j] + __half2float(off);
+            if (!isnan(x)) key[c] = pack_key(x, grp * kG + (k % kG));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) warp_sort_keys(key[c], lane);
+    warp_merge_keys(key[0], key[1], lane);
+    warp_merge_keys(key[2], key[3], lane);
+    warp_merge_keys(key[0], key[2], lane);
+    const int i = key_index(key[0]);
+    const bool real = i != kNoWindow;
+    cand_idx[q * kTopK + lane] = real ? i : -1;
+    cand_lb[q * kTopK + lane] = real ? key_value(key[0]) + qnorm[q] : INFINITY;
 }
 
 // k_select for a device-side query list (one part per query)
@@ -445,8 +546,8 @@ __global__ void __launch_bounds__(256) k_select_list(const KeptGroups *__restric
     if (q < 0 || q >= Q) return;
     // same as k_select for row q with one part
     const int lane = threadIdx.x & 31;
-    float sv[4];
-    int si[4];
+    const unsigned long long kNone = pack_key(INFINITY, kNoWindow);
+    unsigned long long key[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const KeptGroups &rec = kept[(long)q * 2 + (c >> 1)];
@@ -454,18 +555,17 @@ __global__ void __launch_bounds__(256) k_select_list(const KeptGroups *__restric
         const int grp = rec.gmap[k / kG];
         const __half off = reinterpret_cast<const __half *>(&rec.pay[k / kG])[k % kG];
         const float x = rec.gmin[k / kG] + __half2float(off);
-        const bool real = grp != kNoGroup && !isnan(x);
-        sv[c] = real ? x : INFINITY;
-        si[c] = real ? grp * kG + (k % kG) : kNoWindow;
+        key[c] = (grp != kNoGroup && !isnan(x)) ? pack_key(x, grp * kG + (k % kG)) : kNone;
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) warp_sort32(sv[c], si[c], lane);
-    warp_merge32(sv[0], si[0], sv[1], si[1], lane);
-    warp_merge32(sv[2], si[2], sv[3], si[3], lane);
-    warp_merge32(sv[0], si[0], sv[2], si[2], lane);
-    const bool real = si[0] != kNoWindow;
-    cand_idx[(size_t)q * kTopK + lane] = real ? si[0] : -1;
-    cand_lb[(size_t)q * kTopK + lane] = real ? sv[0] + qnorm[q] : INFINITY;
+    for (int c = 0; c < 4; ++c) warp_sort_keys(key[c], lane);
+    warp_merge_keys(key[0], key[1], lane);
+    warp_merge_keys(key[2], key[3], lane);
+    warp_merge_keys(key[0], key[2], lane);
+    const int i = key_index(key[0]);
+    const bool real = i != kNoWindow;
+    cand_idx[(size_t)q * kTopK + lane] = real ? i : -1;
+    cand_lb[(size_t)q * kTopK + lane] = real ? key_value(key[0]) + qnorm[q] : INFINITY;
 }
 
 // One warp per query: merges the sorted part lists into the final candidate list.
@@ -476,21 +576,18 @@ __global__ void k_merge_parts(const float *__restrict__ part_v, const int *__res
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= Q) return;
     const size_t base = (size_t)q * nparts * kTopK;
-    float v = part_v[base + lane];
-    int i = part_i[base + lane];
-    for (int p = 1; p < nparts; ++p) {
-        const float w = part_v[base + (size_t)p * kTopK + lane];
-        const int j = part_i[base + (size_t)p * kTopK + lane];
-        if (__any_sync(kFull, lex_less(w, j, __shfl_sync(kFull, v, 31), __shfl_sync(kFull, i, 31))))
-            warp_merge32(v, i, w, j, lane);
-    }
+    unsigned long long k = pack_key(part_v[base + lane], part_i[base + lane]);
+    for (int p = 1; p < nparts; ++p)
+        warp_merge_keys(k, pack_key(part_v[base + (size_t)p * kTopK + lane], part_i[base + (size_t)p * kTopK + lane]),
+                        lane);
+    int i = key_index(k);
     bool real = i != kNoWindow;
     if (real && perm) {  // cluster-ordered positions -> window indices
         real = i >= 0 && i < nperm;
         i = real ? perm[i] : kNoWindow;
     }
     cand_idx[(size_t)q * kTopK + lane] = real ? i : -1;
-    cand_lb[(size_t)q * kTopK + lane] = real ? v + qnorm[q] : INFINITY;
+    cand_lb[(size_t)q * kTopK + lane] = real ? key_value(k) + qnorm[q] : INFINITY;
 }
 
 // Query vectors as FP16 MMA operand tiles: rows = queries, K = (y, r, 1, 1, 1, 0...); rows past Q
@@ -611,11 +708,22 @@ __global__ void k_pack_queries_f8(const float *__restrict__ qcoord, int Q, int d
 // --- cluster-restricted probe planning (learned proposal) ---
 // Pairs (query q, probe rank r, cluster top[4q + r]) grouped by cluster; each cluster's pairs are
 // cut into blocks of <= 128 rows that scan the tiles holding the cluster's members.
-__global__ void k_ivf_count(const int *__restrict__ top, int Q, int C, int *__restrict__ cnt) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 4L * Q; i += (long)gridDim.x * blockDim.x) {
+// Pair counts per cluster: a shared-memory histogram per block (most pairs fall into a few
+// large clusters, so global atomics per pair would serialise), one global add per bin.
+constexpr int kIvfChunk = 8192;  // pairs per block of the count and scatter kernels
+
+__global__ void __launch_bounds__(1024) k_ivf_count(const int *__restrict__ top, int Q, int C, int *__restrict__ cnt) {
+    __shared__ int h[1024];
+    for (int c = threadIdx.x; c < 1024; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    const long p0 = (long)blockIdx.x * kIvfChunk, p1 = min(4L * Q, p0 + kIvfChunk);
+    for (long i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
         const int c = top[i];
-        if (c >= 0 && c < C) atomicAdd(&cnt[c], 1);
+        if (c >= 0 && c < C) atomicAdd(&h[c], 1);
     }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x)
+        if (h[c]) atomicAdd(&cnt[c], h[c]);
 }
 
 // one block: pair offsets, per-cluster fill cursors, and the block table (C <= 1024)
@@ -648,36 +756,65 @@ __global__ void __launch_bounds__(1024) k_ivf_plan(const int *__restrict__ cnt, 
     if (c == 1023) *nblk = min(sb[1023], max_blocks);
 }
 
-__global__ void k_ivf_scatter(const int *__restrict__ top, int Q, int C, int *__restrict__ cursor,
-                              int *__restrict__ pair_q, int *__restrict__ pair_r) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 4L * Q; i += (long)gridDim.x * blockDim.x) {
-        const int c = top[i];
-        if (c < 0 || c >= C) continue;
-        const int slot = atomicAdd(&cursor[c], 1);
+// Writes each pair into its cluster's range: positions within the block from a shared-memory
+// histogram, one global reservation per (block, cluster).
+__global__ void __launch_bounds__(1024) k_ivf_scatter(const int *__restrict__ top, int Q, int C, int *__restrict__ cursor,
+                                                      int *__restrict__ pair_q, int *__restrict__ pair_r) {
+    __shared__ int h[1024], base[1024];
+    for (int c = threadIdx.x; c < 1024; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    const long p0 = (long)blockIdx.x * kIvfChunk, p1 = min(4L * Q, p0 + kIvfChunk);
+    constexpr int kPer = kIvfChunk / 1024;
+    int pos[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const long i = p0 + threadIdx.x + (long)k * 1024;
+        pos[k] = -1;
+        if (i < p1) {
+            const int c = top[i];
+            if (c >= 0 && c < C) pos[k] = atomicAdd(&h[c], 1);
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) base[c] = h[c] ? atomicAdd(&cursor[c], h[c]) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const long i = p0 + threadIdx.x + (long)k * 1024;
+        if (pos[k] < 0) continue;
+        const int slot = base[top[i]] + pos[k];
         pair_q[slot] = (int)(i >> 2);
         pair_r[slot] = (int)(i & 3);
     }
 }
 
-// FP16 query tiles of the cluster-restricted blocks: block b, row r = pair f0 + r
+// FP16 query tiles of the cluster-restricted blocks: block b, row r = pair f0 + r; a thread
+// converts 8 consecutive values and stores them as one 16-byte core-matrix row.
 __global__ void k_pack_queries_ivf(const float *__restrict__ qcoord, int d, int da, int K, const int4 *__restrict__ blk,
                                    const int *__restrict__ nblk, const int *__restrict__ pair_q,
                                    __half *__restrict__ out) {
     const int b = blockIdx.x;
     if (b >= *nblk) return;
     const int4 e = blk[b];
-    for (int i = threadIdx.x; i < kQM * K; i += blockDim.x) {
-        const int r = i / K, k = i - r * K;
-        float v = 0.0f;
-        if (r < e.y) {
-            const int q = pair_q[e.x + r];
-            if (k <= d)
-                v = qcoord[(size_t)q * da + k];
-            else if (k <= d + 3)
-                v = 1.0f;
+    const int k8n = K / 8;
+    for (int i = threadIdx.x; i < kQM * k8n; i += blockDim.x) {
+        const int r = i / k8n, k0 = (i - r * k8n) * 8;
+        const int q = r < e.y ? pair_q[e.x + r] : -1;
+        float v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int k = k0 + t;
+            v[t] = q < 0 ? 0.0f : (k <= d ? qcoord[(size_t)q * da + k] : (k <= d + 3 ? 1.0f : 0.0f));
         }
-        *reinterpret_cast<__half *>(reinterpret_cast<unsigned char *>(out + (size_t)b * kQM * K) +
-                                    core_offset(r, k, kQM)) = __float2half_rn(v);
+        uint4 pk;
+        uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const __half2 h2 = __floats2half2_rn(v[2 * t], v[2 * t + 1]);
+            pw[t] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(out + (size_t)b * kQM * K) +
+                                   core_offset(r, k0, kQM)) = pk;
     }
 }
 
@@ -1019,12 +1156,12 @@ void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float
     const int maxb = ivf_max_blocks(Q, C);
     cudaMemsetAsync(b.cnt, 0, sizeof(int) * C, st);
     count_launches(5);
-    k_ivf_count<<<152 * 4, 256, 0, st>>>(top, Q, C, b.cnt);
+    const int nchunk = (int)ceil_div(4L * Q, kIvfChunk);
+    k_ivf_count<<<nchunk, 1024, 0, st>>>(top, Q, C, b.cnt);
     k_ivf_plan<<<1, 1024, 0, st>>>(b.cnt, moff, C, maxb, b.poff, b.cursor, b.blk, b.nblk);
-    k_ivf_scatter<<<152 * 4, 256, 0, st>>>(top, Q, C, b.cursor, b.pair_q, b.pair_r);
+    k_ivf_scatter<<<nchunk, 1024, 0, st>>>(top, Q, C, b.cursor, b.pair_q, b.pair_r);
     k_pack_queries_ivf<<<maxb, 256, 0, st>>>(qcoord, d, da, K, b.blk, b.nblk, b.pair_q, b.qtile);
-    // a record no block writes (none should) reads as empty: NaN minima are dropped by k_select
-    cudaMemsetAsync(b.kept, 0xFF, tc_kept_bytes(Q, 4), st);
+    // every (query, probe) pair has a row in some block, so every kept record is written
     static bool attr = false;
     const size_t smem = sizeof(TcSmem) + 1024;
     if (!attr) {
@@ -1075,7 +1212,7 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
     const int eb = fp8 ? 1 : 2;
     const int nstages = std::min(kMaxStages, kRing / (kTN * K * eb));
     KeptGroups *kept = reinterpret_cast<KeptGroups *>(kept_buf);
-    ProfScope ps(kProfSearchTc, st, nparts > 1 ? 3 : 2);
+    ProfScope ps(kProfSearchTc, st, 2);
     if (fp8)
         k_search_tc<1><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
                                                                   qscale, enorm, N, thr0, qlist, qcount, IvfArgs{},
@@ -1089,11 +1226,11 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
         k_select_list<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(kept, qlist, qcount, Q, qnorm, cand_idx, cand_lb);
         return;
     }
-    k_select<<<ceil_div((long)Q * nparts * 32, 256), 256, 0, st>>>(kept, Q, nparts, qnorm, nullptr, N, cand_idx,
-                                                                    cand_lb, part_v, part_i);
     if (nparts > 1)
-        k_merge_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, Q, nparts, qnorm, cand_idx,
-                                                                   cand_lb, nullptr, 0);
+        k_select_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(kept, Q, nparts, tpp, qnorm, cand_idx, cand_lb);
+    else
+        k_select<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(kept, Q, 1, qnorm, nullptr, N, cand_idx, cand_lb,
+                                                              part_v, part_i);
 }
 
 size_t tc_kept_bytes(int Q, int nparts) { return sizeof(KeptGroups) * 2 * (size_t)std::max(Q, 1) * nparts; }

@@ -95,6 +95,25 @@ def test_f16_warm_start_and_parts_change_nothing():
     idx.close()
 
 
+@pytest.mark.parametrize("mode", ["f16", "fp8"])
+def test_tc_split_changes_nothing(mode):
+    """Explicit exemplar splits (1 part, even, ragged last part) with and without the warm bound
+    give the single-part result bit for bit: the merge takes the best groups of the union."""
+    Z = P.synthetic_exemplar(2, 160, 4.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=48)
+    X = _t(P.random_patch_init(Z, 256, 256, 8, 4))
+    ref = None
+    for parts in [1, 2, 4, 7]:
+        idx.set_tc_parts(parts)
+        for _ in range(2):  # cold, then warm from the previous lists
+            nn, d2 = pts.nn_search(idx, X, 2, mode)
+            if ref is None:
+                ref = (nn.clone(), d2.clone())
+            assert torch.equal(nn, ref[0]) and torch.equal(d2, ref[1]), (mode, parts)
+    idx.set_tc_parts(0)
+    idx.close()
+
+
 def test_f16_energy_within_1_01_of_exact():
     Z = P.synthetic_exemplar(0, 64, 3.0)
     idx = pts.ExemplarIndex(_t(Z), 8, d=24)
