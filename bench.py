@@ -203,6 +203,7 @@ LEVEL_MODES = {
     # the FP16 tensor-core brute force, the coarsest exact (as f16c)
     "proposal": ["exact", "f16", "proposal"],
 }
+PCA_PASS_MIN_VAR = 0.85  # the exact search skips its PCA pass below this retained variance
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
 
 
@@ -337,9 +338,9 @@ def main():
     total_ms, launches, kern, energies, clocks = timed_run(modes, True)
     qps = queries_per_step(cfg) * args.steps * world / (total_ms / 1000.0)
     if args.mode == "exact":
-        ex_ms, ex_energies = total_ms, energies
+        ex_ms, ex_kern, ex_energies = total_ms, kern, energies
     else:
-        ex_ms, _, _, ex_energies, _ = timed_run(LEVEL_MODES["exact"], False)
+        ex_ms, _, ex_kern, ex_energies, _ = timed_run(LEVEL_MODES["exact"], True)
     exact_qps = queries_per_step(cfg) * args.steps * world / (ex_ms / 1000.0)
     ratios = [e / x for e, x in zip(energies, ex_energies)]
 
@@ -368,6 +369,20 @@ def main():
         e2e_ms = t.item()
     e2e_qps = queries_per_step(cfg) * args.steps * world / (e2e_ms / 1000.0)
 
+    # ---- the exact FP32 arm against the FP32 SIMT pipe (FMA rate measured here, this GPU) ----
+    fma_tf, _ = pts.fp32_fma_peak()
+    it = cfg["iters"] + 1
+    pca_levels = [(l, ix.info) for l, ix in zip(sizes, pidx.indices) if ix.info["var_retained"] >= PCA_PASS_MIN_VAR]
+    ex_roof = {"kernel": "k_search_pca (FP32 SIMT PCA-space bound GEMM + top-32)", "bound": "alu",
+               "achieved": None, "peak": fma_tf, "unit": "TFLOP/s", "frac": None,
+               "note": "algorithmic 2(d+1) flops per (query, window) pair at the levels that run the PCA pass "
+                       f"(d = {[inf['d'] for _, inf in pca_levels]}); peak = FP32 FMA probe measured in this run "
+                       f"(nominal {PEAK_FP32_TFLOPS:.1f} = 152 SMs x 128 lanes x 2 x 2070 MHz)"}
+    if "search_topk" in ex_kern and pca_levels:
+        fl = sum(2.0 * (inf["d"] + 1) * l["N"] * l["Q"] * it for l, inf in pca_levels)
+        ach = fl / (ex_kern["search_topk"]["ms_per_step"] / 1000.0) / 1e12
+        ex_roof.update(achieved=ach, frac=ach / fma_tf)
+
     # ---- roofline of the dominant kernel of this mode ----
     bf16_burst, bf16_sust, peak_src = _peaks()
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"]) if kern else None
@@ -390,12 +405,17 @@ def main():
                         note=f"algorithmic 2(d_fast+1) flops per (query, window) pair, d_fast={dfs}; peak = BF16 "
                              f"sustained (dense FP16 has the BF16 rate), {peak_src}")
     elif dom == "search_topk":
-        fl = sum(2.0 * (cfg["d"] + 1) * l["N"] * l["Q"] * it for l, m in zip(sizes, modes) if m == "exact")
+        roof.update(ex_roof, traffic=None)
+    elif dom == "search_full" and all(m != "exact" or ix.info["var_retained"] < PCA_PASS_MIN_VAR
+                                      for m, ix in zip(modes, pidx.indices)):
+        # exact levels without a PCA pass send every query to the full-dimension pass, and the
+        # other modes never reach it: the work is 2 D flops per (query, window) pair there
+        fl = sum(2.0 * 3 * l["w"] ** 2 * l["N"] * l["Q"] * it for l, m in zip(sizes, modes) if m == "exact")
         ach = fl / (kern[dom]["ms_per_step"] / 1000.0) / 1e12
-        roof.update(bound="alu", achieved=ach, peak=PEAK_FP32_TFLOPS, unit="TFLOP/s", frac=ach / PEAK_FP32_TFLOPS,
-                    kernel="k_search_pca (FP32 SIMT PCA-bound GEMM + top-32)", traffic=35.3e6,
-                    note="algorithmic 2(d+1) flops per pair; peak = 152 SMs x 128 lanes x 2 x 2070 MHz (derived); "
-                         "traffic = ncu dram read+write of one finest-level launch")
+        roof.update(bound="alu", achieved=ach, peak=fma_tf, unit="TFLOP/s", frac=ach / fma_tf,
+                    kernel="k_search_full (FP32 SIMT full-dimension GEMM + top-32)",
+                    note="algorithmic 2D flops per (query, window) pair at the exact levels; peak = FP32 FMA "
+                         "probe measured in this run")
     elif dom is not None:
         roof.update(note="dominant kernel without a roofline model in this script")
 
@@ -409,7 +429,11 @@ def main():
                        queries_per_step=queries_per_step(cfg), index_build_s=index_build_s,
                        proposal_train_s=train_s, proposal_pairs=n_pairs, proposal_clusters=args.clusters,
                        proposal_train_loss=train_loss, parallelism=f"replicas x{world}"),
-        "exact_fp32": {"value": exact_qps, "ms_per_step": ex_ms / args.steps},
+        "em_iterations_per_s": cfg["iters"] * cfg["levels"] * args.steps * world / (total_ms / 1000.0),
+        "exact_fp32": {"value": exact_qps, "ms_per_step": ex_ms / args.steps,
+                       "em_iterations_per_s": cfg["iters"] * cfg["levels"] * args.steps * world / (ex_ms / 1000.0),
+                       "kernels_per_step": ex_kern, "roofline": ex_roof},
+        "fp32_fma_peak_tflops": fma_tf,
         "speedup_vs_exact": qps / exact_qps,
         "final_energy_ratio_vs_exact": {"max": max(ratios), "mean": float(np.mean(ratios)),
                                         "within_1.01": bool(max(ratios) <= 1.01)},

@@ -390,6 +390,13 @@ pts_status pts_tc_selftest(int N, int K, int f16, double *max_abs_err, double *m
 void pts_profile_enable(int on);
 pts_status pts_profile_read(const char *kernel, double *total_ms, long long *launches);
 
+/* FP32 FMA throughput of this GPU (no counterpart in the paper; the denominator of the
+ * exact-mode rooflines, whose kernels run on the FP32 SIMT pipe).  A grid of 2 CTAs x 1024
+ * threads per SM, each thread running 8 independent FMA chains for `iters` x 128 FMAs
+ * (iters in 1..10^6), is timed with CUDA events on `stream` `reps` times (1..100); writes the
+ * best rate in TFLOP/s (2 flops per FMA) and its milliseconds.  Synchronises `stream`. */
+pts_status pts_fp32_fma_peak(int iters, int reps, void *stream, double *tflops, double *best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     PtsError,
     build_exemplar_index,
     downsample2,
+    fp32_fma_peak,
     gemm_selftest,
     irls_weights,
     kmeans,

@@ -104,6 +104,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     L.pts_launch_count.restype = ctypes.c_longlong
     L.pts_profile_enable.argtypes = [_I]
     L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
+    L.pts_fp32_fma_peak.argtypes = [_I, _I, _vp, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
 
 
 def _check(status: int) -> None:
@@ -355,3 +356,10 @@ def gemm_selftest(M: int, N: int, K: int) -> float:
     e = ctypes.c_double(0.0)
     _check(lib().pts_gemm_selftest(M, N, K, ctypes.byref(e)))
     return e.value
+
+
+def fp32_fma_peak(iters: int = 20000, reps: int = 5) -> tuple[float, float]:
+    """(TFLOP/s, ms) of the best of `reps` launches of the FP32 FMA probe on the current stream."""
+    tf, ms = _Dd(), _Dd()
+    _check(lib().pts_fp32_fma_peak(int(iters), int(reps), _stream(), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value

@@ -128,7 +128,7 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     Workspace &ws = idx->ws;
     ProposalState &pr = idx->prop;
     if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no proposal trained on this index");
-    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                    ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
     PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
     launch_mlp_top4(pr.infer, ws.qcoord.ptr, Q, std::min(idx->d, 64), idx->da_fast, pr.top.ptr, idx->status.ptr, st);
@@ -185,11 +185,11 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     if (idx->var_retained < kPcaPassMinVar) {
         // the d-dimensional bound would certify few queries: every query goes to the
         // full-dimension pass (its bound needs only ||u_q||^2 and the slack)
-        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, 0, idx->da, 0, nullptr,
+        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, 0, idx->da, 0, nullptr,
                        ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
         launch_list_all(ws.fail_list.ptr, fail_count, Q, st);
     } else {
-        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0,
+        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0,
                        ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st, &ws.proj_part);
         launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
                            idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
@@ -217,7 +217,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             break;
         case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
-            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
@@ -248,7 +248,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             // bound's rounding error is too large for a useful early exit, so every candidate is
             // re-ranked
             Workspace &ws = idx->ws;
-            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
@@ -331,7 +331,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad window");
     if (params->d > kMaxD) return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: d > 64");
     if (params->d_fast > kMaxDFast)
-        return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: d_fast > 92");
+        return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: d_fast > 124");
     const long N = (long)(He - w + 1) * (We - w + 1);
     if (N < 2 || N > (1L << 30))
         return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad exemplar size");
@@ -351,6 +351,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     idx->N = (int)N;
     pts_status s;
     if ((s = idx->exemplar.ensure((size_t)He * We * 3, "exemplar")) != PTS_OK) return fail(s);
+    if ((s = idx->exemplar4.ensure((size_t)He * We, "exemplar rgba")) != PTS_OK) return fail(s);
     if ((s = idx->status.ensure(1, "status")) != PTS_OK) return fail(s);
     if ((s = idx->mu.ensure(idx->D, "mean")) != PTS_OK) return fail(s);
     if ((s = idx->basis.ensure((size_t)kMaxDPca * idx->D, "basis")) != PTS_OK) return fail(s);
@@ -359,6 +360,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     cudaError_t e = cudaMemcpyAsync(idx->exemplar.ptr, exemplar, sizeof(float) * He * We * 3,
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "copy exemplar"));
+    launch_rgba(idx->exemplar.ptr, (long)He * We, idx->exemplar4.ptr, st);
     cudaMemsetAsync(idx->status.ptr, 0, sizeof(int), st);
     // one PCA serves both searches: the exact search uses its first d components, the
     // tensor-core and proposal searches the first d_fast (components are ordered by variance)
@@ -373,6 +375,8 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
                        idx->mu.ptr, idx->basis.ptr, idx->eig.ptr, &dd, &idx->var_retained,
                        &idx->eig_top, &idx->eig_iters, &trace, idx->status.ptr, st);
     if (s != PTS_OK) return fail(s);
+    if ((s = idx->basisT.ensure((size_t)idx->D * kMaxDPca, "transposed basis")) != PTS_OK) return fail(s);
+    launch_basis_transpose(idx->basis.ptr, dd, idx->D, idx->basisT.ptr, st);
     if (params->d > 0) {
         dd = std::min(params->d, dd);
     } else {  // smallest d (<= 64) whose eigenvalues reach var_frac of the trace
@@ -405,7 +409,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return fail(s);
     if ((s = idx->enorm.ensure((size_t)idx->ntiles * kBN, "exemplar norms")) != PTS_OK) return fail(s);
     launch_exemplar_pad(idx->et.ptr, idx->enorm.ptr, idx->N, idx->ntiles, idx->da, st);
-    launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basis.ptr, dd, idx->da, 1,
+    launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basisT.ptr, dd, idx->da, 1,
                    idx->et.ptr, idx->enorm.ptr, nullptr, 0.0f, nullptr, st);
     launch_norm_max(idx->enorm.ptr, idx->N, idx->umax.ptr, st);
     if ((s = idx->efull.ensure((size_t)idx->ntiles * padded_dim(w) * kBN, "full exemplar vectors")) !=
@@ -420,7 +424,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         DevBuf<float> norm_tmp;
         if ((s = norm_tmp.ensure((size_t)idx->ntiles * kBN, "norm scratch")) != PTS_OK) return fail(s);
         launch_exemplar_pad(idx->et_fast.ptr, norm_tmp.ptr, idx->N, idx->ntiles, idx->da_fast, st);
-        launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 1,
+        launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 1,
                        idx->et_fast.ptr, norm_tmp.ptr, nullptr, 0.0f, nullptr, st);
         cudaStreamSynchronize(st);
         norm_tmp.release();
@@ -466,8 +470,10 @@ void pts_index_destroy(pts_index idx) {
     ws.partial.release();
     ws.ticket.release();
     idx->exemplar.release();
+    idx->exemplar4.release();
     idx->mu.release();
     idx->basis.release();
+    idx->basisT.release();
     idx->eig.release();
     idx->et.release();
     idx->enorm.release();
@@ -574,7 +580,7 @@ pts_status m_step(pts_index idx, const int32_t *nn, const float *weights, int Ho
                   int stride, float *output, void *stream) {
     if (!idx || !nn || !output) return set_error(PTS_ERR_INVALID_ARG, "m_step: null pointer");
     PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "m_step"));
-    launch_m_step(nn, weights, idx->exemplar.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride,
+    launch_m_step(nn, weights, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride,
                   output, idx->status.ptr, as_stream(stream));
     PTS_CUDA_TRY(cudaGetLastError());
     return PTS_OK;
@@ -598,7 +604,7 @@ pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int st
         launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, ws.energy.ptr + t, ws.partial.ptr,
                     ws.ticket.ptr, st);
         if (t == iters) break;
-        launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar.ptr, idx->We, idx->nx, idx->N, idx->w, Ho,
+        launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho,
                       Wo, stride, output, idx->status.ptr, st);
     }
     PTS_CUDA_TRY(cudaGetLastError());
@@ -616,7 +622,7 @@ pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int W
     PTS_TRY(ensure_workspace(idx, Q));
     cudaStream_t st = as_stream(stream);
     Workspace &ws = idx->ws;
-    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
+    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
                    ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
     PTS_CUDA_TRY(cudaMemcpy2DAsync(y_out, sizeof(float) * idx->d, ws.qcoord.ptr, sizeof(float) * idx->da,
                                    sizeof(float) * idx->d, Q, cudaMemcpyDeviceToDevice, st));
@@ -633,7 +639,7 @@ pts_status pts_proposal_top4(pts_index idx, const float *output, int Ho, int Wo,
     const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
     PTS_TRY(ensure_workspace(idx, Q));
     Workspace &ws = idx->ws;
-    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basis.ptr, idx->d_fast, idx->da_fast, 0,
+    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                    ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
     if (fused) {
         launch_mlp_top4(pr.infer, ws.qcoord.ptr, Q, std::min(idx->d, 64), idx->da_fast, top_out, idx->status.ptr, st);

@@ -8,7 +8,10 @@
 // thread owns one patch: it walks the covering windows in increasing query
 // order (the order of the sum above), gathers the co-located s x s block of
 // each matched exemplar window and writes its s*s*3 outputs once.  No
-// atomics, deterministic.  The exemplar (<= a few MB) stays in L2.
+// atomics, deterministic.  The exemplar (<= a few MB) stays in L2, read from
+// an RGBA copy (alpha 0) so that each gathered pixel is one 16-byte load.
+#include <algorithm>
+
 #include "pts_internal.cuh"
 
 namespace pts {
@@ -16,7 +19,7 @@ namespace {
 
 template <int S>
 __global__ void __launch_bounds__(128)
-    k_m_step(const int *__restrict__ nn, const float *__restrict__ wts, const float *__restrict__ Z,
+    k_m_step(const int *__restrict__ nn, const float *__restrict__ wts, const float4 *__restrict__ Z4,
              int We, int ex, int N, int w, int Ho, int Wo, int qy_n, int qx_n,
              float *__restrict__ out, int *__restrict__ status) {
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,14 +49,16 @@ __global__ void __launch_bounds__(128)
             const float wt = wts ? __ldg(wts + p) : 1.0f;
             const int ey = n / ex, exx = n - ey * ex;
             const int ox = (px - qx) * S;
-            const float *zb = Z + ((size_t)(ey + oy) * We + (exx + ox)) * 3;
+            const float4 *zb = Z4 + (size_t)(ey + oy) * We + (exx + ox);
 #pragma unroll
             for (int t = 0; t < S; ++t)
 #pragma unroll
-                for (int u = 0; u < S; ++u)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        num[t][u][c] = fmaf(wt, __ldg(zb + ((size_t)t * We + u) * 3 + c), num[t][u][c]);
+                for (int u = 0; u < S; ++u) {
+                    const float4 v = __ldg(zb + (size_t)t * We + u);
+                    num[t][u][0] = fmaf(wt, v.x, num[t][u][0]);
+                    num[t][u][1] = fmaf(wt, v.y, num[t][u][1]);
+                    num[t][u][2] = fmaf(wt, v.z, num[t][u][2]);
+                }
             den += wt;
         }
     }
@@ -66,6 +71,11 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int c = 0; c < 3; ++c) o[u * 3 + c] = num[t][u][c] / den;
     }
+}
+
+__global__ void k_rgba(const float *__restrict__ Z, long npix, float4 *__restrict__ out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < npix; i += (long)gridDim.x * blockDim.x)
+        out[i] = make_float4(Z[3 * i], Z[3 * i + 1], Z[3 * i + 2], 0.0f);
 }
 
 // IRLS weights and energy (Eqs. 5-8).  Fixed grid; each block sums its
@@ -159,7 +169,13 @@ __global__ void k_upsample2(const float *__restrict__ in, int H, int W, float *_
 
 }  // namespace
 
-void launch_m_step(const int *nn, const float *wts, const float *Z, int We, int ex, int N, int w,
+void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st) {
+    if (npix <= 0) return;
+    count_launches(1);
+    k_rgba<<<(unsigned)std::min<long>(ceil_div(npix, 256), 152 * 8), 256, 0, st>>>(Z, npix, out);
+}
+
+void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w,
                    int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st) {
     const int qy_n = (Ho - w) / stride + 1, qx_n = (Wo - w) / stride + 1;
     const int PX = Wo / stride, PY = Ho / stride;
@@ -167,13 +183,13 @@ void launch_m_step(const int *nn, const float *wts, const float *Z, int We, int 
     ProfScope ps(kProfMStep, st, 1);
     switch (stride) {
         case 1:
-            k_m_step<1><<<grid, block, 0, st>>>(nn, wts, Z, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            k_m_step<1><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
             break;
         case 2:
-            k_m_step<2><<<grid, block, 0, st>>>(nn, wts, Z, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            k_m_step<2><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
             break;
         case 4:
-            k_m_step<4><<<grid, block, 0, st>>>(nn, wts, Z, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            k_m_step<4><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
             break;
         default:
             break;  // rejected by the caller

@@ -1,5 +1,6 @@
 // profile.cu -- launch counting and CUDA-event timing of kernel classes
 // (measurement support for the benchmark; no counterpart in the paper).
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string.h>
@@ -40,6 +41,25 @@ void clear_records() {
         }
         v.clear();
     }
+}
+
+// 8 independent FMA chains per thread, 16 steps unrolled per iteration; a and b keep the values
+// bounded (|a| < 1).  The sum is stored only when it equals a value it cannot reach, which keeps
+// every chain live without a store per thread.
+__global__ void __launch_bounds__(1024, 2) k_fma_peak(int iters, float a, float b, float never, float *out) {
+    float x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = (float)(threadIdx.x + c) * 1e-3f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = fmaf(x[c], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    if (s == never) out[blockIdx.x] = s;
 }
 
 }  // namespace
@@ -104,6 +124,44 @@ pts_status pts_profile_read(const char *kernel, double *total_ms, long long *lau
     }
     *total_ms = ms;
     *launches = (long long)pts::g_recs[cls].size();
+    return PTS_OK;
+}
+
+pts_status pts_fp32_fma_peak(int iters, int reps, void *stream, double *tflops, double *best_ms) {
+    if (!tflops || !best_ms || iters < 1 || iters > 1000000 || reps < 1 || reps > 100)
+        return pts::set_error(PTS_ERR_INVALID_ARG, "pts_fp32_fma_peak: iters in 1..1e6, reps in 1..100, outputs non-null");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    PTS_CUDA_TRY(cudaGetDevice(&dev));
+    PTS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 2 * sms;
+    pts::DevBuf<float> out;
+    PTS_TRY(out.ensure((size_t)blocks, "fma probe output"));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PTS_CUDA_TRY(cudaEventCreate(&e0));
+    PTS_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e30;
+    pts_status rc = PTS_OK;
+    for (int r = 0; r <= reps && rc == PTS_OK; ++r) {  // the first launch is a warm-up
+        pts::count_launches(1);
+        cudaEventRecord(e0, st);
+        pts::k_fma_peak<<<blocks, 1024, 0, st>>>(iters, 0.999f, 1e-3f, -1.0f, out.ptr);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            rc = pts::set_error(PTS_ERR_CUDA, "pts_fp32_fma_peak: launch failed");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out.release();
+    if (rc != PTS_OK) return rc;
+    const double fmas = (double)blocks * 1024.0 * 8.0 * 16.0 * iters;
+    *best_ms = best;
+    *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
     return PTS_OK;
 }
 

@@ -4,11 +4,11 @@
 //   y = B^T (v - mu)         (d coordinates)
 //   ||u||^2 = ||v - mu||^2
 //   r = sqrt(max(0, ||u||^2 - ||y||^2))  (norm of the discarded part)
-// A tiled SIMT GEMM (windows x D) (D x d): a block owns 64 windows and all d <= 128 outputs.
+// A tiled SIMT GEMM (windows x D) (D x d): a block owns 128 windows and all d <= 128 outputs.
 // Windows are read straight from the HWC image, never materialised: per 32-element slice of
-// the window vector the block stages the 64 centred slices and the basis slice in shared memory
-// (per-window base offsets and per-element offsets are precomputed, so a staged element is one
-// gather), and each thread accumulates a 4-window x 8-coordinate register tile.
+// the window vector the block stages the 128 centred slices and the slice of the transposed
+// basis ([D][128], built with the index) in shared memory, and each thread accumulates an
+// 8-window x 8-coordinate (4 for d <= 64) register tile.
 //
 // layout 0 (queries):  coord[win][da]              = (y, r, 0, ...)
 //                      tau[win] = tau_scale * (||u||^2 + max_n ||u_n||^2)
@@ -23,23 +23,22 @@
 namespace pts {
 namespace {
 
-constexpr int kPWin = 64;           // windows per block
+constexpr int kPWin = 128;          // windows per block
 constexpr int kPK = 32;             // window-vector elements per slice
-constexpr int kXs = kPWin + 1;      // row stride of the staged window slices
+constexpr int kXs = kPWin + 4;      // row stride of the staged window slices (16-byte rows)
+constexpr int kBT = kMaxDPca;       // row stride of the transposed basis [D][kBT]
 
 template <int PD>
 struct ProjSmem {
-    static constexpr int kBs = PD + 4;  // row stride of the staged basis slice (16-byte rows)
     union {
         struct {
-            float xs[kPK * kXs];              // [k][window], centred
-            alignas(16) float bs[kPK * kBs];  // [k][coordinate]
+            alignas(16) float xs[kPK * kXs];  // [k][window], centred
+            alignas(16) float bs[kPK * PD];   // [k][coordinate]
         } st;
         float ys[kPWin * (PD + 1)];           // the finished tile, [window][coordinate]
     } u;
-    long base[kPWin];               // image offset of each window's first element
-    int koff[kPK];                  // image offset of each element of the slice
-    float un[kPWin];
+    long base[kPWin];                 // image offset of each window's first element
+    float un[2][kPWin];               // ||u||^2 of each window, the two staging halves
 };
 
 struct ProjOut {
@@ -69,21 +68,28 @@ __device__ __forceinline__ void write_window(const ProjOut &o, long win, const f
     if (lane == 0) o.norm[win] = u2;
 }
 
-// PD = 64 or 128 output columns (d <= PD); thread tile 4 windows x PD/16 coordinates.  With
-// gridDim.y > 1 the block covers one slice range of the window vector and writes its partial
-// sums to part[blockIdx.y][win][PD + 1] (coordinates, then ||u||^2), reduced by k_project_finish.
+// PD = 64 or 128 output columns (d <= PD).  Thread (tx, ty) of 16 x 16 accumulates windows
+// ty*4 + {0..3} + {0, 64} times coordinates tx*4 + {0..3} + 64 g (g < PD/64): every operand
+// read is a 16-byte shared load, the window reads broadcast and the basis reads contiguous.
+// Staging: thread t gathers window t % 128 at the slice rows t / 128 + 2i (i < 16), adding its
+// squares to the window's norm, and four (PD = 128) or two float4 of the transposed basis; the
+// next slice is loaded into registers while the current one is multiplied.  With gridDim.y > 1
+// the block covers one slice range of the window vector and writes its partial sums to
+// part[blockIdx.y][win][PD + 1] (coordinates, then ||u||^2), reduced by k_project_finish.
 template <int PD>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_project(const float *__restrict__ img, int W, int w, int stride, int qx_n, int Qn,
-              const float *__restrict__ mu, const float *__restrict__ basis, int kper, ProjOut o,
+              const float *__restrict__ mu, const float *__restrict__ basisT, int kper, ProjOut o,
               float *__restrict__ part) {
-    constexpr int JD = PD / 16;
-    constexpr int kBs = ProjSmem<PD>::kBs;
-    __shared__ ProjSmem<PD> sm;
+    constexpr int NG = PD / 64;      // float4 groups of coordinates per thread
+    constexpr int TJ = 4 * NG;       // coordinates per thread
+    constexpr int NB = PD / 32;      // float4 of the basis slice per thread
+    extern __shared__ __align__(16) unsigned char proj_smem[];
+    ProjSmem<PD> &sm = *reinterpret_cast<ProjSmem<PD> *>(proj_smem);
     float *const xs = sm.u.st.xs;
     float *const bs = sm.u.st.bs;
     float *const ys = sm.u.ys;
-    const int row = 3 * w, D = row * w, d = o.d;
+    const int row = 3 * w, D = row * w, d = o.d, W3 = 3 * W;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long win0 = (long)blockIdx.x * kPWin;
     const int kbeg = blockIdx.y * kper, kend = min(D, kbeg + kper);
@@ -92,90 +98,124 @@ __global__ void __launch_bounds__(256)
         const long wq = win < Qn ? win : 0;
         const long qy = wq / qx_n, qx = wq - qy * qx_n;
         sm.base[tid] = (qy * stride * (long)W + qx * stride) * 3;
-        sm.un[tid] = 0.0f;
     }
-    float acc[4][JD];
+    __syncthreads();
+    const int sw = tid & (kPWin - 1), sk = tid >> 7;
+    const bool wvalid = win0 + sw < Qn;
+    const float *const src = img + sm.base[sw];
+    // element k0 + sk of the window vector at (row dy, offset e): image offset dy * W3 + e
+    int e0 = (kbeg + sk) % row;
+    long off0 = (long)((kbeg + sk) / row) * W3 + e0;
+    float xr[16];
+    float4 br[NB];
+    auto load_slice = [&](int k0) {
+        int e = e0;
+        long off = off0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < JD; ++j) acc[i][j] = 0.0f;
-    float un = 0.0f;
-    for (int k0 = kbeg; k0 < kend; k0 += kPK) {
-        if (tid < kPK) {
-            const int k = min(k0 + tid, D - 1);
-            const int dy = k / row, e = k - dy * row;
-            sm.koff[tid] = dy * W * 3 + e;
-        }
-        __syncthreads();
-        // window slices: consecutive threads take consecutive elements of one window
-#pragma unroll
-        for (int it = 0; it < kPWin * kPK / 256; ++it) {
-            const int idx = tid + 256 * it;
-            const int wl = idx / kPK, kk = idx - wl * kPK;
-            const int k = k0 + kk;
-            float v = 0.0f;
-            if (k < kend && win0 + wl < Qn) v = __ldg(img + sm.base[wl] + sm.koff[kk]) - __ldg(mu + k);
-            xs[kk * kXs + wl] = v;
-        }
-        // basis slice: row j of the basis is contiguous in k
-        for (int idx = tid; idx < PD * kPK; idx += 256) {
-            const int j = idx / kPK, kk = idx - j * kPK;
-            const int k = k0 + kk;
-            bs[kk * kBs + j] = (j < d && k < kend) ? __ldg(basis + (size_t)j * D + k) : 0.0f;
-        }
-        __syncthreads();
-        if (tid < kPWin) {
-#pragma unroll 8
-            for (int kk = 0; kk < kPK; ++kk) {
-                const float a = xs[kk * kXs + tid];
-                un = fmaf(a, a, un);
+        for (int i = 0; i < 16; ++i) {
+            const int k = k0 + sk + 2 * i;
+            xr[i] = (k < kend && wvalid) ? __ldg(src + off) - __ldg(mu + k) : 0.0f;
+            e += 2;
+            off += 2;
+            if (e >= row) {  // row >= 3: one wrap at most
+                e -= row;
+                off += W3 - row;
             }
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int f = tid + 256 * i;  // float4 index in the 32 x PD slice
+            const int kk = f / (PD / 4), j4 = f - kk * (PD / 4);
+            br[i] = (k0 + kk < kend) ? __ldg(reinterpret_cast<const float4 *>(basisT + (size_t)(k0 + kk) * kBT) + j4)
+                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    };
+    auto advance = [&]() {  // e0, off0 -> the same role in the next slice (32 elements on)
+        int e = e0 + kPK;
+        long off = off0 + kPK;
+        while (e >= row) {
+            e -= row;
+            off += W3 - row;
+        }
+        e0 = e;
+        off0 = off;
+    };
+    float acc[8][TJ];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < TJ; ++j) acc[i][j] = 0.0f;
+    float un = 0.0f;
+    load_slice(kbeg);
+    for (int k0 = kbeg; k0 < kend; k0 += kPK) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            xs[(sk + 2 * i) * kXs + sw] = xr[i];
+            un = fmaf(xr[i], xr[i], un);
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int f = tid + 256 * i;
+            const int kk = f / (PD / 4), j = 4 * (f - kk * (PD / 4));
+            float4 b = br[i];
+            b.x = j < d ? b.x : 0.0f;
+            b.y = j + 1 < d ? b.y : 0.0f;
+            b.z = j + 2 < d ? b.z : 0.0f;
+            b.w = j + 3 < d ? b.w : 0.0f;
+            *reinterpret_cast<float4 *>(&bs[kk * PD + j]) = b;
+        }
+        __syncthreads();
+        if (k0 + kPK < kend) {
+            advance();
+            load_slice(k0 + kPK);
         }
 #pragma unroll 4
         for (int kk = 0; kk < kPK; ++kk) {
-            float a[4];
+            const float4 a0 = *reinterpret_cast<const float4 *>(&xs[kk * kXs + ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&xs[kk * kXs + ty * 4 + 64]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[TJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = xs[kk * kXs + ty * 4 + i];
-            float b[JD];
-#pragma unroll
-            for (int j4 = 0; j4 < JD / 4; ++j4) {
-                const float4 bv = *reinterpret_cast<const float4 *>(&bs[kk * kBs + tx * JD + 4 * j4]);
-                b[4 * j4] = bv.x;
-                b[4 * j4 + 1] = bv.y;
-                b[4 * j4 + 2] = bv.z;
-                b[4 * j4 + 3] = bv.w;
+            for (int g = 0; g < NG; ++g) {
+                const float4 bv = *reinterpret_cast<const float4 *>(&bs[kk * PD + g * 64 + tx * 4]);
+                b[4 * g] = bv.x;
+                b[4 * g + 1] = bv.y;
+                b[4 * g + 2] = bv.z;
+                b[4 * g + 3] = bv.w;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < JD; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < TJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
+    sm.un[sk][sw] = un;
+    __syncthreads();
     if (gridDim.y > 1) {
         float *pb = part + (size_t)blockIdx.y * Qn * (PD + 1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const long win = win0 + ty * 4 + i;
+        for (int i = 0; i < 8; ++i) {
+            const long win = win0 + ty * 4 + (i & 3) + 64 * (i >> 2);
             if (win < Qn)
 #pragma unroll
-                for (int j = 0; j < JD; ++j) pb[win * (PD + 1) + tx * JD + j] = acc[i][j];
+                for (int j = 0; j < TJ; ++j) pb[win * (PD + 1) + (j >> 2) * 64 + tx * 4 + (j & 3)] = acc[i][j];
         }
-        if (tid < kPWin && win0 + tid < Qn) pb[(win0 + tid) * (PD + 1) + PD] = un;
+        if (tid < kPWin && win0 + tid < Qn) pb[(win0 + tid) * (PD + 1) + PD] = sm.un[0][tid] + sm.un[1][tid];
         return;
     }
     // (the loop ends with a barrier, so the staging buffers may be overwritten)
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < JD; ++j) ys[(ty * 4 + i) * (PD + 1) + tx * JD + j] = acc[i][j];
-    if (tid < kPWin) sm.un[tid] = un;
+        for (int j = 0; j < TJ; ++j)
+            ys[(ty * 4 + (i & 3) + 64 * (i >> 2)) * (PD + 1) + (j >> 2) * 64 + tx * 4 + (j & 3)] = acc[i][j];
     __syncthreads();
     const int lane = tid & 31, wp = tid >> 5;
     for (int wl = wp; wl < kPWin; wl += 8) {
         const long win = win0 + wl;
         if (win >= Qn) break;
-        write_window(o, win, &ys[wl * (PD + 1)], sm.un[wl], lane);
+        write_window(o, win, &ys[wl * (PD + 1)], sm.un[0][wl] + sm.un[1][wl], lane);
     }
 }
 
@@ -224,6 +264,14 @@ __global__ void __launch_bounds__(256) k_window_norms(const float *__restrict__ 
     }
 }
 
+// basisT[k][j] = basis[j][k] for the computed components j < dcount, 0 past them
+__global__ void k_basis_transpose(const float *__restrict__ basis, int dcount, int D, float *__restrict__ basisT) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)D * kBT) return;
+    const int k = (int)(i / kBT), j = (int)(i - (long)k * kBT);
+    basisT[i] = j < dcount ? basis[(size_t)j * D + k] : 0.0f;
+}
+
 __global__ void k_fill(float *p, long n, float v) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         p[i] = v;
@@ -246,7 +294,7 @@ __global__ void k_norm_max(const float *__restrict__ v, int n, float *__restrict
 }  // namespace
 
 void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
-                    const float *basis, int d, int da, int layout, float *out_coord,
+                    const float *basisT, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
                     cudaStream_t st, DevBuf<float> *scratch) {
     const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
@@ -271,10 +319,18 @@ void launch_project(const float *img, int H, int W, int w, int stride, const flo
     nsplit = ceil_div(D, kper);
     const dim3 grid((unsigned)nblk, nsplit);
     float *part = nsplit > 1 ? scratch->ptr : nullptr;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_project<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ProjSmem<64>));
+        cudaFuncSetAttribute(k_project<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ProjSmem<128>));
+        attr = true;
+    }
     if (PDc == 64)
-        k_project<64><<<grid, 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basis, kper, o, part);
+        k_project<64><<<grid, 256, sizeof(ProjSmem<64>), st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basisT, kper, o,
+                                                               part);
     else
-        k_project<128><<<grid, 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basis, kper, o, part);
+        k_project<128><<<grid, 256, sizeof(ProjSmem<128>), st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basisT, kper,
+                                                                 o, part);
     if (nsplit > 1) {
         count_launches(1);
         if (PDc == 64)
@@ -282,6 +338,11 @@ void launch_project(const float *img, int H, int W, int w, int stride, const flo
         else
             k_project_finish<128><<<(unsigned)ceil_div(Qn, 8), 256, 0, st>>>(part, nsplit, (int)Qn, o);
     }
+}
+
+void launch_basis_transpose(const float *basis, int dcount, int D, float *basisT, cudaStream_t st) {
+    count_launches(1);
+    k_basis_transpose<<<(unsigned)ceil_div((long)D * kBT, 256), 256, 0, st>>>(basis, dcount, D, basisT);
 }
 
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st) {

@@ -165,8 +165,10 @@ struct pts_index_s {
     int eig_iters = 0;
     float unorm2_max = 0.0f;
     pts::DevBuf<float> exemplar;  // He*We*3
+    pts::DevBuf<float4> exemplar4; // He*We pixels as (r, g, b, 0): one 16-byte load per pixel
     pts::DevBuf<float> mu;        // D
     pts::DevBuf<float> basis;     // d*D
+    pts::DevBuf<float> basisT;    // [D][128]: the basis transposed, 0 past the computed components
     pts::DevBuf<double> eig;      // d
     pts::DevBuf<float> et;        // [ntiles][da][kBN] = -2 * (y_n, r_n, 0...)
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
@@ -203,9 +205,10 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
                           double *trace_out, int *status, cudaStream_t st);
 // project.cu
 void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
-                    const float *basis, int d, int da, int layout, float *out_coord,
+                    const float *basisT, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
                     cudaStream_t st, DevBuf<float> *scratch = nullptr);
+void launch_basis_transpose(const float *basis, int dcount, int D, float *basisT, cudaStream_t st);
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st);
 void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
 // search_f32.cu
@@ -319,7 +322,8 @@ struct ProfScope {
     ~ProfScope() { prof_end(cls, st, tok); }
 };
 // mstep.cu
-void launch_m_step(const int *nn, const float *wts, const float *Z, int We, int ex, int N, int w,
+void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st);
+void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w,
                    int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st);
 void launch_irls(const float *d2, int Q, float r, float delta, float *wts, double *energy_out,
                  double *partial, unsigned int *ticket, cudaStream_t st);

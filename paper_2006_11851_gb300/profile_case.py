@@ -3,6 +3,11 @@ or (--pyramid) whole coarse-to-fine syntheses with a search mode per level.
 
     python -m paper_2006_11851_gb300.profile_case --level 2 --mode exact --steps 2
     python -m paper_2006_11851_gb300.profile_case --pyramid --modes exact,f16,f16 --steps 2
+    python -m paper_2006_11851_gb300.profile_case --big 4096 --steps 3
+
+--big H projects (d = 64) and averages (M-step) one H x H output against the finest level's
+index (256x256 exemplar, w = 8), so that the working set is far above the L2 cache: a uniform
+random image and uniform random matches with weights in [0.5, 1.5).
 
 Levels follow the 3-level workload (256x256 exemplar, shrink 4; windows 32/16/8; outputs
 128/256/512, d = 64).  The output image is a seeded random-patch initialisation.  Prints the
@@ -32,9 +37,12 @@ def main() -> int:
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--pyramid", action="store_true")
     ap.add_argument("--modes", default="exact,f16,f16")
+    ap.add_argument("--big", type=int, default=0)
     args = ap.parse_args()
     if args.pyramid:
         return run_pyramid(args)
+    if args.big:
+        return run_big(args)
     He, w, Ho = LEVELS[args.level]
     dev = torch.device("cuda:0")
     Z = P.synthetic_exemplar(0, 256, 4.0)
@@ -70,6 +78,38 @@ def run_pyramid(args) -> int:
         e1.synchronize()
         print(f"synthesis {s}: {e0.elapsed_time(e1):.3f} ms  final energies {E[:, -1]}")
     pidx.close()
+    return 0
+
+
+def run_big(args) -> int:
+    dev = torch.device("cuda:0")
+    z = torch.from_numpy(P.synthetic_exemplar(0, 256, 4.0)).to(dev)
+    idx = pts.ExemplarIndex(z, 8, d=args.d)
+    H = args.big
+    g = torch.Generator().manual_seed(0)
+    X = torch.rand(H, H, 3, generator=g).to(dev)
+    Q = idx.num_queries(H, H, 2)
+    nn = torch.randint(0, idx.info["N"], (Q,), generator=g, dtype=torch.int32).to(dev)
+    wts = (torch.rand(Q, generator=g) + 0.5).to(dev)
+    out = torch.empty(H, H, 3, device=dev)
+    da = idx.info["da"]
+    for s in range(args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        pts.project_queries(idx, X, 2)
+        ev[1].record()
+        pts.m_step(idx, nn, wts, H, H, 2, out)
+        ev[2].record()
+        ev[2].synchronize()
+        tp, tm = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        # compulsory bytes: projection reads the image and writes Q x da coordinates + 2 floats;
+        # the M-step reads Q matches and weights and writes the image
+        bp = H * H * 12 + Q * (da + 2) * 4
+        bm = Q * 8 + H * H * 12
+        print(f"step {s}: project {tp:.3f} ms ({bp / tp / 1e6:.0f} GB/s, "
+              f"{2.0 * idx.info['D'] * idx.info['d'] * Q / tp / 1e9:.1f} TFLOP/s)  "
+              f"m_step {tm:.3f} ms ({bm / tm / 1e6:.0f} GB/s)  Q={Q}")
+    idx.close()
     return 0
 
 
