@@ -114,7 +114,8 @@ pts_status exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail
     }
     launch_search_full(ra.X, ra.Wo, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
                        ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr,
-                       ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, np, idx->status.ptr, st);
+                       ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, np, idx->status.ptr, st, idx->N,
+                       &ws.full_pdist);
     launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out,
                   ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
     launch_brute_fallback(ra, ws.fail2_list.ptr, fail2_count, brute_count, ws.best64.ptr, idx->status.ptr, st);
@@ -461,6 +462,7 @@ void pts_index_destroy(pts_index idx) {
     ws.fail_list.release();
     ws.fail2_list.release();
     ws.qfull.release();
+    ws.full_pdist.release();
     ws.best64.release();
     ws.counters.release();
     ws.nn.release();

@@ -90,6 +90,7 @@ struct Workspace {
     DevBuf<int> fail_list;     // [Q] queries not certified by the PCA pass
     DevBuf<int> fail2_list;    // [Q] queries not certified by the full-dimension pass
     DevBuf<float> qfull;       // [Qpad/64][Dp][64] centred full vectors of failing queries
+    DevBuf<float> full_pdist;  // [splits][Q][ntiles*128] partial sums of a split full pass
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
     DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
@@ -219,7 +220,8 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                        int nparts, int *status, cudaStream_t st);
+                        int nparts, int *status, cudaStream_t st, int N,
+                        DevBuf<float> *pdist);
 int full_parts(int Q, int ntiles);
 void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st);

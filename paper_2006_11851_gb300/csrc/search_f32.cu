@@ -26,8 +26,10 @@
 #include <float.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "pts_internal.cuh"
+#include "warp_keys.cuh"
 
 namespace pts {
 namespace {
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                   int Q, int Dp, const float *__restrict__ efull,  // [ntiles][Dp][128] = -2 u_n
                   const float *__restrict__ enorm, int ntiles, int tiles_per_part,
                   const float *__restrict__ qnorm, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
-                  float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status) {
+                  float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status,
+                  int kc_split, float *__restrict__ pdist) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FullSmem &sm = *reinterpret_cast<FullSmem *>(smem_raw);
     const int nf = static_cast<int>(*fail_count);
@@ -195,8 +198,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (fbase >= nf) return;  // uniform for the CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = warp * 8;
-    const int nchunks = Dp / kKC;
-    // this CTA's exemplar tiles (blockIdx.y splits them; parts are merged afterwards)
+    // this CTA's exemplar tiles (blockIdx.y splits them; parts are merged afterwards) and chunks
+    // of the vector (blockIdx.z splits them when pdist is given: partial sums, summed afterwards)
+    const int c0 = blockIdx.z * kc_split, c1 = min(Dp / kKC, c0 + kc_split);
+    const int nchunks = c1 - c0;
     const int t_begin = blockIdx.y * tiles_per_part;
     const int nt = max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
     const long total = (long)nt * nchunks;
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     auto issue = [&](long it) {
         const int s = (int)(it % kStages);
         const long t = it / nchunks;
-        const int c = (int)(it - t * nchunks);
+        const int c = c0 + (int)(it - t * nchunks);
         mbar_expect_tx(&sm.bar[s], (uint32_t)(kKC * (kBQ + kBN) * 4));
         bulk_g2s(&sm.a[s][0][0], qa + (size_t)c * kKC * kBQ, kKC * kBQ * 4u, &sm.bar[s]);
         bulk_g2s(&sm.e[s][0][0], efull + ((size_t)(t_begin + t) * Dp + (size_t)c * kKC) * kBN, kKC * kBN * 4u,
@@ -224,9 +229,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (long it = 0; it < total; ++it) {
         const int s = (int)(it % kStages);
         const long t = it / nchunks;
-        const int c = (int)(it - t * nchunks);
-        if (c == 0) {
-            const float4 nv = __ldg(reinterpret_cast<const float4 *>(enorm + (t_begin + t) * kBN + lane * 4));
+        const int c = c0 + (int)(it - t * nchunks);
+        if (c == c0) {
+            const float4 nv = blockIdx.z == 0
+                                  ? __ldg(reinterpret_cast<const float4 *>(enorm + (t_begin + t) * kBN + lane * 4))
+                                  : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 acc[i][0] = nv.x;
@@ -258,10 +265,24 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
-        if (c == nchunks - 1) top.offer(acc, (int)(t_begin + t) * kBN, lane);
+        if (c == c1 - 1) {
+            if (pdist) {  // partial sums of this chunk range: [z][f][tile * 128 + window]
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int f = fbase + row0 + i;
+                    if (f < nf)
+                        *reinterpret_cast<float4 *>(pdist + ((size_t)blockIdx.z * Q + f) * ((size_t)ntiles * kBN) +
+                                                    (size_t)(t_begin + t) * kBN + lane * 4) =
+                            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                }
+            } else {
+                top.offer(acc, (int)(t_begin + t) * kBN, lane);
+            }
+        }
         __syncthreads();  // stage s is free
         if (tid == 0 && it + kStages < total) issue(it + kStages);
     }
+    if (pdist) return;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int f = fbase + row0 + i;
@@ -327,6 +348,40 @@ __global__ void k_merge_fail_parts(const float *__restrict__ part_v, const int *
     }
 }
 
+// One warp per listed query of a pass split along the vector: the nsplit partial sums of each
+// window added in split order, then the 32 smallest (p, n) kept by sorting each 32 windows and
+// merging them into the running list (skipped when none beats its 32nd).  Padding windows
+// (n >= N, p = +inf) never enter.
+__global__ void __launch_bounds__(256) k_full_select(const float *__restrict__ pdist, int nsplit, int npad, int N,
+                                                     const int *__restrict__ fail_list,
+                                                     const unsigned int *__restrict__ fail_count, int Q,
+                                                     const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                     float *__restrict__ cand_lb, int *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const long f = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= (long)*fail_count) return;
+    const unsigned long long kNone = pack_key(INFINITY, INT_MAX);
+    unsigned long long best = kNone;
+    for (int n0 = 0; n0 < npad; n0 += 32) {
+        const int n = n0 + lane;
+        float v = 0.0f;
+        for (int sp = 0; sp < nsplit; ++sp) v += pdist[((size_t)sp * Q + f) * npad + n];
+        unsigned long long k = (n < N && v < INFINITY) ? pack_key(v, n) : kNone;
+        if (!__any_sync(kFull, k < __shfl_sync(kFull, best, 31))) continue;
+        warp_sort_keys(k, lane);
+        warp_merge_keys(best, k, lane);
+    }
+    const int q = fail_list[f];
+    const int i = key_index(best);
+    const bool real = i != INT_MAX;
+    if (q >= 0 && q < Q) {
+        cand_idx[(size_t)q * kTopK + lane] = real ? i : -1;
+        cand_lb[(size_t)q * kTopK + lane] = real ? key_value(best) + qnorm[q] : INFINITY;
+    } else if (lane == 0) {
+        atomicOr(status, kDevErrBounds);
+    }
+}
+
 // u_q = x_q - mu of the failing queries, tiled [F/64][Dp][64], zero rows k >= D
 __global__ void k_gather_full(const float *__restrict__ X, int Wo, int w, int stride, int qx,
                               const float *__restrict__ mu, const int *__restrict__ fail_list,
@@ -385,7 +440,7 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                        int nparts, int *status, cudaStream_t st) {
+                        int nparts, int *status, cudaStream_t st, int N, DevBuf<float> *pdist) {
     static bool attr = false;
     const size_t smem = sizeof(FullSmem);
     if (!attr) {
@@ -396,12 +451,34 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
     count_launches(1);
     k_gather_full<<<152 * 4, 256, 0, st>>>(X, Wo, w, stride, qx, mu, fail_list, fail_count, Q, Dp,
                                            qfull);
+    // A grid of few (query block, tile) pairs with long vectors (the coarse levels, where every
+    // query takes this pass) is split along the vector as well, for about four CTAs per slot,
+    // each split at least four chunks long and the partial sums at most 256 MB.
+    const int nqb = ceil_div(Q, kBQ), nchunks = Dp / kKC;
+    const size_t npad = (size_t)ntiles * kBN;
+    int nsplit = 1;
+    if (pdist && (long)nqb * ntiles < 4L * 2 * 152) {
+        nsplit = std::min<long>(nchunks / 4, ceil_div(4L * 2 * 152, (long)nqb * ntiles));
+        while (nsplit > 1 && (size_t)nsplit * Q * npad * sizeof(float) > (256u << 20)) --nsplit;
+        if (nsplit > 1 && pdist->ensure((size_t)nsplit * Q * npad, "full-pass partial sums") != PTS_OK) nsplit = 1;
+    }
+    if (nsplit > 1) {
+        const int kcs = ceil_div(nchunks, nsplit);
+        nsplit = ceil_div(nchunks, kcs);
+        ProfScope ps(kProfSearchFull, st, 2);
+        k_search_full<<<dim3(nqb, ntiles, nsplit), kThreads, smem, st>>>(
+            qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles, 1, qnorm, cand_idx, cand_lb, part_v, part_i,
+            status, kcs, pdist->ptr);
+        k_full_select<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(pdist->ptr, nsplit, (int)npad, N, fail_list,
+                                                                    fail_count, Q, qnorm, cand_idx, cand_lb, status);
+        return;
+    }
     const int tpp = ceil_div(ntiles, nparts);
     const int np = ceil_div(ntiles, tpp);
     ProfScope ps(kProfSearchFull, st, np > 1 ? 2 : 1);
-    k_search_full<<<dim3(ceil_div(Q, kBQ), np), kThreads, smem, st>>>(qfull, fail_list, fail_count, Q, Dp,
-                                                                      efull, enorm, ntiles, tpp, qnorm, cand_idx,
-                                                                      cand_lb, part_v, part_i, status);
+    k_search_full<<<dim3(nqb, np), kThreads, smem, st>>>(qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles,
+                                                         tpp, qnorm, cand_idx, cand_lb, part_v, part_i, status,
+                                                         nchunks, nullptr);
     if (np > 1)
         k_merge_fail_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, fail_list, fail_count,
                                                                         Q, qnorm, cand_idx, cand_lb, status);
