@@ -192,8 +192,14 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     } else {
         launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0,
                        ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st, &ws.proj_part);
+        const int pp = pca_parts(Q, idx->ntiles);
+        if (pp > 1) {
+            PTS_TRY(ws.part_v.ensure((size_t)Q * pp * kTopK, "part lists"));
+            PTS_TRY(ws.part_i.ensure((size_t)Q * pp * kTopK, "part lists"));
+        }
         launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
-                           idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
+                           idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st, pp, ws.part_v.ptr,
+                           ws.part_i.ptr);
         // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
         launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
                       d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);

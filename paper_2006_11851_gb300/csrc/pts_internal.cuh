@@ -215,7 +215,8 @@ void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
 // search_f32.cu
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
-                        cudaStream_t st);
+                        cudaStream_t st, int nparts = 1,
+                        float *part_v = nullptr, int *part_i = nullptr);
 void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
@@ -223,6 +224,7 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
                         int nparts, int *status, cudaStream_t st, int N,
                         DevBuf<float> *pdist);
 int full_parts(int Q, int ntiles);
+int pca_parts(int Q, int ntiles);
 void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st);
 // search_tc.cu

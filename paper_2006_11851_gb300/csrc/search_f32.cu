@@ -94,8 +94,9 @@ struct PcaSmem {
 
 __global__ void __launch_bounds__(kThreads, 2)
     k_search_pca(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int da,
-                 const float *__restrict__ et, const float *__restrict__ enorm, int ntiles,
-                 int *__restrict__ cand_idx, float *__restrict__ cand_lb, int *__restrict__ status) {
+                 const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int tiles_per_part,
+                 int *__restrict__ cand_idx, float *__restrict__ cand_lb, float *__restrict__ part_v,
+                 int *__restrict__ part_i, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PcaSmem &sm = *reinterpret_cast<PcaSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -121,16 +122,21 @@ __global__ void __launch_bounds__(kThreads, 2)
         bulk_g2s(&sm.e[buf][0][0], et + (size_t)t * tile_floats, tile_floats * 4u, &sm.bar[buf]);
         bulk_g2s(&sm.en[buf][0], enorm + (size_t)t * kBN, kBN * 4u, &sm.bar[buf]);
     };
+    // this CTA's exemplar tiles (blockIdx.y splits them; the parts' lists are merged afterwards)
+    const int t_begin = blockIdx.y * tiles_per_part;
+    const int t_end = min(ntiles, t_begin + tiles_per_part);
+    const int nt = max(0, t_end - t_begin);
     if (tid == 0) {
-        issue(0, 0);
-        if (ntiles > 1) issue(1, 1);
+        if (nt > 0) issue(t_begin, 0);
+        if (nt > 1) issue(t_begin + 1, 1);
     }
-    for (int t = 0; t < ntiles; ++t) {
-        const int buf = t & 1;
-        if (tid == 0 && !mbar_wait_bounded(&sm.bar[buf], (t >> 1) & 1, status)) sm.abort_flag = 1;
+    for (int i = 0; i < nt; ++i) {
+        const int t = t_begin + i;
+        const int buf = i & 1;
+        if (tid == 0 && !mbar_wait_bounded(&sm.bar[buf], (i >> 1) & 1, status)) sm.abort_flag = 1;
         __syncthreads();
         if (sm.abort_flag) {
-            if (tid == 0 && t + 1 < ntiles) mbar_wait_bounded(&sm.bar[buf ^ 1], ((t + 1) >> 1) & 1, status);
+            if (tid == 0 && i + 1 < nt) mbar_wait_bounded(&sm.bar[buf ^ 1], ((i + 1) >> 1) & 1, status);
             __syncthreads();
             return;
         }
@@ -158,16 +164,41 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         top.offer(acc, t * kBN, lane);
         __syncthreads();  // all warps are done with buffer `buf`
-        if (tid == 0 && t + 2 < ntiles) issue(t + 2, buf);
+        if (tid == 0 && i + 2 < nt) issue(t + 2, buf);
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int q = qbase + row0 + i;
         if (q < Q) {
-            cand_idx[(size_t)q * kTopK + lane] = top.li[i];
-            cand_lb[(size_t)q * kTopK + lane] = top.ld[i] + qnorm[q];
+            if (gridDim.y > 1) {
+                const size_t o = ((size_t)q * gridDim.y + blockIdx.y) * kTopK + lane;
+                part_v[o] = top.ld[i];
+                part_i[o] = top.li[i];
+            } else {
+                cand_idx[(size_t)q * kTopK + lane] = top.li[i];
+                cand_lb[(size_t)q * kTopK + lane] = top.ld[i] + qnorm[q];
+            }
         }
     }
+}
+
+// One warp per query: the 32 smallest (p, n) of its nparts sorted part lists (missing entries
+// are (+inf, -1) and sort last), + ||u_q||^2.
+__global__ void __launch_bounds__(256) k_merge_pca_parts(const float *__restrict__ part_v,
+                                                         const int *__restrict__ part_i, int nparts, int Q,
+                                                         const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                         float *__restrict__ cand_lb) {
+    const int lane = threadIdx.x & 31;
+    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    const size_t base = (size_t)q * nparts * kTopK;
+    unsigned long long k = pack_key(part_v[base + lane], part_i[base + lane]);
+    for (int p = 1; p < nparts; ++p)
+        warp_merge_keys(k, pack_key(part_v[base + (size_t)p * kTopK + lane], part_i[base + (size_t)p * kTopK + lane]),
+                        lane);
+    const float v = key_value(k);
+    cand_idx[(size_t)q * kTopK + lane] = v < INFINITY ? key_index(k) : -1;
+    cand_lb[(size_t)q * kTopK + lane] = v + qnorm[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -420,9 +451,20 @@ __global__ void k_exemplar_full(const float *__restrict__ Z, int We, int w, int 
 
 }  // namespace
 
+// Exemplar parts of the PCA pass: only a grid of fewer query blocks than SMs is split (to about
+// two CTAs per SM, at least 8 tiles a part).  Larger grids stay whole: every part restarts its
+// top-32 from empty, and on the 64,009-query fine level a 3-way split measured slower.
+int pca_parts(int Q, int ntiles) {
+    const long nqb = ceil_div(Q, kBQ);
+    if (nqb >= 152) return 1;
+    int p = (int)std::min<long>(8, ceil_div(2L * 152, std::max(nqb, 1L)));
+    while (p > 1 && ntiles / p < 8) --p;
+    return p;
+}
+
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
-                        cudaStream_t st) {
+                        cudaStream_t st, int nparts, float *part_v, int *part_i) {
     static bool attr = false;
     const size_t smem = sizeof(PcaSmem);
     if (!attr) {
@@ -431,9 +473,15 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
     }
     const int grid = ceil_div(Q, kBQ);
     if (grid == 0) return;
-    ProfScope ps(kProfSearchTopk, st, 1);
-    k_search_pca<<<grid, kThreads, smem, st>>>(qcoord, qnorm, Q, da, et, enorm, ntiles, cand_idx,
-                                               cand_lb, status);
+    if (!part_v || !part_i) nparts = 1;
+    const int tpp = ceil_div(ntiles, std::max(nparts, 1));
+    const int np = ceil_div(ntiles, tpp);
+    ProfScope ps(kProfSearchTopk, st, np > 1 ? 2 : 1);
+    k_search_pca<<<dim3(grid, np), kThreads, smem, st>>>(qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx,
+                                                         cand_lb, part_v, part_i, status);
+    if (np > 1)
+        k_merge_pca_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, Q, qnorm, cand_idx,
+                                                                       cand_lb);
 }
 
 void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
