@@ -446,7 +446,8 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         n = args.cpu_sample or 0
-        per = [n] * 3 if n else [512, 1024, 3072]
+        # about 0.57 TFLOP of FP64 brute force (~10 s on the 16 host cores measured)
+        per = [n] * 3 if n else [2048, 6144, 18432]
         rate, threads, timed, secs = oracle_sample_rate(per)
         line["cpu_baseline"] = {"value": rate, "unit": "queries/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{per} queries per level (coarse to fine) of one E-step each, "

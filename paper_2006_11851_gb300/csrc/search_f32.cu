@@ -29,6 +29,7 @@
 #include <climits>
 
 #include "pts_internal.cuh"
+#include "tc_common.cuh"
 #include "warp_keys.cuh"
 
 namespace pts {
@@ -88,7 +89,8 @@ struct PcaSmem {
     float a[kMaxDA][kBQ];     // query vectors, transposed
     float e[2][kMaxDA][kBN];  // exemplar tiles (double buffer)
     float en[2][kBN];         // exemplar norms
-    uint64_t bar[2];
+    uint64_t bar[2];          // tile of buffer b landed
+    uint64_t empty[2];        // all 8 warps are done with buffer b
     int abort_flag;
 };
 
@@ -113,6 +115,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (tid == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
+        mbar_init(&sm.empty[0], kThreads / 32);
+        mbar_init(&sm.empty[1], kThreads / 32);
         fence_mbar_init();
         sm.abort_flag = 0;
     }
@@ -126,19 +130,29 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int t_begin = blockIdx.y * tiles_per_part;
     const int t_end = min(ntiles, t_begin + tiles_per_part);
     const int nt = max(0, t_end - t_begin);
+    // No block-wide barrier in the loop: every warp waits for the tile's copy itself and releases
+    // the buffer with one arrival; lane 0 of warp 0 refills a buffer once all 8 warps released it.
+    // Every wait is bounded; a failed wait aborts the whole CTA (warp-uniform breaks), and thread 0
+    // then waits for the last copy issued into each buffer before the CTA exits.
+    int last_issued[2] = {-1, -1};  // tile slot i last copied into each buffer (thread 0)
     if (tid == 0) {
-        if (nt > 0) issue(t_begin, 0);
-        if (nt > 1) issue(t_begin + 1, 1);
+        if (nt > 0) {
+            issue(t_begin, 0);
+            last_issued[0] = 0;
+        }
+        if (nt > 1) {
+            issue(t_begin + 1, 1);
+            last_issued[1] = 1;
+        }
     }
     for (int i = 0; i < nt; ++i) {
         const int t = t_begin + i;
         const int buf = i & 1;
-        if (tid == 0 && !mbar_wait_bounded(&sm.bar[buf], (i >> 1) & 1, status)) sm.abort_flag = 1;
-        __syncthreads();
-        if (sm.abort_flag) {
-            if (tid == 0 && i + 1 < nt) mbar_wait_bounded(&sm.bar[buf ^ 1], ((i + 1) >> 1) & 1, status);
-            __syncthreads();
-            return;
+        const uint32_t par = (uint32_t)((i >> 1) & 1);
+        const bool ok = mbar_wait_or_abort(&sm.bar[buf], par, status, &sm.abort_flag);
+        if (!__all_sync(kFull, ok)) {
+            sm.abort_flag = 1;
+            break;
         }
         float acc[8][4];
         const float4 nv = *reinterpret_cast<const float4 *>(&sm.en[buf][lane * 4]);
@@ -162,9 +176,28 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[buf]);  // this warp's last read of `buf` is done
         top.offer(acc, t * kBN, lane);
-        __syncthreads();  // all warps are done with buffer `buf`
-        if (tid == 0 && i + 2 < nt) issue(t + 2, buf);
+        if (warp == 0 && i + 2 < nt) {
+            bool refilled = false;
+            if (lane == 0 && mbar_wait_or_abort(&sm.empty[buf], par, status, &sm.abort_flag)) {
+                issue(t + 2, buf);
+                last_issued[buf] = i + 2;
+                refilled = true;
+            }
+            if (!__shfl_sync(kFull, refilled, 0)) {
+                sm.abort_flag = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (sm.abort_flag) {
+        if (tid == 0)
+            for (int b = 0; b < 2; ++b)
+                if (last_issued[b] >= 0) mbar_wait_bounded(&sm.bar[b], (uint32_t)((last_issued[b] >> 1) & 1), status);
+        return;
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -210,7 +243,8 @@ constexpr int kStages = 4;  // ring depth
 struct FullSmem {
     float a[kStages][kKC][kBQ];
     float e[kStages][kKC][kBN];
-    uint64_t bar[kStages];
+    uint64_t bar[kStages];    // chunk of stage s landed
+    uint64_t empty[kStages];  // all 8 warps are done with stage s
     int abort_flag;
 };
 
@@ -240,7 +274,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     TopK8 top;
     top.init();
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sm.bar[s], 1);
+            mbar_init(&sm.empty[s], kThreads / 32);
+        }
         fence_mbar_init();
         sm.abort_flag = 0;
     }
@@ -254,8 +291,18 @@ __global__ void __launch_bounds__(kThreads, 2)
         bulk_g2s(&sm.e[s][0][0], efull + ((size_t)(t_begin + t) * Dp + (size_t)c * kKC) * kBN, kKC * kBN * 4u,
                  &sm.bar[s]);
     };
+    // As in k_search_pca: no block-wide barrier in the loop; every warp waits for a chunk itself
+    // and releases its stage with one arrival, lane 0 of warp 0 refills a stage once all 8 warps
+    // released it; bounded waits, warp-uniform aborts, and on abort thread 0 waits for the last
+    // copy issued into each stage before the CTA exits.
+    long last_issued[kStages];
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) last_issued[s] = -1;
     if (tid == 0)
-        for (long it = 0; it < kStages && it < total; ++it) issue(it);
+        for (long it = 0; it < kStages && it < total; ++it) {
+            issue(it);
+            last_issued[it] = it;
+        }
     float acc[8][4];
     for (long it = 0; it < total; ++it) {
         const int s = (int)(it % kStages);
@@ -273,15 +320,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                 acc[i][3] = nv.w;
             }
         }
-        if (tid == 0 && !mbar_wait_bounded(&sm.bar[s], (uint32_t)((it / kStages) & 1), status))
+        const uint32_t par = (uint32_t)((it / kStages) & 1);
+        const bool ok = mbar_wait_or_abort(&sm.bar[s], par, status, &sm.abort_flag);
+        if (!__all_sync(kFull, ok)) {
             sm.abort_flag = 1;
-        __syncthreads();
-        if (sm.abort_flag) {
-            if (tid == 0)
-                for (long j = it + 1; j < it + kStages && j < total; ++j)
-                    mbar_wait_bounded(&sm.bar[j % kStages], (uint32_t)((j / kStages) & 1), status);
-            __syncthreads();
-            return;
+            break;
         }
         const float *eb = &sm.e[s][0][lane * 4];
 #pragma unroll 8
@@ -296,6 +339,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[s]);  // this warp's last read of stage s is done
         if (c == c1 - 1) {
             if (pdist) {  // partial sums of this chunk range: [z][f][tile * 128 + window]
 #pragma unroll
@@ -310,8 +355,26 @@ __global__ void __launch_bounds__(kThreads, 2)
                 top.offer(acc, (int)(t_begin + t) * kBN, lane);
             }
         }
-        __syncthreads();  // stage s is free
-        if (tid == 0 && it + kStages < total) issue(it + kStages);
+        if (warp == 0 && it + kStages < total) {
+            bool refilled = false;
+            if (lane == 0 && mbar_wait_or_abort(&sm.empty[s], par, status, &sm.abort_flag)) {
+                issue(it + kStages);
+                last_issued[s] = it + kStages;
+                refilled = true;
+            }
+            if (!__shfl_sync(kFull, refilled, 0)) {
+                sm.abort_flag = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (sm.abort_flag) {
+        if (tid == 0)
+            for (int b = 0; b < kStages; ++b)
+                if (last_issued[b] >= 0)
+                    mbar_wait_bounded(&sm.bar[b], (uint32_t)((last_issued[b] / kStages) & 1), status);
+        return;
     }
     if (pdist) return;
 #pragma unroll
