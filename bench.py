@@ -16,8 +16,11 @@ the per-level exemplar indices are built once, before timing.
 Search modes per level (--mode): exact (certified FP32, the baseline the ratio
 is taken against), f16 (FP16 tensor-core PCA-space search + exact FP32 re-rank
 on every level), f16c (default: the coarsest level exact, the finer two f16),
-proposal (learned cluster proposal on the finest level).  Every run also times
-exact mode on the same seeds and reports the final exact energy of both.
+proposal (the learned cluster proposal on the finest level, f16 on the middle
+one, exact on the coarsest; the network is trained before timing).  Every run
+also times exact mode on the same seeds and reports the final exact energy of
+both; --also names a further mode timed in the same run and reported under
+other_modes (default proposal).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload's queries (E-step only).  Multi-GPU runs are independent replicas
@@ -223,6 +226,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="f16c", choices=list(LEVEL_MODES))
+    ap.add_argument("--also", default="proposal", choices=[""] + list(LEVEL_MODES),
+                    help="a second mode timed in the same run, reported under other_modes")
     ap.add_argument("--train-seeds", type=int, default=16)
     ap.add_argument("--train-pairs", type=int, default=2_000_000)
     ap.add_argument("--clusters", type=int, default=1024)
@@ -271,10 +276,12 @@ def main():
         return torch.from_numpy(P.random_patch_init(z0, Hc, Hc, wc, seed)).to(dev)
 
     train_s, n_pairs, train_loss = 0.0, 0, []
-    if "proposal" in modes:
+    also = args.also if args.also and args.also != args.mode else ""
+    need = modes + (LEVEL_MODES[also] if also else [])
+    if "proposal" in need:
         # training seeds 1000.. are disjoint from the timed seeds 0..(warmup + steps)
         t0 = time.perf_counter()
-        loss, n_pairs = train_level_proposal(pidx, modes.index("proposal"),
+        loss, n_pairs = train_level_proposal(pidx, need.index("proposal") % cfg["levels"],
                                              [1000 + s for s in range(args.train_seeds)], iters=cfg["iters"],
                                              n_pairs=args.train_pairs, init_fn=init_dev, n_clusters=args.clusters,
                                              epochs=args.epochs, seed=7)
@@ -320,8 +327,8 @@ def main():
         launches = L.pts_launch_count() - launches0
         kern = {}
         if profile:
-            for name in ("search_topk", "search_full", "search_tc", "rerank", "project", "m_step", "brute", "irls",
-                         "mlp", "probe"):
+            for name in ("search_topk", "search_full", "search_tc", "search_tc_list", "rerank", "project", "m_step",
+                         "brute", "irls", "mlp", "probe"):
                 ms, n = ctypes.c_double(), ctypes.c_longlong()
                 L.pts_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(n))
                 if n.value:
@@ -343,6 +350,15 @@ def main():
         ex_ms, _, ex_kern, ex_energies, _ = timed_run(LEVEL_MODES["exact"], True)
     exact_qps = queries_per_step(cfg) * args.steps * world / (ex_ms / 1000.0)
     ratios = [e / x for e, x in zip(energies, ex_energies)]
+    other = {}
+    if also:
+        a_ms, _, _, a_energies, _ = timed_run(LEVEL_MODES[also], False)
+        a_qps = queries_per_step(cfg) * args.steps * world / (a_ms / 1000.0)
+        a_ratios = [e / x for e, x in zip(a_energies, ex_energies)]
+        other[also] = {"level_modes": LEVEL_MODES[also], "value": a_qps, "ms_per_step": a_ms / args.steps,
+                       "speedup_vs_exact": a_qps / exact_qps,
+                       "final_energy_ratio_vs_exact": {"max": max(a_ratios), "mean": float(np.mean(a_ratios)),
+                                                       "within_1.01": bool(max(a_ratios) <= 1.01)}}
 
     # ---- end to end through the public API with host buffers ----
     inits = [P.random_patch_init(z0, Hc, Hc, wc, args.warmup + i) for i in range(args.steps)]
@@ -422,7 +438,7 @@ def main():
     line = {
         "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"exact": "f32", "fp8c": "e4m3+f32"}.get(args.mode, "f16+f32"),
+        "scaling": "weak", "vs_baseline": None, "dtype": {"exact": "f32", "fp8c": "e4m3+f32", "proposal": "bf16+f16+f32"}.get(args.mode, "f16+f32"),
         "data": "synthetic",
         "config": dict(cfg, mode=args.mode, level_modes=modes, l2="flushed between steps (256 MB write)",
                        d_fast=[ix.info["d_fast"] for ix in pidx.indices],
@@ -437,6 +453,7 @@ def main():
         "speedup_vs_exact": qps / exact_qps,
         "final_energy_ratio_vs_exact": {"max": max(ratios), "mean": float(np.mean(ratios)),
                                         "within_1.01": bool(max(ratios) <= 1.01)},
+        "other_modes": other,
         "roofline": roof,
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(inits[0].nbytes),
                 "d2h_bytes_per_step": int(out_host.numel() * 4 + 8 * (cfg["iters"] + 1) * cfg["levels"])},

@@ -342,7 +342,9 @@ pts_status pts_upsample2(const float *in, int H, int W, float *out, void *stream
  *   pts_profile_read     total device milliseconds and launch count of one
  *                        kernel class ("search_topk", "search_full",
  *                        "rerank", "project", "m_step", "brute", "irls",
- *                        "search_tc", "mlp", "probe"); synchronises on the
+ *                        "search_tc", "search_tc_list" (tensor-core
+ *                        searches of a device query list), "mlp",
+ *                        "probe"); synchronises on the
  *                        recorded events.  Returns INVALID_ARG for an unknown
  *                        name.
  */

@@ -10,7 +10,10 @@
 // chunk) and staged by 1-D bulk copies into one 128 KB buffer, each load issued as soon as the
 // MMAs reading the previous contents have completed.  Accumulators: TMEM columns 0..255 and
 // 256..511.  The arithmetic is that of the generic GEMM path (same BF16 operands, K-order,
-// bias add and GELU), so the clusters match mlp_forward + k_top4.  Thread = query row.
+// bias add and GELU), so the clusters match mlp_forward + k_top4.  16 warps: warp w reads TMEM
+// lane quarter w % 4 (its 32 query rows) and column group w / 4 (64 of every 256 columns), so
+// each epilogue runs 4 warps per SM sub-partition; in the last layer each warp keeps the top-4
+// of its column group and the four lists of a row are merged at the end.
 #include <math.h>
 
 #include <algorithm>
@@ -22,6 +25,7 @@ namespace pts {
 namespace {
 
 constexpr int kIM = 128;    // queries per CTA
+constexpr int kIThreads = 512;  // 16 warps: 4 lane quarters x 4 column groups
 constexpr int kIH = kMlpH;  // 256
 constexpr int kIChunk = 256;
 constexpr uint32_t kW1Bytes = kIH * 64 * 2, kWBytes = kIChunk * kIH * 2;
@@ -36,13 +40,15 @@ struct InferSmem {
 
 __device__ __forceinline__ float gelu_i(float a) { return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f)); }
 
-// D[tmem_col .. +255] (rows = TMEM lanes) + bias -> gelu -> BF16 rows of the next A operand
+// D[tmem_col + 64 cg .. +63] (rows = TMEM lanes of quarter qt) + bias -> gelu -> BF16 rows of
+// the next A operand
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, uint32_t col, const float *__restrict__ bias,
-                                                unsigned char *h, int warp, int lane) {
-    const int r = warp * 32 + lane;
-    for (int cc = 0; cc < kIH; cc += 64) {
+                                                unsigned char *h, int qt, int cg, int lane) {
+    const int r = qt * 32 + lane;
+    {
+        const int cc = cg * 64;
         float v[64];
-        tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + col + (uint32_t)cc, v);
+        tmem_ld64(tmem + ((uint32_t)(qt * 32) << 16) + col + (uint32_t)cc, v);
 #pragma unroll
         for (int k8 = 0; k8 < 8; ++k8) {
             uint4 pk;
@@ -59,7 +65,12 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, uint32_t col, con
     }
 }
 
-__global__ void __launch_bounds__(kIM, 1)
+// (z, id) before (z2, id2): larger logit, then smaller cluster id
+__device__ __forceinline__ bool logit_before(float z, int id, float z2, int id2) {
+    return z > z2 || (z == z2 && id < id2);
+}
+
+__global__ void __launch_bounds__(kIThreads, 1)
     k_mlp_infer(const float *__restrict__ qcoord, int Q, int d, int ldq, const __nv_bfloat16 *__restrict__ wp1,
                 const float *__restrict__ b1, const __nv_bfloat16 *__restrict__ wp2, const float *__restrict__ b2,
                 const __nv_bfloat16 *__restrict__ wp3, const float *__restrict__ b3p, int nchunk,
@@ -67,16 +78,19 @@ __global__ void __launch_bounds__(kIM, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     InferSmem &sm = *reinterpret_cast<InferSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = blockIdx.x * kIM + tid;
-    // x tile: row tid, 64 values, 8 per 16-byte core-matrix row
-    for (int k8 = 0; k8 < 8; ++k8) {
+    const int qt = warp & 3, cg = warp >> 2;  // TMEM lane quarter, column group
+    const int row = qt * 32 + lane;           // this thread's query row in the epilogues
+    const int q = blockIdx.x * kIM + row;
+    // x tile: row tid (threads < 128), 64 values, 8 per 16-byte core-matrix row
+    for (int k8 = 0; k8 < 8 && tid < kIM; ++k8) {
         uint4 pk;
         uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int k = 8 * k8 + 2 * t;
-            const float a = (q < Q && k < d) ? qcoord[(size_t)q * ldq + k] : 0.0f;
-            const float b = (q < Q && k + 1 < d) ? qcoord[(size_t)q * ldq + k + 1] : 0.0f;
+            const long qx = (long)blockIdx.x * kIM + tid;
+            const float a = (qx < Q && k < d) ? qcoord[(size_t)qx * ldq + k] : 0.0f;
+            const float b = (qx < Q && k + 1 < d) ? qcoord[(size_t)qx * ldq + k + 1] : 0.0f;
             const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
             pw[t] = *reinterpret_cast<const uint32_t *>(&v);
         }
@@ -120,7 +134,7 @@ __global__ void __launch_bounds__(kIM, 1)
         mbar_expect_tx(&sm.bar_w, kWBytes);
         bulk_g2s(sm.w, wp2, kWBytes, &sm.bar_w);
     }
-    hidden_epilogue(tmem, 0, b1, sm.h, warp, lane);
+    hidden_epilogue(tmem, 0, b1, sm.h, qt, cg, lane);
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -142,7 +156,7 @@ __global__ void __launch_bounds__(kIM, 1)
         mbar_expect_tx(&sm.bar_w, kWBytes);
         bulk_g2s(sm.w, wp3, kWBytes, &sm.bar_w);
     }
-    hidden_epilogue(tmem, 256u, b2, sm.h, warp, lane);  // h1 is no longer read
+    hidden_epilogue(tmem, 256u, b2, sm.h, qt, cg, lane);  // h1 is no longer read
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -168,9 +182,10 @@ __global__ void __launch_bounds__(kIM, 1)
             mbar_expect_tx(&sm.bar_w, kWBytes);
             bulk_g2s(sm.w, wp3 + (size_t)(c + 1) * kIChunk * kIH, kWBytes, &sm.bar_w);
         }
-        for (int cc = 0; cc < kIChunk; cc += 64) {
+        {
+            const int cc = cg * 64;  // ids rise along the scan: a strict test keeps the smaller id first
             float v[64];
-            tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + dcol + (uint32_t)cc, v);
+            tmem_ld64(tmem + ((uint32_t)(qt * 32) << 16) + dcol + (uint32_t)cc, v);
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
                 const int id = c * kIChunk + cc + j;
@@ -206,8 +221,33 @@ __global__ void __launch_bounds__(kIM, 1)
         __syncthreads();
         tc_fence_after();
     }
-    if (q < Q)
-        for (int j = 0; j < 4; ++j) top[(size_t)q * 4 + j] = ti[j] == INT_MAX ? 0 : ti[j];
+    // merge the column groups' lists of each row (the x tile is no longer read)
+    float *mv = reinterpret_cast<float *>(sm.x);                // [3][128][4]
+    int *mi = reinterpret_cast<int *>(sm.x) + 3 * kIM * 4;      // [3][128][4]
+    if (cg > 0)
+        for (int j = 0; j < 4; ++j) {
+            mv[((cg - 1) * kIM + row) * 4 + j] = tv[j];
+            mi[((cg - 1) * kIM + row) * 4 + j] = ti[j];
+        }
+    __syncthreads();
+    if (cg == 0) {
+        for (int g = 0; g < 3; ++g)
+            for (int j = 0; j < 4; ++j) {
+                float z = mv[(g * kIM + row) * 4 + j];
+                int id = mi[(g * kIM + row) * 4 + j];
+                for (int k = 0; k < 4; ++k)  // insert (z, id): swap down the sorted list
+                    if (logit_before(z, id, tv[k], ti[k])) {
+                        const float tz = tv[k];
+                        const int tid2 = ti[k];
+                        tv[k] = z;
+                        ti[k] = id;
+                        z = tz;
+                        id = tid2;
+                    }
+            }
+        if (q < Q)
+            for (int j = 0; j < 4; ++j) top[(size_t)q * 4 + j] = ti[j] == INT_MAX ? 0 : ti[j];
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -269,7 +309,7 @@ void launch_mlp_top4(const MlpInfer &f, const float *qcoord, int Q, int d, int l
         attr = true;
     }
     ProfScope ps(kProfMlp, st, 1);
-    k_mlp_infer<<<ceil_div(Q, kIM), kIM, smem, st>>>(qcoord, Q, std::min(d, 64), ldq, f.wp1.ptr, f.b1, f.wp2.ptr, f.b2,
+    k_mlp_infer<<<ceil_div(Q, kIM), kIThreads, smem, st>>>(qcoord, Q, std::min(d, 64), ldq, f.wp1.ptr, f.b1, f.wp2.ptr, f.b2,
                                                      f.wp3.ptr, f.b3p.ptr, f.nchunk, top, status);
 }
 

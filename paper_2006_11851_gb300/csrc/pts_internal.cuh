@@ -311,7 +311,7 @@ void launch_resolve(const int *fail_list, const unsigned int *fail_count,
                     cudaStream_t st);
 // profile.cu: launch counting and event timing of kernel classes
 enum ProfClass { kProfSearchTopk = 0, kProfSearchFull, kProfRerank, kProfProject, kProfMStep,
-                 kProfSearchTc, kProfMlp, kProfProbe, kProfBrute, kProfIrls, kProfClasses };
+                 kProfSearchTc, kProfMlp, kProfProbe, kProfBrute, kProfIrls, kProfSearchTcList, kProfClasses };
 void count_launches(int n);
 void prof_begin(int cls, cudaStream_t st, void **token);
 void prof_end(int cls, cudaStream_t st, void *token);

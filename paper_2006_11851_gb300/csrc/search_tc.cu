@@ -436,16 +436,13 @@ __global__ void __launch_bounds__(256) k_select(const KeptGroups *__restrict__ k
     }
 }
 
-// One warp per query of a search whose tiles were split into nparts parts of tpp tiles.  Each
+// Query q of a search whose tiles were split into nparts parts of tpp tiles, one warp.  Each
 // part kept the 8 best groups of its own tiles per column half, so their union holds the 8 best
 // of the whole half: first those, by (minimum, group), then the 32 smallest (score, window) pairs
 // of the 2 x 8 groups.  The result is the single-part one, whatever the split or a warm bound.
-__global__ void __launch_bounds__(256) k_select_parts(const KeptGroups *__restrict__ kept, int Q, int nparts, int tpp,
-                                                      const float *__restrict__ qnorm, int *__restrict__ cand_idx,
-                                                      float *__restrict__ cand_lb) {
-    const int lane = threadIdx.x & 31;
-    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (q >= Q) return;
+__device__ __forceinline__ void select_parts_row(const KeptGroups *__restrict__ kept, long q, int nparts, int tpp,
+                                                 const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                 float *__restrict__ cand_lb, int lane) {
     const unsigned long long kNone = pack_key(INFINITY, kNoWindow);
     unsigned long long best[2];
 #pragma unroll
@@ -496,6 +493,15 @@ __global__ void __launch_bounds__(256) k_select_parts(const KeptGroups *__restri
     const bool real = i != kNoWindow;
     cand_idx[q * kTopK + lane] = real ? i : -1;
     cand_lb[q * kTopK + lane] = real ? key_value(key[0]) + qnorm[q] : INFINITY;
+}
+
+// select_parts_row for every query, one warp each
+__global__ void __launch_bounds__(256) k_select_parts(const KeptGroups *__restrict__ kept, int Q, int nparts, int tpp,
+                                                      const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                      float *__restrict__ cand_lb) {
+    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    select_parts_row(kept, q, nparts, tpp, qnorm, cand_idx, cand_lb, threadIdx.x & 31);
 }
 
 // k_select for a device-side query list (one part per query)
@@ -1159,7 +1165,6 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount, int fp8,
                       const float *qscale, const float *enorm, int N, void *kept_buf) {
-    if (qlist) nparts = 1;  // a listed search writes its candidates directly
     static bool attr[2] = {false, false};
     const size_t smem = sizeof(TcSmem) + 1024;
     if (!attr[fp8 ? 1 : 0]) {
@@ -1169,13 +1174,16 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
             cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr[fp8 ? 1 : 0] = true;
     }
+    // a listed search runs unsplit: the proposal's fallback lists about a third of the fine
+    // level's queries, enough blocks to fill the SMs, and a split measured slower there
+    if (qlist) nparts = 1;
     const int nqb = tc_query_blocks(Q);
     if (nqb == 0) return;
     const int tpp = (ntiles + nparts - 1) / nparts;
     const int eb = fp8 ? 1 : 2;
     const int nstages = std::min(kMaxStages, kRing / (kTN * K * eb));
     KeptGroups *kept = reinterpret_cast<KeptGroups *>(kept_buf);
-    ProfScope ps(kProfSearchTc, st, 2);
+    ProfScope ps(qlist ? kProfSearchTcList : kProfSearchTc, st, 2);
     if (fp8)
         k_search_tc<1><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
                                                                   qscale, enorm, N, thr0, qlist, qcount, IvfArgs{},

@@ -161,3 +161,32 @@ def test_proposal_energy_and_speed(trained):
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / 5
     assert timed("proposal") < timed("exact")
+
+
+def test_fallback_equals_tensor_core_search():
+    """With a fallback threshold near zero every query with a nonzero distance falls back to the
+    FP16 tensor-core search over all windows (the listed search); its result must then be the
+    "f16" mode's result bit for bit (same candidates, same re-rank)."""
+    Z = P.synthetic_exemplar(3, 160, 4.0)
+    pidx = PyramidIndex(_t(Z), [16, 8], d=64)
+    z0 = pidx.exemplars[0].cpu().numpy()
+    init = lambda s: _t(P.random_patch_init(z0, 128, 128, 16, s))  # noqa: E731
+    try:
+        y, nn, d2 = collect_pairs(pidx, 1, init, range(2), iters=3)
+        y, nn, d2 = subsample(y, nn, d2, 100_000)
+        pts.train_proposal(pidx.indices[1], y, nn, d2, n_clusters=64, epochs=2, batch=4096, seed=2,
+                           fallback_factor=1e-6)
+        ix = pidx.indices[1]
+        X = init(30)
+        pts.synthesize_level(pidx.indices[0], X, 5, mode="exact")
+        X = pts.upsample2(X)
+        pts.synthesize_level(ix, X, 2, mode="exact")
+        nn_p, d2_p = pts.nn_search(ix, X, 2, "proposal")
+        st = ix.search_stats()
+        nn_f, d2_f = pts.nn_search(ix, X, 2, "f16")
+        pos = d2_f > 0
+        assert st["fallback_queries"] >= int(pos.sum().item())
+        assert torch.equal(d2_p, d2_f)
+        assert torch.equal(nn_p[pos], nn_f[pos])
+    finally:
+        pidx.close()
