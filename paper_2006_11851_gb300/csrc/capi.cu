@@ -233,8 +233,8 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             // the candidate lists of the previous search on this grid seed the bound
             const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
             if (warm)
-                launch_warm_threshold(ws.cand_idx.ptr, ws.qcoord.ptr, idx->d_fast, idx->da_fast, ws.qnorm.ptr,
-                                      idx->etc.ptr, idx->umax.ptr, Q, idx->ktc, idx->N, kWarmEps, ws.thr0.ptr, st);
+                launch_warm_threshold(ws.cand_idx.ptr, ws.qtile.ptr, ws.qnorm.ptr, idx->etc.ptr, idx->umax.ptr, Q, idx->ktc,
+                                      idx->N, kWarmEps, ws.thr0.ptr, st);
             PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, nparts), "kept groups"));
             launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, ntc, nparts,
                              warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr,

@@ -251,9 +251,8 @@ size_t tc_kept_bytes(int Q, int nparts);
 void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float *qcoord, const float *qnorm, int d,
                       int da, int K, const __half *etile_ivf, int ntiles, int N, const int *members, IvfBuffers &b,
                       int *cand_idx, float *cand_lb, int *status, cudaStream_t st);
-void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
-                           const __half *etile, const float *umax, int Q, int K, int N, float eps_scale, float *thr0,
-                           cudaStream_t st);
+void launch_warm_threshold(const int *prev_idx, const __half *qtile, const float *qnorm, const __half *etile,
+                           const float *umax, int Q, int K, int N, float eps_scale, float *thr0, cudaStream_t st);
 void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const void *etile, int ntiles,
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount, int fp8,

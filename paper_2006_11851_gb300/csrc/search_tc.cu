@@ -72,50 +72,6 @@ struct TcSmem {
 };
 static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "tensor-core search tile set exceeds shared memory");
 
-// (a, ia) < (b, ib) lexicographically
-__device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
-    return (a < b) || (a == b && ia < ib);
-}
-
-// Ascending bitonic sort of one (value, index) pair per lane.
-__device__ __forceinline__ void warp_sort32(float &v, int &i, int lane) {
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const float ov = __shfl_xor_sync(kFull, v, j);
-            const int oi = __shfl_xor_sync(kFull, i, j);
-            const bool keep_min = (((lane & k) == 0) == ((lane & j) == 0));
-            const bool take = keep_min ? lex_less(ov, oi, v, i) : lex_less(v, i, ov, oi);
-            if (take) {
-                v = ov;
-                i = oi;
-            }
-        }
-    }
-}
-
-// (v, i) := the 32 smallest of two ascending lists (v, i) and (w, j), ascending: the
-// elementwise min of one list and the other reversed is bitonic; five stages sort it.
-__device__ __forceinline__ void warp_merge32(float &v, int &i, float w, int j, int lane) {
-    const float rw = __shfl_sync(kFull, w, 31 - lane);
-    const int rj = __shfl_sync(kFull, j, 31 - lane);
-    if (lex_less(rw, rj, v, i)) {
-        v = rw;
-        i = rj;
-    }
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        const float ov = __shfl_xor_sync(kFull, v, s);
-        const int oi = __shfl_xor_sync(kFull, i, s);
-        const bool take = ((lane & s) == 0) ? lex_less(ov, oi, v, i) : lex_less(v, i, ov, oi);
-        if (take) {
-            v = ov;
-            i = oi;
-        }
-    }
-}
-
 // Sorted register list of the kept groups: value gv[k] (group minimum) and gs[k] = group << 4 |
 // slot, ascending in (value, group).
 struct GroupList {
@@ -788,13 +744,15 @@ __global__ void k_pack_queries_ivf(const float *__restrict__ qcoord, int d, int 
 }
 
 // Warm start: the previous search's 32 windows of each query, scored in FP32 from the same FP16
-// operands the tensor cores multiply (16-byte rows of the operand layout, 8 values per load).  A
-// window's score bounds its group's minimum from above, so with g_1 <= g_2 <= ... the smallest
-// score of each distinct group of one column half among them, that half's 8th best group
-// minimum is at most g_8; plus a margin for a different summation order, that is the half's
-// bound (thr0[2 q + half]).  With fewer than 8 distinct groups in a half its bound is +inf.
-// One warp per query.
-__global__ void k_warm_threshold(const int *__restrict__ prev_idx, const float *__restrict__ qcoord, int d, int da,
+// operands the tensor cores multiply (16-byte rows of the operand layout, 8 values per load, the
+// query's row read from its packed tile).  A window's score bounds its group's minimum from
+// above, so with g_1 <= g_2 <= ... the smallest score of each distinct group of one column half
+// among them, that half's 8th best group minimum is at most g_8; plus a margin for a different
+// summation order, that is the half's bound (thr0[2 q + half]).  With fewer than 8 distinct
+// groups in a half its bound is +inf.  One warp per query, two sorts of 64-bit keys: by (half,
+// group, score), which puts each group's minimum first in its run, then the minima by (half,
+// score) with every other entry after the minima of its half.
+__global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half *__restrict__ qtile,
                                  const float *__restrict__ qnorm, const __half *__restrict__ etile,
                                  const float *__restrict__ umax, int Q, int K, int N, float eps_scale,
                                  float *__restrict__ thr0) {
@@ -806,44 +764,46 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const float *
     float p = INFINITY;
     if (valid) {
         const unsigned char *e = reinterpret_cast<const unsigned char *>(etile + (size_t)(n / kTN) * kTN * K);
-        const float *qr = qcoord + (size_t)q * da;
-        const int m = n % kTN;
+        const unsigned char *a = reinterpret_cast<const unsigned char *>(qtile + (size_t)(q / kQM) * kQM * K);
+        const int m = n % kTN, r = q % kQM;
         p = 0.0f;
         for (int k8 = 0; k8 < K; k8 += 8) {
             const uint4 ev = __ldg(reinterpret_cast<const uint4 *>(e + core_offset(m, k8, kTN)));
+            const uint4 av = __ldg(reinterpret_cast<const uint4 *>(a + core_offset(r, k8, kQM)));
             const __half2 *eh = reinterpret_cast<const __half2 *>(&ev);
+            const __half2 *ah = reinterpret_cast<const __half2 *>(&av);
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                float v[2];
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int k = k8 + 2 * h + t;
-                    v[t] = k <= d ? qr[k] : (k <= d + 3 ? 1.0f : 0.0f);  // the operand the MMA reads
-                }
-                const float2 af = __half22float2(__floats2half2_rn(v[0], v[1]));
+                const float2 af = __half22float2(ah[h]);
                 const float2 ef = __half22float2(eh[h]);
                 p = fmaf(af.x, ef.x, p);
                 p = fmaf(af.y, ef.y, p);
             }
         }
     }
-    // each group's smallest score once (ties: lowest lane), per column half
-    const int grp = valid ? n / kG : -1 - lane;
-    const int half = valid ? (grp % (kTN / kG)) / (kTN / kG / 2) : -1;
-    bool first = valid;
-    for (int j = 0; j < 32; ++j) {
-        const int gj = __shfl_sync(kFull, grp, j);
-        const float pj = __shfl_sync(kFull, p, j);
-        if (j != lane && gj == grp && (pj < p || (pj == p && j < lane))) first = false;
-    }
-    const float eps = eps_scale * (qnorm[q] + 2.0f * *umax);
-    for (int h = 0; h < 2; ++h) {
-        float key = first && half == h ? p : INFINITY;
-        int idx = lane;
-        warp_sort32(key, idx, lane);
-        const float g8 = __shfl_sync(kFull, key, kKeep - 1);
+    constexpr unsigned long long kLast = ~0ull;
+    const int grp = valid ? n / kG : 0;
+    const unsigned half = valid ? (unsigned)((grp % (kTN / kG)) / (kTN / kG / 2)) : 0u;
+    const unsigned score = (unsigned)(pack_key(p, 0) >> 32);  // order-preserving bits of p
+    unsigned long long k1 = valid ? ((unsigned long long)((half << 27) | (unsigned)grp) << 32) | score : kLast;
+    warp_sort_keys(k1, lane);
+    const unsigned long long before = __shfl_up_sync(kFull, k1, 1);
+    const bool first = k1 != kLast && (lane == 0 || (before >> 32) != (k1 >> 32));
+    const unsigned h1 = (unsigned)(k1 >> 59);  // the half bit
+    unsigned long long k2 = k1 == kLast ? kLast
+                                        : ((unsigned long long)h1 << 32) | (first ? (k1 & 0xffffffffull) : 0xffffffffull);
+    warp_sort_keys(k2, lane);
+    const int n0 = __popc(__ballot_sync(kFull, (k2 >> 32) == 0));  // entries of half 0
+    const unsigned long long s0 = __shfl_sync(kFull, k2, 7);
+    const unsigned long long s1 = __shfl_sync(kFull, k2, min(n0 + 7, 31));
+    if (lane == 0) {
+        const float eps = eps_scale * (qnorm[q] + 2.0f * *umax);
         // |error| of an FP32 sum of K exact products <= K 2^-24 sum|terms|, sum|terms| <= qnorm + 2 umax
-        if (lane == 0) thr0[2 * (size_t)q + h] = isinf(g8) ? INFINITY : g8 + eps;
+        float g0 = INFINITY, g1 = INFINITY;
+        if (n0 > 7 && (unsigned)s0 != 0xffffffffu) g0 = key_value(s0 << 32);
+        if (n0 + 7 < 32 && (s1 >> 32) == 1 && (unsigned)s1 != 0xffffffffu) g1 = key_value(s1 << 32);
+        thr0[2 * (size_t)q] = isinf(g0) ? INFINITY : g0 + eps;
+        thr0[2 * (size_t)q + 1] = isinf(g1) ? INFINITY : g1 + eps;
     }
 }
 
@@ -1152,13 +1112,12 @@ void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float
                                                                members, N);
 }
 
-void launch_warm_threshold(const int *prev_idx, const float *qcoord, int d, int da, const float *qnorm,
-                           const __half *etile, const float *umax, int Q, int K, int N, float eps_scale, float *thr0,
-                           cudaStream_t st) {
+void launch_warm_threshold(const int *prev_idx, const __half *qtile, const float *qnorm, const __half *etile,
+                           const float *umax, int Q, int K, int N, float eps_scale, float *thr0, cudaStream_t st) {
     if (Q == 0) return;
     count_launches(1);
-    k_warm_threshold<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qcoord, d, da, qnorm, etile, umax, Q, K,
-                                                                   N, eps_scale, thr0);
+    k_warm_threshold<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qtile, qnorm, etile, umax, Q, K, N,
+                                                                   eps_scale, thr0);
 }
 
 void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const void *etile, int ntiles,
