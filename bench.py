@@ -210,6 +210,19 @@ PCA_PASS_MIN_VAR = 0.85  # the exact search skips its PCA pass below this retain
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
 
 
+# DRAM bytes (read + write) of one fine-level k_search_tc launch (Q = 64,009, N = 62,001) from the
+# ncu capture summarised in profiles/k_search_tc_fine_level_512_f16.md; reported only while the
+# search source is the one the counters were taken on.
+TC_TRAFFIC_BYTES = 32.895e6 + 0.016e6
+TC_TRAFFIC_SHA256 = "b7fcd083d0f889cf0e3f39b24886c7b4457d8f13d3a86f31190cccb212c53c41"
+
+
+def _tc_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2006_11851_gb300", "csrc", "search_tc.cu"), "rb") as f:
+        return TC_TRAFFIC_BYTES if hashlib.sha256(f.read()).hexdigest() == TC_TRAFFIC_SHA256 else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -417,9 +430,10 @@ def main():
                              f"({peak_src}) x the nominal FP8/BF16 ratio")
         else:
             roof.update(bound="tensor", achieved=ach, peak=bf16_sust, unit="TFLOP/s", frac=ach / bf16_sust,
-                        kernel="k_search_tc (FP16 tcgen05 PCA-space GEMM + top-32)",
+                        kernel="k_search_tc (FP16 tcgen05 PCA-space GEMM + top-32)", traffic=_tc_traffic(),
                         note=f"algorithmic 2(d_fast+1) flops per (query, window) pair, d_fast={dfs}; peak = BF16 "
-                             f"sustained (dense FP16 has the BF16 rate), {peak_src}")
+                             f"sustained (dense FP16 has the BF16 rate), {peak_src}; traffic = DRAM bytes of one "
+                             "fine-level launch (ncu), the algorithmic operand bytes being 32.3 MB")
     elif dom == "search_topk":
         roof.update(ex_roof, traffic=None)
     elif dom == "search_full" and all(m != "exact" or ix.info["var_retained"] < PCA_PASS_MIN_VAR
