@@ -75,6 +75,7 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->w), "full query vectors"));
     PTS_TRY(ws.best64.ensure(cap, "packed minima"));
     PTS_TRY(ws.thr0.ensure(2 * (size_t)cap, "warm-start bounds"));
+    PTS_TRY(ws.pca_thr.ensure((size_t)cap, "PCA-pass bounds"));
     PTS_TRY(ws.counters.ensure(4, "counters"));
     PTS_TRY(ws.nn.ensure(cap, "nn"));
     PTS_TRY(ws.d2.ensure(cap, "d2"));
@@ -197,9 +198,15 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
             PTS_TRY(ws.part_v.ensure((size_t)Q * pp * kTopK, "part lists"));
             PTS_TRY(ws.part_i.ensure((size_t)Q * pp * kTopK, "part lists"));
         }
+        // the candidates of the previous search on this grid (any mode) bound the 32nd best
+        const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
+        if (warm) {
+            launch_warm_pca(ws.cand_idx.ptr, ws.qcoord.ptr, idx->da, idx->et_rows.ptr, idx->enorm.ptr, Q, idx->N,
+                            ws.pca_thr.ptr, st);
+        }
         launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
                            idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st, pp, ws.part_v.ptr,
-                           ws.part_i.ptr);
+                           ws.part_i.ptr, warm ? ws.pca_thr.ptr : nullptr);
         // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
         launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
                       d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
@@ -419,6 +426,9 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basisT.ptr, dd, idx->da, 1,
                    idx->et.ptr, idx->enorm.ptr, nullptr, 0.0f, nullptr, st);
     launch_norm_max(idx->enorm.ptr, idx->N, idx->umax.ptr, st);
+    if ((s = idx->et_rows.ensure((size_t)idx->N * idx->da, "window-major exemplar vectors")) != PTS_OK)
+        return fail(s);
+    launch_tiles_to_rows(idx->et.ptr, idx->N, idx->da, idx->et_rows.ptr, st);
     if ((s = idx->efull.ensure((size_t)idx->ntiles * padded_dim(w) * kBN, "full exemplar vectors")) !=
         PTS_OK)
         return fail(s);
@@ -477,6 +487,15 @@ void pts_index_destroy(pts_index idx) {
     ws.energy.release();
     ws.partial.release();
     ws.ticket.release();
+    ws.thr0.release();
+    ws.pca_thr.release();
+    ws.qtile.release();
+    ws.qtile8.release();
+    ws.qscale.release();
+    ws.proj_part.release();
+    ws.kept.release();
+    ws.part_v.release();
+    ws.part_i.release();
     idx->exemplar.release();
     idx->exemplar4.release();
     idx->mu.release();
@@ -484,9 +503,12 @@ void pts_index_destroy(pts_index idx) {
     idx->basisT.release();
     idx->eig.release();
     idx->et.release();
+    idx->et_rows.release();
     idx->enorm.release();
     idx->efull.release();
     idx->etc.release();
+    idx->etc8.release();
+    idx->f8scale.release();
     idx->et_fast.release();
     {
         ProposalState &pr = idx->prop;
@@ -497,6 +519,17 @@ void pts_index_destroy(pts_index idx) {
         pr.members.release();
         pr.median.release();
         pr.top.release();
+        pr.etc_ivf.release();
+        for (auto *b : {&pr.ivf_cnt, &pr.ivf_poff, &pr.ivf_cursor, &pr.ivf_nblk, &pr.pair_q, &pr.pair_r, &pr.ivf_part_i})
+            b->release();
+        pr.ivf_blk.release();
+        pr.ivf_qtile.release();
+        pr.ivf_part_v.release();
+        pr.ivf_kept.release();
+        pr.infer.wp1.release();
+        pr.infer.wp2.release();
+        pr.infer.wp3.release();
+        pr.infer.b3p.release();
         MlpState &m = pr.mlp;
         for (auto *b : {&m.params, &m.grads, &m.adam_m, &m.adam_v, &m.a1, &m.a2, &m.z, &m.dh, &m.loss}) b->release();
         for (auto *b : {&m.wb, &m.wt, &m.xb, &m.xt, &m.h1b, &m.h1t, &m.h2b, &m.h2t, &m.dzb, &m.dzt, &m.dab, &m.dat})

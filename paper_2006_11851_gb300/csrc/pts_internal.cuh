@@ -93,6 +93,7 @@ struct Workspace {
     DevBuf<float> full_pdist;  // [splits][Q][ntiles*128] partial sums of a split full pass
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
     DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
+    DevBuf<float> pca_thr;     // [Q] warm-start bound of the exact PCA pass
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
     DevBuf<uint8_t> qtile8;    // [ceil(Q/128)][128 x Kf8] FP8 query operand tiles
     DevBuf<float> qscale;      // [Q] FP8 query row scales
@@ -172,6 +173,7 @@ struct pts_index_s {
     pts::DevBuf<float> basisT;    // [D][128]: the basis transposed, 0 past the computed components
     pts::DevBuf<double> eig;      // d
     pts::DevBuf<float> et;        // [ntiles][da][kBN] = -2 * (y_n, r_n, 0...)
+    pts::DevBuf<float> et_rows;   // [N][da], the same vectors window-major (warm-start bound)
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
     pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
     pts::DevBuf<float> et_fast;   // [ntiles][da_fast][kBN] = -2 (y_n, r_n, 0...) with d_fast coordinates
@@ -216,7 +218,8 @@ void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st, int nparts = 1,
-                        float *part_v = nullptr, int *part_i = nullptr);
+                        float *part_v = nullptr, int *part_i = nullptr,
+                        const float *thr_init = nullptr);
 void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
@@ -225,6 +228,9 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
                         DevBuf<float> *pdist);
 int full_parts(int Q, int ntiles);
 int pca_parts(int Q, int ntiles);
+void launch_tiles_to_rows(const float *et, int N, int da, float *rows, cudaStream_t st);
+void launch_warm_pca(const int *prev_idx, const float *qcoord, int da, const float *et_rows, const float *enorm, int Q,
+                     int N, float *thr, cudaStream_t st);
 void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st);
 // search_tc.cu

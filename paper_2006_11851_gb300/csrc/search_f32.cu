@@ -73,7 +73,7 @@ struct TopK8 {
                         ld[i] = cd;
                         li[i] = ci;
                     }
-                    thr[i] = __shfl_sync(kFull, ld[i], 31);
+                    thr[i] = fminf(thr[i], __shfl_sync(kFull, ld[i], 31));
                     fl &= ~(1u << src);
                     fl &= __ballot_sync(kFull, p[i][j] < thr[i]);
                 }
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_search_pca(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int da,
                  const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int tiles_per_part,
                  int *__restrict__ cand_idx, float *__restrict__ cand_lb, float *__restrict__ part_v,
-                 int *__restrict__ part_i, int *__restrict__ status) {
+                 int *__restrict__ part_i, int *__restrict__ status, const float *__restrict__ thr_init) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PcaSmem &sm = *reinterpret_cast<PcaSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -111,6 +111,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int row0 = warp * 8;
     TopK8 top;
     top.init();
+    if (thr_init)  // warm start: a value enters only below the bound (which caps the 32nd best)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = qbase + row0 + i;
+            top.thr[i] = q < Q ? thr_init[q] : INFINITY;
+        }
     const uint32_t tile_floats = static_cast<uint32_t>(da) * kBN;
     if (tid == 0) {
         mbar_init(&sm.bar[0], 1);
@@ -212,6 +218,50 @@ __global__ void __launch_bounds__(kThreads, 2)
                 cand_lb[(size_t)q * kTopK + lane] = top.ld[i] + qnorm[q];
             }
         }
+    }
+}
+
+// Warm start of the exact PCA pass: the previous search's 32 distinct windows of each query scored
+// with the current query vector by the pass's own arithmetic (||u_n||^2, then one FMA per
+// coordinate in coordinate order, so each value equals the pass's bit for bit).  Their largest is
+// at least the 32nd smallest over all windows; with a 2^-20 relative margin it bounds the values
+// that can enter the top-32 (the list still fills, ties included).  +inf when a lane has no
+// window.  One warp per query.
+__global__ void __launch_bounds__(256) k_warm_pca(const int *__restrict__ prev_idx, const float *__restrict__ qcoord,
+                                                  int da, const float *__restrict__ et_rows,
+                                                  const float *__restrict__ enorm, int Q, int N,
+                                                  float *__restrict__ thr) {
+    const int lane = threadIdx.x & 31;
+    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    const int n = prev_idx[q * kTopK + lane];
+    const bool valid = n >= 0 && n < N;
+    float p = INFINITY;
+    if (valid) {
+        const float *a = qcoord + q * da;
+        const float *e = et_rows + (size_t)n * da;
+        p = enorm[n];
+        for (int k = 0; k < da; k += 4) {  // da is a multiple of 4
+            const float4 av = __ldg(reinterpret_cast<const float4 *>(a + k));
+            const float4 ev = __ldg(reinterpret_cast<const float4 *>(e + k));
+            p = fmaf(av.x, ev.x, p);
+            p = fmaf(av.y, ev.y, p);
+            p = fmaf(av.z, ev.z, p);
+            p = fmaf(av.w, ev.w, p);
+        }
+    }
+    float m = p;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, s));
+    if (lane == 0) thr[q] = isinf(m) ? INFINITY : m + fmaxf(fabsf(m), 1e-30f) * 9.5367431640625e-7f;
+}
+
+// [ntiles][da][128] -> [N][da]
+__global__ void k_tiles_to_rows(const float *__restrict__ et, int N, int da, float *__restrict__ rows) {
+    const long total = (long)N * da;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const int n = (int)(i / da), k = (int)(i - (long)n * da);
+        rows[i] = et[((size_t)(n / kBN) * da + k) * kBN + n % kBN];
     }
 }
 
@@ -514,6 +564,18 @@ __global__ void k_exemplar_full(const float *__restrict__ Z, int We, int w, int 
 
 }  // namespace
 
+void launch_tiles_to_rows(const float *et, int N, int da, float *rows, cudaStream_t st) {
+    count_launches(1);
+    k_tiles_to_rows<<<152 * 4, 256, 0, st>>>(et, N, da, rows);
+}
+
+void launch_warm_pca(const int *prev_idx, const float *qcoord, int da, const float *et_rows, const float *enorm, int Q,
+                     int N, float *thr, cudaStream_t st) {
+    if (Q <= 0) return;
+    count_launches(1);
+    k_warm_pca<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(prev_idx, qcoord, da, et_rows, enorm, Q, N, thr);
+}
+
 // Exemplar parts of the PCA pass: only a grid of fewer query blocks than SMs is split (to about
 // two CTAs per SM, at least 8 tiles a part).  Larger grids stay whole: every part restarts its
 // top-32 from empty, and on the 64,009-query fine level a 3-way split measured slower.
@@ -527,7 +589,7 @@ int pca_parts(int Q, int ntiles) {
 
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
-                        cudaStream_t st, int nparts, float *part_v, int *part_i) {
+                        cudaStream_t st, int nparts, float *part_v, int *part_i, const float *thr_init) {
     static bool attr = false;
     const size_t smem = sizeof(PcaSmem);
     if (!attr) {
@@ -541,7 +603,7 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
     const int np = ceil_div(ntiles, tpp);
     ProfScope ps(kProfSearchTopk, st, np > 1 ? 2 : 1);
     k_search_pca<<<dim3(grid, np), kThreads, smem, st>>>(qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx,
-                                                         cand_lb, part_v, part_i, status);
+                                                         cand_lb, part_v, part_i, status, thr_init);
     if (np > 1)
         k_merge_pca_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, Q, qnorm, cand_idx,
                                                                        cand_lb);

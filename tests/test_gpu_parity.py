@@ -275,3 +275,25 @@ def test_invalid_arguments(c1):
         pts.ExemplarIndex(_t(Z[:6, :6]), 8)
     with pytest.raises(pts.PtsError):
         pts.pca_fit(_t(Z), 8, 129)
+
+
+def test_index_destroy_returns_device_memory():
+    """Building an index, searching it in every mode that allocates workspace (exact, FP16, FP8)
+    and destroying it leaves the device's free memory where it was (one warm-up cycle first, so
+    the caching allocator and the CUDA context have settled)."""
+    Z = P.synthetic_exemplar(4, 96, 3.0)
+    X = _t(P.random_patch_init(Z, 192, 192, 8, 1))
+
+    def cycle():
+        idx = pts.ExemplarIndex(_t(Z), 8, d=32)
+        for mode in ("exact", "f16", "fp8", "f16"):
+            pts.nn_search(idx, X, 2, mode)
+        idx.close()
+        torch.cuda.synchronize()
+
+    cycle()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        cycle()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < 8 << 20, (free0 - free1)
