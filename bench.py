@@ -338,6 +338,7 @@ def main():
                 finals.append(X)
         torch.cuda.synchronize()
         launches = L.pts_launch_count() - launches0
+        last_stats = pidx.indices[-1].search_stats()  # the finest level's last search phase
         kern = {}
         if profile:
             for name in ("search_topk", "search_full", "search_tc", "search_tc_list", "rerank", "project", "m_step",
@@ -353,6 +354,7 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = t.item()
         energies = [exact_energy(X) for X in finals]
+        timed_run.last_stats = last_stats
         return total_ms, launches, kern, energies, clk.summary()
 
     total_ms, launches, kern, energies, clocks = timed_run(modes, True)
@@ -366,12 +368,15 @@ def main():
     other = {}
     if also:
         a_ms, _, _, a_energies, _ = timed_run(LEVEL_MODES[also], False)
+        a_stats = timed_run.last_stats
         a_qps = queries_per_step(cfg) * args.steps * world / (a_ms / 1000.0)
         a_ratios = [e / x for e, x in zip(a_energies, ex_energies)]
         other[also] = {"level_modes": LEVEL_MODES[also], "value": a_qps, "ms_per_step": a_ms / args.steps,
                        "speedup_vs_exact": a_qps / exact_qps,
                        "final_energy_ratio_vs_exact": {"max": max(a_ratios), "mean": float(np.mean(a_ratios)),
                                                        "within_1.01": bool(max(a_ratios) <= 1.01)}}
+        if "proposal" in LEVEL_MODES[also]:
+            other[also]["fallback_fraction_last_search"] = a_stats["fallback_queries"] / max(1, a_stats["queries"])
 
     # ---- end to end through the public API with host buffers ----
     inits = [P.random_patch_init(z0, Hc, Hc, wc, args.warmup + i) for i in range(args.steps)]
