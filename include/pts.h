@@ -51,7 +51,7 @@ typedef enum {
     PTS_ERR_CUDA = -2,        /* a CUDA runtime call failed */
     PTS_ERR_OOM = -3,         /* device allocation failed */
     PTS_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
-    PTS_ERR_UNSUPPORTED = -6, /* valid request this build does not support */
+    PTS_ERR_UNSUPPORTED = -6, /* valid request the library does not support */
     PTS_ERR_DEVICE = -7       /* a device-side check failed (see message) */
 } pts_status;
 
