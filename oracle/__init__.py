@@ -7,7 +7,8 @@ does, and nothing here imports the product package.
 
 The arithmetic lives in ``pts_oracle.c`` (plain C, FP64, OpenMP only across
 independent queries/rows); this module builds it with gcc on first use and
-marshals numpy arrays.  The EM driver below follows the paper's two phases
+marshals numpy arrays.  Histogram matching (section 3, Eq. 9) is plain numpy in
+``histogram.py``.  The EM driver below follows the paper's two phases
 (section 2.1: search phase, then optimization phase, repeated).
 """
 from __future__ import annotations
