@@ -321,6 +321,37 @@ pts_status synthesize_level(pts_index index, float *output, int Ho, int Wo, int 
                             float r, float delta, int mode, double *energy_out, void *stream);
 
 /*
+ * Histogram matching (section 3, Eq. 9; the last step of the synthesis
+ * procedure, section 4).  Histograms: one per colour channel, nbins equal bins
+ * over [0, 1] (2 <= nbins <= 256), as fractions of the image's pixels; a value's
+ * bin is clamp(v, 0, 1) * nbins in FP32, floored, capped at nbins - 1.
+ *
+ * m_step_hist -- m_step with the weights of Eq. 9: the contribution of window
+ * p to pixel i is weighted
+ *   W_p,i = w_p / (1 + sum_j max[0, H_x,j(b_j(c)) - H_z,j(b_j(c))]),
+ * c = z_{nn(p)}[i - p] the exemplar pixel it brings, j over the three channels,
+ * H_x the histograms of `current` (the image the search phase matched, device
+ * Ho x Wo x 3), H_z those of the index's exemplar; each pixel is divided by its
+ * own sum of weights.  `output` may be `current` (its histograms are taken
+ * first).  Other arguments and errors as m_step; PTS_ERR_INVALID_ARG for nbins
+ * outside 2..256.  The energy is no longer guaranteed not to rise.
+ *
+ * pts_histogram_match -- each channel of `image` (device H x W x 3, in place)
+ * mapped onto the exemplar's distribution, v -> F_z^-1(F_x(v)), with both CDFs
+ * piecewise linear inside the bins (F(v) = C[b] + (v nbins - b) h[b] for v in
+ * bin b; F_z^-1(u) = (m + (u - C_z[m]) / h_z[m]) / nbins for the non-empty bin
+ * m with C_z[m] <= u < C_z[m+1], 1 beyond).  Asynchronous.
+ *
+ * synthesize_level_hist -- synthesize_level with the M-step of m_step_hist
+ * (H_x re-taken before every M-step).  nbins must be in 2..256.
+ */
+pts_status m_step_hist(pts_index index, const int32_t *nn, const float *weights, int Ho, int Wo, int stride,
+                       int nbins, const float *current, float *output, void *stream);
+pts_status pts_histogram_match(pts_index index, float *image, int H, int W, int nbins, void *stream);
+pts_status synthesize_level_hist(pts_index index, float *output, int Ho, int Wo, int stride, int iters, float r,
+                                 float delta, int mode, int nbins, double *energy_out, void *stream);
+
+/*
  * Pyramid filters for coarse-to-fine synthesis (section 2.1: a coarse result
  * is up-sampled by interpolation to initialise the next level).  The paper
  * names no filter; the library uses

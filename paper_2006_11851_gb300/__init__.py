@@ -15,10 +15,12 @@ from ._binding import (  # noqa: F401
     downsample2,
     fp32_fma_peak,
     gemm_selftest,
+    histogram_match,
     irls_weights,
     kmeans,
     lib,
     m_step,
+    m_step_hist,
     mlp_grad,
     nn_search,
     pca_fit,

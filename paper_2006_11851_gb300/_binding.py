@@ -84,6 +84,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.irls_weights.argtypes = [_vp, _I, _F, _F, _vp, _vp, _vp]
         L.m_step.argtypes = [_vp, _vp, _vp, _I, _I, _I, _vp, _vp]
         L.synthesize_level.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _vp, _vp]
+        L.synthesize_level_hist.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _I, _vp, _vp]
+        L.m_step_hist.argtypes = [_vp, _vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
+        L.pts_histogram_match.argtypes = [_vp, _vp, _I, _I, _I, _vp]
         L.pts_downsample2.argtypes = [_vp, _I, _I, _vp, _vp]
         L.pts_upsample2.argtypes = [_vp, _I, _I, _vp, _vp]
         _declare_optional(L)
@@ -251,14 +254,46 @@ def m_step(index: ExemplarIndex, nn: torch.Tensor, weights: torch.Tensor | None,
 
 
 def synthesize_level(index: ExemplarIndex, output: torch.Tensor, iters: int, r: float = 2.0,
-                     delta: float = 1e-3, mode="exact", stride: int = 2) -> np.ndarray:
-    """Runs EM in place on `output`; returns the iters + 1 energies (host)."""
+                     delta: float = 1e-3, mode="exact", stride: int = 2, hist_bins: int = 0) -> np.ndarray:
+    """Runs EM in place on `output`; returns the iters + 1 energies (host).  hist_bins > 0 uses
+    the M-step with the histogram weights of Eq. 9 (synthesize_level_hist)."""
     _need(output, torch.float32, "output")
     Ho, Wo, _ = output.shape
     E = np.zeros(iters + 1, dtype=np.float64)
-    _check(lib().synthesize_level(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta,
-                                  _mode(mode), E.ctypes.data_as(ctypes.c_void_p), _stream()))
+    if hist_bins:
+        _check(lib().synthesize_level_hist(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta, _mode(mode),
+                                           int(hist_bins), E.ctypes.data_as(ctypes.c_void_p), _stream()))
+    else:
+        _check(lib().synthesize_level(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta,
+                                      _mode(mode), E.ctypes.data_as(ctypes.c_void_p), _stream()))
     return E
+
+
+def m_step_hist(index: ExemplarIndex, nn: torch.Tensor, weights: torch.Tensor | None, current: torch.Tensor,
+                nbins: int, stride: int = 2, out: torch.Tensor | None = None) -> torch.Tensor:
+    """The M-step with the weights of Eq. 9, histograms of `current` against the exemplar's."""
+    _need(nn, torch.int32, "nn")
+    _need(current, torch.float32, "current")
+    if weights is not None:
+        _need(weights, torch.float32, "weights")
+    Ho, Wo, _ = current.shape
+    if out is None:
+        out = torch.empty_like(current)
+    _need(out, torch.float32, "out", (Ho, Wo, 3))
+    Q = index.num_queries(Ho, Wo, stride)
+    if nn.numel() != Q or (weights is not None and weights.numel() != Q):
+        raise ValueError("nn/weights must have one entry per query")
+    _check(lib().m_step_hist(index.handle, _ptr(nn), _ptr(weights), Ho, Wo, stride, int(nbins), _ptr(current),
+                             _ptr(out), _stream()))
+    return out
+
+
+def histogram_match(index: ExemplarIndex, image: torch.Tensor, nbins: int) -> torch.Tensor:
+    """Maps each channel of `image` (in place) onto the exemplar's histogram; returns it."""
+    _need(image, torch.float32, "image")
+    H, W, _ = image.shape
+    _check(lib().pts_histogram_match(index.handle, _ptr(image), H, W, int(nbins), _stream()))
+    return image
 
 
 def downsample2(img: torch.Tensor) -> torch.Tensor:

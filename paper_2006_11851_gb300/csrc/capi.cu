@@ -496,6 +496,7 @@ void pts_index_destroy(pts_index idx) {
     ws.kept.release();
     ws.part_v.release();
     ws.part_i.release();
+    ws.hist.release();
     idx->exemplar.release();
     idx->exemplar4.release();
     idx->mu.release();
@@ -627,32 +628,97 @@ pts_status m_step(pts_index idx, const int32_t *nn, const float *weights, int Ho
     return PTS_OK;
 }
 
-pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int stride, int iters,
-                            float r, float delta, int mode, double *energy_out, void *stream) {
-    if (!idx || !output || !energy_out)
-        return set_error(PTS_ERR_INVALID_ARG, "synthesize_level: null pointer");
-    if (iters < 0) return set_error(PTS_ERR_INVALID_ARG, "synthesize_level: iters < 0");
+pts_status m_step_hist(pts_index idx, const int32_t *nn, const float *weights, int Ho, int Wo, int stride, int nbins,
+                       const float *current, float *output, void *stream) {
+    if (!idx || !nn || !output || !current) return set_error(PTS_ERR_INVALID_ARG, "m_step_hist: null pointer");
+    if (nbins < 2 || nbins > kMaxHistBins) return set_error(PTS_ERR_INVALID_ARG, "m_step_hist: nbins in 2..256");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "m_step_hist"));
+    cudaStream_t st = as_stream(stream);
+    Workspace &ws = idx->ws;
+    PTS_TRY(ws.hist.ensure(6 * kMaxHistBins, "histograms"));
+    unsigned int *cx = ws.hist.ptr, *cz = ws.hist.ptr + 3 * kMaxHistBins;
+    const long nx = (long)Ho * Wo, nz = (long)idx->He * idx->We;
+    launch_hist3(current, nx, nbins, cx, st);
+    launch_hist3(idx->exemplar.ptr, nz, nbins, cz, st);
+    launch_m_step_hist(nn, weights, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride, nbins, cx, nx,
+                       cz, nz, output, idx->status.ptr, st);
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
+pts_status pts_histogram_match(pts_index idx, float *image, int H, int W, int nbins, void *stream) {
+    if (!idx || !image) return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: null pointer");
+    if (nbins < 2 || nbins > kMaxHistBins)
+        return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: nbins in 2..256");
+    if (H < 1 || W < 1) return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: empty image");
+    cudaStream_t st = as_stream(stream);
+    Workspace &ws = idx->ws;
+    PTS_TRY(ws.hist.ensure(6 * kMaxHistBins, "histograms"));
+    unsigned int *cx = ws.hist.ptr, *cz = ws.hist.ptr + 3 * kMaxHistBins;
+    const long nx = (long)H * W, nz = (long)idx->He * idx->We;
+    launch_hist3(image, nx, nbins, cx, st);
+    launch_hist3(idx->exemplar.ptr, nz, nbins, cz, st);
+    launch_hist_match(image, nx, nbins, cx, nx, cz, nz, st);
+    PTS_CUDA_TRY(cudaGetLastError());
+    return PTS_OK;
+}
+
+// the EM loop of synthesize_level; nbins > 0 takes the M-step of m_step_hist
+static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r,
+                                  float delta, int mode, int nbins, double *energy_out, void *stream,
+                                  const char *name) {
+    if (!idx || !output || !energy_out) return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": null pointer");
+    if (iters < 0) return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": iters < 0");
     if (!(r > 0.0f && r <= 2.0f) || !(delta > 0.0f))
-        return set_error(PTS_ERR_INVALID_ARG, "synthesize_level: need 0 < r <= 2 and delta > 0");
-    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "synthesize_level"));
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": need 0 < r <= 2 and delta > 0");
+    if (nbins != 0 && (nbins < 2 || nbins > kMaxHistBins))
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": nbins in 2..256");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, name));
     cudaStream_t st = as_stream(stream);
     const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
     PTS_TRY(ensure_workspace(idx, Q));
     Workspace &ws = idx->ws;
     PTS_TRY(ws.energy.ensure(iters + 1, "energies"));
+    unsigned int *cx = nullptr, *cz = nullptr;
+    const long nx = (long)Ho * Wo, nz = (long)idx->He * idx->We;
+    if (nbins) {
+        PTS_TRY(ws.hist.ensure(6 * kMaxHistBins, "histograms"));
+        cx = ws.hist.ptr;
+        cz = ws.hist.ptr + 3 * kMaxHistBins;
+        launch_hist3(idx->exemplar.ptr, nz, nbins, cz, st);
+    }
     for (int t = 0; t <= iters; ++t) {
         PTS_TRY(nn_search_impl(idx, output, Ho, Wo, stride, mode, ws.nn.ptr, ws.d2.ptr, st));
         launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, ws.energy.ptr + t, ws.partial.ptr,
                     ws.ticket.ptr, st);
         if (t == iters) break;
-        launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho,
-                      Wo, stride, output, idx->status.ptr, st);
+        if (nbins) {
+            launch_hist3(output, nx, nbins, cx, st);  // of the image the E-step matched
+            launch_m_step_hist(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo,
+                               stride, nbins, cx, nx, cz, nz, output, idx->status.ptr, st);
+        } else {
+            launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho,
+                          Wo, stride, output, idx->status.ptr, st);
+        }
     }
     PTS_CUDA_TRY(cudaGetLastError());
     PTS_CUDA_TRY(cudaMemcpyAsync(energy_out, ws.energy.ptr, sizeof(double) * (iters + 1),
                                  cudaMemcpyDeviceToHost, st));
     PTS_CUDA_TRY(cudaStreamSynchronize(st));
     return read_status(idx, st);
+}
+
+pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r, float delta,
+                            int mode, double *energy_out, void *stream) {
+    return synthesize_impl(idx, output, Ho, Wo, stride, iters, r, delta, mode, 0, energy_out, stream,
+                           "synthesize_level");
+}
+
+pts_status synthesize_level_hist(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r,
+                                 float delta, int mode, int nbins, double *energy_out, void *stream) {
+    if (nbins == 0) return set_error(PTS_ERR_INVALID_ARG, "synthesize_level_hist: nbins in 2..256");
+    return synthesize_impl(idx, output, Ho, Wo, stride, iters, r, delta, mode, nbins, energy_out, stream,
+                           "synthesize_level_hist");
 }
 
 pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int Wo, int stride, float *y_out,

@@ -17,11 +17,23 @@
 namespace pts {
 namespace {
 
-template <int S>
+// HIST: the weights of Eq. 9 (section 3).  The contribution of window p to pixel i is weighted
+// w_p / (1 + sum_j max[0, H_x,j(b_j(c)) - H_z,j(b_j(c))]), c the exemplar pixel it brings, the
+// excess table (3 x nbins, from the two images' channel counts) built per block in shared memory;
+// every pixel is normalised by its own sum of weights.  Without HIST the patch's four pixels share
+// one sum.
+template <int S, bool HIST>
 __global__ void __launch_bounds__(128)
     k_m_step(const int *__restrict__ nn, const float *__restrict__ wts, const float4 *__restrict__ Z4,
              int We, int ex, int N, int w, int Ho, int Wo, int qy_n, int qx_n,
-             float *__restrict__ out, int *__restrict__ status) {
+             float *__restrict__ out, int *__restrict__ status, int nbins, const unsigned int *__restrict__ cx,
+             long nx, const unsigned int *__restrict__ cz, long nz) {
+    __shared__ float hex[HIST ? 3 * kMaxHistBins : 1];
+    if constexpr (HIST) {
+        for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x)
+            hex[i] = (float)fmax(0.0, (double)cx[i] / (double)nx - (double)cz[i] / (double)nz);
+        __syncthreads();
+    }
     const int px = blockIdx.x * blockDim.x + threadIdx.x;
     const int py = blockIdx.y;
     if (px >= Wo / S || py >= Ho / S) return;
@@ -29,12 +41,18 @@ __global__ void __launch_bounds__(128)
     const int qy_lo = max(0, py - ws + 1), qy_hi = min(py, qy_n - 1);
     const int qx_lo = max(0, px - ws + 1), qx_hi = min(px, qx_n - 1);
     float num[S][S][3];
+    float dpix[HIST ? S : 1][HIST ? S : 1];
 #pragma unroll
     for (int t = 0; t < S; ++t)
 #pragma unroll
         for (int u = 0; u < S; ++u)
 #pragma unroll
             for (int c = 0; c < 3; ++c) num[t][u][c] = 0.0f;
+    if constexpr (HIST)
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+#pragma unroll
+            for (int u = 0; u < S; ++u) dpix[t][u] = 0.0f;
     float den = 0.0f;
     bool bad = false;
     for (int qy = qy_lo; qy <= qy_hi; ++qy) {
@@ -55,9 +73,15 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
                 for (int u = 0; u < S; ++u) {
                     const float4 v = __ldg(zb + (size_t)t * We + u);
-                    num[t][u][0] = fmaf(wt, v.x, num[t][u][0]);
-                    num[t][u][1] = fmaf(wt, v.y, num[t][u][1]);
-                    num[t][u][2] = fmaf(wt, v.z, num[t][u][2]);
+                    float wv = wt;
+                    if constexpr (HIST) {
+                        wv = wt / (1.0f + hex[hist_bin(v.x, nbins)] + hex[nbins + hist_bin(v.y, nbins)] +
+                                   hex[2 * nbins + hist_bin(v.z, nbins)]);
+                        dpix[t][u] += wv;
+                    }
+                    num[t][u][0] = fmaf(wv, v.x, num[t][u][0]);
+                    num[t][u][1] = fmaf(wv, v.y, num[t][u][1]);
+                    num[t][u][2] = fmaf(wv, v.z, num[t][u][2]);
                 }
             den += wt;
         }
@@ -67,9 +91,12 @@ __global__ void __launch_bounds__(128)
     for (int t = 0; t < S; ++t) {
         float *o = out + ((size_t)(py * S + t) * Wo + px * S) * 3;
 #pragma unroll
-        for (int u = 0; u < S; ++u)
+        for (int u = 0; u < S; ++u) {
+            float d = den;
+            if constexpr (HIST) d = dpix[t][u];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) o[u * 3 + c] = num[t][u][c] / den;
+            for (int c = 0; c < 3; ++c) o[u * 3 + c] = num[t][u][c] / d;
+        }
     }
 }
 
@@ -183,13 +210,41 @@ void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, in
     ProfScope ps(kProfMStep, st, 1);
     switch (stride) {
         case 1:
-            k_m_step<1><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            k_m_step<1, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status, 0,
+                                                       nullptr, 1, nullptr, 1);
             break;
         case 2:
-            k_m_step<2><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            k_m_step<2, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status, 0,
+                                                       nullptr, 1, nullptr, 1);
             break;
         case 4:
-            k_m_step<4><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status);
+            k_m_step<4, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status, 0,
+                                                       nullptr, 1, nullptr, 1);
+            break;
+        default:
+            break;  // rejected by the caller
+    }
+}
+
+void launch_m_step_hist(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w, int Ho, int Wo,
+                        int stride, int nbins, const unsigned int *cx, long nx, const unsigned int *cz, long nz,
+                        float *out, int *status, cudaStream_t st) {
+    const int qy_n = (Ho - w) / stride + 1, qx_n = (Wo - w) / stride + 1;
+    const int PX = Wo / stride, PY = Ho / stride;
+    dim3 block(128), grid(ceil_div(PX, 128), PY);
+    ProfScope ps(kProfMStep, st, 1);
+    switch (stride) {
+        case 1:
+            k_m_step<1, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status,
+                                                      nbins, cx, nx, cz, nz);
+            break;
+        case 2:
+            k_m_step<2, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status,
+                                                      nbins, cx, nx, cz, nz);
+            break;
+        case 4:
+            k_m_step<4, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status,
+                                                      nbins, cx, nx, cz, nz);
             break;
         default:
             break;  // rejected by the caller

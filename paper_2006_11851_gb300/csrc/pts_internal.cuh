@@ -94,6 +94,7 @@ struct Workspace {
     DevBuf<unsigned long long> best64;  // [Q] packed (d2 bits, n)
     DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
     DevBuf<float> pca_thr;     // [Q] warm-start bound of the exact PCA pass
+    DevBuf<unsigned int> hist; // [2][3][256] channel histograms (image, exemplar)
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
     DevBuf<uint8_t> qtile8;    // [ceil(Q/128)][128 x Kf8] FP8 query operand tiles
     DevBuf<float> qscale;      // [Q] FP8 query row scales
@@ -332,6 +333,19 @@ struct ProfScope {
 };
 // mstep.cu
 void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st);
+// histogram.cu (section 3, Eq. 9)
+constexpr int kMaxHistBins = 256;
+// bin of a channel value: clamped to [0, 1], times nbins in FP32, floored, capped at the last bin
+__device__ __forceinline__ int hist_bin(float v, int nbins) {
+    const float c = fminf(fmaxf(v, 0.0f), 1.0f);
+    return min((int)floorf(c * (float)nbins), nbins - 1);
+}
+void launch_hist3(const float *img, long npix, int nbins, unsigned int *counts, cudaStream_t st);
+void launch_hist_match(float *img, long npix, int nbins, const unsigned int *cx, long nx, const unsigned int *cz,
+                       long nz, cudaStream_t st);
+void launch_m_step_hist(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w, int Ho, int Wo,
+                        int stride, int nbins, const unsigned int *cx, long nx, const unsigned int *cz, long nz,
+                        float *out, int *status, cudaStream_t st);
 void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w,
                    int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st);
 void launch_irls(const float *d2, int Q, float r, float delta, float *wts, double *energy_out,

@@ -3,7 +3,7 @@ or (--pyramid) whole coarse-to-fine syntheses with a search mode per level.
 
     python -m paper_2006_11851_gb300.profile_case --level 2 --mode exact --steps 2
     python -m paper_2006_11851_gb300.profile_case --pyramid --modes exact,f16,f16 --steps 2
-    python -m paper_2006_11851_gb300.profile_case --big 4096 --steps 3
+    python -m paper_2006_11851_gb300.profile_case --big 4096 --steps 3 [--hist 32]
 
 --big H projects (d = 64) and averages (M-step) one H x H output against the finest level's
 index (256x256 exemplar, w = 8), so that the working set is far above the L2 cache: a uniform
@@ -38,6 +38,8 @@ def main() -> int:
     ap.add_argument("--pyramid", action="store_true")
     ap.add_argument("--modes", default="exact,f16,f16")
     ap.add_argument("--big", type=int, default=0)
+    ap.add_argument("--hist", type=int, default=0, help="with --big: also time the Eq. 9 M-step and the final "
+                                                        "histogram matching with this many bins")
     args = ap.parse_args()
     if args.pyramid:
         return run_pyramid(args)
@@ -106,9 +108,21 @@ def run_big(args) -> int:
         # the M-step reads Q matches and weights and writes the image
         bp = H * H * 12 + Q * (da + 2) * 4
         bm = Q * 8 + H * H * 12
-        print(f"step {s}: project {tp:.3f} ms ({bp / tp / 1e6:.0f} GB/s, "
-              f"{2.0 * idx.info['D'] * idx.info['d'] * Q / tp / 1e9:.1f} TFLOP/s)  "
-              f"m_step {tm:.3f} ms ({bm / tm / 1e6:.0f} GB/s)  Q={Q}")
+        msg = (f"step {s}: project {tp:.3f} ms ({bp / tp / 1e6:.0f} GB/s, "
+               f"{2.0 * idx.info['D'] * idx.info['d'] * Q / tp / 1e9:.1f} TFLOP/s)  "
+               f"m_step {tm:.3f} ms ({bm / tm / 1e6:.0f} GB/s)  Q={Q}")
+        if args.hist:
+            out2 = torch.empty_like(out)
+            eh = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            eh[0].record()
+            pts.m_step_hist(idx, nn, wts, X, args.hist, out=out2)
+            eh[1].record()
+            pts.histogram_match(idx, out2, args.hist)
+            eh[2].record()
+            eh[2].synchronize()
+            msg += (f"  m_step_hist {eh[0].elapsed_time(eh[1]):.3f} ms  "
+                    f"histogram_match {eh[1].elapsed_time(eh[2]):.3f} ms")
+        print(msg)
     idx.close()
     return 0
 

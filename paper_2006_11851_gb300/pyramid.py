@@ -7,7 +7,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from ._binding import ExemplarIndex, downsample2, synthesize_level, upsample2
+from ._binding import ExemplarIndex, downsample2, histogram_match, synthesize_level, upsample2
 
 
 class PyramidIndex:
@@ -35,21 +35,26 @@ class PyramidIndex:
 
 def synthesize_pyramid(pidx: PyramidIndex, init_coarse: torch.Tensor, iters: int = 5,
                        r: float = 2.0, delta: float = 1e-3, mode="exact", stride: int = 2,
-                       keep_levels: bool = False):
+                       keep_levels: bool = False, hist_bins: int = 0):
     """Runs every level in place, coarse to fine.
 
     mode is one search mode for every level or a list with one per level.
-    Returns (final image, energies [levels, iters + 1], per-level images if
-    keep_levels).  init_coarse is the initial image of level 0.
+    hist_bins > 0 runs the M-steps with the histogram weights of Eq. 9 and ends
+    with the final histogram matching of the result to the finest exemplar
+    (section 4).  Returns (final image, energies [levels, iters + 1], per-level
+    images if keep_levels).  init_coarse is the initial image of level 0.
     """
     X = init_coarse.contiguous()
     energies = np.zeros((pidx.levels, iters + 1))
     imgs = []
     modes = list(mode) if isinstance(mode, (list, tuple)) else [mode] * pidx.levels
     for lev, ix in enumerate(pidx.indices):
-        energies[lev] = synthesize_level(ix, X, iters, r=r, delta=delta, mode=modes[lev], stride=stride)
+        energies[lev] = synthesize_level(ix, X, iters, r=r, delta=delta, mode=modes[lev], stride=stride,
+                                         hist_bins=hist_bins)
         if keep_levels:
             imgs.append(X.clone())
         if lev + 1 < pidx.levels:
             X = upsample2(X)
+    if hist_bins:
+        histogram_match(pidx.indices[-1], X, hist_bins)
     return X, energies, imgs
