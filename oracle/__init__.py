@@ -324,6 +324,35 @@ def synthesize_level(Z, X0, w: int, iters: int, r: float = 2.0, delta: float = 1
     return out
 
 
+def synthesize_level_converge(Z, X0, w: int, max_iters: int, r: float = 0.8, delta: float = 1e-3, stride: int = 2,
+                              nthreads: int = 0, f32_io: bool = True):
+    """EM iterations until the search phase returns, for every query, the window it returned the
+    iteration before (the set {z_p} no longer changes: section 2.1's stopping rule), or until
+    max_iters M-steps have run; the last search phase gives the final energy.  Returns a dict with
+    X, E and E_delta (iters + 1 entries, as synthesize_level) and iters, the M-steps run."""
+    Z = _f64(Z)
+    X = _f64(X0)
+    Ho, Wo, _ = X.shape
+    E, Ed = [], []
+    nn_prev = None
+    it = 0
+    while True:
+        if f32_io:
+            X = X.astype(np.float32).astype(np.float64)
+        nn, d2 = nn_bruteforce(X, Z, w, stride, nthreads=nthreads)
+        W, er, ed = irls(d2, r, delta)
+        if f32_io:
+            W = W.astype(np.float32).astype(np.float64)
+        E.append(er)
+        Ed.append(ed)
+        if it == max_iters or (nn_prev is not None and np.array_equal(nn, nn_prev)):
+            break
+        X = m_step(nn, W, Z, w, Ho, Wo, stride, X_prev=X)
+        nn_prev = nn
+        it += 1
+    return {"X": X, "E": np.array(E), "E_delta": np.array(Ed), "iters": it}
+
+
 # ---------------------------------------------------------------------------
 # learned cluster proposal (replaces the k-means tree of section 2.2)
 # ---------------------------------------------------------------------------

@@ -323,3 +323,45 @@ def test_generator_golden_hashes():
         seed, size, shrink = key.split("_")
         img = P.synthetic_exemplar(int(seed), int(size), float(shrink))
         assert P.array_digest(img) == digest, key
+
+
+# --------------------------------------------------------------------------
+# stopping rule of section 2.1: iterate until {z_p} no longer changes
+# --------------------------------------------------------------------------
+def test_converge_stops_at_once_on_the_exemplar(oracle_lib):
+    """Seeded with the exemplar: the first search matches every window to itself, the M-step
+    returns the exemplar, the second search repeats the first: one M-step, energy 0."""
+    Z = P.synthetic_exemplar(22, 32, 3.0)
+    res = oracle.synthesize_level_converge(Z, Z, 8, 10, r=0.8)
+    assert res["iters"] == 1
+    assert np.all(res["E"] == 0.0) and len(res["E"]) == 2
+
+
+def test_converged_image_is_a_fixed_point(oracle_lib):
+    """r = 2 (all weights 1): when two consecutive searches return the same windows, one more
+    iteration of the plain EM loop returns the image unchanged, a fixed point of the E- and
+    M-steps.  (For r < 2 the IRLS weights still move with the image, so only the windows are fixed.)"""
+    Z = P.synthetic_exemplar(23, 32, 3.0)
+    X0 = P.random_patch_init(Z, 40, 40, 8, 3)
+    res = oracle.synthesize_level_converge(Z, X0, 8, 40, r=2.0)
+    assert 1 <= res["iters"] < 40
+    again = oracle.synthesize_level(Z, res["X"], 8, 1, r=2.0)
+    np.testing.assert_array_equal(again["X"], res["X"])
+
+
+def test_converge_robust_energy_never_rises(oracle_lib):
+    """r = 0.8: the delta-form energy, which Eq. 8 majorises, never rises until the rule stops."""
+    Z = P.synthetic_exemplar(23, 32, 3.0)
+    X0 = P.random_patch_init(Z, 40, 40, 8, 5)
+    res = oracle.synthesize_level_converge(Z, X0, 8, 40, r=0.8, f32_io=False)
+    assert 1 <= res["iters"] <= 40
+    assert np.all(np.diff(res["E_delta"]) <= 1e-12 * res["E_delta"][0])
+
+
+def test_converge_respects_the_iteration_cap(oracle_lib):
+    Z = P.synthetic_exemplar(24, 32, 3.0)
+    X0 = P.random_patch_init(Z, 40, 40, 8, 4)
+    res = oracle.synthesize_level_converge(Z, X0, 8, 1, r=0.8)
+    assert res["iters"] == 1 and len(res["E"]) == 2
+    res0 = oracle.synthesize_level_converge(Z, X0, 8, 0, r=0.8)
+    assert res0["iters"] == 0 and len(res0["E"]) == 1
