@@ -352,6 +352,23 @@ pts_status synthesize_level_hist(pts_index index, float *output, int Ho, int Wo,
                                  float delta, int mode, int nbins, double *energy_out, void *stream);
 
 /*
+ * synthesize_level_converge -- the EM loop of synthesize_level with section
+ * 2.1's stopping rule: iterate until the search phase returns, for every
+ * query, the window it returned the iteration before (the set {z_p} no longer
+ * changes), or until max_iters M-steps have run (max_iters >= 0).  nbins 0
+ * takes the plain M-step, 2..256 that of m_step_hist.  The paper prefers the
+ * robust r = 0.8 (delta as in synthesize_level).
+ * energy_out  HOST, max_iters + 1 float64, of which iters_out + 1 are written:
+ *             energy_out[t] is the energy of the iterate entering iteration t,
+ *             energy_out[iters_out] that of the result.
+ * iters_out   HOST, one int: the M-steps run.
+ * Synchronises `stream` once per iteration (the rule reads a device count).
+ */
+pts_status synthesize_level_converge(pts_index index, float *output, int Ho, int Wo, int stride, int max_iters,
+                                     float r, float delta, int mode, int nbins, double *energy_out, int *iters_out,
+                                     void *stream);
+
+/*
  * Pyramid filters for coarse-to-fine synthesis (section 2.1: a coarse result
  * is up-sampled by interpolation to initialise the next level).  The paper
  * names no filter; the library uses

@@ -87,6 +87,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.synthesize_level_hist.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _I, _vp, _vp]
         L.m_step_hist.argtypes = [_vp, _vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
         L.pts_histogram_match.argtypes = [_vp, _vp, _I, _I, _I, _vp]
+        L.synthesize_level_converge.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _I, _vp,
+                                                ctypes.POINTER(_I), _vp]
         L.pts_downsample2.argtypes = [_vp, _I, _I, _vp, _vp]
         L.pts_upsample2.argtypes = [_vp, _I, _I, _vp, _vp]
         _declare_optional(L)
@@ -267,6 +269,20 @@ def synthesize_level(index: ExemplarIndex, output: torch.Tensor, iters: int, r: 
         _check(lib().synthesize_level(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta,
                                       _mode(mode), E.ctypes.data_as(ctypes.c_void_p), _stream()))
     return E
+
+
+def synthesize_level_converge(index: ExemplarIndex, output: torch.Tensor, max_iters: int, r: float = 0.8,
+                              delta: float = 1e-3, mode="exact", stride: int = 2, hist_bins: int = 0):
+    """EM in place on `output` until the searched windows repeat (or max_iters M-steps);
+    returns (energies [iters + 1] on the host, iters)."""
+    _need(output, torch.float32, "output")
+    Ho, Wo, _ = output.shape
+    E = np.zeros(max_iters + 1, dtype=np.float64)
+    it = _I(0)
+    _check(lib().synthesize_level_converge(index.handle, _ptr(output), Ho, Wo, stride, int(max_iters), r, delta,
+                                           _mode(mode), int(hist_bins), E.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(it), _stream()))
+    return E[:it.value + 1], it.value
 
 
 def m_step_hist(index: ExemplarIndex, nn: torch.Tensor, weights: torch.Tensor | None, current: torch.Tensor,

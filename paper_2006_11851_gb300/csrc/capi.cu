@@ -497,6 +497,8 @@ void pts_index_destroy(pts_index idx) {
     ws.part_v.release();
     ws.part_i.release();
     ws.hist.release();
+    ws.nn_prev.release();
+    ws.diff.release();
     idx->exemplar.release();
     idx->exemplar4.release();
     idx->mu.release();
@@ -712,6 +714,62 @@ pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int st
                             int mode, double *energy_out, void *stream) {
     return synthesize_impl(idx, output, Ho, Wo, stride, iters, r, delta, mode, 0, energy_out, stream,
                            "synthesize_level");
+}
+
+pts_status synthesize_level_converge(pts_index idx, float *output, int Ho, int Wo, int stride, int max_iters, float r,
+                                     float delta, int mode, int nbins, double *energy_out, int *iters_out,
+                                     void *stream) {
+    const char *name = "synthesize_level_converge";
+    if (!idx || !output || !energy_out || !iters_out)
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": null pointer");
+    if (max_iters < 0) return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": max_iters < 0");
+    if (!(r > 0.0f && r <= 2.0f) || !(delta > 0.0f))
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": need 0 < r <= 2 and delta > 0");
+    if (nbins != 0 && (nbins < 2 || nbins > kMaxHistBins))
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": nbins 0 or in 2..256");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, name));
+    cudaStream_t st = as_stream(stream);
+    const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
+    PTS_TRY(ensure_workspace(idx, Q));
+    Workspace &ws = idx->ws;
+    PTS_TRY(ws.energy.ensure(max_iters + 1, "energies"));
+    PTS_TRY(ws.nn_prev.ensure((size_t)std::max(Q, 1), "previous windows"));
+    PTS_TRY(ws.diff.ensure(1, "changed windows"));
+    unsigned int *cx = nullptr, *cz = nullptr;
+    const long nx = (long)Ho * Wo, nz = (long)idx->He * idx->We;
+    if (nbins) {
+        PTS_TRY(ws.hist.ensure(6 * kMaxHistBins, "histograms"));
+        cx = ws.hist.ptr;
+        cz = ws.hist.ptr + 3 * kMaxHistBins;
+        launch_hist3(idx->exemplar.ptr, nz, nbins, cz, st);
+    }
+    int it = 0;
+    PTS_TRY(nn_search_impl(idx, output, Ho, Wo, stride, mode, ws.nn.ptr, ws.d2.ptr, st));
+    launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, ws.energy.ptr, ws.partial.ptr, ws.ticket.ptr, st);
+    while (it < max_iters) {
+        if (nbins) {
+            launch_hist3(output, nx, nbins, cx, st);
+            launch_m_step_hist(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo,
+                               stride, nbins, cx, nx, cz, nz, output, idx->status.ptr, st);
+        } else {
+            launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride,
+                          output, idx->status.ptr, st);
+        }
+        PTS_CUDA_TRY(cudaMemcpyAsync(ws.nn_prev.ptr, ws.nn.ptr, sizeof(int) * Q, cudaMemcpyDeviceToDevice, st));
+        ++it;
+        PTS_TRY(nn_search_impl(idx, output, Ho, Wo, stride, mode, ws.nn.ptr, ws.d2.ptr, st));
+        launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, ws.energy.ptr + it, ws.partial.ptr, ws.ticket.ptr, st);
+        launch_count_diff(ws.nn.ptr, ws.nn_prev.ptr, Q, ws.diff.ptr, st);
+        unsigned int changed = 0;
+        PTS_CUDA_TRY(cudaMemcpyAsync(&changed, ws.diff.ptr, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        PTS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (changed == 0) break;
+    }
+    PTS_CUDA_TRY(cudaGetLastError());
+    PTS_CUDA_TRY(cudaMemcpyAsync(energy_out, ws.energy.ptr, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    *iters_out = it;
+    return read_status(idx, st);
 }
 
 pts_status synthesize_level_hist(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r,

@@ -100,6 +100,16 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// how many entries of a and b differ (the stopping rule of section 2.1: no window changed)
+__global__ void __launch_bounds__(256) k_count_diff(const int *__restrict__ a, const int *__restrict__ b, int n,
+                                                    unsigned int *__restrict__ count) {
+    unsigned int c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += a[i] != b[i] ? 1u : 0u;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) c += __shfl_xor_sync(0xffffffffu, c, s);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 __global__ void k_rgba(const float *__restrict__ Z, long npix, float4 *__restrict__ out) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < npix; i += (long)gridDim.x * blockDim.x)
         out[i] = make_float4(Z[3 * i], Z[3 * i + 1], Z[3 * i + 2], 0.0f);
@@ -195,6 +205,13 @@ __global__ void k_upsample2(const float *__restrict__ in, int H, int W, float *_
 }
 
 }  // namespace
+
+void launch_count_diff(const int *a, const int *b, int n, unsigned int *count, cudaStream_t st) {
+    cudaMemsetAsync(count, 0, sizeof(unsigned int), st);
+    if (n <= 0) return;
+    count_launches(1);
+    k_count_diff<<<(unsigned)std::min<long>(ceil_div((long)n, 256), 152 * 4), 256, 0, st>>>(a, b, n, count);
+}
 
 void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st) {
     if (npix <= 0) return;

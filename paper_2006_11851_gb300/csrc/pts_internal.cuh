@@ -95,6 +95,8 @@ struct Workspace {
     DevBuf<float> thr0;        // [Q][2] warm-start bounds (one per column half of a tile)
     DevBuf<float> pca_thr;     // [Q] warm-start bound of the exact PCA pass
     DevBuf<unsigned int> hist; // [2][3][256] channel histograms (image, exemplar)
+    DevBuf<int> nn_prev;       // [Q] the previous search's windows (stopping rule)
+    DevBuf<unsigned int> diff; // [1] how many windows changed
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
     DevBuf<uint8_t> qtile8;    // [ceil(Q/128)][128 x Kf8] FP8 query operand tiles
     DevBuf<float> qscale;      // [Q] FP8 query row scales
@@ -333,6 +335,7 @@ struct ProfScope {
 };
 // mstep.cu
 void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st);
+void launch_count_diff(const int *a, const int *b, int n, unsigned int *count, cudaStream_t st);
 // histogram.cu (section 3, Eq. 9)
 constexpr int kMaxHistBins = 256;
 // bin of a channel value: clamped to [0, 1], times nbins in FP32, floored, capped at the last bin

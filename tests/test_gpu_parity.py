@@ -297,3 +297,27 @@ def test_index_destroy_returns_device_memory():
         cycle()
     free1 = torch.cuda.mem_get_info()[0]
     assert free0 - free1 < 8 << 20, (free0 - free1)
+
+
+@pytest.mark.parametrize("r", [2.0, 0.8])
+def test_converge_against_oracle(c1, r):
+    """Section 2.1's stopping rule: the GPU loop stops after as many M-steps as the oracle's."""
+    Z, idx = c1
+    X0 = P.random_patch_init(Z, 96, 96, 8, 6)
+    xt = _t(X0)
+    E, it = pts.synthesize_level_converge(idx, xt, 30, r=r, mode="exact")
+    ref = oracle.synthesize_level_converge(Z, X0, 8, 30, r=r)
+    assert it == ref["iters"], (it, ref["iters"])
+    np.testing.assert_allclose(E, ref["E"], rtol=1e-3)
+    diff = np.abs(xt.cpu().numpy() - ref["X"])
+    assert np.mean(diff < 1e-4) > 0.99
+
+
+def test_converge_reproduces_exemplar_in_one_step(c1):
+    """Seeded with the exemplar the windows repeat after one M-step.  (FP32 averaging of equal
+    values can be 1 ulp off at border pixels, so the second energy is ~0, not 0.)"""
+    Z, idx = c1
+    xt = _t(Z)
+    E, it = pts.synthesize_level_converge(idx, xt, 10, r=2.0, mode="exact")
+    assert it == 1 and E[0] == 0.0 and E[1] < 1e-8
+    np.testing.assert_allclose(xt.cpu().numpy(), Z, atol=1e-6)
