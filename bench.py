@@ -205,6 +205,8 @@ LEVEL_MODES = {
     # the learned proposal on the finest level (the proposal trained there), the middle level on
     # the FP16 tensor-core brute force, the coarsest exact (as f16c)
     "proposal": ["exact", "f16", "proposal"],
+    # the paper's own search on the finest level (k = 4 k-means tree, greedy descent), for comparison
+    "kmtree": ["exact", "f16", "kmtree"],
 }
 PCA_PASS_MIN_VAR = 0.85  # the exact search skips its PCA pass below this retained variance
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
@@ -301,6 +303,10 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         train_loss = [float(x) for x in loss]
+
+    if "kmtree" in need:
+        pts.build_kmeans_tree(pidx.indices[need.index("kmtree") % cfg["levels"]], 10)
+        torch.cuda.synchronize()
 
     n_total = args.warmup + args.steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

@@ -74,13 +74,21 @@ typedef enum {
  *                     max_n |2 y_nj| / 448, the query y s_j / t_q with a per-row
  *                     scale t_q; the epilogue forms ||u_n||^2 + t_q acc in FP32.
  *                     Not certified; every candidate is re-ranked in FP32.
- *   PTS_PROPOSAL      learned cluster proposal + FP32 probe + re-rank, with
- *                     the exact search as fallback. */
+ *   PTS_PROPOSAL      learned cluster proposal: the network ranks k-means
+ *                     clusters, the 4 best are probed on the FP16 tensor cores,
+ *                     the candidates re-ranked in exact FP32; queries whose
+ *                     result fails the distance test (pts_train_proposal) are
+ *                     searched as in PTS_F16_RERANK.
+ *   PTS_KMTREE        the paper's own search (section 2.2): greedy descent of a
+ *                     k = 4 hierarchical k-means tree over the PCA coordinates
+ *                     (pts_build_kmeans_tree) to a leaf, whose windows are
+ *                     re-ranked in exact FP32.  Approximate. */
 typedef enum {
     PTS_EXACT_F32 = 0,
     PTS_F16_RERANK = 1,
     PTS_FP8_RERANK = 2,
-    PTS_PROPOSAL = 3
+    PTS_PROPOSAL = 3,
+    PTS_KMTREE = 4
 } pts_mode;
 
 typedef struct pts_index_s *pts_index; /* opaque, owned by the library */
@@ -180,6 +188,28 @@ pts_status pts_index_get_info(pts_index index, pts_index_info *info);
  * for a NULL index or parts < 0; parts larger than the tile count act as the
  * tile count. */
 pts_status pts_index_set_tc_parts(pts_index index, int parts);
+
+/*
+ * pts_build_kmeans_tree -- builds the search tree of PTS_KMTREE (section 2.2): hierarchical
+ * k-means with k = 4 over the index's d PCA coordinates, each node split until it holds fewer
+ * than 4 windows (a split that leaves a child with all of its parent's windows makes that child
+ * a leaf).  Each split seeds the centroids with the node's windows at 1/8, 3/8, 5/8 and 7/8 of its
+ * range and runs `iters` Lloyd iterations (1..100); deterministic.  Synchronises `stream` once
+ * per tree level.
+ * pts_kmtree_info -- internal nodes, leaves and levels of the built tree (host ints, any may be
+ * NULL); PTS_ERR_INVALID_ARG when no tree is built.
+ * pts_kmtree_export -- copies the tree to HOST arrays (each may be NULL): child[4 * internal]
+ * (>= 0 internal node, <= -2 leaf -c - 2, -1 none), leaf_begin/leaf_end[leaves] (ranges of
+ * perm), perm[N] (windows in leaf order), cent[4 * internal * d] (child centroids).
+ * Synchronises `stream`.
+ * pts_kmtree_last_leaves -- the leaf each query reached in the last PTS_KMTREE search (HOST,
+ * Q ints).  Synchronises `stream`.
+ */
+pts_status pts_build_kmeans_tree(pts_index index, int iters, void *stream);
+pts_status pts_kmtree_info(pts_index index, int *n_internal, int *n_leaves, int *depth);
+pts_status pts_kmtree_export(pts_index index, int *child, int *leaf_begin, int *leaf_end, int *perm, float *cent,
+                             void *stream);
+pts_status pts_kmtree_last_leaves(pts_index index, int *leaves, int Q, void *stream);
 
 /* Reads and clears the index's device status word (synchronises `stream`).
  * Returns PTS_OK, PTS_ERR_DEVICE or PTS_ERR_TIMEOUT. */

@@ -12,12 +12,16 @@ from ._binding import (  # noqa: F401
     ExemplarIndex,
     PtsError,
     build_exemplar_index,
+    build_kmeans_tree,
     downsample2,
     fp32_fma_peak,
     gemm_selftest,
     histogram_match,
     irls_weights,
     kmeans,
+    kmtree_export,
+    kmtree_info,
+    kmtree_last_leaves,
     lib,
     m_step,
     m_step_hist,

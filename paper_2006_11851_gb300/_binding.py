@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-MODES = {"exact": 0, "f16": 1, "fp8": 2, "proposal": 3}  # pts_mode
+MODES = {"exact": 0, "f16": 1, "fp8": 2, "proposal": 3, "kmtree": 4}  # pts_mode
 
 _LOCK = threading.Lock()
 _LIB = None
@@ -87,6 +87,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.synthesize_level_hist.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _I, _vp, _vp]
         L.m_step_hist.argtypes = [_vp, _vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
         L.pts_histogram_match.argtypes = [_vp, _vp, _I, _I, _I, _vp]
+        L.pts_build_kmeans_tree.argtypes = [_vp, _I, _vp]
+        L.pts_kmtree_info.argtypes = [_vp, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+        L.pts_kmtree_export.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.pts_kmtree_last_leaves.argtypes = [_vp, _vp, _I, _vp]
         L.synthesize_level_converge.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _I, _vp,
                                                 ctypes.POINTER(_I), _vp]
         L.pts_downsample2.argtypes = [_vp, _I, _I, _vp, _vp]
@@ -414,3 +418,35 @@ def fp32_fma_peak(iters: int = 20000, reps: int = 5) -> tuple[float, float]:
     tf, ms = _Dd(), _Dd()
     _check(lib().pts_fp32_fma_peak(int(iters), int(reps), _stream(), ctypes.byref(tf), ctypes.byref(ms)))
     return tf.value, ms.value
+
+
+def build_kmeans_tree(index: ExemplarIndex, iters: int = 10) -> dict:
+    """Builds the k = 4 hierarchical k-means tree of mode "kmtree"; returns its shape."""
+    _check(lib().pts_build_kmeans_tree(index.handle, int(iters), _stream()))
+    return kmtree_info(index)
+
+
+def kmtree_info(index: ExemplarIndex) -> dict:
+    a, b, c = _I(), _I(), _I()
+    _check(lib().pts_kmtree_info(index.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"internal": a.value, "leaves": b.value, "depth": c.value}
+
+
+def kmtree_export(index: ExemplarIndex) -> dict:
+    """The tree as numpy arrays: child [internal, 4], leaf_begin, leaf_end, perm, cent [internal, 4, d]."""
+    info = kmtree_info(index)
+    ni, nl, d, N = info["internal"], info["leaves"], index.d, index.info["N"]
+    child = np.zeros((ni, 4), dtype=np.int32)
+    lb, le = np.zeros(nl, dtype=np.int32), np.zeros(nl, dtype=np.int32)
+    perm = np.zeros(N, dtype=np.int32)
+    cent = np.zeros((ni, 4, d), dtype=np.float32)
+    _check(lib().pts_kmtree_export(index.handle, child.ctypes.data_as(ctypes.c_void_p), lb.ctypes.data_as(ctypes.c_void_p),
+                                   le.ctypes.data_as(ctypes.c_void_p), perm.ctypes.data_as(ctypes.c_void_p),
+                                   cent.ctypes.data_as(ctypes.c_void_p), _stream()))
+    return {"child": child, "leaf_begin": lb, "leaf_end": le, "perm": perm, "cent": cent}
+
+
+def kmtree_last_leaves(index: ExemplarIndex, Q: int) -> np.ndarray:
+    out = np.zeros(Q, dtype=np.int32)
+    _check(lib().pts_kmtree_last_leaves(index.handle, out.ctypes.data_as(ctypes.c_void_p), int(Q), _stream()))
+    return out

@@ -173,6 +173,23 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     return PTS_OK;
 }
 
+// the paper's k-means tree: descent to a leaf, exact re-rank of its windows
+pts_status search_kmtree(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q, int32_t *nn_out,
+                         float *d2_out, cudaStream_t st) {
+    KmTree &tr = idx->tree;
+    if (!tr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no k-means tree built on this index");
+    Workspace &ws = idx->ws;
+    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
+                   ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
+    PTS_TRY(tr.leaf_of_query.ensure((size_t)std::max(Q, 1), "tree leaves of the queries"));
+    launch_tree_search(tr, ws.qcoord.ptr, idx->da, Q, ws.cand_idx.ptr, ws.cand_lb.ptr, tr.leaf_of_query.ptr, st);
+    const int qx = (Wo - idx->w) / stride + 1;
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
+    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
+                  ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
+    return PTS_OK;
+}
+
 // the E-step in exact mode (see include/pts.h)
 pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q,
                         int32_t *nn_out, float *d2_out, cudaStream_t st) {
@@ -256,6 +273,9 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
         }
         case PTS_PROPOSAL:
             PTS_TRY(search_proposal(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
+            break;
+        case PTS_KMTREE:
+            PTS_TRY(search_kmtree(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
             break;
         case PTS_FP8_RERANK: {
             // FP8 E4M3 operands with per-dimension scales (the epilogue adds the FP32 norms); the
@@ -533,6 +553,10 @@ void pts_index_destroy(pts_index idx) {
         pr.infer.wp2.release();
         pr.infer.wp3.release();
         pr.infer.b3p.release();
+        KmTree &tr = idx->tree;
+        for (auto *b : {&tr.child, &tr.leaf_begin, &tr.leaf_end, &tr.perm, &tr.tmp, &tr.leaf_of_query}) b->release();
+        tr.cent.release();
+        tr.label.release();
         MlpState &m = pr.mlp;
         for (auto *b : {&m.params, &m.grads, &m.adam_m, &m.adam_v, &m.a1, &m.a2, &m.z, &m.dh, &m.loss}) b->release();
         for (auto *b : {&m.wb, &m.wt, &m.xb, &m.xt, &m.h1b, &m.h1t, &m.h2b, &m.h2t, &m.dzb, &m.dzt, &m.dab, &m.dat})
@@ -564,6 +588,51 @@ pts_status pts_index_get_info(pts_index idx, pts_index_info *info) {
 pts_status pts_index_set_tc_parts(pts_index idx, int parts) {
     if (!idx || parts < 0) return set_error(PTS_ERR_INVALID_ARG, "pts_index_set_tc_parts: null index or parts < 0");
     idx->tc_parts_override = parts;
+    return PTS_OK;
+}
+
+pts_status pts_build_kmeans_tree(pts_index idx, int iters, void *stream) {
+    if (!idx || iters < 1 || iters > 100)
+        return set_error(PTS_ERR_INVALID_ARG, "pts_build_kmeans_tree: null index or iters outside 1..100");
+    idx->tree.ready = 0;
+    return build_kmtree(idx->tree, idx->et_rows.ptr, idx->N, idx->da, idx->d, iters, as_stream(stream));
+}
+
+pts_status pts_kmtree_info(pts_index idx, int *n_internal, int *n_leaves, int *depth) {
+    if (!idx || !idx->tree.ready) return set_error(PTS_ERR_INVALID_ARG, "pts_kmtree_info: no k-means tree built");
+    if (n_internal) *n_internal = idx->tree.n_internal;
+    if (n_leaves) *n_leaves = idx->tree.n_leaves;
+    if (depth) *depth = idx->tree.depth;
+    return PTS_OK;
+}
+
+pts_status pts_kmtree_export(pts_index idx, int *child, int *leaf_begin, int *leaf_end, int *perm, float *cent,
+                             void *stream) {
+    if (!idx || !idx->tree.ready) return set_error(PTS_ERR_INVALID_ARG, "pts_kmtree_export: no k-means tree built");
+    const KmTree &tr = idx->tree;
+    cudaStream_t st = as_stream(stream);
+    if (child)
+        PTS_CUDA_TRY(cudaMemcpyAsync(child, tr.child.ptr, sizeof(int) * 4 * tr.n_internal, cudaMemcpyDeviceToHost, st));
+    if (leaf_begin)
+        PTS_CUDA_TRY(cudaMemcpyAsync(leaf_begin, tr.leaf_begin.ptr, sizeof(int) * tr.n_leaves, cudaMemcpyDeviceToHost,
+                                     st));
+    if (leaf_end)
+        PTS_CUDA_TRY(cudaMemcpyAsync(leaf_end, tr.leaf_end.ptr, sizeof(int) * tr.n_leaves, cudaMemcpyDeviceToHost, st));
+    if (perm) PTS_CUDA_TRY(cudaMemcpyAsync(perm, tr.perm.ptr, sizeof(int) * tr.N, cudaMemcpyDeviceToHost, st));
+    if (cent)
+        PTS_CUDA_TRY(cudaMemcpyAsync(cent, tr.cent.ptr, sizeof(float) * 4 * (size_t)tr.n_internal * tr.d,
+                                     cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    return PTS_OK;
+}
+
+pts_status pts_kmtree_last_leaves(pts_index idx, int *leaves, int Q, void *stream) {
+    if (!idx || !leaves || Q < 0) return set_error(PTS_ERR_INVALID_ARG, "pts_kmtree_last_leaves: bad argument");
+    if (!idx->tree.ready || idx->tree.leaf_of_query.count < (size_t)Q)
+        return set_error(PTS_ERR_INVALID_ARG, "pts_kmtree_last_leaves: no tree search of that size");
+    cudaStream_t st = as_stream(stream);
+    PTS_CUDA_TRY(cudaMemcpyAsync(leaves, idx->tree.leaf_of_query.ptr, sizeof(int) * Q, cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
     return PTS_OK;
 }
 

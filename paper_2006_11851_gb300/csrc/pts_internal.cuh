@@ -137,6 +137,18 @@ struct MlpInfer {  // packed weights of the fused inference kernel (mlp_infer.cu
     const float *b1 = nullptr, *b2 = nullptr;
 };
 
+// the paper's hierarchical k-means tree (k = 4), kmtree.cu
+struct KmTree {
+    DevBuf<float> cent;          // [internal][4][d] child centroids
+    DevBuf<int> child;           // [internal][4]: >= 0 internal, <= -2 leaf -c - 2, -1 none
+    DevBuf<int> leaf_begin, leaf_end;  // ranges in perm
+    DevBuf<int> perm;            // windows in leaf order
+    DevBuf<int> tmp;             // build scratch
+    DevBuf<unsigned char> label; // build scratch
+    DevBuf<int> leaf_of_query;   // [Q] the leaf each query reached (last search)
+    int n_internal = 0, n_leaves = 0, depth = 0, d = 0, N = 0, ready = 0;
+};
+
 struct ProposalState {
     int ready = 0, C = 0;
     float factor = 1.2f;
@@ -192,6 +204,7 @@ struct pts_index_s {
     int last_mode = 0;
     int tc_parts_override = 0;  // exemplar split of the tensor-core search chosen by the autotuner
     pts::ProposalState prop;
+    pts::KmTree tree;
 };
 
 namespace pts {
@@ -336,6 +349,10 @@ struct ProfScope {
 // mstep.cu
 void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st);
 void launch_count_diff(const int *a, const int *b, int n, unsigned int *count, cudaStream_t st);
+// kmtree.cu (section 2.2's k-means tree)
+pts_status build_kmtree(KmTree &tr, const float *rows, int N, int da, int d, int iters, cudaStream_t st);
+void launch_tree_search(const KmTree &tr, const float *qcoord, int da_q, int Q, int *cand_idx, float *cand_lb,
+                        int *leaf_out, cudaStream_t st);
 // histogram.cu (section 3, Eq. 9)
 constexpr int kMaxHistBins = 256;
 // bin of a channel value: clamped to [0, 1], times nbins in FP32, floored, capped at the last bin

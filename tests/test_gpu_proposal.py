@@ -190,3 +190,27 @@ def test_fallback_equals_tensor_core_search():
         assert torch.equal(nn_p[pos], nn_f[pos])
     finally:
         pidx.close()
+
+
+def test_network_gains_over_the_papers_tree(trained):
+    """What the trained network buys over the search it replaces, the k = 4 k-means tree of
+    section 2.2 with greedy descent, on the same mid-synthesis image: the share of queries given
+    the exact nearest window, and the matched energy against exact search's."""
+    pidx, init, _ = trained
+    ix = pidx.indices[1]
+    pts.build_kmeans_tree(ix, 10)
+    X = init(24)
+    pts.synthesize_level(pidx.indices[0], X, 5, mode="exact")
+    X = pts.upsample2(X)
+    pts.synthesize_level(ix, X, 2, mode="exact")
+    nn_e, d2_e = pts.nn_search(ix, X, 2, "exact")
+    nn_p, d2_p = pts.nn_search(ix, X, 2, "proposal")
+    nn_t, d2_t = pts.nn_search(ix, X, 2, "kmtree")
+    rec_p = float((nn_p == nn_e).float().mean())
+    rec_t = float((nn_t == nn_e).float().mean())
+    e_p = float(d2_p.double().sum() / d2_e.double().sum())
+    e_t = float(d2_t.double().sum() / d2_e.double().sum())
+    print(f"recall@1: proposal {rec_p:.4f}, tree {rec_t:.4f}; matched energy / exact: proposal {e_p:.4f}, "
+          f"tree {e_t:.4f}")
+    assert rec_p > rec_t + 0.1
+    assert e_p < e_t
