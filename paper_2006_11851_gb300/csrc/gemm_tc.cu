@@ -162,12 +162,8 @@ __global__ void k_f32_to_bf16(const float *__restrict__ in, long n, __nv_bfloat1
 void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
                       const float *bias, int gelu, float *Cf, __nv_bfloat16 *Cb, float *Cpre, int ldc, int *status,
                       cudaStream_t st) {
-    static bool attr = false;
     const size_t smem = sizeof(GemmSmem) + 128;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_gemm_bf16), (int)smem);
     dim3 grid(ceil_div(N, kGN), ceil_div(M, kGM));
     ProfScope ps(kProfMlp, st, 1);
     k_gemm_bf16<<<grid, kGThreads, smem, st>>>(M, N, K, A, lda, B, ldb, bias, gelu, Cf, Cb, Cpre, ldc, status);

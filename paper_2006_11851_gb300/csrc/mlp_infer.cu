@@ -302,12 +302,8 @@ pts_status mlp_pack_infer(MlpState &s, MlpInfer &f, cudaStream_t st) {
 void launch_mlp_top4(const MlpInfer &f, const float *qcoord, int Q, int d, int ldq, int *top, int *status,
                      cudaStream_t st) {
     if (Q <= 0) return;
-    static bool attr = false;
     const size_t smem = sizeof(InferSmem) + 1024;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_mlp_infer), (int)smem);
     ProfScope ps(kProfMlp, st, 1);
     k_mlp_infer<<<ceil_div(Q, kIM), kIThreads, smem, st>>>(qcoord, Q, std::min(d, 64), ldq, f.wp1.ptr, f.b1, f.wp2.ptr, f.b2,
                                                      f.wp3.ptr, f.b3p.ptr, f.nchunk, top, status);

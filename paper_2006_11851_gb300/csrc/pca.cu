@@ -461,14 +461,8 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
 
     const size_t jac_smem = big ? 0 : sizeof(double) * 2 * m * m;
     const size_t chol_smem = big ? 0 : sizeof(double) * m * m;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * 2 * kMaxM * kMaxM));
-        cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * kMaxM * kMaxM));
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_jacobi_small), (int)(sizeof(double) * 2 * kMaxM * kMaxM));
+    set_smem_attr(reinterpret_cast<const void *>(k_chol), (int)(sizeof(double) * kMaxM * kMaxM));
 
     count_launches(1);
     k_win_mean<<<D, 256, 0, st>>>(exemplar, We, w, ex, N, mu64);

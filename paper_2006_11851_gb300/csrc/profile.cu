@@ -66,6 +66,22 @@ __global__ void __launch_bounds__(1024, 2) k_fma_peak(int iters, float a, float 
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+void set_smem_attr(const void *kernel, int bytes) {
+    struct Done {
+        const void *kernel;
+        int device, bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Done> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Done &d : done)
+        if (d.kernel == kernel && d.device == dev && d.bytes >= bytes) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done.push_back({kernel, dev, bytes});
+}
+
 // Event timing is switched off while a CUDA graph is being captured (an event recorded into a
 // capture would become a graph node, not a timing point); on = true restores the previous state.
 void prof_suspend(bool on) {

@@ -319,12 +319,8 @@ void launch_project(const float *img, int H, int W, int w, int stride, const flo
     nsplit = ceil_div(D, kper);
     const dim3 grid((unsigned)nblk, nsplit);
     float *part = nsplit > 1 ? scratch->ptr : nullptr;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_project<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ProjSmem<64>));
-        cudaFuncSetAttribute(k_project<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ProjSmem<128>));
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_project<64>), (int)sizeof(ProjSmem<64>));
+    set_smem_attr(reinterpret_cast<const void *>(k_project<128>), (int)sizeof(ProjSmem<128>));
     if (PDc == 64)
         k_project<64><<<grid, 256, sizeof(ProjSmem<64>), st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basisT, kper, o,
                                                                part);

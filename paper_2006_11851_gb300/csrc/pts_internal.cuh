@@ -334,6 +334,9 @@ void launch_resolve(const int *fail_list, const unsigned int *fail_count,
 enum ProfClass { kProfSearchTopk = 0, kProfSearchFull, kProfRerank, kProfProject, kProfMStep,
                  kProfSearchTc, kProfMlp, kProfProbe, kProfBrute, kProfIrls, kProfSearchTcList, kProfClasses };
 void count_launches(int n);
+// Raises a kernel's dynamic shared-memory limit on the current device (once per kernel, device
+// and size; thread-safe).
+void set_smem_attr(const void *kernel, int bytes);
 void prof_begin(int cls, cudaStream_t st, void **token);
 void prof_end(int cls, cudaStream_t st, void *token);
 struct ProfScope {

@@ -590,12 +590,8 @@ int pca_parts(int Q, int ntiles) {
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st, int nparts, float *part_v, int *part_i, const float *thr_init) {
-    static bool attr = false;
     const size_t smem = sizeof(PcaSmem);
-    if (!attr) {
-        cudaFuncSetAttribute(k_search_pca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_search_pca), (int)smem);
     const int grid = ceil_div(Q, kBQ);
     if (grid == 0) return;
     if (!part_v || !part_i) nparts = 1;
@@ -614,12 +610,8 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                         int nparts, int *status, cudaStream_t st, int N, DevBuf<float> *pdist) {
-    static bool attr = false;
     const size_t smem = sizeof(FullSmem);
-    if (!attr) {
-        cudaFuncSetAttribute(k_search_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_search_full), (int)smem);
     const int Dp = padded_dim(w);
     count_launches(1);
     k_gather_full<<<152 * 4, 256, 0, st>>>(X, Wo, w, stride, qx, mu, fail_list, fail_count, Q, Dp,

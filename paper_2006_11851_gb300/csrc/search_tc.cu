@@ -1091,12 +1091,8 @@ void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float
     k_ivf_scatter<<<nchunk, 1024, 0, st>>>(top, Q, C, b.cursor, b.pair_q, b.pair_r);
     k_pack_queries_ivf<<<maxb, 256, 0, st>>>(qcoord, d, da, K, b.blk, b.nblk, b.pair_q, b.qtile);
     // every (query, probe) pair has a row in some block, so every kept record is written
-    static bool attr = false;
     const size_t smem = sizeof(TcSmem) + 1024;
-    if (!attr) {
-        cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_smem_attr(reinterpret_cast<const void *>(k_search_tc<2>), (int)smem);
     const int nstages = std::min(kMaxStages, kRing / (kTN * K * 2));
     {
         ProfScope ps(kProfProbe, st, 1);
@@ -1124,15 +1120,11 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
                       int nparts, const float *thr0, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                       int *status, cudaStream_t st, const int *qlist, const unsigned int *qcount, int fp8,
                       const float *qscale, const float *enorm, int N, void *kept_buf) {
-    static bool attr[2] = {false, false};
     const size_t smem = sizeof(TcSmem) + 1024;
-    if (!attr[fp8 ? 1 : 0]) {
-        if (fp8)
-            cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        else
-            cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr[fp8 ? 1 : 0] = true;
-    }
+    if (fp8)
+        set_smem_attr(reinterpret_cast<const void *>(k_search_tc<1>), (int)smem);
+    else
+        set_smem_attr(reinterpret_cast<const void *>(k_search_tc<2>), (int)smem);
     // a listed search runs unsplit: the proposal's fallback lists about a third of the fine
     // level's queries, enough blocks to fill the SMs, and a split measured slower there
     if (qlist) nparts = 1;

@@ -275,6 +275,38 @@ def test_invalid_arguments(c1):
         pts.ExemplarIndex(_t(Z[:6, :6]), 8)
     with pytest.raises(pts.PtsError):
         pts.pca_fit(_t(Z), 8, 129)
+    X = torch.zeros(128, 128, 3, device=DEV)
+    Q = idx.num_queries(128, 128, 2)
+    nn = torch.zeros(Q, dtype=torch.int32, device=DEV)
+    with pytest.raises(pts.PtsError):
+        pts.m_step_hist(idx, nn, None, X, 1)          # nbins outside 2..256
+    with pytest.raises(pts.PtsError):
+        pts.histogram_match(idx, X.clone(), 300)
+    with pytest.raises(pts.PtsError):
+        pts.synthesize_level(idx, X.clone(), 1, hist_bins=1)
+    with pytest.raises(pts.PtsError):
+        pts.synthesize_level_converge(idx, X.clone(), -1)
+    with pytest.raises(pts.PtsError):
+        pts.build_kmeans_tree(idx, 0)                 # Lloyd iterations outside 1..100
+    fresh = pts.ExemplarIndex(_t(Z), 8, d=24)
+    with pytest.raises(pts.PtsError):
+        pts.nn_search(fresh, X, 2, "kmtree")          # no tree built
+    with pytest.raises(pts.PtsError):
+        pts.nn_search(fresh, X, 2, "proposal")        # no proposal trained
+    fresh.close()
+
+
+def test_tree_on_a_two_window_exemplar():
+    """N = 2 windows (fewer than k = 4): the tree is one leaf, so its search is exact."""
+    Z = P.synthetic_exemplar(12, 9, 1.0)[:, :8]          # 9 x 8 exemplar, w = 8: windows at y = 0, 1
+    idx = pts.ExemplarIndex(_t(Z), 8, d=4)
+    info = pts.build_kmeans_tree(idx, 5)
+    assert info["leaves"] == 1
+    X = P.random_patch_init(Z, 16, 16, 8, 1)
+    nn_t, d2_t = pts.nn_search(idx, _t(X), 2, "kmtree")
+    nn_e, d2_e = pts.nn_search(idx, _t(X), 2, "exact")
+    assert torch.equal(nn_t, nn_e) and torch.equal(d2_t, d2_e)
+    idx.close()
 
 
 def test_index_destroy_returns_device_memory():
