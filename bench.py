@@ -65,6 +65,21 @@ def level_sizes(cfg=WORKLOAD):
     return out
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Units processed by all ranks (each the same share: weak scaling) per second of the slowest."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def queries_per_step(cfg=WORKLOAD):
     return sum(l["Q"] for l in level_sizes(cfg)) * (cfg["iters"] + 1)
 
@@ -354,28 +369,24 @@ def main():
                 if n.value:
                     kern[name] = {"ms_per_step": ms.value / args.steps, "launches_per_step": n.value / args.steps}
             L.pts_profile_enable(0)
-        total_ms = sum(times)
-        if dist:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = t.item()
+        total_ms = max_over_ranks(sum(times), dist, dev)
         energies = [exact_energy(X) for X in finals]
         timed_run.last_stats = last_stats
         return total_ms, launches, kern, energies, clk.summary()
 
     total_ms, launches, kern, energies, clocks = timed_run(modes, True)
-    qps = queries_per_step(cfg) * args.steps * world / (total_ms / 1000.0)
+    qps = whole_job_rate(queries_per_step(cfg) * args.steps, world, total_ms)
     if args.mode == "exact":
         ex_ms, ex_kern, ex_energies = total_ms, kern, energies
     else:
         ex_ms, _, ex_kern, ex_energies, _ = timed_run(LEVEL_MODES["exact"], True)
-    exact_qps = queries_per_step(cfg) * args.steps * world / (ex_ms / 1000.0)
+    exact_qps = whole_job_rate(queries_per_step(cfg) * args.steps, world, ex_ms)
     ratios = [e / x for e, x in zip(energies, ex_energies)]
     other = {}
     if also:
         a_ms, _, _, a_energies, _ = timed_run(LEVEL_MODES[also], False)
         a_stats = timed_run.last_stats
-        a_qps = queries_per_step(cfg) * args.steps * world / (a_ms / 1000.0)
+        a_qps = whole_job_rate(queries_per_step(cfg) * args.steps, world, a_ms)
         a_ratios = [e / x for e, x in zip(a_energies, ex_energies)]
         other[also] = {"level_modes": LEVEL_MODES[also], "value": a_qps, "ms_per_step": a_ms / args.steps,
                        "speedup_vs_exact": a_qps / exact_qps,
@@ -403,11 +414,8 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         e2e_ms += ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
-    e2e_qps = queries_per_step(cfg) * args.steps * world / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e_qps = whole_job_rate(queries_per_step(cfg) * args.steps, world, e2e_ms)
 
     # ---- the exact FP32 arm against the FP32 SIMT pipe (FMA rate measured here, this GPU) ----
     fma_tf, _ = pts.fp32_fma_peak()
