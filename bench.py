@@ -229,9 +229,10 @@ PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 /
 
 # DRAM bytes (read + write) of one fine-level k_search_tc launch (Q = 64,009, N = 62,001) from the
 # ncu capture summarised in profiles/k_search_tc_fine_level_512_f16.md; reported only while the
-# search source is the one the counters were taken on.
+# search source file is unchanged (the digest below is of that file with the profiled kernel; any
+# later edit of the file, even of host code, turns the figure off until it is checked again).
 TC_TRAFFIC_BYTES = 32.895e6 + 0.016e6
-TC_TRAFFIC_SHA256 = "b7fcd083d0f889cf0e3f39b24886c7b4457d8f13d3a86f31190cccb212c53c41"
+TC_TRAFFIC_SHA256 = "4b5499d4d88b59aebde481e9e069bb86098a30e2aeda747b742473846ff456c5"
 
 
 def _tc_traffic():
