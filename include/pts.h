@@ -351,6 +351,16 @@ pts_status synthesize_level(pts_index index, float *output, int Ho, int Wo, int 
                             float r, float delta, int mode, double *energy_out, void *stream);
 
 /*
+ * synthesize_level_async -- synthesize_level without its closing synchronisation, so that a
+ * caller can queue several levels (or jobs) back to back: the energies go to energy_dev
+ * (DEVICE, iters + 1 float64) and an error a kernel raises stays in the index's device status
+ * word until pts_index_device_status reads it.  Host-side argument errors return at once.  The
+ * first call on a new grid size may still synchronise (it sizes the workspace).
+ */
+pts_status synthesize_level_async(pts_index index, float *output, int Ho, int Wo, int stride, int iters,
+                                  float r, float delta, int mode, double *energy_dev, void *stream);
+
+/*
  * Histogram matching (section 3, Eq. 9; the last step of the synthesis
  * procedure, section 4).  Histograms: one per colour channel, nbins equal bins
  * over [0, 1] (2 <= nbins <= 256), as fractions of the image's pixels; a value's

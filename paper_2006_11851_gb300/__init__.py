@@ -32,6 +32,7 @@ from ._binding import (  # noqa: F401
     proposal_info,
     proposal_top4,
     synthesize_level,
+    synthesize_level_async,
     synthesize_level_converge,
     train_proposal,
     upsample2,

@@ -85,6 +85,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.m_step.argtypes = [_vp, _vp, _vp, _I, _I, _I, _vp, _vp]
         L.synthesize_level.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _vp, _vp]
         L.synthesize_level_hist.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _I, _vp, _vp]
+        L.synthesize_level_async.argtypes = [_vp, _vp, _I, _I, _I, _I, _F, _F, _I, _vp, _vp]
         L.m_step_hist.argtypes = [_vp, _vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
         L.pts_histogram_match.argtypes = [_vp, _vp, _I, _I, _I, _vp]
         L.pts_build_kmeans_tree.argtypes = [_vp, _I, _vp]
@@ -273,6 +274,21 @@ def synthesize_level(index: ExemplarIndex, output: torch.Tensor, iters: int, r: 
         _check(lib().synthesize_level(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta,
                                       _mode(mode), E.ctypes.data_as(ctypes.c_void_p), _stream()))
     return E
+
+
+def synthesize_level_async(index: ExemplarIndex, output: torch.Tensor, iters: int, r: float = 2.0,
+                           delta: float = 1e-3, mode="exact", stride: int = 2,
+                           energy: torch.Tensor | None = None) -> torch.Tensor:
+    """synthesize_level without the closing synchronisation: returns the iters + 1 energies as a
+    device float64 tensor; kernel errors wait in the device status (index.device_status())."""
+    _need(output, torch.float32, "output")
+    Ho, Wo, _ = output.shape
+    if energy is None:
+        energy = torch.empty(iters + 1, device=output.device, dtype=torch.float64)
+    _need(energy, torch.float64, "energy", (iters + 1,))
+    _check(lib().synthesize_level_async(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta, _mode(mode),
+                                        _ptr(energy), _stream()))
+    return energy
 
 
 def synthesize_level_converge(index: ExemplarIndex, output: torch.Tensor, max_iters: int, r: float = 0.8,

@@ -737,7 +737,7 @@ pts_status pts_histogram_match(pts_index idx, float *image, int H, int W, int nb
 // the EM loop of synthesize_level; nbins > 0 takes the M-step of m_step_hist
 static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r,
                                   float delta, int mode, int nbins, double *energy_out, void *stream,
-                                  const char *name) {
+                                  const char *name, double *energy_dev = nullptr) {
     if (!idx || !output || !energy_out) return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": null pointer");
     if (iters < 0) return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": iters < 0");
     if (!(r > 0.0f && r <= 2.0f) || !(delta > 0.0f))
@@ -750,6 +750,7 @@ static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, 
     PTS_TRY(ensure_workspace(idx, Q));
     Workspace &ws = idx->ws;
     PTS_TRY(ws.energy.ensure(iters + 1, "energies"));
+    double *energy = energy_dev ? energy_dev : ws.energy.ptr;
     unsigned int *cx = nullptr, *cz = nullptr;
     const long nx = (long)Ho * Wo, nz = (long)idx->He * idx->We;
     if (nbins) {
@@ -760,8 +761,7 @@ static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, 
     }
     for (int t = 0; t <= iters; ++t) {
         PTS_TRY(nn_search_impl(idx, output, Ho, Wo, stride, mode, ws.nn.ptr, ws.d2.ptr, st));
-        launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, ws.energy.ptr + t, ws.partial.ptr,
-                    ws.ticket.ptr, st);
+        launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, energy + t, ws.partial.ptr, ws.ticket.ptr, st);
         if (t == iters) break;
         if (nbins) {
             launch_hist3(output, nx, nbins, cx, st);  // of the image the E-step matched
@@ -773,10 +773,18 @@ static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, 
         }
     }
     PTS_CUDA_TRY(cudaGetLastError());
+    if (energy_dev) return PTS_OK;  // asynchronous: the caller reads the device status later
     PTS_CUDA_TRY(cudaMemcpyAsync(energy_out, ws.energy.ptr, sizeof(double) * (iters + 1),
                                  cudaMemcpyDeviceToHost, st));
     PTS_CUDA_TRY(cudaStreamSynchronize(st));
     return read_status(idx, st);
+}
+
+pts_status synthesize_level_async(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r,
+                                  float delta, int mode, double *energy_dev, void *stream) {
+    if (!energy_dev) return set_error(PTS_ERR_INVALID_ARG, "synthesize_level_async: null pointer");
+    return synthesize_impl(idx, output, Ho, Wo, stride, iters, r, delta, mode, 0, energy_dev, stream,
+                           "synthesize_level_async", energy_dev);
 }
 
 pts_status synthesize_level(pts_index idx, float *output, int Ho, int Wo, int stride, int iters, float r, float delta,

@@ -7,7 +7,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from ._binding import ExemplarIndex, downsample2, histogram_match, synthesize_level, upsample2
+from ._binding import (ExemplarIndex, downsample2, histogram_match, synthesize_level, synthesize_level_async,
+                       upsample2)
 
 
 class PyramidIndex:
@@ -45,16 +46,26 @@ def synthesize_pyramid(pidx: PyramidIndex, init_coarse: torch.Tensor, iters: int
     images if keep_levels).  init_coarse is the initial image of level 0.
     """
     X = init_coarse.contiguous()
-    energies = np.zeros((pidx.levels, iters + 1))
     imgs = []
     modes = list(mode) if isinstance(mode, (list, tuple)) else [mode] * pidx.levels
+    if hist_bins:
+        energies = np.zeros((pidx.levels, iters + 1))
+    else:  # the levels are queued back to back; one synchronisation at the end
+        E = torch.empty(pidx.levels, iters + 1, device=X.device, dtype=torch.float64)
     for lev, ix in enumerate(pidx.indices):
-        energies[lev] = synthesize_level(ix, X, iters, r=r, delta=delta, mode=modes[lev], stride=stride,
-                                         hist_bins=hist_bins)
+        if hist_bins:
+            energies[lev] = synthesize_level(ix, X, iters, r=r, delta=delta, mode=modes[lev], stride=stride,
+                                             hist_bins=hist_bins)
+        else:
+            synthesize_level_async(ix, X, iters, r=r, delta=delta, mode=modes[lev], stride=stride, energy=E[lev])
         if keep_levels:
             imgs.append(X.clone())
         if lev + 1 < pidx.levels:
             X = upsample2(X)
     if hist_bins:
         histogram_match(pidx.indices[-1], X, hist_bins)
+    else:
+        energies = E.cpu().numpy()
+        for ix in pidx.indices:
+            ix.device_status()  # a kernel's error surfaces here
     return X, energies, imgs
