@@ -56,6 +56,25 @@ def test_bad_arguments_rejected_on_host(libpts):
     libpts.synthesize_level.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 4 + \
         [ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     assert libpts.synthesize_level(None, None, 16, 16, 2, 1, 2.0, 1e-3, 0, None, None) == -1
+    vp, i, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    libpts.synthesize_level_async.argtypes = [vp, vp, i, i, i, i, f, f, i, vp, vp]
+    assert libpts.synthesize_level_async(None, None, 16, 16, 2, 1, 2.0, 1e-3, 0, None, None) == -1
+    libpts.synthesize_level_hist.argtypes = [vp, vp, i, i, i, i, f, f, i, i, vp, vp]
+    assert libpts.synthesize_level_hist(None, None, 16, 16, 2, 1, 2.0, 1e-3, 0, 32, None, None) == -1
+    libpts.synthesize_level_converge.argtypes = [vp, vp, i, i, i, i, f, f, i, i, vp, vp, vp]
+    assert libpts.synthesize_level_converge(None, None, 16, 16, 2, 5, 0.8, 1e-3, 0, 0, None, None, None) == -1
+    libpts.m_step_hist.argtypes = [vp, vp, vp, i, i, i, i, vp, vp, vp]
+    assert libpts.m_step_hist(None, None, None, 16, 16, 2, 32, None, None, None) == -1
+    libpts.pts_histogram_match.argtypes = [vp, vp, i, i, i, vp]
+    assert libpts.pts_histogram_match(None, None, 16, 16, 32, None) == -1
+    libpts.pts_build_kmeans_tree.argtypes = [vp, i, vp]
+    assert libpts.pts_build_kmeans_tree(None, 10, None) == -1
+    libpts.pts_kmtree_info.argtypes = [vp, vp, vp, vp]
+    assert libpts.pts_kmtree_info(None, None, None, None) == -1
+    libpts.pts_index_set_tc_parts.argtypes = [vp, i]
+    assert libpts.pts_index_set_tc_parts(None, 1) == -1
+    libpts.pts_fp32_fma_peak.argtypes = [i, i, vp, vp, vp]
+    assert libpts.pts_fp32_fma_peak(0, 1, None, None, None) == -1
 
 
 def test_python_binding_fails_loudly_without_gpu():
