@@ -7,8 +7,11 @@ does, and nothing here imports the product package.
 
 The arithmetic lives in ``pts_oracle.c`` (plain C, FP64, OpenMP only across
 independent queries/rows); this module builds it with gcc on first use and
-marshals numpy arrays.  Histogram matching (section 3, Eq. 9) is plain numpy in
-``histogram.py``.  The EM driver below follows the paper's two phases
+marshals numpy arrays.  Images are H x W x C with C = 3 (RGB) or 4 (RGBS: the
+scale map of section 1 as a fourth channel); the channel count comes from the
+image's shape.  Histogram matching (section 3, Eq. 9) is plain numpy in
+``histogram.py``, the scale map (Eqs. 1-3) and its use in synthesis in
+``scale.py``, the k-means tree checks in ``kmtree.py``.  The EM driver below follows the paper's two phases
 (section 2.1: search phase, then optimization phase, repeated).
 """
 from __future__ import annotations
@@ -65,19 +68,19 @@ _D = ctypes.c_double
 def _declare(L: ctypes.CDLL) -> None:
     L.or_max_threads.argtypes = [_I]
     L.or_max_threads.restype = _I
-    L.or_nn_bruteforce.argtypes = [_d, _I, _I, _d, _I, _I, _I, _I, _i32, _I, _i32, _d, _I]
-    L.or_pair_dist2.argtypes = [_d, _I, _I, _d, _I, _I, _I, _I, _i32, _i32, _I, _d]
-    L.or_window_mean.argtypes = [_d, _I, _I, _I, _d]
-    L.or_window_cov.argtypes = [_d, _I, _I, _I, _d, _d, _I]
+    L.or_nn_bruteforce.argtypes = [_d, _I, _I, _d, _I, _I, _I, _I, _I, _i32, _I, _i32, _d, _I]
+    L.or_pair_dist2.argtypes = [_d, _I, _I, _d, _I, _I, _I, _I, _I, _i32, _i32, _I, _d]
+    L.or_window_mean.argtypes = [_d, _I, _I, _I, _I, _d]
+    L.or_window_cov.argtypes = [_d, _I, _I, _I, _I, _d, _d, _I]
     L.or_jacobi_eigh.argtypes = [_d, _I, _d, _d, _I]
     L.or_jacobi_eigh.restype = _I
-    L.or_pca_fit.argtypes = [_d, _I, _I, _I, _I, _d, _d, _d, _I]
+    L.or_pca_fit.argtypes = [_d, _I, _I, _I, _I, _I, _d, _d, _d, _I]
     L.or_pca_fit.restype = _I
-    L.or_project.argtypes = [_d, _I, _I, _I, _I, _d, _d, _I, _i32, _I, _d, _d, _d]
+    L.or_project.argtypes = [_d, _I, _I, _I, _I, _I, _d, _d, _I, _i32, _I, _d, _d, _d]
     L.or_irls.argtypes = [_d, _I, _D, _D, _d, _d, _d]
-    L.or_m_step.argtypes = [_i32, _d, _d, _I, _I, _I, _I, _I, _I, _d]
-    L.or_downsample2.argtypes = [_d, _I, _I, _d]
-    L.or_upsample2.argtypes = [_d, _I, _I, _d]
+    L.or_m_step.argtypes = [_i32, _d, _d, _I, _I, _I, _I, _I, _I, _I, _d]
+    L.or_downsample2.argtypes = [_d, _I, _I, _I, _d]
+    L.or_upsample2.argtypes = [_d, _I, _I, _I, _d]
     if hasattr(L, "or_kmeans_assign"):
         _declare_learn(L)
 
@@ -102,6 +105,21 @@ def _f64(a) -> np.ndarray:
 
 def _i32a(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _image(a) -> np.ndarray:
+    """FP64 copy of an H x W x C image; C = 3 (RGB) or 4 (RGBS, section 3's scale channel)."""
+    a = _f64(a)
+    if a.ndim != 3 or a.shape[2] not in (3, 4):
+        raise ValueError(f"expected an H x W x 3 or H x W x 4 image, got shape {a.shape}")
+    return a
+
+
+def _same_channels(*imgs) -> int:
+    C = imgs[0].shape[2]
+    if any(im.shape[2] != C for im in imgs):
+        raise ValueError("images differ in their channel count")
+    return C
 
 
 def threads(n: int = 0) -> int:
@@ -133,7 +151,8 @@ def num_queries(Ho: int, Wo: int, w: int, stride: int = 2) -> int:
 # ---------------------------------------------------------------------------
 def nn_bruteforce(X, Z, w: int, stride: int = 2, qlist=None, nthreads: int = 0):
     """(nn int32, d2 float64) of the listed queries (all if qlist is None)."""
-    X, Z = _f64(X), _f64(Z)
+    X, Z = _image(X), _image(Z)
+    C = _same_channels(X, Z)
     Ho, Wo, _ = X.shape
     He, We, _ = Z.shape
     Q = num_queries(Ho, Wo, w, stride)
@@ -147,7 +166,7 @@ def nn_bruteforce(X, Z, w: int, stride: int = 2, qlist=None, nthreads: int = 0):
             raise ValueError("query index out of range")
     nn = np.empty(nq, np.int32)
     d2 = np.empty(nq, np.float64)
-    lib().or_nn_bruteforce(_p(X), Ho, Wo, _p(Z), He, We, w, stride,
+    lib().or_nn_bruteforce(_p(X), Ho, Wo, _p(Z), He, We, w, C, stride,
                            None if ql is None else _p(ql, ctypes.c_int32), nq,
                            _p(nn, ctypes.c_int32), _p(d2), int(nthreads))
     return nn, d2
@@ -155,7 +174,8 @@ def nn_bruteforce(X, Z, w: int, stride: int = 2, qlist=None, nthreads: int = 0):
 
 def pair_dist2(X, Z, w: int, stride: int, q, n) -> np.ndarray:
     """Full-dimension squared distance for each (query q[i], exemplar window n[i])."""
-    X, Z = _f64(X), _f64(Z)
+    X, Z = _image(X), _image(Z)
+    C = _same_channels(X, Z)
     q, n = _i32a(q), _i32a(n)
     Ho, Wo, _ = X.shape
     He, We, _ = Z.shape
@@ -164,7 +184,7 @@ def pair_dist2(X, Z, w: int, stride: int, q, n) -> np.ndarray:
     if len(q) != len(n) or (len(q) and (q.min() < 0 or q.max() >= Q or n.min() < 0 or n.max() >= N)):
         raise ValueError("bad pair list")
     out = np.empty(len(q), np.float64)
-    lib().or_pair_dist2(_p(X), Ho, Wo, _p(Z), He, We, w, stride, _p(q, ctypes.c_int32),
+    lib().or_pair_dist2(_p(X), Ho, Wo, _p(Z), He, We, w, C, stride, _p(q, ctypes.c_int32),
                         _p(n, ctypes.c_int32), len(q), _p(out))
     return out
 
@@ -173,21 +193,21 @@ def pair_dist2(X, Z, w: int, stride: int, q, n) -> np.ndarray:
 # PCA (section 2.2)
 # ---------------------------------------------------------------------------
 def window_mean(Z, w: int) -> np.ndarray:
-    Z = _f64(Z)
-    He, We, _ = Z.shape
+    Z = _image(Z)
+    He, We, C = Z.shape
     num_exemplar_windows(He, We, w)
-    mu = np.empty(3 * w * w)
-    lib().or_window_mean(_p(Z), He, We, w, _p(mu))
+    mu = np.empty(C * w * w)
+    lib().or_window_mean(_p(Z), He, We, w, C, _p(mu))
     return mu
 
 
 def window_cov(Z, w: int, nthreads: int = 0) -> np.ndarray:
-    Z = _f64(Z)
-    He, We, _ = Z.shape
+    Z = _image(Z)
+    He, We, C = Z.shape
     mu = window_mean(Z, w)
-    D = 3 * w * w
+    D = C * w * w
     cov = np.empty((D, D))
-    lib().or_window_cov(_p(Z), He, We, w, _p(mu), _p(cov), int(nthreads))
+    lib().or_window_cov(_p(Z), He, We, w, C, _p(mu), _p(cov), int(nthreads))
     return cov
 
 
@@ -203,25 +223,27 @@ def jacobi_eigh(A, nthreads: int = 0):
 
 def pca_fit(Z, w: int, d: int, nthreads: int = 0):
     """(mu[D], basis[d, D], eigenvalues[min(N, D)] descending, sweeps)."""
-    Z = _f64(Z)
-    He, We, _ = Z.shape
+    Z = _image(Z)
+    He, We, C = Z.shape
     N = num_exemplar_windows(He, We, w)
-    D = 3 * w * w
+    D = C * w * w
     if not 0 < d <= min(D, N):
         raise ValueError("bad d")
     mu = np.empty(D)
     basis = np.empty((d, D))
     ev = np.empty(min(N, D))
-    sweeps = lib().or_pca_fit(_p(Z), He, We, w, d, _p(mu), _p(basis), _p(ev), int(nthreads))
+    sweeps = lib().or_pca_fit(_p(Z), He, We, w, C, d, _p(mu), _p(basis), _p(ev), int(nthreads))
     return mu, basis, ev, sweeps
 
 
 def project(img, w: int, stride: int, mu, basis, lst=None):
     """(y [n, d], ||v - mu||^2 [n], residual norm [n]) of the listed windows."""
-    img, mu, basis = _f64(img), _f64(mu), _f64(basis)
-    H, W, _ = img.shape
+    img, mu, basis = _image(img), _f64(mu), _f64(basis)
+    H, W, C = img.shape
     total = np.prod(grid(H, W, w, stride))
     d = basis.shape[0]
+    if mu.shape != (C * w * w,) or basis.shape[1:] != (C * w * w,):
+        raise ValueError("mu / basis do not match the image's window dimension")
     if lst is None:
         lp, cnt = None, int(total)
     else:
@@ -230,7 +252,7 @@ def project(img, w: int, stride: int, mu, basis, lst=None):
     y = np.empty((cnt, d))
     un = np.empty(cnt)
     rs = np.empty(cnt)
-    lib().or_project(_p(img), H, W, w, stride, _p(mu), _p(basis), d, lp, cnt, _p(y), _p(un), _p(rs))
+    lib().or_project(_p(img), H, W, w, C, stride, _p(mu), _p(basis), d, lp, cnt, _p(y), _p(un), _p(rs))
     return y, un, rs
 
 
@@ -247,34 +269,37 @@ def irls(d2, r: float = 2.0, delta: float = 1e-3):
 
 
 def m_step(nn, Wt, Z, w: int, Ho: int, Wo: int, stride: int = 2, X_prev=None) -> np.ndarray:
-    """New output image (Ho x Wo x 3, float64) from matched windows and weights."""
-    Z = _f64(Z)
-    He, We, _ = Z.shape
+    """New output image (Ho x Wo x C, float64, C the exemplar's channels) from matched windows and
+    weights."""
+    Z = _image(Z)
+    He, We, C = Z.shape
     Q = num_queries(Ho, Wo, w, stride)
     N = num_exemplar_windows(He, We, w)
     nn = _i32a(nn)
     if nn.shape != (Q,) or (Q and (nn.min() < 0 or nn.max() >= N)):
         raise ValueError("bad nn")
-    X = np.zeros((Ho, Wo, 3)) if X_prev is None else _f64(X_prev).copy()
+    X = np.zeros((Ho, Wo, C)) if X_prev is None else _image(X_prev).copy()
+    if X.shape != (Ho, Wo, C):
+        raise ValueError("X_prev does not match the output size and the exemplar's channels")
     Wp = None if Wt is None else _f64(Wt)
-    lib().or_m_step(_p(nn, ctypes.c_int32), None if Wp is None else _p(Wp), _p(Z), He, We, w, Ho, Wo,
+    lib().or_m_step(_p(nn, ctypes.c_int32), None if Wp is None else _p(Wp), _p(Z), He, We, w, C, Ho, Wo,
                     stride, _p(X))
     return X
 
 
 def downsample2(img) -> np.ndarray:
-    img = _f64(img)
-    H, W, _ = img.shape
-    out = np.empty(((H + 1) // 2, (W + 1) // 2, 3))
-    lib().or_downsample2(_p(img), H, W, _p(out))
+    img = _image(img)
+    H, W, C = img.shape
+    out = np.empty(((H + 1) // 2, (W + 1) // 2, C))
+    lib().or_downsample2(_p(img), H, W, C, _p(out))
     return out
 
 
 def upsample2(img) -> np.ndarray:
-    img = _f64(img)
-    H, W, _ = img.shape
-    out = np.empty((2 * H, 2 * W, 3))
-    lib().or_upsample2(_p(img), H, W, _p(out))
+    img = _image(img)
+    H, W, C = img.shape
+    out = np.empty((2 * H, 2 * W, C))
+    lib().or_upsample2(_p(img), H, W, C, _p(out))
     return out
 
 

@@ -8,9 +8,12 @@
  * library never does.  It shares no code, header or table with the CUDA path.
  *
  * Conventions (shared with the CUDA path only through the written contract):
- *   images      H x W x 3, row-major, channel fastest ("HWC"), double here;
+ *   images      H x W x C, row-major, channel fastest ("HWC"), double here;
+ *               C = 3 (RGB), or 4 (RGBS: the scale map of section 1 as a
+ *               fourth channel beside R, G and B, as section 3 builds its
+ *               neighbourhood vectors);
  *   window      the w x w block whose top-left pixel is (y0, x0);
- *   vector      element (dy, dx, c) of a window sits at (dy*w + dx)*3 + c;
+ *   vector      element (dy, dx, c) of a window sits at (dy*w + dx)*C + c;
  *   exemplar    windows at every stride-1 origin fully inside the exemplar,
  *               index n = y*(We - w + 1) + x;
  *   queries     windows of the output at origins on the stride grid
@@ -48,12 +51,12 @@ OR_EXPORT int or_max_threads(int nthreads) { return set_threads(nthreads); }
 /* ---------------------------------------------------------------------------
  * E-step (Energy Optimization, Eq. 4): z_p is the exemplar neighbourhood most
  * similar to x_p under the Euclidean norm.  Brute force over every exemplar
- * window in the full dimension D = 3 w^2; ties go to the smallest index n
+ * window in the full dimension D = C w^2; ties go to the smallest index n
  * (strict '<').  qlist selects the query indices to evaluate (NULL = all Q,
  * then nq must be Q).  Outputs nn[i], d2[i] for i < nq.
  * ------------------------------------------------------------------------ */
 OR_EXPORT void or_nn_bruteforce(const double *X, int Ho, int Wo, const double *Z, int He, int We,
-                                int w, int stride, const int32_t *qlist, int nq, int32_t *nn,
+                                int w, int C, int stride, const int32_t *qlist, int nq, int32_t *nn,
                                 double *d2, int nthreads) {
     set_threads(nthreads);
     const int qx = (Wo - w) / stride + 1;
@@ -70,9 +73,9 @@ OR_EXPORT void or_nn_bruteforce(const double *X, int Ho, int Wo, const double *Z
             double s = 0.0;
             for (int dy = 0; dy < w; ++dy)
                 for (int dx = 0; dx < w; ++dx)
-                    for (int c = 0; c < 3; ++c) {
-                        const double a = X[((long)(y0 + dy) * Wo + (x0 + dx)) * 3 + c];
-                        const double b = Z[((long)(ey + dy) * We + (exx + dx)) * 3 + c];
+                    for (int c = 0; c < C; ++c) {
+                        const double a = X[((long)(y0 + dy) * Wo + (x0 + dx)) * C + c];
+                        const double b = Z[((long)(ey + dy) * We + (exx + dx)) * C + c];
                         s += (a - b) * (a - b);
                     }
             if (s < best) {
@@ -88,7 +91,7 @@ OR_EXPORT void or_nn_bruteforce(const double *X, int Ho, int Wo, const double *Z
 /* Full-dimension squared distance between query q of X and exemplar window n
  * (Eq. 4 term).  Used to score candidate lists. */
 OR_EXPORT void or_pair_dist2(const double *X, int Ho, int Wo, const double *Z, int He, int We,
-                             int w, int stride, const int32_t *q, const int32_t *n, int count,
+                             int w, int C, int stride, const int32_t *q, const int32_t *n, int count,
                              double *d2) {
     (void)Ho;
     (void)He;
@@ -100,9 +103,9 @@ OR_EXPORT void or_pair_dist2(const double *X, int Ho, int Wo, const double *Z, i
         double s = 0.0;
         for (int dy = 0; dy < w; ++dy)
             for (int dx = 0; dx < w; ++dx)
-                for (int c = 0; c < 3; ++c) {
-                    const double a = X[((long)(y0 + dy) * Wo + (x0 + dx)) * 3 + c];
-                    const double b = Z[((long)(ey + dy) * We + (exx + dx)) * 3 + c];
+                for (int c = 0; c < C; ++c) {
+                    const double a = X[((long)(y0 + dy) * Wo + (x0 + dx)) * C + c];
+                    const double b = Z[((long)(ey + dy) * We + (exx + dx)) * C + c];
                     s += (a - b) * (a - b);
                 }
         d2[i] = s;
@@ -115,8 +118,8 @@ OR_EXPORT void or_pair_dist2(const double *X, int Ho, int Wo, const double *Z, i
  *   mu    = (1/N) sum_n v_n
  *   Sigma = (1/N) sum_n (v_n - mu)(v_n - mu)^T
  * ------------------------------------------------------------------------ */
-OR_EXPORT void or_window_mean(const double *Z, int He, int We, int w, double *mu) {
-    const int D = 3 * w * w;
+OR_EXPORT void or_window_mean(const double *Z, int He, int We, int w, int C, double *mu) {
+    const int D = C * w * w;
     const int ex = We - w + 1;
     const long N = (long)(He - w + 1) * ex;
     for (int k = 0; k < D; ++k) mu[k] = 0.0;
@@ -124,35 +127,35 @@ OR_EXPORT void or_window_mean(const double *Z, int He, int We, int w, double *mu
         const int ey = (int)(n / ex), exx = (int)(n % ex);
         for (int dy = 0; dy < w; ++dy)
             for (int dx = 0; dx < w; ++dx)
-                for (int c = 0; c < 3; ++c)
-                    mu[(dy * w + dx) * 3 + c] += Z[((long)(ey + dy) * We + (exx + dx)) * 3 + c];
+                for (int c = 0; c < C; ++c)
+                    mu[(dy * w + dx) * C + c] += Z[((long)(ey + dy) * We + (exx + dx)) * C + c];
     }
     for (int k = 0; k < D; ++k) mu[k] /= (double)N;
 }
 
 /* Centered window vectors u_n = v_n - mu for n in [n0, n0 + cnt), row-major cnt x D. */
-static void centered_windows(const double *Z, int We, int w, const double *mu, long n0, long cnt,
+static void centered_windows(const double *Z, int We, int w, int C, const double *mu, long n0, long cnt,
                              double *U) {
-    const int D = 3 * w * w;
+    const int D = C * w * w;
     const int ex = We - w + 1;
     for (long i = 0; i < cnt; ++i) {
         const long n = n0 + i;
         const int ey = (int)(n / ex), exx = (int)(n % ex);
         for (int dy = 0; dy < w; ++dy)
             for (int dx = 0; dx < w; ++dx)
-                for (int c = 0; c < 3; ++c) {
-                    const int k = (dy * w + dx) * 3 + c;
-                    U[i * D + k] = Z[((long)(ey + dy) * We + (exx + dx)) * 3 + c] - mu[k];
+                for (int c = 0; c < C; ++c) {
+                    const int k = (dy * w + dx) * C + c;
+                    U[i * D + k] = Z[((long)(ey + dy) * We + (exx + dx)) * C + c] - mu[k];
                 }
     }
 }
 
 /* Sigma (D x D, full symmetric) = (1/N) sum_n u_n u_n^T; each entry is the
  * sum over n in increasing order. */
-OR_EXPORT void or_window_cov(const double *Z, int He, int We, int w, const double *mu, double *cov,
+OR_EXPORT void or_window_cov(const double *Z, int He, int We, int w, int C, const double *mu, double *cov,
                              int nthreads) {
     set_threads(nthreads);
-    const int D = 3 * w * w;
+    const int D = C * w * w;
     const int ex = We - w + 1;
     const long N = (long)(He - w + 1) * ex;
     const long chunk = 512;
@@ -160,7 +163,7 @@ OR_EXPORT void or_window_cov(const double *Z, int He, int We, int w, const doubl
     memset(cov, 0, sizeof(double) * (size_t)D * D);
     for (long n0 = 0; n0 < N; n0 += chunk) {
         const long cnt = (N - n0 < chunk) ? (N - n0) : chunk;
-        centered_windows(Z, We, w, mu, n0, cnt, U);
+        centered_windows(Z, We, w, C, mu, n0, cnt, U);
 #pragma omp parallel for schedule(dynamic, 8)
         for (int i = 0; i < D; ++i)
             for (long t = 0; t < cnt; ++t) {
@@ -180,12 +183,12 @@ OR_EXPORT void or_window_cov(const double *Z, int He, int We, int w, const doubl
  * N < D, where Sigma = (1/N) U^T U shares its nonzero eigenvalues with G and
  * its eigenvectors are U^T g / sqrt(N lambda) (singular value decomposition
  * of U). */
-static void window_gram(const double *Z, int He, int We, int w, const double *mu, double *G,
+static void window_gram(const double *Z, int He, int We, int w, int C, const double *mu, double *G,
                         double *U) {
-    const int D = 3 * w * w;
+    const int D = C * w * w;
     const int ex = We - w + 1;
     const long N = (long)(He - w + 1) * ex;
-    centered_windows(Z, We, w, mu, 0, N, U);
+    centered_windows(Z, We, w, C, mu, 0, N, U);
 #pragma omp parallel for schedule(dynamic, 8)
     for (long a = 0; a < N; ++a)
         for (long b = a; b < N; ++b) {
@@ -322,17 +325,17 @@ OR_EXPORT int or_jacobi_eigh(double *A, int n, double *evals, double *V, int nth
 /* PCA fit (section 2.2): mean mu (D), top-d eigenvectors basis[j*D + k] and
  * all eigenvalues evals_all (min(N, D) entries, descending) of Sigma.
  * Uses the Gram matrix when N < D (see window_gram).  Returns Jacobi sweeps. */
-OR_EXPORT int or_pca_fit(const double *Z, int He, int We, int w, int d, double *mu, double *basis,
+OR_EXPORT int or_pca_fit(const double *Z, int He, int We, int w, int C, int d, double *mu, double *basis,
                          double *evals_all, int nthreads) {
     set_threads(nthreads);
-    const int D = 3 * w * w;
+    const int D = C * w * w;
     const long N = (long)(He - w + 1) * (We - w + 1);
-    or_window_mean(Z, He, We, w, mu);
+    or_window_mean(Z, He, We, w, C, mu);
     int sweeps;
     if (N >= D) {
         double *cov = (double *)malloc(sizeof(double) * (size_t)D * D);
         double *V = (double *)malloc(sizeof(double) * (size_t)D * D);
-        or_window_cov(Z, He, We, w, mu, cov, nthreads);
+        or_window_cov(Z, He, We, w, C, mu, cov, nthreads);
         sweeps = or_jacobi_eigh(cov, D, evals_all, V, nthreads);
         for (int j = 0; j < d; ++j)
             for (int k = 0; k < D; ++k) basis[(long)j * D + k] = V[(long)k * D + j];
@@ -342,7 +345,7 @@ OR_EXPORT int or_pca_fit(const double *Z, int He, int We, int w, int d, double *
         double *U = (double *)malloc(sizeof(double) * (size_t)N * D);
         double *G = (double *)malloc(sizeof(double) * (size_t)N * N);
         double *V = (double *)malloc(sizeof(double) * (size_t)N * N);
-        window_gram(Z, He, We, w, mu, G, U);
+        window_gram(Z, He, We, w, C, mu, G, U);
         sweeps = or_jacobi_eigh(G, (int)N, evals_all, V, nthreads);
         for (int j = 0; j < d; ++j) {
             /* eigenvector of Sigma: U^T g_j, normalised */
@@ -368,11 +371,11 @@ OR_EXPORT int or_pca_fit(const double *Z, int He, int We, int w, int d, double *
  * resid = ||(v - mu) - B y|| of the part PCA discards.  Windows sit on the
  * stride grid of the image (stride 1 for the exemplar, the patch stride for
  * queries). */
-OR_EXPORT void or_project(const double *img, int H, int W, int w, int stride, const double *mu,
+OR_EXPORT void or_project(const double *img, int H, int W, int w, int C, int stride, const double *mu,
                           const double *basis, int d, const int32_t *list, int count, double *y,
                           double *unorm2, double *resid) {
     (void)H;
-    const int D = 3 * w * w;
+    const int D = C * w * w;
     const int qx = (W - w) / stride + 1;
 #pragma omp parallel
     {
@@ -384,9 +387,9 @@ OR_EXPORT void or_project(const double *img, int H, int W, int w, int stride, co
             double un = 0.0;
             for (int dy = 0; dy < w; ++dy)
                 for (int dx = 0; dx < w; ++dx)
-                    for (int c = 0; c < 3; ++c) {
-                        const int k = (dy * w + dx) * 3 + c;
-                        u[k] = img[((long)(y0 + dy) * W + (x0 + dx)) * 3 + c] - mu[k];
+                    for (int c = 0; c < C; ++c) {
+                        const int k = (dy * w + dx) * C + c;
+                        u[k] = img[((long)(y0 + dy) * W + (x0 + dx)) * C + c] - mu[k];
                         un += u[k] * u[k];
                     }
             for (int j = 0; j < d; ++j) {
@@ -452,11 +455,11 @@ OR_EXPORT void or_irls(const double *d2, int Q, double r, double delta, double *
  * their value from X (never happens when (Ho-w) and (Wo-w) are multiples of s).
  * ------------------------------------------------------------------------ */
 OR_EXPORT void or_m_step(const int32_t *nn, const double *Wt, const double *Z, int He, int We,
-                         int w, int Ho, int Wo, int stride, double *X) {
+                         int w, int C, int Ho, int Wo, int stride, double *X) {
     (void)He;
     const int qy = (Ho - w) / stride + 1, qx = (Wo - w) / stride + 1;
     const int ex = We - w + 1;
-    double *num = (double *)calloc((size_t)Ho * Wo * 3, sizeof(double));
+    double *num = (double *)calloc((size_t)Ho * Wo * C, sizeof(double));
     double *den = (double *)calloc((size_t)Ho * Wo, sizeof(double));
     for (int p = 0; p < qy * qx; ++p) {
         const int y0 = (p / qx) * stride, x0 = (p % qx) * stride;
@@ -466,13 +469,13 @@ OR_EXPORT void or_m_step(const int32_t *nn, const double *Wt, const double *Z, i
             for (int dx = 0; dx < w; ++dx) {
                 const long o = (long)(y0 + dy) * Wo + (x0 + dx);
                 den[o] += wp;
-                for (int c = 0; c < 3; ++c)
-                    num[o * 3 + c] += wp * Z[((long)(ey + dy) * We + (exx + dx)) * 3 + c];
+                for (int c = 0; c < C; ++c)
+                    num[o * C + c] += wp * Z[((long)(ey + dy) * We + (exx + dx)) * C + c];
             }
     }
     for (long o = 0; o < (long)Ho * Wo; ++o)
         if (den[o] > 0.0)
-            for (int c = 0; c < 3; ++c) X[o * 3 + c] = num[o * 3 + c] / den[o];
+            for (int c = 0; c < C; ++c) X[o * C + c] = num[o * C + c] / den[o];
     free(num);
     free(den);
 }
@@ -496,23 +499,23 @@ static int mirror(int i, int n) {
     return i;
 }
 
-OR_EXPORT void or_downsample2(const double *img, int H, int W, double *out) {
+OR_EXPORT void or_downsample2(const double *img, int H, int W, int C, double *out) {
     static const double k[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
     const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
     for (int y = 0; y < Ho; ++y)
         for (int x = 0; x < Wo; ++x)
-            for (int c = 0; c < 3; ++c) {
+            for (int c = 0; c < C; ++c) {
                 double s = 0.0;
                 for (int a = 0; a < 5; ++a)
                     for (int b = 0; b < 5; ++b) {
                         const int yy = mirror(2 * y + a - 2, H), xx = mirror(2 * x + b - 2, W);
-                        s += k[a] * k[b] * img[((long)yy * W + xx) * 3 + c];
+                        s += k[a] * k[b] * img[((long)yy * W + xx) * C + c];
                     }
-                out[((long)y * Wo + x) * 3 + c] = s;
+                out[((long)y * Wo + x) * C + c] = s;
             }
 }
 
-OR_EXPORT void or_upsample2(const double *img, int H, int W, double *out) {
+OR_EXPORT void or_upsample2(const double *img, int H, int W, int C, double *out) {
     const int Ho = 2 * H, Wo = 2 * W;
     for (int Y = 0; Y < Ho; ++Y)
         for (int Xc = 0; Xc < Wo; ++Xc) {
@@ -524,12 +527,12 @@ OR_EXPORT void or_upsample2(const double *img, int H, int W, double *out) {
             const int y0 = (int)floor(sy), x0 = (int)floor(sx);
             const int y1 = y0 + 1 < H ? y0 + 1 : H - 1, x1 = x0 + 1 < W ? x0 + 1 : W - 1;
             const double fy = sy - y0, fx = sx - x0;
-            for (int c = 0; c < 3; ++c) {
-                const double v00 = img[((long)y0 * W + x0) * 3 + c];
-                const double v01 = img[((long)y0 * W + x1) * 3 + c];
-                const double v10 = img[((long)y1 * W + x0) * 3 + c];
-                const double v11 = img[((long)y1 * W + x1) * 3 + c];
-                out[((long)Y * Wo + Xc) * 3 + c] =
+            for (int c = 0; c < C; ++c) {
+                const double v00 = img[((long)y0 * W + x0) * C + c];
+                const double v01 = img[((long)y0 * W + x1) * C + c];
+                const double v10 = img[((long)y1 * W + x0) * C + c];
+                const double v11 = img[((long)y1 * W + x1) * C + c];
+                out[((long)Y * Wo + Xc) * C + c] =
                     (1 - fy) * ((1 - fx) * v00 + fx * v01) + fy * ((1 - fx) * v10 + fx * v11);
             }
         }

@@ -12,6 +12,7 @@ random numbers and paints images.  Everything it produces is an *input*:
   non-overlapping w x w exemplar windows drawn uniformly at random.
 * ``random_nn`` / ``random_weights`` / ``sample_indices``: seeded index and
   weight arrays for step-wise tests.
+* ``uniform_field``: per-pixel uniforms for the scale-guided initialisation.
 * ``batched_jobs``: the job list of the 64-job batched workload.
 
 All randomness comes from SplitMix64 (Steele, Lea & Flood, "Fast splittable
@@ -150,6 +151,12 @@ def random_patch_init(exemplar: np.ndarray, Ho: int, Wo: int, w: int, seed: int)
         ww = min(w, Wo - bx * w)
         out[by * w:by * w + h, bx * w:bx * w + ww] = exemplar[ey:ey + h, ex:ex + ww]
     return out
+
+
+def uniform_field(seed: int, H: int, W: int) -> np.ndarray:
+    """H x W float64 uniforms in [0, 1) (seeded): the per-pixel draws of an initialisation that
+    picks one of several equally good exemplar pixels."""
+    return SplitMix64(seed * 47 + 23).uniform(H * W).reshape(H, W)
 
 
 def random_nn(seed: int, Q: int, N: int) -> np.ndarray:
