@@ -99,8 +99,8 @@ typedef struct {
                         capped at 64 */
     double var_frac; /* used when d <= 0 */
     int max_iters;   /* eigen-solver iteration cap (0 = 200) */
-    int d_fast;      /* PCA dimensions of the tensor-core and proposal searches, 1..92
-                        (0 = 92, capped by the covariance rank) */
+    int d_fast;      /* PCA dimensions of the tensor-core and proposal searches, 1..124
+                        (0 = 124; capped by the covariance rank min(D, N - 1)) */
 } pts_index_params;
 
 typedef struct {
@@ -142,6 +142,29 @@ const char *pts_last_error(void);
 const char *pts_version(void);
 
 /*
+ * Device memory (no counterpart in the paper).  Every buffer the library owns (index tables,
+ * workspaces, scratch) is allocated through one pair of functions: cudaMalloc / cudaFree by
+ * default, or the caller's, e.g. a framework's caching allocator.
+ *   alloc(bytes, stream, user)  returns device memory of at least `bytes` bytes on the current
+ *                               device, or NULL on failure (the library call then returns
+ *                               PTS_ERR_OOM); `stream` is always NULL (the legacy stream);
+ *   release(ptr, stream, user)  takes back a pointer alloc returned.  The library synchronises
+ *                               the device first, as cudaFree does, so nothing it queued still
+ *                               reads the memory.
+ * pts_set_allocator installs both (alloc and release non-NULL) or restores cudaMalloc /
+ * cudaFree (both NULL); one NULL is PTS_ERR_INVALID_ARG.  It may be called only while the
+ * library holds no device memory (no index or batch alive): otherwise PTS_ERR_INVALID_ARG, so
+ * no pointer is ever returned to an allocator that did not make it.  Not to be called
+ * concurrently with other library calls.
+ * pts_live_allocations counts the library's allocations not yet freed (every destroy call
+ * brings it back to where it was before the matching create).
+ */
+typedef void *(*pts_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*pts_free_fn)(void *ptr, void *stream, void *user);
+pts_status pts_set_allocator(pts_alloc_fn alloc, pts_free_fn release, void *user);
+long long pts_live_allocations(void);
+
+/*
  * pca_fit -- PCA of the exemplar's neighbourhood vectors (section 2.2: the
  * search runs on PCA-reduced vectors; the paper keeps 95% of the variance).
  * d may be up to 128 here; an index keeps up to max(d, d_fast) components.
@@ -178,6 +201,23 @@ void pts_index_destroy(pts_index index);
 
 /* Fills *info (host) with the index's sizes and PCA summary. */
 pts_status pts_index_get_info(pts_index index, pts_index_info *info);
+
+/*
+ * Index files (section 2.2's preprocessing run once per exemplar and window width).
+ * pts_index_save writes everything a search needs -- the exemplar, the PCA (mean, basis,
+ * eigenvalues), every search table, and, when present, the trained proposal (clusters,
+ * cluster-ordered tiles, the network's FP32 weights) and the k-means tree -- to `path`
+ * (written under a temporary name, then renamed).  Synchronises the device.
+ * pts_index_load reads such a file into a new index on the current device, owned by the caller
+ * (free it with pts_index_destroy).  Every search on it returns what the same search on the
+ * saved index returns.  The file's header and its length are checked before anything is
+ * allocated: a file that is not an index file, was written with another byte order or layout
+ * version, is truncated, or whose tables disagree with its header gives PTS_ERR_INVALID_ARG
+ * (see pts_last_error).  Synchronises the device.  Files are in host byte order; the x86-64 and
+ * AArch64 hosts of this library share it.
+ */
+pts_status pts_index_save(pts_index index, const char *path);
+pts_status pts_index_load(const char *path, pts_index *out);
 
 /* Sets how many CTAs split the exemplar tiles of one 128-query block in the
  * tensor-core searches (PTS_F16_RERANK, PTS_FP8_RERANK); 0 restores the
@@ -462,6 +502,12 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
                             int tune, void *stream, pts_batch *out);
 /* Replays the batch's graph on `stream` (asynchronous): every job runs from its current output. */
 pts_status pts_batch_run(pts_batch batch, void *stream);
+/* The one-call form: pts_batch_create (8 streams at most, autotuned), one pts_batch_run,
+ * pts_batch_destroy.  Synchronises `stream`; returns the first error of the three, else the
+ * first job whose index reports a device-side error (PTS_ERR_DEVICE / PTS_ERR_TIMEOUT).  For
+ * repeated runs of the same jobs keep the batch instead: building it costs a sizing search per
+ * job and a graph capture. */
+pts_status synthesize_batched(const pts_job *jobs, int n_jobs, int iters, float r, float delta, void *stream);
 /* Kernel launches one run issues, and (parts_out, n_jobs ints, may be NULL) each job's exemplar
  * split chosen by the autotuner (0 for exact jobs). */
 pts_status pts_batch_info(pts_batch batch, long long *launches_per_run, int *parts_out);

@@ -4,7 +4,7 @@ Bashir & Ghouri, "Perspective Texture Synthesis Based on Improved Energy
 Optimization" (arXiv:2006.11851).  The compute path is the C-ABI CUDA library
 ``libpts`` (include/pts.h); this package is a thin ctypes binding with the same
 entry-point names that takes torch CUDA tensors and passes their pointers,
-sizes and the current stream.  There is no CPU fallback: every call raises if
+sizes and the current stream (the batched entry points are in ``batched``).  There is no CPU fallback: every call raises if
 the CUDA library is not built or no GPU is present.
 """
 from ._binding import (  # noqa: F401
@@ -17,12 +17,15 @@ from ._binding import (  # noqa: F401
     fp32_fma_peak,
     gemm_selftest,
     histogram_match,
+    index_load,
+    index_save,
     irls_weights,
     kmeans,
     kmtree_export,
     kmtree_info,
     kmtree_last_leaves,
     lib,
+    live_allocations,
     m_step,
     m_step_hist,
     mlp_grad,
@@ -31,10 +34,12 @@ from ._binding import (  # noqa: F401
     project_queries,
     proposal_info,
     proposal_top4,
+    set_allocator,
     synthesize_level,
     synthesize_level_async,
     synthesize_level_converge,
     train_proposal,
     upsample2,
+    use_torch_allocator,
 )
 from .pyramid import synthesize_pyramid  # noqa: F401

@@ -115,6 +115,10 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     L.pts_profile_enable.argtypes = [_I]
     L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
     L.pts_fp32_fma_peak.argtypes = [_I, _I, _vp, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
+    L.pts_index_save.argtypes = [_vp, ctypes.c_char_p]
+    L.pts_index_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_vp)]
+    L.pts_set_allocator.argtypes = [_vp, _vp, _vp]
+    L.pts_live_allocations.restype = ctypes.c_longlong
 
 
 def _check(status: int) -> None:
@@ -177,11 +181,31 @@ class ExemplarIndex:
         _check(L.build_exemplar_index(_ptr(exemplar), He, We, w, ctypes.byref(p), _stream(),
                                       ctypes.byref(self._h)))
         self.device = exemplar.device
+        self._read_info()
+
+    def _read_info(self) -> None:
         info = _IndexInfo()
-        _check(L.pts_index_get_info(self._h, ctypes.byref(info)))
+        _check(lib().pts_index_get_info(self._h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in _IndexInfo._fields_}
         self.w, self.N, self.d, self.D = info.w, info.N, info.d, info.D
-        self.He, self.We = He, We
+        self.He, self.We = info.He, info.We
+
+    def save(self, path: str) -> None:
+        """Write the index (PCA, search tables, and any trained proposal or k-means tree) to a file
+        (pts_index_save; synchronises the device)."""
+        _check(lib().pts_index_save(self.handle, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "ExemplarIndex":
+        """An index read from a file written by save(), on the current CUDA device
+        (pts_index_load; synchronises the device)."""
+        L = lib()
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p()
+        _check(L.pts_index_load(os.fsencode(path), ctypes.byref(self._h)))
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._read_info()
+        return self
 
     @property
     def handle(self):
@@ -214,6 +238,62 @@ class ExemplarIndex:
     def set_tc_parts(self, parts: int) -> None:
         """Exemplar split of the tensor-core searches (0 = automatic); results do not depend on it."""
         _check(lib().pts_index_set_tc_parts(self.handle, int(parts)))
+
+
+def index_save(index: ExemplarIndex, path: str) -> None:
+    """pts_index_save: ExemplarIndex.save."""
+    index.save(path)
+
+
+def index_load(path: str) -> ExemplarIndex:
+    """pts_index_load: ExemplarIndex.load."""
+    return ExemplarIndex.load(path)
+
+
+def live_allocations() -> int:
+    """Device allocations the library holds (pts_live_allocations)."""
+    return int(lib().pts_live_allocations())
+
+
+_ALLOC_FNS = None
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Route the library's device allocations through alloc(bytes) -> int pointer and free(ptr)
+    (pts_set_allocator); with no arguments, back to cudaMalloc / cudaFree.  Allowed only while
+    the library holds no device memory.  use_torch_allocator() installs torch's caching
+    allocator."""
+    global _ALLOC_FNS
+    L = lib()
+    if alloc is None and free is None:
+        _check(L.pts_set_allocator(None, None, None))
+        _ALLOC_FNS = None
+        return
+    if alloc is None or free is None:
+        raise ValueError("give both alloc and free, or neither")
+    alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return alloc(int(nbytes)) or None
+        except Exception:  # an exception must not cross into C: report failure instead
+            return None
+
+    def _free(ptr, stream, user):
+        try:
+            free(int(ptr))
+        except Exception:
+            pass
+
+    fns = (alloc_t(_alloc), free_t(_free))  # kept alive while registered
+    _check(L.pts_set_allocator(ctypes.cast(fns[0], _vp), ctypes.cast(fns[1], _vp), None))
+    _ALLOC_FNS = fns
+
+
+def use_torch_allocator() -> None:
+    """Serve the library's device memory from torch's CUDA caching allocator (current device)."""
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n), torch.cuda.caching_allocator_delete)
 
 
 def build_exemplar_index(exemplar: torch.Tensor, w: int, d: int = 0, var_frac: float = 0.95,

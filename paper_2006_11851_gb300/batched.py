@@ -52,6 +52,28 @@ def _declare(L):
     L.pts_batch_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]
     L.pts_batch_destroy.argtypes = [ctypes.c_void_p]
     L.pts_batch_destroy.restype = None
+    L.synthesize_batched.argtypes = [ctypes.POINTER(_Job), ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_void_p]
+
+
+def synthesize_batched(indices: list, outputs: list, energies: list, mode="f16", iters: int = 5, r: float = 2.0,
+                       delta: float = 1e-3, stride: int = 2) -> None:
+    """One call of the library's synthesize_batched: job k runs `iters` EM iterations of
+    outputs[k] (square Ho x Ho x 3, CUDA) against indices[k], then the final search; outputs and
+    energies[k] (iters + 1 float64, CUDA) are written in place.  Synchronises the current stream."""
+    L = lib()
+    _declare(L)
+    n = len(indices)
+    if not (len(outputs) == len(energies) == n):
+        raise ValueError("one output and one energy array per index")
+    jobs = (_Job * n)()
+    for k in range(n):
+        Ho, Wo, C = outputs[k].shape
+        if C != 3 or not outputs[k].is_cuda or energies[k].numel() != iters + 1:
+            raise ValueError(f"job {k}: output must be CUDA H x W x 3 and energy hold iters + 1 values")
+        jobs[k] = _Job(indices[k].handle.value, outputs[k].data_ptr(), Ho, Wo, stride, _mode(mode),
+                       energies[k].data_ptr())
+    _check(L.synthesize_batched(jobs, n, iters, r, delta, _stream()))
 
 
 class Batch:

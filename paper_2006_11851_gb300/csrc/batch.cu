@@ -7,6 +7,7 @@
 // and energy, M-step -- into one graph, the jobs spread round-robin over n_streams forked
 // streams (jobs are independent: each has its own index and workspace).  pts_batch_run replays
 // the graph.  Energies go to device arrays so the graph has no host copy or synchronisation.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -244,6 +245,18 @@ void pts_batch_destroy(pts_batch b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     delete b;
+}
+
+pts_status synthesize_batched(const pts_job *jobs, int n_jobs, int iters, float r, float delta, void *stream) {
+    pts_batch b = nullptr;
+    PTS_TRY(pts_batch_create(jobs, n_jobs, iters, r, delta, std::min(n_jobs, 8), 1, stream, &b));
+    pts_status s = pts_batch_run(b, stream);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    pts_batch_destroy(b);
+    if (s != PTS_OK) return s;
+    if (e != cudaSuccess) return cuda_error(e, "synthesize_batched");
+    for (int k = 0; k < n_jobs; ++k) PTS_TRY(pts_index_device_status(jobs[k].index, stream));
+    return PTS_OK;
 }
 
 }  // extern "C"

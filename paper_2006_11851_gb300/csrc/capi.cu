@@ -4,7 +4,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -322,6 +324,56 @@ pts_status cuda_error(cudaError_t e, const char *where) {
     return PTS_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// device memory: cudaMalloc / cudaFree, or the allocator registered by pts_set_allocator
+// ---------------------------------------------------------------------------
+namespace {
+struct Allocator {
+    pts_alloc_fn alloc = nullptr;
+    pts_free_fn release = nullptr;
+    void *user = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;                 // empty: cudaMalloc / cudaFree
+std::atomic<long long> g_live{0};  // library allocations not yet freed
+}  // namespace
+
+pts_status dev_alloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    // the lock spans the allocation, so the allocator cannot be swapped while one is being made
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc.alloc) {
+        *p = g_alloc.alloc(bytes, nullptr, g_alloc.user);
+        if (!*p) return set_error(PTS_ERR_OOM, std::string("registered allocator failed for ") + what);
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            return set_error(PTS_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+        }
+    }
+    g_live.fetch_add(1);
+    return PTS_OK;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    Allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    // while this allocation is still counted live, pts_set_allocator cannot swap the allocator
+    if (a.release) {
+        cudaDeviceSynchronize();
+        a.release(p, nullptr, a.user);
+    } else {
+        cudaFree(p);
+    }
+    g_live.fetch_sub(1);
+}
+
 }  // namespace pts
 
 using namespace pts;
@@ -331,6 +383,22 @@ extern "C" {
 const char *pts_last_error(void) { return g_last_error.c_str(); }
 
 const char *pts_version(void) { return "pts-gb300 0.1 (sm_103a)"; }
+
+pts_status pts_set_allocator(pts_alloc_fn alloc, pts_free_fn release, void *user) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return set_error(PTS_ERR_INVALID_ARG, "pts_set_allocator: give both functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_live.load() != 0)
+        return set_error(PTS_ERR_INVALID_ARG,
+                         "pts_set_allocator: the library still holds device memory (" + std::to_string(g_live.load()) +
+                             " allocations); destroy every index and batch first");
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.user = alloc ? user : nullptr;
+    return PTS_OK;
+}
+
+long long pts_live_allocations(void) { return g_live.load(); }
 
 pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double var_frac,
                    float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream) {

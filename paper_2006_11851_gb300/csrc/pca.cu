@@ -405,16 +405,15 @@ void dgemm(int M, int N, int K, const double *A, int lda, const double *B, int l
 struct Scratch {
     std::vector<void *> ptrs;
     ~Scratch() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : ptrs) dev_free(p);
     }
     template <typename T>
     pts_status get(T **p, size_t n, const char *what) {
-        if (cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-            cudaGetLastError();
-            *p = nullptr;
-            return set_error(PTS_ERR_OOM, std::string("cudaMalloc failed for ") + what);
-        }
-        ptrs.push_back(*p);
+        void *q = nullptr;
+        *p = nullptr;
+        PTS_TRY(dev_alloc(&q, std::max<size_t>(n, 1) * sizeof(T), what));
+        *p = static_cast<T *>(q);
+        ptrs.push_back(q);
         return PTS_OK;
     }
 };

@@ -54,27 +54,37 @@ inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------
 // device memory owned by the library
 // ---------------------------------------------------------------------------
+// Every library allocation goes through these two: cudaMalloc / cudaFree, or the allocator a
+// caller registered with pts_set_allocator (capi.cu).  dev_free synchronises the device before
+// it hands memory to a registered allocator, as cudaFree does, so no queued kernel can still
+// be reading it when the allocator gives it out again.
+pts_status dev_alloc(void **p, size_t bytes, const char *what);
+void dev_free(void *p);
+
+// A buffer frees itself when it goes out of scope (so scratch buffers are returned on every
+// path, early error returns included); it cannot be copied, so no two owners share a pointer.
 template <typename T>
 struct DevBuf {
     T *ptr = nullptr;
     size_t count = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
     pts_status ensure(size_t n, const char *what) {
         if (n <= count && ptr) return PTS_OK;
-        if (ptr) cudaFree(ptr);
+        if (ptr) dev_free(ptr);
         ptr = nullptr;
         count = 0;
         if (n == 0) n = 1;
-        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
-        if (e != cudaSuccess) {
-            ptr = nullptr;
-            cudaGetLastError();
-            return set_error(PTS_ERR_OOM, std::string("cudaMalloc failed for ") + what);
-        }
+        void *p = nullptr;
+        PTS_TRY(dev_alloc(&p, n * sizeof(T), what));
+        ptr = static_cast<T *>(p);
         count = n;
         return PTS_OK;
     }
     void release() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) dev_free(ptr);
         ptr = nullptr;
         count = 0;
     }

@@ -17,7 +17,9 @@ def _declared():
             continue
         src = open(os.path.join(ROOT, "include", f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, re.M):
+        # function declarations (typedefs of function-pointer types are not functions)
+        for m in re.finditer(r"^(?!\s*typedef\b)\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b([a-z_][a-z0-9_]*)\s*\(",
+                             src, re.M):
             name = m.group(1)
             if name not in ("if", "while", "sizeof", "defined"):
                 names.append(name)
@@ -84,3 +86,85 @@ def test_python_binding_fails_loudly_without_gpu():
     import paper_2006_11851_gb300 as pts
     with pytest.raises(TypeError):
         pts.nn_search(None, torch.zeros(16, 16, 3), 2)
+
+
+def test_allocator_registration_on_host(libpts):
+    libpts.pts_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    libpts.pts_live_allocations.restype = ctypes.c_longlong
+    alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    calls = []
+    a = alloc_t(lambda n, s, u: calls.append(n) or None)
+    fr = free_t(lambda p, s, u: calls.append(p))
+    cast = ctypes.cast
+    assert libpts.pts_set_allocator(cast(a, ctypes.c_void_p), None, None) == -1       # one of the two
+    assert libpts.pts_set_allocator(None, cast(fr, ctypes.c_void_p), None) == -1
+    assert libpts.pts_live_allocations() == 0                                        # nothing allocated here
+    assert libpts.pts_set_allocator(cast(a, ctypes.c_void_p), cast(fr, ctypes.c_void_p), None) == 0
+    assert libpts.pts_set_allocator(None, None, None) == 0                           # back to cudaMalloc
+    assert calls == []
+    libpts.synthesize_batched.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_void_p]
+    assert libpts.synthesize_batched(None, 0, 1, 2.0, 1e-3, None) == -1
+
+
+# index files: the header layout of persist.cu, written field by field in host byte order
+_HEADER = "<8sII16ifddiifiiii"
+
+
+def _index_file(**over):
+    """Bytes of a consistent index file for a 12 x 12 exemplar, w = 4, d = 8, d_fast = 16 (every
+    table zero), with header fields replaced by `over`."""
+    import struct
+    f = dict(He=12, We=12, w=4, D=48, N=81, d=8, da=12, d_fast=16, da_fast=20, ny=9, nx=9, ntiles=1,
+             ktc=32, kf8=32, eig_iters=5, tc_parts=0, unorm2_max=1.0, var=0.9, eig_top=1.0)
+    f.update(over)
+    head = struct.pack(_HEADER, over.get("magic", b"PTSINDEX"), over.get("version", 1),
+                       over.get("order", 0x01020304), f["He"], f["We"], f["w"], f["D"], f["N"], f["d"], f["da"],
+                       f["d_fast"], f["da_fast"], f["ny"], f["nx"], f["ntiles"], f["ktc"], f["kf8"],
+                       f["eig_iters"], f["tc_parts"], f["unorm2_max"], f["var"], f["eig_top"], 0, 0, 0.0, 0, 0, 0, 0)
+    tcr = 256  # one tensor-core tile of 256 windows
+    secs = [(b"EXEM", 4, 12 * 12 * 3), (b"EXE4", 16, 144), (b"MEAN", 4, 48), (b"BASI", 4, 128 * 48),
+            (b"BAST", 4, 48 * 128), (b"EIGV", 8, 128), (b"ETIL", 4, 12 * 128), (b"EROW", 4, 81 * 12),
+            (b"ENRM", 4, 128), (b"EFUL", 4, 64 * 128), (b"EFST", 4, 20 * 128), (b"ETCH", 2, tcr * 32),
+            (b"ETC8", 1, tcr * 32), (b"F8SC", 4, 17), (b"UMAX", 4, 1)]
+    body = b"".join(t + struct.pack("<IQ", e, c) + bytes(e * c) for t, e, c in secs)
+    return head + body
+
+
+def test_index_files_checked_on_host(libpts, tmp_path):
+    libpts.pts_last_error.restype = ctypes.c_char_p
+    libpts.pts_index_load.argtypes = [ctypes.c_char_p, ctypes.c_void_p]
+    libpts.pts_index_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    libpts.pts_index_destroy.argtypes = [ctypes.c_void_p]
+    out = ctypes.c_void_p()
+
+    def load(data):
+        p = tmp_path / "idx.bin"
+        p.write_bytes(data)
+        rc = libpts.pts_index_load(str(p).encode(), ctypes.byref(out))
+        return rc, libpts.pts_last_error().decode()
+
+    assert libpts.pts_index_save(None, str(tmp_path / "x").encode()) == -1
+    assert libpts.pts_index_load(str(tmp_path / "missing.bin").encode(), ctypes.byref(out)) == -1
+    assert libpts.pts_index_load(None, ctypes.byref(out)) == -1
+    good = _index_file()
+    for data, msg in [(b"", "ends early"),
+                      (_index_file(magic=b"NOTINDEX"), "not an index file"),
+                      (_index_file(order=0x04030201), "byte order"),
+                      (_index_file(version=2), "version"),
+                      (_index_file(D=49), "window grid"),
+                      (_index_file(N=80), "window count"),
+                      (_index_file(da=16), "PCA dimensions"),
+                      (_index_file(ktc=48), "tile sizes"),
+                      (good[:-1], "length"),
+                      (good + b"\0", "length")]:
+        rc, err = load(data)
+        assert rc == -1 and msg in err, (msg, rc, err)
+        assert not out.value
+    # a consistent file passes every check and reaches the device: without a GPU that step fails
+    rc, err = load(good)
+    if rc == 0:  # pragma: no cover - only where a GPU is present
+        libpts.pts_index_destroy(out)
+    else:
+        assert rc == -2 and "CUDA" in err, (rc, err)
