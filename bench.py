@@ -232,7 +232,7 @@ PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 /
 # search source file is unchanged (the digest below is of that file with the profiled kernel; any
 # later edit of the file, even of host code, turns the figure off until it is checked again).
 TC_TRAFFIC_BYTES = 32.895e6 + 0.016e6
-TC_TRAFFIC_SHA256 = "4b5499d4d88b59aebde481e9e069bb86098a30e2aeda747b742473846ff456c5"
+TC_TRAFFIC_SHA256 = "660fa2e83d816908525f5da692b80445999fa7298898454b436fe745017a9eda"
 
 
 def _tc_traffic():

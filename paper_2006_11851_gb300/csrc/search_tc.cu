@@ -1051,9 +1051,9 @@ int tc_tiles(int N) { return (N + kTN - 1) / kTN; }
 
 int tc_tile_rows() { return kTN; }
 
-// Parts per query block.  Each part keeps its own 32 best per query, and a running top-32 over
-// n windows inserts about 32 (1 + ln(n / 32)) of them, so splitting the exemplar multiplies the
-// insertion work; it only pays when the query blocks alone leave most SMs idle.
+// Parts per query block.  Each part keeps its own best groups per query (k_select_parts merges
+// them), so every extra part adds a set of kept-group records, its own warm-up of the running
+// lists and a wider merge; the split is used only when the query blocks alone leave SMs idle.
 int tc_parts(int Q, int ntiles) {
     const int nqb = tc_query_blocks(Q);
     int p = 1;
