@@ -523,6 +523,15 @@ void pts_batch_destroy(pts_batch batch);
  * K <= 128).  Writes the largest absolute error and the largest |reference|.
  * Synchronises the device. */
 pts_status pts_tc_selftest(int N, int K, int f16, double *max_abs_err, double *max_abs_ref);
+
+/* Self-test of the bounded device waits (no counterpart in the paper).  One thread waits on a
+ * new mbarrier phase with the library's bounded wait (abortable != 0: the variant that also
+ * raises an abort flag for the kernel's other roles).  With arrive != 0 the phase completes:
+ * PTS_OK and *completed_out = 1.  With arrive == 0 nothing completes it: the wait gives up after
+ * about one second, the kernel returns, and the call returns PTS_ERR_TIMEOUT with
+ * *completed_out = 0 (PTS_ERR_DEVICE if the abortable wait did not raise its flag).  The context
+ * stays usable.  Synchronises the device. */
+pts_status pts_wait_selftest(int arrive, int abortable, int *completed_out);
 void pts_profile_enable(int on);
 pts_status pts_profile_read(const char *kernel, double *total_ms, long long *launches);
 

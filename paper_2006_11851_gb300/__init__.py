@@ -41,5 +41,6 @@ from ._binding import (  # noqa: F401
     train_proposal,
     upsample2,
     use_torch_allocator,
+    wait_selftest,
 )
 from .pyramid import synthesize_pyramid  # noqa: F401

@@ -115,6 +115,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     L.pts_profile_enable.argtypes = [_I]
     L.pts_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Dd), ctypes.POINTER(ctypes.c_longlong)]
     L.pts_fp32_fma_peak.argtypes = [_I, _I, _vp, ctypes.POINTER(_Dd), ctypes.POINTER(_Dd)]
+    L.pts_wait_selftest.argtypes = [_I, _I, ctypes.POINTER(_I)]
     L.pts_index_save.argtypes = [_vp, ctypes.c_char_p]
     L.pts_index_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_vp)]
     L.pts_set_allocator.argtypes = [_vp, _vp, _vp]
@@ -507,6 +508,14 @@ def gemm_selftest(M: int, N: int, K: int) -> float:
     e = ctypes.c_double(0.0)
     _check(lib().pts_gemm_selftest(M, N, K, ctypes.byref(e)))
     return e.value
+
+
+def wait_selftest(arrive: bool, abortable: bool = False) -> tuple[int, bool]:
+    """(status, completed) of pts_wait_selftest: status 0 when the phase completed, the library's
+    PTS_ERR_TIMEOUT (-5) when the bounded wait gave up."""
+    done = ctypes.c_int(0)
+    st = lib().pts_wait_selftest(1 if arrive else 0, 1 if abortable else 0, ctypes.byref(done))
+    return int(st), bool(done.value)
 
 
 def fp32_fma_peak(iters: int = 20000, reps: int = 5) -> tuple[float, float]:

@@ -77,6 +77,8 @@ def test_bad_arguments_rejected_on_host(libpts):
     assert libpts.pts_index_set_tc_parts(None, 1) == -1
     libpts.pts_fp32_fma_peak.argtypes = [i, i, vp, vp, vp]
     assert libpts.pts_fp32_fma_peak(0, 1, None, None, None) == -1
+    libpts.pts_wait_selftest.argtypes = [i, i, vp]
+    assert libpts.pts_wait_selftest(0, 1, None) == -1
 
 
 def test_python_binding_fails_loudly_without_gpu():
@@ -168,3 +170,31 @@ def test_index_files_checked_on_host(libpts, tmp_path):
         libpts.pts_index_destroy(out)
     else:
         assert rc == -2 and "CUDA" in err, (rc, err)
+
+
+def test_allocator_returning_null_fails_the_build_cleanly(libpts):
+    """Host-side fault injection: a registered allocator that always fails.  The index build
+    returns PTS_ERR_OOM at its first allocation, before any device work, and holds nothing."""
+    class Params(ctypes.Structure):
+        _fields_ = [("d", ctypes.c_int), ("var_frac", ctypes.c_double), ("max_iters", ctypes.c_int),
+                    ("d_fast", ctypes.c_int)]
+    libpts.pts_last_error.restype = ctypes.c_char_p
+    libpts.pts_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    libpts.pts_live_allocations.restype = ctypes.c_longlong
+    libpts.build_exemplar_index.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(Params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    asked, freed = [], []
+    a = alloc_t(lambda n, s, u: asked.append(n) or None)
+    fr = free_t(lambda p, s, u: freed.append(p))
+    assert libpts.pts_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(fr, ctypes.c_void_p), None) == 0
+    try:
+        out = ctypes.c_void_p()
+        p = Params(16, 0.95, 0, 0)
+        rc = libpts.build_exemplar_index(ctypes.c_void_p(16), 32, 32, 8, ctypes.byref(p), None, ctypes.byref(out))
+        assert rc == -3 and b"registered allocator failed" in libpts.pts_last_error()
+        assert asked == [32 * 32 * 3 * 4] and freed == [] and not out.value
+        assert libpts.pts_live_allocations() == 0
+    finally:
+        assert libpts.pts_set_allocator(None, None, None) == 0
