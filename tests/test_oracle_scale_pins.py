@@ -319,3 +319,22 @@ def test_scale_channel_pulls_matches_to_the_right_scale():
         q = np.arange(qy * qx)
         errs[lam] = np.abs(S_z[nn // ex, nn % ex] - S_x[2 * (q // qx), 2 * (q % qx)]).mean()
     assert errs[4.0] < 0.5 * errs[0.0]
+
+
+def test_rgbs_pca_dimension_is_in_the_papers_range():
+    """Section 2.2: 95% of the variance of 8 x 8 RGBS neighbourhoods (256 dimensions) is kept by
+    about 20-45 PCA components.  Checked qualitatively, as the paper's photographs are not
+    available: on the synthetic 128² exemplar (three seeds, the scale map of its own slant at
+    tilt 0) the oracle needs 30-31 components, and the colour channels alone (192 dimensions)
+    need far more, since the smooth scale channel carries much of the variance."""
+    lo, hi = PAPER["pca_dims_rgbs_8x8"]["value"]
+    frac = PAPER["pca_variance_kept"]["value"]
+    sigma = math.degrees(math.acos(0.5))
+    for seed in (0, 1, 2):
+        Z = P.synthetic_exemplar(seed, 128, 4.0).astype(np.float64)
+        d95 = {}
+        for name, img in (("rgbs", OS.rgbs(Z, OS.scale_map(128, 128, sigma, 0.0))), ("rgb", Z)):
+            _, _, ev, _ = O.pca_fit(img, 8, 1)
+            d95[name] = int(np.searchsorted(np.cumsum(ev) / ev.sum(), frac) + 1)
+        assert lo <= d95["rgbs"] <= hi, (seed, d95)
+        assert d95["rgb"] > 2 * d95["rgbs"], (seed, d95)
