@@ -19,7 +19,7 @@ import time
 import numpy as np
 import torch
 
-from ._binding import ExemplarIndex, _check, _mode, _ptr, _stream, lib, synthesize_level
+from ._binding import ExemplarIndex, _check, _mode, _need, _ptr, _stream, lib, synthesize_level
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import pts_inputs as P  # noqa: E402
@@ -68,9 +68,11 @@ def synthesize_batched(indices: list, outputs: list, energies: list, mode="f16",
         raise ValueError("one output and one energy array per index")
     jobs = (_Job * n)()
     for k in range(n):
+        _need(outputs[k], torch.float32, f"outputs[{k}]")
+        _need(energies[k], torch.float64, f"energies[{k}]", (iters + 1,))
         Ho, Wo, C = outputs[k].shape
-        if C != 3 or not outputs[k].is_cuda or energies[k].numel() != iters + 1:
-            raise ValueError(f"job {k}: output must be CUDA H x W x 3 and energy hold iters + 1 values")
+        if C != 3:
+            raise ValueError(f"job {k}: output must be H x W x 3")
         jobs[k] = _Job(indices[k].handle.value, outputs[k].data_ptr(), Ho, Wo, stride, _mode(mode),
                        energies[k].data_ptr())
     _check(L.synthesize_batched(jobs, n, iters, r, delta, _stream()))
