@@ -232,7 +232,7 @@ PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 /
 # search source file is unchanged (the digest below is of that file with the profiled kernel; any
 # later edit of the file, even of host code, turns the figure off until it is checked again).
 TC_TRAFFIC_BYTES = 32.895e6 + 0.016e6
-TC_TRAFFIC_SHA256 = "660fa2e83d816908525f5da692b80445999fa7298898454b436fe745017a9eda"
+TC_TRAFFIC_SHA256 = "7020a2668531bcb00e066f77285b35f59d3ccb4680aa0f71bf5f311f132fe94f"
 
 
 def _tc_traffic():

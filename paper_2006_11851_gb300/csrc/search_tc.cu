@@ -808,8 +808,9 @@ __global__ void k_warm_threshold(const int *__restrict__ prev_idx, const __half 
 }
 
 // --- self-test: one 128 x N x K tile through the same descriptors, written back row-major.
-// With TA the A operand goes through tensor memory (tcgen05.st, then an MMA reading [a_tmem]),
-// as the search issues it.
+// With TA the A operand goes through tensor memory (tcgen05.st, then an MMA reading [a_tmem]).
+// The search keeps A in shared memory: its two 256-column accumulators fill all 512 columns of
+// tensor memory, so A has no room there.
 template <typename T, bool TA>
 __global__ void __launch_bounds__(128) k_tc_selftest(const T *__restrict__ A, const T *__restrict__ B, int N, int K,
                                                      uint32_t idesc, float *__restrict__ D, int *__restrict__ status) {
