@@ -117,7 +117,7 @@ def test_destroy_returns_every_allocation():
     z0 = pidx.exemplars[0].cpu().numpy()
     init = lambda s: _t(P.random_patch_init(z0, 96, 96, 16, s))  # noqa: E731
     y, nn, d2 = collect_pairs(pidx, 1, init, range(1), iters=2)
-    pts.train_proposal(pidx.indices[1], y, nn, d2, n_clusters=16, epochs=1, batch=1024, seed=3)
+    pts.train_proposal(pidx.indices[1], y, nn, d2, n_clusters=64, epochs=1, batch=4096, seed=3)
     pts.build_kmeans_tree(pidx.indices[1], 5)
     assert pts.live_allocations() > before
     pidx.close()
@@ -175,8 +175,8 @@ def test_torch_allocator_serves_the_library():
 
 
 def test_synthesize_batched_equals_the_batch():
-    specs = batched.job_specs(3, seed=4, max_exemplar=160, max_output=288)
-    b = batched.Batch(specs, mode="f16", iters=2)
+    specs = batched.job_specs(6, seed=3, max_exemplar=160, max_output=288)
+    b = batched.Batch(specs, mode="f16", iters=2, n_streams=3)
     try:
         b.reset()
         b.run()
