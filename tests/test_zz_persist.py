@@ -11,8 +11,8 @@ the GPU, through the C ABI:
   - synthesize_batched equals the captured batch it wraps;
   - building, training and destroying an index leaves no library allocation behind.
 
-These exercise host-side bookkeeping over kernels the other GPU tests check against the oracle;
-the file is collected last.
+These exercise host-side bookkeeping over kernels the other GPU tests check against the oracle,
+so the file is collected after them.
 """
 import filecmp
 import os
