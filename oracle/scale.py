@@ -173,3 +173,36 @@ def synthesize_level_rgbs(Z4, X4, w: int, iters: int, r: float = 2.0, delta: flo
         X = m_step(nn, W, Z4, w, Ho, Wo, stride, X_prev=X)
         X[:, :, 3] = guide
     return {"X": X, "E": np.array(E), "E_delta": np.array(Ed)}
+
+
+def synthesize_pyramid_rgbs(Z, sigma_deg: float, tau_deg: float, Ho: int, Wo: int, windows, iters: int, u,
+                            lam: float = 1.0, nbins: int = 64, r: float = 2.0, delta: float = 1e-3,
+                            stride: int = 2, nthreads: int = 0):
+    """The whole method of section 3 on RGBS images, coarse to fine (section 2.1's pyramid): at
+    every level the exemplar's scale map (Eqs. 1-3 at that level's size) and its resampling to the
+    level's output size; the coarsest output initialised from exemplar pixels of the same scale
+    (u: uniforms of the coarsest output's shape), each finer one from the coarser result's colours
+    up-sampled by 2; then the EM iterations of synthesize_level_rgbs.  Z (He x We x 3) is the
+    finest exemplar, (Ho, Wo) the finest output size, windows the window width per level (coarsest
+    first).  Returns the final colour image (Ho x Wo x 3) and the per-level energy arrays."""
+    from . import exemplar_pyramid, upsample2
+
+    levels = len(windows)
+    pyr = exemplar_pyramid(Z, levels)
+    X, energies = None, []
+    for lev, w in enumerate(windows):
+        Zl = pyr[lev]
+        He, We = Zl.shape[:2]
+        h, wd = Ho >> (levels - 1 - lev), Wo >> (levels - 1 - lev)
+        S_z = scale_map(He, We, sigma_deg, tau_deg)
+        S_x = resample(S_z, h, wd)
+        if X is None:
+            X0, _ = scale_guided_init(Zl, S_z, S_x, u, nbins)
+        else:
+            X0 = upsample2(X[:, :, :3])
+            if X0.shape[:2] != (h, wd):
+                raise ValueError("level sizes must double from one level to the next")
+        out = synthesize_level_rgbs(rgbs(Zl, S_z, lam), rgbs(X0, S_x, lam), w, iters, r, delta, stride, nthreads)
+        X = out["X"]
+        energies.append(out["E"])
+    return X[:, :, :3], energies

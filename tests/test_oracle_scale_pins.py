@@ -338,3 +338,26 @@ def test_rgbs_pca_dimension_is_in_the_papers_range():
             d95[name] = int(np.searchsorted(np.cumsum(ev) / ev.sum(), frac) + 1)
         assert lo <= d95["rgbs"] <= hi, (seed, d95)
         assert d95["rgb"] > 2 * d95["rgbs"], (seed, d95)
+
+
+def test_rgbs_pyramid_keeps_each_levels_map_and_lowers_the_energy():
+    """Coarse to fine on RGBS images: each level's scale channel is that level's resampled map
+    (checked through the final level), the energy never rises within a level (r = 2), and the
+    perspective survives: rows of the output match exemplar windows of the same scale."""
+    sigma = math.degrees(math.acos(0.5))
+    Z = P.synthetic_exemplar(8, 48, 4.0).astype(np.float64)
+    u = P.uniform_field(5, 24, 24)
+    X, energies = OS.synthesize_pyramid_rgbs(Z, sigma, 0.0, 48, 48, [8, 4], 3, u)
+    assert X.shape == (48, 48, 3) and len(energies) == 2
+    for E in energies:
+        assert np.all(np.diff(E) <= 1e-6 * E[0])
+    S_z = OS.scale_map(48, 48, sigma, 0.0)
+    S_x = OS.resample(S_z, 48, 48)
+    X4 = OS.rgbs(X, S_x)
+    nn, _ = O.nn_bruteforce(X4, OS.rgbs(Z, S_z), 4, 2)
+    qy, qx = O.grid(48, 48, 4, 2)
+    rows = nn // (48 - 4 + 1)
+    want = 2 * (np.arange(qy * qx) // qx)
+    assert np.abs(rows - want).mean() < 4.0       # within a texel's height of the same scale
+    with pytest.raises(ValueError, match="double"):     # 24 up-sampled is 48, not 49
+        OS.synthesize_pyramid_rgbs(Z, sigma, 0.0, 49, 49, [8, 4], 1, u)
