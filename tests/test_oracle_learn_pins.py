@@ -104,3 +104,48 @@ def test_kmeans_pp_picks_distinct_points(oracle_lib):
     assert idx[0] == int(u[0] * 50)
     assert len(set(idx.tolist())) == 50
     np.testing.assert_array_equal(C, Y[idx])
+
+
+def test_kmeans_empty_clusters_reseed_with_largest_cost_unused_points(oracle_lib):
+    """Reading c-17: a cluster left without members takes the point of largest assignment cost
+    not yet used in the same update (smallest index on ties), so two empty clusters take the
+    two costliest points in cost order.  Hand-built 1-D case: centroids 0, 10, 1000 and 2000 over
+    the points 0, 0.1, 10, 10.2 and 50 leave clusters 2 and 3 empty."""
+    Y = np.array([[0.0], [0.1], [10.0], [10.2], [50.0]])
+    C0 = np.array([[0.0], [10.0], [1000.0], [2000.0]])
+    a, cost = oracle.kmeans_assign(Y, C0)
+    np.testing.assert_array_equal(a, [0, 0, 1, 1, 1])
+    np.testing.assert_allclose(cost, [0.0, 0.01, 0.0, 0.04, 1600.0], rtol=1e-12, atol=1e-15)
+    C, cnt = oracle.kmeans_update(Y, a, 4, cost)
+    np.testing.assert_array_equal(cnt, [2, 3, 0, 0])
+    assert C[0, 0] == pytest.approx(0.05, rel=1e-14)
+    assert C[1, 0] == pytest.approx((10.0 + 10.2 + 50.0) / 3, rel=1e-14)
+    assert C[2, 0] == 50.0           # largest cost, 1600
+    assert C[3, 0] == 10.2           # the next largest unused, 0.04 (not 50 again)
+    # equal costs: the smallest index among the unused points
+    Y2 = np.array([[0.0], [2.0], [4.0], [6.0]])
+    C2 = np.array([[1.0], [5.0], [100.0]])
+    a2, cost2 = oracle.kmeans_assign(Y2, C2)
+    np.testing.assert_array_equal(a2, [0, 0, 1, 1])
+    assert np.all(cost2 == 1.0)
+    C2n, cnt2 = oracle.kmeans_update(Y2, a2, 3, cost2)
+    assert cnt2[2] == 0 and C2n[2, 0] == 0.0
+    # without costs an empty cluster keeps no re-seed (stays at zero in the fresh array)
+    C3, _ = oracle.kmeans_update(Y, a, 4)
+    assert C3[2, 0] == 0.0 and C3[3, 0] == 0.0
+
+
+def test_kmeans_duplicate_points_empty_a_cluster_and_lloyd_reseeds(oracle_lib):
+    """Two distinct values and k = 3: after k-means++ has taken both, every distance is 0 and its
+    third pick lands on a duplicate, whose cluster loses every tie to the lower id and is empty.
+    Lloyd then re-seeds it with the unused point of largest cost (all costs 0: the smallest
+    index), which here is point 0, a duplicate again -- so the cluster stays empty and the run
+    stops when the assignment repeats."""
+    Y = np.array([[0.0, 0.0]] * 4 + [[3.0, 4.0]] * 4)
+    u = np.array([0.0, 0.5, 0.99])
+    Cpp, idx = oracle.kmeans_pp(Y, 3, u)
+    assert idx[0] == 0 and Y[idx[1]].tolist() == [3.0, 4.0]
+    C, a, hist = oracle.kmeans(Y, 3, u, iters=10)
+    np.testing.assert_array_equal(np.bincount(a, minlength=3)[:2], [4, 4])
+    assert np.sum(a == 2) == 0
+    assert hist[-1] == 0.0

@@ -301,6 +301,46 @@ def test_downsample_preserves_constants_and_ramps(oracle_lib):
     assert o[3, 5, 0] == pytest.approx(1 / 256)
 
 
+@pytest.mark.parametrize("H", [8, 9])
+def test_downsample_border_mirrors_without_edge_repeat(oracle_lib, H):
+    """Reading c-9 of section 2.1's coarse-to-fine step at the border: index -1 maps to 1 and H to
+    H-2 (the edge sample is not repeated).  Hand-computed taps of the 1-D binomial [1 4 6 4 1]/16
+    for an impulse on the first and on the last row, even and odd H: an edge-repeating or clamping
+    border gives 10/16 or 11/16 at the first output row instead of 6/16, and moves the weights of
+    the last row."""
+    W = 6
+    top = np.zeros((H, W, 3))
+    top[0] = 1.0                     # impulse on row 0 (constant along x, so only the rows count)
+    o = oracle.downsample2(top)
+    assert o.shape == ((H + 1) // 2, (W + 1) // 2, 3)
+    # out row 0 reads rows -2..2 -> 2 1 0 1 2: row 0 only at the centre tap
+    assert o[0, 1, 0] == pytest.approx(6 / 16, abs=1e-15)
+    # out row 1 reads rows 0..4: row 0 at the first tap
+    assert o[1, 1, 0] == pytest.approx(1 / 16, abs=1e-15)
+    assert np.all(o[2:] == 0.0)
+    bot = np.zeros((H, W, 3))
+    bot[H - 1] = 1.0                 # impulse on the last row
+    o = oracle.downsample2(bot)
+    if H == 8:
+        # out row 3 reads rows 4 5 6 7 8 -> 4 5 6 7 6: row 7 at the fourth tap only
+        assert o[3, 1, 0] == pytest.approx(4 / 16, abs=1e-15)
+        assert o[2, 1, 0] == 0.0     # rows 2..6
+    else:
+        # out row 4 reads rows 6 7 8 9 10 -> 6 7 8 7 6: row 8 at the centre tap only
+        assert o[4, 1, 0] == pytest.approx(6 / 16, abs=1e-15)
+        # out row 3 reads rows 4..8: row 8 at the last tap
+        assert o[3, 1, 0] == pytest.approx(1 / 16, abs=1e-15)
+    # the corner of a 2-D impulse: both directions at the centre tap
+    cor = np.zeros((H, H, 3))
+    cor[0, 0] = 1.0
+    assert oracle.downsample2(cor)[0, 0, 2] == pytest.approx(36 / 256, abs=1e-15)
+    cor[0, 0] = 0.0
+    cor[H - 1, H - 1] = 1.0
+    want = (4 / 16) ** 2 if H == 8 else (6 / 16) ** 2
+    last = (H + 1) // 2 - 1
+    assert oracle.downsample2(cor)[last, last, 1] == pytest.approx(want, abs=1e-15)
+
+
 def test_upsample_bilinear(oracle_lib):
     H = W = 6
     yy, xx = np.mgrid[0:H, 0:W].astype(float)
