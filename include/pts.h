@@ -351,9 +351,12 @@ pts_status irls_weights(const float *dist2, int Q, float r, float delta, float *
  * Same weights and energy as irls_weights (the energy may differ in the last
  * bits: the partial sums are grouped differently).  Limits and behaviour:
  *   Q           at most 8,388,608; larger Q returns PTS_ERR_INVALID_ARG;
- *   first call  on each device looks up the array's device address
- *               (cudaGetSymbolAddress) with that device current; make that
- *               first call before any stream capture;
+ *   first call  in each CUDA context (each device's primary context, or a
+ *               context the caller made current) looks up the array's
+ *               device address (cudaGetSymbolAddress) and caches it under
+ *               that context's id, so a device reset or a second context
+ *               gets a fresh lookup; make that first call before any stream
+ *               capture;
  *   sharing     all calls share the one array, which keeps the previous
  *               call's contents; each call clears the counter it needs, but
  *               calls that overlap on the GPU (for example on two streams)
@@ -497,10 +500,19 @@ typedef struct pts_batch_s *pts_batch; /* opaque, owned by the library */
  * tensor-core search's exemplar split per job shape by timing the candidates (cached per
  * process), then captures all jobs' iterations into one CUDA graph, jobs spread round-robin
  * over n_streams (1..64) forked streams.  The job structs are copied; outputs and energy arrays
- * stay the caller's.  Synchronises `stream`.  Jobs' outputs are searched (not modified) here. */
+ * stay the caller's.  Synchronises `stream`.  Jobs' outputs are searched (not modified) here.
+ * Each index's own exemplar split (pts_index_set_tc_parts) is left as the caller had it.
+ * Lifetime: the graph holds raw device pointers into every job's index (its tables and the
+ * workspace its searches use), its output and its energy array.  Keep them all alive and do not
+ * move them while the batch may run: a search on a job's index that needs larger or other
+ * buffers (a bigger output, another mode, a trained proposal) reallocates them, and after that,
+ * or after pts_index_destroy of a job's index, pts_batch_run returns PTS_ERR_INVALID_ARG; create
+ * the batch again.  Outputs and energy arrays are the caller's to keep in place. */
 pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r, float delta, int n_streams,
                             int tune, void *stream, pts_batch *out);
-/* Replays the batch's graph on `stream` (asynchronous): every job runs from its current output. */
+/* Replays the batch's graph on `stream` (asynchronous): every job runs from its current output.
+ * PTS_ERR_INVALID_ARG, with nothing launched, if a job's index was destroyed or had buffers
+ * reallocated since pts_batch_create (see above). */
 pts_status pts_batch_run(pts_batch batch, void *stream);
 /* The one-call form: pts_batch_create (8 streams at most, autotuned), one pts_batch_run,
  * pts_batch_destroy.  Synchronises `stream`; returns the first error of the three, else the

@@ -9,6 +9,7 @@
 // the graph.  Energies go to device arrays so the graph has no host copy or synchronisation.
 #include <algorithm>
 #include <map>
+#include <string>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -23,6 +24,9 @@ struct pts_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long launches = 0;
+    // each job's index generation when the graph was captured: the graph holds raw pointers into
+    // the index's tables and workspace, so a run is refused once any of them has moved
+    std::vector<unsigned long long> gens;
 };
 
 namespace pts {
@@ -36,24 +40,30 @@ int job_queries(const pts_job &j) {
     return ((j.Ho - w) / j.stride + 1) * ((j.Wo - w) / j.stride + 1);
 }
 
+// A CUDA event destroyed with its scope (so an early error return leaks nothing).
+struct ScopedEvent {
+    cudaEvent_t e = nullptr;
+    ~ScopedEvent() {
+        if (e) cudaEventDestroy(e);
+    }
+};
+
 // Times `reps` searches of the job's image with the given exemplar split (ms per search).
 pts_status time_search(const pts_job &j, int parts, int reps, cudaStream_t st, float *ms) {
     pts_index idx = j.index;
     Workspace &ws = idx->ws;
     idx->tc_parts_override = parts;
     PTS_TRY(nn_search_impl(idx, j.output, j.Ho, j.Wo, j.stride, j.mode, ws.nn.ptr, ws.d2.ptr, st));
-    cudaEvent_t a, b;
-    PTS_CUDA_TRY(cudaEventCreate(&a));
-    PTS_CUDA_TRY(cudaEventCreate(&b));
-    PTS_CUDA_TRY(cudaEventRecord(a, st));
+    ScopedEvent a, b;
+    PTS_CUDA_TRY(cudaEventCreate(&a.e));
+    PTS_CUDA_TRY(cudaEventCreate(&b.e));
+    PTS_CUDA_TRY(cudaEventRecord(a.e, st));
     for (int k = 0; k < reps; ++k)
         PTS_TRY(nn_search_impl(idx, j.output, j.Ho, j.Wo, j.stride, j.mode, ws.nn.ptr, ws.d2.ptr, st));
-    PTS_CUDA_TRY(cudaEventRecord(b, st));
-    PTS_CUDA_TRY(cudaEventSynchronize(b));
+    PTS_CUDA_TRY(cudaEventRecord(b.e, st));
+    PTS_CUDA_TRY(cudaEventSynchronize(b.e));
     float t = 0.0f;
-    PTS_CUDA_TRY(cudaEventElapsedTime(&t, a, b));
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    PTS_CUDA_TRY(cudaEventElapsedTime(&t, a.e, b.e));
     *ms = t / reps;
     return PTS_OK;
 }
@@ -119,6 +129,9 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
     for (int k = 0; k < n_jobs; ++k) {
         const pts_job &j = jobs[k];
         if (!j.index || !j.output || !j.energy) return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: null job field");
+        unsigned long long g = 0;
+        if (!index_generation(j.index, &g))
+            return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a job's index is not a live index");
         if (j.mode < PTS_EXACT_F32 || j.mode > PTS_PROPOSAL || j.mode == PTS_PROPOSAL)
             return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: job mode must be exact, f16 or fp8");
         PTS_TRY(check_grid_public(j.Ho, j.Wo, j.index->w, j.stride, "pts_batch_create"));
@@ -133,7 +146,14 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
     b->iters = iters;
     b->r = r;
     b->delta = delta;
+    // the autotuner sets each index's split for the capture; the caller's settings come back after
+    std::vector<int> saved_parts(n_jobs);
+    for (int k = 0; k < n_jobs; ++k) saved_parts[k] = jobs[k].index->tc_parts_override;
+    auto restore_parts = [&]() {
+        for (int k = 0; k < n_jobs; ++k) jobs[k].index->tc_parts_override = saved_parts[k];
+    };
     auto fail = [&](pts_status s) {
+        restore_parts();
         pts_batch_destroy(b);
         return s;
     };
@@ -221,12 +241,25 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
         if (x) cudaStreamDestroy(x);
     if (cap) cudaStreamDestroy(cap);
     if (s != PTS_OK) return fail(s);
+    restore_parts();
+    b->gens.resize(b->jobs.size());
+    for (size_t k = 0; k < b->jobs.size(); ++k)
+        if (!index_generation(b->jobs[k].index, &b->gens[k]))
+            return fail(set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a job's index is not a live index"));
     *out = b;
     return PTS_OK;
 }
 
 pts_status pts_batch_run(pts_batch b, void *stream) {
     if (!b || !b->exec) return set_error(PTS_ERR_INVALID_ARG, "pts_batch_run: no batch");
+    for (size_t k = 0; k < b->jobs.size(); ++k) {
+        unsigned long long g = 0;
+        if (!index_generation(b->jobs[k].index, &g) || g != b->gens[k])
+            return set_error(PTS_ERR_INVALID_ARG,
+                             "pts_batch_run: job " + std::to_string(k) +
+                                 "'s index was destroyed or its buffers moved since pts_batch_create; create the "
+                                 "batch again");
+    }
     count_launches((int)b->launches);
     PTS_CUDA_TRY(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)));
     return PTS_OK;

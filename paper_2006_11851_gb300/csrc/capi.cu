@@ -314,6 +314,48 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
 }
 
 
+// ---------------------------------------------------------------------------
+// registry of live indices and their buffer generations
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_registry_mu;
+std::vector<pts_index> g_live_indices;
+unsigned long long g_generation = 0;
+}  // namespace
+
+void register_index(pts_index idx) {
+    std::lock_guard<std::mutex> lk(g_registry_mu);
+    idx->generation = ++g_generation;
+    g_live_indices.push_back(idx);
+}
+
+void unregister_index(pts_index idx) {
+    std::lock_guard<std::mutex> lk(g_registry_mu);
+    g_live_indices.erase(std::remove(g_live_indices.begin(), g_live_indices.end(), idx), g_live_indices.end());
+}
+
+bool index_generation(pts_index idx, unsigned long long *gen) {
+    std::lock_guard<std::mutex> lk(g_registry_mu);
+    for (pts_index p : g_live_indices)
+        if (p == idx) {
+            *gen = p->generation;
+            return true;
+        }
+    return false;
+}
+
+void note_buffer_moved(const void *buf) {
+    const char *b = static_cast<const char *>(buf);
+    std::lock_guard<std::mutex> lk(g_registry_mu);
+    for (pts_index p : g_live_indices) {
+        const char *lo = reinterpret_cast<const char *>(p);
+        if (b >= lo && b < lo + sizeof(pts_index_s)) {
+            p->generation = ++g_generation;
+            return;
+        }
+    }
+}
+
 pts_status set_error(pts_status s, const std::string &msg) {
     g_last_error = msg;
     return s;
@@ -439,6 +481,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad exemplar size");
     cudaStream_t st = as_stream(stream);
     pts_index idx = new pts_index_s();
+    register_index(idx);
     auto fail = [&](pts_status s) {
         pts_index_destroy(idx);
         return s;
@@ -556,6 +599,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
 
 void pts_index_destroy(pts_index idx) {
     if (!idx) return;
+    unregister_index(idx);
     cudaDeviceSynchronize();
     Workspace &ws = idx->ws;
     ws.qcoord.release();

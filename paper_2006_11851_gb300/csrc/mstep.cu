@@ -291,10 +291,16 @@ void launch_upsample2(const float *in, int H, int W, float *out, cudaStream_t st
 // irls_weights_noalloc: the IRLS reduction with its scratch in a fixed array
 // compiled into the library, for callers that cannot allocate device memory.
 // Scratch: one double per block of kNoAllocPerBlock distances plus the
-// completion ticket.  The array's device address is looked up once per device
-// (cudaGetSymbolAddress) by the first call made with that device current.
+// completion ticket.  The array's device address belongs to a CUDA context: it is
+// looked up (cudaGetSymbolAddress) by the first call made in each context and
+// cached under the context's process-unique id (cuCtxGetId), so a reset device
+// or a second context on the same device gets its own lookup.
 // ---------------------------------------------------------------------------
+#include <cuda.h>
+
 #include <mutex>
+#include <utility>
+#include <vector>
 
 namespace pts {
 namespace {
@@ -303,9 +309,27 @@ constexpr int kNoAllocPerBlock = 256 * 8;
 constexpr size_t kNoAllocTicketOffset = kNoAllocMaxBlocks * sizeof(double);
 static __device__ __align__(256) unsigned char g_irls_scratch[kNoAllocTicketOffset + 256];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
+std::vector<std::pair<unsigned long long, void *>> g_noalloc_addr;  // (context id, array address)
+
+// driver entry points through the runtime, so the library does not link libcuda itself
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+bool load_ctx_entry_points() {
+    if (g_ctx_get_current && g_ctx_get_id) return true;
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+        return false;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(b);
+    return true;
+}
 }  // namespace
 }  // namespace pts
 
@@ -318,20 +342,32 @@ extern "C" pts_status irls_weights_noalloc(const float *dist2, int Q, float r, f
     if ((long)Q > (long)kNoAllocMaxBlocks * kNoAllocPerBlock)
         return set_error(PTS_ERR_INVALID_ARG,
                          "irls_weights_noalloc: Q exceeds the fixed scratch limit of 8388608 distances");
-    int dev = 0;
-    PTS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices)
-        return set_error(PTS_ERR_UNSUPPORTED, "irls_weights_noalloc: device ordinal above 63");
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        if (!load_ctx_entry_points())
+            return set_error(PTS_ERR_CUDA, "irls_weights_noalloc: driver context entry points unavailable");
+        CUcontext ctx = nullptr;
+        unsigned long long ctx_id = 0;
+        if (g_ctx_get_current(&ctx) != CUDA_SUCCESS)
+            return set_error(PTS_ERR_CUDA, "irls_weights_noalloc: cuCtxGetCurrent failed");
+        if (!ctx) {
+            // no context current yet: a runtime call makes the device's primary context current
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_irls_scratch);
             if (e != cudaSuccess) return cuda_error(e, "irls_weights_noalloc: cudaGetSymbolAddress");
-            g_noalloc_addr[dev] = p;
+            if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx)
+                return set_error(PTS_ERR_CUDA, "irls_weights_noalloc: no current CUDA context");
         }
-        base = g_noalloc_addr[dev];
+        if (g_ctx_get_id(ctx, &ctx_id) != CUDA_SUCCESS)
+            return set_error(PTS_ERR_CUDA, "irls_weights_noalloc: cuCtxGetId failed");
+        for (const auto &e : g_noalloc_addr)
+            if (e.first == ctx_id) base = e.second;
+        if (!base) {
+            cudaError_t e = cudaGetSymbolAddress(&base, g_irls_scratch);
+            if (e != cudaSuccess) return cuda_error(e, "irls_weights_noalloc: cudaGetSymbolAddress");
+            g_noalloc_addr.emplace_back(ctx_id, base);
+        }
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     double *partial = static_cast<double *>(base);

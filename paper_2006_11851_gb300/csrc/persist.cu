@@ -123,6 +123,59 @@ pts_status check_header(const Header &h) {
     return PTS_OK;
 }
 
+// The integer tables the kernels index with (cluster lists, the tree's links and leaf ranges)
+// are checked on the host before anything reaches the device, so a damaged file cannot make a
+// kernel read or write outside its buffers.
+pts_status check_tables(const Header &h, const std::vector<Section> &secs,
+                        const std::vector<std::vector<unsigned char>> &data) {
+    auto bad = [](const char *what) { return set_error(PTS_ERR_INVALID_ARG, std::string("index file table: ") + what); };
+    auto table = [&](const char (&t)[5]) -> const int32_t * {
+        for (size_t i = 0; i < secs.size(); ++i)
+            if (secs[i].tag == tag(t)) return reinterpret_cast<const int32_t *>(data[i].data());
+        return nullptr;
+    };
+    const long N = h.N;
+    auto is_permutation = [&](const int32_t *p) {
+        std::vector<unsigned char> seen((size_t)N, 0);
+        for (long i = 0; i < N; ++i) {
+            if (p[i] < 0 || p[i] >= N || seen[(size_t)p[i]]) return false;
+            seen[(size_t)p[i]] = 1;
+        }
+        return true;
+    };
+    if (h.prop_ready) {
+        const int C = h.prop_C;
+        const int32_t *assign = table("PASG"), *cnt = table("PCNT"), *off = table("POFF"), *mem = table("PMEM");
+        if (!assign || !cnt || !off || !mem) return bad("proposal tables missing");
+        if (off[0] != 0 || off[C] != N) return bad("cluster offsets do not run from 0 to N");
+        for (int c = 0; c < C; ++c)
+            if (off[c + 1] < off[c] || cnt[c] != off[c + 1] - off[c]) return bad("cluster offsets or sizes");
+        for (long i = 0; i < N; ++i)
+            if (assign[i] < 0 || assign[i] >= C) return bad("a window's cluster is out of range");
+        if (!is_permutation(mem)) return bad("cluster members are not a permutation of the windows");
+        for (int c = 0; c < C; ++c)
+            for (int i = off[c]; i < off[c + 1]; ++i)
+                if (assign[mem[i]] != c) return bad("a cluster lists a window of another cluster");
+    }
+    if (h.tree_ready) {
+        const int32_t *child = table("TCHI"), *lb = table("TLBG"), *le = table("TLEN"), *perm = table("TPRM");
+        if (!child || !lb || !le || !perm) return bad("tree tables missing");
+        for (long node = 0; node < h.tree_internal; ++node)
+            for (int k = 0; k < kTreeBranch; ++k) {
+                const int32_t c = child[node * kTreeBranch + k];
+                // internal children come after their parent (nodes are numbered level by level),
+                // which also rules out cycles
+                const bool internal = c >= 0 && c > node && c < h.tree_internal;
+                const bool leaf = c <= -2 && (long)(-(long)c - 2) < h.tree_leaves;
+                if (c != -1 && !internal && !leaf) return bad("a tree child reference is out of range");
+            }
+        for (long l = 0; l < h.tree_leaves; ++l)
+            if (lb[l] < 0 || lb[l] > le[l] || le[l] > N) return bad("a tree leaf range is out of range");
+        if (!is_permutation(perm)) return bad("the tree's window order is not a permutation");
+    }
+    return PTS_OK;
+}
+
 struct File {
     FILE *f = nullptr;
     ~File() {
@@ -251,13 +304,29 @@ pts_status pts_index_load(const char *path, pts_index *out) {
     if (fstat(fileno(f.f), &stt) != 0 || (uint64_t)stt.st_size != expect)
         return set_error(PTS_ERR_INVALID_ARG, "pts_index_load: file length does not match its header");
 
+    // read and check every section on the host before any device work
+    std::vector<std::vector<unsigned char>> data(secs.size());
+    for (size_t i = 0; i < secs.size(); ++i) {
+        Section c{0, 0, 0};
+        PTS_TRY(read_all(f.f, &c.tag, 4));
+        PTS_TRY(read_all(f.f, &c.elem, 4));
+        PTS_TRY(read_all(f.f, &c.count, 8));
+        if (c.tag != secs[i].tag || c.elem != secs[i].elem || c.count != secs[i].count)
+            return set_error(PTS_ERR_INVALID_ARG, "pts_index_load: a section does not match the header");
+        data[i].resize((size_t)c.elem * c.count);
+        PTS_TRY(read_all(f.f, data[i].data(), data[i].size()));
+    }
+    PTS_TRY(check_tables(h, secs, data));
+
     pts_index idx = new pts_index_s();
+    register_index(idx);
     auto fail = [&](pts_status st) {
         pts_index_destroy(idx);
         return st;
     };
     if (cudaGetDevice(&idx->device) != cudaSuccess) {
         cudaGetLastError();
+        unregister_index(idx);
         delete idx;
         return set_error(PTS_ERR_CUDA, "pts_index_load: no CUDA device");
     }
@@ -307,20 +376,10 @@ pts_status pts_index_load(const char *path, pts_index *out) {
         if ((s = tr.leaf_end.ensure(h.tree_leaves, "tree leaves")) != PTS_OK) return fail(s);
         if ((s = tr.perm.ensure(h.N, "tree permutation")) != PTS_OK) return fail(s);
     }
-    // read the sections into them
+    // upload the checked sections
     const std::vector<void *> dev = device_tables(idx, h);
-    std::vector<unsigned char> host;
     for (size_t i = 0; i < secs.size(); ++i) {
-        Section c{0, 0, 0};
-        if ((s = read_all(f.f, &c.tag, 4)) != PTS_OK || (s = read_all(f.f, &c.elem, 4)) != PTS_OK ||
-            (s = read_all(f.f, &c.count, 8)) != PTS_OK)
-            return fail(s);
-        if (c.tag != secs[i].tag || c.elem != secs[i].elem || c.count != secs[i].count)
-            return fail(set_error(PTS_ERR_INVALID_ARG, "pts_index_load: a section does not match the header"));
-        const size_t bytes = (size_t)c.elem * c.count;
-        host.resize(bytes);
-        if ((s = read_all(f.f, host.data(), bytes)) != PTS_OK) return fail(s);
-        cudaError_t e = cudaMemcpy(dev[i], host.data(), bytes, cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMemcpy(dev[i], data[i].data(), data[i].size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_error(e, "pts_index_load: upload table"));
     }
     if (cudaMemset(idx->status.ptr, 0, sizeof(int)) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "status"));

@@ -60,6 +60,10 @@ inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 // be reading it when the allocator gives it out again.
 pts_status dev_alloc(void **p, size_t bytes, const char *what);
 void dev_free(void *p);
+// Called when the device buffer object at `buf` gets new memory: if the object lies inside a
+// live index, that index's generation advances (a captured batch graph that holds the old
+// pointer is then refused).  capi.cu keeps the registry of live indices.
+void note_buffer_moved(const void *buf);
 
 // A buffer frees itself when it goes out of scope (so scratch buffers are returned on every
 // path, early error returns included); it cannot be copied, so no two owners share a pointer.
@@ -76,6 +80,7 @@ struct DevBuf {
         if (ptr) dev_free(ptr);
         ptr = nullptr;
         count = 0;
+        note_buffer_moved(this);
         if (n == 0) n = 1;
         void *p = nullptr;
         PTS_TRY(dev_alloc(&p, n * sizeof(T), what));
@@ -84,7 +89,10 @@ struct DevBuf {
         return PTS_OK;
     }
     void release() {
-        if (ptr) dev_free(ptr);
+        if (ptr) {
+            dev_free(ptr);
+            note_buffer_moved(this);
+        }
         ptr = nullptr;
         count = 0;
     }
@@ -215,7 +223,16 @@ struct pts_index_s {
     int tc_parts_override = 0;  // exemplar split of the tensor-core search chosen by the autotuner
     pts::ProposalState prop;
     pts::KmTree tree;
+    unsigned long long generation = 0;  // advances whenever one of the index's buffers moves
 };
+
+namespace pts {
+// Registry of live indices (capi.cu): register right after construction, unregister before the
+// buffers are released.  index_generation returns false for an index that is not live.
+void register_index(pts_index idx);
+void unregister_index(pts_index idx);
+bool index_generation(pts_index idx, unsigned long long *gen);
+}  // namespace pts
 
 namespace pts {
 

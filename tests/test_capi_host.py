@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -114,23 +115,51 @@ def test_allocator_registration_on_host(libpts):
 _HEADER = "<8sII16ifddiifiiii"
 
 
-def _index_file(**over):
+def _index_file(tables=None, **over):
     """Bytes of a consistent index file for a 12 x 12 exemplar, w = 4, d = 8, d_fast = 16 (every
-    table zero), with header fields replaced by `over`."""
+    table zero), with header fields replaced by `over`.  `tables` adds a trained proposal
+    ("prop": C = 4 clusters) and/or a k-means tree ("tree": a root with four leaves), given as
+    {tag: int32 array} for their integer tables; tables left out are valid ones."""
     import struct
-    f = dict(He=12, We=12, w=4, D=48, N=81, d=8, da=12, d_fast=16, da_fast=20, ny=9, nx=9, ntiles=1,
+    tables = tables or {}
+    N, C = 81, 4
+    f = dict(He=12, We=12, w=4, D=48, N=N, d=8, da=12, d_fast=16, da_fast=20, ny=9, nx=9, ntiles=1,
              ktc=32, kf8=32, eig_iters=5, tc_parts=0, unorm2_max=1.0, var=0.9, eig_top=1.0)
     f.update(over)
+    prop, tree = "prop" in tables, "tree" in tables
     head = struct.pack(_HEADER, over.get("magic", b"PTSINDEX"), over.get("version", 1),
                        over.get("order", 0x01020304), f["He"], f["We"], f["w"], f["D"], f["N"], f["d"], f["da"],
                        f["d_fast"], f["da_fast"], f["ny"], f["nx"], f["ntiles"], f["ktc"], f["kf8"],
-                       f["eig_iters"], f["tc_parts"], f["unorm2_max"], f["var"], f["eig_top"], 0, 0, 0.0, 0, 0, 0, 0)
+                       f["eig_iters"], f["tc_parts"], f["unorm2_max"], f["var"], f["eig_top"],
+                       int(prop), C if prop else 0, 1.2 if prop else 0.0, int(tree), 1 if tree else 0,
+                       4 if tree else 0, 1 if tree else 0)
     tcr = 256  # one tensor-core tile of 256 windows
     secs = [(b"EXEM", 4, 12 * 12 * 3), (b"EXE4", 16, 144), (b"MEAN", 4, 48), (b"BASI", 4, 128 * 48),
             (b"BAST", 4, 48 * 128), (b"EIGV", 8, 128), (b"ETIL", 4, 12 * 128), (b"EROW", 4, 81 * 12),
             (b"ENRM", 4, 128), (b"EFUL", 4, 64 * 128), (b"EFST", 4, 20 * 128), (b"ETCH", 2, tcr * 32),
             (b"ETC8", 1, tcr * 32), (b"F8SC", 4, 17), (b"UMAX", 4, 1)]
-    body = b"".join(t + struct.pack("<IQ", e, c) + bytes(e * c) for t, e, c in secs)
+    ints = {}
+    bounds = np.array([0, 20, 40, 60, N], np.int32)          # four ranges of windows
+    if prop:
+        assign = np.repeat(np.arange(C, dtype=np.int32), np.diff(bounds))
+        ints.update({b"PASG": assign, b"PCNT": np.diff(bounds).astype(np.int32), b"POFF": bounds,
+                     b"PMEM": np.arange(N, dtype=np.int32)})
+        ints.update(tables["prop"])
+        secs += [(b"PCEN", 4, C * 8), (b"PASG", 4, N), (b"PCNT", 4, C), (b"POFF", 4, C + 1), (b"PMEM", 4, N),
+                 (b"PMED", 4, C), (b"PETC", 2, tcr * 32), (b"PMLP", 4, 256 * 64 + 256 + 256 * 256 + 256 + C * 256 + C)]
+    if tree:
+        ints.update({b"TCHI": np.array([-2, -3, -4, -5], np.int32), b"TLBG": bounds[:4], b"TLEN": bounds[1:],
+                     b"TPRM": np.arange(N, dtype=np.int32)})
+        ints.update(tables["tree"])
+        secs += [(b"TCEN", 4, 4 * 8), (b"TCHI", 4, 4), (b"TLBG", 4, 4), (b"TLEN", 4, 4), (b"TPRM", 4, N)]
+
+    def payload(t, e, c):
+        if t in ints:
+            a = np.ascontiguousarray(ints[t], dtype=np.int32)
+            assert a.size == c
+            return a.tobytes()
+        return bytes(e * c)
+    body = b"".join(t + struct.pack("<IQ", e, c) + payload(t, e, c) for t, e, c in secs)
     return head + body
 
 
@@ -198,3 +227,53 @@ def test_allocator_returning_null_fails_the_build_cleanly(libpts):
         assert libpts.pts_live_allocations() == 0
     finally:
         assert libpts.pts_set_allocator(None, None, None) == 0
+
+
+def test_index_file_integer_tables_checked_on_host(libpts, tmp_path):
+    """Cluster lists and tree links are indices the search kernels follow: one damaged value in
+    a saved file must be refused on the host (PTS_ERR_INVALID_ARG) before any device work; the
+    same file undamaged passes every check and reaches the device (which fails without a GPU)."""
+    libpts.pts_last_error.restype = ctypes.c_char_p
+    libpts.pts_index_load.argtypes = [ctypes.c_char_p, ctypes.c_void_p]
+    libpts.pts_index_destroy.argtypes = [ctypes.c_void_p]
+    out = ctypes.c_void_p()
+
+    def load(data):
+        p = tmp_path / "idx.bin"
+        p.write_bytes(data)
+        rc = libpts.pts_index_load(str(p).encode(), ctypes.byref(out))
+        return rc, libpts.pts_last_error().decode()
+
+    perm_dup = np.arange(81, dtype=np.int32)
+    perm_dup[5] = 6
+    perm_big = np.arange(81, dtype=np.int32)
+    perm_big[80] = 81
+    bad_assign = np.repeat(np.arange(4, dtype=np.int32), [20, 20, 20, 21])
+    bad_assign[3] = 4
+    moved = np.repeat(np.arange(4, dtype=np.int32), [20, 20, 20, 21])
+    moved[3] = 1
+    cases = [
+        ({"tree": {b"TCHI": np.array([-2, -3, 7, -5], np.int32)}}, "child reference"),       # no node 7
+        ({"tree": {b"TCHI": np.array([-2, 0, -4, -5], np.int32)}}, "child reference"),       # a cycle
+        ({"tree": {b"TCHI": np.array([-2, -3, -4, -6], np.int32)}}, "child reference"),      # leaf 4 of 4
+        ({"tree": {b"TLEN": np.array([20, 40, 60, 82], np.int32)}}, "leaf range"),
+        ({"tree": {b"TLBG": np.array([0, 41, 40, 60], np.int32)}}, "leaf range"),
+        ({"tree": {b"TPRM": perm_dup}}, "permutation"),
+        ({"tree": {b"TPRM": perm_big}}, "permutation"),
+        ({"prop": {b"POFF": np.array([0, 20, 40, 60, 80], np.int32)}}, "0 to N"),
+        ({"prop": {b"POFF": np.array([0, 40, 20, 60, 81], np.int32)}}, "offsets or sizes"),
+        ({"prop": {b"PCNT": np.array([20, 20, 20, 20], np.int32)}}, "offsets or sizes"),
+        ({"prop": {b"PASG": bad_assign}}, "out of range"),
+        ({"prop": {b"PMEM": perm_dup}}, "permutation"),
+        ({"prop": {b"PASG": moved}}, "another cluster"),
+    ]
+    for tables, msg in cases:
+        rc, err = load(_index_file(tables))
+        assert rc == -1 and msg in err, (tables, msg, rc, err)
+        assert not out.value
+    for tables in ({"tree": {}}, {"prop": {}}, {"tree": {}, "prop": {}}):
+        rc, err = load(_index_file(tables))
+        if rc == 0:  # pragma: no cover - only where a GPU is present
+            libpts.pts_index_destroy(out)
+        else:
+            assert rc == -2 and "CUDA" in err, (tables, rc, err)
