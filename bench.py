@@ -49,7 +49,8 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 
 WORKLOAD = {
     "workload": "plain method at scale: exemplar 256x256 (shrink 4x), 3-level pyramid, "
-                "windows 32/16/8, outputs 128/256/512, PCA 64, stride 2, 5 EM iterations/level",
+                "windows 32/16/8, outputs 128/256/512, PCA 64 (exact-mode bound; the tensor-core search "
+                "ranks by d_fast = 124 components), stride 2, 5 EM iterations/level",
     "exemplar": 256, "shrink": 4.0, "levels": 3, "windows": [32, 16, 8], "outputs": [128, 256, 512],
     "d": 64, "iters": 5, "r": 2.0, "stride": 2,
 }
@@ -250,6 +251,111 @@ def _peaks():
         return 1900.0, 1700.0, "fallback"
 
 
+def exact_route_counts(pts, pidx, x0, cfg):
+    """One exact-mode synthesis of the workload replayed search by search (the same calls
+    synthesize_level makes: search, IRLS weights, M-step; a last search), returning per level the
+    queries the full-dimension pass took, the queries certified from the PCA bound and all
+    queries, summed over the level's searches."""
+    X = x0.clone()
+    rng, cert, allq = [], [], []
+    for lev, ix in enumerate(pidx.indices):
+        r = c = a = 0
+        for t in range(cfg["iters"] + 1):
+            nn, d2 = pts.nn_search(ix, X, cfg["stride"], "exact")
+            st = ix.search_stats()
+            r, c, a = r + st["range_queries"], c + st["certified"], a + st["queries"]
+            if t < cfg["iters"]:
+                wts, _ = pts.irls_weights(d2, cfg["r"], 1e-3)
+                H, W, _ = X.shape
+                X = pts.m_step(ix, nn, wts, H, W, cfg["stride"])
+        rng.append(r)
+        cert.append(c)
+        allq.append(a)
+        if lev + 1 < pidx.levels:
+            X = pts.upsample2(X)
+    return {"range_queries": rng, "certified": cert, "queries": allq}
+
+
+PRECISION_FORM = {
+    "workload": "precision form: exemplar 512x512 (shrink 4x), output 1024x1024, window 16x16 (D = 768), "
+                "PCA 64 (exact-mode bound; the tensor-core searches rank by d_fast = 124 components), stride 2, "
+                "one level, 5 EM iterations + final search",
+    "exemplar": 512, "shrink": 4.0, "w": 16, "Ho": 1024, "d": 64, "iters": 5, "r": 2.0, "stride": 2,
+}
+
+
+def time_precision_form(pts, P, L, dev, stream, flush, steps, warmup, bf16_burst, peak_src):
+    """queries/s of every search mode on the precision-form workload (one level), the FP16/FP8
+    search's tensor roofline, and each mode's final energy (measured by the certified exact
+    search) against exact mode's on the same seeds."""
+    import ctypes
+
+    import torch
+    cfg = PRECISION_FORM
+    Z = P.synthetic_exemplar(0, cfg["exemplar"], cfg["shrink"])
+    t0 = time.perf_counter()
+    idx = pts.ExemplarIndex(torch.from_numpy(Z).to(dev), cfg["w"], d=cfg["d"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Ho, w, it = cfg["Ho"], cfg["w"], cfg["iters"] + 1
+    Q, N, dfast = idx.num_queries(Ho, Ho, cfg["stride"]), idx.info["N"], idx.info["d_fast"]
+    res = {"config": dict(cfg, N=N, Q=Q, d_fast=dfast, index_build_s=build_s,
+                          l2="flushed between steps (256 MB write)"), "modes": {}}
+
+    def init(seed):
+        return torch.from_numpy(P.random_patch_init(Z, Ho, Ho, w, seed)).to(dev)
+
+    def run(mode, x):
+        pts.synthesize_level_async(idx, x, cfg["iters"], r=cfg["r"], mode=mode, stride=cfg["stride"])
+
+    finals = {}
+    for mode in ("f16", "fp8", "exact"):
+        n, nw = (steps, warmup) if mode != "exact" else (1, 1)
+        for i in range(nw):
+            run(mode, init(i))
+        xs = [init(warmup + i) for i in range(n)]
+        torch.cuda.synchronize()
+        ms = 0.0
+        for x in xs:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run(mode, x)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        idx.device_status()
+        entry = {"value": Q * it * n / (ms / 1000.0), "unit": "queries/s", "ms_per_step": ms / n, "steps": n}
+        if mode != "exact":
+            x = init(warmup)
+            L.pts_profile_enable(1)
+            run(mode, x)
+            torch.cuda.synchronize()
+            tms, cnt = ctypes.c_double(), ctypes.c_longlong()
+            L.pts_profile_read(b"search_tc", ctypes.byref(tms), ctypes.byref(cnt))
+            L.pts_profile_enable(0)
+            pk = bf16_burst * (2.0 if mode == "fp8" else 1.0)
+            ach = 2.0 * (dfast + 1) * N * Q * it / (tms.value / 1000.0) / 1e12
+            entry["roofline"] = {"kernel": "k_search_tc" + ("<FP8>" if mode == "fp8" else ""), "bound": "tensor",
+                                 "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                                 "launches": int(cnt.value),
+                                 "note": f"2(d_fast+1) flops per (query, window) pair, d_fast = {dfast}; peak = "
+                                         f"{'2 x ' if mode == 'fp8' else ''}BF16 burst, {peak_src}"}
+        fin = []
+        for x in xs:
+            _, d2 = pts.nn_search(idx, x, cfg["stride"], "exact")
+            fin.append(float(d2.double().sum()))
+        finals[mode] = fin
+        res["modes"][mode] = entry
+    for mode in ("f16", "fp8"):
+        k = len(finals["exact"])
+        ratios = [a / b for a, b in zip(finals[mode][:k], finals["exact"])]
+        res["modes"][mode]["final_energy_ratio_vs_exact"] = max(ratios)
+        res["modes"][mode]["speedup_vs_exact"] = res["modes"][mode]["value"] / res["modes"]["exact"]["value"]
+    idx.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,6 +372,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries per level for the CPU baseline")
     ap.add_argument("--d-fast", type=int, default=0, help="PCA dimensions of the tensor-core search (0 = library default)")
+    ap.add_argument("--no-precision-form", action="store_true",
+                    help="skip the 512x512 -> 1024x1024, w = 16 precision-form timing (other_configs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -375,12 +483,16 @@ def main():
         timed_run.last_stats = last_stats
         return total_ms, launches, kern, energies, clk.summary()
 
-    total_ms, launches, kern, energies, clocks = timed_run(modes, True)
+    # `value` from a pass with the library's per-kernel event recording off; the kernel shares and
+    # the roofline's kernel time from a second, profiled pass over the same seeds
+    total_ms, launches, _, energies, clocks = timed_run(modes, False)
+    prof_ms, _, kern, _, _ = timed_run(modes, True)
     qps = whole_job_rate(queries_per_step(cfg) * args.steps, world, total_ms)
     if args.mode == "exact":
-        ex_ms, ex_kern, ex_energies = total_ms, kern, energies
+        ex_ms, ex_energies = total_ms, energies
     else:
-        ex_ms, _, ex_kern, ex_energies, _ = timed_run(LEVEL_MODES["exact"], True)
+        ex_ms, _, _, ex_energies, _ = timed_run(LEVEL_MODES["exact"], False)
+    _, _, ex_kern, _, _ = timed_run(LEVEL_MODES["exact"], True)
     exact_qps = whole_job_rate(queries_per_step(cfg) * args.steps, world, ex_ms)
     ratios = [e / x for e, x in zip(energies, ex_energies)]
     other = {}
@@ -422,15 +534,31 @@ def main():
     fma_tf, _ = pts.fp32_fma_peak()
     it = cfg["iters"] + 1
     pca_levels = [(l, ix.info) for l, ix in zip(sizes, pidx.indices) if ix.info["var_retained"] >= PCA_PASS_MIN_VAR]
-    ex_roof = {"kernel": "k_search_pca (FP32 SIMT PCA-space bound GEMM + top-32)", "bound": "alu",
-               "achieved": None, "peak": fma_tf, "unit": "TFLOP/s", "frac": None,
-               "note": "algorithmic 2(d+1) flops per (query, window) pair at the levels that run the PCA pass "
-                       f"(d = {[inf['d'] for _, inf in pca_levels]}); peak = FP32 FMA probe measured in this run "
-                       f"(nominal {PEAK_FP32_TFLOPS:.1f} = 152 SMs x 128 lanes x 2 x 2070 MHz)"}
+    # queries the full-dimension pass took per step: one untimed exact step replayed search by
+    # search through the public API, reading each search's statistics
+    route = exact_route_counts(pts, pidx, init_dev(args.warmup), cfg)
+    full_fl = sum(2.0 * l["D"] * l["N"] * n for l, n in zip(sizes, route["range_queries"]))
+    pca_fl = sum(2.0 * (inf["d"] + 1) * l["N"] * l["Q"] * it for l, inf in pca_levels)
+    ex_roofs = {}
     if "search_topk" in ex_kern and pca_levels:
-        fl = sum(2.0 * (inf["d"] + 1) * l["N"] * l["Q"] * it for l, inf in pca_levels)
-        ach = fl / (ex_kern["search_topk"]["ms_per_step"] / 1000.0) / 1e12
-        ex_roof.update(achieved=ach, frac=ach / fma_tf)
+        ach = pca_fl / (ex_kern["search_topk"]["ms_per_step"] / 1000.0) / 1e12
+        ex_roofs["search_topk"] = {
+            "kernel": "k_search_pca (FP32 SIMT PCA-space bound GEMM + top-32)", "bound": "alu", "achieved": ach,
+            "peak": fma_tf, "unit": "TFLOP/s", "frac": ach / fma_tf,
+            "note": "algorithmic 2(d+1) flops per (query, window) pair at the levels that run the PCA pass "
+                    f"(d = {[inf['d'] for _, inf in pca_levels]}); peak = FP32 FMA probe measured in this run "
+                    f"(nominal {PEAK_FP32_TFLOPS:.1f} = 152 SMs x 128 lanes x 2 x 2070 MHz)"}
+    if "search_full" in ex_kern and full_fl > 0:
+        ach = full_fl / (ex_kern["search_full"]["ms_per_step"] / 1000.0) / 1e12
+        ex_roofs["search_full"] = {
+            "kernel": "k_search_full (FP32 SIMT full-dimension GEMM + top-32)", "bound": "alu", "achieved": ach,
+            "peak": fma_tf, "unit": "TFLOP/s", "frac": ach / fma_tf,
+            "note": "algorithmic 2D flops per (listed query, window) pair, listed queries per step "
+                    f"{route['range_queries']} (coarse to fine); peak = FP32 FMA probe measured in this run"}
+    ex_dom = max((k for k in ex_roofs), key=lambda k: ex_kern[k]["ms_per_step"], default=None)
+    ex_roof = dict(ex_roofs[ex_dom]) if ex_dom else {"kernel": None, "bound": "alu", "achieved": None,
+                                                      "peak": fma_tf, "unit": "TFLOP/s", "frac": None}
+    ex_roof["others"] = {k: v for k, v in ex_roofs.items() if k != ex_dom}
 
     # ---- roofline of the dominant kernel of this mode ----
     bf16_burst, bf16_sust, peak_src = _peaks()
@@ -443,19 +571,20 @@ def main():
         ach = fl / (kern[dom]["ms_per_step"] / 1000.0) / 1e12
         if "fp8" in modes:
             # dense FP8 runs at twice the BF16 rate (nominal 4.5 vs 2.25 PFLOP/s)
-            pk = 2.0 * bf16_sust
+            pk = 2.0 * bf16_burst
             roof.update(bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
                         kernel="k_search_tc<FP8> (E4M3 tcgen05 PCA-space GEMM + top-32)",
-                        note=f"algorithmic 2(d_fast+1) flops per pair, d_fast={dfs}; peak = 2 x BF16 sustained "
+                        note=f"algorithmic 2(d_fast+1) flops per pair, d_fast={dfs}; peak = 2 x BF16 burst "
                              f"({peak_src}) x the nominal FP8/BF16 ratio")
         else:
-            roof.update(bound="tensor", achieved=ach, peak=bf16_sust, unit="TFLOP/s", frac=ach / bf16_sust,
+            roof.update(bound="tensor", achieved=ach, peak=bf16_burst, unit="TFLOP/s", frac=ach / bf16_burst,
                         kernel="k_search_tc (FP16 tcgen05 PCA-space GEMM + top-32)", traffic=_tc_traffic(),
                         note=f"algorithmic 2(d_fast+1) flops per (query, window) pair, d_fast={dfs}; peak = BF16 "
-                             f"sustained (dense FP16 has the BF16 rate), {peak_src}; traffic = DRAM bytes of one "
-                             "fine-level launch (ncu), the algorithmic operand bytes being 32.3 MB")
-    elif dom == "search_topk":
-        roof.update(ex_roof, traffic=None)
+                             f"burst (dense FP16 has the BF16 rate; a step lasts milliseconds), {peak_src}; "
+                             "traffic = DRAM bytes of one fine-level launch (ncu), the algorithmic operand bytes "
+                             "being 32.3 MB")
+    elif dom in ex_roofs and args.mode == "exact":
+        roof.update(ex_roofs[dom], traffic=None)
     elif dom == "search_full" and all(m != "exact" or ix.info["var_retained"] < PCA_PASS_MIN_VAR
                                       for m, ix in zip(modes, pidx.indices)):
         # exact levels without a PCA pass send every query to the full-dimension pass, and the
@@ -469,8 +598,20 @@ def main():
     elif dom is not None:
         roof.update(note="dominant kernel without a roofline model in this script")
 
+    other_cfgs = {}
+    if not args.no_precision_form:
+        other_cfgs["precision_form"] = time_precision_form(pts, P, L, dev, stream, flush, args.steps, args.warmup,
+                                                           bf16_burst, peak_src)
+
+    headline = None
+    if also == "proposal" or args.mode == "proposal":
+        pv = qps if args.mode == "proposal" else other["proposal"]["value"]
+        pr = ratios if args.mode == "proposal" else None
+        headline = {"proposal_vs_exact": pv / exact_qps,
+                    "final_energy_within_1.01": bool(max(pr) <= 1.01) if pr else
+                    other["proposal"]["final_energy_ratio_vs_exact"]["within_1.01"]}
     line = {
-        "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": qps, "headline_learned_proposal": headline, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"exact": "f32", "fp8c": "e4m3+f32", "proposal": "bf16+f16+f32"}.get(args.mode, "f16+f32"),
         "data": "synthetic",
@@ -482,12 +623,15 @@ def main():
         "em_iterations_per_s": cfg["iters"] * cfg["levels"] * args.steps * world / (total_ms / 1000.0),
         "exact_fp32": {"value": exact_qps, "ms_per_step": ex_ms / args.steps,
                        "em_iterations_per_s": cfg["iters"] * cfg["levels"] * args.steps * world / (ex_ms / 1000.0),
-                       "kernels_per_step": ex_kern, "roofline": ex_roof},
+                       "kernels_per_step": ex_kern, "roofline": ex_roof,
+                       "full_pass_fraction_per_level": [r / max(1, a) for r, a in zip(route["range_queries"],
+                                                                                       route["queries"])]},
         "fp32_fma_peak_tflops": fma_tf,
         "speedup_vs_exact": qps / exact_qps,
         "final_energy_ratio_vs_exact": {"max": max(ratios), "mean": float(np.mean(ratios)),
                                         "within_1.01": bool(max(ratios) <= 1.01)},
         "other_modes": other,
+        "other_configs": other_cfgs,
         "roofline": roof,
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(inits[0].nbytes),
                 "d2h_bytes_per_step": int(out_host.numel() * 4 + 8 * (cfg["iters"] + 1) * cfg["levels"])},

@@ -120,6 +120,9 @@ typedef struct {
     long long range_pairs;    /* exact mode: queries that pass did not certify */
     long long brute_queries;  /* exact mode: queries that needed a direct scan */
     long long fallback_queries; /* proposal mode: queries sent to the exact search */
+    long long full_splits;    /* exact mode: pieces the full-dimension pass cut the window
+                                 vectors into (partial sums added in fixed order); 1 = not
+                                 cut, 0 = no full-dimension pass ran */
 } pts_search_stats;
 
 /* Parameters of the learned cluster proposal (pts_train_proposal). */

@@ -42,7 +42,8 @@ class _IndexInfo(ctypes.Structure):
 class _SearchStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_longlong), ("certified", ctypes.c_longlong),
                 ("range_queries", ctypes.c_longlong), ("range_pairs", ctypes.c_longlong),
-                ("brute_queries", ctypes.c_longlong), ("fallback_queries", ctypes.c_longlong)]
+                ("brute_queries", ctypes.c_longlong), ("fallback_queries", ctypes.c_longlong),
+                ("full_splits", ctypes.c_longlong)]
 
 
 class _ProposalParams(ctypes.Structure):

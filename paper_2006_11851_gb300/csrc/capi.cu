@@ -115,7 +115,7 @@ pts_status exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail
         PTS_TRY(ws.part_v.ensure((size_t)ra.Q * np * kTopK, "part lists"));
         PTS_TRY(ws.part_i.ensure((size_t)ra.Q * np * kTopK, "part lists"));
     }
-    launch_search_full(ra.X, ra.Wo, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
+    idx->last.full_splits = launch_search_full(ra.X, ra.Wo, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
                        ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr,
                        ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, np, idx->status.ptr, st, idx->N,
                        &ws.full_pdist);
@@ -244,6 +244,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
     PTS_TRY(ensure_workspace(idx, Q));
     idx->last_mode = mode;
     idx->last.queries = Q;
+    idx->last.full_splits = 0;
     switch (mode) {
         case PTS_EXACT_F32:
             PTS_TRY(search_exact(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));

@@ -263,7 +263,7 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
                         cudaStream_t st, int nparts = 1,
                         float *part_v = nullptr, int *part_i = nullptr,
                         const float *thr_init = nullptr);
-void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
+int launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,

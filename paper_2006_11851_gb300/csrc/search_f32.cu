@@ -605,7 +605,7 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
                                                                        cand_lb);
 }
 
-void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
+int launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
@@ -636,7 +636,7 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
             status, kcs, pdist->ptr);
         k_full_select<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(pdist->ptr, nsplit, (int)npad, N, fail_list,
                                                                     fail_count, Q, qnorm, cand_idx, cand_lb, status);
-        return;
+        return nsplit;
     }
     const int tpp = ceil_div(ntiles, nparts);
     const int np = ceil_div(ntiles, tpp);
@@ -647,6 +647,7 @@ void launch_search_full(const float *X, int Wo, int w, int stride, int qx, const
     if (np > 1)
         k_merge_fail_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, fail_list, fail_count,
                                                                         Q, qnorm, cand_idx, cand_lb, status);
+    return 1;
 }
 
 // Exemplar parts of the full-dimension pass: enough CTAs for two per SM when the query blocks

@@ -1,7 +1,11 @@
-"""Batched synthesis (one CUDA graph over jobs of uneven sizes) against the same jobs run one by
-one through synthesize_level: identical outputs and energies, and identical on a second replay."""
+"""Batched synthesis (one CUDA graph over jobs of uneven sizes): against the FP64 oracle run job
+by job, and against the same jobs run one by one through synthesize_level (identical outputs and
+energies, and identical on a second replay)."""
 import numpy as np
 import pytest
+
+import oracle
+import pts_inputs as P
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,4 +41,66 @@ def test_batch_matches_sequential(mode):
     assert b.launches_per_run > 0
     if mode == "f16":
         assert all(p >= 1 for p in b.parts)
+    b.close()
+
+
+# Uneven jobs small enough for the oracle: 8x8 and 16x16 windows, exemplars 36..64, outputs 48..96.
+SMALL_JOBS = [
+    {"job": 0, "He": 48, "Ho": 80, "w": 8, "d": 24, "seed": 0},
+    {"job": 1, "He": 40, "Ho": 64, "w": 16, "d": 32, "seed": 1},
+    {"job": 2, "He": 64, "Ho": 96, "w": 8, "d": 32, "seed": 2},
+    {"job": 3, "He": 36, "Ho": 48, "w": 16, "d": 48, "seed": 3},
+]
+
+
+@pytest.mark.parametrize("mode", ["exact", "f16"])
+def test_batch_against_oracle(mode):
+    """Each job of one graph replay against the oracle's EM run of that job (section 2.1, Eq. 4),
+    from the same seeded exemplar and initialisation.  Exact mode: every energy within 1e-3
+    relative (the first, an E-step on the initialisation, within 1e-5) and 99% of the pixels
+    within 1e-4 (a near-tie may flip a match).  FP16 mode: the final image's energy, measured by
+    the oracle's exact search, within 1.01x of the oracle's exact run."""
+    iters = 3
+    b = Batch(SMALL_JOBS, mode=mode, iters=iters, n_streams=2)
+    b.reset()
+    b.run()
+    torch.cuda.synchronize()
+    for k, s in enumerate(SMALL_JOBS):
+        Z = P.synthetic_exemplar(s["seed"], s["He"], 4.0)
+        X0 = P.random_patch_init(Z, s["Ho"], s["Ho"], s["w"], 1000 + s["seed"])
+        np.testing.assert_array_equal(b.inits[k].cpu().numpy(), X0)
+        ref = oracle.synthesize_level(Z, X0, s["w"], iters, r=2.0)
+        E = b.energies[k].cpu().numpy()
+        X = b.outputs[k].cpu().numpy()
+        if mode == "exact":
+            assert abs(E[0] / ref["E"][0] - 1) < 1e-5, (k, E[0], ref["E"][0])
+            np.testing.assert_allclose(E, ref["E"], rtol=1e-3)
+            assert np.mean(np.abs(X - ref["X"]) < 1e-4) > 0.99, k
+        else:
+            _, d2 = oracle.nn_bruteforce(X, Z, s["w"], 2)
+            assert d2.sum() <= 1.01 * ref["E"][-1], (k, d2.sum(), ref["E"][-1])
+    b.close()
+
+
+def test_batch_refuses_to_run_after_its_indices_change():
+    """The captured graph holds raw pointers into each job's index.  A search that makes the index
+    reallocate its workspace (a larger output), or destroying a job's index, must make the next
+    pts_batch_run refuse with PTS_ERR_INVALID_ARG before launching anything."""
+    specs = SMALL_JOBS[:2]
+    b = Batch(specs, mode="f16", iters=1, n_streams=2)
+    b.run()
+    torch.cuda.synchronize()
+    x = torch.zeros(specs[0]["Ho"], specs[0]["Ho"], 3, device="cuda")
+    pts.nn_search(b.indices[0], x, 2, "f16")          # same size and mode: nothing moves
+    b.run()
+    torch.cuda.synchronize()
+    big = torch.zeros(specs[0]["Ho"] + 96, specs[0]["Ho"] + 96, 3, device="cuda")
+    pts.nn_search(b.indices[0], big, 2, "f16")        # more queries: the workspace grows
+    with pytest.raises(pts.PtsError, match="create the batch again"):
+        b.run()
+    b.close()
+    b = Batch(specs, mode="exact", iters=1, n_streams=1)
+    b.indices[1].close()
+    with pytest.raises(pts.PtsError, match="destroyed"):
+        b.run()
     b.close()

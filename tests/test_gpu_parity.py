@@ -5,6 +5,8 @@ Tolerances: NN indices per the tie rule in tests/_util.py; pixels 1e-4
 absolute (FP32 path); energies 1e-5 relative per E-step, final energy of an
 EM run within 1.001x; eigenvalues 1e-9 relative; PCA projector 1e-6.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -248,17 +250,50 @@ def test_pyramid_three_levels_small():
 def test_full_size_fine_level_sampled():
     """256x256 exemplar, w = 8, d = 64, 512x512 output: 64,009 queries against
     62,001 windows, in the launch configuration the benchmark times; the
-    oracle checks a seeded sample of queries."""
+    oracle checks a seeded sample of 2,048 queries."""
     Z = P.synthetic_exemplar(0, 256, 4.0)
     idx = pts.ExemplarIndex(_t(Z), 8, d=64)
     X = P.random_patch_init(Z, 512, 512, 8, 0)
     nn, d2 = pts.nn_search(idx, _t(X), 2, "exact")
     Q = oracle.num_queries(512, 512, 8)
-    sub = P.sample_indices(11, Q, 192)
+    sub = P.sample_indices(11, Q, 2048)
     nn_o, d2_o = oracle.nn_bruteforce(X, Z, 8, 2, qlist=sub)
     check_nn(X, Z, 8, 2, nn.cpu().numpy()[sub], d2.cpu().numpy()[sub], nn_o, d2_o, qlist=sub)
     st = idx.search_stats()
     assert st["queries"] == Q and st["certified"] + st["range_queries"] == Q
+    idx.close()
+
+
+def _profiled_launches(L, name):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    assert L.pts_profile_read(name.encode(), ctypes.byref(ms), ctypes.byref(n)) == 0
+    return n.value
+
+
+def test_coarsest_level_exact_all_queries():
+    """The benchmark's coarsest level: the 256x256 exemplar down-sampled twice (64x64), w = 32
+    (D = 3,072), d = 64, 128x128 output -- all 2,401 queries of the random-patch initialisation
+    and of the oracle's next two iterates against its full-dimension FP64 brute force.  Its 64
+    components keep under 85% of the variance, so the search skips the PCA pass (nothing
+    certified from the 32 best bounds, every query sent to the full-dimension pass), and that
+    pass, having few (query block, tile) pairs, is split along the vector (partial sums added in
+    fixed order afterwards), which the search statistics report."""
+    Z = oracle.exemplar_pyramid(P.synthetic_exemplar(0, 256, 4.0), 3)[0].astype(np.float32)
+    idx = pts.ExemplarIndex(_t(Z), 32, d=64)
+    assert idx.info["var_retained"] < 0.85
+    X0 = P.random_patch_init(Z, 128, 128, 32, 100)
+    ref = oracle.synthesize_level(Z, X0, 32, 2, keep_trajectory=True)
+    L = pts.lib()
+    for Xt, nn_o, d2_o, _ in ref["trajectory"]:
+        L.pts_profile_enable(1)
+        nn, d2 = pts.nn_search(idx, _t(Xt), 2, "exact")
+        torch.cuda.synchronize()
+        topk = _profiled_launches(L, "search_topk")
+        L.pts_profile_enable(0)
+        check_nn(Xt, Z, 32, 2, nn.cpu().numpy(), d2.cpu().numpy(), nn_o, d2_o, max_mismatch_frac=0.01)
+        st = idx.search_stats()
+        assert st["queries"] == 2401 and st["certified"] == 0 and st["range_queries"] == 2401
+        assert topk == 0 and st["full_splits"] > 1, (topk, st)
     idx.close()
 
 

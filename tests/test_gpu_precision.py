@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 import pts_inputs as P
+from _ideal import group_rule_mismatch
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -129,20 +130,26 @@ def test_f16_energy_within_1_01_of_exact():
 
 
 def test_f16_full_size_fine_level_sampled():
+    """The benchmark's fine level (256x256 exemplar, w = 8, 512x512 output, random-patch
+    initialisation) on 2,048 sampled queries.  The mismatch bound is derived at this size: the
+    tensor-core search's candidate rule evaluated with the oracle's FP64 PCA bound
+    (tests/_ideal.py) gives the rate the rule itself misses, and FP16 rounding may add at most
+    0.01 on top (the same allowance as the small cases)."""
     Z = P.synthetic_exemplar(0, 256, 4.0)
     idx = pts.ExemplarIndex(_t(Z), 8, d=64)
     X = P.random_patch_init(Z, 512, 512, 8, 0)
     nn, d2 = pts.nn_search(idx, _t(X), 2, "f16")
     Q = oracle.num_queries(512, 512, 8)
-    sub = P.sample_indices(12, Q, 128)
+    sub = P.sample_indices(12, Q, 2048)
     nn_o, d2_o = oracle.nn_bruteforce(X, Z, 8, 2, qlist=sub)
     nn_g, d2_g = nn.cpu().numpy()[sub], d2.cpu().numpy()[sub].astype(np.float64)
     pd = oracle.pair_dist2(X, Z, 8, 2, sub, nn_g)
     np.testing.assert_allclose(d2_g, pd, rtol=1e-5, atol=1e-6)
     assert np.all(pd >= d2_o * (1 - 1e-12))
-    # a random-patch initialisation is the hardest case for the PCA-space ranking (most windows
-    # straddle patch seams); on converging images the rate is several times lower
-    assert np.mean(nn_g != nn_o) < 0.035
+    ideal = float(np.mean(group_rule_mismatch(X, Z, 8, idx.info["d_fast"], sub, nn_o)))
+    mism = float(np.mean(nn_g != nn_o))
+    print(f"\nfine level f16: mismatch {mism:.4f}, the candidate rule in FP64 {ideal:.4f}")
+    assert mism <= ideal + 0.01, (mism, ideal)
     idx.close()
 
 

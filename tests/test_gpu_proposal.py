@@ -50,6 +50,22 @@ def test_kmeans_matches_oracle():
     assert np.mean(a_g == a_o) > 0.99
 
 
+def test_kmeans_empty_cluster_reseed_matches_oracle():
+    """A hand-found 11-point case whose third Lloyd update leaves cluster 2 empty; the re-seed
+    (reading c-17) must take the unused point of largest cost, and two points tie at cost
+    1.953125 (exact in FP32), so the smallest index (point 3, not 8) must win.  All coordinates
+    are multiples of 1/4, so the GPU's FP32 costs equal the oracle's FP64 ones where it matters."""
+    Y = np.array([[0.75, 2.25], [1.75, 3.75], [2.25, 3.25], [2.75, 0.0], [1.0, 1.75], [0.75, 2.25],
+                  [1.75, 2.75], [3.25, 3.75], [0.0, 0.5], [2.5, 3.0], [0.0, 2.25]])
+    u = np.array([0.2219481468896175, 0.3235902000698858, 0.1342355651416305, 0.7882371723686297])
+    C_o, a_o, hist = oracle.kmeans(Y, 4, u, iters=25)
+    assert C_o[2].tolist() == [2.75, 0.0]          # the re-seeded centroid is point 3
+    C_g, a_g, it = pts.kmeans(_t(Y), 4, u, iters=25)
+    np.testing.assert_array_equal(a_g.cpu().numpy(), a_o)
+    np.testing.assert_allclose(C_g.cpu().numpy(), C_o, rtol=1e-6)
+    assert it == len(hist) - 1
+
+
 def _mlp_params(seed, C, scale=0.15):
     g = P.SplitMix64(seed)
     shapes = [(256, 64), (256,), (256, 256), (256,), (C, 256), (C,)]
