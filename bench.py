@@ -372,6 +372,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries per level for the CPU baseline")
     ap.add_argument("--d-fast", type=int, default=0, help="PCA dimensions of the tensor-core search (0 = library default)")
+    ap.add_argument("--no-robust", action="store_true", help="skip the robust-schedule timing (other_configs)")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the 512x512 -> 1024x1024, w = 16 precision-form timing (other_configs)")
     args = ap.parse_args()
@@ -533,20 +534,21 @@ def main():
     # ---- the exact FP32 arm against the FP32 SIMT pipe (FMA rate measured here, this GPU) ----
     fma_tf, _ = pts.fp32_fma_peak()
     it = cfg["iters"] + 1
-    pca_levels = [(l, ix.info) for l, ix in zip(sizes, pidx.indices) if ix.info["var_retained"] >= PCA_PASS_MIN_VAR]
+    pca_levels = [(l, ix.info) for l, ix in zip(sizes, pidx.indices) if ix.info["exact_var"] >= PCA_PASS_MIN_VAR]
     # queries the full-dimension pass took per step: one untimed exact step replayed search by
     # search through the public API, reading each search's statistics
     route = exact_route_counts(pts, pidx, init_dev(args.warmup), cfg)
     full_fl = sum(2.0 * l["D"] * l["N"] * n for l, n in zip(sizes, route["range_queries"]))
-    pca_fl = sum(2.0 * (inf["d"] + 1) * l["N"] * l["Q"] * it for l, inf in pca_levels)
+    pca_fl = sum(2.0 * (inf["exact_dims"] + 1) * l["N"] * l["Q"] * it for l, inf in pca_levels)
     ex_roofs = {}
     if "search_topk" in ex_kern and pca_levels:
         ach = pca_fl / (ex_kern["search_topk"]["ms_per_step"] / 1000.0) / 1e12
         ex_roofs["search_topk"] = {
             "kernel": "k_search_pca (FP32 SIMT PCA-space bound GEMM + top-32)", "bound": "alu", "achieved": ach,
             "peak": fma_tf, "unit": "TFLOP/s", "frac": ach / fma_tf,
-            "note": "algorithmic 2(d+1) flops per (query, window) pair at the levels that run the PCA pass "
-                    f"(d = {[inf['d'] for _, inf in pca_levels]}); peak = FP32 FMA probe measured in this run "
+            "note": "algorithmic 2(k+1) flops per (query, window) pair at the levels that run the PCA pass "
+                    f"(k = {[inf['exact_dims'] for _, inf in pca_levels]} bound components); peak = FP32 FMA probe "
+                    "measured in this run "
                     f"(nominal {PEAK_FP32_TFLOPS:.1f} = 152 SMs x 128 lanes x 2 x 2070 MHz)"}
     if "search_full" in ex_kern and full_fl > 0:
         ach = full_fl / (ex_kern["search_full"]["ms_per_step"] / 1000.0) / 1e12
@@ -585,7 +587,7 @@ def main():
                              "being 32.3 MB")
     elif dom in ex_roofs and args.mode == "exact":
         roof.update(ex_roofs[dom], traffic=None)
-    elif dom == "search_full" and all(m != "exact" or ix.info["var_retained"] < PCA_PASS_MIN_VAR
+    elif dom == "search_full" and all(m != "exact" or ix.info["exact_var"] < PCA_PASS_MIN_VAR
                                       for m, ix in zip(modes, pidx.indices)):
         # exact levels without a PCA pass send every query to the full-dimension pass, and the
         # other modes never reach it: the work is 2 D flops per (query, window) pair there
@@ -602,6 +604,32 @@ def main():
     if not args.no_precision_form:
         other_cfgs["precision_form"] = time_precision_form(pts, P, L, dev, stream, flush, args.steps, args.warmup,
                                                            bf16_burst, peak_src)
+
+    if not args.no_robust:
+        # section 2.1's own schedule: r = 0.8 with the stopping rule at every level, same search
+        # modes and seeds; queries counted as the searches the schedule ran
+        rob_ms, rob_q, rob_steps, rob_ratios = 0.0, 0, [], []
+        for i in range(args.steps):
+            x0 = init_dev(args.warmup + i)
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            X, E, _ = synthesize_pyramid(pidx, x0, iters=0, mode=modes, schedule="robust")
+            ev1.record(stream)
+            ev1.synchronize()
+            rob_ms += ev0.elapsed_time(ev1)
+            rob_steps.append([len(e) - 1 for e in E])
+            rob_q += sum(L_["Q"] * len(e) for L_, e in zip(sizes, E))
+            rob_ratios.append(exact_energy(X) / ex_energies[i])
+        other_cfgs["robust_schedule"] = {
+            "schedule": "r = 0.8, IRLS weights max(d, 1e-3)^(r-2), EM at each level until the searched windows "
+                        "repeat (at most 30 M-steps), search modes as level_modes",
+            "value": rob_q / (rob_ms / 1000.0), "unit": "queries/s", "ms_per_step": rob_ms / args.steps,
+            "m_steps_per_level": np.mean(rob_steps, axis=0).tolist(),
+            "em_iterations_per_s": float(np.sum(rob_steps)) / (rob_ms / 1000.0),
+            "final_energy_ratio_vs_exact_fixed_schedule": {"max": max(rob_ratios), "mean": float(np.mean(rob_ratios))}}
 
     headline = None
     if also == "proposal" or args.mode == "proposal":

@@ -13,10 +13,12 @@
  *   - the coarse-to-fine driver (section 2.1).
  *
  * Conventions used by every entry point:
- *   images     float32, H x W x 3, row-major, channel fastest (HWC), DEVICE
- *              memory owned by the caller;
+ *   images     float32, H x W x C, row-major, channel fastest (HWC), DEVICE
+ *              memory owned by the caller; C = 3 (RGB), or C = 4 (RGBS: RGB
+ *              and the scale map of section 1 as a fourth channel) for the
+ *              images an RGBS index searches and updates;
  *   window     the w x w block whose top-left pixel is (y0, x0); vector
- *              element (dy, dx, c) is number (dy*w + dx)*3 + c; D = 3 w^2;
+ *              element (dy, dx, c) is number (dy*w + dx)*C + c; D = C w^2;
  *   exemplar   windows at every stride-1 origin inside the exemplar:
  *              N = (He-w+1)(We-w+1), index n = y*(We-w+1) + x;
  *   queries    output windows whose origins lie on the stride grid
@@ -101,6 +103,11 @@ typedef struct {
     int max_iters;   /* eigen-solver iteration cap (0 = 200) */
     int d_fast;      /* PCA dimensions of the tensor-core and proposal searches, 1..124
                         (0 = 124; capped by the covariance rank min(D, N - 1)) */
+    int channels;    /* 0 or 3: RGB images; 4: RGBS images (sections 2.2 and 3: the scale
+                        map as a fourth channel; D = 4 w^2).  With 4, the exemplar and every
+                        image searched or updated have 4 channels, the M-step updates R, G
+                        and B and leaves the fourth channel as it is, and the histogram
+                        entry points are refused */
 } pts_index_params;
 
 typedef struct {
@@ -111,6 +118,10 @@ typedef struct {
     double eig_top;          /* largest eigenvalue */
     int eig_iters;           /* subspace iterations used */
     float unorm2_max;        /* max_n ||v_n - mu||^2 over exemplar windows */
+    int channels;            /* channels per pixel of the images: 3 (RGB) or 4 (RGBS) */
+    int exact_dims;          /* PCA components of the exact search's lower bound */
+    double exact_var;        /* the variance fraction they keep (below 0.85 the exact search
+                                skips its PCA pass and scans every window in full dimension) */
 } pts_index_info;
 
 typedef struct {
@@ -185,15 +196,21 @@ long long pts_live_allocations(void);
  */
 pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double var_frac,
                    float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream);
+/* pca_fit for images of C channels (3: RGB, 4: RGBS, the scale map as a fourth channel,
+ * sections 2.2 and 3): exemplar device He x We x C float32, D = C w^2; otherwise as pca_fit. */
+pts_status pca_fit_channels(const float *exemplar, int He, int We, int C, int w, int d, double var_frac,
+                            float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream);
 
 /*
  * build_exemplar_index -- everything the search needs about one exemplar and
  * window width: a device copy of the exemplar, the PCA (as pca_fit), and the
  * projected exemplar windows y_n = B^T(v_n - mu) with their residual norms
  * ||(I - B B^T)(v_n - mu)|| and squared norms ||v_n - mu||^2 (section 2.2).
- * exemplar is a device pointer; the index keeps its own copy, so the caller
- * may free it afterwards.  Synchronises `stream`.  *out receives a new index
- * (release it with pts_index_destroy).
+ * exemplar is a device pointer to He x We x C float32 (C = params->channels:
+ * 3, or 4 for an RGBS exemplar whose fourth channel is its scale map); the
+ * index keeps its own copy, so the caller may free it afterwards.
+ * Synchronises `stream`.  *out receives a new index (release it with
+ * pts_index_destroy).
  */
 pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
                                 const pts_index_params *params, void *stream, pts_index *out);
@@ -213,9 +230,11 @@ pts_status pts_index_get_info(pts_index index, pts_index_info *info);
  * (written under a temporary name, then renamed).  Synchronises the device.
  * pts_index_load reads such a file into a new index on the current device, owned by the caller
  * (free it with pts_index_destroy).  Every search on it returns what the same search on the
- * saved index returns.  The file's header and its length are checked before anything is
- * allocated: a file that is not an index file, was written with another byte order or layout
- * version, is truncated, or whose tables disagree with its header gives PTS_ERR_INVALID_ARG
+ * saved index returns.  The file's header, its length and the integer tables the kernels
+ * index with (cluster offsets, members and assignments; tree links, leaf ranges and window
+ * order) are checked before anything is allocated: a file that is not an index file, was
+ * written with another byte order or layout version, is truncated, whose tables disagree with
+ * its header, or whose integer tables are out of range gives PTS_ERR_INVALID_ARG
  * (see pts_last_error).  Synchronises the device.  Files are in host byte order; the x86-64 and
  * AArch64 hosts of this library share it.
  */
@@ -231,6 +250,14 @@ pts_status pts_index_load(const char *path, pts_index *out);
  * for a NULL index or parts < 0; parts larger than the tile count act as the
  * tile count. */
 pts_status pts_index_set_tc_parts(pts_index index, int parts);
+
+/* The components of the exact search's PCA lower bound (section 2.2's PCA; no counterpart in
+ * the paper, a tuning knob): fast = 0 (the default) bounds with the index's first d components,
+ * fast = 1 with its d_fast components when d_fast > d (fewer queries need the full-dimension
+ * pass, each bound costs about twice as much; on the benchmark's levels the default is faster).
+ * Results are the certified nearest windows of Eq. 4 either way.  PTS_ERR_INVALID_ARG for other
+ * values. */
+pts_status pts_index_set_exact_bound(pts_index index, int fast);
 
 /*
  * pts_build_kmeans_tree -- builds the search tree of PTS_KMTREE (section 2.2): hierarchical
@@ -260,7 +287,7 @@ pts_status pts_index_device_status(pts_index index, void *stream);
 
 /*
  * nn_search -- the search phase (E-step, Eq. 4): for every query window of
- * `output` (device, Ho x Wo x 3 float32) on the stride grid, the index n of
+ * `output` (device, Ho x Wo x C float32, C the index's channels) on the stride grid, the index n of
  * its nearest exemplar window and the squared full-dimension distance
  * ||x_p - z_n||^2 computed in FP32 from the pixels.
  * nn_out     device, Q int32.   dist2_out  device, Q float32.
@@ -272,7 +299,7 @@ pts_status nn_search(pts_index index, const float *output, int Ho, int Wo, int s
 
 /*
  * pts_project_queries -- PCA coordinates y_q = B^T (x_q - mu) (section 2.2) of every query
- * window of `output` (device Ho x Wo x 3), written to y_out (device Q x d float32, row-major).
+ * window of `output` (device Ho x Wo x C), written to y_out (device Q x d float32, row-major).
  * Used to collect training pairs for the proposal.  Asynchronous.
  */
 pts_status pts_project_queries(pts_index index, const float *output, int Ho, int Wo, int stride, float *y_out,
@@ -377,7 +404,9 @@ pts_status irls_weights_noalloc(const float *dist2, int Q, float r, float delta,
  * computed once per s x s patch (section 2.2) by gathering from the index's
  * exemplar copy, in increasing query order, without atomics.
  * nn device Q int32 (values in [0, N)); weights device Q float32 or NULL
- * (all 1); output device Ho x Wo x 3 float32, overwritten (not read).
+ * (all 1); output device Ho x Wo x C float32 (C the index's channels): R, G
+ * and B overwritten (not read); with C = 4 the fourth channel is left as it
+ * is (the output's scale map stays fixed, section 3).
  * Out-of-range nn values are clamped and flagged in the device status word.
  */
 pts_status m_step(pts_index index, const int32_t *nn, const float *weights, int Ho, int Wo,
@@ -388,7 +417,8 @@ pts_status m_step(pts_index index, const int32_t *nn, const float *weights, int 
  * (section 2.1) on one level: search phase (nn_search in `mode`), IRLS
  * weights (r, delta), optimization phase (m_step), repeated; then one last
  * search phase so that energy_out[iters] is the energy of the result.
- * output      device Ho x Wo x 3: in = initial image, out = result.
+ * output      device Ho x Wo x C (C the index's channels): in = initial image,
+ *             out = result.
  * energy_out  HOST, iters + 1 float64: energy_out[t] is the energy of the
  *             iterate entering iteration t (Eq. 4 / Eq. 5).
  * Synchronises `stream` once at the end and returns the device status.
@@ -455,6 +485,44 @@ pts_status synthesize_level_converge(pts_index index, float *output, int Ho, int
                                      void *stream);
 
 /*
+ * The scale map (Methodology section 1, Eqs. 1-3) and its use in synthesis (section 3).
+ * Maps are DEVICE float64 arrays, row 0 at the top.  Readings: the image-plane origin is the
+ * bottom-left pixel (row r has p(y) = h - 1 - r) and w/2, h/2 are real halves; Eq. 3's leading
+ * term, printed as Y_max, is read as S_max, so S = S_max - (p(Y_proj) - Y_min) S_delta / Y_delta
+ * runs from S_max (near pixel (1, 1)) to S_min (the top-right pixel) and is 1 everywhere for a
+ * fronto-parallel plane.  Every value is FP64 with each operation rounded on its own, in the
+ * order written (no fused multiply-add): bit-reproducible.
+ *
+ * pts_scale_map        Eqs. 1-3 for an h x w image: S_max = 1/cos(slant), S_min = cos(slant)
+ *                      (Eq. 1); Y_max = (w-1-w/2) sin(tilt) + (h-1-h/2) cos(tilt), Y_min =
+ *                      -Y_max (Eq. 2); S_out device h x w.  slant in [0, 90), tilt in [0, 90]
+ *                      degrees; Y_delta = 0 is refused.  Asynchronous.
+ * pts_scale_resample   section 3 step 2: S (He x We) resampled bilinearly, corner-aligned, to
+ *                      Ho x Wo (all sides >= 2).  Asynchronous.
+ * pts_scale_guided_init section 3 step 3: the initial output (out: device Ho x Wo x 3 float32)
+ *                      filled from exemplar pixels of the same scale.  The exemplar map's range
+ *                      [lo, hi] is cut into nbins (1..1024) equal bins, bin(s) = floor((s - lo) /
+ *                      (hi - lo) nbins) clamped; output pixel o, in the bin of S_x[o], copies
+ *                      exemplar pixel floor(u[o] m) of that bin's m pixels in raster order; an
+ *                      empty bin borrows the nearest filled bin (the lower one on a tie).
+ *                      exemplar device He x We x 3, S_z device He x We, S_x and u (uniforms in
+ *                      [0, 1)) device Ho x Wo float64; src_out device Ho x Wo int32 (may be
+ *                      NULL): the raster index of the exemplar pixel copied.  Synchronises
+ *                      `stream` (its scratch is released before it returns).
+ * pts_rgbs             the RGBS image of sections 2.2 and 3: out (device H x W x 4, 16-byte
+ *                      aligned) = (R, G, B, lam S) from rgb (H x W x 3) and S (H x W float64),
+ *                      the fourth value lam S rounded to float32.  Asynchronous.
+ * pts_rgb_of           the colour channels of an RGBS image (16-byte aligned) into H x W x 3.
+ */
+pts_status pts_scale_map(int h, int w, double slant_deg, double tilt_deg, double *S_out, void *stream);
+pts_status pts_scale_resample(const double *S, int He, int We, int Ho, int Wo, double *S_out, void *stream);
+pts_status pts_scale_guided_init(const float *exemplar, const double *S_z, int He, int We, const double *S_x,
+                                 const double *u, int Ho, int Wo, int nbins, float *out, int32_t *src_out,
+                                 void *stream);
+pts_status pts_rgbs(const float *rgb, const double *S, double lam, int H, int W, float *out, void *stream);
+pts_status pts_rgb_of(const float *rgbs, int H, int W, float *rgb_out, void *stream);
+
+/*
  * Pyramid filters for coarse-to-fine synthesis (section 2.1: a coarse result
  * is up-sampled by interpolation to initialise the next level).  The paper
  * names no filter; the library uses
@@ -491,7 +559,8 @@ long long pts_launch_count(void);
  */
 typedef struct {
     pts_index index;  /* the job's exemplar index; no two jobs of a batch may share one */
-    float *output;    /* device Ho x Wo x 3 float32; in: initial image, out: result */
+    float *output;    /* device Ho x Wo x C float32 (C the index's channels); in: initial image,
+                         out: result */
     int Ho, Wo, stride;
     int mode;         /* PTS_EXACT_F32, PTS_F16_RERANK or PTS_FP8_RERANK */
     double *energy;   /* device, iters + 1 doubles: energy entering each iteration, then the final */

@@ -34,6 +34,11 @@ from ._binding import (  # noqa: F401
     project_queries,
     proposal_info,
     proposal_top4,
+    rgb_of,
+    rgbs,
+    scale_guided_init,
+    scale_map,
+    scale_resample,
     set_allocator,
     synthesize_level,
     synthesize_level_async,
@@ -43,4 +48,4 @@ from ._binding import (  # noqa: F401
     use_torch_allocator,
     wait_selftest,
 )
-from .pyramid import synthesize_pyramid  # noqa: F401
+from .pyramid import synthesize_pyramid, synthesize_pyramid_rgbs  # noqa: F401

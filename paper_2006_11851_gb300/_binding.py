@@ -29,14 +29,15 @@ class PtsError(RuntimeError):
 
 class _IndexParams(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("var_frac", ctypes.c_double), ("max_iters", ctypes.c_int),
-                ("d_fast", ctypes.c_int)]
+                ("d_fast", ctypes.c_int), ("channels", ctypes.c_int)]
 
 
 class _IndexInfo(ctypes.Structure):
     _fields_ = [("He", ctypes.c_int), ("We", ctypes.c_int), ("w", ctypes.c_int), ("D", ctypes.c_int),
                 ("N", ctypes.c_int), ("d", ctypes.c_int), ("da", ctypes.c_int), ("d_fast", ctypes.c_int),
                 ("var_retained", ctypes.c_double), ("eig_top", ctypes.c_double),
-                ("eig_iters", ctypes.c_int), ("unorm2_max", ctypes.c_float)]
+                ("eig_iters", ctypes.c_int), ("unorm2_max", ctypes.c_float), ("channels", ctypes.c_int),
+                ("exact_dims", ctypes.c_int), ("exact_var", ctypes.c_double)]
 
 
 class _SearchStats(ctypes.Structure):
@@ -73,6 +74,12 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.pts_last_error.restype = ctypes.c_char_p
         L.pts_version.restype = ctypes.c_char_p
         L.pca_fit.argtypes = [_vp, _I, _I, _I, _I, _Dd, _vp, _vp, _vp, ctypes.POINTER(_I), _vp]
+        L.pca_fit_channels.argtypes = [_vp, _I, _I, _I, _I, _I, _Dd, _vp, _vp, _vp, ctypes.POINTER(_I), _vp]
+        L.pts_scale_map.argtypes = [_I, _I, _Dd, _Dd, _vp, _vp]
+        L.pts_scale_resample.argtypes = [_vp, _I, _I, _I, _I, _vp, _vp]
+        L.pts_scale_guided_init.argtypes = [_vp, _vp, _I, _I, _vp, _vp, _I, _I, _I, _vp, _vp, _vp]
+        L.pts_rgbs.argtypes = [_vp, _vp, _Dd, _I, _I, _vp, _vp]
+        L.pts_rgb_of.argtypes = [_vp, _I, _I, _vp, _vp]
         L.build_exemplar_index.argtypes = [_vp, _I, _I, _I, ctypes.POINTER(_IndexParams), _vp,
                                            ctypes.POINTER(_vp)]
         L.pts_index_destroy.argtypes = [_vp]
@@ -80,6 +87,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.pts_index_get_info.argtypes = [_vp, ctypes.POINTER(_IndexInfo)]
         L.pts_index_device_status.argtypes = [_vp, _vp]
         L.pts_index_set_tc_parts.argtypes = [_vp, _I]
+        L.pts_index_set_exact_bound.argtypes = [_vp, _I]
         L.nn_search.argtypes = [_vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
         L.pts_index_search_stats.argtypes = [_vp, ctypes.POINTER(_SearchStats), _vp]
         L.irls_weights.argtypes = [_vp, _I, _F, _F, _vp, _vp, _vp]
@@ -146,6 +154,14 @@ def _need(t: torch.Tensor, dtype: torch.dtype, name: str, shape=None) -> torch.T
     return t
 
 
+def _image_of(index: "ExemplarIndex", img: torch.Tensor, name: str = "output"):
+    """(H, W) of a float32 CUDA image whose channel count is the index's (3 RGB, 4 RGBS)."""
+    _need(img, torch.float32, name)
+    if img.dim() != 3 or img.shape[2] != index.C:
+        raise ValueError(f"{name} must be H x W x {index.C} for this index")
+    return img.shape[0], img.shape[1]
+
+
 def _mode(mode) -> int:
     if isinstance(mode, str):
         return MODES[mode]
@@ -153,33 +169,38 @@ def _mode(mode) -> int:
 
 
 def pca_fit(exemplar: torch.Tensor, w: int, d: int, var_frac: float = 0.95):
-    """(mean[D] f32, basis[d, D] f32, eigenvalues[d] f64, d_used) on the GPU."""
+    """(mean[D] f32, basis[d, D] f32, eigenvalues[d] f64, d_used) on the GPU; the exemplar is
+    H x W x 3 (RGB) or H x W x 4 (RGBS), D = C w^2."""
     _need(exemplar, torch.float32, "exemplar")
-    He, We, _ = exemplar.shape
-    D = 3 * w * w
+    He, We, C = exemplar.shape
+    if C not in (3, 4):
+        raise ValueError("exemplar must be H x W x 3 or H x W x 4")
+    D = C * w * w
     cap = d if d > 0 else 64
     mean = torch.empty(D, device=exemplar.device, dtype=torch.float32)
     basis = torch.empty(cap, D, device=exemplar.device, dtype=torch.float32)
     eig = torch.empty(cap, device=exemplar.device, dtype=torch.float64)
     dout = ctypes.c_int(0)
-    _check(lib().pca_fit(_ptr(exemplar), He, We, w, d, var_frac, _ptr(mean), _ptr(basis), _ptr(eig),
-                         ctypes.byref(dout), _stream()))
+    _check(lib().pca_fit_channels(_ptr(exemplar), He, We, C, w, d, var_frac, _ptr(mean), _ptr(basis), _ptr(eig),
+                                  ctypes.byref(dout), _stream()))
     k = dout.value
     return mean, basis[:k].contiguous(), eig[:k].contiguous(), k
 
 
 class ExemplarIndex:
-    """Owns a pts_index (build_exemplar_index); freed by close() or on GC."""
+    """Owns a pts_index (build_exemplar_index); freed by close() or on GC.  The exemplar is
+    H x W x 3 (RGB) or H x W x 4 (RGBS: the scale map as a fourth channel); every image searched
+    or updated with the index has the same channel count."""
 
     def __init__(self, exemplar: torch.Tensor, w: int, d: int = 0, var_frac: float = 0.95,
                  max_iters: int = 0, d_fast: int = 0):
         L = lib()
         _need(exemplar, torch.float32, "exemplar")
         He, We, C = exemplar.shape
-        if C != 3:
-            raise ValueError("exemplar must be H x W x 3")
+        if C not in (3, 4):
+            raise ValueError("exemplar must be H x W x 3 (RGB) or H x W x 4 (RGBS)")
         self._h = ctypes.c_void_p()
-        p = _IndexParams(int(d), float(var_frac), int(max_iters), int(d_fast))
+        p = _IndexParams(int(d), float(var_frac), int(max_iters), int(d_fast), int(C))
         _check(L.build_exemplar_index(_ptr(exemplar), He, We, w, ctypes.byref(p), _stream(),
                                       ctypes.byref(self._h)))
         self.device = exemplar.device
@@ -190,7 +211,7 @@ class ExemplarIndex:
         _check(lib().pts_index_get_info(self._h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in _IndexInfo._fields_}
         self.w, self.N, self.d, self.D = info.w, info.N, info.d, info.D
-        self.He, self.We = info.He, info.We
+        self.He, self.We, self.C = info.He, info.We, info.channels
 
     def save(self, path: str) -> None:
         """Write the index (PCA, search tables, and any trained proposal or k-means tree) to a file
@@ -240,6 +261,12 @@ class ExemplarIndex:
     def set_tc_parts(self, parts: int) -> None:
         """Exemplar split of the tensor-core searches (0 = automatic); results do not depend on it."""
         _check(lib().pts_index_set_tc_parts(self.handle, int(parts)))
+
+    def set_exact_bound(self, fast: bool) -> None:
+        """Components of the exact search's PCA bound: the index's d_fast (True) or its first d
+        (False, the default); the certified results do not depend on it."""
+        _check(lib().pts_index_set_exact_bound(self.handle, 1 if fast else 0))
+        self._read_info()
 
 
 def index_save(index: ExemplarIndex, path: str) -> None:
@@ -306,8 +333,7 @@ def build_exemplar_index(exemplar: torch.Tensor, w: int, d: int = 0, var_frac: f
 def nn_search(index: ExemplarIndex, output: torch.Tensor, stride: int = 2, mode="exact",
               nn_out: torch.Tensor | None = None, d2_out: torch.Tensor | None = None):
     """(nn int32[Q], dist2 float32[Q]) of every query window of `output`."""
-    _need(output, torch.float32, "output")
-    Ho, Wo, _ = output.shape
+    Ho, Wo = _image_of(index, output)
     Q = index.num_queries(Ho, Wo, stride) if (Ho - index.w) % stride == 0 and (Wo - index.w) % stride == 0 else 0
     if nn_out is None:
         nn_out = torch.empty(max(Q, 1), device=output.device, dtype=torch.int32)
@@ -333,8 +359,10 @@ def m_step(index: ExemplarIndex, nn: torch.Tensor, weights: torch.Tensor | None,
     if weights is not None:
         _need(weights, torch.float32, "weights")
     if out is None:
+        if index.C != 3:
+            raise ValueError("an RGBS M-step updates R, G and B of an existing image: pass out")
         out = torch.empty(Ho, Wo, 3, device=nn.device, dtype=torch.float32)
-    _need(out, torch.float32, "out", (Ho, Wo, 3))
+    _need(out, torch.float32, "out", (Ho, Wo, index.C))
     Q = index.num_queries(Ho, Wo, stride)
     if nn.numel() != Q or (weights is not None and weights.numel() != Q):
         raise ValueError("nn/weights must have one entry per query")
@@ -346,8 +374,7 @@ def synthesize_level(index: ExemplarIndex, output: torch.Tensor, iters: int, r: 
                      delta: float = 1e-3, mode="exact", stride: int = 2, hist_bins: int = 0) -> np.ndarray:
     """Runs EM in place on `output`; returns the iters + 1 energies (host).  hist_bins > 0 uses
     the M-step with the histogram weights of Eq. 9 (synthesize_level_hist)."""
-    _need(output, torch.float32, "output")
-    Ho, Wo, _ = output.shape
+    Ho, Wo = _image_of(index, output)
     E = np.zeros(iters + 1, dtype=np.float64)
     if hist_bins:
         _check(lib().synthesize_level_hist(index.handle, _ptr(output), Ho, Wo, stride, iters, r, delta, _mode(mode),
@@ -363,8 +390,7 @@ def synthesize_level_async(index: ExemplarIndex, output: torch.Tensor, iters: in
                            energy: torch.Tensor | None = None) -> torch.Tensor:
     """synthesize_level without the closing synchronisation: returns the iters + 1 energies as a
     device float64 tensor; kernel errors wait in the device status (index.device_status())."""
-    _need(output, torch.float32, "output")
-    Ho, Wo, _ = output.shape
+    Ho, Wo = _image_of(index, output)
     if energy is None:
         energy = torch.empty(iters + 1, device=output.device, dtype=torch.float64)
     _need(energy, torch.float64, "energy", (iters + 1,))
@@ -377,8 +403,7 @@ def synthesize_level_converge(index: ExemplarIndex, output: torch.Tensor, max_it
                               delta: float = 1e-3, mode="exact", stride: int = 2, hist_bins: int = 0):
     """EM in place on `output` until the searched windows repeat (or max_iters M-steps);
     returns (energies [iters + 1] on the host, iters)."""
-    _need(output, torch.float32, "output")
-    Ho, Wo, _ = output.shape
+    Ho, Wo = _image_of(index, output)
     E = np.zeros(max_iters + 1, dtype=np.float64)
     it = _I(0)
     _check(lib().synthesize_level_converge(index.handle, _ptr(output), Ho, Wo, stride, int(max_iters), r, delta,
@@ -389,7 +414,10 @@ def synthesize_level_converge(index: ExemplarIndex, output: torch.Tensor, max_it
 
 def m_step_hist(index: ExemplarIndex, nn: torch.Tensor, weights: torch.Tensor | None, current: torch.Tensor,
                 nbins: int, stride: int = 2, out: torch.Tensor | None = None) -> torch.Tensor:
-    """The M-step with the weights of Eq. 9, histograms of `current` against the exemplar's."""
+    """The M-step with the weights of Eq. 9, histograms of `current` against the exemplar's (RGB
+    indices only)."""
+    if index.C != 3:
+        raise ValueError("histogram weights need an RGB index")
     _need(nn, torch.int32, "nn")
     _need(current, torch.float32, "current")
     if weights is not None:
@@ -435,8 +463,7 @@ def upsample2(img: torch.Tensor) -> torch.Tensor:
 # ---------------------------------------------------------------------------
 def project_queries(index: ExemplarIndex, output: torch.Tensor, stride: int = 2) -> torch.Tensor:
     """PCA coordinates [Q, d] of every query window of `output`."""
-    _need(output, torch.float32, "output")
-    Ho, Wo, _ = output.shape
+    Ho, Wo = _image_of(index, output)
     y = torch.empty(index.num_queries(Ho, Wo, stride), index.d, device=output.device, dtype=torch.float32)
     _check(lib().pts_project_queries(index.handle, _ptr(output), Ho, Wo, stride, _ptr(y), _stream()))
     return y
@@ -461,8 +488,7 @@ def train_proposal(index: ExemplarIndex, y: torch.Tensor, nn: torch.Tensor, d2: 
 
 def proposal_top4(index: ExemplarIndex, output: torch.Tensor, stride: int = 2, fused: bool = True) -> torch.Tensor:
     """[Q, 4] int32: the network's 4 best-ranked clusters per query (fused kernel or GEMM path)."""
-    _need(output, torch.float32, "output")
-    Ho, Wo, _ = output.shape
+    Ho, Wo = _image_of(index, output)
     top = torch.empty(index.num_queries(Ho, Wo, stride), 4, dtype=torch.int32, device=output.device)
     _check(lib().pts_proposal_top4(index.handle, _ptr(output), Ho, Wo, stride, 1 if fused else 0, _ptr(top), _stream()))
     return top
@@ -555,4 +581,65 @@ def kmtree_export(index: ExemplarIndex) -> dict:
 def kmtree_last_leaves(index: ExemplarIndex, Q: int) -> np.ndarray:
     out = np.zeros(Q, dtype=np.int32)
     _check(lib().pts_kmtree_last_leaves(index.handle, out.ctypes.data_as(ctypes.c_void_p), int(Q), _stream()))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the scale map (section 1, Eqs. 1-3) and its use in synthesis (section 3)
+# ---------------------------------------------------------------------------
+def scale_map(h: int, w: int, slant_deg: float, tilt_deg: float, device=None) -> torch.Tensor:
+    """Eq. 3's local scale of every pixel of an h x w image: float64 [h, w] on the GPU."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    S = torch.empty(h, w, device=dev, dtype=torch.float64)
+    _check(lib().pts_scale_map(int(h), int(w), float(slant_deg), float(tilt_deg), _ptr(S), _stream()))
+    return S
+
+
+def scale_resample(S: torch.Tensor, Ho: int, Wo: int) -> torch.Tensor:
+    """The map S resampled bilinearly (corner-aligned) to Ho x Wo: float64 [Ho, Wo]."""
+    _need(S, torch.float64, "S")
+    out = torch.empty(Ho, Wo, device=S.device, dtype=torch.float64)
+    _check(lib().pts_scale_resample(_ptr(S), S.shape[0], S.shape[1], int(Ho), int(Wo), _ptr(out), _stream()))
+    return out
+
+
+def scale_guided_init(exemplar: torch.Tensor, S_z: torch.Tensor, S_x: torch.Tensor, u: torch.Tensor,
+                      nbins: int = 64):
+    """(initial output Ho x Wo x 3 float32, source pixel per output pixel int32 [Ho, Wo]): every
+    output pixel copies an exemplar pixel of its scale bin."""
+    _need(exemplar, torch.float32, "exemplar")
+    _need(S_z, torch.float64, "S_z")
+    _need(S_x, torch.float64, "S_x")
+    _need(u, torch.float64, "u")
+    He, We, C = exemplar.shape
+    Ho, Wo = S_x.shape
+    if C != 3 or tuple(S_z.shape) != (He, We) or tuple(u.shape) != (Ho, Wo):
+        raise ValueError("exemplar H x W x 3, S_z H x W, u of S_x's shape")
+    out = torch.empty(Ho, Wo, 3, device=exemplar.device, dtype=torch.float32)
+    src = torch.empty(Ho, Wo, device=exemplar.device, dtype=torch.int32)
+    _check(lib().pts_scale_guided_init(_ptr(exemplar), _ptr(S_z), He, We, _ptr(S_x), _ptr(u), Ho, Wo, int(nbins),
+                                       _ptr(out), _ptr(src), _stream()))
+    return out, src
+
+
+def rgbs(rgb: torch.Tensor, S: torch.Tensor, lam: float = 1.0) -> torch.Tensor:
+    """The H x W x 4 image (R, G, B, lam S)."""
+    _need(rgb, torch.float32, "rgb")
+    _need(S, torch.float64, "S")
+    H, W, C = rgb.shape
+    if C != 3 or tuple(S.shape) != (H, W):
+        raise ValueError("rgb H x W x 3 and S H x W")
+    out = torch.empty(H, W, 4, device=rgb.device, dtype=torch.float32)
+    _check(lib().pts_rgbs(_ptr(rgb), _ptr(S), float(lam), H, W, _ptr(out), _stream()))
+    return out
+
+
+def rgb_of(img: torch.Tensor) -> torch.Tensor:
+    """R, G and B of an H x W x 4 image."""
+    _need(img, torch.float32, "img")
+    H, W, C = img.shape
+    if C != 4:
+        raise ValueError("img must be H x W x 4")
+    out = torch.empty(H, W, 3, device=img.device, dtype=torch.float32)
+    _check(lib().pts_rgb_of(_ptr(img), H, W, _ptr(out), _stream()))
     return out

@@ -209,7 +209,7 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
                 if (s != PTS_OK) break;
                 launch_irls(ws.d2.ptr, Q, r, delta, ws.wts.ptr, j.energy + t, ws.partial.ptr, ws.ticket.ptr, js);
                 if (t < iters)
-                    launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, j.Ho,
+                    launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->C, idx->w, j.Ho,
                                   j.Wo, j.stride, j.output, idx->status.ptr, js);
             }
         }

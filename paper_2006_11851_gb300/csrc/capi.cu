@@ -74,7 +74,7 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     PTS_TRY(ws.cand_lb.ensure((size_t)cap * kTopK, "candidate bounds"));
     PTS_TRY(ws.fail_list.ensure(cap, "fail list"));
     PTS_TRY(ws.fail2_list.ensure(cap, "second fail list"));
-    PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->w), "full query vectors"));
+    PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->D), "full query vectors"));
     PTS_TRY(ws.best64.ensure(cap, "packed minima"));
     PTS_TRY(ws.thr0.ensure(2 * (size_t)cap, "warm-start bounds"));
     PTS_TRY(ws.pca_thr.ensure((size_t)cap, "PCA-pass bounds"));
@@ -115,7 +115,7 @@ pts_status exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail
         PTS_TRY(ws.part_v.ensure((size_t)ra.Q * np * kTopK, "part lists"));
         PTS_TRY(ws.part_i.ensure((size_t)ra.Q * np * kTopK, "part lists"));
     }
-    idx->last.full_splits = launch_search_full(ra.X, ra.Wo, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
+    idx->last.full_splits = launch_search_full(ra.X, ra.Wo, idx->C, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
                        ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr,
                        ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, np, idx->status.ptr, st, idx->N,
                        &ws.full_pdist);
@@ -132,7 +132,7 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
     Workspace &ws = idx->ws;
     ProposalState &pr = idx->prop;
     if (!pr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no proposal trained on this index");
-    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
+    launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                    ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
     PTS_TRY(pr.top.ensure((size_t)std::max(Q, 1) * 4, "probed clusters"));
     launch_mlp_top4(pr.infer, ws.qcoord.ptr, Q, std::min(idx->d, 64), idx->da_fast, pr.top.ptr, idx->status.ptr, st);
@@ -156,7 +156,7 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
                      pr.etc_ivf.ptr, tc_tiles(idx->N), idx->N, pr.members.ptr, ib, ws.cand_idx.ptr, ws.cand_lb.ptr,
                      idx->status.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out, d2_out,
                   ws.fail_list.ptr, ws.counters.ptr + 3, ws.best64.ptr, idx->status.ptr, st);
@@ -181,12 +181,12 @@ pts_status search_kmtree(pts_index idx, const float *X, int Ho, int Wo, int stri
     KmTree &tr = idx->tree;
     if (!tr.ready) return set_error(PTS_ERR_INVALID_ARG, "nn_search: no k-means tree built on this index");
     Workspace &ws = idx->ws;
-    launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
+    launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
                    ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
     PTS_TRY(tr.leaf_of_query.ensure((size_t)std::max(Q, 1), "tree leaves of the queries"));
     launch_tree_search(tr, ws.qcoord.ptr, idx->da, Q, ws.cand_idx.ptr, ws.cand_lb.ptr, tr.leaf_of_query.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
                   ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
     return PTS_OK;
@@ -196,21 +196,27 @@ pts_status search_kmtree(pts_index idx, const float *X, int Ho, int Wo, int stri
 pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q,
                         int32_t *nn_out, float *d2_out, cudaStream_t st) {
     Workspace &ws = idx->ws;
+    // the bound's components: the index's d_fast (the larger PCA) or its first d
+    const bool fast = idx->exact_fast && idx->d_fast > idx->d && idx->et_fast_rows.ptr;
+    const int bd = fast ? idx->d_fast : idx->d, bda = fast ? idx->da_fast : idx->da;
+    const float *bet = fast ? idx->et_fast.ptr : idx->et.ptr;
+    const float *brows = fast ? idx->et_fast_rows.ptr : idx->et_rows.ptr;
+    const double bvar = fast ? idx->var_fast : idx->var_retained;
     const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
     unsigned int *fail_count = ws.counters.ptr + 0;
     unsigned int *fail2_count = ws.counters.ptr + 1;
     unsigned int *brute_count = ws.counters.ptr + 2;
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
-    if (idx->var_retained < kPcaPassMinVar) {
-        // the d-dimensional bound would certify few queries: every query goes to the
-        // full-dimension pass (its bound needs only ||u_q||^2 and the slack)
-        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, 0, idx->da, 0, nullptr,
+    if (bvar < kPcaPassMinVar) {
+        // the bound would certify few queries: every query goes to the full-dimension pass (its
+        // bound needs only ||u_q||^2 and the slack)
+        launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, 0, idx->da, 0, nullptr,
                        ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
         launch_list_all(ws.fail_list.ptr, fail_count, Q, st);
     } else {
-        launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0,
+        launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, bd, bda, 0,
                        ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st, &ws.proj_part);
         const int pp = pca_parts(Q, idx->ntiles);
         if (pp > 1) {
@@ -220,10 +226,10 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
         // the candidates of the previous search on this grid (any mode) bound the 32nd best
         const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
         if (warm) {
-            launch_warm_pca(ws.cand_idx.ptr, ws.qcoord.ptr, idx->da, idx->et_rows.ptr, idx->enorm.ptr, Q, idx->N,
+            launch_warm_pca(ws.cand_idx.ptr, ws.qcoord.ptr, bda, brows, idx->enorm.ptr, Q, idx->N,
                             ws.pca_thr.ptr, st);
         }
-        launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, idx->da, idx->et.ptr, idx->enorm.ptr,
+        launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, bda, bet, idx->enorm.ptr,
                            idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st, pp, ws.part_v.ptr,
                            ws.part_i.ptr, warm ? ws.pca_thr.ptr : nullptr);
         // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
@@ -251,7 +257,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             break;
         case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
-            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
+            launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
@@ -268,7 +274,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
                              ws.part_i.ptr, idx->status.ptr, st, nullptr, nullptr, 0, nullptr, nullptr, idx->N,
                              ws.kept.ptr);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
-                          idx->nx, idx->N, Q};
+                          idx->nx, idx->N, Q, idx->C};
             // candidates in ascending bound order; stop where bound - slack exceeds the best
             launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out, d2_out,
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
@@ -285,7 +291,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             // bound's rounding error is too large for a useful early exit, so every candidate is
             // re-ranked
             Workspace &ws = idx->ws;
-            launch_project(X, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
+            launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
@@ -298,7 +304,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
                              ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st,
                              nullptr, nullptr, 1, ws.qscale.ptr, idx->enorm.ptr, idx->N, ws.kept.ptr);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
-                          idx->nx, idx->N, Q};
+                          idx->nx, idx->N, Q, idx->C};
             launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
             break;
@@ -445,7 +451,13 @@ long long pts_live_allocations(void) { return g_live.load(); }
 
 pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double var_frac,
                    float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream) {
+    return pca_fit_channels(exemplar, He, We, 3, w, d, var_frac, mean_out, basis_out, eigvals_out, d_out, stream);
+}
+
+pts_status pca_fit_channels(const float *exemplar, int He, int We, int C, int w, int d, double var_frac,
+                            float *mean_out, float *basis_out, double *eigvals_out, int *d_out, void *stream) {
     if (!exemplar || !basis_out) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: null pointer");
+    if (C != 3 && C != 4) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: channels must be 3 or 4");
     if (w < 1 || w > He || w > We) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: bad window");
     if (d > kMaxDPca) return set_error(PTS_ERR_INVALID_ARG, "pca_fit: d > 128");
     if (d <= 0 && !(var_frac > 0.0 && var_frac <= 1.0))
@@ -455,7 +467,7 @@ pts_status pca_fit(const float *exemplar, int He, int We, int w, int d, double v
     PTS_TRY(status.ensure(1, "status"));
     PTS_CUDA_TRY(cudaMemsetAsync(status.ptr, 0, sizeof(int), st));
     int dd = 0;
-    pts_status s = pca_fit_device(exemplar, He, We, w, d, var_frac, 0, mean_out, basis_out,
+    pts_status s = pca_fit_device(exemplar, He, We, C, w, d, var_frac, 0, mean_out, basis_out,
                                   eigvals_out, &dd, nullptr, nullptr, nullptr, nullptr, status.ptr, st);
     if (s == PTS_OK) {
         int h = 0;
@@ -480,6 +492,8 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     const long N = (long)(He - w + 1) * (We - w + 1);
     if (N < 2 || N > (1L << 30))
         return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: bad exemplar size");
+    const int C = params->channels == 0 ? 3 : params->channels;
+    if (C != 3 && C != 4) return set_error(PTS_ERR_INVALID_ARG, "build_exemplar_index: channels must be 3 or 4");
     cudaStream_t st = as_stream(stream);
     pts_index idx = new pts_index_s();
     register_index(idx);
@@ -491,22 +505,23 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     idx->He = He;
     idx->We = We;
     idx->w = w;
-    idx->D = 3 * w * w;
+    idx->C = C;
+    idx->D = C * w * w;
     idx->ny = He - w + 1;
     idx->nx = We - w + 1;
     idx->N = (int)N;
     pts_status s;
-    if ((s = idx->exemplar.ensure((size_t)He * We * 3, "exemplar")) != PTS_OK) return fail(s);
+    if ((s = idx->exemplar.ensure((size_t)He * We * C, "exemplar")) != PTS_OK) return fail(s);
     if ((s = idx->exemplar4.ensure((size_t)He * We, "exemplar rgba")) != PTS_OK) return fail(s);
     if ((s = idx->status.ensure(1, "status")) != PTS_OK) return fail(s);
     if ((s = idx->mu.ensure(idx->D, "mean")) != PTS_OK) return fail(s);
     if ((s = idx->basis.ensure((size_t)kMaxDPca * idx->D, "basis")) != PTS_OK) return fail(s);
     if ((s = idx->eig.ensure(kMaxDPca, "eigenvalues")) != PTS_OK) return fail(s);
     if ((s = idx->umax.ensure(1, "norm max")) != PTS_OK) return fail(s);
-    cudaError_t e = cudaMemcpyAsync(idx->exemplar.ptr, exemplar, sizeof(float) * He * We * 3,
+    cudaError_t e = cudaMemcpyAsync(idx->exemplar.ptr, exemplar, sizeof(float) * He * We * C,
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return fail(cuda_error(e, "copy exemplar"));
-    launch_rgba(idx->exemplar.ptr, (long)He * We, idx->exemplar4.ptr, st);
+    launch_rgba(idx->exemplar.ptr, (long)He * We, C, idx->exemplar4.ptr, st);
     cudaMemsetAsync(idx->status.ptr, 0, sizeof(int), st);
     // one PCA serves both searches: the exact search uses its first d components, the
     // tensor-core and proposal searches the first d_fast (components are ordered by variance)
@@ -517,7 +532,7 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
     const int d_pca = (int)std::min<long>(std::max(d_req, d_fast), rank_cap);
     int dd = 0;
     double trace = 0.0;
-    s = pca_fit_device(idx->exemplar.ptr, He, We, w, d_pca, params->var_frac, params->max_iters,
+    s = pca_fit_device(idx->exemplar.ptr, He, We, C, w, d_pca, params->var_frac, params->max_iters,
                        idx->mu.ptr, idx->basis.ptr, idx->eig.ptr, &dd, &idx->var_retained,
                        &idx->eig_top, &idx->eig_iters, &trace, idx->status.ptr, st);
     if (s != PTS_OK) return fail(s);
@@ -555,16 +570,16 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         return fail(s);
     if ((s = idx->enorm.ensure((size_t)idx->ntiles * kBN, "exemplar norms")) != PTS_OK) return fail(s);
     launch_exemplar_pad(idx->et.ptr, idx->enorm.ptr, idx->N, idx->ntiles, idx->da, st);
-    launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basisT.ptr, dd, idx->da, 1,
+    launch_project(idx->exemplar.ptr, He, We, C, w, 1, idx->mu.ptr, idx->basisT.ptr, dd, idx->da, 1,
                    idx->et.ptr, idx->enorm.ptr, nullptr, 0.0f, nullptr, st);
     launch_norm_max(idx->enorm.ptr, idx->N, idx->umax.ptr, st);
     if ((s = idx->et_rows.ensure((size_t)idx->N * idx->da, "window-major exemplar vectors")) != PTS_OK)
         return fail(s);
     launch_tiles_to_rows(idx->et.ptr, idx->N, idx->da, idx->et_rows.ptr, st);
-    if ((s = idx->efull.ensure((size_t)idx->ntiles * padded_dim(w) * kBN, "full exemplar vectors")) !=
+    if ((s = idx->efull.ensure((size_t)idx->ntiles * padded_dim(idx->D) * kBN, "full exemplar vectors")) !=
         PTS_OK)
         return fail(s);
-    launch_exemplar_full(idx->exemplar.ptr, We, w, idx->nx, idx->N, idx->mu.ptr, idx->efull.ptr,
+    launch_exemplar_full(idx->exemplar.ptr, We, C, w, idx->nx, idx->N, idx->mu.ptr, idx->efull.ptr,
                          idx->ntiles, st);
     // fast-mode search vectors: d_fast coordinates + the residual beyond them
     if ((s = idx->et_fast.ensure((size_t)idx->ntiles * idx->da_fast * kBN, "fast exemplar vectors")) != PTS_OK)
@@ -573,10 +588,20 @@ pts_status build_exemplar_index(const float *exemplar, int He, int We, int w,
         DevBuf<float> norm_tmp;
         if ((s = norm_tmp.ensure((size_t)idx->ntiles * kBN, "norm scratch")) != PTS_OK) return fail(s);
         launch_exemplar_pad(idx->et_fast.ptr, norm_tmp.ptr, idx->N, idx->ntiles, idx->da_fast, st);
-        launch_project(idx->exemplar.ptr, He, We, w, 1, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 1,
+        launch_project(idx->exemplar.ptr, He, We, C, w, 1, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 1,
                        idx->et_fast.ptr, norm_tmp.ptr, nullptr, 0.0f, nullptr, st);
         cudaStreamSynchronize(st);
         norm_tmp.release();
+    }
+    if ((s = idx->et_fast_rows.ensure((size_t)idx->N * idx->da_fast, "window-major fast exemplar vectors")) != PTS_OK)
+        return fail(s);
+    launch_tiles_to_rows(idx->et_fast.ptr, idx->N, idx->da_fast, idx->et_fast_rows.ptr, st);
+    {
+        std::vector<double> ev(idx->d_fast);
+        cudaMemcpy(ev.data(), idx->eig.ptr, sizeof(double) * idx->d_fast, cudaMemcpyDeviceToHost);
+        double kept = 0.0;
+        for (double v : ev) kept += v;
+        idx->var_fast = trace > 0 ? kept / trace : 0.0;
     }
     idx->ktc = tc_padded_k(idx->d_fast);
     if ((s = idx->etc.ensure((size_t)tc_tiles(idx->N) * tc_tile_rows() * idx->ktc, "fp16 exemplar tiles")) != PTS_OK)
@@ -646,6 +671,7 @@ void pts_index_destroy(pts_index idx) {
     idx->etc8.release();
     idx->f8scale.release();
     idx->et_fast.release();
+    idx->et_fast_rows.release();
     {
         ProposalState &pr = idx->prop;
         pr.centroids.release();
@@ -695,6 +721,16 @@ pts_status pts_index_get_info(pts_index idx, pts_index_info *info) {
     info->eig_top = idx->eig_top;
     info->eig_iters = idx->eig_iters;
     info->unorm2_max = idx->unorm2_max;
+    info->channels = idx->C;
+    const bool fast = idx->exact_fast && idx->d_fast > idx->d;
+    info->exact_dims = fast ? idx->d_fast : idx->d;
+    info->exact_var = fast ? idx->var_fast : idx->var_retained;
+    return PTS_OK;
+}
+
+pts_status pts_index_set_exact_bound(pts_index idx, int fast) {
+    if (!idx || (fast != 0 && fast != 1)) return set_error(PTS_ERR_INVALID_ARG, "pts_index_set_exact_bound: bad argument");
+    idx->exact_fast = fast;
     return PTS_OK;
 }
 
@@ -806,7 +842,7 @@ pts_status m_step(pts_index idx, const int32_t *nn, const float *weights, int Ho
                   int stride, float *output, void *stream) {
     if (!idx || !nn || !output) return set_error(PTS_ERR_INVALID_ARG, "m_step: null pointer");
     PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "m_step"));
-    launch_m_step(nn, weights, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride,
+    launch_m_step(nn, weights, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->C, idx->w, Ho, Wo, stride,
                   output, idx->status.ptr, as_stream(stream));
     PTS_CUDA_TRY(cudaGetLastError());
     return PTS_OK;
@@ -816,6 +852,7 @@ pts_status m_step_hist(pts_index idx, const int32_t *nn, const float *weights, i
                        const float *current, float *output, void *stream) {
     if (!idx || !nn || !output || !current) return set_error(PTS_ERR_INVALID_ARG, "m_step_hist: null pointer");
     if (nbins < 2 || nbins > kMaxHistBins) return set_error(PTS_ERR_INVALID_ARG, "m_step_hist: nbins in 2..256");
+    if (idx->C != 3) return set_error(PTS_ERR_INVALID_ARG, "m_step_hist: histogram weights need an RGB index");
     PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "m_step_hist"));
     cudaStream_t st = as_stream(stream);
     Workspace &ws = idx->ws;
@@ -834,6 +871,7 @@ pts_status pts_histogram_match(pts_index idx, float *image, int H, int W, int nb
     if (!idx || !image) return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: null pointer");
     if (nbins < 2 || nbins > kMaxHistBins)
         return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: nbins in 2..256");
+    if (idx->C != 3) return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: needs an RGB index");
     if (H < 1 || W < 1) return set_error(PTS_ERR_INVALID_ARG, "pts_histogram_match: empty image");
     cudaStream_t st = as_stream(stream);
     Workspace &ws = idx->ws;
@@ -857,6 +895,8 @@ static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, 
         return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": need 0 < r <= 2 and delta > 0");
     if (nbins != 0 && (nbins < 2 || nbins > kMaxHistBins))
         return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": nbins in 2..256");
+    if (nbins != 0 && idx->C != 3)
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": histogram weights need an RGB index");
     PTS_TRY(check_grid(Ho, Wo, idx->w, stride, name));
     cudaStream_t st = as_stream(stream);
     const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
@@ -881,7 +921,7 @@ static pts_status synthesize_impl(pts_index idx, float *output, int Ho, int Wo, 
             launch_m_step_hist(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo,
                                stride, nbins, cx, nx, cz, nz, output, idx->status.ptr, st);
         } else {
-            launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho,
+            launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->C, idx->w, Ho,
                           Wo, stride, output, idx->status.ptr, st);
         }
     }
@@ -917,6 +957,8 @@ pts_status synthesize_level_converge(pts_index idx, float *output, int Ho, int W
         return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": need 0 < r <= 2 and delta > 0");
     if (nbins != 0 && (nbins < 2 || nbins > kMaxHistBins))
         return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": nbins 0 or in 2..256");
+    if (nbins != 0 && idx->C != 3)
+        return set_error(PTS_ERR_INVALID_ARG, std::string(name) + ": histogram weights need an RGB index");
     PTS_TRY(check_grid(Ho, Wo, idx->w, stride, name));
     cudaStream_t st = as_stream(stream);
     const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
@@ -942,7 +984,7 @@ pts_status synthesize_level_converge(pts_index idx, float *output, int Ho, int W
             launch_m_step_hist(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo,
                                stride, nbins, cx, nx, cz, nz, output, idx->status.ptr, st);
         } else {
-            launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->w, Ho, Wo, stride,
+            launch_m_step(ws.nn.ptr, ws.wts.ptr, idx->exemplar4.ptr, idx->We, idx->nx, idx->N, idx->C, idx->w, Ho, Wo, stride,
                           output, idx->status.ptr, st);
         }
         PTS_CUDA_TRY(cudaMemcpyAsync(ws.nn_prev.ptr, ws.nn.ptr, sizeof(int) * Q, cudaMemcpyDeviceToDevice, st));
@@ -977,7 +1019,7 @@ pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int W
     PTS_TRY(ensure_workspace(idx, Q));
     cudaStream_t st = as_stream(stream);
     Workspace &ws = idx->ws;
-    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
+    launch_project(output, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d, idx->da, 0, ws.qcoord.ptr,
                    ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
     PTS_CUDA_TRY(cudaMemcpy2DAsync(y_out, sizeof(float) * idx->d, ws.qcoord.ptr, sizeof(float) * idx->da,
                                    sizeof(float) * idx->d, Q, cudaMemcpyDeviceToDevice, st));
@@ -994,7 +1036,7 @@ pts_status pts_proposal_top4(pts_index idx, const float *output, int Ho, int Wo,
     const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
     PTS_TRY(ensure_workspace(idx, Q));
     Workspace &ws = idx->ws;
-    launch_project(output, Ho, Wo, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
+    launch_project(output, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                    ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
     if (fused) {
         launch_mlp_top4(pr.infer, ws.qcoord.ptr, Q, std::min(idx->d, 64), idx->da_fast, top_out, idx->status.ptr, st);

@@ -7,9 +7,11 @@
 // covering set of query windows (section 2.2, 2x2 patch processing), so one
 // thread owns one patch: it walks the covering windows in increasing query
 // order (the order of the sum above), gathers the co-located s x s block of
-// each matched exemplar window and writes its s*s*3 outputs once.  No
+// each matched exemplar window and writes its s*s*3 colour outputs once.  No
 // atomics, deterministic.  The exemplar (<= a few MB) stays in L2, read from
-// an RGBA copy (alpha 0) so that each gathered pixel is one 16-byte load.
+// an RGBA copy (fourth value 0, or the scale channel of an RGBS exemplar) so
+// that each gathered pixel is one 16-byte load.  The output has C = 3 or 4
+// channels; with 4 its fourth (the scale map, section 1) is left as it is.
 #include <algorithm>
 
 #include "pts_internal.cuh"
@@ -25,7 +27,7 @@ namespace {
 template <int S, bool HIST>
 __global__ void __launch_bounds__(128)
     k_m_step(const int *__restrict__ nn, const float *__restrict__ wts, const float4 *__restrict__ Z4,
-             int We, int ex, int N, int w, int Ho, int Wo, int qy_n, int qx_n,
+             int We, int ex, int N, int C, int w, int Ho, int Wo, int qy_n, int qx_n,
              float *__restrict__ out, int *__restrict__ status, int nbins, const unsigned int *__restrict__ cx,
              long nx, const unsigned int *__restrict__ cz, long nz) {
     __shared__ float hex[HIST ? 3 * kMaxHistBins : 1];
@@ -89,13 +91,13 @@ __global__ void __launch_bounds__(128)
     if (bad) atomicOr(status, kDevErrBounds);
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-        float *o = out + ((size_t)(py * S + t) * Wo + px * S) * 3;
+        float *o = out + ((size_t)(py * S + t) * Wo + px * S) * C;
 #pragma unroll
         for (int u = 0; u < S; ++u) {
             float d = den;
             if constexpr (HIST) d = dpix[t][u];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) o[u * 3 + c] = num[t][u][c] / d;
+            for (int c = 0; c < 3; ++c) o[u * C + c] = num[t][u][c] / d;
         }
     }
 }
@@ -110,9 +112,9 @@ __global__ void __launch_bounds__(256) k_count_diff(const int *__restrict__ a, c
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-__global__ void k_rgba(const float *__restrict__ Z, long npix, float4 *__restrict__ out) {
+__global__ void k_rgba(const float *__restrict__ Z, long npix, int C, float4 *__restrict__ out) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < npix; i += (long)gridDim.x * blockDim.x)
-        out[i] = make_float4(Z[3 * i], Z[3 * i + 1], Z[3 * i + 2], 0.0f);
+        out[i] = make_float4(Z[C * i], Z[C * i + 1], Z[C * i + 2], C == 4 ? Z[C * i + 3] : 0.0f);
 }
 
 // IRLS weights and energy (Eqs. 5-8).  Fixed grid; each block sums its
@@ -213,13 +215,13 @@ void launch_count_diff(const int *a, const int *b, int n, unsigned int *count, c
     k_count_diff<<<(unsigned)std::min<long>(ceil_div((long)n, 256), 152 * 4), 256, 0, st>>>(a, b, n, count);
 }
 
-void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st) {
+void launch_rgba(const float *Z, long npix, int C, float4 *out, cudaStream_t st) {
     if (npix <= 0) return;
     count_launches(1);
-    k_rgba<<<(unsigned)std::min<long>(ceil_div(npix, 256), 152 * 8), 256, 0, st>>>(Z, npix, out);
+    k_rgba<<<(unsigned)std::min<long>(ceil_div(npix, 256), 152 * 8), 256, 0, st>>>(Z, npix, C, out);
 }
 
-void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w,
+void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int C, int w,
                    int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st) {
     const int qy_n = (Ho - w) / stride + 1, qx_n = (Wo - w) / stride + 1;
     const int PX = Wo / stride, PY = Ho / stride;
@@ -227,15 +229,15 @@ void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, in
     ProfScope ps(kProfMStep, st, 1);
     switch (stride) {
         case 1:
-            k_m_step<1, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status, 0,
+            k_m_step<1, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out, status, 0,
                                                        nullptr, 1, nullptr, 1);
             break;
         case 2:
-            k_m_step<2, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status, 0,
+            k_m_step<2, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out, status, 0,
                                                        nullptr, 1, nullptr, 1);
             break;
         case 4:
-            k_m_step<4, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status, 0,
+            k_m_step<4, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out, status, 0,
                                                        nullptr, 1, nullptr, 1);
             break;
         default:
@@ -252,15 +254,15 @@ void launch_m_step_hist(const int *nn, const float *wts, const float4 *Z4, int W
     ProfScope ps(kProfMStep, st, 1);
     switch (stride) {
         case 1:
-            k_m_step<1, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status,
+            k_m_step<1, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, 3, w, Ho, Wo, qy_n, qx_n, out, status,
                                                       nbins, cx, nx, cz, nz);
             break;
         case 2:
-            k_m_step<2, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status,
+            k_m_step<2, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, 3, w, Ho, Wo, qy_n, qx_n, out, status,
                                                       nbins, cx, nx, cz, nz);
             break;
         case 4:
-            k_m_step<4, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, w, Ho, Wo, qy_n, qx_n, out, status,
+            k_m_step<4, true><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, 3, w, Ho, Wo, qy_n, qx_n, out, status,
                                                       nbins, cx, nx, cz, nz);
             break;
         default:

@@ -27,15 +27,15 @@ constexpr int kMaxM = 112;     // subspace widths up to this keep the m x m work
 constexpr int kMaxMBig = 256;  // beyond it (up to this) the m x m matrices live in global memory
 
 __global__ void __launch_bounds__(256)
-    k_win_mean(const float *__restrict__ Z, int We, int w, int ex, long N, double *__restrict__ mu) {
+    k_win_mean(const float *__restrict__ Z, int We, int C, int w, int ex, long N, double *__restrict__ mu) {
     __shared__ double red[256];
     const int k = blockIdx.x;
-    const int row = 3 * w;
+    const int row = C * w;
     const int dy = k / row, rem = k - dy * row;
     double acc = 0.0;
     for (long n = threadIdx.x; n < N; n += 256) {
         const long ey = n / ex, exx = n - ey * ex;
-        acc += (double)Z[((ey + dy) * We + exx) * 3 + rem];
+        acc += (double)Z[((ey + dy) * We + exx) * C + rem];
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256)
 // partial covariance of n in [slice*slice_len, ...) for the 64x64 tile pair
 // (bi, bj), bi <= bj, enumerated by blockIdx.x
 __global__ void __launch_bounds__(256)
-    k_cov(const float *__restrict__ Z, int We, int w, int ex, long N, const double *__restrict__ mu,
+    k_cov(const float *__restrict__ Z, int We, int C, int w, int ex, long N, const double *__restrict__ mu,
           int D, int T, long slice_len, double *__restrict__ part) {
     __shared__ double sA[16][64 + 1];
     __shared__ double sB[16][64 + 1];
@@ -62,17 +62,17 @@ __global__ void __launch_bounds__(256)
         ++bi;
     }
     const int bj = bi + rem;
-    const int row = 3 * w;
+    const int row = C * w;
     const int tid = threadIdx.x;
     if (tid < 64) {
         const int k = bi * 64 + tid;
         const int kk = k < D ? k : 0;
-        koffA[tid] = (kk / row) * We * 3 + (kk % row);
+        koffA[tid] = (kk / row) * We * C + (kk % row);
         muA[tid] = k < D ? mu[k] : 0.0;
     } else if (tid < 128) {
         const int k = bj * 64 + tid - 64;
         const int kk = k < D ? k : 0;
-        koffB[tid - 64] = (kk / row) * We * 3 + (kk % row);
+        koffB[tid - 64] = (kk / row) * We * C + (kk % row);
         muB[tid - 64] = k < D ? mu[k] : 0.0;
     }
     __syncthreads();
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256)
             double va = 0.0, vb = 0.0;
             if (n < n1) {
                 const long ey = n / ex, exx = n - ey * ex;
-                const long base = (ey * We + exx) * 3;
+                const long base = (ey * We + exx) * C;
                 if (bi * 64 + c < D) va = (double)Z[base + koffA[c]] - muA[c];
                 if (bj * 64 + c < D) vb = (double)Z[base + koffB[c]] - muB[c];
             }
@@ -420,11 +420,11 @@ struct Scratch {
 
 }  // namespace
 
-pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, double var_frac,
+pts_status pca_fit_device(const float *exemplar, int He, int We, int nch, int w, int d, double var_frac,
                           int max_iters, float *mean_out, float *basis_out, double *eig_out,
                           int *d_used, double *var_retained, double *eig_top, int *iters_used,
                           double *trace_out, int *status, cudaStream_t st) {
-    const int D = 3 * w * w;
+    const int D = nch * w * w;
     const int ex = We - w + 1;
     const long N = (long)(He - w + 1) * ex;
     int dd = d > 0 ? d : kMaxD;
@@ -464,9 +464,9 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, d
     set_smem_attr(reinterpret_cast<const void *>(k_chol), (int)(sizeof(double) * kMaxM * kMaxM));
 
     count_launches(1);
-    k_win_mean<<<D, 256, 0, st>>>(exemplar, We, w, ex, N, mu64);
+    k_win_mean<<<D, 256, 0, st>>>(exemplar, We, nch, w, ex, N, mu64);
     count_launches(1);
-    k_cov<<<dim3(npairs, ns), 256, 0, st>>>(exemplar, We, w, ex, N, mu64, D, T, slice_len, part);
+    k_cov<<<dim3(npairs, ns), 256, 0, st>>>(exemplar, We, nch, w, ex, N, mu64, D, T, slice_len, part);
     count_launches(1);
     k_cov_reduce<<<ceil_div((long)D * D, 256), 256, 0, st>>>(part, ns, D, N, C);
     count_launches(1);

@@ -23,7 +23,7 @@ namespace pts {
 namespace {
 
 constexpr char kMagic[8] = {'P', 'T', 'S', 'I', 'N', 'D', 'E', 'X'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;  // 2: the channel count joined the header
 constexpr uint32_t kByteOrder = 0x01020304u;
 constexpr int kTreeBranch = 4;  // k of the k-means tree (section 2.2)
 
@@ -40,6 +40,7 @@ struct Header {
     int32_t prop_ready = 0, prop_C = 0;
     float prop_factor = 0.0f;
     int32_t tree_ready = 0, tree_internal = 0, tree_leaves = 0, tree_depth = 0;
+    int32_t C = 3;  // channels per pixel (3 RGB, 4 RGBS)
 };
 
 // One section: its tag, element size and count as the header implies them.
@@ -53,7 +54,7 @@ struct Section {
 std::vector<Section> sections_of(const Header &h) {
     const uint64_t tcr = (uint64_t)tc_tiles(h.N) * tc_tile_rows();
     std::vector<Section> s = {
-        {tag("EXEM"), 4, (uint64_t)h.He * h.We * 3},
+        {tag("EXEM"), 4, (uint64_t)h.He * h.We * h.C},
         {tag("EXE4"), 16, (uint64_t)h.He * h.We},
         {tag("MEAN"), 4, (uint64_t)h.D},
         {tag("BASI"), 4, (uint64_t)kMaxDPca * h.D},
@@ -62,7 +63,7 @@ std::vector<Section> sections_of(const Header &h) {
         {tag("ETIL"), 4, (uint64_t)h.ntiles * h.da * kBN},
         {tag("EROW"), 4, (uint64_t)h.N * h.da},
         {tag("ENRM"), 4, (uint64_t)h.ntiles * kBN},
-        {tag("EFUL"), 4, (uint64_t)h.ntiles * padded_dim(h.w) * kBN},
+        {tag("EFUL"), 4, (uint64_t)h.ntiles * padded_dim(h.D) * kBN},
         {tag("EFST"), 4, (uint64_t)h.ntiles * h.da_fast * kBN},
         {tag("ETCH"), 2, tcr * h.ktc},
         {tag("ETC8"), 1, tcr * h.kf8},
@@ -98,13 +99,15 @@ void header_fields(Header &h, F &&f) {
     f(h.unorm2_max), f(h.var_retained), f(h.eig_top);
     f(h.prop_ready), f(h.prop_C), f(h.prop_factor);
     f(h.tree_ready), f(h.tree_internal), f(h.tree_leaves), f(h.tree_depth);
+    f(h.C);
 }
 
 // The header is consistent with an index the build could have made.
 pts_status check_header(const Header &h) {
     auto bad = [](const char *what) { return set_error(PTS_ERR_INVALID_ARG, std::string("index file header: ") + what); };
     if (h.w < 1 || h.He < h.w || h.We < h.w || h.He > (1 << 16) || h.We > (1 << 16)) return bad("bad image or window size");
-    if (h.D != 3 * h.w * h.w || h.ny != h.He - h.w + 1 || h.nx != h.We - h.w + 1) return bad("inconsistent window grid");
+    if (h.C != 3 && h.C != 4) return bad("channels must be 3 or 4");
+    if (h.D != h.C * h.w * h.w || h.ny != h.He - h.w + 1 || h.nx != h.We - h.w + 1) return bad("inconsistent window grid");
     const long N = (long)h.ny * h.nx;
     if (N < 2 || N > (1L << 30) || h.N != N) return bad("inconsistent window count");
     if (h.d < 1 || h.d > kMaxD || h.da != ((h.d + 1 + 3) & ~3)) return bad("bad PCA dimensions");
@@ -233,6 +236,7 @@ pts_status pts_index_save(pts_index idx, const char *path) {
     h.tree_internal = idx->tree.ready ? idx->tree.n_internal : 0;
     h.tree_leaves = idx->tree.ready ? idx->tree.n_leaves : 0;
     h.tree_depth = idx->tree.ready ? idx->tree.depth : 0;
+    h.C = idx->C;
     PTS_TRY(check_header(h));
     const std::vector<Section> secs = sections_of(h);
     const std::vector<void *> dev = device_tables(idx, h);
@@ -331,12 +335,13 @@ pts_status pts_index_load(const char *path, pts_index *out) {
         return set_error(PTS_ERR_CUDA, "pts_index_load: no CUDA device");
     }
     idx->He = h.He, idx->We = h.We, idx->w = h.w, idx->D = h.D, idx->N = h.N, idx->d = h.d, idx->da = h.da;
+    idx->C = h.C;
     idx->d_fast = h.d_fast, idx->da_fast = h.da_fast, idx->ny = h.ny, idx->nx = h.nx, idx->ntiles = h.ntiles;
     idx->ktc = h.ktc, idx->kf8 = h.kf8, idx->eig_iters = h.eig_iters, idx->tc_parts_override = h.tc_parts;
     idx->unorm2_max = h.unorm2_max, idx->var_retained = h.var_retained, idx->eig_top = h.eig_top;
     // allocate every table at the size the build gives it
     const uint64_t tcr = (uint64_t)tc_tiles(h.N) * tc_tile_rows();
-    if ((s = idx->exemplar.ensure((size_t)h.He * h.We * 3, "exemplar")) != PTS_OK) return fail(s);
+    if ((s = idx->exemplar.ensure((size_t)h.He * h.We * h.C, "exemplar")) != PTS_OK) return fail(s);
     if ((s = idx->exemplar4.ensure((size_t)h.He * h.We, "exemplar rgba")) != PTS_OK) return fail(s);
     if ((s = idx->mu.ensure(h.D, "mean")) != PTS_OK) return fail(s);
     if ((s = idx->basis.ensure((size_t)kMaxDPca * h.D, "basis")) != PTS_OK) return fail(s);
@@ -345,7 +350,7 @@ pts_status pts_index_load(const char *path, pts_index *out) {
     if ((s = idx->et.ensure((size_t)h.ntiles * h.da * kBN, "exemplar vectors")) != PTS_OK) return fail(s);
     if ((s = idx->et_rows.ensure((size_t)h.N * h.da, "window-major exemplar vectors")) != PTS_OK) return fail(s);
     if ((s = idx->enorm.ensure((size_t)h.ntiles * kBN, "exemplar norms")) != PTS_OK) return fail(s);
-    if ((s = idx->efull.ensure((size_t)h.ntiles * padded_dim(h.w) * kBN, "full exemplar vectors")) != PTS_OK)
+    if ((s = idx->efull.ensure((size_t)h.ntiles * padded_dim(h.D) * kBN, "full exemplar vectors")) != PTS_OK)
         return fail(s);
     if ((s = idx->et_fast.ensure((size_t)h.ntiles * h.da_fast * kBN, "fast exemplar vectors")) != PTS_OK)
         return fail(s);
@@ -383,6 +388,19 @@ pts_status pts_index_load(const char *path, pts_index *out) {
         if (e != cudaSuccess) return fail(cuda_error(e, "pts_index_load: upload table"));
     }
     if (cudaMemset(idx->status.ptr, 0, sizeof(int)) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "status"));
+    // the window-major copy of the fast vectors and their variance fraction follow from the tables
+    if ((s = idx->et_fast_rows.ensure((size_t)h.N * h.da_fast, "window-major fast exemplar vectors")) != PTS_OK)
+        return fail(s);
+    launch_tiles_to_rows(idx->et_fast.ptr, h.N, h.da_fast, idx->et_fast_rows.ptr, nullptr);
+    {
+        const double *ev = nullptr;
+        for (size_t i = 0; i < secs.size(); ++i)
+            if (secs[i].tag == tag("EIGV")) ev = reinterpret_cast<const double *>(data[i].data());
+        double kept_d = 0.0, kept_fast = 0.0;
+        for (int j = 0; j < h.d; ++j) kept_d += ev[j];
+        for (int j = 0; j < h.d_fast && j < kMaxDPca; ++j) kept_fast += ev[j];
+        idx->var_fast = kept_d > 0.0 ? h.var_retained * kept_fast / kept_d : 0.0;
+    }
     if (h.prop_ready) {
         // the network's BF16 weights and the inference kernel's packed copy follow from the FP32
         // weights exactly as at the end of training

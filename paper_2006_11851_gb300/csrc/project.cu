@@ -5,7 +5,8 @@
 //   ||u||^2 = ||v - mu||^2
 //   r = sqrt(max(0, ||u||^2 - ||y||^2))  (norm of the discarded part)
 // A tiled SIMT GEMM (windows x D) (D x d): a block owns 128 windows and all d <= 128 outputs.
-// Windows are read straight from the HWC image, never materialised: per 32-element slice of
+// Windows are read straight from the HWC image (C = 3 or 4 channels), never materialised: per
+// 32-element slice of
 // the window vector the block stages the 128 centred slices and the slice of the transposed
 // basis ([D][128], built with the index) in shared memory, and each thread accumulates an
 // 8-window x 8-coordinate (4 for d <= 64) register tile.
@@ -78,7 +79,7 @@ __device__ __forceinline__ void write_window(const ProjOut &o, long win, const f
 // part[blockIdx.y][win][PD + 1] (coordinates, then ||u||^2), reduced by k_project_finish.
 template <int PD>
 __global__ void __launch_bounds__(256, 2)
-    k_project(const float *__restrict__ img, int W, int w, int stride, int qx_n, int Qn,
+    k_project(const float *__restrict__ img, int W, int C, int w, int stride, int qx_n, int Qn,
               const float *__restrict__ mu, const float *__restrict__ basisT, int kper, ProjOut o,
               float *__restrict__ part) {
     constexpr int NG = PD / 64;      // float4 groups of coordinates per thread
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256, 2)
     float *const xs = sm.u.st.xs;
     float *const bs = sm.u.st.bs;
     float *const ys = sm.u.ys;
-    const int row = 3 * w, D = row * w, d = o.d, W3 = 3 * W;
+    const int row = C * w, D = row * w, d = o.d, W3 = C * W;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const long win0 = (long)blockIdx.x * kPWin;
     const int kbeg = blockIdx.y * kper, kend = min(D, kbeg + kper);
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256, 2)
         const long win = win0 + tid;
         const long wq = win < Qn ? win : 0;
         const long qy = wq / qx_n, qx = wq - qy * qx_n;
-        sm.base[tid] = (qy * stride * (long)W + qx * stride) * 3;
+        sm.base[tid] = (qy * stride * (long)W + qx * stride) * C;
     }
     __syncthreads();
     const int sw = tid & (kPWin - 1), sk = tid >> 7;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(256, 2)
             xr[i] = (k < kend && wvalid) ? __ldg(src + off) - __ldg(mu + k) : 0.0f;
             e += 2;
             off += 2;
-            if (e >= row) {  // row >= 3: one wrap at most
+            if (e >= row) {  // row >= 3: one wrap at most (e advances by 2)
                 e -= row;
                 off += W3 - row;
             }
@@ -237,18 +238,18 @@ __global__ void __launch_bounds__(256) k_project_finish(const float *__restrict_
 
 // ||v - mu||^2 (and tau) of each window only, one warp per window (the search needs no
 // coordinates when it runs in full dimension).
-__global__ void __launch_bounds__(256) k_window_norms(const float *__restrict__ img, int W, int w, int stride, int qx_n,
+__global__ void __launch_bounds__(256) k_window_norms(const float *__restrict__ img, int W, int C, int w, int stride, int qx_n,
                                                       int Qn, const float *__restrict__ mu, ProjOut o) {
     const int lane = threadIdx.x & 31;
     const long win = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (win >= Qn) return;
-    const int row = 3 * w;
+    const int row = C * w;
     const long qy = win / qx_n, qx = win - qy * qx_n;
-    const float *src = img + (qy * stride * (long)W + qx * stride) * 3;
+    const float *src = img + (qy * stride * (long)W + qx * stride) * C;
     float un = 0.0f;
     for (int dy = 0; dy < w; ++dy)
         for (int e = lane; e < row; e += 32) {
-            const float a = __ldg(src + (size_t)dy * W * 3 + e) - __ldg(mu + dy * row + e);
+            const float a = __ldg(src + (size_t)dy * W * C + e) - __ldg(mu + dy * row + e);
             un = fmaf(a, a, un);
         }
 #pragma unroll
@@ -293,7 +294,7 @@ __global__ void k_norm_max(const float *__restrict__ v, int n, float *__restrict
 
 }  // namespace
 
-void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
+void launch_project(const float *img, int H, int W, int C, int w, int stride, const float *mu,
                     const float *basisT, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
                     cudaStream_t st, DevBuf<float> *scratch) {
@@ -303,10 +304,10 @@ void launch_project(const float *img, int H, int W, int w, int stride, const flo
     const ProjOut o{d, da, layout, out_coord, out_norm, out_tau, tau_scale, umax};
     ProfScope ps(kProfProject, st, 1);
     if (d <= 0) {
-        k_window_norms<<<(unsigned)ceil_div(Qn * 32, 256), 256, 0, st>>>(img, W, w, stride, qx_n, (int)Qn, mu, o);
+        k_window_norms<<<(unsigned)ceil_div(Qn * 32, 256), 256, 0, st>>>(img, W, C, w, stride, qx_n, (int)Qn, mu, o);
         return;
     }
-    const int D = 3 * w * w;
+    const int D = C * w * w;
     const long nblk = ceil_div(Qn, kPWin);
     // slices of the window vector per block: enough blocks for two per SM when the windows alone
     // leave SMs idle, each slice range at least 256 long
@@ -322,11 +323,11 @@ void launch_project(const float *img, int H, int W, int w, int stride, const flo
     set_smem_attr(reinterpret_cast<const void *>(k_project<64>), (int)sizeof(ProjSmem<64>));
     set_smem_attr(reinterpret_cast<const void *>(k_project<128>), (int)sizeof(ProjSmem<128>));
     if (PDc == 64)
-        k_project<64><<<grid, 256, sizeof(ProjSmem<64>), st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basisT, kper, o,
-                                                               part);
+        k_project<64><<<grid, 256, sizeof(ProjSmem<64>), st>>>(img, W, C, w, stride, qx_n, (int)Qn, mu, basisT, kper,
+                                                               o, part);
     else
-        k_project<128><<<grid, 256, sizeof(ProjSmem<128>), st>>>(img, W, w, stride, qx_n, (int)Qn, mu, basisT, kper,
-                                                                 o, part);
+        k_project<128><<<grid, 256, sizeof(ProjSmem<128>), st>>>(img, W, C, w, stride, qx_n, (int)Qn, mu, basisT,
+                                                                 kper, o, part);
     if (nsplit > 1) {
         count_launches(1);
         if (PDc == 64)

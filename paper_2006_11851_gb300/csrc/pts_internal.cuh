@@ -192,6 +192,7 @@ struct ProposalState {
 
 struct pts_index_s {
     int device = 0;
+    int C = 3;  // channels per pixel: 3 (RGB) or 4 (RGB + the scale map, section 1)
     int He = 0, We = 0, w = 0, D = 0, N = 0, d = 0, da = 0;
     int d_fast = 0, da_fast = 0;  // PCA dimensions / vector length of the fast modes
     int ny = 0, nx = 0;  // exemplar window grid
@@ -210,6 +211,9 @@ struct pts_index_s {
     pts::DevBuf<float> enorm;     // [ntiles*kBN] ||u_n||^2, +inf for padding
     pts::DevBuf<float> efull;     // [ntiles][Dp][kBN] = -2 u_n (full dimension)
     pts::DevBuf<float> et_fast;   // [ntiles][da_fast][kBN] = -2 (y_n, r_n, 0...) with d_fast coordinates
+    pts::DevBuf<float> et_fast_rows;  // [N][da_fast], the same vectors window-major (warm-start bound)
+    double var_fast = 0.0;        // variance fraction the d_fast components keep
+    int exact_fast = 0;           // the exact search bounds with the d_fast components (else the first d)
     pts::DevBuf<__half> etc;      // [tc_tiles(N)][tc_tile_rows() x Ktc] FP16 MMA operand tiles
     pts::DevBuf<uint8_t> etc8;    // [tc_tiles(N)][tc_tile_rows() x Kf8] FP8 E4M3 operand tiles
     pts::DevBuf<float> f8scale;   // [d_fast + 1] per-dimension scales of the FP8 tiles
@@ -245,12 +249,12 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
 pts_status ensure_workspace(pts_index idx, int Q);
 pts_status check_grid_public(int H, int W, int w, int stride, const char *what);
 void prof_suspend(bool on);
-pts_status pca_fit_device(const float *exemplar, int He, int We, int w, int d, double var_frac,
+pts_status pca_fit_device(const float *exemplar, int He, int We, int C, int w, int d, double var_frac,
                           int max_iters, float *mean_out, float *basis_out, double *eig_out,
                           int *d_used, double *var_retained, double *eig_top, int *iters_used,
                           double *trace_out, int *status, cudaStream_t st);
 // project.cu
-void launch_project(const float *img, int H, int W, int w, int stride, const float *mu,
+void launch_project(const float *img, int H, int W, int C, int w, int stride, const float *mu,
                     const float *basisT, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
                     cudaStream_t st, DevBuf<float> *scratch = nullptr);
@@ -263,7 +267,7 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
                         cudaStream_t st, int nparts = 1,
                         float *part_v = nullptr, int *part_i = nullptr,
                         const float *thr_init = nullptr);
-int launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
+int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
@@ -274,7 +278,7 @@ int pca_parts(int Q, int ntiles);
 void launch_tiles_to_rows(const float *et, int N, int da, float *rows, cudaStream_t st);
 void launch_warm_pca(const int *prev_idx, const float *qcoord, int da, const float *et_rows, const float *enorm, int Q,
                      int N, float *thr, cudaStream_t st);
-void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
+void launch_exemplar_full(const float *Z, int We, int C, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st);
 // search_tc.cu
 int tc_padded_k(int d);
@@ -336,7 +340,7 @@ void mlp_gather(MlpState &s, const float *Y, int d, int ldy, const int *perm, in
                 cudaStream_t st);
 pts_status gemm_selftest(int M, int N, int K, double *max_rel_err);
 // full-dimension vectors are padded with zero rows to a multiple of 32
-inline int padded_dim(int w) { return (3 * w * w + 31) / 32 * 32; }
+inline int padded_dim(int D) { return (D + 31) / 32 * 32; }
 // rerank.cu
 struct RerankArgs {
     const float *X;
@@ -344,6 +348,7 @@ struct RerankArgs {
     const float *Z;
     int We, w, ex, N;
     int Q;
+    int C;  // channels per pixel of both images (3: RGB, 4: RGB + scale)
 };
 // qlist/qcount == NULL: all Q queries; else the listed ones (count on the device)
 void launch_list_all(int *list, unsigned int *count, int Q, cudaStream_t st);
@@ -377,7 +382,7 @@ struct ProfScope {
     ~ProfScope() { prof_end(cls, st, tok); }
 };
 // mstep.cu
-void launch_rgba(const float *Z, long npix, float4 *out, cudaStream_t st);
+void launch_rgba(const float *Z, long npix, int C, float4 *out, cudaStream_t st);
 void launch_count_diff(const int *a, const int *b, int n, unsigned int *count, cudaStream_t st);
 // kmtree.cu (section 2.2's k-means tree)
 pts_status build_kmtree(KmTree &tr, const float *rows, int N, int da, int d, int iters, cudaStream_t st);
@@ -396,7 +401,7 @@ void launch_hist_match(float *img, long npix, int nbins, const unsigned int *cx,
 void launch_m_step_hist(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w, int Ho, int Wo,
                         int stride, int nbins, const unsigned int *cx, long nx, const unsigned int *cz, long nz,
                         float *out, int *status, cudaStream_t st);
-void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int w,
+void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, int ex, int N, int C, int w,
                    int Ho, int Wo, int stride, float *out, int *status, cudaStream_t st);
 void launch_irls(const float *d2, int Q, float r, float delta, float *wts, double *energy_out,
                  double *partial, unsigned int *ticket, cudaStream_t st);

@@ -15,7 +15,7 @@
 // k_resolve      writes nn/d2 of listed queries from the packed minima.
 //
 // Distances are sums of squared FP32 differences read straight from the two
-// images (a window row is 3w contiguous floats in HWC layout), reduced across
+// images (a window row is C w contiguous floats in HWC layout, C channels), reduced across
 // the warp by a fixed butterfly, so the result is deterministic.
 #include <algorithm>
 
@@ -36,13 +36,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 // and exemplar window n, one warp, lanes striding over each window row.
 __device__ __forceinline__ float window_dist2(const RerankArgs &a, int y0, int x0, int n, int lane) {
     const int ey = n / a.ex, ex0 = n - ey * a.ex;
-    const int row = 3 * a.w;
-    const float *xq = a.X + ((size_t)y0 * a.Wo + x0) * 3;
-    const float *zn = a.Z + ((size_t)ey * a.We + ex0) * 3;
+    const int row = a.C * a.w;
+    const float *xq = a.X + ((size_t)y0 * a.Wo + x0) * a.C;
+    const float *zn = a.Z + ((size_t)ey * a.We + ex0) * a.C;
     float s = 0.0f;
     for (int dy = 0; dy < a.w; ++dy) {
-        const float *xr = xq + (size_t)dy * a.Wo * 3;
-        const float *zr = zn + (size_t)dy * a.We * 3;
+        const float *xr = xq + (size_t)dy * a.Wo * a.C;
+        const float *zr = zn + (size_t)dy * a.We * a.C;
         for (int e = lane; e < row; e += 32) {
             const float t = __ldg(xr + e) - __ldg(zr + e);
             s = fmaf(t, t, s);
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_rerank(RerankArgs a, const int *__restr
 // element lane + 32p within a row) and reduced by the same butterfly: the distances are bitwise
 // those of k_rerank.  Evaluating the second candidate of a pair that k_rerank would have skipped
 // cannot change the minimum (its distance exceeds the best so far).
-template <int W>
+template <int W, int CH>
 __global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__restrict__ qlist,
                                                   const unsigned int *__restrict__ qcount,
                                                   const int *__restrict__ cand_idx,
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__res
                                                   unsigned int *__restrict__ fail_count,
                                                   unsigned long long *__restrict__ best64,
                                                   int *__restrict__ status) {
-    constexpr int R = 3 * W, PER = (R + 31) / 32;
+    constexpr int R = CH * W, PER = (R + 31) / 32;
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int q = wid;
@@ -132,21 +132,21 @@ __global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__res
     }
     if (q < 0 || q >= a.Q) return;
     const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
-    const float *xq = a.X + ((size_t)y0 * a.Wo + x0) * 3;
+    const float *xq = a.X + ((size_t)y0 * a.Wo + x0) * CH;
     float xv[W][PER];
 #pragma unroll
     for (int dy = 0; dy < W; ++dy)
 #pragma unroll
         for (int p = 0; p < PER; ++p) {
             const int e = lane + 32 * p;
-            xv[dy][p] = e < R ? __ldg(xq + (size_t)dy * a.Wo * 3 + e) : 0.0f;
+            xv[dy][p] = e < R ? __ldg(xq + (size_t)dy * a.Wo * CH + e) : 0.0f;
         }
     const int my_idx = cand_idx[(size_t)q * kTopK + lane];
     const float my_lb = cand_lb[(size_t)q * kTopK + lane];
     const float tq = certify ? tau[q] : 0.0f;
     float best = INFINITY;
     int best_n = -1;
-    const size_t zrow = (size_t)a.We * 3;
+    const size_t zrow = (size_t)a.We * CH;
     for (int i = 0; i < kTopK; i += 2) {
         int n0 = __shfl_sync(kFull, my_idx, i);
         int n1 = __shfl_sync(kFull, my_idx, i + 1);
@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__res
         }
         const int m0 = n0 < 0 ? 0 : n0, m1 = n1 < 0 ? 0 : n1;
         const int ey0 = m0 / a.ex, ey1 = m1 / a.ex;
-        const float *z0 = a.Z + ((size_t)ey0 * a.We + (m0 - ey0 * a.ex)) * 3;
-        const float *z1 = a.Z + ((size_t)ey1 * a.We + (m1 - ey1 * a.ex)) * 3;
+        const float *z0 = a.Z + ((size_t)ey0 * a.We + (m0 - ey0 * a.ex)) * CH;
+        const float *z1 = a.Z + ((size_t)ey1 * a.We + (m1 - ey1 * a.ex)) * CH;
         float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
         for (int dy = 0; dy < W; ++dy)
@@ -225,9 +225,9 @@ __global__ void __launch_bounds__(256) k_brute(RerankArgs a, const int *__restri
             const int ey = n / a.ex, ex0 = n - ey * a.ex;
             float s = 0.0f;
             for (int dy = 0; dy < a.w; ++dy) {
-                const float *xr = a.X + ((size_t)(y0 + dy) * a.Wo + x0) * 3;
-                const float *zr = a.Z + ((size_t)(ey + dy) * a.We + ex0) * 3;
-                for (int e = 0; e < 3 * a.w; ++e) {
+                const float *xr = a.X + ((size_t)(y0 + dy) * a.Wo + x0) * a.C;
+                const float *zr = a.Z + ((size_t)(ey + dy) * a.We + ex0) * a.C;
+                for (int e = 0; e < a.C * a.w; ++e) {
                     const float t = __ldg(xr + e) - __ldg(zr + e);
                     s = fmaf(t, t, s);
                 }
@@ -285,11 +285,14 @@ void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qc
     ProfScope ps(kProfRerank, st, 1);
 #define PTS_RERANK_ARGS a, qlist, qcount, cand_idx, cand_lb, tau, certify, nn_out, d2_out, fail_list, fail_count, \
                         best64, status
-    switch (a.w) {
-        case 4: k_rerank_w<4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 8: k_rerank_w<8><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 16: k_rerank_w<16><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 32: k_rerank_w<32><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+    switch (a.C * 64 + a.w) {
+        case 3 * 64 + 4: k_rerank_w<4, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 3 * 64 + 8: k_rerank_w<8, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 3 * 64 + 16: k_rerank_w<16, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 3 * 64 + 32: k_rerank_w<32, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 4 * 64 + 4: k_rerank_w<4, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 4 * 64 + 8: k_rerank_w<8, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 4 * 64 + 16: k_rerank_w<16, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
         default: k_rerank<<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
     }
 #undef PTS_RERANK_ARGS

@@ -85,22 +85,26 @@ struct TopK8 {
 // ---------------------------------------------------------------------------
 // pass 1: PCA-space lower bounds
 // ---------------------------------------------------------------------------
+// DAM: the longest search vector the layout holds (68: d <= 64 coordinates + residual; 128:
+// the d_fast <= 124 coordinates of the index's larger PCA + residual)
+template <int DAM>
 struct PcaSmem {
-    float a[kMaxDA][kBQ];     // query vectors, transposed
-    float e[2][kMaxDA][kBN];  // exemplar tiles (double buffer)
+    float a[DAM][kBQ];     // query vectors, transposed
+    float e[2][DAM][kBN];  // exemplar tiles (double buffer)
     float en[2][kBN];         // exemplar norms
     uint64_t bar[2];          // tile of buffer b landed
     uint64_t empty[2];        // all 8 warps are done with buffer b
     int abort_flag;
 };
 
-__global__ void __launch_bounds__(kThreads, 2)
+template <int DAM>
+__global__ void __launch_bounds__(kThreads, DAM <= kMaxDA ? 2 : 1)
     k_search_pca(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int da,
                  const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int tiles_per_part,
                  int *__restrict__ cand_idx, float *__restrict__ cand_lb, float *__restrict__ part_v,
                  int *__restrict__ part_i, int *__restrict__ status, const float *__restrict__ thr_init) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    PcaSmem &sm = *reinterpret_cast<PcaSmem *>(smem_raw);
+    PcaSmem<DAM> &sm = *reinterpret_cast<PcaSmem<DAM> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int qbase = blockIdx.x * kBQ;
     for (int i = tid; i < kBQ * da; i += kThreads) {
@@ -527,11 +531,11 @@ __global__ void __launch_bounds__(256) k_full_select(const float *__restrict__ p
 }
 
 // u_q = x_q - mu of the failing queries, tiled [F/64][Dp][64], zero rows k >= D
-__global__ void k_gather_full(const float *__restrict__ X, int Wo, int w, int stride, int qx,
+__global__ void k_gather_full(const float *__restrict__ X, int Wo, int C, int w, int stride, int qx,
                               const float *__restrict__ mu, const int *__restrict__ fail_list,
                               const unsigned int *__restrict__ fail_count, int Q, int Dp,
                               float *__restrict__ qfull) {
-    const int D = 3 * w * w, row = 3 * w;
+    const int row = C * w, D = row * w;
     const long n = (long)(*fail_count) * Dp;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const int f = (int)(i / Dp), k = (int)(i - (long)f * Dp);
@@ -541,7 +545,7 @@ __global__ void k_gather_full(const float *__restrict__ X, int Wo, int w, int st
             q = q < 0 ? 0 : (q >= Q ? Q - 1 : q);
             const int y0 = (q / qx) * stride, x0 = (q % qx) * stride;
             const int dy = k / row, e = k - dy * row;
-            v = X[((size_t)(y0 + dy) * Wo + x0) * 3 + e] - mu[k];
+            v = X[((size_t)(y0 + dy) * Wo + x0) * C + e] - mu[k];
         }
         qfull[((size_t)(f / kBQ) * Dp + k) * kBQ + (f % kBQ)] = v;
     }
@@ -549,16 +553,16 @@ __global__ void k_gather_full(const float *__restrict__ X, int Wo, int w, int st
 
 // -2 u_n of every exemplar window, tiled [ntiles][Dp][128] (the caller zeroes
 // the buffer first, so padding rows and columns stay 0)
-__global__ void k_exemplar_full(const float *__restrict__ Z, int We, int w, int ex, int N, int Dp,
+__global__ void k_exemplar_full(const float *__restrict__ Z, int We, int C, int w, int ex, int N, int Dp,
                                 const float *__restrict__ mu, float *__restrict__ efull) {
-    const int D = 3 * w * w, row = 3 * w;
+    const int row = C * w, D = row * w;
     const long n = (long)N * D;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const int win = (int)(i / D), k = (int)(i - (long)win * D);
         const int ey = win / ex, exx = win - ey * ex;
         const int dy = k / row, e = k - dy * row;
         efull[((size_t)(win / kBN) * Dp + k) * kBN + (win % kBN)] =
-            -2.0f * (Z[((size_t)(ey + dy) * We + exx) * 3 + e] - mu[k]);
+            -2.0f * (Z[((size_t)(ey + dy) * We + exx) * C + e] - mu[k]);
     }
 }
 
@@ -590,31 +594,37 @@ int pca_parts(int Q, int ntiles) {
 void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st, int nparts, float *part_v, int *part_i, const float *thr_init) {
-    const size_t smem = sizeof(PcaSmem);
-    set_smem_attr(reinterpret_cast<const void *>(k_search_pca), (int)smem);
+    const bool wide = da > kMaxDA;
+    const size_t smem = wide ? sizeof(PcaSmem<kMaxDAFast>) : sizeof(PcaSmem<kMaxDA>);
+    set_smem_attr(reinterpret_cast<const void *>(k_search_pca<kMaxDA>), (int)sizeof(PcaSmem<kMaxDA>));
+    set_smem_attr(reinterpret_cast<const void *>(k_search_pca<kMaxDAFast>), (int)sizeof(PcaSmem<kMaxDAFast>));
     const int grid = ceil_div(Q, kBQ);
     if (grid == 0) return;
     if (!part_v || !part_i) nparts = 1;
     const int tpp = ceil_div(ntiles, std::max(nparts, 1));
     const int np = ceil_div(ntiles, tpp);
     ProfScope ps(kProfSearchTopk, st, np > 1 ? 2 : 1);
-    k_search_pca<<<dim3(grid, np), kThreads, smem, st>>>(qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx,
-                                                         cand_lb, part_v, part_i, status, thr_init);
+    if (wide)
+        k_search_pca<kMaxDAFast><<<dim3(grid, np), kThreads, smem, st>>>(
+            qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx, cand_lb, part_v, part_i, status, thr_init);
+    else
+        k_search_pca<kMaxDA><<<dim3(grid, np), kThreads, smem, st>>>(
+            qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx, cand_lb, part_v, part_i, status, thr_init);
     if (np > 1)
         k_merge_pca_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, Q, qnorm, cand_idx,
                                                                        cand_lb);
 }
 
-int launch_search_full(const float *X, int Wo, int w, int stride, int qx, const float *mu,
+int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
                         int nparts, int *status, cudaStream_t st, int N, DevBuf<float> *pdist) {
     const size_t smem = sizeof(FullSmem);
     set_smem_attr(reinterpret_cast<const void *>(k_search_full), (int)smem);
-    const int Dp = padded_dim(w);
+    const int Dp = padded_dim(C * w * w);
     count_launches(1);
-    k_gather_full<<<152 * 4, 256, 0, st>>>(X, Wo, w, stride, qx, mu, fail_list, fail_count, Q, Dp,
+    k_gather_full<<<152 * 4, 256, 0, st>>>(X, Wo, C, w, stride, qx, mu, fail_list, fail_count, Q, Dp,
                                            qfull);
     // A grid of few (query block, tile) pairs with long vectors (the coarse levels, where every
     // query takes this pass) is split along the vector as well, for about four CTAs per slot,
@@ -657,12 +667,12 @@ int full_parts(int Q, int ntiles) {
     return std::max(1, std::min(ntiles, (2 * 152) / std::max(nqb, 1)));
 }
 
-void launch_exemplar_full(const float *Z, int We, int w, int ex, int N, const float *mu,
+void launch_exemplar_full(const float *Z, int We, int C, int w, int ex, int N, const float *mu,
                           float *efull, int ntiles, cudaStream_t st) {
-    const int Dp = padded_dim(w);
+    const int Dp = padded_dim(C * w * w);
     cudaMemsetAsync(efull, 0, sizeof(float) * (size_t)ntiles * Dp * kBN, st);
     count_launches(1);
-    k_exemplar_full<<<152 * 8, 256, 0, st>>>(Z, We, w, ex, N, Dp, mu, efull);
+    k_exemplar_full<<<152 * 8, 256, 0, st>>>(Z, We, C, w, ex, N, Dp, mu, efull);
 }
 
 }  // namespace pts

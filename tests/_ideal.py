@@ -6,7 +6,9 @@ minimum score (ties to the smaller group), and re-ranks the 32 smallest scores a
 groups' windows in full dimension.  Evaluated with the oracle's FP64 PCA bound
 LB(q, n) = ||y_q - y_n||^2 + (r_q - r_n)^2 in place of the FP16 scores, the misses that remain
 are those of the rule itself, not of its arithmetic; the GPU's mismatch rate is tested against
-this rate plus an allowance for FP16 rounding.
+this rate plus an allowance for FP16 rounding.  With fp16_operands the scores are instead formed
+from the operands rounded to FP16 as the search stores them (query (y, r), exemplar -2 (y, r)),
+their products summed in FP64, plus the exemplar norm: the rule with FP16 operand rounding alone.
 """
 import numpy as np
 
@@ -15,7 +17,7 @@ import oracle
 TILE, HALF, GROUP, KEEP, TOPK = 256, 128, 8, 8, 32
 
 
-def group_rule_mismatch(X, Z, w, d, qs, nn_o, stride=2, chunk=128):
+def group_rule_mismatch(X, Z, w, d, qs, nn_o, stride=2, chunk=128, fp16_operands=False):
     """Boolean per sampled query q in qs: the rule's window differs from the oracle's nn_o."""
     mu, B, _, _ = oracle.pca_fit(Z, w, d)
     ye, _, re = oracle.project(Z, w, 1, mu, B)
@@ -29,10 +31,18 @@ def group_rule_mismatch(X, Z, w, d, qs, nn_o, stride=2, chunk=128):
     gid = np.arange(T)[:, None, None] * (TILE // GROUP) + np.arange(2)[None, :, None] * ng \
         + np.arange(ng)[None, None, :]                   # [tile, half, group] -> global group id
     miss = np.zeros(len(qs), dtype=bool)
+    if fp16_operands:
+        f16 = lambda v: v.astype(np.float16).astype(np.float64)  # noqa: E731
+        E16 = f16(-2.0 * np.concatenate([ye, re[:, None]], 1))
+        Q16 = f16(np.concatenate([yq, rq[:, None]], 1))
+        nrm = ne + re ** 2
     for a in range(0, len(qs), chunk):
         b = min(len(qs), a + chunk)
-        lb = (yq[a:b] ** 2).sum(1)[:, None] + ne[None, :] - 2.0 * (yq[a:b] @ ye.T) \
-            + (rq[a:b, None] - re[None, :]) ** 2
+        if fp16_operands:
+            lb = nrm[None, :] + Q16[a:b] @ E16.T
+        else:
+            lb = (yq[a:b] ** 2).sum(1)[:, None] + ne[None, :] - 2.0 * (yq[a:b] @ ye.T) \
+                + (rq[a:b, None] - re[None, :]) ** 2
         lbp = np.full((b - a, T * TILE), np.inf)
         lbp[:, :N] = lb
         gmin = lbp.reshape(b - a, T, 2, ng, GROUP).min(-1)

@@ -112,7 +112,7 @@ def test_allocator_registration_on_host(libpts):
 
 
 # index files: the header layout of persist.cu, written field by field in host byte order
-_HEADER = "<8sII16ifddiifiiii"
+_HEADER = "<8sII16ifddiifiiiii"
 
 
 def _index_file(tables=None, **over):
@@ -127,12 +127,12 @@ def _index_file(tables=None, **over):
              ktc=32, kf8=32, eig_iters=5, tc_parts=0, unorm2_max=1.0, var=0.9, eig_top=1.0)
     f.update(over)
     prop, tree = "prop" in tables, "tree" in tables
-    head = struct.pack(_HEADER, over.get("magic", b"PTSINDEX"), over.get("version", 1),
+    head = struct.pack(_HEADER, over.get("magic", b"PTSINDEX"), over.get("version", 2),
                        over.get("order", 0x01020304), f["He"], f["We"], f["w"], f["D"], f["N"], f["d"], f["da"],
                        f["d_fast"], f["da_fast"], f["ny"], f["nx"], f["ntiles"], f["ktc"], f["kf8"],
                        f["eig_iters"], f["tc_parts"], f["unorm2_max"], f["var"], f["eig_top"],
                        int(prop), C if prop else 0, 1.2 if prop else 0.0, int(tree), 1 if tree else 0,
-                       4 if tree else 0, 1 if tree else 0)
+                       4 if tree else 0, 1 if tree else 0, over.get("C", 3))
     tcr = 256  # one tensor-core tile of 256 windows
     secs = [(b"EXEM", 4, 12 * 12 * 3), (b"EXE4", 16, 144), (b"MEAN", 4, 48), (b"BASI", 4, 128 * 48),
             (b"BAST", 4, 48 * 128), (b"EIGV", 8, 128), (b"ETIL", 4, 12 * 128), (b"EROW", 4, 81 * 12),
@@ -183,7 +183,9 @@ def test_index_files_checked_on_host(libpts, tmp_path):
     for data, msg in [(b"", "ends early"),
                       (_index_file(magic=b"NOTINDEX"), "not an index file"),
                       (_index_file(order=0x04030201), "byte order"),
-                      (_index_file(version=2), "version"),
+                      (_index_file(version=1), "version"),
+                      (_index_file(C=5), "channels"),
+                      (_index_file(C=4), "window grid"),
                       (_index_file(D=49), "window grid"),
                       (_index_file(N=80), "window count"),
                       (_index_file(da=16), "PCA dimensions"),
@@ -206,7 +208,7 @@ def test_allocator_returning_null_fails_the_build_cleanly(libpts):
     returns PTS_ERR_OOM at its first allocation, before any device work, and holds nothing."""
     class Params(ctypes.Structure):
         _fields_ = [("d", ctypes.c_int), ("var_frac", ctypes.c_double), ("max_iters", ctypes.c_int),
-                    ("d_fast", ctypes.c_int)]
+                    ("d_fast", ctypes.c_int), ("channels", ctypes.c_int)]
     libpts.pts_last_error.restype = ctypes.c_char_p
     libpts.pts_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     libpts.pts_live_allocations.restype = ctypes.c_longlong
@@ -220,7 +222,7 @@ def test_allocator_returning_null_fails_the_build_cleanly(libpts):
     assert libpts.pts_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(fr, ctypes.c_void_p), None) == 0
     try:
         out = ctypes.c_void_p()
-        p = Params(16, 0.95, 0, 0)
+        p = Params(16, 0.95, 0, 0, 0)
         rc = libpts.build_exemplar_index(ctypes.c_void_p(16), 32, 32, 8, ctypes.byref(p), None, ctypes.byref(out))
         assert rc == -3 and b"registered allocator failed" in libpts.pts_last_error()
         assert asked == [32 * 32 * 3 * 4] and freed == [] and not out.value

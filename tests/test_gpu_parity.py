@@ -388,3 +388,27 @@ def test_converge_reproduces_exemplar_in_one_step(c1):
     E, it = pts.synthesize_level_converge(idx, xt, 10, r=2.0, mode="exact")
     assert it == 1 and E[0] == 0.0 and E[1] < 1e-8
     np.testing.assert_allclose(xt.cpu().numpy(), Z, atol=1e-6)
+
+
+def test_exact_bound_components_change_the_route_not_the_result():
+    """The exact search's PCA bound with the index's first d components (the default) or its
+    d_fast: both routes return the certified nearest windows of Eq. 4, bit for bit the same, and
+    the larger bound certifies at least as many queries from the 32 best bounds."""
+    Z = P.synthetic_exemplar(0, 128, 4.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=32)
+    X = _t(P.random_patch_init(Z, 256, 256, 8, 3))
+    assert idx.info["exact_dims"] == 32
+    nn_d, d2_d = pts.nn_search(idx, X, 2, "exact")
+    st_d = idx.search_stats()
+    idx.set_exact_bound(True)
+    assert idx.info["exact_dims"] == idx.info["d_fast"] > 32
+    nn_f, d2_f = pts.nn_search(idx, X, 2, "exact")
+    st_f = idx.search_stats()
+    assert torch.equal(nn_f, nn_d) and torch.equal(d2_f, d2_d)
+    assert st_f["certified"] >= st_d["certified"], (st_f, st_d)
+    Q = idx.num_queries(256, 256, 2)
+    sub = P.sample_indices(13, Q, 256)
+    Xh = X.cpu().numpy()
+    nn_o, d2_o = oracle.nn_bruteforce(Xh, Z, 8, 2, qlist=sub)
+    check_nn(Xh, Z, 8, 2, nn_f.cpu().numpy()[sub], d2_f.cpu().numpy()[sub], nn_o, d2_o, qlist=sub)
+    idx.close()
