@@ -555,15 +555,21 @@ long long pts_launch_count(void);
 /*
  * Batched synthesis (no counterpart in the paper; the batched form of the EM loop of section 2.1
  * for many independent jobs of uneven sizes).  A job is one level: `iters` EM iterations on its
- * own index and output, then the final search phase.
+ * own index and output, then the final search phase.  Jobs can be chained into pyramids
+ * (section 2.1's coarse to fine): a job whose `parent` is an earlier job of the batch starts each
+ * run from that job's result up-sampled by 2 (pts_upsample2), after the parent has finished.
  */
 typedef struct {
     pts_index index;  /* the job's exemplar index; no two jobs of a batch may share one */
     float *output;    /* device Ho x Wo x C float32 (C the index's channels); in: initial image,
                          out: result */
     int Ho, Wo, stride;
-    int mode;         /* PTS_EXACT_F32, PTS_F16_RERANK or PTS_FP8_RERANK */
+    int mode;         /* PTS_EXACT_F32, PTS_F16_RERANK, PTS_FP8_RERANK, PTS_PROPOSAL (the index
+                         has a trained proposal) or PTS_KMTREE (the index has a built tree) */
     double *energy;   /* device, iters + 1 doubles: energy entering each iteration, then the final */
+    int parent;       /* -1: the run starts from `output` as the caller left it; k >= 0 (an
+                         earlier job, RGB indices, the parent's output exactly half this job's
+                         Ho and Wo): the run starts from job k's result up-sampled by 2 */
 } pts_job;
 
 typedef struct pts_batch_s *pts_batch; /* opaque, owned by the library */

@@ -5,8 +5,11 @@
 // autotunes the tensor-core search's exemplar split per job shape (the candidate with the least
 // measured time, cached by shape), then captures all jobs' iterations -- search, IRLS weights
 // and energy, M-step -- into one graph, the jobs spread round-robin over n_streams forked
-// streams (jobs are independent: each has its own index and workspace).  pts_batch_run replays
-// the graph.  Energies go to device arrays so the graph has no host copy or synchronisation.
+// streams (jobs are independent: each has its own index and workspace).  A job chained to a
+// parent (a pyramid's next level) runs on its parent's stream after it, starting from the
+// parent's result up-sampled by 2.  Any search mode whose tables the job's index holds may run
+// (exact, FP16, FP8, the learned proposal, the k-means tree).  pts_batch_run replays the graph.
+// Energies go to device arrays so the graph has no host copy or synchronisation.
 #include <algorithm>
 #include <map>
 #include <string>
@@ -132,8 +135,20 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
         unsigned long long g = 0;
         if (!index_generation(j.index, &g))
             return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a job's index is not a live index");
-        if (j.mode < PTS_EXACT_F32 || j.mode > PTS_PROPOSAL || j.mode == PTS_PROPOSAL)
-            return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: job mode must be exact, f16 or fp8");
+        if (j.mode < PTS_EXACT_F32 || j.mode > PTS_KMTREE)
+            return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: unknown job mode");
+        if (j.mode == PTS_PROPOSAL && !j.index->prop.ready)
+            return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a proposal job's index has no trained proposal");
+        if (j.mode == PTS_KMTREE && !j.index->tree.ready)
+            return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a tree job's index has no k-means tree");
+        if (j.parent < -1 || j.parent >= k)
+            return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a parent must be an earlier job (or -1)");
+        if (j.parent >= 0) {
+            const pts_job &pj = jobs[j.parent];
+            if (j.index->C != 3 || pj.index->C != 3 || 2 * pj.Ho != j.Ho || 2 * pj.Wo != j.Wo)
+                return set_error(PTS_ERR_INVALID_ARG,
+                                 "pts_batch_create: a chained job needs RGB indices and twice its parent's size");
+        }
         PTS_TRY(check_grid_public(j.Ho, j.Wo, j.index->w, j.stride, "pts_batch_create"));
         for (int m = 0; m < k; ++m)
             if (jobs[m].index == j.index)
@@ -198,12 +213,21 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
         capturing = true;
         cudaEventRecord(ev[n_streams], cap);
         for (int i = 0; i < n_streams; ++i) cudaStreamWaitEvent(ss[i], ev[n_streams], 0);
+        // roots go round-robin over the streams; a chained job runs on its parent's stream, after it
+        std::vector<int> stream_of(b->jobs.size(), 0);
+        int next_root = 0;
+        for (size_t k = 0; k < b->jobs.size(); ++k)
+            stream_of[k] = b->jobs[k].parent >= 0 ? stream_of[b->jobs[k].parent] : (next_root++ % n_streams);
         for (size_t k = 0; k < b->jobs.size() && s == PTS_OK; ++k) {
             const pts_job &j = b->jobs[k];
             pts_index idx = j.index;
             Workspace &ws = idx->ws;
-            cudaStream_t js = ss[k % n_streams];
+            cudaStream_t js = ss[stream_of[k]];
             const int Q = job_queries(j);
+            if (j.parent >= 0) {
+                const pts_job &pj = b->jobs[j.parent];
+                launch_upsample2(pj.output, pj.Ho, pj.Wo, j.output, js);
+            }
             for (int t = 0; t <= iters && s == PTS_OK; ++t) {
                 s = nn_search_impl(idx, j.output, j.Ho, j.Wo, j.stride, j.mode, ws.nn.ptr, ws.d2.ptr, js);
                 if (s != PTS_OK) break;

@@ -74,3 +74,27 @@ def train_level_proposal(pidx: PyramidIndex, level: int, seeds, iters: int = 5, 
     y, nn, d2 = subsample(y, nn, d2, n_pairs, seed=12345)
     loss = train_proposal(pidx.indices[level], y, nn, d2, **params)
     return loss, y.shape[0]
+
+
+def train_job_proposal(ix, exemplar: torch.Tensor, Ho: int, w: int, seeds, iters: int = 5, n_pairs: int = 500_000,
+                       r: float = 2.0, stride: int = 2, **params):
+    """Train the proposal of a single-level index on (query, exact nearest window) pairs from its
+    own exact-mode EM runs: one run per seed from random exemplar patches (Ho x Ho output).
+    Returns the per-epoch loss."""
+    ys, nns, d2s = [], [], []
+    z = exemplar.cpu().numpy()
+    for s in seeds:
+        X = torch.from_numpy(P.random_patch_init(z, Ho, Ho, w, s)).to(exemplar.device)
+        for t in range(iters + 1):
+            ys.append(project_queries(ix, X, stride).clone())
+            nn, d2 = nn_search(ix, X, stride, "exact")
+            nns.append(nn.clone())
+            d2s.append(d2.clone())
+            if t == iters:
+                break
+            W, _ = irls_weights(d2, r)
+            X = m_step(ix, nn, W, Ho, Ho, stride, out=X)
+    y, nn, d2 = subsample(torch.cat(ys).contiguous(), torch.cat(nns).contiguous(), torch.cat(d2s).contiguous(),
+                          n_pairs, seed=54321)
+    params.setdefault("n_clusters", min(1024, max(4, ix.N // 64)))
+    return train_proposal(ix, y, nn, d2, **params)

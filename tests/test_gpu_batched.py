@@ -104,3 +104,62 @@ def test_batch_refuses_to_run_after_its_indices_change():
     with pytest.raises(pts.PtsError, match="destroyed"):
         b.run()
     b.close()
+
+
+def test_batch_pyramid_levels_against_oracle():
+    """Pyramid levels inside one batch (section 2.1's coarse to fine): two 3-level jobs whose
+    finer levels start from the coarser results up-sampled by 2 within the graph.  Every level's
+    final energy against the oracle's run of the same pyramid (its FP64 exemplar pyramid, its
+    up-sampling) within 1e-3, and the batch equal to the same levels run one by one."""
+    from paper_2006_11851_gb300.batched import run_eager
+    specs = [{"job": 0, "He": 48, "Ho": 96, "w": 8, "d": 16, "seed": 4, "levels": 3},
+             {"job": 1, "He": 64, "Ho": 128, "w": 8, "d": 16, "seed": 5, "levels": 3}]
+    iters = 3
+    b = Batch(specs, mode="exact", iters=iters, n_streams=2)
+    assert b.parents == [-1, 0, 1, -1, 3, 4]
+    b.reset()
+    b.run()
+    torch.cuda.synchronize()
+    outs = [x.clone() for x in b.outputs]
+    ens = [e.cpu().numpy().copy() for e in b.energies]
+    for s, ks in zip(specs, b.levels):
+        pyr_o = oracle.exemplar_pyramid(P.synthetic_exemplar(s["seed"], s["He"], 4.0), 3)
+        Xo = b.inits[ks[0]].cpu().numpy()
+        for lev, k in enumerate(ks):
+            ref = oracle.synthesize_level(pyr_o[lev].astype(np.float32), Xo, s["w"], iters)
+            assert abs(ens[k][-1] / ref["E"][-1] - 1) < 1e-3, (s["job"], lev, ens[k], ref["E"])
+            Xo = oracle.upsample2(ref["X"]) if lev < 2 else ref["X"]
+    b.reset()
+    run_eager(b)
+    torch.cuda.synchronize()
+    for k, x in enumerate(b.outputs):
+        assert torch.equal(x, outs[k]), k
+    b.close()
+
+
+def test_batch_with_proposal_and_tree_jobs():
+    """The learned proposal (trained on the job's own exact runs) and the paper's k-means tree as
+    job modes of a batch, beside an FP16 job: the graph replay equals each job run alone through
+    synthesize_level, bit for bit."""
+    from paper_2006_11851_gb300.batched import run_eager
+    specs = [{"job": 0, "He": 96, "Ho": 160, "w": 8, "d": 32, "seed": 6, "mode": "f16"},
+             {"job": 1, "He": 96, "Ho": 160, "w": 8, "d": 32, "seed": 7, "mode": "proposal"},
+             {"job": 2, "He": 80, "Ho": 128, "w": 16, "d": 48, "seed": 8, "mode": "kmtree"}]
+    b = Batch(specs, iters=2, n_streams=3, proposal_params={"n_clusters": 64, "epochs": 2, "batch": 1024})
+    assert b.modes == ["f16", "proposal", "kmtree"]
+    b.reset()
+    b.run()
+    torch.cuda.synchronize()
+    outs = [x.clone() for x in b.outputs]
+    ens = [e.clone() for e in b.energies]
+    b.reset()
+    run_eager(b)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert torch.equal(b.outputs[k], outs[k]), k
+    # the eager path returns host energies; the graph's device energies are those of the same run
+    for k, (ix, x0) in enumerate(zip(b.indices, b.inits)):
+        x = x0.clone()
+        E = pts.synthesize_level(ix, x, 2, mode=b.modes[k])
+        np.testing.assert_array_equal(E, ens[k].cpu().numpy())
+    b.close()
