@@ -243,7 +243,9 @@ pts_status pts_index_load(const char *path, pts_index *out);
 
 /* Sets how many CTAs split the exemplar tiles of one 128-query block in the
  * tensor-core searches (PTS_F16_RERANK, PTS_FP8_RERANK); 0 restores the
- * automatic choice, which fills the 152 SMs when the query blocks alone do not.
+ * automatic choice, which fills the 152 SMs when the query blocks alone do not,
+ * and otherwise splits only the query blocks of the last, partial wave (one CTA
+ * per SM), each over up to 4 CTAs, when at least one full wave precedes them.
  * The candidates, hence the results, are the same for every split: each part
  * keeps its own best groups and the merge takes the best of their union.
  * A tuning knob only (pts_batch_create sets it from timings).  PTS_ERR_INVALID_ARG

@@ -94,8 +94,9 @@ pts_status autotune(pts_batch b, cudaStream_t st) {
                 continue;
             }
         }
-        // candidates: the default rule and splits of 1, 2 and 4 parts (each part >= 16 tiles)
-        std::vector<int> cand = {tc_parts(Q, ntc), 1, 2, 4};
+        // candidates: automatic (the default rule with its tail split) and splits of 1, 2 and 4
+        // parts (each part >= 16 tiles)
+        std::vector<int> cand = {0, 1, 2, 4};
         int best = cand[0];
         float best_ms = 1e30f;
         for (int p : cand) {

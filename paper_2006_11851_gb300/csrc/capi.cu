@@ -260,7 +260,10 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
-            const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
+            // 0: automatic -- the default split rule, one part plus the tail split of launch_search_tc
+            const int auto_parts = tc_parts(Q, ntc);
+            const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc)
+                                                          : (auto_parts > 1 ? auto_parts : 0);
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
             launch_pack_queries(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->ktc, ws.qtile.ptr, st);
             // the candidate lists of the previous search on this grid seed the bound
@@ -268,7 +271,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             if (warm)
                 launch_warm_threshold(ws.cand_idx.ptr, ws.qtile.ptr, ws.qnorm.ptr, idx->etc.ptr, idx->umax.ptr, Q, idx->ktc,
                                       idx->N, kWarmEps, ws.thr0.ptr, st);
-            PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, nparts), "kept groups"));
+            PTS_TRY(ws.kept.ensure(tc_kept_bytes_search(Q, ntc, nparts), "kept groups"));
             launch_search_tc(ws.qtile.ptr, ws.qnorm.ptr, Q, idx->ktc, idx->etc.ptr, ntc, nparts,
                              warm ? ws.thr0.ptr : nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr,
                              ws.part_i.ptr, idx->status.ptr, st, nullptr, nullptr, 0, nullptr, nullptr, idx->N,
@@ -294,12 +297,15 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
                            ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st, &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
-            const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc) : tc_parts(Q, ntc);
+            // 0: automatic -- the default split rule, one part plus the tail split of launch_search_tc
+            const int auto_parts = tc_parts(Q, ntc);
+            const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc)
+                                                          : (auto_parts > 1 ? auto_parts : 0);
             PTS_TRY(ws.qtile8.ensure((size_t)tc_query_blocks(Q) * 128 * idx->kf8, "fp8 query tiles"));
             PTS_TRY(ws.qscale.ensure((size_t)std::max(Q, 1), "fp8 query scales"));
             launch_pack_queries_f8(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->kf8, idx->f8scale.ptr,
                                    ws.qtile8.ptr, ws.qscale.ptr, st);
-            PTS_TRY(ws.kept.ensure(tc_kept_bytes(Q, nparts), "kept groups"));
+            PTS_TRY(ws.kept.ensure(tc_kept_bytes_search(Q, ntc, nparts), "kept groups"));
             launch_search_tc(ws.qtile8.ptr, ws.qnorm.ptr, Q, idx->kf8, idx->etc8.ptr, ntc, nparts, nullptr,
                              ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st,
                              nullptr, nullptr, 1, ws.qscale.ptr, idx->enorm.ptr, idx->N, ws.kept.ptr);

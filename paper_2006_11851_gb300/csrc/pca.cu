@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kMaxM = 112;     // subspace widths up to this keep the m x m work in shared memory
 constexpr int kMaxMBig = 256;  // beyond it (up to this) the m x m matrices live in global memory
+constexpr int kRitzEvery = 4;  // subspace-iteration steps per Rayleigh-Ritz solve
 
 __global__ void __launch_bounds__(256)
     k_win_mean(const float *__restrict__ Z, int We, int C, int w, int ex, long N, double *__restrict__ mu) {
@@ -491,6 +492,17 @@ pts_status pca_fit_device(const float *exemplar, int He, int We, int nch, int w,
     int it = 0;
     for (it = 1; it <= max_iters; ++it) {
         dgemm<false, false>(D, m, D, C, D, V, m, Y, m, st);  // Y = Sigma V
+        // Rayleigh-Ritz (and the convergence test) every kRitzEvery-th step and at the cap: the
+        // steps between are plain power steps on the orthonormalised block, which span the same
+        // subspace the Ritz vectors would (rotating inside it changes nothing), so only the test
+        // is less frequent while the eigen-solve, which dominates a step, runs a quarter as often.
+        // The first step always solves it: when the block is the whole space (m = D) that is the
+        // exact answer, and no power step on a rank-deficient covariance is needed
+        if (it != 1 && it % kRitzEvery != 0 && it != max_iters) {
+            std::swap(V, Y);
+            orth(V);
+            continue;
+        }
         dgemm<true, false>(m, m, D, V, m, Y, m, G, m, st);   // H = V^T Y
         count_launches(1);
         k_jacobi_small<<<1, 512, jac_smem, st>>>(G, m, th, S, jwork, status);

@@ -300,6 +300,8 @@ struct IvfBuffers {
     void *kept;
 };
 int ivf_max_blocks(int Q, int C);
+void tc_tail_plan(int Q, int ntiles, int *tail_from, int *tail_parts);
+size_t tc_kept_bytes_search(int Q, int ntiles, int nparts);
 size_t tc_kept_bytes(int Q, int nparts);
 void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float *qcoord, const float *qnorm, int d,
                       int da, int K, const __half *etile_ivf, int ntiles, int N, const int *members, IvfBuffers &b,

@@ -178,14 +178,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float *__restrict__ qscale, const float *__restrict__ enorm, int N,
                 const float *__restrict__ thr0, const int *__restrict__ qlist,
                 const unsigned int *__restrict__ qcount, IvfArgs ivf, KeptGroups *__restrict__ kept,
-                int *__restrict__ status) {
+                int *__restrict__ status, int tail_from, int tail_parts) {
     // with a query list, tile row f holds query qlist[f] (f < *qcount); blocks past the list exit
     const int nrows = qlist ? (int)min((unsigned int)Q, *qcount) : Q;
+    // Query block, exemplar part and the part count of this block.  With tail_parts > 1 (a 1-D
+    // grid), the blocks before tail_from run unsplit and each later query block is split over
+    // tail_parts CTAs of tiles_per_part tiles: only the last, partial wave is cut finer.  Their
+    // records go to a second region after the unsplit blocks' ones.
+    int qb = blockIdx.x, part = blockIdx.y, nsplit = gridDim.y, tpp = tiles_per_part;
+    KeptGroups *kbase = kept;
+    int qoff = 0;
+    if (tail_parts > 1) {
+        if ((int)blockIdx.x < tail_from) {
+            part = 0;
+            nsplit = 1;
+            tpp = ntiles;
+        } else {
+            const int j = (int)blockIdx.x - tail_from;
+            qb = tail_from + j / tail_parts;
+            part = j % tail_parts;
+            nsplit = tail_parts;
+            kbase = kept + (size_t)tail_from * kQM * 2;
+            qoff = tail_from * kQM;
+        }
+    }
     int4 blk = make_int4(0, 0, 0, 0);
     if (ivf.blk) {
         if ((int)blockIdx.x >= *ivf.nblk) return;
         blk = ivf.blk[blockIdx.x];
-    } else if ((int)blockIdx.x * kQM >= nrows) {
+    } else if (qb * kQM >= nrows) {
         return;
     }
     // tile row r -> query (and, for cluster-restricted blocks, its part slot); -1 when empty
@@ -195,17 +216,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             *slot = ivf.pair_r[blk.x + r];
             return ivf.pair_q[blk.x + r];
         }
-        const int f = blockIdx.x * kQM + r;
-        *slot = blockIdx.y;
+        const int f = qb * kQM + r;
+        *slot = part;
         return f < nrows ? (qlist ? qlist[f] : f) : -1;
     };
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     volatile int *abort_flag = &sm.abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nparts = ivf.blk ? 4 : gridDim.y;
-    const int t_begin = ivf.blk ? blk.z : blockIdx.y * tiles_per_part;
-    const int nt = ivf.blk ? blk.w : max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
+    const int nparts = ivf.blk ? 4 : nsplit;
+    const int t_begin = ivf.blk ? blk.z : part * tpp;
+    const int nt = ivf.blk ? blk.w : max(0, min(ntiles, t_begin + tpp) - t_begin);
     const uint32_t stage_bytes = (uint32_t)(kTN * K * EB);
     const uint32_t q_bytes = (uint32_t)(kQM * K * EB);
     const unsigned char *qtile_b = static_cast<const unsigned char *>(qtile);
@@ -237,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- producer ----------------
         if (lane == 0) {
             mbar_expect_tx(&sm.q_full, q_bytes);
-            bulk_g2s(sm.q, qtile_b + (size_t)blockIdx.x * q_bytes, q_bytes, &sm.q_full);
+            bulk_g2s(sm.q, qtile_b + (size_t)(ivf.blk ? blockIdx.x : qb) * q_bytes, q_bytes, &sm.q_full);
             int issued = 0;
             for (int i = 0; i < nt; ++i) {
                 const int s = i % nstages;
@@ -329,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!*abort_flag && q >= 0) {
             int slot = 0;
             row_query(row, &slot);
-            KeptGroups *rec = kept + (((size_t)q * nparts + slot) * 2 + half);
+            KeptGroups *rec = kbase + (((size_t)(q - qoff) * nparts + slot) * 2 + half);
 #pragma unroll
             for (int k = 0; k < kKeep; ++k) {
                 const int sl = L.gs[k] & 15;
@@ -1100,7 +1121,7 @@ void launch_ivf_probe(const int *top, int Q, int C, const int *moff, const float
         const IvfArgs ivf{b.blk, b.nblk, b.pair_q, b.pair_r};
         k_search_tc<2><<<maxb, kThreads, smem, st>>>(b.qtile, qnorm, Q, K, etile_ivf, ntiles, ntiles, nstages, nullptr,
                                                     nullptr, N, nullptr, nullptr, nullptr, ivf,
-                                                    reinterpret_cast<KeptGroups *>(b.kept), status);
+                                                    reinterpret_cast<KeptGroups *>(b.kept), status, 0, 0);
     }
     count_launches(2);
     k_select<<<ceil_div((long)Q * 4 * 32, 256), 256, 0, st>>>(reinterpret_cast<const KeptGroups *>(b.kept), Q, 4, qnorm,
@@ -1128,22 +1149,37 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
         set_smem_attr(reinterpret_cast<const void *>(k_search_tc<2>), (int)smem);
     // a listed search runs unsplit: the proposal's fallback lists about a third of the fine
     // level's queries, enough blocks to fill the SMs, and a split measured slower there
+    // nparts 0: automatic, one part with the tail split of tc_tail_plan; >= 1: that many parts
     if (qlist) nparts = 1;
     const int nqb = tc_query_blocks(Q);
     if (nqb == 0) return;
-    const int tpp = (ntiles + nparts - 1) / nparts;
+    int tail_from = nqb, tail_parts = 1;
+    if (nparts == 0) tc_tail_plan(Q, ntiles, &tail_from, &tail_parts);
+    nparts = std::max(nparts, 1);
+    const int tpp = tail_parts > 1 ? (ntiles + tail_parts - 1) / tail_parts : (ntiles + nparts - 1) / nparts;
     const int eb = fp8 ? 1 : 2;
     const int nstages = std::min(kMaxStages, kRing / (kTN * K * eb));
     KeptGroups *kept = reinterpret_cast<KeptGroups *>(kept_buf);
-    ProfScope ps(qlist ? kProfSearchTcList : kProfSearchTc, st, 2);
+    ProfScope ps(qlist ? kProfSearchTcList : kProfSearchTc, st, tail_parts > 1 ? 3 : 2);
+    const dim3 grid = tail_parts > 1 ? dim3(tail_from + (nqb - tail_from) * tail_parts, 1) : dim3(nqb, nparts);
     if (fp8)
-        k_search_tc<1><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
-                                                                  qscale, enorm, N, thr0, qlist, qcount, IvfArgs{},
-                                                                  kept, status);
+        k_search_tc<1><<<grid, kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages, qscale, enorm, N,
+                                                     thr0, qlist, qcount, IvfArgs{}, kept, status, tail_from,
+                                                     tail_parts);
     else
-        k_search_tc<2><<<dim3(nqb, nparts), kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages,
-                                                                  qscale, enorm, N, thr0, qlist, qcount, IvfArgs{},
-                                                                  kept, status);
+        k_search_tc<2><<<grid, kThreads, smem, st>>>(qtile, qnorm, Q, K, etile, ntiles, tpp, nstages, qscale, enorm, N,
+                                                     thr0, qlist, qcount, IvfArgs{}, kept, status, tail_from,
+                                                     tail_parts);
+    if (tail_parts > 1) {
+        // the unsplit blocks' queries, then the split ones (records in their own region)
+        const int qmain = tail_from * kQM;
+        k_select<<<ceil_div((long)qmain * 32, 256), 256, 0, st>>>(kept, qmain, 1, qnorm, nullptr, N, cand_idx, cand_lb,
+                                                                 part_v, part_i);
+        k_select_parts<<<ceil_div((long)(Q - qmain) * 32, 256), 256, 0, st>>>(
+            kept + (size_t)qmain * 2, Q - qmain, tail_parts, tpp, qnorm + qmain, cand_idx + (size_t)qmain * kTopK,
+            cand_lb + (size_t)qmain * kTopK);
+        return;
+    }
     if (qlist) {
         // listed queries only: select for every row of the list
         k_select_list<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(kept, qlist, qcount, Q, qnorm, cand_idx, cand_lb);
@@ -1157,6 +1193,29 @@ void launch_search_tc(const void *qtile, const float *qnorm, int Q, int K, const
 }
 
 size_t tc_kept_bytes(int Q, int nparts) { return sizeof(KeptGroups) * 2 * (size_t)std::max(Q, 1) * nparts; }
+
+// A search over the whole exemplar runs its query blocks unsplit, except those of the last,
+// partial wave (one CTA per SM): when at least one full wave precedes them and they would leave
+// most SMs idle, each is cut into up to 4 parts of the tiles, so the tail takes a fraction of a
+// wave instead of a whole one.  Results equal the unsplit search (the parts' groups are merged).
+void tc_tail_plan(int Q, int ntiles, int *tail_from, int *tail_parts) {
+    const int nqb = tc_query_blocks(Q), sms = 152;
+    *tail_from = nqb;
+    *tail_parts = 1;
+    const int full = nqb / sms * sms, tail = nqb - full;
+    if (full == 0 || tail == 0 || 2 * tail > sms) return;
+    const int p = std::min(4, std::min(sms / tail, ntiles / 16));
+    if (p < 2) return;
+    *tail_from = full;
+    *tail_parts = p;
+}
+
+size_t tc_kept_bytes_search(int Q, int ntiles, int nparts) {
+    if (nparts >= 1) return tc_kept_bytes(Q, nparts);
+    int tail_from = 0, tail_parts = 1;
+    tc_tail_plan(Q, ntiles, &tail_from, &tail_parts);
+    return tc_kept_bytes(Q, tail_parts);
+}
 
 int tc_padded_k8(int d) { return ((d + 1) + 31) / 32 * 32; }
 

@@ -4,10 +4,14 @@ or (--pyramid) whole coarse-to-fine syntheses with a search mode per level.
     python -m paper_2006_11851_gb300.profile_case --level 2 --mode exact --steps 2
     python -m paper_2006_11851_gb300.profile_case --pyramid --modes exact,f16,f16 --steps 2
     python -m paper_2006_11851_gb300.profile_case --big 4096 --steps 3 [--hist 32]
+    python -m paper_2006_11851_gb300.profile_case --rgbs --modes exact,f16,f16 --steps 2
 
 --big H projects (d = 64) and averages (M-step) one H x H output against the finest level's
 index (256x256 exemplar, w = 8), so that the working set is far above the L2 cache: a uniform
 random image and uniform random matches with weights in [0.5, 1.5).
+
+--rgbs runs the RGBS method of section 3 coarse to fine on the same workload (scale map of the
+synthetic exemplar's geometry, slant 60 degrees, tilt 0; scale-guided initialisation).
 
 Levels follow the 3-level workload (256x256 exemplar, shrink 4; windows 32/16/8; outputs
 128/256/512, d = 64).  The output image is a seeded random-patch initialisation.  Prints the
@@ -38,6 +42,7 @@ def main() -> int:
     ap.add_argument("--pyramid", action="store_true")
     ap.add_argument("--modes", default="exact,f16,f16")
     ap.add_argument("--big", type=int, default=0)
+    ap.add_argument("--rgbs", action="store_true")
     ap.add_argument("--hist", type=int, default=0, help="with --big: also time the Eq. 9 M-step and the final "
                                                         "histogram matching with this many bins")
     args = ap.parse_args()
@@ -45,6 +50,8 @@ def main() -> int:
         return run_pyramid(args)
     if args.big:
         return run_big(args)
+    if args.rgbs:
+        return run_rgbs(args)
     He, w, Ho = LEVELS[args.level]
     dev = torch.device("cuda:0")
     Z = P.synthetic_exemplar(0, 256, 4.0)
@@ -80,6 +87,22 @@ def run_pyramid(args) -> int:
         e1.synchronize()
         print(f"synthesis {s}: {e0.elapsed_time(e1):.3f} ms  final energies {E[:, -1]}")
     pidx.close()
+    return 0
+
+
+def run_rgbs(args) -> int:
+    dev = torch.device("cuda:0")
+    Z = torch.from_numpy(P.synthetic_exemplar(0, 256, 4.0)).to(dev)
+    modes = args.modes.split(",")
+    for s in range(args.steps):
+        u = torch.from_numpy(P.uniform_field(s, LEVELS[0][2], LEVELS[0][2])).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, E = pts.synthesize_pyramid_rgbs(Z, 60.0, 0.0, LEVELS[2][2], LEVELS[2][2], [w for _, w, _ in LEVELS], 5, u,
+                                           d=args.d, mode=modes)
+        e1.record()
+        e1.synchronize()
+        print(f"rgbs synthesis {s}: {e0.elapsed_time(e1):.3f} ms  final energies {[e[-1] for e in E]}")
     return 0
 
 

@@ -40,7 +40,7 @@ def test_batch_matches_sequential(mode):
         np.testing.assert_array_equal(E, ens[k])
     assert b.launches_per_run > 0
     if mode == "f16":
-        assert all(p >= 1 for p in b.parts)
+        assert all(p in (0, 1, 2, 4) for p in b.parts)  # 0: the automatic split
     b.close()
 
 

@@ -97,6 +97,26 @@ def test_f16_warm_start_and_parts_change_nothing():
 
 
 @pytest.mark.parametrize("mode", ["f16", "fp8"])
+def test_tail_split_changes_nothing(mode):
+    """The benchmark's fine level (501 query blocks, 3 full waves of 152 and a tail of 45): by
+    default only the tail's query blocks are split over several CTAs; the result equals uniform
+    splits of every block (2 and 3 parts) bit for bit, cold and warm."""
+    Z = P.synthetic_exemplar(0, 256, 4.0)
+    idx = pts.ExemplarIndex(_t(Z), 8, d=64)
+    X = _t(P.random_patch_init(Z, 512, 512, 8, 7))
+    ref = None
+    for parts in [0, 2, 3, 0]:
+        idx.set_tc_parts(parts)
+        for _ in range(2):
+            nn, d2 = pts.nn_search(idx, X, 2, mode)
+            if ref is None:
+                ref = (nn.clone(), d2.clone())
+            assert torch.equal(nn, ref[0]) and torch.equal(d2, ref[1]), (mode, parts)
+    idx.set_tc_parts(0)
+    idx.close()
+
+
+@pytest.mark.parametrize("mode", ["f16", "fp8"])
 def test_tc_split_changes_nothing(mode):
     """Explicit exemplar splits (1 part, even, ragged last part) with and without the warm bound
     give the single-part result bit for bit: the merge takes the best groups of the union."""
@@ -104,7 +124,7 @@ def test_tc_split_changes_nothing(mode):
     idx = pts.ExemplarIndex(_t(Z), 8, d=48)
     X = _t(P.random_patch_init(Z, 256, 256, 8, 4))
     ref = None
-    for parts in [1, 2, 4, 7]:
+    for parts in [1, 2, 4, 7, 0]:
         idx.set_tc_parts(parts)
         for _ in range(2):  # cold, then warm from the previous lists
             nn, d2 = pts.nn_search(idx, X, 2, mode)
