@@ -232,8 +232,8 @@ PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 /
 # ncu capture summarised in profiles/k_search_tc_fine_level_512_f16.md; reported only while the
 # search source file is unchanged (the digest below is of that file with the profiled kernel; any
 # later edit of the file, even of host code, turns the figure off until it is checked again).
-TC_TRAFFIC_BYTES = 32.895e6 + 0.016e6
-TC_TRAFFIC_SHA256 = "7020a2668531bcb00e066f77285b35f59d3ccb4680aa0f71bf5f311f132fe94f"
+TC_TRAFFIC_BYTES = 32.899e6 + 0.142e6
+TC_TRAFFIC_SHA256 = "6b12a965e026a288a1ba46d825b5243810b45fc9d6e980149759b4b7107215e3"
 
 
 def _tc_traffic():
@@ -356,6 +356,51 @@ def time_precision_form(pts, P, L, dev, stream, flush, steps, warmup, bf16_burst
     return res
 
 
+BATCHED_FORM = {
+    "workload": "batched form: 64 independent single-level jobs in one CUDA graph, exemplars 128-512 px "
+                "square (shrink 4, generator seeds 0-63), outputs 256-1024 px square, windows 8x8 (even jobs) "
+                "and 16x16 (odd jobs), PCA 32/48/64, FP16 tensor-core search + FP32 re-rank, 5 EM iterations + "
+                "final search per job, exemplar split per job shape picked by the autotuner",
+    "jobs": 64, "iters": 5, "mode": "f16",
+}
+
+
+def time_batched(dev, stream, flush, steps, warmup):
+    """queries/s and EM iterations/s of one graph replay of the 64-job batch."""
+    import torch
+    from paper_2006_11851_gb300.batched import Batch, job_specs
+    cfg = BATCHED_FORM
+    specs = job_specs(cfg["jobs"])
+    t0 = time.perf_counter()
+    b = Batch(specs, mode=cfg["mode"], iters=cfg["iters"], n_streams=8)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        b.reset()
+        b.run()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        b.reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run()
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    for ix in b.indices:
+        ix.device_status()
+    q = b.queries()
+    out = {"config": dict(cfg, index_build_and_autotune_s=build_s, queries_per_run=q,
+                          launches_per_run=b.launches_per_run, autotuned_parts=b.parts.tolist()),
+           "value": q * steps / (ms / 1000.0), "unit": "queries/s", "ms_per_run": ms / steps, "runs": steps,
+           "em_iterations_per_s": len(b.indices) * cfg["iters"] * steps / (ms / 1000.0)}
+    b.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,6 +418,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries per level for the CPU baseline")
     ap.add_argument("--d-fast", type=int, default=0, help="PCA dimensions of the tensor-core search (0 = library default)")
     ap.add_argument("--no-robust", action="store_true", help="skip the robust-schedule timing (other_configs)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched form: 64 uneven jobs in one CUDA graph (other_configs)")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the 512x512 -> 1024x1024, w = 16 precision-form timing (other_configs)")
     args = ap.parse_args()
@@ -630,6 +677,9 @@ def main():
             "m_steps_per_level": np.mean(rob_steps, axis=0).tolist(),
             "em_iterations_per_s": float(np.sum(rob_steps)) / (rob_ms / 1000.0),
             "final_energy_ratio_vs_exact_fixed_schedule": {"max": max(rob_ratios), "mean": float(np.mean(rob_ratios))}}
+
+    if not args.no_batched:
+        other_cfgs["batched"] = time_batched(dev, stream, flush, args.steps, args.warmup)
 
     headline = None
     if also == "proposal" or args.mode == "proposal":

@@ -412,3 +412,27 @@ def test_exact_bound_components_change_the_route_not_the_result():
     nn_o, d2_o = oracle.nn_bruteforce(Xh, Z, 8, 2, qlist=sub)
     check_nn(Xh, Z, 8, 2, nn_f.cpu().numpy()[sub], d2_f.cpu().numpy()[sub], nn_o, d2_o, qlist=sub)
     idx.close()
+
+
+@pytest.mark.parametrize("He,Ho,w,d,stride", [(64, 128, 8, 24, 2), (48, 64, 16, 64, 2), (40, 52, 8, 32, 4),
+                                              (30, 37, 5, 12, 1)])
+def test_project_queries_against_oracle(He, Ho, w, d, stride):
+    """Query projection y_q = B^T (x_q - mu) (section 2.2) on its own, against the oracle's FP64
+    projection onto its FP64 basis.  Eigenvectors are defined up to sign, so coordinates are
+    compared in absolute value, for components separated from their neighbours by a gap; the
+    squared norm of all d coordinates is compared as it is (it does not depend on the basis
+    chosen inside the subspace).  FP32 path: 1e-4 relative to the largest window norm."""
+    Z = P.synthetic_exemplar(9, He, 3.0)
+    X = P.random_patch_init(Z, Ho, Ho, w, 4)
+    idx = pts.ExemplarIndex(_t(Z), w, d=d)
+    y = pts.project_queries(idx, _t(X), stride).cpu().numpy().astype(np.float64)
+    mu, B, ev, _ = oracle.pca_fit(Z, w, d)
+    yo, uo, _ = oracle.project(X, w, stride, mu, B)
+    assert y.shape == yo.shape
+    scale = np.sqrt(uo.max())
+    gap = np.minimum(np.abs(np.diff(ev[:d + 1], prepend=np.inf))[:d], np.abs(np.diff(ev[:d + 1]))[:d])
+    ok = gap > 1e-4 * ev[0]
+    assert ok.sum() >= d // 2
+    np.testing.assert_allclose(np.abs(y[:, ok]), np.abs(yo[:, ok]), atol=1e-4 * scale)
+    np.testing.assert_allclose((y ** 2).sum(1), (yo ** 2).sum(1), atol=1e-4 * scale ** 2)
+    idx.close()
