@@ -253,27 +253,30 @@ def _peaks():
 
 def exact_route_counts(pts, pidx, x0, cfg):
     """One exact-mode synthesis of the workload replayed search by search (the same calls
-    synthesize_level makes: search, IRLS weights, M-step; a last search), returning per level the
-    queries the full-dimension pass took, the queries certified from the PCA bound and all
-    queries, summed over the level's searches."""
+    synthesize_level makes: search, IRLS weights, M-step; a last search), returning per level,
+    summed over the level's searches: the queries the full-dimension pass took, the queries the
+    first PCA bound did not certify (the second bound's queries when it runs), those certified by
+    the first bound and all queries."""
     X = x0.clone()
-    rng, cert, allq = [], [], []
+    rng, second, cert, allq = [], [], [], []
     for lev, ix in enumerate(pidx.indices):
-        r = c = a = 0
+        r = s2 = c = a = 0
         for t in range(cfg["iters"] + 1):
             nn, d2 = pts.nn_search(ix, X, cfg["stride"], "exact")
             st = ix.search_stats()
-            r, c, a = r + st["range_queries"], c + st["certified"], a + st["queries"]
+            r, c, a = r + st["full_queries"], c + st["certified"], a + st["queries"]
+            s2 += st["second_queries"]
             if t < cfg["iters"]:
                 wts, _ = pts.irls_weights(d2, cfg["r"], 1e-3)
                 H, W, _ = X.shape
                 X = pts.m_step(ix, nn, wts, H, W, cfg["stride"])
         rng.append(r)
+        second.append(s2)
         cert.append(c)
         allq.append(a)
         if lev + 1 < pidx.levels:
             X = pts.upsample2(X)
-    return {"range_queries": rng, "certified": cert, "queries": allq}
+    return {"range_queries": rng, "second_bound_queries": second, "certified": cert, "queries": allq}
 
 
 PRECISION_FORM = {
@@ -587,6 +590,9 @@ def main():
     route = exact_route_counts(pts, pidx, init_dev(args.warmup), cfg)
     full_fl = sum(2.0 * l["D"] * l["N"] * n for l, n in zip(sizes, route["range_queries"]))
     pca_fl = sum(2.0 * (inf["exact_dims"] + 1) * l["N"] * l["Q"] * it for l, inf in pca_levels)
+    # the second bound (d_fast components) on the first bound's uncertified queries, same class
+    pca_fl += sum(2.0 * (inf["d_fast"] + 1) * l["N"] * n
+                  for l, inf, n in zip(sizes, [ix.info for ix in pidx.indices], route["second_bound_queries"]))
     ex_roofs = {}
     if "search_topk" in ex_kern and pca_levels:
         ach = pca_fl / (ex_kern["search_topk"]["ms_per_step"] / 1000.0) / 1e12

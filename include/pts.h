@@ -61,11 +61,15 @@ typedef enum {
  *   PTS_EXACT_F32     the full-dimension nearest neighbour of Eq. 4.  PCA
  *                     coordinates plus the residual norm give a lower bound
  *                     on every full-dimension distance; the 32 best bounds
- *                     are re-ranked in full dimension and certified.
- *                     Uncertified queries get a full-dimension GEMM pass
- *                     (top-32 again, re-ranked, certified against the FP32
- *                     rounding bound), and what still fails a direct scan.
- *                     FP32 SIMT, no tensor cores.
+ *                     are re-ranked in full dimension and certified (the
+ *                     best distance lies below the 32nd bound by a slack
+ *                     tau_q = 8 sqrt(D) 2^-24 (||u_q||^2 + max_n ||u_n||^2)
+ *                     that models FP32 rounding; it is not a worst-case
+ *                     bound).  Queries the first d components leave
+ *                     uncertified get the same bound with the index's d_fast
+ *                     components, then a full-dimension GEMM pass (top-32
+ *                     again, re-ranked, certified the same way), and what
+ *                     still fails a direct scan.  FP32 SIMT, no tensor cores.
  *   PTS_F16_RERANK    PCA-space bounds (d_fast coordinates + residual) as an
  *                     FP16 tensor-core GEMM (FP32 accumulate), top-32 by
  *                     bound, exact FP32 full-dimension re-rank.  Not
@@ -126,14 +130,20 @@ typedef struct {
 
 typedef struct {
     long long queries;        /* queries of the last nn_search */
-    long long certified;      /* exact mode: certified from the 32 best bounds */
-    long long range_queries;  /* exact mode: queries sent to the full-dimension pass */
-    long long range_pairs;    /* exact mode: queries that pass did not certify */
+    long long certified;      /* exact mode: certified from the 32 best bounds of the first PCA bound */
+    long long range_queries;  /* exact mode: queries the first bound did not certify (sent to the
+                                 second bound when it runs, else to the full-dimension pass) */
+    long long range_pairs;    /* exact mode: queries the full-dimension pass did not certify */
     long long brute_queries;  /* exact mode: queries that needed a direct scan */
     long long fallback_queries; /* proposal mode: queries sent to the exact search */
     long long full_splits;    /* exact mode: pieces the full-dimension pass cut the window
                                  vectors into (partial sums added in fixed order); 1 = not
                                  cut, 0 = no full-dimension pass ran */
+    long long second_certified; /* exact mode: queries the second bound (the index's d_fast
+                                 components, run on the first bound's uncertified queries)
+                                 certified */
+    long long full_queries;   /* exact mode: queries the full-dimension pass searched */
+    long long second_queries; /* exact mode: queries the second bound searched (0 when it did not run) */
 } pts_search_stats;
 
 /* Parameters of the learned cluster proposal (pts_train_proposal). */
@@ -254,11 +264,12 @@ pts_status pts_index_load(const char *path, pts_index *out);
 pts_status pts_index_set_tc_parts(pts_index index, int parts);
 
 /* The components of the exact search's PCA lower bound (section 2.2's PCA; no counterpart in
- * the paper, a tuning knob): fast = 0 (the default) bounds with the index's first d components,
- * fast = 1 with its d_fast components when d_fast > d (fewer queries need the full-dimension
- * pass, each bound costs about twice as much; on the benchmark's levels the default is faster).
- * Results are the certified nearest windows of Eq. 4 either way.  PTS_ERR_INVALID_ARG for other
- * values. */
+ * the paper, a tuning knob).  fast = 0 (the default): every query is bounded with the index's
+ * first d components, and the queries that bound cannot certify are bounded again with its d_fast
+ * components (when d_fast > d) before the full-dimension pass takes what is left.  fast = 1: one
+ * bound, with the d_fast components (each bound costs about twice as much).  fast = 2: one bound,
+ * with the first d components.  Results are the certified nearest windows of Eq. 4 whatever the
+ * choice.  PTS_ERR_INVALID_ARG for a NULL index or other values. */
 pts_status pts_index_set_exact_bound(pts_index index, int fast);
 
 /*

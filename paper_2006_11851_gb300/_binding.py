@@ -44,7 +44,8 @@ class _SearchStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_longlong), ("certified", ctypes.c_longlong),
                 ("range_queries", ctypes.c_longlong), ("range_pairs", ctypes.c_longlong),
                 ("brute_queries", ctypes.c_longlong), ("fallback_queries", ctypes.c_longlong),
-                ("full_splits", ctypes.c_longlong)]
+                ("full_splits", ctypes.c_longlong), ("second_certified", ctypes.c_longlong),
+                ("full_queries", ctypes.c_longlong), ("second_queries", ctypes.c_longlong)]
 
 
 class _ProposalParams(ctypes.Structure):
@@ -262,10 +263,11 @@ class ExemplarIndex:
         """Exemplar split of the tensor-core searches (0 = automatic); results do not depend on it."""
         _check(lib().pts_index_set_tc_parts(self.handle, int(parts)))
 
-    def set_exact_bound(self, fast: bool) -> None:
-        """Components of the exact search's PCA bound: the index's d_fast (True) or its first d
-        (False, the default); the certified results do not depend on it."""
-        _check(lib().pts_index_set_exact_bound(self.handle, 1 if fast else 0))
+    def set_exact_bound(self, fast) -> None:
+        """Components of the exact search's PCA bound: 0 / False (the default) the first d, then
+        d_fast for what that bound leaves uncertified; 1 / True d_fast only; 2 the first d only.
+        The certified results do not depend on it."""
+        _check(lib().pts_index_set_exact_bound(self.handle, int(fast)))
         self._read_info()
 
 

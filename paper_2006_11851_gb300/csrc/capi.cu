@@ -74,7 +74,7 @@ pts_status ensure_workspace(pts_index idx, int Q) {
     PTS_TRY(ws.cand_lb.ensure((size_t)cap * kTopK, "candidate bounds"));
     PTS_TRY(ws.fail_list.ensure(cap, "fail list"));
     PTS_TRY(ws.fail2_list.ensure(cap, "second fail list"));
-    PTS_TRY(ws.qfull.ensure(qpad * padded_dim(idx->D), "full query vectors"));
+    PTS_TRY(ws.qfull.ensure(qpad * std::max(padded_dim(idx->D), padded_dim(idx->da_fast)), "full query vectors"));
     PTS_TRY(ws.best64.ensure(cap, "packed minima"));
     PTS_TRY(ws.thr0.ensure(2 * (size_t)cap, "warm-start bounds"));
     PTS_TRY(ws.pca_thr.ensure((size_t)cap, "PCA-pass bounds"));
@@ -105,24 +105,23 @@ pts_status read_status(pts_index idx, cudaStream_t st) {
     return PTS_OK;
 }
 
-// Exact search for the queries listed in ws.fail_list (count on the device): full-dimension
-// GEMM top-32, certified re-rank, direct scan for what is still uncertified.
-pts_status exact_on_list(pts_index idx, const RerankArgs &ra, unsigned int *fail_count, unsigned int *fail2_count,
-                         unsigned int *brute_count, int32_t *nn_out, float *d2_out, cudaStream_t st) {
+// Exact search for the queries listed in in_list (count on the device): full-dimension GEMM
+// top-32, certified re-rank (what stays uncertified goes to out_list), direct scan of those.
+pts_status exact_on_list(pts_index idx, const RerankArgs &ra, int *in_list, unsigned int *in_count, int *out_list,
+                         unsigned int *out_count, unsigned int *brute_count, int32_t *nn_out, float *d2_out,
+                         cudaStream_t st) {
     Workspace &ws = idx->ws;
-    const int np = full_parts(ra.Q, idx->ntiles);
-    if (np > 1) {
-        PTS_TRY(ws.part_v.ensure((size_t)ra.Q * np * kTopK, "part lists"));
-        PTS_TRY(ws.part_i.ensure((size_t)ra.Q * np * kTopK, "part lists"));
-    }
-    idx->last.full_splits = launch_search_full(ra.X, ra.Wo, idx->C, idx->w, ra.stride, ra.qx, idx->mu.ptr, ws.fail_list.ptr, fail_count, ra.Q,
-                       ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr,
-                       ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, np, idx->status.ptr, st, idx->N,
-                       &ws.full_pdist);
-    launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out,
-                  ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
-    launch_brute_fallback(ra, ws.fail2_list.ptr, fail2_count, brute_count, ws.best64.ptr, idx->status.ptr, st);
-    launch_resolve(ws.fail2_list.ptr, fail2_count, ws.best64.ptr, ra.Q, nn_out, d2_out, st);
+    PTS_TRY(ws.part_v.ensure(full_part_capacity(ra.Q), "part lists"));
+    PTS_TRY(ws.part_i.ensure(full_part_capacity(ra.Q), "part lists"));
+    idx->last.full_splits = launch_search_full(ra.X, ra.Wo, idx->C, idx->w, ra.stride, ra.qx, idx->mu.ptr, in_list,
+                                               in_count, ra.Q, ws.qfull.ptr, idx->efull.ptr, idx->enorm.ptr,
+                                               idx->ntiles, ws.qnorm.ptr, ws.cand_idx.ptr, ws.cand_lb.ptr,
+                                               ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st, idx->N,
+                                               &ws.full_pdist);
+    launch_rerank(ra, in_list, in_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out, d2_out, out_list,
+                  out_count, ws.best64.ptr, idx->status.ptr, st);
+    launch_brute_fallback(ra, out_list, out_count, brute_count, ws.best64.ptr, idx->status.ptr, st);
+    launch_resolve(out_list, out_count, ws.best64.ptr, ra.Q, nn_out, d2_out, st);
     return PTS_OK;
 }
 
@@ -197,7 +196,7 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
                         int32_t *nn_out, float *d2_out, cudaStream_t st) {
     Workspace &ws = idx->ws;
     // the bound's components: the index's d_fast (the larger PCA) or its first d
-    const bool fast = idx->exact_fast && idx->d_fast > idx->d && idx->et_fast_rows.ptr;
+    const bool fast = idx->exact_fast == 1 && idx->d_fast > idx->d && idx->et_fast_rows.ptr;
     const int bd = fast ? idx->d_fast : idx->d, bda = fast ? idx->da_fast : idx->da;
     const float *bet = fast ? idx->et_fast.ptr : idx->et.ptr;
     const float *brows = fast ? idx->et_fast_rows.ptr : idx->et_rows.ptr;
@@ -208,6 +207,8 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     unsigned int *fail_count = ws.counters.ptr + 0;
     unsigned int *fail2_count = ws.counters.ptr + 1;
     unsigned int *brute_count = ws.counters.ptr + 2;
+    unsigned int *fail3_count = ws.counters.ptr + 3;
+    idx->last_cascade = 0;
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
     if (bvar < kPcaPassMinVar) {
         // the bound would certify few queries: every query goes to the full-dimension pass (its
@@ -235,8 +236,28 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
         // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
         launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
                       d2_out, ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
+        // pass 1b, for the listed queries only: the same bound with the index's d_fast components
+        // (the larger PCA the tensor-core searches use), certified the same way
+        if (!fast && idx->exact_fast == 0 && idx->d_fast > idx->d && idx->var_fast >= kPcaPassMinVar &&
+            idx->da_fast % 32 == 0) {
+            idx->last_cascade = 1;
+            launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast,
+                           idx->da_fast, 0, ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st,
+                           &ws.proj_part);
+            PTS_TRY(ws.part_v.ensure(full_part_capacity(Q), "part lists"));
+            PTS_TRY(ws.part_i.ensure(full_part_capacity(Q), "part lists"));
+            launch_search_rows(ws.qcoord.ptr, idx->da_fast, ws.fail_list.ptr, fail_count, Q, idx->da_fast,
+                               ws.qfull.ptr, idx->et_fast.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr,
+                               ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st);
+            launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,
+                          d2_out, ws.fail2_list.ptr, fail2_count, ws.best64.ptr, idx->status.ptr, st);
+            PTS_TRY(exact_on_list(idx, ra, ws.fail2_list.ptr, fail2_count, ws.fail_list.ptr, fail3_count, brute_count,
+                                  nn_out, d2_out, st));
+            return PTS_OK;
+        }
     }
-    PTS_TRY(exact_on_list(idx, ra, fail_count, fail2_count, brute_count, nn_out, d2_out, st));
+    PTS_TRY(exact_on_list(idx, ra, ws.fail_list.ptr, fail_count, ws.fail2_list.ptr, fail2_count, brute_count, nn_out,
+                          d2_out, st));
     return PTS_OK;
 }
 
@@ -728,14 +749,14 @@ pts_status pts_index_get_info(pts_index idx, pts_index_info *info) {
     info->eig_iters = idx->eig_iters;
     info->unorm2_max = idx->unorm2_max;
     info->channels = idx->C;
-    const bool fast = idx->exact_fast && idx->d_fast > idx->d;
+    const bool fast = idx->exact_fast == 1 && idx->d_fast > idx->d;
     info->exact_dims = fast ? idx->d_fast : idx->d;
     info->exact_var = fast ? idx->var_fast : idx->var_retained;
     return PTS_OK;
 }
 
 pts_status pts_index_set_exact_bound(pts_index idx, int fast) {
-    if (!idx || (fast != 0 && fast != 1)) return set_error(PTS_ERR_INVALID_ARG, "pts_index_set_exact_bound: bad argument");
+    if (!idx || fast < 0 || fast > 2) return set_error(PTS_ERR_INVALID_ARG, "pts_index_set_exact_bound: bad argument");
     idx->exact_fast = fast;
     return PTS_OK;
 }
@@ -811,15 +832,24 @@ pts_status pts_index_search_stats(pts_index idx, pts_search_stats *stats, void *
         unsigned int c[4] = {0, 0, 0, 0};
         PTS_CUDA_TRY(cudaMemcpyAsync(c, idx->ws.counters.ptr, sizeof(c), cudaMemcpyDeviceToHost, st));
         PTS_CUDA_TRY(cudaStreamSynchronize(st));
+        stats->second_certified = 0;
+        stats->second_queries = 0;
         if (idx->last_mode == PTS_EXACT_F32) {
             stats->range_queries = c[0];
             stats->certified = stats->queries - c[0];
+            // with the second bound: c[1] of the c[0] queries reached the full pass, c[3] of those
+            // stayed uncertified
+            stats->full_queries = idx->last_cascade ? c[1] : c[0];
+            stats->second_certified = idx->last_cascade ? c[0] - c[1] : 0;
+            stats->second_queries = idx->last_cascade ? c[0] : 0;
+            stats->range_pairs = idx->last_cascade ? c[3] : c[1];
         } else {
             stats->fallback_queries = c[0];
             stats->range_queries = 0;
             stats->certified = 0;
+            stats->full_queries = 0;
+            stats->range_pairs = c[1];
         }
-        stats->range_pairs = c[1];
         stats->brute_queries = c[2];
     }
     return PTS_OK;

@@ -19,6 +19,8 @@ namespace pts {
 constexpr int kBN = 128;   // exemplar windows per tile (32 lanes x 4)
 constexpr int kBQ = 64;    // queries per CTA (8 warps x 8 rows)
 constexpr int kTopK = 32;  // candidates kept per query (one per lane)
+constexpr int kMaxAdaptiveParts = 32;    // exemplar parts of an adaptive full-dimension pass
+constexpr int kAdaptiveItems = 4 * 152;  // its (query block, part) items: two rounds of its grid
 constexpr int kMaxDA = 68;     // exact search: d <= 64 coordinates + residual, padded to 4
 constexpr int kMaxD = 64;      // PCA dimensions of the exact search
 constexpr int kMaxDPca = 128;  // PCA dimensions an index may keep (fast modes use up to kMaxDFast)
@@ -213,7 +215,8 @@ struct pts_index_s {
     pts::DevBuf<float> et_fast;   // [ntiles][da_fast][kBN] = -2 (y_n, r_n, 0...) with d_fast coordinates
     pts::DevBuf<float> et_fast_rows;  // [N][da_fast], the same vectors window-major (warm-start bound)
     double var_fast = 0.0;        // variance fraction the d_fast components keep
-    int exact_fast = 0;           // the exact search bounds with the d_fast components (else the first d)
+    int exact_fast = 0;           // exact bound: 0 d then d_fast, 1 d_fast only, 2 d only
+    int last_cascade = 0;         // the last exact search ran the second (d_fast) bound on its listed queries
     pts::DevBuf<__half> etc;      // [tc_tiles(N)][tc_tile_rows() x Ktc] FP16 MMA operand tiles
     pts::DevBuf<uint8_t> etc8;    // [tc_tiles(N)][tc_tile_rows() x Kf8] FP8 E4M3 operand tiles
     pts::DevBuf<float> f8scale;   // [d_fast + 1] per-dimension scales of the FP8 tiles
@@ -267,13 +270,21 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
                         cudaStream_t st, int nparts = 1,
                         float *part_v = nullptr, int *part_i = nullptr,
                         const float *thr_init = nullptr);
+// The listed queries' rows of `rows` (da floats each) searched against tiles [ntiles][Dp][128]
+// with the full pass's GEMM + top-32 (Dp a multiple of 32; qtiles holds [F/64][Dp][64];
+// part_v / part_i hold full_part_capacity(Q) entries).
+void launch_search_rows(const float *rows, int da, const int *list, const unsigned int *count, int Q, int Dp,
+                        float *qtiles, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
+                        int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
+                        cudaStream_t st);
 int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                        int nparts, int *status, cudaStream_t st, int N,
+                        int *status, cudaStream_t st, int N,
                         DevBuf<float> *pdist);
-int full_parts(int Q, int ntiles);
+// entries of each part list the full-dimension passes need for Q queries
+size_t full_part_capacity(int Q);
 int pca_parts(int Q, int ntiles);
 void launch_tiles_to_rows(const float *et, int N, int da, float *rows, cudaStream_t st);
 void launch_warm_pca(const int *prev_idx, const float *qcoord, int da, const float *et_rows, const float *enorm, int Q,

@@ -294,6 +294,22 @@ __global__ void __launch_bounds__(256) k_merge_pca_parts(const float *__restrict
 constexpr int kKC = 32;     // K rows per chunk
 constexpr int kStages = 4;  // ring depth
 
+// Exemplar parts of an adaptive full pass with nf listed queries: as many parts (at most
+// kMaxAdaptiveParts, each at least 4 tiles) as keep the (query block, part) items within two
+// rounds of the grid, kAdaptiveItems = 2 x 2 x 152.  The pass and its merge take the same value
+// from the same device count.  Items never exceed kAdaptiveItems when there is more than one
+// part, so the part lists need at most kAdaptiveItems * kBQ records of 32 (full_part_capacity).
+__device__ __forceinline__ int adaptive_parts(int nf, int ntiles) {
+    const int nqb = (nf + kBQ - 1) / kBQ;
+    if (nqb <= 0) return 1;
+    int p = kAdaptiveItems / nqb;
+    p = min(p, kMaxAdaptiveParts);
+    p = min(p, ntiles / 4);
+    if (p <= 1) return 1;
+    const int tpp = (ntiles + p - 1) / p;
+    return (ntiles + tpp - 1) / tpp;
+}
+
 struct FullSmem {
     float a[kStages][kKC][kBQ];
     float e[kStages][kKC][kBN];
@@ -309,24 +325,25 @@ __global__ void __launch_bounds__(kThreads, 2)
                   const float *__restrict__ enorm, int ntiles, int tiles_per_part,
                   const float *__restrict__ qnorm, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
                   float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status,
-                  int kc_split, float *__restrict__ pdist) {
+                  int kc_split, float *__restrict__ pdist, int adaptive) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FullSmem &sm = *reinterpret_cast<FullSmem *>(smem_raw);
     const int nf = static_cast<int>(*fail_count);
-    const int fbase = blockIdx.x * kBQ;
-    if (fbase >= nf) return;  // uniform for the CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = warp * 8;
-    // this CTA's exemplar tiles (blockIdx.y splits them; parts are merged afterwards) and chunks
-    // of the vector (blockIdx.z splits them when pdist is given: partial sums, summed afterwards)
-    const int c0 = blockIdx.z * kc_split, c1 = min(Dp / kKC, c0 + kc_split);
-    const int nchunks = c1 - c0;
-    const int t_begin = blockIdx.y * tiles_per_part;
-    const int nt = max(0, min(ntiles, t_begin + tiles_per_part) - t_begin);
-    const long total = (long)nt * nchunks;
-    const float *qa = qfull + (size_t)blockIdx.x * Dp * kBQ;
-    TopK8 top;
-    top.init();
+    // Work items (query block, exemplar part).  Fixed grids: blockIdx.x is the block, blockIdx.y
+    // the part.  Adaptive grids (a fixed number of CTAs, whatever the device-side count of listed
+    // queries): the part count follows that count (adaptive_parts), and each CTA takes items
+    // blockIdx.x, blockIdx.x + gridDim.x, ...
+    int nparts = gridDim.y, tpp = tiles_per_part;
+    int item = 0, nitems = 1, step = 1;
+    if (adaptive) {
+        nparts = adaptive_parts(nf, ntiles);
+        tpp = (ntiles + nparts - 1) / nparts;
+        nitems = (nf + kBQ - 1) / kBQ * nparts;
+        item = blockIdx.x;
+        step = gridDim.x;
+    }
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sm.bar[s], 1);
@@ -336,8 +353,27 @@ __global__ void __launch_bounds__(kThreads, 2)
         sm.abort_flag = 0;
     }
     __syncthreads();
+    // Stages and barrier phases follow one running chunk count g0 + it over all of this CTA's
+    // items, so the barriers are initialised once.  Every copy of an item is consumed before its
+    // closing block barrier, so the next item fills its first stages without waiting.
+    long g0 = 0;
+    for (; item < nitems; item += step) {
+    const int qb = adaptive ? item / nparts : (int)blockIdx.x;
+    const int part = adaptive ? item % nparts : (int)blockIdx.y;
+    const int fbase = qb * kBQ;
+    if (fbase >= nf) return;  // uniform for the CTA
+    // this item's exemplar tiles (parts are merged afterwards) and chunks of the vector
+    // (blockIdx.z splits them when pdist is given: partial sums, summed afterwards)
+    const int c0 = blockIdx.z * kc_split, c1 = min(Dp / kKC, c0 + kc_split);
+    const int nchunks = c1 - c0;
+    const int t_begin = part * tpp;
+    const int nt = max(0, min(ntiles, t_begin + tpp) - t_begin);
+    const long total = (long)nt * nchunks;
+    const float *qa = qfull + (size_t)qb * Dp * kBQ;
+    TopK8 top;
+    top.init();
     auto issue = [&](long it) {
-        const int s = (int)(it % kStages);
+        const int s = (int)((g0 + it) % kStages);
         const long t = it / nchunks;
         const int c = c0 + (int)(it - t * nchunks);
         mbar_expect_tx(&sm.bar[s], (uint32_t)(kKC * (kBQ + kBN) * 4));
@@ -355,11 +391,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (tid == 0)
         for (long it = 0; it < kStages && it < total; ++it) {
             issue(it);
-            last_issued[it] = it;
+            last_issued[(g0 + it) % kStages] = g0 + it;
         }
     float acc[8][4];
     for (long it = 0; it < total; ++it) {
-        const int s = (int)(it % kStages);
+        const int s = (int)((g0 + it) % kStages);
         const long t = it / nchunks;
         const int c = c0 + (int)(it - t * nchunks);
         if (c == c0) {
@@ -374,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 acc[i][3] = nv.w;
             }
         }
-        const uint32_t par = (uint32_t)((it / kStages) & 1);
+        const uint32_t par = (uint32_t)(((g0 + it) / kStages) & 1);
         const bool ok = mbar_wait_or_abort(&sm.bar[s], par, status, &sm.abort_flag);
         if (!__all_sync(kFull, ok)) {
             sm.abort_flag = 1;
@@ -413,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             bool refilled = false;
             if (lane == 0 && mbar_wait_or_abort(&sm.empty[s], par, status, &sm.abort_flag)) {
                 issue(it + kStages);
-                last_issued[s] = it + kStages;
+                last_issued[s] = g0 + it + kStages;
                 refilled = true;
             }
             if (!__shfl_sync(kFull, refilled, 0)) {
@@ -431,12 +467,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         return;
     }
     if (pdist) return;
+    g0 += total;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int f = fbase + row0 + i;
         if (f < nf) {
-            if (gridDim.y > 1) {
-                const size_t o = ((size_t)f * gridDim.y + blockIdx.y) * kTopK + lane;
+            if (nparts > 1) {
+                const size_t o = ((size_t)f * nparts + part) * kTopK + lane;
                 part_v[o] = top.ld[i];
                 part_i[o] = top.li[i];
                 continue;
@@ -450,6 +487,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         }
     }
+    __syncthreads();  // every warp is done with the stages before the next item re-arms them
+    }
 }
 
 // (a, ia) < (b, ib) lexicographically; window -1 (no window) only ever pairs with +inf
@@ -459,13 +498,16 @@ __device__ __forceinline__ bool lex_less_f(float a, int ia, float b, int ib) {
 
 // One warp per listed query: the 32 smallest (p, n) over the parts' sorted lists (the elementwise
 // minimum of a list and another reversed is bitonic; five stages sort it).
-__global__ void k_merge_fail_parts(const float *__restrict__ part_v, const int *__restrict__ part_i, int nparts,
+__global__ void k_merge_fail_parts(const float *__restrict__ part_v, const int *__restrict__ part_i, int ntiles,
                                    const int *__restrict__ fail_list, const unsigned int *__restrict__ fail_count,
                                    int Q, const float *__restrict__ qnorm, int *__restrict__ cand_idx,
                                    float *__restrict__ cand_lb, int *__restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (f >= (int)*fail_count) return;
+    const int nf = (int)*fail_count;
+    if (f >= nf) return;
+    const int nparts = adaptive_parts(nf, ntiles);
+    if (nparts == 1) return;  // the pass wrote the candidates itself
     const size_t base = (size_t)f * nparts * kTopK;
     float v = part_v[base + lane];
     int i = part_i[base + lane];
@@ -566,6 +608,24 @@ __global__ void k_exemplar_full(const float *__restrict__ Z, int We, int C, int 
     }
 }
 
+// Rows of listed queries (row q of rows, da floats) as the pass's query tiles [F/64][Dp][64],
+// zero past da: the second, larger PCA bound of the exact search runs through k_search_full on
+// these instead of full window vectors.
+__global__ void k_gather_rows(const float *__restrict__ rows, int da, const int *__restrict__ list,
+                              const unsigned int *__restrict__ count, int Q, int Dp, float *__restrict__ out) {
+    const long n = (long)(*count) * Dp;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / Dp), k = (int)(i - (long)f * Dp);
+        float v = 0.0f;
+        if (k < da) {
+            int q = list[f];
+            q = q < 0 ? 0 : (q >= Q ? Q - 1 : q);
+            v = rows[(size_t)q * da + k];
+        }
+        out[((size_t)(f / kBQ) * Dp + k) * kBQ + (f % kBQ)] = v;
+    }
+}
+
 }  // namespace
 
 void launch_tiles_to_rows(const float *et, int N, int da, float *rows, cudaStream_t st) {
@@ -615,11 +675,28 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
                                                                        cand_lb);
 }
 
+// The full-dimension pass over the listed queries (count on the device): a fixed grid of two
+// CTAs per SM takes the (query block, exemplar part) items, the part count set on the device from
+// the count (adaptive_parts), then the part lists are merged (the merge returns at once when
+// there is one part).  part_v / part_i hold full_part_capacity(Q) entries.
+static void launch_full_adaptive(const float *qtiles, const int *list, const unsigned int *count, int Q, int Dp,
+                                 const float *etiles, const float *enorm, int ntiles, const float *qnorm,
+                                 int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
+                                 cudaStream_t st) {
+    if (Q <= 0) return;
+    const int grid = (int)std::min<long>((long)ceil_div((long)Q, kBQ) * kMaxAdaptiveParts, 2L * 152);
+    k_search_full<<<grid, kThreads, sizeof(FullSmem), st>>>(qtiles, list, count, Q, Dp, etiles, enorm, ntiles, 0,
+                                                            qnorm, cand_idx, cand_lb, part_v, part_i, status,
+                                                            Dp / kKC, nullptr, 1);
+    k_merge_fail_parts<<<ceil_div((long)std::min(Q, kAdaptiveItems * kBQ) * 32, 256), 256, 0, st>>>(
+        part_v, part_i, ntiles, list, count, Q, qnorm, cand_idx, cand_lb, status);
+}
+
 int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx, const float *mu,
                         const int *fail_list, const unsigned int *fail_count, int Q,
                         float *qfull, const float *efull, const float *enorm, int ntiles,
                         const float *qnorm, int *cand_idx, float *cand_lb, float *part_v, int *part_i,
-                        int nparts, int *status, cudaStream_t st, int N, DevBuf<float> *pdist) {
+                        int *status, cudaStream_t st, int N, DevBuf<float> *pdist) {
     const size_t smem = sizeof(FullSmem);
     set_smem_attr(reinterpret_cast<const void *>(k_search_full), (int)smem);
     const int Dp = padded_dim(C * w * w);
@@ -643,28 +720,32 @@ int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx,
         ProfScope ps(kProfSearchFull, st, 2);
         k_search_full<<<dim3(nqb, ntiles, nsplit), kThreads, smem, st>>>(
             qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles, 1, qnorm, cand_idx, cand_lb, part_v, part_i,
-            status, kcs, pdist->ptr);
+            status, kcs, pdist->ptr, 0);
         k_full_select<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(pdist->ptr, nsplit, (int)npad, N, fail_list,
                                                                     fail_count, Q, qnorm, cand_idx, cand_lb, status);
         return nsplit;
     }
-    const int tpp = ceil_div(ntiles, nparts);
-    const int np = ceil_div(ntiles, tpp);
-    ProfScope ps(kProfSearchFull, st, np > 1 ? 2 : 1);
-    k_search_full<<<dim3(nqb, np), kThreads, smem, st>>>(qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles,
-                                                         tpp, qnorm, cand_idx, cand_lb, part_v, part_i, status,
-                                                         nchunks, nullptr);
-    if (np > 1)
-        k_merge_fail_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, fail_list, fail_count,
-                                                                        Q, qnorm, cand_idx, cand_lb, status);
+    ProfScope ps(kProfSearchFull, st, 2);
+    launch_full_adaptive(qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v,
+                         part_i, status, st);
     return 1;
 }
 
-// Exemplar parts of the full-dimension pass: enough CTAs for two per SM when the query blocks
-// alone leave SMs idle.
-int full_parts(int Q, int ntiles) {
-    const int nqb = ceil_div(Q, kBQ);
-    return std::max(1, std::min(ntiles, (2 * 152) / std::max(nqb, 1)));
+void launch_search_rows(const float *rows, int da, const int *list, const unsigned int *count, int Q, int Dp,
+                        float *qtiles, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
+                        int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
+                        cudaStream_t st) {
+    const size_t smem = sizeof(FullSmem);
+    set_smem_attr(reinterpret_cast<const void *>(k_search_full), (int)smem);
+    count_launches(1);
+    k_gather_rows<<<152 * 4, 256, 0, st>>>(rows, da, list, count, Q, Dp, qtiles);
+    ProfScope ps(kProfSearchTopk, st, 2);
+    launch_full_adaptive(qtiles, list, count, Q, Dp, etiles, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v, part_i,
+                         status, st);
+}
+
+size_t full_part_capacity(int Q) {
+    return std::min<size_t>((size_t)std::max(Q, 1) * kMaxAdaptiveParts, (size_t)kAdaptiveItems * kBQ) * kTopK;
 }
 
 void launch_exemplar_full(const float *Z, int We, int C, int w, int ex, int N, const float *mu,

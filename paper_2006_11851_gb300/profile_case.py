@@ -5,6 +5,7 @@ or (--pyramid) whole coarse-to-fine syntheses with a search mode per level.
     python -m paper_2006_11851_gb300.profile_case --pyramid --modes exact,f16,f16 --steps 2
     python -m paper_2006_11851_gb300.profile_case --big 4096 --steps 3 [--hist 32]
     python -m paper_2006_11851_gb300.profile_case --rgbs --modes exact,f16,f16 --steps 2
+    python -m paper_2006_11851_gb300.profile_case --level 2 --mode proposal --steps 3
 
 --big H projects (d = 64) and averages (M-step) one H x H output against the finest level's
 index (256x256 exemplar, w = 8), so that the working set is far above the L2 cache: a uniform
@@ -12,6 +13,9 @@ random image and uniform random matches with weights in [0.5, 1.5).
 
 --rgbs runs the RGBS method of section 3 coarse to fine on the same workload (scale map of the
 synthetic exemplar's geometry, slant 60 degrees, tilt 0; scale-guided initialisation).
+
+--mode proposal first trains the level's proposal as the benchmark does, on a smaller budget
+(4 training seeds, 500,000 pairs, 4 epochs, 1024 clusters), then times its searches.
 
 Levels follow the 3-level workload (256x256 exemplar, shrink 4; windows 32/16/8; outputs
 128/256/512, d = 64).  The output image is a seeded random-patch initialisation.  Prints the
@@ -59,6 +63,10 @@ def main() -> int:
     for _ in range(2 - args.level):
         z = pts.downsample2(z)
     idx = pts.ExemplarIndex(z.contiguous(), w, d=args.d)
+    if args.mode == "proposal":
+        from paper_2006_11851_gb300.proposal import train_job_proposal
+        train_job_proposal(idx, z.contiguous(), Ho, w, [1000 + t for t in range(4)], n_pairs=500_000, epochs=4,
+                           n_clusters=1024)
     X = torch.from_numpy(P.random_patch_init(z.cpu().numpy(), Ho, Ho, w, 0)).to(dev)
     for s in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -391,9 +391,10 @@ def test_converge_reproduces_exemplar_in_one_step(c1):
 
 
 def test_exact_bound_components_change_the_route_not_the_result():
-    """The exact search's PCA bound with the index's first d components (the default) or its
-    d_fast: both routes return the certified nearest windows of Eq. 4, bit for bit the same, and
-    the larger bound certifies at least as many queries from the 32 best bounds."""
+    """The exact search's PCA bound with the index's first d components (the default, followed by
+    the d_fast bound on the queries it leaves uncertified), with its d_fast components alone, or
+    with the first d alone: every route returns the certified nearest windows of Eq. 4, bit for bit the same, and the
+    larger bound certifies at least as many queries from the 32 best bounds."""
     Z = P.synthetic_exemplar(0, 128, 4.0)
     idx = pts.ExemplarIndex(_t(Z), 8, d=32)
     X = _t(P.random_patch_init(Z, 256, 256, 8, 3))
@@ -406,6 +407,19 @@ def test_exact_bound_components_change_the_route_not_the_result():
     st_f = idx.search_stats()
     assert torch.equal(nn_f, nn_d) and torch.equal(d2_f, d2_d)
     assert st_f["certified"] >= st_d["certified"], (st_f, st_d)
+    # the default route runs the second bound (d_fast components) on the first bound's
+    # uncertified queries before the full-dimension pass
+    assert st_d["second_queries"] == st_d["range_queries"] > 0, st_d
+    assert st_d["full_queries"] == st_d["range_queries"] - st_d["second_certified"], st_d
+    assert st_d["full_queries"] < st_d["range_queries"], st_d
+    # the first d components alone: no second bound, every uncertified query takes the full pass
+    idx.set_exact_bound(2)
+    assert idx.info["exact_dims"] == 32
+    nn_2, d2_2 = pts.nn_search(idx, X, 2, "exact")
+    st_2 = idx.search_stats()
+    assert torch.equal(nn_2, nn_d) and torch.equal(d2_2, d2_d)
+    assert st_2["second_queries"] == 0 and st_2["full_queries"] == st_2["range_queries"], st_2
+    assert st_2["certified"] == st_d["certified"], (st_2, st_d)
     Q = idx.num_queries(256, 256, 2)
     sub = P.sample_indices(13, Q, 256)
     Xh = X.cpu().numpy()
