@@ -88,13 +88,38 @@ typedef enum {
  *   PTS_KMTREE        the paper's own search (section 2.2): greedy descent of a
  *                     k = 4 hierarchical k-means tree over the PCA coordinates
  *                     (pts_build_kmeans_tree) to a leaf, whose windows are
- *                     re-ranked in exact FP32.  Approximate. */
+ *                     re-ranked in exact FP32.  Approximate.
+ *   PTS_EXACT_TC      the nearest windows of PTS_EXACT_F32 through the tensor
+ *                     cores: full-dimension scores ||u_n||^2 - 2 u_q . u_n from
+ *                     an FP16 GEMM of 2^12 u (FP32 accumulate) over all D
+ *                     components, the 32 best re-ranked in FP32 and certified
+ *                     with tau_q = ((2^-9 + (D + 2) 2^-22)(1 + 2^-10) +
+ *                     8 sqrt(D) 2^-24)(||u_q||^2 + max_n ||u_n||^2): the FP16
+ *                     rounding of both operands and an FP32 accumulation
+ *                     allowed 2^-22 relative error per addition, bounded in
+ *                     the worst case, plus the FP32 model of PTS_EXACT_F32.
+ *                     Uncertified queries (and queries with a value |x - mu|
+ *                     >= 16, past the FP16 range) take PTS_EXACT_F32's
+ *                     full-dimension pass.  The results are those of
+ *                     PTS_EXACT_F32.  For levels whose PCA keeps too little
+ *                     variance for a useful PCA bound (the coarse levels).
+ *                     The scores of all pairs go through device memory, so the
+ *                     mode runs PTS_EXACT_F32 instead when they would take
+ *                     more than 256 MB (Q times N rounded up to 256, 4 bytes
+ *                     each), where moving them costs more than the FP32
+ *                     route's bounds save.  The index builds its FP16 tiles
+ *                     (2 D bytes per window) on the first such search.  The
+ *                     mode also runs PTS_EXACT_F32 when an exemplar value lies
+ *                     past the FP16 range or max_n ||u_n||^2 < D 2^-21 (a nearly
+ *                     constant exemplar, where FP16 underflow would not be
+ *                     covered). */
 typedef enum {
     PTS_EXACT_F32 = 0,
     PTS_F16_RERANK = 1,
     PTS_FP8_RERANK = 2,
     PTS_PROPOSAL = 3,
-    PTS_KMTREE = 4
+    PTS_KMTREE = 4,
+    PTS_EXACT_TC = 5
 } pts_mode;
 
 typedef struct pts_index_s *pts_index; /* opaque, owned by the library */

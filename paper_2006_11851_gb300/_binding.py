@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-MODES = {"exact": 0, "f16": 1, "fp8": 2, "proposal": 3, "kmtree": 4}  # pts_mode
+MODES = {"exact": 0, "f16": 1, "fp8": 2, "proposal": 3, "kmtree": 4, "exact_tc": 5}  # pts_mode
 
 _LOCK = threading.Lock()
 _LIB = None

@@ -136,7 +136,7 @@ pts_status pts_batch_create(const pts_job *jobs, int n_jobs, int iters, float r,
         unsigned long long g = 0;
         if (!index_generation(j.index, &g))
             return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a job's index is not a live index");
-        if (j.mode < PTS_EXACT_F32 || j.mode > PTS_KMTREE)
+        if (j.mode < PTS_EXACT_F32 || j.mode > PTS_EXACT_TC)
             return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: unknown job mode");
         if (j.mode == PTS_PROPOSAL && !j.index->prop.ready)
             return set_error(PTS_ERR_INVALID_ARG, "pts_batch_create: a proposal job's index has no trained proposal");

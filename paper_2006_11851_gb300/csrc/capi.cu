@@ -261,6 +261,83 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     return PTS_OK;
 }
 
+// The nearest windows of Eq. 4 through the full-dimension FP16 GEMM (search_tcf.cu): scores of
+// every pair, the 32 best per query re-ranked in FP32 and certified with the GEMM's rounding
+// slack; the rest takes the FP32 full pass of exact mode.  Slack per unit of ||u_q||^2 + max_n
+// ||u_n||^2 (scores -2 (2^-12 a_hat . 2^-12 b_hat) + ||u_n||^2 with a_hat = fl16(2^12 u_q)):
+//   FP16 operands: |a_hat b_hat - a b| <= (2^-10 + 2^-22) |a b| for normal values, and the terms
+//     of values below the FP16 normal range add at most D 2^-31 in all, which is below
+//     2^-10 max_n ||u_n||^2 when that is >= D 2^-21 (checked): 2^-9 + 2^-22 in all, after
+//     sum |a_i b_i| <= (||u_q||^2 + ||u_n||^2) / 2 and the factor 2 of the score;
+//   FP32 accumulation of D products, each addition within 2^-22 of its partial sum (a
+//     truncating accumulator included): D 2^-22 (1 + 2^-10);
+//   the epilogue's FMA and the bound's addition of ||u_q||^2: 2^-21;
+//   the FP32 norms and the FP32 re-rank: exact mode's model, kTauC sqrt(D) 2^-24.
+float tcf_slack(int D) {
+    return (float)((std::ldexp(1.0, -9) + (D + 2) * std::ldexp(1.0, -22)) * (1.0 + std::ldexp(1.0, -10)) +
+                   kTauC * std::sqrt((double)D) * std::ldexp(1.0, -24));
+}
+
+// FP16 full-dimension tiles of the exemplar, built on the first PTS_EXACT_TC search (one
+// synchronisation); tcf_state -1 when they cannot be used
+pts_status ensure_tcf_tiles(pts_index idx, cudaStream_t st) {
+    if (idx->tcf_state != 0) return PTS_OK;
+    if (!((double)idx->unorm2_max >= idx->D * std::ldexp(1.0, -21))) {
+        idx->tcf_state = -1;
+        return PTS_OK;
+    }
+    const size_t n = (size_t)tcf_tiles(idx->N) * 256 * tcf_k(idx->D);
+    PTS_TRY(idx->efull16.ensure(n, "FP16 full-dimension tiles"));
+    DevBuf<int> over;
+    PTS_TRY(over.ensure(1, "range flag"));
+    PTS_CUDA_TRY(cudaMemsetAsync(over.ptr, 0, sizeof(int), st));
+    launch_pack_exemplar_full16(idx->exemplar.ptr, idx->We, idx->C, idx->w, idx->nx, idx->N, idx->mu.ptr,
+                                idx->efull16.ptr, over.ptr, st);
+    int h = 0;
+    PTS_CUDA_TRY(cudaMemcpyAsync(&h, over.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PTS_CUDA_TRY(cudaStreamSynchronize(st));
+    idx->tcf_state = h ? -1 : 1;
+    if (h) idx->efull16.release();
+    return PTS_OK;
+}
+
+// PTS_EXACT_TC runs the FP32 route when its scores (Q x 256-window tiles x 4 bytes) would pass
+// this size: their write and read then cost more than the FP32 route's bounds save.
+constexpr size_t kTcfScoreBytes = 256u << 20;
+
+pts_status search_exact_tc(pts_index idx, const float *X, int Ho, int Wo, int stride, int Q, int32_t *nn_out,
+                           float *d2_out, cudaStream_t st) {
+    const int npad = tcf_tiles(idx->N) * 256;
+    if ((size_t)Q * npad * sizeof(float) > kTcfScoreBytes)
+        return search_exact(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st);
+    PTS_TRY(ensure_tcf_tiles(idx, st));
+    if (idx->tcf_state != 1) return search_exact(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st);
+    Workspace &ws = idx->ws;
+    const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
+    const int qx = (Wo - idx->w) / stride + 1;
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
+    unsigned int *fail_count = ws.counters.ptr + 0;
+    unsigned int *fail2_count = ws.counters.ptr + 1;
+    unsigned int *brute_count = ws.counters.ptr + 2;
+    idx->last_cascade = 0;
+    PTS_TRY(ws.qtile16.ensure((size_t)tcf_query_blocks(Q) * 128 * tcf_k(idx->D), "FP16 query tiles"));
+    PTS_TRY(ws.tau_tc.ensure((size_t)std::max(Q, 1), "FP16 slack"));
+    PTS_TRY(ws.full_pdist.ensure((size_t)std::max(Q, 1) * npad, "full-dimension scores"));
+    PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
+    // ||u_q||^2 and exact mode's slack (the FP32 pass uses it), then the GEMM's slack from it
+    launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, 0, idx->da, 0, nullptr,
+                   ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
+    launch_scale_tau(ws.tau.ptr, tcf_slack(idx->D) / tau_scale, Q, ws.tau_tc.ptr, st);
+    launch_search_tcf(X, Wo, idx->C, idx->w, stride, qx, 0, Q, Q, idx->mu.ptr, idx->efull16.ptr, idx->N,
+                      idx->enorm.ptr, ws.qnorm.ptr, ws.qtile16.ptr, ws.full_pdist.ptr, ws.tau_tc.ptr, ws.cand_idx.ptr,
+                      ws.cand_lb.ptr, idx->status.ptr, st);
+    launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau_tc.ptr, 1, nn_out, d2_out,
+                  ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
+    PTS_TRY(exact_on_list(idx, ra, ws.fail_list.ptr, fail_count, ws.fail2_list.ptr, fail2_count, brute_count, nn_out,
+                          d2_out, st));
+    return PTS_OK;
+}
+
 pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int stride, int mode,
                           int32_t *nn_out, float *d2_out, cudaStream_t st) {
     PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "nn_search"));
@@ -306,6 +383,9 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
         }
         case PTS_PROPOSAL:
             PTS_TRY(search_proposal(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
+            break;
+        case PTS_EXACT_TC:
+            PTS_TRY(search_exact_tc(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
             break;
         case PTS_KMTREE:
             PTS_TRY(search_kmtree(idx, X, Ho, Wo, stride, Q, nn_out, d2_out, st));
@@ -828,13 +908,16 @@ pts_status pts_index_search_stats(pts_index idx, pts_search_stats *stats, void *
     cudaStream_t st = as_stream(stream);
     *stats = idx->last;
     stats->fallback_queries = 0;
-    if (idx->ws.counters.ptr && (idx->last_mode == PTS_EXACT_F32 || idx->last_mode == PTS_PROPOSAL)) {
+    const bool exact_route = idx->last_mode == PTS_EXACT_F32 || idx->last_mode == PTS_EXACT_TC;
+    if (idx->ws.counters.ptr && (exact_route || idx->last_mode == PTS_PROPOSAL)) {
         unsigned int c[4] = {0, 0, 0, 0};
         PTS_CUDA_TRY(cudaMemcpyAsync(c, idx->ws.counters.ptr, sizeof(c), cudaMemcpyDeviceToHost, st));
         PTS_CUDA_TRY(cudaStreamSynchronize(st));
         stats->second_certified = 0;
         stats->second_queries = 0;
-        if (idx->last_mode == PTS_EXACT_F32) {
+        if (exact_route) {
+            // PTS_EXACT_TC: c[0] queries the FP16 GEMM's candidates left uncertified (the first
+            // bound's role), c[1] of those still uncertified after the full pass
             stats->range_queries = c[0];
             stats->certified = stats->queries - c[0];
             // with the second bound: c[1] of the c[0] queries reached the full pass, c[3] of those

@@ -12,7 +12,7 @@ namespace pts {
 namespace {
 
 const char *kNames[kProfClasses] = {"search_topk", "search_full", "rerank", "project", "m_step",
-                                    "search_tc", "mlp", "probe", "brute", "irls", "search_tc_list"};
+                                    "search_tc", "mlp", "probe", "brute", "irls", "search_tc_list", "search_tcf"};
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_enabled{0};
 std::mutex g_mu;

@@ -246,12 +246,29 @@ __global__ void __launch_bounds__(256) k_window_norms(const float *__restrict__ 
     const int row = C * w;
     const long qy = win / qx_n, qx = win - qy * qx_n;
     const float *src = img + (qy * stride * (long)W + qx * stride) * C;
-    float un = 0.0f;
-    for (int dy = 0; dy < w; ++dy)
+    const size_t pitch = (size_t)W * C;
+    // four window rows at a time into four partial sums, so that their loads are in flight together
+    float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f, u3 = 0.0f;
+    int dy = 0;
+    for (; dy + 4 <= w; dy += 4)
         for (int e = lane; e < row; e += 32) {
-            const float a = __ldg(src + (size_t)dy * W * C + e) - __ldg(mu + dy * row + e);
-            un = fmaf(a, a, un);
+            const float *s0 = src + dy * pitch + e;
+            const float *m0 = mu + dy * row + e;
+            const float a0 = __ldg(s0) - __ldg(m0);
+            const float a1 = __ldg(s0 + pitch) - __ldg(m0 + row);
+            const float a2 = __ldg(s0 + 2 * pitch) - __ldg(m0 + 2 * row);
+            const float a3 = __ldg(s0 + 3 * pitch) - __ldg(m0 + 3 * row);
+            u0 = fmaf(a0, a0, u0);
+            u1 = fmaf(a1, a1, u1);
+            u2 = fmaf(a2, a2, u2);
+            u3 = fmaf(a3, a3, u3);
         }
+    for (; dy < w; ++dy)
+        for (int e = lane; e < row; e += 32) {
+            const float a = __ldg(src + dy * pitch + e) - __ldg(mu + dy * row + e);
+            u0 = fmaf(a, a, u0);
+        }
+    float un = (u0 + u1) + (u2 + u3);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) un += __shfl_xor_sync(0xffffffffu, un, s);
     if (lane == 0) {

@@ -120,6 +120,8 @@ struct Workspace {
     DevBuf<__half> qtile;      // [ceil(Q/128)][128 x Ktc] FP16 query operand tiles
     DevBuf<uint8_t> qtile8;    // [ceil(Q/128)][128 x Kf8] FP8 query operand tiles
     DevBuf<float> qscale;      // [Q] FP8 query row scales
+    DevBuf<__half> qtile16;    // [ceil(Q/128)][128 x tcf_k(D)] FP16 full-dimension query tiles
+    DevBuf<float> tau_tc;      // [Q] slack of the full-dimension FP16 scores
     DevBuf<float> proj_part;   // per-slice partial sums of a split projection
     DevBuf<unsigned char> kept;  // kept groups of the tensor-core search, one record per (row, half)
     DevBuf<float> part_v;      // [Q][parts][32] per-part candidate lists of the tensor-core search
@@ -222,6 +224,8 @@ struct pts_index_s {
     pts::DevBuf<float> f8scale;   // [d_fast + 1] per-dimension scales of the FP8 tiles
     int kf8 = 0;                  // K of the FP8 search
     int ktc = 0;                  // K of the tensor-core search
+    pts::DevBuf<__half> efull16;  // [tcf_tiles(N)][256 x tcf_k(D)] FP16 full-dimension tiles (PTS_EXACT_TC)
+    int tcf_state = 0;            // those tiles: 0 not built, 1 ready, -1 unusable (a value out of FP16 range)
     pts::DevBuf<float> umax;      // [1]
     pts::DevBuf<int> status;      // [1] device status word
     pts::Workspace ws;
@@ -375,9 +379,30 @@ void launch_brute_fallback(const RerankArgs &a, const int *fail_list,
 void launch_resolve(const int *fail_list, const unsigned int *fail_count,
                     const unsigned long long *best64, int Q, int *nn_out, float *d2_out,
                     cudaStream_t st);
+// search_tcf.cu: the full-dimension FP16 tensor-core search (PTS_EXACT_TC)
+int tcf_k(int D);             // K of its operands: D rounded up to 64
+int tcf_tiles(int N);         // 256-window tiles
+int tcf_query_blocks(int Q);  // 128-query blocks
+// s (z - mu) of every exemplar window in FP16 tiles; *over is set when a value leaves the FP16 range
+void launch_pack_exemplar_full16(const float *Z, int We, int C, int w, int nx, int N, const float *mu,
+                                 __half *etile, int *over, cudaStream_t st);
+// tau_out = tau * ratio for Q queries
+void launch_scale_tau(const float *tau, float ratio, int Q, float *tau_out, cudaStream_t st);
+// Queries q0 .. q0 + nq - 1: packs them (FP16, into qtile), scores them against every window
+// (score[nq][tcf_tiles(N) * 256]) and writes their 32 best to the candidate lists; a query with a
+// value past the FP16 range gets tau_out[q] = +inf.
+void launch_search_tcf(const float *X, int Wo, int C, int w, int stride, int qx, int q0, int nq, int Q,
+                       const float *mu, const __half *etile, int N, const float *enorm, const float *qnorm,
+                       __half *qtile, float *score, float *tau_out, int *cand_idx, float *cand_lb, int *status,
+                       cudaStream_t st);
+// the 32 smallest of the sum over splits of score[split][f][n] (n < N) for queries q0 + f, f < nq
+// (search_f32.cu)
+void launch_full_select_range(const float *score, int nsplit, int npad, int N, int q0, int nq, int Q,
+                              const float *qnorm, int *cand_idx, float *cand_lb, int *status, cudaStream_t st);
 // profile.cu: launch counting and event timing of kernel classes
 enum ProfClass { kProfSearchTopk = 0, kProfSearchFull, kProfRerank, kProfProject, kProfMStep,
-                 kProfSearchTc, kProfMlp, kProfProbe, kProfBrute, kProfIrls, kProfSearchTcList, kProfClasses };
+                 kProfSearchTc, kProfMlp, kProfProbe, kProfBrute, kProfIrls, kProfSearchTcList, kProfSearchTcf,
+                 kProfClasses };
 void count_launches(int n);
 // Raises a kernel's dynamic shared-memory limit on the current device (once per kernel, device
 // and size; thread-safe).

@@ -542,26 +542,67 @@ __global__ void k_merge_fail_parts(const float *__restrict__ part_v, const int *
 // window added in split order, then the 32 smallest (p, n) kept by sorting each 32 windows and
 // merging them into the running list (skipped when none beats its 32nd).  Padding windows
 // (n >= N, p = +inf) never enter.
-__global__ void __launch_bounds__(256) k_full_select(const float *__restrict__ pdist, int nsplit, int npad, int N,
-                                                     const int *__restrict__ fail_list,
-                                                     const unsigned int *__restrict__ fail_count, int Q,
-                                                     const float *__restrict__ qnorm, int *__restrict__ cand_idx,
-                                                     float *__restrict__ cand_lb, int *__restrict__ status) {
-    const int lane = threadIdx.x & 31;
-    const long f = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (f >= (long)*fail_count) return;
+constexpr int kSelCap = 128;  // keys a warp collects at or below its threshold (full_select_row)
+
+// The 32 smallest (score, window) pairs of one query, one warp: score n = sum over the splits of
+// row[split * split_stride + n] for n < N (NaN and +inf skipped), sorted; to the candidate lists
+// with ||u_q||^2 added.  Lane l reads windows l, l + 32, ... (npad is a multiple of 32).  A first
+// pass keeps each lane's two smallest scores; the 32nd smallest T of those 64 values bounds the
+// 32nd smallest score from above (at least 32 scores are <= T), so a second pass collects the
+// scores <= T into buf (kSelCap keys of this warp) and sorts only those.  When more than kSelCap
+// scores lie at or below T (many ties), the warp sorts every score chunk by chunk instead.  The
+// result is the same either way: the 32 smallest (score, window) keys.
+__device__ __forceinline__ void full_select_row(const float *__restrict__ row, size_t split_stride, int nsplit,
+                                                int npad, int N, int q, int Q, const float *__restrict__ qnorm,
+                                                int *__restrict__ cand_idx, float *__restrict__ cand_lb,
+                                                int *__restrict__ status, int lane, unsigned long long *buf) {
     const unsigned long long kNone = pack_key(INFINITY, INT_MAX);
-    unsigned long long best = kNone;
-    for (int n0 = 0; n0 < npad; n0 += 32) {
-        const int n = n0 + lane;
+    auto score = [&](int n) -> float {
         float v = 0.0f;
-        for (int sp = 0; sp < nsplit; ++sp) v += pdist[((size_t)sp * Q + f) * npad + n];
-        unsigned long long k = (n < N && v < INFINITY) ? pack_key(v, n) : kNone;
-        if (!__any_sync(kFull, k < __shfl_sync(kFull, best, 31))) continue;
-        warp_sort_keys(k, lane);
-        warp_merge_keys(best, k, lane);
+        for (int sp = 0; sp < nsplit; ++sp) v += row[(size_t)sp * split_stride + n];
+        return (n < N && v < INFINITY) ? v : INFINITY;  // NaN fails the test too
+    };
+    float m1 = INFINITY, m2 = INFINITY;
+    for (int n0 = 0; n0 < npad; n0 += 32) {
+        const float v = score(n0 + lane);
+        m2 = fminf(m2, fmaxf(m1, v));
+        m1 = fminf(m1, v);
     }
-    const int q = fail_list[f];
+    unsigned long long a = pack_key(m1, lane), b = pack_key(m2, 32 + lane);
+    warp_sort_keys(a, lane);
+    warp_sort_keys(b, lane);
+    warp_merge_keys(a, b, lane);
+    const float T = key_value(__shfl_sync(kFull, a, 31));
+    int cnt = 0;  // warp-uniform
+    for (int n0 = 0; n0 < npad; n0 += 32) {
+        const float v = score(n0 + lane);
+        const bool take = v < INFINITY && v <= T;
+        const unsigned m = __ballot_sync(kFull, take);
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (take && pos < kSelCap) buf[pos] = pack_key(v, n0 + lane);
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    unsigned long long best = kNone;
+    if (cnt <= kSelCap) {
+        for (int g = 0; g < cnt; g += 32) {
+            unsigned long long k = g + lane < cnt ? buf[g + lane] : kNone;
+            warp_sort_keys(k, lane);
+            if (g == 0)
+                best = k;
+            else
+                warp_merge_keys(best, k, lane);
+        }
+    } else {
+        for (int n0 = 0; n0 < npad; n0 += 32) {
+            const float v = score(n0 + lane);
+            unsigned long long k = v < INFINITY ? pack_key(v, n0 + lane) : kNone;
+            if (!__any_sync(kFull, k < __shfl_sync(kFull, best, 31))) continue;
+            warp_sort_keys(k, lane);
+            warp_merge_keys(best, k, lane);
+        }
+    }
+    __syncwarp();
     const int i = key_index(best);
     const bool real = i != INT_MAX;
     if (q >= 0 && q < Q) {
@@ -570,6 +611,34 @@ __global__ void __launch_bounds__(256) k_full_select(const float *__restrict__ p
     } else if (lane == 0) {
         atomicOr(status, kDevErrBounds);
     }
+}
+
+// listed queries: row f of pdist [split][Q][npad] belongs to query fail_list[f]
+__global__ void __launch_bounds__(256) k_full_select(const float *__restrict__ pdist, int nsplit, int npad, int N,
+                                                     const int *__restrict__ fail_list,
+                                                     const unsigned int *__restrict__ fail_count, int Q,
+                                                     const float *__restrict__ qnorm, int *__restrict__ cand_idx,
+                                                     float *__restrict__ cand_lb, int *__restrict__ status) {
+    __shared__ unsigned long long buf[256 / 32][kSelCap];
+    const int lane = threadIdx.x & 31;
+    const long f = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= (long)*fail_count) return;
+    full_select_row(pdist + (size_t)f * npad, (size_t)Q * npad, nsplit, npad, N, fail_list[f], Q, qnorm, cand_idx,
+                    cand_lb, status, lane, buf[threadIdx.x >> 5]);
+}
+
+// a range of queries: row f of score [nsplit][nq][npad] belongs to query q0 + f
+__global__ void __launch_bounds__(256) k_full_select_range(const float *__restrict__ score, int nsplit, int npad,
+                                                           int N, int q0, int nq, int Q,
+                                                           const float *__restrict__ qnorm,
+                                                           int *__restrict__ cand_idx, float *__restrict__ cand_lb,
+                                                           int *__restrict__ status) {
+    __shared__ unsigned long long buf[256 / 32][kSelCap];
+    const int lane = threadIdx.x & 31;
+    const long f = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (f >= nq) return;
+    full_select_row(score + (size_t)f * npad, (size_t)nq * npad, nsplit, npad, N, q0 + (int)f, Q, qnorm, cand_idx,
+                    cand_lb, status, lane, buf[threadIdx.x >> 5]);
 }
 
 // u_q = x_q - mu of the failing queries, tiled [F/64][Dp][64], zero rows k >= D
@@ -742,6 +811,14 @@ void launch_search_rows(const float *rows, int da, const int *list, const unsign
     ProfScope ps(kProfSearchTopk, st, 2);
     launch_full_adaptive(qtiles, list, count, Q, Dp, etiles, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v, part_i,
                          status, st);
+}
+
+void launch_full_select_range(const float *score, int nsplit, int npad, int N, int q0, int nq, int Q,
+                              const float *qnorm, int *cand_idx, float *cand_lb, int *status, cudaStream_t st) {
+    if (nq <= 0) return;
+    count_launches(1);
+    k_full_select_range<<<ceil_div((long)nq * 32, 256), 256, 0, st>>>(score, nsplit, npad, N, q0, nq, Q, qnorm,
+                                                                      cand_idx, cand_lb, status);
 }
 
 size_t full_part_capacity(int Q) {

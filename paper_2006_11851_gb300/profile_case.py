@@ -6,6 +6,7 @@ or (--pyramid) whole coarse-to-fine syntheses with a search mode per level.
     python -m paper_2006_11851_gb300.profile_case --big 4096 --steps 3 [--hist 32]
     python -m paper_2006_11851_gb300.profile_case --rgbs --modes exact,f16,f16 --steps 2
     python -m paper_2006_11851_gb300.profile_case --level 2 --mode proposal --steps 3
+    python -m paper_2006_11851_gb300.profile_case --level 0 --mode exact_tc --steps 3
 
 --big H projects (d = 64) and averages (M-step) one H x H output against the finest level's
 index (256x256 exemplar, w = 8), so that the working set is far above the L2 cache: a uniform
