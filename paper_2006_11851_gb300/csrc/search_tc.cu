@@ -70,6 +70,7 @@ struct TcSmem {
     uint32_t tmem_base;
     int abort_flag;
 };
+static_assert(kAcc == 2, "the MMA issuer alternates two accumulators");
 static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "tensor-core search tile set exceeds shared memory");
 
 // Sorted register list of the kept groups: value gv[k] (group minimum) and gs[k] = group << 4 |
@@ -99,15 +100,21 @@ __device__ __forceinline__ int group_insert(GroupList &L, float x, int group) {
     return slot;
 }
 
+// minimum of three (a NaN operand is ignored, as by fminf)
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // 64 columns (8 groups) of a tile for the calling thread's query.
 __device__ __forceinline__ void scan64(const float (&v)[64], int group0, GroupList &L, uint4 *pay_row) {
     float m[8];
 #pragma unroll
     for (int g = 0; g < 8; ++g)
-        m[g] = fminf(fminf(fminf(v[8 * g], v[8 * g + 1]), fminf(v[8 * g + 2], v[8 * g + 3])),
-                     fminf(fminf(v[8 * g + 4], v[8 * g + 5]), fminf(v[8 * g + 6], v[8 * g + 7])));
-    const float mm =
-        fminf(fminf(fminf(m[0], m[1]), fminf(m[2], m[3])), fminf(fminf(m[4], m[5]), fminf(m[6], m[7])));
+        m[g] = min3f(min3f(v[8 * g], v[8 * g + 1], v[8 * g + 2]), min3f(v[8 * g + 3], v[8 * g + 4], v[8 * g + 5]),
+                     fminf(v[8 * g + 6], v[8 * g + 7]));
+    const float mm = min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), fminf(m[6], m[7]));
     if (!__any_sync(kFull, mm < L.gv[kKeep - 1])) return;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
@@ -282,26 +289,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t lbo_q = (uint32_t)(kQM / 8) * 128u, lbo_e = (uint32_t)(kTN / 8) * 128u;
             const uint32_t qaddr = smem_u32(sm.q);
             bool ok = mbar_wait_or_abort(&sm.q_full, 0, status, abort_flag);
+            // descriptors built once: the address field (bits 0-13, 16-byte units) of every later
+            // operand is the base's plus an offset, all inside shared memory
+            const uint64_t adesc0 = smem_desc(qaddr, lbo_q, 128u);
+            const uint64_t bdesc0 = smem_desc(smem_u32(sm.e), lbo_e, 128u);
+            const uint64_t a_step = (2u * lbo_q) >> 4, b_step = (2u * lbo_e) >> 4, b_stage = stage_bytes >> 4;
+            const int nks = K * EB / 32;
+            int s = 0;
+            uint32_t full_par = 0;
             for (int i = 0; i < nt && ok; ++i) {
-                const int s = i % nstages, a = i % kAcc;
+                const int a = i & 1;  // kAcc == 2
                 if (i >= kAcc &&
-                    !mbar_wait_or_abort(&sm.acc_empty[a], (uint32_t)(((i / kAcc) - 1) & 1), status, abort_flag))
+                    !mbar_wait_or_abort(&sm.acc_empty[a], (uint32_t)(((i >> 1) - 1) & 1), status, abort_flag))
                     break;
-                if (!mbar_wait_or_abort(&sm.full[s], (uint32_t)((i / nstages) & 1), status, abort_flag)) break;
+                if (!mbar_wait_or_abort(&sm.full[s], full_par, status, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t eaddr = smem_u32(sm.e + (size_t)s * stage_bytes);
+                const uint64_t bd = bdesc0 + (uint64_t)s * b_stage;
                 const uint32_t dcol = tmem + (uint32_t)(a * kTN);
                 // one instruction per 32 bytes of K (16 FP16 or 32 FP8 values): two core-matrix columns
-                for (int ks = 0; ks < K * EB / 32; ++ks) {
-                    const uint64_t adesc = smem_desc(qaddr + ks * 2u * lbo_q, lbo_q, 128u);
-                    const uint64_t bdesc = smem_desc(eaddr + ks * 2u * lbo_e, lbo_e, 128u);
+                for (int ks = 0; ks < nks; ++ks) {
                     if constexpr (EB == 2)
-                        mma_bf16(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
+                        mma_bf16(dcol, adesc0 + ks * a_step, bd + ks * b_step, idesc, ks > 0 ? 1u : 0u);
                     else
-                        mma_f8(dcol, adesc, bdesc, idesc, ks > 0 ? 1u : 0u);
+                        mma_f8(dcol, adesc0 + ks * a_step, bd + ks * b_step, idesc, ks > 0 ? 1u : 0u);
                 }
                 mma_commit(&sm.empty[s]);
                 mma_commit(&sm.acc_full[a]);
+                if (++s == nstages) {
+                    s = 0;
+                    full_par ^= 1u;
+                }
             }
             // all MMAs issued by this thread have completed once `done` fires
             mma_commit(&sm.done);
@@ -335,16 +352,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int group0 = (t_begin + i) * (kTN / kG) + half * (kTN / kG / 2);
             const int col0 = group0 * kG;
-            float v[64];
-            tmem_ld64(lane_addr + (uint32_t)(a * kTN), v);
-            if constexpr (EB == 1) fp8_finish(v, tq, enorm, col0, N);
-            scan64(v, group0, L, pay_row);
-            tmem_ld64(lane_addr + (uint32_t)(a * kTN + 64), v);
+            // both 64-column halves in one load: one wait, and the accumulator is released
+            // before the scan
+            float v[128];
+            tmem_ld128(lane_addr + (uint32_t)(a * kTN), v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.acc_empty[a]);
-            if constexpr (EB == 1) fp8_finish(v, tq, enorm, col0 + 64, N);
-            scan64(v, group0 + 8, L, pay_row);
+            float (&v0)[64] = *reinterpret_cast<float (*)[64]>(&v[0]);
+            float (&v1)[64] = *reinterpret_cast<float (*)[64]>(&v[64]);
+            if constexpr (EB == 1) fp8_finish(v0, tq, enorm, col0, N);
+            scan64(v0, group0, L, pay_row);
+            if constexpr (EB == 1) fp8_finish(v1, tq, enorm, col0 + 64, N);
+            scan64(v1, group0 + 8, L, pay_row);
         }
         // hand the kept groups to k_select (one record per output row and column half)
         if (!*abort_flag && q >= 0) {
