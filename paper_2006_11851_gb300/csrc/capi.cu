@@ -155,7 +155,8 @@ pts_status search_proposal(pts_index idx, const float *X, int Ho, int Wo, int st
                      pr.etc_ivf.ptr, tc_tiles(idx->N), idx->N, pr.members.ptr, ib, ws.cand_idx.ptr, ws.cand_lb.ptr,
                      idx->status.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C,
+                  idx->exemplar4.ptr};
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out, d2_out,
                   ws.fail_list.ptr, ws.counters.ptr + 3, ws.best64.ptr, idx->status.ptr, st);
@@ -185,7 +186,8 @@ pts_status search_kmtree(pts_index idx, const float *X, int Ho, int Wo, int stri
     PTS_TRY(tr.leaf_of_query.ensure((size_t)std::max(Q, 1), "tree leaves of the queries"));
     launch_tree_search(tr, ws.qcoord.ptr, idx->da, Q, ws.cand_idx.ptr, ws.cand_lb.ptr, tr.leaf_of_query.ptr, st);
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C,
+                  idx->exemplar4.ptr};
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
                   ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
     return PTS_OK;
@@ -203,7 +205,8 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
     const double bvar = fast ? idx->var_fast : idx->var_retained;
     const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C,
+                  idx->exemplar4.ptr};
     unsigned int *fail_count = ws.counters.ptr + 0;
     unsigned int *fail2_count = ws.counters.ptr + 1;
     unsigned int *brute_count = ws.counters.ptr + 2;
@@ -315,7 +318,8 @@ pts_status search_exact_tc(pts_index idx, const float *X, int Ho, int Wo, int st
     Workspace &ws = idx->ws;
     const float tau_scale = kTauC * sqrtf((float)idx->D) * 5.9604645e-8f;
     const int qx = (Wo - idx->w) / stride + 1;
-    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C};
+    RerankArgs ra{X, Ho, Wo, stride, qx, idx->exemplar.ptr, idx->We, idx->w, idx->nx, idx->N, Q, idx->C,
+                  idx->exemplar4.ptr};
     unsigned int *fail_count = ws.counters.ptr + 0;
     unsigned int *fail2_count = ws.counters.ptr + 1;
     unsigned int *brute_count = ws.counters.ptr + 2;
@@ -375,7 +379,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
                              ws.part_i.ptr, idx->status.ptr, st, nullptr, nullptr, 0, nullptr, nullptr, idx->N,
                              ws.kept.ptr);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
-                          idx->nx, idx->N, Q, idx->C};
+                          idx->nx, idx->N, Q, idx->C, idx->exemplar4.ptr};
             // candidates in ascending bound order; stop where bound - slack exceeds the best
             launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 2, nn_out, d2_out,
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
@@ -411,7 +415,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
                              ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st,
                              nullptr, nullptr, 1, ws.qscale.ptr, idx->enorm.ptr, idx->N, ws.kept.ptr);
             RerankArgs ra{X, Ho, Wo, stride, (Wo - idx->w) / stride + 1, idx->exemplar.ptr, idx->We, idx->w,
-                          idx->nx, idx->N, Q, idx->C};
+                          idx->nx, idx->N, Q, idx->C, idx->exemplar4.ptr};
             launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 0, nn_out, d2_out,
                           ws.fail_list.ptr, ws.counters.ptr, ws.best64.ptr, idx->status.ptr, st);
             break;

@@ -366,6 +366,7 @@ struct RerankArgs {
     int We, w, ex, N;
     int Q;
     int C;  // channels per pixel of both images (3: RGB, 4: RGB + scale)
+    const float4 *Z4;  // the exemplar as one (r, g, b, scale or 0) float4 per pixel
 };
 // qlist/qcount == NULL: all Q queries; else the listed ones (count on the device)
 void launch_list_all(int *list, unsigned int *count, int Q, cudaStream_t st);

@@ -16,7 +16,10 @@
 //
 // Distances are sums of squared FP32 differences read straight from the two
 // images (a window row is C w contiguous floats in HWC layout, C channels), reduced across
-// the warp by a fixed butterfly, so the result is deterministic.
+// the warp by a fixed butterfly, so the result is deterministic.  Windows of 8, 16 and 32
+// pixels go through k_rerank_px, which reads the exemplar's RGBA copy (one 16-byte load per
+// pixel); its per-lane order of terms differs from k_rerank's, so the last bits of a distance
+// depend on the window width's kernel, never on the mode or the run.
 #include <algorithm>
 
 #include "pts_internal.cuh"
@@ -204,6 +207,109 @@ __global__ void __launch_bounds__(256) k_rerank_w(RerankArgs a, const int *__res
     }
 }
 
+// k_rerank for windows of W x W pixels (W * W a multiple of 32) with the exemplar read as one
+// 16-byte (r, g, b, s-or-0) load per pixel: lane l holds query pixels l, l + 32, ..., and sums
+// its pixels' channel terms in that order before the butterfly, so each candidate costs a lane
+// W * W / 32 vector loads.  P candidates are evaluated together; those beyond the first of a
+// group that k_rerank would have skipped have distances above the best so far and change
+// nothing.  The distances are deterministic FP32 sums (a different order from k_rerank's).
+template <int W, int CH, int P>
+__global__ void __launch_bounds__(256) k_rerank_px(RerankArgs a, const int *__restrict__ qlist,
+                                                   const unsigned int *__restrict__ qcount,
+                                                   const int *__restrict__ cand_idx,
+                                                   const float *__restrict__ cand_lb,
+                                                   const float *__restrict__ tau, int certify,
+                                                   int *__restrict__ nn_out, float *__restrict__ d2_out,
+                                                   int *__restrict__ fail_list,
+                                                   unsigned int *__restrict__ fail_count,
+                                                   unsigned long long *__restrict__ best64,
+                                                   int *__restrict__ status) {
+    static_assert((W * W) % 32 == 0 && (CH == 3 || CH == 4), "pixel-parallel re-rank shape");
+    constexpr int PX = W * W / 32;
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int q = wid;
+    if (qlist) {
+        if (wid >= (int)*qcount) return;
+        q = qlist[wid];
+    }
+    if (q < 0 || q >= a.Q) return;
+    const int y0 = (q / a.qx) * a.stride, x0 = (q % a.qx) * a.stride;
+    float xq[PX][CH];
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        const int p = lane + 32 * j, dy = p / W, dx = p % W;
+        const float *src = a.X + ((size_t)(y0 + dy) * a.Wo + x0 + dx) * CH;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) xq[j][c] = __ldg(src + c);
+    }
+    const int my_idx = cand_idx[(size_t)q * kTopK + lane];
+    const float my_lb = cand_lb[(size_t)q * kTopK + lane];
+    const float tq = certify ? tau[q] : 0.0f;
+    float best = INFINITY;
+    int best_n = -1;
+    for (int i = 0; i < kTopK; i += P) {
+        int n[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) n[c] = __shfl_sync(kFull, my_idx, i + c);
+        const float lb0 = __shfl_sync(kFull, my_lb, i);
+        if (n[0] < 0) break;  // fewer than 32 windows exist
+        if (certify && lb0 - tq > best) break;  // bounds are ascending
+        const float4 *z[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            if (n[c] >= a.N) {
+                if (lane == 0) atomicOr(status, kDevErrBounds);
+                n[c] = -1;
+            }
+            const int m = n[c] < 0 ? 0 : n[c], ey = m / a.ex;
+            z[c] = a.Z4 + (size_t)ey * a.We + (m - ey * a.ex);
+        }
+        float s[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) s[c] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PX; ++j) {
+            const int p = lane + 32 * j, off = (p / W) * a.We + p % W;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const float4 e = __ldg(z[c] + off);
+                float t = xq[j][0] - e.x;
+                s[c] = fmaf(t, t, s[c]);
+                t = xq[j][1] - e.y;
+                s[c] = fmaf(t, t, s[c]);
+                t = xq[j][2] - e.z;
+                s[c] = fmaf(t, t, s[c]);
+                if constexpr (CH == 4) {
+                    t = xq[j][CH - 1] - e.w;
+                    s[c] = fmaf(t, t, s[c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            const float d = warp_sum(s[c]);
+            if (n[c] >= 0 && (d < best || (d == best && n[c] < best_n))) {
+                best = d;
+                best_n = n[c];
+            }
+        }
+    }
+    const int last_idx = __shfl_sync(kFull, my_idx, kTopK - 1);
+    const float last_lb = __shfl_sync(kFull, my_lb, kTopK - 1);
+    const bool done = certify != 1 || last_idx < 0 || best <= last_lb - tq;
+    if (lane == 0) {
+        if (done) {
+            nn_out[q] = best_n;
+            d2_out[q] = best;
+        } else {
+            const unsigned int slot = atomicAdd(fail_count, 1u);
+            fail_list[slot] = q;
+            best64[q] = pack_dist_idx(best, best_n);
+        }
+    }
+}
+
 // One CTA per listed query; each thread scores whole windows.
 __global__ void __launch_bounds__(256) k_brute(RerankArgs a, const int *__restrict__ fail_list,
                                                const unsigned int *__restrict__ fail_count,
@@ -287,12 +393,12 @@ void launch_rerank(const RerankArgs &a, const int *qlist, const unsigned int *qc
                         best64, status
     switch (a.C * 64 + a.w) {
         case 3 * 64 + 4: k_rerank_w<4, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 3 * 64 + 8: k_rerank_w<8, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 3 * 64 + 16: k_rerank_w<16, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 3 * 64 + 32: k_rerank_w<32, 3><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 3 * 64 + 8: k_rerank_px<8, 3, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 3 * 64 + 16: k_rerank_px<16, 3, 2><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 3 * 64 + 32: k_rerank_px<32, 3, 2><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
         case 4 * 64 + 4: k_rerank_w<4, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 4 * 64 + 8: k_rerank_w<8, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
-        case 4 * 64 + 16: k_rerank_w<16, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 4 * 64 + 8: k_rerank_px<8, 4, 4><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
+        case 4 * 64 + 16: k_rerank_px<16, 4, 2><<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
         default: k_rerank<<<grid, 256, 0, st>>>(PTS_RERANK_ARGS); break;
     }
 #undef PTS_RERANK_ARGS
