@@ -237,8 +237,8 @@ PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 /
 # ncu capture summarised in profiles/k_search_tc_fine_level_512_f16.md; reported only while the
 # search source file is unchanged (the digest below is of that file with the profiled kernel; any
 # later edit of the file, even of host code, turns the figure off until it is checked again).
-TC_TRAFFIC_BYTES = 32.899e6 + 0.142e6
-TC_TRAFFIC_SHA256 = "6b12a965e026a288a1ba46d825b5243810b45fc9d6e980149759b4b7107215e3"
+TC_TRAFFIC_BYTES = 32.898e6 + 0.178e6
+TC_TRAFFIC_SHA256 = "926b5a9bd646b03e20344fd71ac3a5a296d5f5e344fb2959b951ff7ac67b4570"
 
 
 def _tc_traffic():

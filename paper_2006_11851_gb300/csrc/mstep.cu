@@ -118,8 +118,11 @@ __global__ void k_rgba(const float *__restrict__ Z, long npix, int C, float4 *__
 }
 
 // IRLS weights and energy (Eqs. 5-8).  Fixed grid; each block sums its
-// grid-stride slice in FP64, tree-reduces, and the last block to finish adds
-// the block partials in block order, so the energy is bitwise reproducible.
+// grid-stride slice in FP64, tree-reduces, and the last block to finish loads
+// the block partials and adds them by the same fixed tree, so the energy is
+// bitwise reproducible.
+static_assert(kIrlsGrid <= 256, "the last block loads one partial per thread");
+
 __global__ void __launch_bounds__(256)
     k_irls(const float *__restrict__ d2, int Q, float r, float delta, float *__restrict__ wts,
            double *__restrict__ energy_out, double *__restrict__ partial,
@@ -151,12 +154,18 @@ __global__ void __launch_bounds__(256)
         last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {  // the whole last block: the partials loaded together, then the same fixed tree
         __threadfence();
-        double s = 0.0;
-        for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double *)partial)[b];
-        if (energy_out) *energy_out = s;
-        *ticket = 0u;
+        red[threadIdx.x] = threadIdx.x < gridDim.x ? ((volatile double *)partial)[threadIdx.x] : 0.0;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (energy_out) *energy_out = red[0];
+            *ticket = 0u;
+        }
     }
 }
 
