@@ -359,15 +359,16 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             break;
         case PTS_F16_RERANK: {
             Workspace &ws = idx->ws;
-            launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->da_fast, 0,
-                           ws.qcoord.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
+            // the projection writes the FP16 query tiles itself (no FP32 coordinates in between)
+            PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * kTcQueryRows * idx->ktc, "query operand tiles"));
+            launch_project_tile16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast,
+                                  idx->ktc, ws.qtile.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st,
+                                  &ws.proj_part);
             const int ntc = tc_tiles(idx->N);
             // 0: automatic -- the default split rule, one part plus the tail split of launch_search_tc
             const int auto_parts = tc_parts(Q, ntc);
             const int nparts = idx->tc_parts_override > 0 ? std::min(idx->tc_parts_override, ntc)
                                                           : (auto_parts > 1 ? auto_parts : 0);
-            PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * 128 * idx->ktc, "query operand tiles"));
-            launch_pack_queries(ws.qcoord.ptr, Q, idx->d_fast, idx->da_fast, idx->ktc, ws.qtile.ptr, st);
             // the candidate lists of the previous search on this grid seed the bound
             const bool warm = ws.warm_q == Q && ws.warm_ho == Ho && ws.warm_wo == Wo && ws.warm_stride == stride;
             if (warm)

@@ -15,11 +15,13 @@
 //                      tau[win] = tau_scale * (||u||^2 + max_n ||u_n||^2)
 // layout 1 (exemplar): coord[win/kBN][da][win%kBN] = -2 (y, r, 0, ...)
 //                      (the tiled, pre-scaled form the search streams)
+// layout 2 (queries, FP16 search): (y, r, 1, 1, 1, 0, ...) rounded to FP16 straight into the
+//                      tensor-core query tiles (128 rows x K each, core-matrix layout), and tau
 #include <math.h>
 
 #include <algorithm>
 
-#include "pts_internal.cuh"
+#include "tc_common.cuh"
 
 namespace pts {
 namespace {
@@ -47,6 +49,8 @@ struct ProjOut {
     float *coord, *norm, *tau;
     float tau_scale;
     const float *umax;
+    __half *tile16;  // layout 2: the FP16 query tiles
+    int ktile;       // layout 2: their K
 };
 
 // ||y||^2, r and the output rows of one window, written by one warp (y in shared or global
@@ -60,6 +64,16 @@ __device__ __forceinline__ void write_window(const ProjOut &o, long win, const f
     if (o.layout == 0) {
         float *c = o.coord + win * o.da;
         for (int j = lane; j < o.da; j += 32) c[j] = j < o.d ? yr[j] : (j == o.d ? r : 0.0f);
+        if (lane == 0) o.tau[win] = o.tau_scale * (u2 + *o.umax);
+    } else if (o.layout == 2) {
+        // the values the FP16 search multiplies: coordinates, the residual, then three ones
+        // against the exemplar's norm slots (hi, mid, lo)
+        unsigned char *t = reinterpret_cast<unsigned char *>(o.tile16 + (size_t)(win / kTcQueryRows) * kTcQueryRows * o.ktile);
+        const int rr = (int)(win % kTcQueryRows);
+        for (int j = lane; j < o.ktile; j += 32) {
+            const float v = j < o.d ? yr[j] : (j == o.d ? r : (j <= o.d + 3 ? 1.0f : 0.0f));
+            *reinterpret_cast<__half *>(t + core_offset(rr, j, kTcQueryRows)) = __float2half_rn(v);
+        }
         if (lane == 0) o.tau[win] = o.tau_scale * (u2 + *o.umax);
     } else {
         const long tile = win / kBN, col = win - tile * kBN;
@@ -311,14 +325,14 @@ __global__ void k_norm_max(const float *__restrict__ v, int n, float *__restrict
 
 }  // namespace
 
-void launch_project(const float *img, int H, int W, int C, int w, int stride, const float *mu,
-                    const float *basisT, int d, int da, int layout, float *out_coord,
-                    float *out_norm, float *out_tau, float tau_scale, const float *umax,
-                    cudaStream_t st, DevBuf<float> *scratch) {
+static void launch_project_impl(const float *img, int H, int W, int C, int w, int stride, const float *mu,
+                                const float *basisT, int d, int da, int layout, float *out_coord, float *out_norm,
+                                float *out_tau, float tau_scale, const float *umax, cudaStream_t st,
+                                DevBuf<float> *scratch, __half *tile16, int ktile) {
     const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
     const long Qn = (long)qy_n * qx_n;
     if (Qn <= 0) return;
-    const ProjOut o{d, da, layout, out_coord, out_norm, out_tau, tau_scale, umax};
+    const ProjOut o{d, da, layout, out_coord, out_norm, out_tau, tau_scale, umax, tile16, ktile};
     ProfScope ps(kProfProject, st, 1);
     if (d <= 0) {
         k_window_norms<<<(unsigned)ceil_div(Qn * 32, 256), 256, 0, st>>>(img, W, C, w, stride, qx_n, (int)Qn, mu, o);
@@ -352,6 +366,28 @@ void launch_project(const float *img, int H, int W, int C, int w, int stride, co
         else
             k_project_finish<128><<<(unsigned)ceil_div(Qn, 8), 256, 0, st>>>(part, nsplit, (int)Qn, o);
     }
+}
+
+void launch_project(const float *img, int H, int W, int C, int w, int stride, const float *mu,
+                    const float *basisT, int d, int da, int layout, float *out_coord,
+                    float *out_norm, float *out_tau, float tau_scale, const float *umax,
+                    cudaStream_t st, DevBuf<float> *scratch) {
+    launch_project_impl(img, H, W, C, w, stride, mu, basisT, d, da, layout, out_coord, out_norm, out_tau, tau_scale,
+                        umax, st, scratch, nullptr, 0);
+}
+
+void launch_project_tile16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
+                           const float *basisT, int d, int K, __half *qtile, float *out_norm, float *out_tau,
+                           float tau_scale, const float *umax, cudaStream_t st, DevBuf<float> *scratch) {
+    const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
+    const long Qn = (long)qy_n * qx_n;
+    if (Qn <= 0) return;
+    // rows past the last query of the last tile stay zero (the projection writes only real rows)
+    if (Qn % kTcQueryRows)
+        cudaMemsetAsync(qtile + (size_t)(Qn / kTcQueryRows) * kTcQueryRows * K, 0,
+                        sizeof(__half) * kTcQueryRows * K, st);
+    launch_project_impl(img, H, W, C, w, stride, mu, basisT, d, 0, 2, nullptr, out_norm, out_tau, tau_scale, umax,
+                        st, scratch, qtile, K);
 }
 
 void launch_basis_transpose(const float *basis, int dcount, int D, float *basisT, cudaStream_t st) {

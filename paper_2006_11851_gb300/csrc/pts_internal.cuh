@@ -18,6 +18,7 @@ namespace pts {
 // ---------------------------------------------------------------------------
 constexpr int kBN = 128;   // exemplar windows per tile (32 lanes x 4)
 constexpr int kBQ = 64;    // queries per CTA (8 warps x 8 rows)
+constexpr int kTcQueryRows = 128;  // queries per tensor-core query tile (the FP16 search's M)
 constexpr int kTopK = 32;  // candidates kept per query (one per lane)
 constexpr int kMaxAdaptiveParts = 32;    // exemplar parts of an adaptive full-dimension pass
 constexpr int kAdaptiveItems = 4 * 152;  // its (query block, part) items: two rounds of its grid
@@ -265,6 +266,12 @@ void launch_project(const float *img, int H, int W, int C, int w, int stride, co
                     const float *basisT, int d, int da, int layout, float *out_coord,
                     float *out_norm, float *out_tau, float tau_scale, const float *umax,
                     cudaStream_t st, DevBuf<float> *scratch = nullptr);
+// The FP16 search's query operand straight from the image: each window's d coordinates, its
+// residual and three ones, rounded to FP16, in the tensor-core query tiles (tc_query_blocks(Q) x
+// kTcQueryRows rows of K), rows past the last query zero; ||u||^2 and tau as launch_project.
+void launch_project_tile16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
+                           const float *basisT, int d, int K, __half *qtile, float *out_norm, float *out_tau,
+                           float tau_scale, const float *umax, cudaStream_t st, DevBuf<float> *scratch = nullptr);
 void launch_basis_transpose(const float *basis, int dcount, int D, float *basisT, cudaStream_t st);
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st);
 void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);

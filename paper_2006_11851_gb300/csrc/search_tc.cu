@@ -46,7 +46,7 @@
 namespace pts {
 namespace {
 
-constexpr int kQM = 128;            // queries per CTA (MMA M)
+constexpr int kQM = kTcQueryRows;   // queries per CTA (MMA M)
 constexpr int kTN = 256;            // exemplar windows per tile (MMA N)
 constexpr int kAcc = 2;             // accumulator stages of kTN columns
 constexpr int kEpiWarps = 8;
