@@ -292,6 +292,50 @@ PRECISION_FORM = {
 }
 
 
+def time_proposal_large(pts, P, dev, stream, flush, steps, warmup):
+    """The learned proposal against the FP16 brute-force search it replaces, on a large exemplar:
+    512x512 (shrink 4x), windows 8x8 (N = 255,025), one 512x512 output level, d = 64; the network
+    (1,024 clusters) trained on four exact-mode EM runs (seeds disjoint from the timed one).  Each
+    timed E-step searches one mid-synthesis image (two FP16 EM iterations from a random-patch
+    initialisation) after an L2 flush; energies measured by the certified exact search."""
+    import torch
+    from paper_2006_11851_gb300.proposal import train_job_proposal
+    Z = torch.from_numpy(P.synthetic_exemplar(0, 512, 4.0)).to(dev)
+    idx = pts.ExemplarIndex(Z, 8, d=64)
+    t0 = time.perf_counter()
+    train_job_proposal(idx, Z, 512, 8, [1000 + s for s in range(4)], n_pairs=1_000_000, epochs=6, n_clusters=1024)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    X = torch.from_numpy(P.random_patch_init(Z.cpu().numpy(), 512, 512, 8, 7)).to(dev)
+    pts.synthesize_level(idx, X, 2, mode="f16")
+    Q = idx.num_queries(512, 512, 2)
+    out = {"workload": "exemplar 512x512 (shrink 4x), windows 8x8 (N = 255,025), output 512x512 (Q = 64,009), "
+                       "d = 64, 1,024 clusters trained on 4 exact-mode EM runs, one mid-synthesis image",
+           "N": idx.N, "Q": Q, "proposal_train_s": train_s}
+    _, d2e = pts.nn_search(idx, X, 2, "exact")
+    e_exact = float(d2e.double().sum())
+    for mode in ("f16", "proposal"):
+        for _ in range(warmup):
+            pts.nn_search(idx, X, 2, mode)
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, d2 = pts.nn_search(idx, X, 2, mode)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms += ev0.elapsed_time(ev1)
+        out[mode] = {"value": Q * steps / (ms / 1000.0), "unit": "queries/s", "ms_per_estep": ms / steps,
+                     "matched_energy_vs_exact": float(d2.double().sum()) / e_exact}
+        if mode == "proposal":
+            st = idx.search_stats()
+            out[mode]["fallback_fraction"] = st["fallback_queries"] / max(1, st["queries"])
+    out["proposal_vs_f16"] = out["proposal"]["value"] / out["f16"]["value"]
+    idx.close()
+    return out
+
+
 def time_precision_form(pts, P, L, dev, stream, flush, steps, warmup, bf16_burst, peak_src):
     """queries/s of every search mode on the precision-form workload (one level), the FP16/FP8
     search's tensor roofline, and each mode's final energy (measured by the certified exact
@@ -426,6 +470,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries per level for the CPU baseline")
     ap.add_argument("--d-fast", type=int, default=0, help="PCA dimensions of the tensor-core search (0 = library default)")
     ap.add_argument("--no-robust", action="store_true", help="skip the robust-schedule timing (other_configs)")
+    ap.add_argument("--no-proposal-large", action="store_true",
+                    help="skip the learned proposal against the FP16 brute force on a 512x512 exemplar")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched form: 64 uneven jobs in one CUDA graph (other_configs)")
     ap.add_argument("--no-precision-form", action="store_true",
@@ -700,6 +746,10 @@ def main():
 
     if not args.no_batched:
         other_cfgs["batched"] = time_batched(dev, stream, flush, args.steps, args.warmup)
+
+    if not args.no_proposal_large:
+        other_cfgs["proposal_large_exemplar"] = time_proposal_large(pts, P, dev, stream, flush, args.steps,
+                                                                    args.warmup)
 
     headline = None
     if also == "proposal" or args.mode == "proposal":

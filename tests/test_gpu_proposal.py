@@ -230,3 +230,47 @@ def test_network_gains_over_the_papers_tree(trained):
           f"tree {e_t:.4f}")
     assert rec_p > rec_t + 0.1
     assert e_p < e_t
+
+
+def test_network_gains_over_brute_force_at_scale():
+    """What the trained network buys over the same search without it, the FP16 tensor-core
+    search over every exemplar window, where the exemplar is large: 512x512 (N = 255,025
+    windows of 8x8), one 512x512 output level, 1,024 clusters trained on four exact-mode EM runs.
+    On one mid-synthesis image the proposal's E-step must take less time than the brute-force
+    search, and the windows it returns must keep the matched energy within 1.01x of exact
+    search's.  (On the benchmark's 256x256 exemplar, 62,001 windows, the brute force is the
+    faster of the two: the network, the probe and the fallback cost more than they save.)"""
+    from paper_2006_11851_gb300.proposal import train_job_proposal
+    Z = _t(P.synthetic_exemplar(0, 512, 4.0))
+    ix = pts.ExemplarIndex(Z, 8, d=64)
+    try:
+        train_job_proposal(ix, Z, 512, 8, [1000 + s for s in range(4)], n_pairs=1_000_000, epochs=6,
+                           n_clusters=1024)
+        X = _t(P.random_patch_init(Z.cpu().numpy(), 512, 512, 8, 7))
+        pts.synthesize_level(ix, X, 2, mode="f16")
+
+        def timed(mode, reps=10):
+            pts.nn_search(ix, X, 2, mode)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                nn, d2 = pts.nn_search(ix, X, 2, mode)
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps, d2
+
+        t_f16, d2_f16 = timed("f16")
+        t_prop, d2_prop = timed("proposal")
+        fallback = ix.search_stats()["fallback_queries"] / ix.search_stats()["queries"]
+        _, d2_e = pts.nn_search(ix, X, 2, "exact")
+        e_exact = float(d2_e.double().sum())
+        ratio_prop = float(d2_prop.double().sum()) / e_exact
+        ratio_f16 = float(d2_f16.double().sum()) / e_exact
+        print(f"\nN = {ix.N}: E-step FP16 brute force {t_f16:.3f} ms, proposal {t_prop:.3f} ms "
+              f"({t_f16 / t_prop:.2f}x), fallback {fallback:.3f}; matched energy / exact: "
+              f"proposal {ratio_prop:.5f}, brute force {ratio_f16:.5f}")
+        assert t_prop < t_f16
+        assert ratio_prop <= 1.01
+    finally:
+        ix.close()
