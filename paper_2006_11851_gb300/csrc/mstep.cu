@@ -24,7 +24,7 @@ namespace {
 // excess table (3 x nbins, from the two images' channel counts) built per block in shared memory;
 // every pixel is normalised by its own sum of weights.  Without HIST the patch's four pixels share
 // one sum.
-template <int S, bool HIST>
+template <int S, bool HIST, int SPL = 1>
 __global__ void __launch_bounds__(128)
     k_m_step(const int *__restrict__ nn, const float *__restrict__ wts, const float4 *__restrict__ Z4,
              int We, int ex, int N, int C, int w, int Ho, int Wo, int qy_n, int qx_n,
@@ -36,9 +36,13 @@ __global__ void __launch_bounds__(128)
             hex[i] = (float)fmax(0.0, (double)cx[i] / (double)nx - (double)cz[i] / (double)nz);
         __syncthreads();
     }
-    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    // SPL consecutive threads share a patch, each taking every SPL-th row of its covering windows;
+    // their sums meet in a fixed xor tree, so the result is deterministic
+    const int sub = (int)threadIdx.x % SPL;
+    const int px = (int)((blockIdx.x * blockDim.x + threadIdx.x) / SPL);
     const int py = blockIdx.y;
-    if (px >= Wo / S || py >= Ho / S) return;
+    const bool live = px < Wo / S && py < Ho / S;
+    if (SPL == 1 && !live) return;
     const int ws = w / S;
     const int qy_lo = max(0, py - ws + 1), qy_hi = min(py, qy_n - 1);
     const int qx_lo = max(0, px - ws + 1), qx_hi = min(px, qx_n - 1);
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(128)
             for (int u = 0; u < S; ++u) dpix[t][u] = 0.0f;
     float den = 0.0f;
     bool bad = false;
-    for (int qy = qy_lo; qy <= qy_hi; ++qy) {
+    for (int qy = live ? qy_lo + sub : qy_hi + 1; qy <= qy_hi; qy += SPL) {
         const int oy = (py - qy) * S;
         for (int qx = qx_lo; qx <= qx_hi; ++qx) {
             const int p = qy * qx_n + qx;
@@ -89,6 +93,21 @@ __global__ void __launch_bounds__(128)
         }
     }
     if (bad) atomicOr(status, kDevErrBounds);
+    if constexpr (SPL > 1) {
+#pragma unroll
+        for (int m = SPL / 2; m > 0; m >>= 1) {
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+#pragma unroll
+                for (int u = 0; u < S; ++u) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) num[t][u][c] += __shfl_xor_sync(0xffffffffu, num[t][u][c], m);
+                    if constexpr (HIST) dpix[t][u] += __shfl_xor_sync(0xffffffffu, dpix[t][u], m);
+                }
+            den += __shfl_xor_sync(0xffffffffu, den, m);
+        }
+        if (!live || sub != 0) return;
+    }
 #pragma unroll
     for (int t = 0; t < S; ++t) {
         float *o = out + ((size_t)(py * S + t) * Wo + px * S) * C;
@@ -241,10 +260,23 @@ void launch_m_step(const int *nn, const float *wts, const float4 *Z4, int We, in
             k_m_step<1, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out, status, 0,
                                                        nullptr, 1, nullptr, 1);
             break;
-        case 2:
-            k_m_step<2, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out, status, 0,
-                                                       nullptr, 1, nullptr, 1);
+        case 2: {
+            // wide windows cover a patch many times: 4 or 8 threads share a patch's windows
+            const int ws = w / 2;
+            if (ws >= 16) {
+                const dim3 g8(ceil_div(PX, 128 / 8), PY);
+                k_m_step<2, false, 8><<<g8, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out,
+                                                             status, 0, nullptr, 1, nullptr, 1);
+            } else if (ws >= 8) {
+                const dim3 g4(ceil_div(PX, 128 / 4), PY);
+                k_m_step<2, false, 4><<<g4, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out,
+                                                             status, 0, nullptr, 1, nullptr, 1);
+            } else {
+                k_m_step<2, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out,
+                                                           status, 0, nullptr, 1, nullptr, 1);
+            }
             break;
+        }
         case 4:
             k_m_step<4, false><<<grid, block, 0, st>>>(nn, wts, Z4, We, ex, N, C, w, Ho, Wo, qy_n, qx_n, out, status, 0,
                                                        nullptr, 1, nullptr, 1);
