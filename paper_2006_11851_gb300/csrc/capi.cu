@@ -329,13 +329,12 @@ pts_status search_exact_tc(pts_index idx, const float *X, int Ho, int Wo, int st
     PTS_TRY(ws.tau_tc.ensure((size_t)std::max(Q, 1), "FP16 slack"));
     PTS_TRY(ws.full_pdist.ensure((size_t)std::max(Q, 1) * npad, "full-dimension scores"));
     PTS_CUDA_TRY(cudaMemsetAsync(ws.counters.ptr, 0, 4 * sizeof(unsigned int), st));
-    // ||u_q||^2 and exact mode's slack (the FP32 pass uses it), then the GEMM's slack from it
-    launch_project(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, 0, idx->da, 0, nullptr,
-                   ws.qnorm.ptr, ws.tau.ptr, tau_scale, idx->umax.ptr, st);
-    launch_scale_tau(ws.tau.ptr, tcf_slack(idx->D) / tau_scale, Q, ws.tau_tc.ptr, st);
-    launch_search_tcf(X, Wo, idx->C, idx->w, stride, qx, 0, Q, Q, idx->mu.ptr, idx->efull16.ptr, idx->N,
-                      idx->enorm.ptr, ws.qnorm.ptr, ws.qtile16.ptr, ws.full_pdist.ptr, ws.tau_tc.ptr, ws.cand_idx.ptr,
-                      ws.cand_lb.ptr, idx->status.ptr, st);
+    // the FP16 query tiles, ||u_q||^2, exact mode's slack (the FP32 pass uses it) and the GEMM's
+    // slack in one pass over the windows, then the GEMM and the 32 best scores of every query
+    launch_pack_queries_full16(X, Wo, idx->C, idx->w, stride, qx, Q, idx->mu.ptr, ws.qtile16.ptr, ws.qnorm.ptr,
+                               ws.tau.ptr, tau_scale, ws.tau_tc.ptr, tcf_slack(idx->D), idx->umax.ptr, st);
+    launch_gemm_tcf(ws.qtile16.ptr, Q, idx->C, idx->w, idx->efull16.ptr, idx->N, idx->enorm.ptr, ws.qnorm.ptr,
+                    ws.full_pdist.ptr, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st);
     launch_rerank(ra, nullptr, nullptr, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau_tc.ptr, 1, nn_out, d2_out,
                   ws.fail_list.ptr, fail_count, ws.best64.ptr, idx->status.ptr, st);
     PTS_TRY(exact_on_list(idx, ra, ws.fail_list.ptr, fail_count, ws.fail2_list.ptr, fail2_count, brute_count, nn_out,

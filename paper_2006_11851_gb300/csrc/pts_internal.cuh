@@ -394,15 +394,14 @@ int tcf_query_blocks(int Q);  // 128-query blocks
 // s (z - mu) of every exemplar window in FP16 tiles; *over is set when a value leaves the FP16 range
 void launch_pack_exemplar_full16(const float *Z, int We, int C, int w, int nx, int N, const float *mu,
                                  __half *etile, int *over, cudaStream_t st);
-// tau_out = tau * ratio for Q queries
-void launch_scale_tau(const float *tau, float ratio, int Q, float *tau_out, cudaStream_t st);
-// Queries q0 .. q0 + nq - 1: packs them (FP16, into qtile), scores them against every window
-// (score[nq][tcf_tiles(N) * 256]) and writes their 32 best to the candidate lists; a query with a
-// value past the FP16 range gets tau_out[q] = +inf.
-void launch_search_tcf(const float *X, int Wo, int C, int w, int stride, int qx, int q0, int nq, int Q,
-                       const float *mu, const __half *etile, int N, const float *enorm, const float *qnorm,
-                       __half *qtile, float *score, float *tau_out, int *cand_idx, float *cand_lb, int *status,
-                       cudaStream_t st);
+// Every query window (all Q of the grid) packed for the full-dimension GEMM, with ||u_q||^2, exact
+// mode's slack tau (tau_scale per unit) and the GEMM's tau_tc (tc_scale per unit, +inf for a query
+// with a value past the FP16 range) from the same pass; then the GEMM and the top-32 of every query.
+void launch_pack_queries_full16(const float *X, int Wo, int C, int w, int stride, int qx, int Q, const float *mu,
+                                __half *qtile, float *qnorm, float *tau, float tau_scale, float *tau_tc, float tc_scale,
+                                const float *umax, cudaStream_t st);
+void launch_gemm_tcf(const __half *qtile, int Q, int C, int w, const __half *etile, int N, const float *enorm,
+                     const float *qnorm, float *score, int *cand_idx, float *cand_lb, int *status, cudaStream_t st);
 // the 32 smallest of the sum over splits of score[split][f][n] (n < N) for queries q0 + f, f < nq
 // (search_f32.cu)
 void launch_full_select_range(const float *score, int nsplit, int npad, int N, int q0, int nq, int Q,

@@ -546,7 +546,8 @@ constexpr int kSelCap = 128;  // keys a warp collects at or below its threshold 
 
 // The 32 smallest (score, window) pairs of one query, one warp: score n = sum over the splits of
 // row[split * split_stride + n] for n < N (NaN and +inf skipped), sorted; to the candidate lists
-// with ||u_q||^2 added.  Lane l reads windows l, l + 32, ... (npad is a multiple of 32).  A first
+// with ||u_q||^2 added.  Lane l reads windows 4l .. 4l + 3, 4l + 128 ... (npad is a multiple of
+// 128 and the rows 16-byte aligned).  A first
 // pass keeps each lane's two smallest scores; the 32nd smallest T of those 64 values bounds the
 // 32nd smallest score from above (at least 32 scores are <= T), so a second pass collects the
 // scores <= T into buf (kSelCap keys of this warp) and sorts only those.  When more than kSelCap
@@ -562,11 +563,31 @@ __device__ __forceinline__ void full_select_row(const float *__restrict__ row, s
         for (int sp = 0; sp < nsplit; ++sp) v += row[(size_t)sp * split_stride + n];
         return (n < N && v < INFINITY) ? v : INFINITY;  // NaN fails the test too
     };
+    // four consecutive scores per lane and load (npad is a multiple of 128, rows 16-byte aligned)
+    auto score4 = [&](int n) -> float4 {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const float4 t = *reinterpret_cast<const float4 *>(row + (size_t)sp * split_stride + n);
+            v.x += t.x;
+            v.y += t.y;
+            v.z += t.z;
+            v.w += t.w;
+        }
+        v.x = (n < N && v.x < INFINITY) ? v.x : INFINITY;
+        v.y = (n + 1 < N && v.y < INFINITY) ? v.y : INFINITY;
+        v.z = (n + 2 < N && v.z < INFINITY) ? v.z : INFINITY;
+        v.w = (n + 3 < N && v.w < INFINITY) ? v.w : INFINITY;
+        return v;
+    };
     float m1 = INFINITY, m2 = INFINITY;
-    for (int n0 = 0; n0 < npad; n0 += 32) {
-        const float v = score(n0 + lane);
-        m2 = fminf(m2, fmaxf(m1, v));
-        m1 = fminf(m1, v);
+    for (int n0 = 0; n0 < npad; n0 += 128) {
+        const float4 v4 = score4(n0 + 4 * lane);
+        const float vs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            m2 = fminf(m2, fmaxf(m1, vs[c]));
+            m1 = fminf(m1, vs[c]);
+        }
     }
     unsigned long long a = pack_key(m1, lane), b = pack_key(m2, 32 + lane);
     warp_sort_keys(a, lane);
@@ -574,13 +595,17 @@ __device__ __forceinline__ void full_select_row(const float *__restrict__ row, s
     warp_merge_keys(a, b, lane);
     const float T = key_value(__shfl_sync(kFull, a, 31));
     int cnt = 0;  // warp-uniform
-    for (int n0 = 0; n0 < npad; n0 += 32) {
-        const float v = score(n0 + lane);
-        const bool take = v < INFINITY && v <= T;
-        const unsigned m = __ballot_sync(kFull, take);
-        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-        if (take && pos < kSelCap) buf[pos] = pack_key(v, n0 + lane);
-        cnt += __popc(m);
+    for (int n0 = 0; n0 < npad; n0 += 128) {
+        const float4 v4 = score4(n0 + 4 * lane);
+        const float vs[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const bool take = vs[c] < INFINITY && vs[c] <= T;
+            const unsigned m = __ballot_sync(kFull, take);
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (take && pos < kSelCap) buf[pos] = pack_key(vs[c], n0 + 4 * lane + c);
+            cnt += __popc(m);
+        }
     }
     __syncwarp();
     unsigned long long best = kNone;

@@ -149,39 +149,34 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
 }
 
-// One thread per (row, 8-column group) of a block of R rows: s (x - mu) of 8 consecutive
-// components of row r's window, rounded to FP16, as one 16-byte row of a core matrix.  Rows past
-// `rows` and components past D are zero.  Row r is window g = win0 + r of the grid, at (y0, x0) =
-// (g / nxw * step, g % nxw * step) of an image of width Wi with C channels.
-// A value past the FP16 range saturates; the row's slack (tau_inf, for queries) becomes +inf, so
-// that its candidates are never certified from its scores, and *over (for exemplar windows) is
-// set, so that the host does not use the tiles.
-template <int R>
-__global__ void k_pack_full16(const float *__restrict__ img, int Wi, int C, int w, int step, int nxw, int win0,
-                              int rows, int K, const float *__restrict__ mu, __half *__restrict__ out, long nthreads,
-                              float *__restrict__ tau_inf, int *__restrict__ over) {
+// The exemplar's FP16 tiles: one thread per (window, 8-column group) of a 256-window tile,
+// s (z - mu) of 8 consecutive components of the window rounded to FP16 as one 16-byte row of a
+// core matrix; windows past N and components past D are zero.  Window n sits at (n / nx, n % nx)
+// of the exemplar (We wide, C channels).  A value past the FP16 range sets *over, and the host
+// then does not use the tiles.
+__global__ void k_pack_exemplar_full16(const float *__restrict__ Z, int We, int C, int w, int nx, int N, int K,
+                                       const float *__restrict__ mu, __half *__restrict__ out, long nthreads,
+                                       int *__restrict__ over) {
     const int D = C * w * w, row = C * w;
     const int kg = K / 8;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nthreads; i += (long)gridDim.x * blockDim.x) {
-        const long blk = i / ((long)R * kg);
-        const int rem = (int)(i - blk * R * kg);
-        const int k8 = rem / R, r = rem - k8 * R;  // r fastest: consecutive threads, consecutive 16 bytes
-        const long win = blk * R + r;
+        const long blk = i / ((long)kFN * kg);
+        const int rem = (int)(i - blk * kFN * kg);
+        const int k8 = rem / kFN, r = rem - k8 * kFN;  // r fastest: consecutive threads, consecutive 16 bytes
+        const long n = blk * kFN + r;
         __align__(16) __half h[8];
-        if (win < rows) {
-            const long g = win0 + win;  // window of the whole grid
-            const int y0 = (int)(g / nxw) * step, x0 = (int)(g % nxw) * step;
+        if (n < N) {
+            const int y0 = (int)(n / nx), x0 = (int)(n % nx);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int k = k8 * 8 + j;
                 float u = 0.0f;
                 if (k < D) {
                     const int dy = k / row, e = k - dy * row;
-                    u = (img[((size_t)(y0 + dy) * Wi + x0) * C + e] - mu[k]) * kFScale;
+                    u = (Z[((size_t)(y0 + dy) * We + x0) * C + e] - mu[k]) * kFScale;
                 }
                 if (!(fabsf(u) <= kFHalfMax)) {  // out of range (or NaN)
-                    if (tau_inf) tau_inf[win] = INFINITY;
-                    if (over) atomicOr(over, 1);
+                    atomicOr(over, 1);
                     u = u > 0.0f ? kFHalfMax : -kFHalfMax;
                 }
                 h[j] = __float2half_rn(u);
@@ -190,14 +185,62 @@ __global__ void k_pack_full16(const float *__restrict__ img, int Wi, int C, int 
 #pragma unroll
             for (int j = 0; j < 8; ++j) h[j] = __float2half_rn(0.0f);
         }
-        unsigned char *base = reinterpret_cast<unsigned char *>(out) + (size_t)blk * R * K * 2;
-        *reinterpret_cast<uint4 *>(base + core_offset(r, k8 * 8, R)) = *reinterpret_cast<const uint4 *>(h);
+        unsigned char *base = reinterpret_cast<unsigned char *>(out) + (size_t)blk * kFN * K * 2;
+        *reinterpret_cast<uint4 *>(base + core_offset(r, k8 * 8, kFN)) = *reinterpret_cast<const uint4 *>(h);
     }
 }
 
-__global__ void k_scale_tau(const float *__restrict__ tau, float ratio, int Q, float *__restrict__ out) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) out[q] = tau[q] * ratio;
+// One warp per query window: s (x - mu) of its D components rounded to FP16 into the query tile
+// (lane l takes the 8-component groups l, l + 32, ...: one 16-byte core-matrix row each), and in
+// the same pass ||x - mu||^2 in FP32, exact mode's slack tau and the GEMM's slack tau_tc (+inf
+// when a value leaves the FP16 range), both per unit of ||u_q||^2 + max_n ||u_n||^2.
+__global__ void __launch_bounds__(256) k_pack_queries_full16(const float *__restrict__ X, int Wo, int C, int w,
+                                                             int stride, int qx, int Q, const float *__restrict__ mu,
+                                                             int K, __half *__restrict__ qtile,
+                                                             float *__restrict__ qnorm, float *__restrict__ tau,
+                                                             float tau_scale, float *__restrict__ tau_tc,
+                                                             float tc_scale, const float *__restrict__ umax) {
+    const int lane = threadIdx.x & 31;
+    const int q = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
+    if (q >= Q) return;
+    const int D = C * w * w, row = C * w;
+    const int y0 = (q / qx) * stride, x0 = (q % qx) * stride;
+    const float *src = X + ((size_t)y0 * Wo + x0) * C;
+    unsigned char *tile = reinterpret_cast<unsigned char *>(qtile + (size_t)(q / kFQ) * kFQ * K);
+    const int r = q % kFQ;
+    float un = 0.0f;
+    bool over = false;
+    for (int g = lane; g < K / 8; g += 32) {
+        __align__(16) __half h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = g * 8 + j;
+            float u = 0.0f;
+            if (k < D) {
+                const int dy = k / row, e = k - dy * row;
+                u = __ldg(src + (size_t)dy * Wo * C + e) - __ldg(mu + k);
+                un = fmaf(u, u, un);
+                u *= kFScale;
+            }
+            if (!(fabsf(u) <= kFHalfMax)) {  // out of range (or NaN)
+                over = true;
+                u = u > 0.0f ? kFHalfMax : -kFHalfMax;
+            }
+            h[j] = __float2half_rn(u);
+        }
+        *reinterpret_cast<uint4 *>(tile + core_offset(r, g * 8, kFQ)) = *reinterpret_cast<const uint4 *>(h);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) un += __shfl_xor_sync(kFullMask, un, o);
+    over = __any_sync(kFullMask, over);
+    if (lane == 0) {
+        const float m = un + *umax;
+        qnorm[q] = un;
+        tau[q] = tau_scale * m;
+        tau_tc[q] = over ? INFINITY : tc_scale * m;
+    }
 }
+
 
 }  // namespace
 
@@ -210,35 +253,36 @@ void launch_pack_exemplar_full16(const float *Z, int We, int C, int w, int nx, i
     const int K = tcf_k(C * w * w);
     const long n = (long)tcf_tiles(N) * kFN * (K / 8);
     count_launches(1);
-    k_pack_full16<kFN><<<(int)std::min<long>(ceil_div(n, 256), 152L * 16), 256, 0, st>>>(Z, We, C, w, 1, nx, 0, N,
-                                                                                       K, mu, etile, n, nullptr, over);
+    k_pack_exemplar_full16<<<(int)std::min<long>(ceil_div(n, 256), 152L * 16), 256, 0, st>>>(Z, We, C, w, nx, N, K, mu,
+                                                                                           etile, n, over);
 }
 
-void launch_scale_tau(const float *tau, float ratio, int Q, float *tau_out, cudaStream_t st) {
+
+void launch_pack_queries_full16(const float *X, int Wo, int C, int w, int stride, int qx, int Q, const float *mu,
+                                __half *qtile, float *qnorm, float *tau, float tau_scale, float *tau_tc, float tc_scale,
+                                const float *umax, cudaStream_t st) {
     if (Q <= 0) return;
+    const int K = tcf_k(C * w * w);
+    // the last tile's rows past the last query stay zero
+    if (Q % kFQ) cudaMemsetAsync(qtile + (size_t)(Q / kFQ) * kFQ * K, 0, sizeof(__half) * kFQ * K, st);
     count_launches(1);
-    k_scale_tau<<<std::max(1, std::min(152 * 4, ceil_div(Q, 256))), 256, 0, st>>>(tau, ratio, Q, tau_out);
+    k_pack_queries_full16<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(X, Wo, C, w, stride, qx, Q, mu, K, qtile, qnorm,
+                                                                       tau, tau_scale, tau_tc, tc_scale, umax);
 }
 
-void launch_search_tcf(const float *X, int Wo, int C, int w, int stride, int qx, int q0, int nq, int Q,
-                       const float *mu, const __half *etile, int N, const float *enorm, const float *qnorm,
-                       __half *qtile, float *score, float *tau_out, int *cand_idx, float *cand_lb, int *status,
-                       cudaStream_t st) {
-    if (nq <= 0) return;
+void launch_gemm_tcf(const __half *qtile, int Q, int C, int w, const __half *etile, int N, const float *enorm,
+                     const float *qnorm, float *score, int *cand_idx, float *cand_lb, int *status, cudaStream_t st) {
+    if (Q <= 0) return;
     const int K = tcf_k(C * w * w);
-    const int nqb = tcf_query_blocks(nq), nt = tcf_tiles(N);
-    const long n = (long)nqb * kFQ * (K / 8);
+    const int nqb = tcf_query_blocks(Q), nt = tcf_tiles(N);
     const size_t smem = sizeof(TcfSmem) + 1024;
     set_smem_attr(reinterpret_cast<const void *>(k_search_tcf), (int)smem);
-    count_launches(1);
-    // window f of the chunk is query q0 + f: rows of the query grid start at multiples of qx
-    k_pack_full16<kFQ><<<(int)std::min<long>(ceil_div(n, 256), 152L * 16), 256, 0, st>>>(
-        X, Wo, C, w, stride, qx, q0, nq, K, mu, qtile, n, tau_out + q0, nullptr);
     {
         ProfScope ps(kProfSearchTcf, st, 1);
-        k_search_tcf<<<dim3(nqb, nt), kFThreads, smem, st>>>(qtile, etile, K, nq, N, nt * kFN, enorm, score, status);
+        k_search_tcf<<<dim3(nqb, nt), kFThreads, smem, st>>>(qtile, etile, K, Q, N, nt * kFN, enorm, score, status);
     }
-    launch_full_select_range(score, 1, nt * kFN, N, q0, nq, Q, qnorm, cand_idx, cand_lb, status, st);
+    launch_full_select_range(score, 1, nt * kFN, N, 0, Q, Q, qnorm, cand_idx, cand_lb, status, st);
 }
+
 
 }  // namespace pts
