@@ -21,7 +21,8 @@ constexpr int kBQ = 64;    // queries per CTA (8 warps x 8 rows)
 constexpr int kTcQueryRows = 128;  // queries per tensor-core query tile (the FP16 search's M)
 constexpr int kTopK = 32;  // candidates kept per query (one per lane)
 constexpr int kMaxAdaptiveParts = 32;    // exemplar parts of an adaptive full-dimension pass
-constexpr int kAdaptiveItems = 4 * 152;  // its (query block, part) items: two rounds of its grid
+constexpr int kAdaptiveGrid = 2 * 152;   // its CTAs (two per SM), each taking items in turn
+constexpr int kPartRows = 1 << 17;       // its part records (of 32 candidates) at most
 constexpr int kMaxDA = 68;     // exact search: d <= 64 coordinates + residual, padded to 4
 constexpr int kMaxD = 64;      // PCA dimensions of the exact search
 constexpr int kMaxDPca = 128;  // PCA dimensions an index may keep (fast modes use up to kMaxDFast)

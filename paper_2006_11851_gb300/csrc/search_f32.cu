@@ -294,20 +294,27 @@ __global__ void __launch_bounds__(256) k_merge_pca_parts(const float *__restrict
 constexpr int kKC = 32;     // K rows per chunk
 constexpr int kStages = 4;  // ring depth
 
-// Exemplar parts of an adaptive full pass with nf listed queries: as many parts (at most
-// kMaxAdaptiveParts, each at least 4 tiles) as keep the (query block, part) items within two
-// rounds of the grid, kAdaptiveItems = 2 x 2 x 152.  The pass and its merge take the same value
-// from the same device count.  Items never exceed kAdaptiveItems when there is more than one
-// part, so the part lists need at most kAdaptiveItems * kBQ records of 32 (full_part_capacity).
+// Exemplar parts of an adaptive full pass with nf listed queries: the part count p (at most
+// kMaxAdaptiveParts, parts of at least 4 tiles, nf * p part records at most kPartRows) whose
+// (query block, part) items finish soonest on the fixed grid of kAdaptiveGrid CTAs, counted as
+// rounds of the grid times tiles per part (the smaller p on a tie).  The pass and its merge
+// take the same value from the same device count.
 __device__ __forceinline__ int adaptive_parts(int nf, int ntiles) {
     const int nqb = (nf + kBQ - 1) / kBQ;
     if (nqb <= 0) return 1;
-    int p = kAdaptiveItems / nqb;
-    p = min(p, kMaxAdaptiveParts);
-    p = min(p, ntiles / 4);
-    if (p <= 1) return 1;
-    const int tpp = (ntiles + p - 1) / p;
-    return (ntiles + tpp - 1) / tpp;
+    const int pmax = max(1, min(min(kMaxAdaptiveParts, ntiles / 4), kPartRows / max(nf, 1)));
+    int best = 1;
+    long best_cost = LONG_MAX;
+    for (int p = 1; p <= pmax; ++p) {
+        const int tpp = (ntiles + p - 1) / p;
+        const int np = (ntiles + tpp - 1) / tpp;
+        const long cost = ((long)nqb * np + kAdaptiveGrid - 1) / kAdaptiveGrid * tpp;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = np;
+        }
+    }
+    return best;
 }
 
 struct FullSmem {
@@ -778,11 +785,11 @@ static void launch_full_adaptive(const float *qtiles, const int *list, const uns
                                  int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
                                  cudaStream_t st) {
     if (Q <= 0) return;
-    const int grid = (int)std::min<long>((long)ceil_div((long)Q, kBQ) * kMaxAdaptiveParts, 2L * 152);
+    const int grid = (int)std::min<long>((long)ceil_div((long)Q, kBQ) * kMaxAdaptiveParts, kAdaptiveGrid);
     k_search_full<<<grid, kThreads, sizeof(FullSmem), st>>>(qtiles, list, count, Q, Dp, etiles, enorm, ntiles, 0,
                                                             qnorm, cand_idx, cand_lb, part_v, part_i, status,
                                                             Dp / kKC, nullptr, 1);
-    k_merge_fail_parts<<<ceil_div((long)std::min(Q, kAdaptiveItems * kBQ) * 32, 256), 256, 0, st>>>(
+    k_merge_fail_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(
         part_v, part_i, ntiles, list, count, Q, qnorm, cand_idx, cand_lb, status);
 }
 
@@ -847,7 +854,7 @@ void launch_full_select_range(const float *score, int nsplit, int npad, int N, i
 }
 
 size_t full_part_capacity(int Q) {
-    return std::min<size_t>((size_t)std::max(Q, 1) * kMaxAdaptiveParts, (size_t)kAdaptiveItems * kBQ) * kTopK;
+    return std::min<size_t>((size_t)std::max(Q, 1) * kMaxAdaptiveParts, (size_t)kPartRows) * kTopK;
 }
 
 void launch_exemplar_full(const float *Z, int We, int C, int w, int ex, int N, const float *mu,
