@@ -294,10 +294,13 @@ __global__ void __launch_bounds__(256) k_merge_pca_parts(const float *__restrict
 constexpr int kKC = 32;     // K rows per chunk
 constexpr int kStages = 4;  // ring depth
 
+constexpr int kItemOverheadTiles = 4;
+
 // Exemplar parts of an adaptive full pass with nf listed queries: the part count p (at most
 // kMaxAdaptiveParts, parts of at least 4 tiles, nf * p part records at most kPartRows) whose
 // (query block, part) items finish soonest on the fixed grid of kAdaptiveGrid CTAs, counted as
-// rounds of the grid times tiles per part (the smaller p on a tie).  The pass and its merge
+// rounds of the grid times the tiles of a part plus kItemOverheadTiles for the item's own costs
+// (its query tile, the ring's fill, its records and their merge); the smaller p on a tie.  The pass and its merge
 // take the same value from the same device count.
 __device__ __forceinline__ int adaptive_parts(int nf, int ntiles) {
     const int nqb = (nf + kBQ - 1) / kBQ;
@@ -308,7 +311,7 @@ __device__ __forceinline__ int adaptive_parts(int nf, int ntiles) {
     for (int p = 1; p <= pmax; ++p) {
         const int tpp = (ntiles + p - 1) / p;
         const int np = (ntiles + tpp - 1) / tpp;
-        const long cost = ((long)nqb * np + kAdaptiveGrid - 1) / kAdaptiveGrid * tpp;
+        const long cost = ((long)nqb * np + kAdaptiveGrid - 1) / kAdaptiveGrid * (tpp + kItemOverheadTiles);
         if (cost < best_cost) {
             best_cost = cost;
             best = np;
