@@ -234,7 +234,7 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
             launch_warm_pca(ws.cand_idx.ptr, ws.qcoord.ptr, bda, brows, idx->enorm.ptr, Q, idx->N,
                             ws.pca_thr.ptr, st);
         }
-        launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, bda, bet, idx->enorm.ptr,
+        launch_search_topk(ws.qcoord.ptr, ws.qnorm.ptr, Q, bda, bd + 1, bet, idx->enorm.ptr,
                            idx->ntiles, ws.cand_idx.ptr, ws.cand_lb.ptr, idx->status.ptr, st, pp, ws.part_v.ptr,
                            ws.part_i.ptr, warm ? ws.pca_thr.ptr : nullptr);
         // pass 1: PCA bounds -> top-32 -> exact re-rank, certified or listed
@@ -250,7 +250,8 @@ pts_status search_exact(pts_index idx, const float *X, int Ho, int Wo, int strid
                            &ws.proj_part);
             PTS_TRY(ws.part_v.ensure(full_part_capacity(Q), "part lists"));
             PTS_TRY(ws.part_i.ensure(full_part_capacity(Q), "part lists"));
-            launch_search_rows(ws.qcoord.ptr, idx->da_fast, ws.fail_list.ptr, fail_count, Q, idx->da_fast,
+            launch_search_rows(ws.qcoord.ptr, idx->da_fast, idx->d_fast + 1, ws.fail_list.ptr, fail_count, Q,
+                               idx->da_fast,
                                ws.qfull.ptr, idx->et_fast.ptr, idx->enorm.ptr, idx->ntiles, ws.qnorm.ptr,
                                ws.cand_idx.ptr, ws.cand_lb.ptr, ws.part_v.ptr, ws.part_i.ptr, idx->status.ptr, st);
             launch_rerank(ra, ws.fail_list.ptr, fail_count, ws.cand_idx.ptr, ws.cand_lb.ptr, ws.tau.ptr, 1, nn_out,

@@ -277,16 +277,17 @@ void launch_basis_transpose(const float *basis, int dcount, int D, float *basisT
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st);
 void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
 // search_f32.cu
-void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
+// da: the stride of a search vector; dk <= da: its components that are not zero padding
+void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, int dk, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st, int nparts = 1,
                         float *part_v = nullptr, int *part_i = nullptr,
                         const float *thr_init = nullptr);
-// The listed queries' rows of `rows` (da floats each) searched against tiles [ntiles][Dp][128]
-// with the full pass's GEMM + top-32 (Dp a multiple of 32; qtiles holds [F/64][Dp][64];
-// part_v / part_i hold full_part_capacity(Q) entries).
-void launch_search_rows(const float *rows, int da, const int *list, const unsigned int *count, int Q, int Dp,
-                        float *qtiles, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
+// The listed queries' rows of `rows` (da floats each, the first dk not zero padding) searched
+// against tiles [ntiles][Dp][128] with the full pass's GEMM + top-32 (Dp a multiple of 32; qtiles
+// holds [F/64][Dp][64]; part_v / part_i hold full_part_capacity(Q) entries).
+void launch_search_rows(const float *rows, int da, int dk, const int *list, const unsigned int *count, int Q,
+                        int Dp, float *qtiles, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
                         int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
                         cudaStream_t st);
 int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx, const float *mu,

@@ -55,6 +55,8 @@ struct TopK8 {
     __device__ __forceinline__ void offer(const float (&p)[8][4], int tile_base, int lane) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
+            const float m = fminf(fminf(p[i][0], p[i][1]), fminf(p[i][2], p[i][3]));
+            if (!__any_sync(kFull, m < thr[i])) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 unsigned fl = __ballot_sync(kFull, p[i][j] < thr[i]);
@@ -99,7 +101,7 @@ struct PcaSmem {
 
 template <int DAM>
 __global__ void __launch_bounds__(kThreads, DAM <= kMaxDA ? 2 : 1)
-    k_search_pca(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int da,
+    k_search_pca(const float *__restrict__ qcoord, const float *__restrict__ qnorm, int Q, int da, int dk,
                  const float *__restrict__ et, const float *__restrict__ enorm, int ntiles, int tiles_per_part,
                  int *__restrict__ cand_idx, float *__restrict__ cand_lb, float *__restrict__ part_v,
                  int *__restrict__ part_i, int *__restrict__ status, const float *__restrict__ thr_init) {
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, DAM <= kMaxDA ? 2 : 1)
         }
         const float *eb = &sm.e[buf][0][lane * 4];
 #pragma unroll 4
-        for (int k = 0; k < da; ++k) {
+        for (int k = 0; k < dk; ++k) {
             const float4 a0 = *reinterpret_cast<const float4 *>(&sm.a[k][row0]);
             const float4 a1 = *reinterpret_cast<const float4 *>(&sm.a[k][row0 + 4]);
             const float4 b = *reinterpret_cast<const float4 *>(eb + k * kBN);
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                   const float *__restrict__ enorm, int ntiles, int tiles_per_part,
                   const float *__restrict__ qnorm, int *__restrict__ cand_idx, float *__restrict__ cand_lb,
                   float *__restrict__ part_v, int *__restrict__ part_i, int *__restrict__ status,
-                  int kc_split, float *__restrict__ pdist, int adaptive) {
+                  int kc_split, float *__restrict__ pdist, int adaptive, int kvalid) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FullSmem &sm = *reinterpret_cast<FullSmem *>(smem_raw);
     const int nf = static_cast<int>(*fail_count);
@@ -382,10 +384,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const float *qa = qfull + (size_t)qb * Dp * kBQ;
     TopK8 top;
     top.init();
-    auto issue = [&](long it) {
-        const int s = (int)((g0 + it) % kStages);
-        const long t = it / nchunks;
-        const int c = c0 + (int)(it - t * nchunks);
+    auto issue = [&](int s, int t, int c) {
         mbar_expect_tx(&sm.bar[s], (uint32_t)(kKC * (kBQ + kBN) * 4));
         bulk_g2s(&sm.a[s][0][0], qa + (size_t)c * kKC * kBQ, kKC * kBQ * 4u, &sm.bar[s]);
         bulk_g2s(&sm.e[s][0][0], efull + ((size_t)(t_begin + t) * Dp + (size_t)c * kKC) * kBN, kKC * kBN * 4u,
@@ -400,14 +399,17 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int s = 0; s < kStages; ++s) last_issued[s] = -1;
     if (tid == 0)
         for (long it = 0; it < kStages && it < total; ++it) {
-            issue(it);
+            const int t = (int)(it / nchunks);
+            issue((int)((g0 + it) % kStages), t, c0 + (int)(it - (long)t * nchunks));
             last_issued[(g0 + it) % kStages] = g0 + it;
         }
+    // stage, phase, tile and chunk of the current chunk and of the next one to copy, advanced
+    // one chunk at a time (no division in the loop)
+    int s = (int)(g0 % kStages), t = 0, c = c0;
+    uint32_t par = (uint32_t)((g0 / kStages) & 1);
+    int nx_t = kStages / nchunks, nx_c = c0 + kStages % nchunks;
     float acc[8][4];
     for (long it = 0; it < total; ++it) {
-        const int s = (int)((g0 + it) % kStages);
-        const long t = it / nchunks;
-        const int c = c0 + (int)(it - t * nchunks);
         if (c == c0) {
             const float4 nv = blockIdx.z == 0
                                   ? __ldg(reinterpret_cast<const float4 *>(enorm + (t_begin + t) * kBN + lane * 4))
@@ -420,15 +422,13 @@ __global__ void __launch_bounds__(kThreads, 2)
                 acc[i][3] = nv.w;
             }
         }
-        const uint32_t par = (uint32_t)(((g0 + it) / kStages) & 1);
         const bool ok = mbar_wait_or_abort(&sm.bar[s], par, status, &sm.abort_flag);
         if (!__all_sync(kFull, ok)) {
             sm.abort_flag = 1;
             break;
         }
         const float *eb = &sm.e[s][0][lane * 4];
-#pragma unroll 8
-        for (int k = 0; k < kKC; ++k) {
+        auto step = [&](int k) {
             const float4 a0 = *reinterpret_cast<const float4 *>(&sm.a[s][k][row0]);
             const float4 a1 = *reinterpret_cast<const float4 *>(&sm.a[s][k][row0 + 4]);
             const float4 b = *reinterpret_cast<const float4 *>(eb + k * kBN);
@@ -438,6 +438,16 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        };
+        // the rows past the vector's kvalid components are zero on both sides and are skipped
+        // (adding 0 x 0 leaves every sum as it is)
+        const int klen = min(kKC, kvalid - c * kKC);
+        if (klen == kKC) {
+#pragma unroll 8
+            for (int k = 0; k < kKC; ++k) step(k);
+        } else {
+#pragma unroll 4
+            for (int k = 0; k < klen; ++k) step(k);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.empty[s]);  // this warp's last read of stage s is done
@@ -458,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (warp == 0 && it + kStages < total) {
             bool refilled = false;
             if (lane == 0 && mbar_wait_or_abort(&sm.empty[s], par, status, &sm.abort_flag)) {
-                issue(it + kStages);
+                issue(s, nx_t, nx_c);
                 last_issued[s] = g0 + it + kStages;
                 refilled = true;
             }
@@ -466,6 +476,18 @@ __global__ void __launch_bounds__(kThreads, 2)
                 sm.abort_flag = 1;
                 break;
             }
+            if (++nx_c == c1) {
+                nx_c = c0;
+                ++nx_t;
+            }
+        }
+        if (++c == c1) {
+            c = c0;
+            ++t;
+        }
+        if (++s == kStages) {
+            s = 0;
+            par ^= 1u;
         }
     }
     __syncthreads();
@@ -755,7 +777,7 @@ int pca_parts(int Q, int ntiles) {
     return p;
 }
 
-void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, const float *et,
+void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, int dk, const float *et,
                         const float *enorm, int ntiles, int *cand_idx, float *cand_lb, int *status,
                         cudaStream_t st, int nparts, float *part_v, int *part_i, const float *thr_init) {
     const bool wide = da > kMaxDA;
@@ -770,10 +792,10 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
     ProfScope ps(kProfSearchTopk, st, np > 1 ? 2 : 1);
     if (wide)
         k_search_pca<kMaxDAFast><<<dim3(grid, np), kThreads, smem, st>>>(
-            qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx, cand_lb, part_v, part_i, status, thr_init);
+            qcoord, qnorm, Q, da, dk, et, enorm, ntiles, tpp, cand_idx, cand_lb, part_v, part_i, status, thr_init);
     else
         k_search_pca<kMaxDA><<<dim3(grid, np), kThreads, smem, st>>>(
-            qcoord, qnorm, Q, da, et, enorm, ntiles, tpp, cand_idx, cand_lb, part_v, part_i, status, thr_init);
+            qcoord, qnorm, Q, da, dk, et, enorm, ntiles, tpp, cand_idx, cand_lb, part_v, part_i, status, thr_init);
     if (np > 1)
         k_merge_pca_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(part_v, part_i, np, Q, qnorm, cand_idx,
                                                                        cand_lb);
@@ -784,14 +806,14 @@ void launch_search_topk(const float *qcoord, const float *qnorm, int Q, int da, 
 // the count (adaptive_parts), then the part lists are merged (the merge returns at once when
 // there is one part).  part_v / part_i hold full_part_capacity(Q) entries.
 static void launch_full_adaptive(const float *qtiles, const int *list, const unsigned int *count, int Q, int Dp,
-                                 const float *etiles, const float *enorm, int ntiles, const float *qnorm,
+                                 int kvalid, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
                                  int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
                                  cudaStream_t st) {
     if (Q <= 0) return;
     const int grid = (int)std::min<long>((long)ceil_div((long)Q, kBQ) * kMaxAdaptiveParts, kAdaptiveGrid);
     k_search_full<<<grid, kThreads, sizeof(FullSmem), st>>>(qtiles, list, count, Q, Dp, etiles, enorm, ntiles, 0,
                                                             qnorm, cand_idx, cand_lb, part_v, part_i, status,
-                                                            Dp / kKC, nullptr, 1);
+                                                            Dp / kKC, nullptr, 1, kvalid);
     k_merge_fail_parts<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(
         part_v, part_i, ntiles, list, count, Q, qnorm, cand_idx, cand_lb, status);
 }
@@ -824,19 +846,19 @@ int launch_search_full(const float *X, int Wo, int C, int w, int stride, int qx,
         ProfScope ps(kProfSearchFull, st, 2);
         k_search_full<<<dim3(nqb, ntiles, nsplit), kThreads, smem, st>>>(
             qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles, 1, qnorm, cand_idx, cand_lb, part_v, part_i,
-            status, kcs, pdist->ptr, 0);
+            status, kcs, pdist->ptr, 0, C * w * w);
         k_full_select<<<ceil_div((long)Q * 32, 256), 256, 0, st>>>(pdist->ptr, nsplit, (int)npad, N, fail_list,
                                                                     fail_count, Q, qnorm, cand_idx, cand_lb, status);
         return nsplit;
     }
     ProfScope ps(kProfSearchFull, st, 2);
-    launch_full_adaptive(qfull, fail_list, fail_count, Q, Dp, efull, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v,
+    launch_full_adaptive(qfull, fail_list, fail_count, Q, Dp, C * w * w, efull, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v,
                          part_i, status, st);
     return 1;
 }
 
-void launch_search_rows(const float *rows, int da, const int *list, const unsigned int *count, int Q, int Dp,
-                        float *qtiles, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
+void launch_search_rows(const float *rows, int da, int dk, const int *list, const unsigned int *count, int Q,
+                        int Dp, float *qtiles, const float *etiles, const float *enorm, int ntiles, const float *qnorm,
                         int *cand_idx, float *cand_lb, float *part_v, int *part_i, int *status,
                         cudaStream_t st) {
     const size_t smem = sizeof(FullSmem);
@@ -844,7 +866,7 @@ void launch_search_rows(const float *rows, int da, const int *list, const unsign
     count_launches(1);
     k_gather_rows<<<152 * 4, 256, 0, st>>>(rows, da, list, count, Q, Dp, qtiles);
     ProfScope ps(kProfSearchTopk, st, 2);
-    launch_full_adaptive(qtiles, list, count, Q, Dp, etiles, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v, part_i,
+    launch_full_adaptive(qtiles, list, count, Q, Dp, dk, etiles, enorm, ntiles, qnorm, cand_idx, cand_lb, part_v, part_i,
                          status, st);
 }
 
