@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, DAM <= kMaxDA ? 2 : 1)
             acc[i][3] = nv.w;
         }
         const float *eb = &sm.e[buf][0][lane * 4];
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < dk; ++k) {
             const float4 a0 = *reinterpret_cast<const float4 *>(&sm.a[k][row0]);
             const float4 a1 = *reinterpret_cast<const float4 *>(&sm.a[k][row0 + 4]);
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // (adding 0 x 0 leaves every sum as it is)
         const int klen = min(kKC, kvalid - c * kKC);
         if (klen == kKC) {
-#pragma unroll 8
+#pragma unroll 4
             for (int k = 0; k < kKC; ++k) step(k);
         } else {
 #pragma unroll 4
