@@ -344,6 +344,29 @@ pts_status pts_project_queries(pts_index index, const float *output, int Ho, int
                                void *stream);
 
 /*
+ * pts_index_pca -- the index's PCA (section 2.2): mean_out (device, D float32) = mu, basis_out
+ * (device, d_fast x D float32, row-major) = the first d_fast unit eigenvectors, the basis every
+ * projection of the index uses.  Asynchronous; PTS_ERR_INVALID_ARG on a null argument.
+ */
+pts_status pts_index_pca(pts_index index, float *mean_out, float *basis_out, void *stream);
+
+/*
+ * pts_query_rows_f16 -- the rows the FP16 search (PTS_F16_RERANK) multiplies, for every query
+ * window of `output` (device Ho x Wo x C): row q = (y_q, r_q, 1, 1, 1, 0, ...) rounded to FP16,
+ * y_q = B^T (x_q - mu) the d_fast PCA coordinates, r_q = sqrt(max(0, ||u_q||^2 - ||y_q||^2)) the
+ * residual norm (section 2.2), the three ones against the exemplar's norm slots.
+ * tensor_cores  1: the projection the search runs (tcgen05, FP16 hi/lo split operands, FP32
+ *               accumulation); 0: the FP32 SIMT projection, for comparison.
+ * rows_out      device, Q x K FP16 values (IEEE binary16 bit patterns), row-major,
+ *               K = 16 * ceil((d_fast + 4) / 16).
+ * norm_out      device, Q float32: ||u_q||^2 = ||x_q - mu||^2.
+ * Asynchronous; uses workspace owned by the index.  PTS_ERR_INVALID_ARG on a null pointer or a
+ * grid the stride does not fit (as nn_search).
+ */
+pts_status pts_query_rows_f16(pts_index index, const float *output, int Ho, int Wo, int stride, int tensor_cores,
+                              uint16_t *rows_out, float *norm_out, void *stream);
+
+/*
  * pts_train_proposal -- builds the learned cluster proposal of PTS_PROPOSAL, which takes
  * the place of the paper's k-means search tree (section 2.2):
  *   1. k-means (k-means++ seeding, Lloyd) over the exemplar windows' PCA coordinates;

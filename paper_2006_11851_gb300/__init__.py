@@ -18,6 +18,7 @@ from ._binding import (  # noqa: F401
     gemm_selftest,
     histogram_match,
     index_load,
+    index_pca,
     index_save,
     irls_weights,
     kmeans,
@@ -33,6 +34,7 @@ from ._binding import (  # noqa: F401
     pca_fit,
     project_queries,
     proposal_info,
+    query_rows_f16,
     proposal_top4,
     rgb_of,
     rgbs,

@@ -114,6 +114,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 def _declare_optional(L: ctypes.CDLL) -> None:
     """Entry points of the learned proposal and the test-support self-tests."""
     L.pts_project_queries.argtypes = [_vp, _vp, _I, _I, _I, _vp, _vp]
+    L.pts_index_pca.argtypes = [_vp, _vp, _vp, _vp]
+    L.pts_query_rows_f16.argtypes = [_vp, _vp, _I, _I, _I, _I, _vp, _vp, _vp]
     L.pts_train_proposal.argtypes = [_vp, _vp, _vp, _vp, _I, ctypes.POINTER(_ProposalParams), _vp, _vp]
     L.pts_kmeans.argtypes = [_vp, _I, _I, _I, _vp, _I, _vp, _vp, ctypes.POINTER(_I), _vp]
     L.pts_mlp_grad.argtypes = [_I, _vp, _vp, _vp, _I, _vp, ctypes.POINTER(_Dd), _vp]
@@ -469,6 +471,28 @@ def project_queries(index: ExemplarIndex, output: torch.Tensor, stride: int = 2)
     y = torch.empty(index.num_queries(Ho, Wo, stride), index.d, device=output.device, dtype=torch.float32)
     _check(lib().pts_project_queries(index.handle, _ptr(output), Ho, Wo, stride, _ptr(y), _stream()))
     return y
+
+
+def index_pca(index: ExemplarIndex) -> tuple[torch.Tensor, torch.Tensor]:
+    """(mean [D], basis [d_fast, D]) of the index's PCA, float32 on its device."""
+    mean = torch.empty(index.D, device=index.device, dtype=torch.float32)
+    basis = torch.empty(index.info["d_fast"], index.D, device=index.device, dtype=torch.float32)
+    _check(lib().pts_index_pca(index.handle, _ptr(mean), _ptr(basis), _stream()))
+    return mean, basis
+
+
+def query_rows_f16(index: ExemplarIndex, output: torch.Tensor, stride: int = 2,
+                   tensor_cores: bool = True) -> tuple[torch.Tensor, torch.Tensor]:
+    """(rows [Q, K] float16, ||u||^2 [Q] float32): the FP16 search's query rows (y, r, 1, 1, 1,
+    0, ...), projected on the tensor cores (the search's own route) or by the FP32 SIMT kernel."""
+    Ho, Wo = _image_of(index, output)
+    Q = index.num_queries(Ho, Wo, stride)
+    K = (index.info["d_fast"] + 4 + 15) // 16 * 16
+    rows = torch.empty(Q, K, device=output.device, dtype=torch.float16)
+    norm = torch.empty(Q, device=output.device, dtype=torch.float32)
+    _check(lib().pts_query_rows_f16(index.handle, _ptr(output), Ho, Wo, stride, int(bool(tensor_cores)), _ptr(rows),
+                                    _ptr(norm), _stream()))
+    return rows, norm
 
 
 def train_proposal(index: ExemplarIndex, y: torch.Tensor, nn: torch.Tensor, d2: torch.Tensor, n_clusters: int = 1024,

@@ -285,6 +285,15 @@ float tcf_slack(int D) {
 
 // FP16 full-dimension tiles of the exemplar, built on the first PTS_EXACT_TC search (one
 // synchronisation); tcf_state -1 when they cannot be used
+// the FP16 hi/lo basis tiles of the tensor-core query projection, built on first use
+pts_status ensure_basis16(pts_index idx, cudaStream_t st) {
+    if (idx->basis16_ready) return PTS_OK;
+    PTS_TRY(idx->basis16.ensure(basis16_bytes(idx->D), "FP16 basis tiles"));
+    launch_pack_basis16(idx->basisT.ptr, idx->D, idx->d_fast, idx->basis16.ptr, st);
+    idx->basis16_ready = true;
+    return PTS_OK;
+}
+
 pts_status ensure_tcf_tiles(pts_index idx, cudaStream_t st) {
     if (idx->tcf_state != 0) return PTS_OK;
     if (!((double)idx->unorm2_max >= idx->D * std::ldexp(1.0, -21))) {
@@ -362,9 +371,10 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             Workspace &ws = idx->ws;
             // the projection writes the FP16 query tiles itself (no FP32 coordinates in between)
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * kTcQueryRows * idx->ktc, "query operand tiles"));
-            launch_project_tile16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast,
-                                  idx->ktc, ws.qtile.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st,
-                                  &ws.proj_part);
+            PTS_TRY(ensure_basis16(idx, st));
+            launch_project_tc16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basis16.ptr, idx->d_fast,
+                                idx->ktc, ws.qtile.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr,
+                                idx->status.ptr, st);
             const int ntc = tc_tiles(idx->N);
             // 0: automatic -- the default split rule, one part plus the tail split of launch_search_tc
             const int auto_parts = tc_parts(Q, ntc);
@@ -1151,6 +1161,39 @@ pts_status pts_project_queries(pts_index idx, const float *output, int Ho, int W
                    ws.qnorm.ptr, ws.tau.ptr, 0.0f, idx->umax.ptr, st);
     PTS_CUDA_TRY(cudaMemcpy2DAsync(y_out, sizeof(float) * idx->d, ws.qcoord.ptr, sizeof(float) * idx->da,
                                    sizeof(float) * idx->d, Q, cudaMemcpyDeviceToDevice, st));
+    return PTS_OK;
+}
+
+pts_status pts_index_pca(pts_index idx, float *mean_out, float *basis_out, void *stream) {
+    if (!idx || !mean_out || !basis_out) return set_error(PTS_ERR_INVALID_ARG, "pts_index_pca: null pointer");
+    cudaStream_t st = as_stream(stream);
+    PTS_CUDA_TRY(cudaMemcpyAsync(mean_out, idx->mu.ptr, sizeof(float) * idx->D, cudaMemcpyDeviceToDevice, st));
+    PTS_CUDA_TRY(cudaMemcpyAsync(basis_out, idx->basis.ptr, sizeof(float) * idx->D * idx->d_fast,
+                                 cudaMemcpyDeviceToDevice, st));
+    return PTS_OK;
+}
+
+pts_status pts_query_rows_f16(pts_index idx, const float *output, int Ho, int Wo, int stride, int tensor_cores,
+                              uint16_t *rows_out, float *norm_out, void *stream) {
+    if (!idx || !output || !rows_out || !norm_out)
+        return set_error(PTS_ERR_INVALID_ARG, "pts_query_rows_f16: null pointer");
+    PTS_TRY(check_grid(Ho, Wo, idx->w, stride, "pts_query_rows_f16"));
+    const int Q = ((Ho - idx->w) / stride + 1) * ((Wo - idx->w) / stride + 1);
+    PTS_TRY(ensure_workspace(idx, Q));
+    cudaStream_t st = as_stream(stream);
+    Workspace &ws = idx->ws;
+    PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * kTcQueryRows * idx->ktc, "query operand tiles"));
+    if (tensor_cores) {
+        PTS_TRY(ensure_basis16(idx, st));
+        launch_project_tc16(output, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basis16.ptr, idx->d_fast,
+                            idx->ktc, ws.qtile.ptr, norm_out, ws.tau.ptr, f16_slack(idx), idx->umax.ptr,
+                            idx->status.ptr, st);
+    } else {
+        launch_project_tile16(output, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast,
+                              idx->ktc, ws.qtile.ptr, norm_out, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st,
+                              &ws.proj_part);
+    }
+    launch_tile16_rows(ws.qtile.ptr, Q, idx->ktc, reinterpret_cast<__half *>(rows_out), st);
     return PTS_OK;
 }
 

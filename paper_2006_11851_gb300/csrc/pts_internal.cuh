@@ -226,6 +226,8 @@ struct pts_index_s {
     pts::DevBuf<float> f8scale;   // [d_fast + 1] per-dimension scales of the FP8 tiles
     int kf8 = 0;                  // K of the FP8 search
     int ktc = 0;                  // K of the tensor-core search
+    pts::DevBuf<unsigned char> basis16;  // the transposed basis' first d_fast rows as FP16 hi/lo tiles (project_tc.cu)
+    bool basis16_ready = false;
     pts::DevBuf<__half> efull16;  // [tcf_tiles(N)][256 x tcf_k(D)] FP16 full-dimension tiles (PTS_EXACT_TC)
     int tcf_state = 0;            // those tiles: 0 not built, 1 ready, -1 unusable (a value out of FP16 range)
     pts::DevBuf<float> umax;      // [1]
@@ -273,6 +275,16 @@ void launch_project(const float *img, int H, int W, int C, int w, int stride, co
 void launch_project_tile16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
                            const float *basisT, int d, int K, __half *qtile, float *out_norm, float *out_tau,
                            float tau_scale, const float *umax, cudaStream_t st, DevBuf<float> *scratch = nullptr);
+// project_tc.cu: the same outputs on the tensor cores (FP16 hi/lo split operands, FP32
+// accumulation; d <= 124, K <= 128), the basis prepacked once per index by launch_pack_basis16
+// (basis16_bytes(D) bytes)
+void launch_project_tc16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
+                         const unsigned char *basis16, int d, int K, __half *qtile, float *out_norm, float *out_tau,
+                         float tau_scale, const float *umax, int *status, cudaStream_t st);
+size_t basis16_bytes(int D);
+// the FP16 query tiles (Q rows of K, core-matrix layout) as row-major rows
+void launch_tile16_rows(const __half *qtile, int Q, int K, __half *rows, cudaStream_t st);
+void launch_pack_basis16(const float *basisT, int D, int d, unsigned char *basis16, cudaStream_t st);
 void launch_basis_transpose(const float *basis, int dcount, int D, float *basisT, cudaStream_t st);
 void launch_exemplar_pad(float *et, float *enorm, int N, int ntiles, int da, cudaStream_t st);
 void launch_norm_max(const float *norm, int n, float *out, cudaStream_t st);
