@@ -285,12 +285,24 @@ float tcf_slack(int D) {
 
 // FP16 full-dimension tiles of the exemplar, built on the first PTS_EXACT_TC search (one
 // synchronisation); tcf_state -1 when they cannot be used
-// the FP16 hi/lo basis tiles of the tensor-core query projection, built on first use
-pts_status ensure_basis16(pts_index idx, cudaStream_t st) {
-    if (idx->basis16_ready) return PTS_OK;
-    PTS_TRY(idx->basis16.ensure(basis16_bytes(idx->D), "FP16 basis tiles"));
-    launch_pack_basis16(idx->basisT.ptr, idx->D, idx->d_fast, idx->basis16.ptr, st);
-    idx->basis16_ready = true;
+// The FP16 search's query rows into ws.qtile, with ||u||^2 (norm) and tau: on the tensor cores
+// (their FP16 hi/lo basis tiles built on first use) unless asked otherwise or the image is past
+// the kernel's 32-bit offsets, else by the FP32 SIMT projection.
+pts_status project_f16_rows(pts_index idx, const float *X, int Ho, int Wo, int stride, int tensor_cores, float *norm,
+                            cudaStream_t st) {
+    Workspace &ws = idx->ws;
+    if (tensor_cores && project_tc16_fits(Ho, Wo, idx->C)) {
+        if (!idx->basis16_ready) {
+            PTS_TRY(idx->basis16.ensure(basis16_bytes(idx->D), "FP16 basis tiles"));
+            launch_pack_basis16(idx->basisT.ptr, idx->D, idx->d_fast, idx->basis16.ptr, st);
+            idx->basis16_ready = true;
+        }
+        launch_project_tc16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basis16.ptr, idx->d_fast, idx->ktc,
+                            ws.qtile.ptr, norm, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, idx->status.ptr, st);
+    } else {
+        launch_project_tile16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->ktc,
+                              ws.qtile.ptr, norm, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);
+    }
     return PTS_OK;
 }
 
@@ -371,10 +383,7 @@ pts_status nn_search_impl(pts_index idx, const float *X, int Ho, int Wo, int str
             Workspace &ws = idx->ws;
             // the projection writes the FP16 query tiles itself (no FP32 coordinates in between)
             PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * kTcQueryRows * idx->ktc, "query operand tiles"));
-            PTS_TRY(ensure_basis16(idx, st));
-            launch_project_tc16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basis16.ptr, idx->d_fast,
-                                idx->ktc, ws.qtile.ptr, ws.qnorm.ptr, ws.tau.ptr, f16_slack(idx), idx->umax.ptr,
-                                idx->status.ptr, st);
+            PTS_TRY(project_f16_rows(idx, X, Ho, Wo, stride, 1, ws.qnorm.ptr, st));
             const int ntc = tc_tiles(idx->N);
             // 0: automatic -- the default split rule, one part plus the tail split of launch_search_tc
             const int auto_parts = tc_parts(Q, ntc);
@@ -1183,16 +1192,7 @@ pts_status pts_query_rows_f16(pts_index idx, const float *output, int Ho, int Wo
     cudaStream_t st = as_stream(stream);
     Workspace &ws = idx->ws;
     PTS_TRY(ws.qtile.ensure((size_t)tc_query_blocks(Q) * kTcQueryRows * idx->ktc, "query operand tiles"));
-    if (tensor_cores) {
-        PTS_TRY(ensure_basis16(idx, st));
-        launch_project_tc16(output, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basis16.ptr, idx->d_fast,
-                            idx->ktc, ws.qtile.ptr, norm_out, ws.tau.ptr, f16_slack(idx), idx->umax.ptr,
-                            idx->status.ptr, st);
-    } else {
-        launch_project_tile16(output, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast,
-                              idx->ktc, ws.qtile.ptr, norm_out, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st,
-                              &ws.proj_part);
-    }
+    PTS_TRY(project_f16_rows(idx, output, Ho, Wo, stride, tensor_cores, norm_out, st));
     launch_tile16_rows(ws.qtile.ptr, Q, idx->ktc, reinterpret_cast<__half *>(rows_out), st);
     return PTS_OK;
 }

@@ -8,9 +8,11 @@
 // SIMT projection's FP16 layout (project.cu).
 //
 // The contraction runs on FP16 operands with FP32 accumulation, at close to FP32 accuracy: each
-// value x is split as x = x_hi + x_lo, x_hi = fp16(x), x_lo = fp16(x - x_hi) (22 significant
-// bits together), and u . b is accumulated as u_hi b_hi + u_lo b_hi + u_hi b_lo; every FP16
-// product is exact in FP32, and the dropped u_lo b_lo is about 2^-22 of |u b|.  The result is
+// value x is split as x = x_hi + x_lo with x_hi of 11 significant bits (exact in FP16) and x_lo
+// rounded to FP16 (22 significant bits together; the window side by Veltkamp's splitting in FP32,
+// t = 8193 x, x_hi = t - (t - x), the basis side by rounding, x_hi = fp16(x)), and u . b is
+// accumulated as u_hi b_hi + u_lo b_hi + u_hi b_lo; every FP16 product is exact in FP32, and the
+// dropped u_lo b_lo is about 2^-22 of |u b|.  The result is
 // rounded to FP16 for the search, so the split only has to keep the coordinates far more accurate
 // than that rounding.  Components past the FP16 range (|u_i| >= 65520) make the row non-finite,
 // as they would the FP16 query row itself.
@@ -68,20 +70,23 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// x = hi + lo with hi = fp16(x), lo = fp16(x - hi), for 8 values -> two 16-byte rows
+// x = hi + lo for 8 values -> two 16-byte rows: Veltkamp's splitting with factor 2^13 + 1 leaves
+// hi with 11 significant bits (exact in FP16 inside its normal range) and lo = x - hi exact in
+// FP32; the explicit roundings keep the compiler from fusing the steps
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
     float h[8], l[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        h[i] = __half2float(__float2half_rn(v[i]));
-        l[i] = v[i] - h[i];
+        const float t = __fmul_rn(v[i], 8193.0f);
+        h[i] = __fsub_rn(t, __fsub_rn(t, v[i]));
+        l[i] = __fsub_rn(v[i], h[i]);
     }
     hi = make_uint4(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]), pack_half2(h[4], h[5]), pack_half2(h[6], h[7]));
     lo = make_uint4(pack_half2(l[0], l[1]), pack_half2(l[2], l[3]), pack_half2(l[4], l[5]), pack_half2(l[6], l[7]));
 }
 
 __global__ void __launch_bounds__(kPThreads, 2)
-    k_project_tc(const float *__restrict__ img, int W, int C, int w, int stride, int qx_n, int Qn,
+    k_project_tc(const float *__restrict__ img, int img_vec, int W, int C, int w, int stride, int qx_n, int Qn,
                  const float *__restrict__ mu, const unsigned char *__restrict__ basis16, int d, int ktile,
                  __half *__restrict__ tile16, float *__restrict__ out_norm, float *__restrict__ out_tau,
                  float tau_scale, const float *__restrict__ umax, int *__restrict__ status) {
@@ -110,50 +115,118 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int r = tid & (kPR - 1), h = tid >> 7;
     const long q = q0 + r;
     const bool valid = q < Qn;
-    long base = 0;
+    int base = 0;
     if (valid) {
-        const long qy = q / qx_n, qx = q - qy * qx_n;
-        base = (qy * stride * (long)W + qx * stride) * C;
+        const int qy = (int)(q / qx_n), qx = (int)(q - (long)qy * qx_n);
+        base = (qy * stride * W + qx * stride) * C;
     }
     const float *const src = img + base;
+    // The two groups' first elements (offset e in their window row, image offset off), advanced
+    // 32 elements per chunk.  When the window row (C w floats) is a multiple of 8 long, a group
+    // never crosses a row: its 8 floats are contiguous, read as float4 or float2 where the
+    // window's and the rows' offsets allow, and the mean as two float4.
+    const bool rows8 = (row & 7) == 0;
+    const int vec = !rows8                                       ? 0
+                    : (((base | W3) & 3) == 0 && img_vec == 4)   ? 4
+                    : (((base | W3) & 1) == 0 && img_vec >= 2) ? 2
+                                                                 : 1;
+    int ge[2], goff[2];
+#pragma unroll
+    for (int gi = 0; gi < 2; ++gi) {
+        const int k = (h + 2 * gi) * 8, dy = k / row;
+        ge[gi] = k - dy * row;
+        goff[gi] = dy * W3 + ge[gi];
+    }
+    // raw image values of this thread's two groups of chunk c (zero past the vector or the image)
+    auto load_chunk = [&](int c, float (&v)[2][8]) {
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+            const int k0 = c * kPC + (h + 2 * gi) * 8;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[gi][i] = 0.0f;
+            if (valid && k0 < D) {
+                const float *p = src + goff[gi];
+                if (vec == 4) {
+                    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+                    const float4 b = __ldg(reinterpret_cast<const float4 *>(p + 4));
+                    v[gi][0] = a.x, v[gi][1] = a.y, v[gi][2] = a.z, v[gi][3] = a.w;
+                    v[gi][4] = b.x, v[gi][5] = b.y, v[gi][6] = b.z, v[gi][7] = b.w;
+                } else if (vec == 2) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 a = __ldg(reinterpret_cast<const float2 *>(p + 2 * i));
+                        v[gi][2 * i] = a.x, v[gi][2 * i + 1] = a.y;
+                    }
+                } else if (vec == 1) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[gi][i] = __ldg(p + i);
+                } else {  // the group may cross window rows and the vector's end
+                    int e = ge[gi], off = goff[gi];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (k0 + i < D) v[gi][i] = __ldg(src + off);
+                        if (++e == row) {
+                            e = 0;
+                            off += W3 - row + 1;
+                        } else {
+                            ++off;
+                        }
+                    }
+                }
+            }
+            // the same group of the next chunk, 32 elements on
+            int e = ge[gi] + kPC, off = goff[gi] + kPC;
+            while (e >= row) {
+                e -= row;
+                off += W3 - row;
+            }
+            ge[gi] = e;
+            goff[gi] = off;
+        }
+    };
+    auto issue_b = [&](int c, int s) {
+        mbar_expect_tx(&sm.b_full[s], 2 * kPTile);
+        bulk_g2s(sm.b[s][0], basis16 + (size_t)c * 2 * kPTile, 2 * kPTile, &sm.b_full[s]);
+    };
     const uint32_t idesc = idesc_f16(kPR, 128);
     float un = 0.0f;
     bool ok = true;
+    // Per chunk c (stage s = c % 2): the values of chunk c + 1 are loaded into registers while
+    // those of chunk c are centred, split and stored; thread 0 issues the MMAs of chunk c, then
+    // the basis copy of chunk c + 1 into the other stage once the MMAs of chunk c - 1 are done.
+    if (tid == 0) issue_b(0, 0);
+    float nv[2][8];
+    load_chunk(0, nv);
     for (int c = 0; c < nk; ++c) {
         const int s = c & 1;
         // the stage was last read by the MMAs of chunk c - 2
         if (c >= 2 && !mbar_wait_bounded(&sm.mma_done[s], (uint32_t)(((c - 2) >> 1) & 1), status)) ok = false;
-        if (tid == 0 && ok) {
-            mbar_expect_tx(&sm.b_full[s], 2 * kPTile);
-            bulk_g2s(sm.b[s][0], basis16 + (size_t)c * 2 * kPTile, 2 * kPTile, &sm.b_full[s]);
-        }
+        float v[2][8];
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[gi][i] = nv[gi][i];
+        if (c + 1 < nk) load_chunk(c + 1, nv);
 #pragma unroll
         for (int gi = 0; gi < 2; ++gi) {
             const int g = h + 2 * gi;
             const int k0 = c * kPC + g * 8;
-            float v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = 0.0f;
             if (valid && k0 < D) {
-                // element k of the window vector: row dy = k / (C w), offset e = k % (C w)
-                const int dy = k0 / row;
-                int e = k0 - dy * row;
-                long off = (long)dy * W3 + e;
+                if (rows8) {
+                    const float4 m0 = __ldg(reinterpret_cast<const float4 *>(mu + k0));
+                    const float4 m1 = __ldg(reinterpret_cast<const float4 *>(mu + k0 + 4));
+                    v[gi][0] -= m0.x, v[gi][1] -= m0.y, v[gi][2] -= m0.z, v[gi][3] -= m0.w;
+                    v[gi][4] -= m1.x, v[gi][5] -= m1.y, v[gi][6] -= m1.z, v[gi][7] -= m1.w;
+                } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (k0 + i < D) v[i] = __ldg(src + off) - __ldg(mu + k0 + i);
-                    if (++e == row) {
-                        e = 0;
-                        off += W3 - row + 1;
-                    } else {
-                        ++off;
-                    }
+                    for (int i = 0; i < 8; ++i)
+                        if (k0 + i < D) v[gi][i] -= __ldg(mu + k0 + i);
                 }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) un = fmaf(v[i], v[i], un);
+                for (int i = 0; i < 8; ++i) un = fmaf(v[gi][i], v[gi][i], un);
             }
             uint4 hi, lo;
-            split8(v, hi, lo);
+            split8(v[gi], hi, lo);
             const uint32_t o = core_offset(r, g * 8, kPR);
             *reinterpret_cast<uint4 *>(sm.a[s][0] + o) = hi;
             *reinterpret_cast<uint4 *>(sm.a[s][1] + o) = lo;
@@ -175,6 +248,11 @@ __global__ void __launch_bounds__(kPThreads, 2)
                     mma_bf16(tmem, smem_desc(ah + o, kPLbo, 128u), smem_desc(bl + o, kPLbo, 128u), idesc, 1u);
                 }
                 mma_commit(&sm.mma_done[s]);
+                if (c + 1 < nk) {
+                    // the other stage's basis slices were last read by the MMAs of chunk c - 1
+                    if (c >= 1) ok = mbar_wait_bounded(&sm.mma_done[s ^ 1], (uint32_t)(((c - 1) >> 1) & 1), status);
+                    if (ok) issue_b(c + 1, s ^ 1);
+                }
             }
         }
     }
@@ -277,9 +355,13 @@ void launch_pack_basis16(const float *basisT, int D, int d, unsigned char *basis
     k_pack_basis16<<<(unsigned)ceil_div((long)nk * kPR * kPC, 256), 256, 0, st>>>(basisT, D, d, nk, basis16);
 }
 
+bool project_tc16_fits(int H, int W, int C) { return (long)H * W * C < (1L << 31); }
+
 void launch_project_tc16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
                          const unsigned char *basis16, int d, int K, __half *qtile, float *out_norm, float *out_tau,
                          float tau_scale, const float *umax, int *status, cudaStream_t st) {
+    const uintptr_t ia = reinterpret_cast<uintptr_t>(img);
+    const int img_vec = ia % 16 == 0 ? 4 : (ia % 8 == 0 ? 2 : 1);  // widest load the image's base allows
     const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
     const long Qn = (long)qy_n * qx_n;
     if (Qn <= 0) return;
@@ -290,7 +372,8 @@ void launch_project_tc16(const float *img, int H, int W, int C, int w, int strid
     set_smem_attr(reinterpret_cast<const void *>(k_project_tc), (int)sizeof(ProjTcSmem));
     ProfScope ps(kProfProject, st, 1);
     k_project_tc<<<(unsigned)ceil_div(Qn, kPR), kPThreads, sizeof(ProjTcSmem), st>>>(
-        img, W, C, w, stride, qx_n, (int)Qn, mu, basis16, d, K, qtile, out_norm, out_tau, tau_scale, umax, status);
+        img, img_vec, W, C, w, stride, qx_n, (int)Qn, mu, basis16, d, K, qtile, out_norm, out_tau, tau_scale, umax,
+        status);
 }
 
 }  // namespace pts

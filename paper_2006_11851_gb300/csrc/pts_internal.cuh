@@ -282,6 +282,7 @@ void launch_project_tc16(const float *img, int H, int W, int C, int w, int strid
                          const unsigned char *basis16, int d, int K, __half *qtile, float *out_norm, float *out_tau,
                          float tau_scale, const float *umax, int *status, cudaStream_t st);
 size_t basis16_bytes(int D);
+bool project_tc16_fits(int H, int W, int C);  // image offsets within the kernel's 32-bit range
 // the FP16 query tiles (Q rows of K, core-matrix layout) as row-major rows
 void launch_tile16_rows(const __half *qtile, int Q, int K, __half *rows, cudaStream_t st);
 void launch_pack_basis16(const float *basisT, int D, int d, unsigned char *basis16, cudaStream_t st);
