@@ -298,7 +298,8 @@ pts_status project_f16_rows(pts_index idx, const float *X, int Ho, int Wo, int s
             idx->basis16_ready = true;
         }
         launch_project_tc16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basis16.ptr, idx->d_fast, idx->ktc,
-                            ws.qtile.ptr, norm, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, idx->status.ptr, st);
+                            ws.qtile.ptr, norm, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, idx->status.ptr, st,
+                            &ws.proj_part);
     } else {
         launch_project_tile16(X, Ho, Wo, idx->C, idx->w, stride, idx->mu.ptr, idx->basisT.ptr, idx->d_fast, idx->ktc,
                               ws.qtile.ptr, norm, ws.tau.ptr, f16_slack(idx), idx->umax.ptr, st, &ws.proj_part);

@@ -25,8 +25,13 @@
 // issues the 2 x 3 MMAs (K = 16) and commits them to the stage's mbarrier, which frees the stage
 // two chunks later.  The 128 x 128 FP32 accumulator stays in TMEM (128 columns); the epilogue
 // reads it with tcgen05.ld, warp w taking TMEM lanes 32 (w % 4) .. + 31 and columns
-// 64 (w / 4) .. + 63, and writes each row's FP16 values as 16-byte stores.
+// 64 (w / 4) .. + 63, and writes each row's FP16 values as 16-byte stores.  A grid of few query
+// blocks also splits the window vector into chunk ranges (blockIdx.y): each CTA then writes its
+// range's FP32 partial coordinates and ||u||^2, and k_project_tc_finish adds the ranges in order
+// and writes the rows.
 #include <math.h>
+
+#include <algorithm>
 
 #include "tc_common.cuh"
 
@@ -38,6 +43,7 @@ constexpr int kPC = 32;                             // window-vector elements pe
 constexpr int kPThreads = 256;
 constexpr uint32_t kPTile = kPR * kPC * 2;          // one 128 x 32 FP16 operand tile (8 KB)
 constexpr uint32_t kPLbo = (kPR / 8) * 128;         // bytes between core matrices adjacent along K
+constexpr int kPartRow = 132;                       // a window's partial sums: 128 coordinates, ||u||^2, padding
 
 struct ProjTcSmem {
     alignas(128) unsigned char a[2][2][kPTile];  // [stage][hi, lo] window slices
@@ -89,12 +95,15 @@ __global__ void __launch_bounds__(kPThreads, 2)
     k_project_tc(const float *__restrict__ img, int img_vec, int W, int C, int w, int stride, int qx_n, int Qn,
                  const float *__restrict__ mu, const unsigned char *__restrict__ basis16, int d, int ktile,
                  __half *__restrict__ tile16, float *__restrict__ out_norm, float *__restrict__ out_tau,
-                 float tau_scale, const float *__restrict__ umax, int *__restrict__ status) {
+                 float tau_scale, const float *__restrict__ umax, int *__restrict__ status, int kc_per,
+                 float *__restrict__ part) {
     extern __shared__ __align__(128) unsigned char ptc_raw[];
     ProjTcSmem &sm = *reinterpret_cast<ProjTcSmem *>(ptc_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = C * w, D = row * w, W3 = C * W;
-    const int nk = (D + kPC - 1) / kPC;
+    // this CTA's chunks of the window vector (blockIdx.y splits them when part is given)
+    const int c_begin = blockIdx.y * kc_per;
+    const int nk = min((D + kPC - 1) / kPC - c_begin, kc_per);
     const long q0 = (long)blockIdx.x * kPR;
     if (warp == 0) {
         tmem_alloc(&sm.tmem, 128);
@@ -133,38 +142,49 @@ __global__ void __launch_bounds__(kPThreads, 2)
     int ge[2], goff[2];
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
-        const int k = (h + 2 * gi) * 8, dy = k / row;
+        const int k = c_begin * kPC + (h + 2 * gi) * 8, dy = k / row;
         ge[gi] = k - dy * row;
         goff[gi] = dy * W3 + ge[gi];
     }
-    // raw image values of this thread's two groups of chunk c (zero past the vector or the image)
-    auto load_chunk = [&](int c, float (&v)[2][8]) {
+    const uint32_t idesc = idesc_f16(kPR, 128);
+    float un = 0.0f;
+    bool ok = true;
+    // chunk c of this CTA (absolute chunk c_begin + c) in stage s = c % 2
+    for (int c = 0; c < nk; ++c) {
+        const int s = c & 1;
+        // the stage was last read by the MMAs of chunk c - 2
+        if (c >= 2 && !mbar_wait_bounded(&sm.mma_done[s], (uint32_t)(((c - 2) >> 1) & 1), status)) ok = false;
+        if (tid == 0 && ok) {
+            mbar_expect_tx(&sm.b_full[s], 2 * kPTile);
+            bulk_g2s(sm.b[s][0], basis16 + (size_t)(c_begin + c) * 2 * kPTile, 2 * kPTile, &sm.b_full[s]);
+        }
 #pragma unroll
         for (int gi = 0; gi < 2; ++gi) {
-            const int k0 = c * kPC + (h + 2 * gi) * 8;
+            const int g = h + 2 * gi;
+            const int k0 = (c_begin + c) * kPC + g * 8;
+            float v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[gi][i] = 0.0f;
+            for (int i = 0; i < 8; ++i) v[i] = 0.0f;
             if (valid && k0 < D) {
                 const float *p = src + goff[gi];
                 if (vec == 4) {
                     const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
                     const float4 b = __ldg(reinterpret_cast<const float4 *>(p + 4));
-                    v[gi][0] = a.x, v[gi][1] = a.y, v[gi][2] = a.z, v[gi][3] = a.w;
-                    v[gi][4] = b.x, v[gi][5] = b.y, v[gi][6] = b.z, v[gi][7] = b.w;
+                    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
                 } else if (vec == 2) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float2 a = __ldg(reinterpret_cast<const float2 *>(p + 2 * i));
-                        v[gi][2 * i] = a.x, v[gi][2 * i + 1] = a.y;
+                        v[2 * i] = a.x, v[2 * i + 1] = a.y;
                     }
                 } else if (vec == 1) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) v[gi][i] = __ldg(p + i);
+                    for (int i = 0; i < 8; ++i) v[i] = __ldg(p + i);
                 } else {  // the group may cross window rows and the vector's end
                     int e = ge[gi], off = goff[gi];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        if (k0 + i < D) v[gi][i] = __ldg(src + off);
+                        if (k0 + i < D) v[i] = __ldg(src + off);
                         if (++e == row) {
                             e = 0;
                             off += W3 - row + 1;
@@ -173,6 +193,18 @@ __global__ void __launch_bounds__(kPThreads, 2)
                         }
                     }
                 }
+                if (rows8) {
+                    const float4 m0 = __ldg(reinterpret_cast<const float4 *>(mu + k0));
+                    const float4 m1 = __ldg(reinterpret_cast<const float4 *>(mu + k0 + 4));
+                    v[0] -= m0.x, v[1] -= m0.y, v[2] -= m0.z, v[3] -= m0.w;
+                    v[4] -= m1.x, v[5] -= m1.y, v[6] -= m1.z, v[7] -= m1.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (k0 + i < D) v[i] -= __ldg(mu + k0 + i);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) un = fmaf(v[i], v[i], un);
             }
             // the same group of the next chunk, 32 elements on
             int e = ge[gi] + kPC, off = goff[gi] + kPC;
@@ -182,51 +214,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
             }
             ge[gi] = e;
             goff[gi] = off;
-        }
-    };
-    auto issue_b = [&](int c, int s) {
-        mbar_expect_tx(&sm.b_full[s], 2 * kPTile);
-        bulk_g2s(sm.b[s][0], basis16 + (size_t)c * 2 * kPTile, 2 * kPTile, &sm.b_full[s]);
-    };
-    const uint32_t idesc = idesc_f16(kPR, 128);
-    float un = 0.0f;
-    bool ok = true;
-    // Per chunk c (stage s = c % 2): the values of chunk c + 1 are loaded into registers while
-    // those of chunk c are centred, split and stored; thread 0 issues the MMAs of chunk c, then
-    // the basis copy of chunk c + 1 into the other stage once the MMAs of chunk c - 1 are done.
-    if (tid == 0) issue_b(0, 0);
-    float nv[2][8];
-    load_chunk(0, nv);
-    for (int c = 0; c < nk; ++c) {
-        const int s = c & 1;
-        // the stage was last read by the MMAs of chunk c - 2
-        if (c >= 2 && !mbar_wait_bounded(&sm.mma_done[s], (uint32_t)(((c - 2) >> 1) & 1), status)) ok = false;
-        float v[2][8];
-#pragma unroll
-        for (int gi = 0; gi < 2; ++gi)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[gi][i] = nv[gi][i];
-        if (c + 1 < nk) load_chunk(c + 1, nv);
-#pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-            const int g = h + 2 * gi;
-            const int k0 = c * kPC + g * 8;
-            if (valid && k0 < D) {
-                if (rows8) {
-                    const float4 m0 = __ldg(reinterpret_cast<const float4 *>(mu + k0));
-                    const float4 m1 = __ldg(reinterpret_cast<const float4 *>(mu + k0 + 4));
-                    v[gi][0] -= m0.x, v[gi][1] -= m0.y, v[gi][2] -= m0.z, v[gi][3] -= m0.w;
-                    v[gi][4] -= m1.x, v[gi][5] -= m1.y, v[gi][6] -= m1.z, v[gi][7] -= m1.w;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (k0 + i < D) v[gi][i] -= __ldg(mu + k0 + i);
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) un = fmaf(v[gi][i], v[gi][i], un);
-            }
             uint4 hi, lo;
-            split8(v[gi], hi, lo);
+            split8(v, hi, lo);
             const uint32_t o = core_offset(r, g * 8, kPR);
             *reinterpret_cast<uint4 *>(sm.a[s][0] + o) = hi;
             *reinterpret_cast<uint4 *>(sm.a[s][1] + o) = lo;
@@ -248,11 +237,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
                     mma_bf16(tmem, smem_desc(ah + o, kPLbo, 128u), smem_desc(bl + o, kPLbo, 128u), idesc, 1u);
                 }
                 mma_commit(&sm.mma_done[s]);
-                if (c + 1 < nk) {
-                    // the other stage's basis slices were last read by the MMAs of chunk c - 1
-                    if (c >= 1) ok = mbar_wait_bounded(&sm.mma_done[s ^ 1], (uint32_t)(((c - 1) >> 1) & 1), status);
-                    if (ok) issue_b(c + 1, s ^ 1);
-                }
             }
         }
     }
@@ -267,6 +251,21 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int rr = quarter * 32 + lane;
     const long qq = q0 + rr;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
+    if (part) {
+        // split vector: this range's partial coordinates and ||u||^2, [y][q][kPartRow]
+        float *const pr = part + ((size_t)blockIdx.y * Qn + qq) * kPartRow;
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16) {
+            float v[16];
+            tmem_ld16w(taddr + (uint32_t)(c16 * 16), v);
+            if (qq < Qn && ok)
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4 *>(pr + half * 64 + c16 * 16 + j) =
+                        make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        if (qq < Qn && half == 0) pr[128] = sm.un[0][rr] + sm.un[1][rr];
+    } else {
     float yn = 0.0f;
 #pragma unroll
     for (int c16 = 0; c16 < 4; ++c16) {
@@ -305,6 +304,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
         out_norm[qq] = u2;
         out_tau[qq] = tau_scale * (u2 + *umax);
     }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -329,6 +329,45 @@ __global__ void k_pack_basis16(const float *__restrict__ basisT, int D, int d, i
     unsigned char *const tile = basis16 + (size_t)c * 2 * kPTile;
     *reinterpret_cast<__half *>(tile + core_offset(n, kk, kPR)) = bh;
     *reinterpret_cast<__half *>(tile + kPTile + core_offset(n, kk, kPR)) = bl;
+}
+
+// Sums the split ranges' partials of each window in range order (deterministic) and writes its
+// FP16 row, ||u||^2 and tau, one warp per window
+__global__ void __launch_bounds__(256) k_project_tc_finish(const float *__restrict__ part, int nsplit, int Qn, int d,
+                                                           int ktile, __half *__restrict__ tile16,
+                                                           float *__restrict__ out_norm, float *__restrict__ out_tau,
+                                                           float tau_scale, const float *__restrict__ umax) {
+    const int lane = threadIdx.x & 31;
+    const long q = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Qn) return;
+    float y[4], u2 = 0.0f, yn = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[i] = 0.0f;
+    for (int p = 0; p < nsplit; ++p) {
+        const float *pr = part + ((size_t)p * Qn + q) * kPartRow;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] += pr[lane + 32 * i];
+        u2 += pr[128];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (lane + 32 * i < d) yn = fmaf(y[i], y[i], yn);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) yn += __shfl_xor_sync(0xffffffffu, yn, o);
+    const float res = sqrtf(fmaxf(u2 - yn, 0.0f));
+    unsigned char *const t = reinterpret_cast<unsigned char *>(tile16 + (size_t)(q / kPR) * kPR * ktile);
+    const int rr = (int)(q % kPR);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int col = lane + 32 * i;
+        if (col >= ktile) continue;
+        const float v = col < d ? y[i] : (col == d ? res : (col <= d + 3 ? 1.0f : 0.0f));
+        *reinterpret_cast<__half *>(t + core_offset(rr, col, kPR)) = __float2half_rn(v);
+    }
+    if (lane == 0) {
+        out_norm[q] = u2;
+        out_tau[q] = tau_scale * (u2 + *umax);
+    }
 }
 
 __global__ void k_tile16_rows(const __half *__restrict__ qtile, int Q, int K, __half *__restrict__ rows) {
@@ -359,7 +398,7 @@ bool project_tc16_fits(int H, int W, int C) { return (long)H * W * C < (1L << 31
 
 void launch_project_tc16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
                          const unsigned char *basis16, int d, int K, __half *qtile, float *out_norm, float *out_tau,
-                         float tau_scale, const float *umax, int *status, cudaStream_t st) {
+                         float tau_scale, const float *umax, int *status, cudaStream_t st, DevBuf<float> *scratch) {
     const uintptr_t ia = reinterpret_cast<uintptr_t>(img);
     const int img_vec = ia % 16 == 0 ? 4 : (ia % 8 == 0 ? 2 : 1);  // widest load the image's base allows
     const int qy_n = (H - w) / stride + 1, qx_n = (W - w) / stride + 1;
@@ -369,11 +408,27 @@ void launch_project_tc16(const float *img, int H, int W, int C, int w, int strid
     if (Qn % kTcQueryRows)
         cudaMemsetAsync(qtile + (size_t)(Qn / kTcQueryRows) * kTcQueryRows * K, 0, sizeof(__half) * kTcQueryRows * K,
                         st);
+    // A grid of at most a quarter as many query blocks as SMs splits the window vector as well (at
+    // least 4 chunks a range, at most 8 ranges, about two CTAs per SM); the ranges' partial sums
+    // are added in range order by k_project_tc_finish.  (At 115 blocks a 2-way split measured
+    // slower than none: 35.1 against 33.0 us.)
+    const long nblk = ceil_div(Qn, kPR);
+    const int nk = ceil_div(C * w * w, kPC);
+    int nsplit = 1;
+    if (scratch && 4 * nblk <= 152)
+        nsplit = (int)std::max(1L, std::min<long>(std::min<long>(8, 2 * 152 / nblk), nk / 4));
+    if (nsplit > 1 && scratch->ensure((size_t)nsplit * Qn * kPartRow, "projection partials") != PTS_OK) nsplit = 1;
+    const int kc_per = ceil_div(nk, nsplit);
+    nsplit = ceil_div(nk, kc_per);
+    float *part = nsplit > 1 ? scratch->ptr : nullptr;
     set_smem_attr(reinterpret_cast<const void *>(k_project_tc), (int)sizeof(ProjTcSmem));
-    ProfScope ps(kProfProject, st, 1);
-    k_project_tc<<<(unsigned)ceil_div(Qn, kPR), kPThreads, sizeof(ProjTcSmem), st>>>(
+    ProfScope ps(kProfProject, st, nsplit > 1 ? 2 : 1);
+    k_project_tc<<<dim3((unsigned)nblk, (unsigned)nsplit), kPThreads, sizeof(ProjTcSmem), st>>>(
         img, img_vec, W, C, w, stride, qx_n, (int)Qn, mu, basis16, d, K, qtile, out_norm, out_tau, tau_scale, umax,
-        status);
+        status, kc_per, part);
+    if (nsplit > 1)
+        k_project_tc_finish<<<(unsigned)ceil_div(Qn * 32, 256), 256, 0, st>>>(part, nsplit, (int)Qn, d, K, qtile,
+                                                                              out_norm, out_tau, tau_scale, umax);
 }
 
 }  // namespace pts

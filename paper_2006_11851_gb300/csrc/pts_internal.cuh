@@ -280,7 +280,8 @@ void launch_project_tile16(const float *img, int H, int W, int C, int w, int str
 // (basis16_bytes(D) bytes)
 void launch_project_tc16(const float *img, int H, int W, int C, int w, int stride, const float *mu,
                          const unsigned char *basis16, int d, int K, __half *qtile, float *out_norm, float *out_tau,
-                         float tau_scale, const float *umax, int *status, cudaStream_t st);
+                         float tau_scale, const float *umax, int *status, cudaStream_t st,
+                         DevBuf<float> *scratch = nullptr);
 size_t basis16_bytes(int D);
 bool project_tc16_fits(int H, int W, int C);  // image offsets within the kernel's 32-bit range
 // the FP16 query tiles (Q rows of K, core-matrix layout) as row-major rows
