@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(kPThreads, 2)
     // chunk c of this CTA (absolute chunk c_begin + c) in stage s = c % 2
     for (int c = 0; c < nk; ++c) {
         const int s = c & 1;
-        // the stage was last read by the MMAs of chunk c - 2
-        if (c >= 2 && !mbar_wait_bounded(&sm.mma_done[s], (uint32_t)(((c - 2) >> 1) & 1), status)) ok = false;
+        // the stage was last read by the MMAs of chunk c - 2 (after a wait gave up, the thread
+        // waits no more: the status word already carries the timeout)
+        if (c >= 2 && ok && !mbar_wait_bounded(&sm.mma_done[s], (uint32_t)(((c - 2) >> 1) & 1), status)) ok = false;
         if (tid == 0 && ok) {
             mbar_expect_tx(&sm.b_full[s], 2 * kPTile);
             bulk_g2s(sm.b[s][0], basis16 + (size_t)(c_begin + c) * 2 * kPTile, 2 * kPTile, &sm.b_full[s]);
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     sm.un[h][r] = un;
     // the last chunk's commit covers every MMA issued before it
     const int last = nk - 1;
-    if (!mbar_wait_bounded(&sm.mma_done[last & 1], (uint32_t)((last >> 1) & 1), status)) ok = false;
+    if (ok && !mbar_wait_bounded(&sm.mma_done[last & 1], (uint32_t)((last >> 1) & 1), status)) ok = false;
     tc_fence_after();
     __syncthreads();
     // epilogue: the accumulator row of window rr, columns 64 half .. 64 half + 63
