@@ -9,7 +9,8 @@
 //
 // The contraction runs on FP16 operands with FP32 accumulation, at close to FP32 accuracy: each
 // value x is split as x = x_hi + x_lo with x_hi of 11 significant bits (exact in FP16) and x_lo
-// rounded to FP16 (22 significant bits together; the window side by Veltkamp's splitting in FP32,
+// rounded to FP16 (22 significant bits together, or an absolute 2^-25 below |x| = 2^-3, where x_lo
+// is an FP16 subnormal; the window side by Veltkamp's splitting in FP32,
 // t = 8193 x, x_hi = t - (t - x), the basis side by rounding, x_hi = fp16(x)), and u . b is
 // accumulated as u_hi b_hi + u_lo b_hi + u_hi b_lo; every FP16 product is exact in FP32, and the
 // dropped u_lo b_lo is about 2^-22 of |u b|.  The result is

@@ -6,9 +6,10 @@ Tolerances, from the arithmetic.  The tensor-core route splits every value into 
 parts (22 significant bits together) and accumulates u_hi b_hi + u_lo b_hi + u_hi b_lo in FP32, so
 a coordinate before its FP16 rounding is within e = 2^-17 ||u|| of the exact one (the dropped
 u_lo b_lo is about 2^-22 |u| |b| per term, the FP32 accumulation of 3 D products a few 2^-24
-||u||; 2^-17 leaves a wide margin).  Rounding to FP16 adds at most 2^-11 of the value, or 2^-25
-below the normal range.  A dropped split term (error near 2^-12 ||u||), a wrong basis row or a
-misplaced element fails the bound.  ||u||^2 is an FP32 sum of D positive terms: within
+||u||; 2^-17 leaves a wide margin; tests/test_split_arith.py checks the split's arithmetic).
+Rounding to FP16 adds at most 2^-11 of the value, or 2^-25 below the normal range.  A dropped
+split term (about 2^-12.8 ||u|| / sqrt(D) per coordinate, several times the bound at the largest
+of the coordinates), a wrong basis row or a misplaced element fails the bound.  ||u||^2 is an FP32 sum of D positive terms: within
 (D + 4) 2^-24 of itself.  The residual's square is a difference of two sums that each carry
 errors near 2^-12 ||u||^2 at most, then rounded to FP16 (2^-10 relative in the square)."""
 import numpy as np
